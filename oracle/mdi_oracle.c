@@ -1,0 +1,629 @@
+/*
+ * mdi_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, obviously-correct CPU implementation in FP64 of what the MDI-LR
+ * hot path computes (Zhong & Feng, "An efficient implementation algorithm for
+ * quasi-Monte Carlo approximations of high-dimensional integrals").  Only the
+ * test-suite, the smoke check and the CPU-baseline leg of the benchmark may load
+ * this file's library.  The product path (the CUDA library) shares no code,
+ * header, table or constant with it, and neither includes the other.
+ *
+ * Every function names the passage of the paper it follows.  No blocking, no
+ * fusion, no reordering beyond what the definition states: sums run in index
+ * order, in double precision, with unsigned __int128 for lattice indices.
+ *
+ * Integrand families (oracle-local numbering).  Product-form ones carry per-axis
+ * parameters c[0..d) and w[0..d):
+ *   OR_EXP   f(x) = exp(sum_j c_j x_j)                phi_j(x) = exp(c_j x)
+ *   OR_OSC   f(x) = cos(2 pi u + sum_j c_j x_j)       phi_j(x) = exp(i c_j x), u = w[0],
+ *            f = Re(exp(2 pi i u) prod_j phi_j)
+ *   OR_GAUSS f(x) = exp(-sum_j c_j^2 (x_j - w_j)^2)   phi_j(x) = exp(-c_j^2 (x - w_j)^2)
+ *   OR_PEAK  f(x) = prod_j (c_j^-2 + (x_j - w_j)^2)^-1
+ * Non-product integrands of the paper's tests (brute-force rules only):
+ *   OR_T1    f(x) = x_2 exp(x_1 x_2) / (e - 2)        (Test 1, d = 2)
+ *   OR_SINSQ f(x) = sin(2 pi + sum_j x_j^2)           (Tests 1-2)
+ *   OR_ALTSQ f(x) = exp(sum_j (-1)^(j+1) x_j^2)       (Test 7, f_5)
+ *   OR_RIDGE f(x) = (1 + sum_j x_j)^-(d+1)            (Test 7, f_6)
+ *
+ * Parity status.  Every function is pinned by tests/test_oracle_pins.py against
+ * values the paper prints, closed forms, identities the paper states, or brute
+ * force; see the pin list in that file.  The node-state sweep or_mdi_nodes is an
+ * approximation the paper does not spell out (it leaves the representation of
+ * its "symbolic functions" open); it is pinned against the exact sweep on cases
+ * small enough to enumerate and against closed forms, and beyond those sizes only
+ * through invariants.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+enum {
+  OR_EXP = 0, OR_OSC = 1, OR_GAUSS = 2, OR_PEAK = 3,
+  OR_T1 = 10, OR_SINSQ = 11, OR_ALTSQ = 12, OR_RIDGE = 13
+};
+
+typedef unsigned __int128 u128;
+typedef double complex cplx;
+
+/* ------------------------------------------------------------------------- */
+/* Integer lattice arithmetic                                                 */
+/* ------------------------------------------------------------------------- */
+
+static uint64_t mulmod(uint64_t x, uint64_t y, uint64_t n) {
+  return (uint64_t)(((u128)x * (u128)y) % (u128)n);
+}
+
+/* Korobov generating vector z(a) = (1, a, a^2, ..., a^(d-1)) mod n
+ * (Section 2.2, Example 2 "Korobov lattice"). */
+int or_korobov_z(int d, uint64_t a, uint64_t n, uint64_t *z) {
+  if (d < 1 || n < 1) return -1;
+  uint64_t v = 1 % n;
+  for (int i = 0; i < d; ++i) {
+    z[i] = v;
+    v = mulmod(v, a % n, n);
+  }
+  return 0;
+}
+
+/* Lattice indices r_{j,i} = j z_i mod n for j = j0 .. j0+count-1, row-major
+ * (count, d): the integer numerators of x_j = {j z / n}, eq. (2.1). */
+int or_lattice_indices(int d, uint64_t n, const uint64_t *z, uint64_t j0, uint64_t count,
+                       uint64_t *r_out) {
+  if (d < 1 || n < 1) return -1;
+  for (uint64_t t = 0; t < count; ++t)
+    for (int i = 0; i < d; ++i) r_out[t * (uint64_t)d + i] = mulmod((j0 + t) % n, z[i] % n, n);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Integrands, evaluated directly from their definitions                      */
+/* ------------------------------------------------------------------------- */
+
+static double f_eval(int fam, int d, const double *x, const double *c, const double *w) {
+  double s = 0.0, p = 1.0;
+  switch (fam) {
+    case OR_EXP:
+      for (int j = 0; j < d; ++j) s += c[j] * x[j];
+      return exp(s);
+    case OR_OSC:
+      for (int j = 0; j < d; ++j) s += c[j] * x[j];
+      return cos(2.0 * M_PI * w[0] + s);
+    case OR_GAUSS:
+      for (int j = 0; j < d; ++j) s += c[j] * c[j] * (x[j] - w[j]) * (x[j] - w[j]);
+      return exp(-s);
+    case OR_PEAK:
+      for (int j = 0; j < d; ++j) p *= 1.0 / (1.0 / (c[j] * c[j]) + (x[j] - w[j]) * (x[j] - w[j]));
+      return p;
+    case OR_T1:
+      return x[1] * exp(x[0] * x[1]) / (M_E - 2.0);
+    case OR_SINSQ:
+      for (int j = 0; j < d; ++j) s += x[j] * x[j];
+      return sin(2.0 * M_PI + s);
+    case OR_ALTSQ:
+      for (int j = 0; j < d; ++j) s += ((j % 2 == 0) ? 1.0 : -1.0) * x[j] * x[j];
+      return exp(s);
+    case OR_RIDGE:
+      for (int j = 0; j < d; ++j) s += x[j];
+      return pow(1.0 + s, -(double)(d + 1));
+  }
+  return NAN;
+}
+
+/* One-dimensional factor phi_j of a product-form integrand (complex for OR_OSC). */
+static cplx phi(int fam, int j, double x, const double *c, const double *w) {
+  switch (fam) {
+    case OR_EXP: return exp(c[j] * x);
+    case OR_OSC: return cexp(I * c[j] * x);
+    case OR_GAUSS: return exp(-c[j] * c[j] * (x - w[j]) * (x - w[j]));
+    case OR_PEAK: return 1.0 / (1.0 / (c[j] * c[j]) + (x - w[j]) * (x - w[j]));
+  }
+  return NAN;
+}
+
+/* Derivatives of phi_j with respect to c_j (which = 0) and w_j (which = 1). */
+static cplx dphi(int fam, int j, int which, double x, const double *c, const double *w) {
+  double cj = c[j], dx = x - w[j];
+  switch (fam) {
+    case OR_EXP: return which == 0 ? x * exp(cj * x) : 0.0;
+    case OR_OSC: return which == 0 ? I * x * cexp(I * cj * x) : 0.0;
+    case OR_GAUSS: {
+      double e = exp(-cj * cj * dx * dx);
+      return which == 0 ? -2.0 * cj * dx * dx * e : 2.0 * cj * cj * dx * e;
+    }
+    case OR_PEAK: {
+      double D = 1.0 / (cj * cj) + dx * dx;
+      return which == 0 ? (2.0 / (cj * cj * cj)) / (D * D) : (2.0 * dx) / (D * D);
+    }
+  }
+  return NAN;
+}
+
+static int is_product(int fam) { return fam >= OR_EXP && fam <= OR_PEAK; }
+
+/* Constant factor in front of the product: exp(2 pi i u) for OR_OSC, else 1. */
+static cplx front(int fam, const double *w) {
+  return fam == OR_OSC ? cexp(I * 2.0 * M_PI * w[0]) : 1.0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Standard lattice rule, eq. (1.2) with the points of eq. (2.1)              */
+/* ------------------------------------------------------------------------- */
+
+/* Q = (1/n) sum_{j<n} f({j z / n}); coordinates are (j z_i mod n) / n computed in
+ * exact 128-bit integer arithmetic and one FP64 division each. */
+double or_slr(int fam, int d, uint64_t n, const uint64_t *z, const double *c, const double *w) {
+  double *x = (double *)malloc(sizeof(double) * (size_t)d);
+  double sum = 0.0;
+  for (uint64_t j = 0; j < n; ++j) {
+    for (int i = 0; i < d; ++i) x[i] = (double)mulmod(j, z[i] % n, n) / (double)n;
+    sum += f_eval(fam, d, x, c, w);
+  }
+  free(x);
+  return sum / (double)n;
+}
+
+/* Derivative of the rule with respect to c_k (grad[k]) and w_k (grad[d+k]) for the
+ * product-form families; for OR_OSC grad[d] is d/du.  Plain definition:
+ * (1/n) sum_j df(x_j)/dtheta, with the analytic derivative of the integrand. */
+int or_slr_grad(int fam, int d, uint64_t n, const uint64_t *z, const double *c, const double *w,
+                double *grad) {
+  if (!is_product(fam)) return -1;
+  double *x = (double *)malloc(sizeof(double) * (size_t)d);
+  for (int k = 0; k < 2 * d; ++k) grad[k] = 0.0;
+  for (uint64_t j = 0; j < n; ++j) {
+    for (int i = 0; i < d; ++i) x[i] = (double)mulmod(j, z[i] % n, n) / (double)n;
+    double f = f_eval(fam, d, x, c, w);
+    if (fam == OR_OSC) {
+      double s = 0.0;
+      for (int i = 0; i < d; ++i) s += c[i] * x[i];
+      double sn = sin(2.0 * M_PI * w[0] + s);
+      for (int k = 0; k < d; ++k) grad[k] += -sn * x[k];
+      grad[d] += -2.0 * M_PI * sn;
+    } else {
+      for (int k = 0; k < d; ++k) {
+        double dx = x[k] - w[k], ck = c[k];
+        if (fam == OR_EXP) {
+          grad[k] += f * x[k];
+        } else if (fam == OR_GAUSS) {
+          grad[k] += f * (-2.0 * ck * dx * dx);
+          grad[d + k] += f * (2.0 * ck * ck * dx);
+        } else { /* OR_PEAK: f / D_k * (-dD_k/dtheta) */
+          double D = 1.0 / (ck * ck) + dx * dx;
+          grad[k] += f * (2.0 / (ck * ck * ck)) / D;
+          grad[d + k] += f * (2.0 * dx) / D;
+        }
+      }
+    }
+  }
+  for (int k = 0; k < 2 * d; ++k) grad[k] /= (double)n;
+  free(x);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Affine transformation of Theorem 3.1 and grid sizes of eq. (3.5)           */
+/* ------------------------------------------------------------------------- */
+
+static uint64_t gcd_u64(uint64_t x, uint64_t y) {
+  while (y) { uint64_t t = x % y; x = y; y = t; }
+  return x;
+}
+
+/* n_i = lcm(z_i, z_{i+1}) / min(z_i, z_{i+1}) for i < d, n_d = ceil(n / z_d), eq. (3.5). */
+int or_grid_sizes(int d, uint64_t n, const uint64_t *z, uint64_t *Nd) {
+  for (int i = 0; i + 1 < d; ++i) {
+    uint64_t lo = z[i] < z[i + 1] ? z[i] : z[i + 1];
+    uint64_t l = (z[i] / gcd_u64(z[i], z[i + 1])) * z[i + 1];
+    Nd[i] = l / lo;
+  }
+  Nd[d - 1] = (n + z[d - 1] - 1) / z[d - 1];
+  return 0;
+}
+
+/* y_j = abs(A x_j + b) for the points j = 0..n-1, eq. (3.1): row i < d gives
+ * x_i / z_i - x_{i+1} / z_{i+1}; the last row gives x_d + b_d with
+ * b_d = -{n x_d / z_d} z_d / n, evaluated from the exact integer r_d = j z_d mod n. */
+int or_affine_y(int d, uint64_t n, const uint64_t *z, double *y_out) {
+  double *x = (double *)malloc(sizeof(double) * (size_t)d);
+  for (uint64_t j = 0; j < n; ++j) {
+    for (int i = 0; i < d; ++i) x[i] = (double)mulmod(j, z[i] % n, n) / (double)n;
+    for (int i = 0; i + 1 < d; ++i)
+      y_out[j * (uint64_t)d + i] = fabs(x[i] / (double)z[i] - x[i + 1] / (double)z[i + 1]);
+    uint64_t rd = mulmod(j, z[d - 1] % n, n);
+    double bd = -(double)(rd % z[d - 1]) / (double)n;
+    y_out[j * (uint64_t)d + d - 1] = fabs(x[d - 1] + bd);
+  }
+  free(x);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The improved rule on the transformed grid, brute force (Lemma 3.2, eq. 4.3) */
+/* ------------------------------------------------------------------------- */
+
+/* For the Korobov vector z = (1, a, ..., a^(d-1)) and n = nd a^(d-1), Lemma 3.2
+ * gives the axis sets y_i in {0, 1/a^i, ..., (a-1)/a^i} (i < d) and
+ * y_d in {0, a^(d-1)/n, ..., (n - a^(d-1))/n}.  Every grid point is mapped back by
+ * x = A^{-1}(y - b) (b = 0 on this grid), i.e. x_d = y_d and
+ * x_i = z_i (y_i + x_{i+1} / z_{i+1}), and the rule averages f over the
+ * prod n_i = n grid points with weight 1 / prod n_i.  Requires n <= 2^40. */
+double or_grid_korobov(int fam, int d, uint64_t a, uint64_t nd, const double *c, const double *w) {
+  uint64_t npts = nd;
+  for (int i = 1; i < d; ++i) npts *= a;
+  double *zf = (double *)malloc(sizeof(double) * (size_t)d);
+  double *x = (double *)malloc(sizeof(double) * (size_t)d);
+  uint64_t *s = (uint64_t *)calloc((size_t)d, sizeof(uint64_t));
+  double ai = 1.0, n = (double)npts, sum = 0.0;
+  for (int i = 0; i < d; ++i) { zf[i] = ai; ai *= (double)a; }
+  for (uint64_t t = 0; t < npts; ++t) {
+    /* digits: s[0..d-2] in [0,a), s[d-1] in [0,nd); s[0] fastest */
+    uint64_t rem = t;
+    for (int i = 0; i + 1 < d; ++i) { s[i] = rem % a; rem /= a; }
+    s[d - 1] = rem;
+    x[d - 1] = (double)s[d - 1] * zf[d - 1] / n;
+    for (int i = d - 2; i >= 0; --i) {
+      double yi = (double)s[i] / (zf[i] * (double)a); /* s_i / a^(i+1) in 1-based terms */
+      x[i] = zf[i] * (yi + x[i + 1] / zf[i + 1]);
+    }
+    sum += f_eval(fam, d, x, c, w);
+  }
+  free(zf); free(x); free(s);
+  return sum / n;
+}
+
+/* ------------------------------------------------------------------------- */
+/* MDI sweeps (Algorithm 1 with m = 1 inside Algorithm 2)                     */
+/* ------------------------------------------------------------------------- */
+/*
+ * Notation.  Level k = 1..d contracts transformed coordinate k (the first
+ * remaining one, Algorithm 1 deletes the first m = 1 components per pass).  The
+ * cluster of level k around a parent value x (the original coordinate x_{k+1})
+ * is u = (q + x) / r_k, q = 0..r_k-1, with r_k = a for k < d and r_d = nd (the
+ * last axis, whose parent is x_{d+1} = 0).  The state after level k is
+ *     G_k(x) = (1/r_k) sum_q phi_k(u) G_{k-1}(u),   G_0 = 1,
+ * which is eq. (4.4) with equal weights; the rule is front * G_d.
+ */
+
+/* (E) Exact level tables: G_k is kept at every parent the lattice needs,
+ * x = m / M_k, M_k = M_{k-1} / r_k, M_0 = n.  Requires n <= 2^32. */
+double or_mdi_exact(int fam, int d, uint64_t a, uint64_t nd, const double *c, const double *w) {
+  if (!is_product(fam)) return NAN;
+  uint64_t M = nd;
+  for (int i = 1; i < d; ++i) M *= a;
+  cplx *G = (cplx *)malloc(sizeof(cplx) * (size_t)M);
+  for (uint64_t m = 0; m < M; ++m) G[m] = 1.0;
+  for (int k = 1; k <= d; ++k) {
+    uint64_t r = (k < d) ? a : nd, Mk = M / r;
+    cplx *H = (cplx *)malloc(sizeof(cplx) * (size_t)Mk);
+    for (uint64_t m = 0; m < Mk; ++m) {
+      cplx acc = 0.0;
+      for (uint64_t q = 0; q < r; ++q) {
+        uint64_t idx = q * Mk + m;
+        acc += phi(fam, k - 1, (double)idx / (double)M, c, w) * G[idx];
+      }
+      H[m] = acc / (double)r;
+    }
+    free(G);
+    G = H;
+    M = Mk;
+  }
+  double out = creal(front(fam, w) * G[0]);
+  free(G);
+  return out;
+}
+
+/* (C) Closed state for the exponential families: G_k(x) = K_k exp(beta_k x).
+ * Substituting into the level recursion gives gamma_k = beta_{k-1} + c_k (times i
+ * for OR_OSC), K_k = K_{k-1} (1/r_k) sum_q exp(gamma_k q / r_k), beta_k = gamma_k / r_k. */
+double or_mdi_closed(int fam, int d, uint64_t a, uint64_t nd, const double *c, const double *w) {
+  if (fam != OR_EXP && fam != OR_OSC) return NAN;
+  cplx beta = 0.0, K = 1.0;
+  for (int k = 1; k <= d; ++k) {
+    double r = (double)((k < d) ? a : nd);
+    cplx ck = (fam == OR_OSC) ? I * c[k - 1] : c[k - 1];
+    cplx gamma = beta + ck, S = 0.0;
+    for (uint64_t q = 0; q < (uint64_t)r; ++q) S += cexp(gamma * (double)q / r);
+    K *= S / r;
+    beta = gamma / r;
+  }
+  return creal(front(fam, w) * K);
+}
+
+/* Forward-mode derivative of the closed-state sweep: grad[k] = dQ/dc_k, and for
+ * OR_OSC grad[d] = dQ/du.  Each tangent is carried through the same recursion. */
+int or_mdi_closed_grad(int fam, int d, uint64_t a, uint64_t nd, const double *c, const double *w,
+                       double *grad) {
+  if (fam != OR_EXP && fam != OR_OSC) return -1;
+  for (int k = 0; k < 2 * d; ++k) grad[k] = 0.0;
+  for (int t = 0; t < d; ++t) {
+    cplx beta = 0.0, K = 1.0, dbeta = 0.0, dK = 0.0;
+    for (int k = 1; k <= d; ++k) {
+      double r = (double)((k < d) ? a : nd);
+      cplx ck = (fam == OR_OSC) ? I * c[k - 1] : c[k - 1];
+      cplx dck = (k - 1 == t) ? ((fam == OR_OSC) ? I : 1.0) : 0.0;
+      cplx gamma = beta + ck, dgamma = dbeta + dck, S = 0.0, dS = 0.0;
+      for (uint64_t q = 0; q < (uint64_t)r; ++q) {
+        cplx e = cexp(gamma * (double)q / r);
+        S += e;
+        dS += e * dgamma * (double)q / r;
+      }
+      dK = dK * (S / r) + K * (dS / r);
+      K *= S / r;
+      beta = gamma / r;
+      dbeta = dgamma / r;
+    }
+    grad[t] = creal(front(fam, w) * dK);
+    if (fam == OR_OSC && t == 0) grad[d] = creal(2.0 * M_PI * I * front(fam, w) * K);
+  }
+  return 0;
+}
+
+/* (S) Node state: G_k is kept at P Chebyshev points of the first kind on [0,1],
+ * xi_p = (1 + cos(pi (2p+1) / (2P))) / 2, and read between them by the barycentric
+ * formula of the second kind with weights (-1)^p sin(pi (2p+1) / (2P))
+ * (Berrut & Trefethen, SIAM Review 46 (2004), eq. 4.2 and Sec. 5). */
+static void cheb_nodes(int P, double *xi, double *bw) {
+  for (int p = 0; p < P; ++p) {
+    double th = M_PI * (2.0 * p + 1.0) / (2.0 * P);
+    xi[p] = 0.5 * (1.0 + cos(th));
+    bw[p] = ((p % 2 == 0) ? 1.0 : -1.0) * sin(th);
+  }
+}
+
+static cplx bary(int P, const double *xi, const double *bw, const cplx *G, double u) {
+  cplx num = 0.0;
+  double den = 0.0;
+  for (int p = 0; p < P; ++p) {
+    if (u == xi[p]) return G[p];
+    double t = bw[p] / (u - xi[p]);
+    num += t * G[p];
+    den += t;
+  }
+  return num / den;
+}
+
+/* Barycentric basis value l_p(u) (the weight of node p when reading at u). */
+static double bary_basis(int P, const double *xi, const double *bw, int p, double u) {
+  double den = 0.0;
+  for (int t = 0; t < P; ++t) {
+    if (u == xi[t]) return t == p ? 1.0 : 0.0;
+    den += bw[t] / (u - xi[t]);
+  }
+  return (bw[p] / (u - xi[p])) / den;
+}
+
+/* Node-state sweep; states_out (optional, (d+1) x P complex as 2 doubles) receives
+ * G_0 .. G_{d-1} at the nodes and G_d in slot [d][0]. */
+static cplx mdi_nodes_core(int fam, int d, uint64_t a, uint64_t nd, int P, const double *c,
+                           const double *w, double *states_out) {
+  double *xi = (double *)malloc(sizeof(double) * (size_t)P);
+  double *bw = (double *)malloc(sizeof(double) * (size_t)P);
+  cplx *G = (cplx *)malloc(sizeof(cplx) * (size_t)P);
+  cplx *H = (cplx *)malloc(sizeof(cplx) * (size_t)P);
+  cheb_nodes(P, xi, bw);
+  for (int p = 0; p < P; ++p) G[p] = 1.0;
+  for (int k = 1; k < d; ++k) {
+    if (states_out)
+      for (int p = 0; p < P; ++p) {
+        states_out[2 * ((size_t)(k - 1) * P + p)] = creal(G[p]);
+        states_out[2 * ((size_t)(k - 1) * P + p) + 1] = cimag(G[p]);
+      }
+    for (int p = 0; p < P; ++p) {
+      cplx acc = 0.0;
+      for (uint64_t q = 0; q < a; ++q) {
+        double u = ((double)q + xi[p]) / (double)a;
+        acc += phi(fam, k - 1, u, c, w) * bary(P, xi, bw, G, u);
+      }
+      H[p] = acc / (double)a;
+    }
+    memcpy(G, H, sizeof(cplx) * (size_t)P);
+  }
+  if (states_out)
+    for (int p = 0; p < P; ++p) {
+      states_out[2 * ((size_t)(d - 1) * P + p)] = creal(G[p]);
+      states_out[2 * ((size_t)(d - 1) * P + p) + 1] = cimag(G[p]);
+    }
+  cplx acc = 0.0;
+  for (uint64_t s = 0; s < nd; ++s) {
+    double u = (double)s / (double)nd;
+    acc += phi(fam, d - 1, u, c, w) * (d > 1 ? bary(P, xi, bw, G, u) : 1.0);
+  }
+  acc /= (double)nd;
+  if (states_out) {
+    states_out[2 * (size_t)d * P] = creal(acc);
+    states_out[2 * (size_t)d * P + 1] = cimag(acc);
+  }
+  free(xi); free(bw); free(G); free(H);
+  return acc;
+}
+
+double or_mdi_nodes(int fam, int d, uint64_t a, uint64_t nd, int P, const double *c,
+                    const double *w) {
+  if (!is_product(fam) || P < 2) return NAN;
+  return creal(front(fam, w) * mdi_nodes_core(fam, d, a, nd, P, c, w, NULL));
+}
+
+/* States of the node sweep, for checking the device's level states and checkpoints. */
+int or_mdi_nodes_states(int fam, int d, uint64_t a, uint64_t nd, int P, const double *c,
+                        const double *w, double *states_out) {
+  if (!is_product(fam) || P < 2) return -1;
+  mdi_nodes_core(fam, d, a, nd, P, c, w, states_out);
+  return 0;
+}
+
+/* Forward-mode derivative of the node-state sweep with respect to c_t and w_t for
+ * the parameters t listed in which[0..nwhich) (indices into the 2d-long gradient:
+ * t < d is c_t, t >= d is w_{t-d}; for OR_OSC index d is u).  The tangent Gdot is
+ * zero below the level of the parameter, picks up the derivative of phi there,
+ * and is carried through the later levels by the same (linear) recursion. */
+int or_mdi_nodes_grad(int fam, int d, uint64_t a, uint64_t nd, int P, const double *c,
+                      const double *w, const int *which, int nwhich, double *grad_out) {
+  if (!is_product(fam) || P < 2) return -1;
+  double *xi = (double *)malloc(sizeof(double) * (size_t)P);
+  double *bw = (double *)malloc(sizeof(double) * (size_t)P);
+  cplx *G = (cplx *)malloc(sizeof(cplx) * (size_t)P), *H = (cplx *)malloc(sizeof(cplx) * (size_t)P);
+  cplx *Gd = (cplx *)malloc(sizeof(cplx) * (size_t)P), *Hd = (cplx *)malloc(sizeof(cplx) * (size_t)P);
+  cheb_nodes(P, xi, bw);
+  for (int iw = 0; iw < nwhich; ++iw) {
+    int t = which[iw];
+    if (fam == OR_OSC && t == d) {
+      cplx Q = mdi_nodes_core(fam, d, a, nd, P, c, w, NULL);
+      grad_out[iw] = creal(2.0 * M_PI * I * front(fam, w) * Q);
+      continue;
+    }
+    int lev = (t < d) ? t : t - d;        /* 0-based axis of the parameter */
+    int kind = (t < d) ? 0 : 1;           /* 0: c, 1: w */
+    if (kind == 1 && (fam == OR_EXP || fam == OR_OSC)) { grad_out[iw] = 0.0; continue; }
+    for (int p = 0; p < P; ++p) { G[p] = 1.0; Gd[p] = 0.0; }
+    for (int k = 1; k < d; ++k) {
+      for (int p = 0; p < P; ++p) {
+        cplx acc = 0.0, accd = 0.0;
+        for (uint64_t q = 0; q < a; ++q) {
+          double u = ((double)q + xi[p]) / (double)a;
+          cplx g = bary(P, xi, bw, G, u), gd = bary(P, xi, bw, Gd, u);
+          acc += phi(fam, k - 1, u, c, w) * g;
+          accd += phi(fam, k - 1, u, c, w) * gd;
+          if (k - 1 == lev) accd += dphi(fam, k - 1, kind, u, c, w) * g;
+        }
+        H[p] = acc / (double)a;
+        Hd[p] = accd / (double)a;
+      }
+      memcpy(G, H, sizeof(cplx) * (size_t)P);
+      memcpy(Gd, Hd, sizeof(cplx) * (size_t)P);
+    }
+    cplx accd = 0.0;
+    for (uint64_t s = 0; s < nd; ++s) {
+      double u = (double)s / (double)nd;
+      cplx g = d > 1 ? bary(P, xi, bw, G, u) : 1.0;
+      cplx gd = d > 1 ? bary(P, xi, bw, Gd, u) : 0.0;
+      accd += phi(fam, d - 1, u, c, w) * gd;
+      if (d - 1 == lev) accd += dphi(fam, d - 1, kind, u, c, w) * g;
+    }
+    grad_out[iw] = creal(front(fam, w) * accd / (double)nd);
+  }
+  free(xi); free(bw); free(G); free(H); free(Gd); free(Hd);
+  return 0;
+}
+
+/* Barycentric basis matrix L[(q,p), t] = l_t((q + xi_p)/a), for checking the
+ * device's interpolation table. */
+int or_bary_matrix(int P, uint64_t a, double *L) {
+  double *xi = (double *)malloc(sizeof(double) * (size_t)P);
+  double *bw = (double *)malloc(sizeof(double) * (size_t)P);
+  cheb_nodes(P, xi, bw);
+  for (uint64_t q = 0; q < a; ++q)
+    for (int p = 0; p < P; ++p)
+      for (int t = 0; t < P; ++t)
+        L[(q * (uint64_t)P + p) * (uint64_t)P + t] =
+            bary_basis(P, xi, bw, t, ((double)q + xi[p]) / (double)a);
+  free(xi); free(bw);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The tensor midpoint rule that reproduces the paper's printed MDI-LR columns */
+/* ------------------------------------------------------------------------- */
+
+/* Brute force over the grid of eq. (3.5): points ((k_i + 1/2) / n_i)_i, equal weight. */
+double or_midpoint_grid(int fam, int d, const uint64_t *Nd, const double *c, const double *w) {
+  uint64_t npts = 1;
+  for (int i = 0; i < d; ++i) npts *= Nd[i];
+  double *x = (double *)malloc(sizeof(double) * (size_t)d), sum = 0.0;
+  for (uint64_t t = 0; t < npts; ++t) {
+    uint64_t rem = t;
+    for (int i = 0; i < d; ++i) { x[i] = ((double)(rem % Nd[i]) + 0.5) / (double)Nd[i]; rem /= Nd[i]; }
+    sum += f_eval(fam, d, x, c, w);
+  }
+  free(x);
+  return sum / (double)npts;
+}
+
+/* The same rule for product-form integrands: product of one-dimensional means. */
+double or_midpoint_product(int fam, int d, const uint64_t *Nd, const double *c, const double *w) {
+  if (!is_product(fam)) return NAN;
+  cplx prod = 1.0;
+  for (int i = 0; i < d; ++i) {
+    cplx s = 0.0;
+    for (uint64_t k = 0; k < Nd[i]; ++k) s += phi(fam, i, ((double)k + 0.5) / (double)Nd[i], c, w);
+    prod *= s / (double)Nd[i];
+  }
+  return creal(front(fam, w) * prod);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Exact integrals over [0,1]^d (textbook antiderivatives per axis)           */
+/* ------------------------------------------------------------------------- */
+
+static cplx axis_integral(int fam, int j, const double *c, const double *w) {
+  double cj = c[j];
+  switch (fam) {
+    case OR_EXP: return cj == 0.0 ? 1.0 : expm1(cj) / cj;
+    case OR_OSC: return cj == 0.0 ? 1.0 : (cexp(I * cj) - 1.0) / (I * cj);
+    case OR_GAUSS: return sqrt(M_PI) / (2.0 * cj) * (erf(cj * (1.0 - w[j])) + erf(cj * w[j]));
+    case OR_PEAK: return cj * (atan(cj * (1.0 - w[j])) + atan(cj * w[j]));
+  }
+  return NAN;
+}
+
+static cplx axis_integral_d(int fam, int j, int kind, const double *c, const double *w) {
+  double cj = c[j], wj = w[j];
+  switch (fam) {
+    case OR_EXP: /* d/dc (e^c - 1)/c */
+      if (kind) return 0.0;
+      return cj == 0.0 ? 0.5 : (cj * exp(cj) - expm1(cj)) / (cj * cj);
+    case OR_OSC: { /* d/dc int_0^1 e^{icx} dx = i int_0^1 x e^{icx} dx */
+      if (kind) return 0.0;
+      if (cj == 0.0) return 0.5 * I;
+      cplx ic = I * cj, e = cexp(ic);
+      return I * (e / ic - (e - 1.0) / (ic * ic));
+    }
+    case OR_GAUSS: {
+      double F = sqrt(M_PI) / (2.0 * cj) * (erf(cj * (1.0 - wj)) + erf(cj * wj));
+      double e1 = exp(-cj * cj * (1.0 - wj) * (1.0 - wj)), e0 = exp(-cj * cj * wj * wj);
+      if (kind == 0) return -F / cj + ((1.0 - wj) * e1 + wj * e0) / cj;
+      return e0 - e1;
+    }
+    case OR_PEAK: {
+      double F = cj * (atan(cj * (1.0 - wj)) + atan(cj * wj));
+      double A1 = 1.0 + cj * cj * (1.0 - wj) * (1.0 - wj), A0 = 1.0 + cj * cj * wj * wj;
+      if (kind == 0) return F / cj + cj * ((1.0 - wj) / A1 + wj / A0);
+      return cj * (-cj / A1 + cj / A0);
+    }
+  }
+  return NAN;
+}
+
+double or_closed_form(int fam, int d, const double *c, const double *w) {
+  if (!is_product(fam)) return NAN;
+  cplx p = 1.0;
+  for (int j = 0; j < d; ++j) p *= axis_integral(fam, j, c, w);
+  return creal(front(fam, w) * p);
+}
+
+/* Exact gradient of the integral: grad[k] = dI/dc_k, grad[d+k] = dI/dw_k
+ * (OR_OSC: grad[d] = dI/du). */
+int or_closed_form_grad(int fam, int d, const double *c, const double *w, double *grad) {
+  if (!is_product(fam)) return -1;
+  for (int k = 0; k < 2 * d; ++k) grad[k] = 0.0;
+  for (int kind = 0; kind < 2; ++kind) {
+    if (kind == 1 && (fam == OR_EXP || fam == OR_OSC)) continue;
+    for (int k = 0; k < d; ++k) {
+      cplx p = 1.0;
+      for (int j = 0; j < d; ++j)
+        p *= (j == k) ? axis_integral_d(fam, j, kind, c, w) : axis_integral(fam, j, c, w);
+      grad[kind * d + k] = creal(front(fam, w) * p);
+    }
+  }
+  if (fam == OR_OSC) {
+    cplx p = 1.0;
+    for (int j = 0; j < d; ++j) p *= axis_integral(fam, j, c, w);
+    grad[d] = creal(2.0 * M_PI * I * front(fam, w) * p);
+  }
+  return 0;
+}
