@@ -1,0 +1,196 @@
+/*
+ * mdi_lr.h -- C ABI of the GB300 (sm_103a) MDI-LR library.
+ *
+ * The library evaluates rank-1 lattice rules for integrals over [0,1]^d
+ * (Zhong & Feng, "An efficient implementation algorithm for quasi-Monte Carlo
+ * approximations of high-dimensional integrals"):
+ *   - lattice_rule_integrate: the standard lattice rule (SLR), eq. (1.2) with the
+ *     points x_j = {j z / n} of eq. (2.1), every point generated and evaluated;
+ *   - mdi_lr_integrate: the MDI-LR algorithm (Algorithm 2 calling Algorithm 1 with
+ *     m = 1) on the Korobov lattice z = (1, a, ..., a^(d-1)) (Example 2) with
+ *     n = n_last * a^(d-1) points, which the affine map of Theorem 3.1 turns into
+ *     a tensor-product grid with a points on each transformed axis and n_last on
+ *     the last (Lemma 3.2; no point has to be added, n* = 0).  For these n the
+ *     MDI-LR value equals the SLR value on the same lattice.
+ *
+ * Integrands are product-form families f(x) = Re(C prod_j phi_j(x_j)):
+ *   MDI_FAM_EXP    f = exp(sum_j c_j x_j)                 (Tests 2, 4, 7: f_1)
+ *   MDI_FAM_OSC    f = cos(2 pi u + sum_j c_j x_j)         (Tests 5-7: cos(2 pi + 2 sum x))
+ *   MDI_FAM_GAUSS  f = exp(-sum_j c_j^2 (x_j - w_j)^2)     (Tests 3, 5-7: Gaussian)
+ *   MDI_FAM_PEAK   f = prod_j 1 / (c_j^-2 + (x_j - w_j)^2)  (Tests 4-7: product peak)
+ * Parameters live in DEVICE memory as 2*d doubles: params[j] = c_j and
+ * params[d + j] = w_j (j < d); for MDI_FAM_OSC params[d] = u and the rest of the
+ * second half is ignored.
+ *
+ * Conventions for every call:
+ *   - The caller owns all memory.  Device buffers (params, out, workspace) are
+ *     plain device pointers (e.g. from a framework allocator); host arrays are read
+ *     before the call returns.  The library allocates no device memory.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL means the legacy default
+ *     stream) and the call returns without synchronising.  Results are valid once
+ *     the stream reaches them.  Launch sequences contain no host synchronisation
+ *     and no pageable copies, so they can be captured into a CUDA graph.
+ *   - Scratch memory comes from `workspace` (device, 256-byte aligned, at least the
+ *     size the matching *_workspace_size call returns).  Two calls that overlap on
+ *     the GPU must not share a workspace.
+ *   - Errors are returned as mdi_status.  Argument errors are detected on the host
+ *     before anything is enqueued.  MDI_ECUDA means a launch was rejected by the
+ *     CUDA runtime (the message is available from mdi_last_cuda_error()).
+ */
+#ifndef MDI_LR_H
+#define MDI_LR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *mdi_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+  MDI_OK = 0,
+  MDI_EINVAL = 1,        /* an argument is out of range or a pointer is NULL */
+  MDI_EUNSUPPORTED = 2,  /* valid for the method, not provided by this library */
+  MDI_EOVERFLOW = 3,     /* a lattice size does not fit the exact integer range */
+  MDI_ECUDA = 4,         /* the CUDA runtime rejected a launch or copy */
+  MDI_EWORKSPACE = 5     /* workspace NULL, misaligned or smaller than required */
+} mdi_status;
+
+typedef enum { MDI_FAM_EXP = 0, MDI_FAM_OSC = 1, MDI_FAM_GAUSS = 2, MDI_FAM_PEAK = 3 } mdi_family;
+
+/* Representation of the level state ("symbolic function" g_{k-m} of eq. (4.4),
+ * which the paper leaves unspecified):
+ *   MDI_STATE_EXACT  the value at every parent the lattice needs, n a/(a-1)
+ *                    evaluations in all; exact, exponential in d.
+ *   MDI_STATE_CLOSED G_k(x) = K_k exp(beta_k x); exact, for EXP and OSC only.
+ *   MDI_STATE_NODES  values at P Chebyshev points, read back by barycentric
+ *                    interpolation; O(d a P^2), for every family.
+ *   MDI_STATE_AUTO   CLOSED for EXP/OSC, NODES otherwise. */
+typedef enum { MDI_STATE_AUTO = 0, MDI_STATE_EXACT = 1, MDI_STATE_CLOSED = 2, MDI_STATE_NODES = 3 } mdi_state;
+
+/* Arithmetic of a call:
+ *   MDI_PREC_FP64             every step in IEEE double.
+ *   MDI_PREC_FP32_EVAL_FP64   integrand factors phi_j in float, everything else double.
+ *   MDI_PREC_FP32_EVAL_DF32   phi_j in float; level contractions (interpolation and
+ *                             the sum over the cluster) in double-float pairs of
+ *                             floats; level states, cross-level products, the final
+ *                             sum and coordinates in double. */
+typedef enum {
+  MDI_PREC_FP64 = 0,
+  MDI_PREC_FP32_EVAL_FP64 = 1,
+  MDI_PREC_FP32_EVAL_DF32 = 2
+} mdi_precision;
+
+typedef struct {
+  int32_t state;       /* mdi_state */
+  int32_t precision;   /* mdi_precision */
+  int32_t nodes;       /* P for MDI_STATE_NODES, 2..32; 0 selects 16 */
+  int32_t block;       /* threads per CTA for the node-state kernels (64..512,
+                          multiple of 32 and of P); 0 selects the library default */
+  int32_t ctas_per_sm; /* resident CTAs per SM for persistent grids; 0 = default */
+  int32_t checkpoint;  /* level-checkpoint interval of the adjoint; 0 = ceil(sqrt(d)) */
+  int32_t reserved[2]; /* must be 0 */
+} mdi_opts;
+
+/* ---------------------------------------------------------------------------
+ * Standard lattice rule, eq. (1.2) with the rank-1 points of eq. (2.1).
+ *   d        dimension, 1..256
+ *   n        number of points, 1 <= n < 2^63
+ *   z        HOST array of d generating-vector entries, 0 <= z_i < n (any vector;
+ *            the paper's gcd(z_i, n) = 1 is not required)
+ *   params   DEVICE, 2*d doubles (see above)
+ *   precision MDI_PREC_FP64 or MDI_PREC_FP32_EVAL_FP64
+ *   out      DEVICE, 1 double: Q = (1/n) sum_{j<n} f((j z mod n) / n)
+ * Indices j z_i mod n are exact 64-bit integers; the sum is a fixed-order
+ * (deterministic) FP64 reduction.
+ * ------------------------------------------------------------------------- */
+mdi_status lattice_rule_integrate(int32_t family, int32_t d, int64_t n, const int64_t *z,
+                                  const double *params, int32_t precision, double *out,
+                                  void *workspace, size_t ws_bytes, mdi_stream_t stream);
+mdi_status lattice_rule_workspace_size(int32_t d, int64_t n, size_t *bytes);
+
+/* ---------------------------------------------------------------------------
+ * MDI-LR, Algorithm 2 (Section 4) with m = 1 on the Korobov lattice.
+ *   d        dimension, >= 1 (EXACT: n <= 2^40; CLOSED: d <= 2^20; NODES: d <= 2^20)
+ *   a        Korobov parameter = points per transformed axis 1..d-1, a >= 1
+ *            (NODES: a <= 64, EXACT: a <= 4096)
+ *   n_last   points on the last transformed axis (n_d of eq. (3.5)), >= 1;
+ *            n = n_last * a^(d-1); Lemma 3.2's equal-N case is n_last = a
+ *   params   DEVICE, 2*d doubles
+ *   opts     HOST, may be NULL (all defaults)
+ *   out      DEVICE, 1 double
+ * ------------------------------------------------------------------------- */
+mdi_status mdi_lr_integrate(int32_t family, int32_t d, int64_t a, int64_t n_last,
+                            const double *params, const mdi_opts *opts, double *out,
+                            void *workspace, size_t ws_bytes, mdi_stream_t stream);
+mdi_status mdi_lr_workspace_size(int32_t family, int32_t d, int64_t a, int64_t n_last,
+                                 const mdi_opts *opts, size_t *bytes);
+
+/* ---------------------------------------------------------------------------
+ * Many independent MDI-LR integrals in one launch sequence (node state for every
+ * family, or closed state for EXP/OSC instances when opts->state is
+ * MDI_STATE_AUTO).  One descriptor per integral:
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t family;       /* mdi_family */
+  int32_t d;            /* 1..MDI_BATCH_MAX_D */
+  int32_t a;            /* 1..64 */
+  int32_t n_last;       /* 1..4096 */
+  int64_t param_offset; /* index into param_pool of this integral's 2*d doubles */
+  int64_t reserved;     /* must be 0 */
+} mdi_batch_desc;       /* 32 bytes */
+
+#define MDI_BATCH_MAX_D 65536
+
+/* One-time set-up of a workspace for mdi_lr_integrate_batched: builds the
+ * barycentric basis tables l_t((q + xi_p)/a) for a = 1..64 and the P of opts (they
+ * depend on nothing else), zeroes the work-queue counters and stamps a tag naming
+ * opts->nodes and the table format of opts->precision.  Enqueued on `stream`; a
+ * prepared workspace serves any number of batched calls with the same nodes and
+ * precision.  Call it again after a batched call failed to launch. */
+mdi_status mdi_lr_batched_prepare(const mdi_opts *opts, void *workspace, size_t ws_bytes, mdi_stream_t stream);
+
+/*   descs      DEVICE, count descriptors
+ *   order      DEVICE, count int32 instance indices in the order CTAs should pick
+ *              them up (from mdi_batch_plan), or NULL for 0..count-1
+ *   count      number of integrals, >= 1
+ *   param_pool DEVICE doubles
+ *   out        DEVICE, count doubles; out[i] belongs to descs[i]
+ *   workspace  prepared by mdi_lr_batched_prepare with the same nodes/precision
+ * One kernel launch: a persistent grid of CTAs takes integrals from an atomic
+ * counter in the workspace; the last CTA to finish re-arms the counter.  A
+ * descriptor outside the limits above, an order entry outside 0..count-1 (that
+ * entry only) or an unprepared workspace yields NaN in the affected outputs. */
+mdi_status mdi_lr_integrate_batched(const mdi_batch_desc *descs, const int32_t *order, int32_t count,
+                                    const double *param_pool, const mdi_opts *opts, double *out,
+                                    void *workspace, size_t ws_bytes, mdi_stream_t stream);
+mdi_status mdi_lr_batched_workspace_size(int32_t count, const mdi_opts *opts, size_t *bytes);
+
+/* Host-side scheduler: writes into order (HOST, count int32) a processing order
+ * for mdi_lr_integrate_batched -- longest estimated work first, ties grouped by a
+ * so that consecutive pick-ups share their interpolation table.  descs is a HOST
+ * copy of the descriptor table.  Returns MDI_EINVAL on an invalid descriptor. */
+mdi_status mdi_batch_plan(const mdi_batch_desc *descs, int32_t count, const mdi_opts *opts,
+                          int32_t *order);
+
+/* ---------------------------------------------------------------------------
+ * Bit-exact view of the on-the-fly index generator used by the lattice kernel:
+ * r_out[t*d + i] = (j0 + t) z_i mod n for t < count (DEVICE, count*d int64),
+ * produced by the same incremental exact arithmetic the kernel uses.
+ * ------------------------------------------------------------------------- */
+mdi_status mdi_debug_lattice_indices(int32_t d, int64_t n, const int64_t *z, int64_t j0,
+                                     int64_t count, int64_t *r_out, mdi_stream_t stream);
+
+const char *mdi_status_string(mdi_status status);
+/* Text of the last CUDA error seen by this library on the calling host thread. */
+const char *mdi_last_cuda_error(void);
+/* ABI version of this header (bumped on any incompatible change). */
+int32_t mdi_abi_version(void);
+#define MDI_ABI_VERSION 1
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MDI_LR_H */

@@ -1,0 +1,212 @@
+"""GB300 (sm_103a) MDI-LR: fast rank-1 lattice rules for high-dimensional integrals.
+
+Thin Python binding of the C ABI in ``include/mdi_lr.h`` (same names).  Every
+step of the computation runs in the CUDA kernels of ``libmdilr.so``; this module
+only marshals arguments: it takes torch tensors for device memory, passes their
+pointers and torch's current CUDA stream, and allocates workspaces through torch.
+
+The method is that of Zhong & Feng: the standard lattice rule (eq. (1.2) over the
+points of eq. (2.1)) and its fast evaluation MDI-LR (Algorithm 2 calling
+Algorithm 1 with m = 1) on the Korobov lattice z = (1, a, ..., a^(d-1)) with
+n = n_last * a^(d-1) points.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _ffi
+from ._ffi import BATCH_DESC_DTYPE, FAMILY, PRECISION, STATE, MdiError, MdiOpts
+
+__all__ = [
+    "lattice_rule_integrate", "lattice_rule_workspace_size", "mdi_lr_integrate", "mdi_lr_workspace_size",
+    "mdi_lr_integrate_batched", "mdi_lr_batched_workspace_size", "mdi_lr_batched_prepare", "mdi_batch_plan", "mdi_debug_lattice_indices",
+    "make_batch_descs", "MdiError", "FAMILY", "STATE", "PRECISION", "BATCH_DESC_DTYPE", "library_path",
+]
+
+
+def library_path() -> str:
+    return _ffi.LIB_PATH
+
+
+def _fam(f) -> int:
+    return FAMILY[f] if isinstance(f, str) else int(f)
+
+
+def _prec(p) -> int:
+    return PRECISION[p] if isinstance(p, str) else int(p)
+
+
+def _state(s) -> int:
+    return STATE[s] if isinstance(s, str) else int(s)
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_f64(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    return t
+
+
+def _opts(state="auto", precision="fp64", nodes=0, block=0, ctas_per_sm=0, checkpoint=0) -> MdiOpts:
+    o = MdiOpts()
+    o.state, o.precision, o.nodes, o.block = _state(state), _prec(precision), int(nodes), int(block)
+    o.ctas_per_sm, o.checkpoint = int(ctas_per_sm), int(checkpoint)
+    return o
+
+
+def _workspace(nbytes: int, device, workspace: Optional[torch.Tensor]) -> torch.Tensor:
+    if workspace is not None:
+        if workspace.numel() * workspace.element_size() < nbytes:
+            raise ValueError(f"workspace too small: need {nbytes} bytes")
+        return workspace
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+# ---------------------------------------------------------------------------
+# Standard lattice rule
+# ---------------------------------------------------------------------------
+def lattice_rule_workspace_size(d: int, n: int) -> int:
+    b = ctypes.c_size_t()
+    _ffi.check(_ffi.load().lattice_rule_workspace_size(d, n, ctypes.byref(b)), "lattice_rule_workspace_size")
+    return b.value
+
+
+def lattice_rule_integrate(family, params: torch.Tensor, n: int, z: Sequence[int], precision="fp64",
+                           out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
+                           stream=None) -> torch.Tensor:
+    """Q = (1/n) sum_{j<n} f({j z / n}) on the GPU; ``params`` holds 2*d doubles
+    (c then w; for "osc" params[d] = u).  Returns a 1-element float64 CUDA tensor."""
+    _dev_f64(params, "params")
+    zz = np.ascontiguousarray(np.asarray(z, dtype=np.int64))
+    d = int(zz.size)
+    if params.numel() < 2 * d:
+        raise ValueError("params must hold 2*d doubles")
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=params.device)
+    ws = _workspace(lattice_rule_workspace_size(d, n), params.device, workspace)
+    st = _ffi.load().lattice_rule_integrate(_fam(family), d, int(n), zz.ctypes.data_as(ctypes.c_void_p),
+                                            ctypes.c_void_p(params.data_ptr()), _prec(precision),
+                                            ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                                            ws.numel(), _stream(stream))
+    _ffi.check(st, "lattice_rule_integrate")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# MDI-LR, one integral
+# ---------------------------------------------------------------------------
+def mdi_lr_workspace_size(family, d: int, a: int, n_last: int, **opts) -> int:
+    b = ctypes.c_size_t()
+    o = _opts(**opts)
+    _ffi.check(_ffi.load().mdi_lr_workspace_size(_fam(family), d, a, n_last, ctypes.byref(o), ctypes.byref(b)),
+               "mdi_lr_workspace_size")
+    return b.value
+
+
+def mdi_lr_integrate(family, params: torch.Tensor, d: int, a: int, n_last: Optional[int] = None,
+                     out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None, stream=None,
+                     **opts) -> torch.Tensor:
+    """MDI-LR value on the Korobov lattice with a points per transformed axis and
+    n_last (default a) on the last one; opts: state, precision, nodes, block,
+    ctas_per_sm.  Returns a 1-element float64 CUDA tensor."""
+    _dev_f64(params, "params")
+    n_last = a if n_last is None else n_last
+    if params.numel() < 2 * d:
+        raise ValueError("params must hold 2*d doubles")
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=params.device)
+    o = _opts(**opts)
+    ws = _workspace(mdi_lr_workspace_size(family, d, a, n_last, **opts), params.device, workspace)
+    st = _ffi.load().mdi_lr_integrate(_fam(family), d, a, n_last, ctypes.c_void_p(params.data_ptr()),
+                                      ctypes.byref(o), ctypes.c_void_p(out.data_ptr()),
+                                      ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
+    _ffi.check(st, "mdi_lr_integrate")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Batched MDI-LR
+# ---------------------------------------------------------------------------
+def make_batch_descs(families, ds, as_, n_lasts, param_offsets) -> np.ndarray:
+    """Host descriptor table (numpy structured array laid out as mdi_batch_desc)."""
+    n = len(ds)
+    descs = np.zeros(n, dtype=BATCH_DESC_DTYPE)
+    descs["family"] = [_fam(f) for f in families]
+    descs["d"], descs["a"], descs["n_last"] = ds, as_, n_lasts
+    descs["param_offset"] = param_offsets
+    return descs
+
+
+def mdi_batch_plan(descs: np.ndarray, **opts) -> np.ndarray:
+    """Longest-first processing order computed by the library's host scheduler."""
+    descs = np.ascontiguousarray(descs, dtype=BATCH_DESC_DTYPE)
+    order = np.zeros(descs.size, dtype=np.int32)
+    o = _opts(**opts)
+    _ffi.check(_ffi.load().mdi_batch_plan(descs.ctypes.data_as(ctypes.c_void_p), descs.size, ctypes.byref(o),
+                                          order.ctypes.data_as(ctypes.c_void_p)), "mdi_batch_plan")
+    return order
+
+
+def mdi_lr_batched_workspace_size(count: int, **opts) -> int:
+    b = ctypes.c_size_t()
+    o = _opts(**opts)
+    _ffi.check(_ffi.load().mdi_lr_batched_workspace_size(count, ctypes.byref(o), ctypes.byref(b)),
+               "mdi_lr_batched_workspace_size")
+    return b.value
+
+
+def mdi_lr_batched_prepare(workspace: Optional[torch.Tensor] = None, device="cuda", stream=None,
+                           **opts) -> torch.Tensor:
+    """Returns a workspace prepared for batched calls with these opts (basis
+    tables built, queue armed).  Reuse it for every call with the same opts."""
+    ws = _workspace(mdi_lr_batched_workspace_size(1, **opts), device, workspace)
+    o = _opts(**opts)
+    _ffi.check(_ffi.load().mdi_lr_batched_prepare(ctypes.byref(o), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                                  _stream(stream)), "mdi_lr_batched_prepare")
+    return ws
+
+
+def mdi_lr_integrate_batched(descs: torch.Tensor, param_pool: torch.Tensor, count: int,
+                             order: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
+                             workspace: Optional[torch.Tensor] = None, stream=None, **opts) -> torch.Tensor:
+    """``descs``: uint8 CUDA tensor holding ``count`` mdi_batch_desc records
+    (``torch.from_numpy(make_batch_descs(...).view(np.uint8)).cuda()``); ``order``:
+    optional int32 CUDA tensor from mdi_batch_plan; ``workspace``: from
+    mdi_lr_batched_prepare with the same opts (prepared here when omitted).
+    Returns ``count`` float64 values."""
+    if not (descs.is_cuda and descs.dtype == torch.uint8 and descs.numel() >= 32 * count):
+        raise TypeError("descs must be a uint8 CUDA tensor of count*32 bytes")
+    _dev_f64(param_pool, "param_pool")
+    if order is not None and not (order.is_cuda and order.dtype == torch.int32 and order.numel() >= count):
+        raise TypeError("order must be an int32 CUDA tensor of count entries")
+    if out is None:
+        out = torch.empty(count, dtype=torch.float64, device=param_pool.device)
+    if workspace is None:
+        workspace = mdi_lr_batched_prepare(device=param_pool.device, stream=stream, **opts)
+    o = _opts(**opts)
+    st = _ffi.load().mdi_lr_integrate_batched(
+        ctypes.c_void_p(descs.data_ptr()), ctypes.c_void_p(order.data_ptr() if order is not None else 0), count,
+        ctypes.c_void_p(param_pool.data_ptr()), ctypes.byref(o), ctypes.c_void_p(out.data_ptr()),
+        ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream(stream))
+    _ffi.check(st, "mdi_lr_integrate_batched")
+    return out
+
+
+def mdi_debug_lattice_indices(n: int, z: Sequence[int], j0: int, count: int, device="cuda",
+                              stream=None) -> torch.Tensor:
+    """(count, d) int64 CUDA tensor of (j0 + t) z_i mod n from the kernel's generator."""
+    zz = np.ascontiguousarray(np.asarray(z, dtype=np.int64))
+    d = int(zz.size)
+    out = torch.empty((count, d), dtype=torch.int64, device=device)
+    st = _ffi.load().mdi_debug_lattice_indices(d, int(n), zz.ctypes.data_as(ctypes.c_void_p), int(j0), int(count),
+                                               ctypes.c_void_p(out.data_ptr()), _stream(stream))
+    _ffi.check(st, "mdi_debug_lattice_indices")
+    return out

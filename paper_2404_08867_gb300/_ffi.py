@@ -1,0 +1,86 @@
+"""ctypes declarations of the C ABI in include/mdi_lr.h (no computation here)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmdilr.so")
+
+MDI_OK, MDI_EINVAL, MDI_EUNSUPPORTED, MDI_EOVERFLOW, MDI_ECUDA, MDI_EWORKSPACE = range(6)
+FAMILY = {"exp": 0, "osc": 1, "gauss": 2, "peak": 3}
+STATE = {"auto": 0, "exact": 1, "closed": 2, "nodes": 3}
+PRECISION = {"fp64": 0, "fp32_eval_fp64": 1, "fp32_eval_df32": 2}
+
+# Every symbol include/mdi_lr.h declares, with its ctypes signature.
+_c = ctypes
+_P = _c.c_void_p
+_I32 = _c.c_int32
+_I64 = _c.c_int64
+_SZ = _c.c_size_t
+
+
+class MdiOpts(ctypes.Structure):
+    _fields_ = [("state", _I32), ("precision", _I32), ("nodes", _I32), ("block", _I32),
+                ("ctas_per_sm", _I32), ("checkpoint", _I32), ("reserved", _I32 * 2)]
+
+
+BATCH_DESC_DTYPE = np.dtype([("family", np.int32), ("d", np.int32), ("a", np.int32), ("n_last", np.int32),
+                             ("param_offset", np.int64), ("reserved", np.int64)])
+assert BATCH_DESC_DTYPE.itemsize == 32
+
+SIGNATURES = {
+    "lattice_rule_integrate": (_I32, [_I32, _I32, _I64, _P, _P, _I32, _P, _P, _SZ, _P]),
+    "lattice_rule_workspace_size": (_I32, [_I32, _I64, _c.POINTER(_SZ)]),
+    "mdi_lr_integrate": (_I32, [_I32, _I32, _I64, _I64, _P, _c.POINTER(MdiOpts), _P, _P, _SZ, _P]),
+    "mdi_lr_workspace_size": (_I32, [_I32, _I32, _I64, _I64, _c.POINTER(MdiOpts), _c.POINTER(_SZ)]),
+    "mdi_lr_integrate_batched": (_I32, [_P, _P, _I32, _P, _c.POINTER(MdiOpts), _P, _P, _SZ, _P]),
+    "mdi_lr_batched_workspace_size": (_I32, [_I32, _c.POINTER(MdiOpts), _c.POINTER(_SZ)]),
+    "mdi_lr_batched_prepare": (_I32, [_c.POINTER(MdiOpts), _P, _SZ, _P]),
+    "mdi_batch_plan": (_I32, [_P, _I32, _c.POINTER(MdiOpts), _P]),
+    "mdi_debug_lattice_indices": (_I32, [_I32, _I64, _P, _I64, _I64, _P, _P]),
+    "mdi_status_string": (_c.c_char_p, [_I32]),
+    "mdi_last_cuda_error": (_c.c_char_p, []),
+    "mdi_abi_version": (_I32, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load():
+    """Loads libmdilr.so.  There is no fallback: without the built library every
+    call fails loudly (build it with ``python -m paper_2404_08867_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing; build it with "
+                                   "`python -m paper_2404_08867_gb300.build` (nvcc, sm_103a)")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            if lib.mdi_abi_version() != 1:
+                raise RuntimeError("libmdilr.so ABI version mismatch; rebuild it")
+            _lib = lib
+    return _lib
+
+
+class MdiError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = load()
+        msg = lib.mdi_status_string(status).decode()
+        if status == MDI_ECUDA:
+            msg += " (" + lib.mdi_last_cuda_error().decode() + ")"
+        super().__init__(f"{where}: {msg}")
+        self.status = status
+
+
+def check(status: int, where: str) -> None:
+    if status != MDI_OK:
+        raise MdiError(status, where)

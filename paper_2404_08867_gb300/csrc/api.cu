@@ -1,0 +1,172 @@
+// api.cu -- the C ABI of include/mdi_lr.h: argument checks, state selection,
+// workspace sizing and the host-side batch scheduler.  Every compute step runs in
+// the kernels of slr.cu, mdi_exact.cu, mdi_closed.cu and mdi_nodes.cu.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "mdi_common.cuh"
+#include "mdi_internal.h"
+
+namespace mdi {
+
+static thread_local std::string g_last_cuda_error;
+
+void set_cuda_error(cudaError_t e) {
+  g_last_cuda_error = std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e);
+}
+
+int sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
+static bool family_ok(int f) { return f >= MDI_FAM_EXP && f <= MDI_FAM_PEAK; }
+
+static bool opts_ok(const mdi_opts *o) {
+  if (!o) return true;
+  if (o->state < MDI_STATE_AUTO || o->state > MDI_STATE_NODES) return false;
+  if (o->precision < MDI_PREC_FP64 || o->precision > MDI_PREC_FP32_EVAL_DF32) return false;
+  if (o->nodes < 0 || o->block < 0 || o->ctas_per_sm < 0 || o->checkpoint < 0) return false;
+  return o->reserved[0] == 0 && o->reserved[1] == 0;
+}
+
+static int resolve_state(int family, const mdi_opts *o) {
+  int s = o ? o->state : MDI_STATE_AUTO;
+  if (s != MDI_STATE_AUTO) return s;
+  return (family == MDI_FAM_EXP || family == MDI_FAM_OSC) ? MDI_STATE_CLOSED : MDI_STATE_NODES;
+}
+
+// Estimated FP64-equivalent operations of one node-state integral (scheduler cost).
+static double nodes_cost(const mdi_batch_desc &d, int P) {
+  const double phi_cost = (d.family == MDI_FAM_PEAK) ? 8.0 : 20.0;
+  return (double)(d.d - 1) * d.a * P * (P + phi_cost) + (double)d.n_last * (2.0 * P + phi_cost);
+}
+
+static bool desc_ok(const mdi_batch_desc &d) {
+  return family_ok(d.family) && d.d >= 1 && d.d <= MDI_BATCH_MAX_D && d.a >= 1 && d.a <= 64 && d.n_last >= 1 &&
+         d.n_last <= 4096 && d.param_offset >= 0 && d.reserved == 0;
+}
+
+}  // namespace mdi
+
+using namespace mdi;
+
+extern "C" {
+
+const char *mdi_status_string(mdi_status s) {
+  switch (s) {
+    case MDI_OK: return "MDI_OK: success";
+    case MDI_EINVAL: return "MDI_EINVAL: invalid argument";
+    case MDI_EUNSUPPORTED: return "MDI_EUNSUPPORTED: combination not provided by this library";
+    case MDI_EOVERFLOW: return "MDI_EOVERFLOW: lattice size exceeds the exact integer range";
+    case MDI_ECUDA: return "MDI_ECUDA: CUDA runtime error";
+    case MDI_EWORKSPACE: return "MDI_EWORKSPACE: workspace missing, misaligned or too small";
+  }
+  return "unknown mdi_status";
+}
+
+const char *mdi_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+int32_t mdi_abi_version(void) { return MDI_ABI_VERSION; }
+
+mdi_status lattice_rule_workspace_size(int32_t d, int64_t n, size_t *bytes) {
+  if (!bytes || d < 1 || n < 1) return MDI_EINVAL;
+  *bytes = slr_workspace_bytes(d, n);
+  return MDI_OK;
+}
+
+mdi_status lattice_rule_integrate(int32_t family, int32_t d, int64_t n, const int64_t *z, const double *params,
+                                  int32_t precision, double *out, void *workspace, size_t ws_bytes,
+                                  mdi_stream_t stream) {
+  if (!family_ok(family)) return MDI_EINVAL;
+  return slr_launch(family, d, n, z, params, precision, out, workspace, ws_bytes, (cudaStream_t)stream);
+}
+
+mdi_status mdi_lr_workspace_size(int32_t family, int32_t d, int64_t a, int64_t n_last, const mdi_opts *opts,
+                                 size_t *bytes) {
+  if (!bytes || !family_ok(family) || d < 1 || a < 1 || n_last < 1 || !opts_ok(opts)) return MDI_EINVAL;
+  switch (resolve_state(family, opts)) {
+    case MDI_STATE_EXACT: {
+      size_t b = exact_workspace_bytes(family, d, a, n_last);
+      if (b == 0) return MDI_EOVERFLOW;
+      *bytes = b;
+      return MDI_OK;
+    }
+    case MDI_STATE_CLOSED:
+      if (family != MDI_FAM_EXP && family != MDI_FAM_OSC) return MDI_EUNSUPPORTED;
+      *bytes = closed_workspace_bytes(d);
+      return MDI_OK;
+    default:
+      *bytes = nodes_single_workspace_bytes(nodes_config(opts));
+      return MDI_OK;
+  }
+}
+
+mdi_status mdi_lr_integrate(int32_t family, int32_t d, int64_t a, int64_t n_last, const double *params,
+                            const mdi_opts *opts, double *out, void *workspace, size_t ws_bytes,
+                            mdi_stream_t stream) {
+  if (!family_ok(family) || d < 1 || a < 1 || n_last < 1 || !params || !out || !opts_ok(opts)) return MDI_EINVAL;
+  const int precision = opts ? opts->precision : MDI_PREC_FP64;
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (resolve_state(family, opts)) {
+    case MDI_STATE_EXACT: return exact_launch(family, d, a, n_last, params, precision, out, workspace, ws_bytes, s);
+    case MDI_STATE_CLOSED: return closed_launch(family, d, a, n_last, params, precision, out, workspace, ws_bytes, s);
+    default: return nodes_single_launch(family, d, a, n_last, params, nodes_config(opts), out, workspace, ws_bytes, s);
+  }
+}
+
+mdi_status mdi_lr_batched_workspace_size(int32_t count, const mdi_opts *opts, size_t *bytes) {
+  if (!bytes || count < 1 || !opts_ok(opts)) return MDI_EINVAL;
+  *bytes = nodes_batched_workspace_bytes(count, nodes_config(opts));
+  return MDI_OK;
+}
+
+mdi_status mdi_lr_batched_prepare(const mdi_opts *opts, void *workspace, size_t ws_bytes, mdi_stream_t stream) {
+  if (!opts_ok(opts)) return MDI_EINVAL;
+  return nodes_prepare(nodes_config(opts), workspace, ws_bytes, (cudaStream_t)stream);
+}
+
+mdi_status mdi_lr_integrate_batched(const mdi_batch_desc *descs, const int32_t *order, int32_t count,
+                                    const double *param_pool, const mdi_opts *opts, double *out, void *workspace,
+                                    size_t ws_bytes, mdi_stream_t stream) {
+  if (!opts_ok(opts)) return MDI_EINVAL;
+  if (opts && opts->state != MDI_STATE_AUTO && opts->state != MDI_STATE_NODES) return MDI_EUNSUPPORTED;
+  return nodes_batched_launch(descs, order, count, param_pool, nodes_config(opts), out, workspace, ws_bytes,
+                              (cudaStream_t)stream);
+}
+
+mdi_status mdi_batch_plan(const mdi_batch_desc *descs, int32_t count, const mdi_opts *opts, int32_t *order) {
+  if (!descs || !order || count < 1 || !opts_ok(opts)) return MDI_EINVAL;
+  const int P = nodes_config(opts).P;
+  std::vector<double> cost((size_t)count);
+  for (int32_t i = 0; i < count; ++i) {
+    if (!desc_ok(descs[i])) return MDI_EINVAL;
+    cost[(size_t)i] = nodes_cost(descs[i], P);
+  }
+  std::vector<int32_t> idx((size_t)count);
+  std::iota(idx.begin(), idx.end(), 0);
+  // Longest processing time first; equal costs grouped by a, then by index.
+  std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) {
+    if (cost[(size_t)x] != cost[(size_t)y]) return cost[(size_t)x] > cost[(size_t)y];
+    return descs[x].a < descs[y].a;
+  });
+  std::memcpy(order, idx.data(), sizeof(int32_t) * (size_t)count);
+  return MDI_OK;
+}
+
+mdi_status mdi_debug_lattice_indices(int32_t d, int64_t n, const int64_t *z, int64_t j0, int64_t count,
+                                     int64_t *r_out, mdi_stream_t stream) {
+  return lattice_indices_launch(d, n, z, j0, count, r_out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,48 @@
+// mdi_internal.h -- launchers behind the C ABI (one per kernel family).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "mdi_lr.h"
+
+namespace mdi {
+
+// slr.cu
+size_t slr_workspace_bytes(int d, int64_t n);
+mdi_status slr_launch(int family, int d, int64_t n, const int64_t *z, const double *params, int precision,
+                      double *out, void *workspace, size_t ws_bytes, cudaStream_t stream);
+mdi_status lattice_indices_launch(int d, int64_t n, const int64_t *z, int64_t j0, int64_t count, int64_t *r_out,
+                                  cudaStream_t stream);
+
+// mdi_exact.cu
+size_t exact_workspace_bytes(int family, int d, int64_t a, int64_t n_last);
+mdi_status exact_launch(int family, int d, int64_t a, int64_t n_last, const double *params, int precision,
+                        double *out, void *workspace, size_t ws_bytes, cudaStream_t stream);
+
+// mdi_closed.cu
+size_t closed_workspace_bytes(int d);
+mdi_status closed_launch(int family, int d, int64_t a, int64_t n_last, const double *params, int precision,
+                         double *out, void *workspace, size_t ws_bytes, cudaStream_t stream);
+
+// mdi_nodes.cu
+struct NodesConfig {
+  int P;            // nodes per state
+  int block;        // threads per CTA
+  int ctas_per_sm;  // persistent CTAs per SM
+  int precision;    // mdi_precision
+};
+NodesConfig nodes_config(const mdi_opts *opts);
+size_t nodes_batched_workspace_bytes(int count, const NodesConfig &cfg);
+mdi_status nodes_prepare(const NodesConfig &cfg, void *workspace, size_t ws_bytes, cudaStream_t stream);
+mdi_status nodes_batched_launch(const mdi_batch_desc *descs, const int32_t *order, int count,
+                                const double *param_pool, const NodesConfig &cfg, double *out, void *workspace,
+                                size_t ws_bytes, cudaStream_t stream);
+// Single integral through the batched machinery (descriptor built on the device).
+size_t nodes_single_workspace_bytes(const NodesConfig &cfg);
+mdi_status nodes_single_launch(int family, int d, int64_t a, int64_t n_last, const double *params,
+                               const NodesConfig &cfg, double *out, void *workspace, size_t ws_bytes,
+                               cudaStream_t stream);
+
+}  // namespace mdi

@@ -1,0 +1,430 @@
+// mdi_nodes.cu -- MDI-LR with the node level state (MDI_STATE_NODES), batched.
+//
+// The paper keeps each "symbolic function" g_{k-m} of eq. (4.4) symbolically; this
+// library keeps the level state G_k(x) (x = the next original coordinate) at P
+// Chebyshev points of the first kind on [0,1],
+//     xi_p = (1 + cos(pi (2p+1) / (2P))) / 2,
+// and reads it between them with the barycentric formula of the second kind
+// (weights (-1)^p sin(pi (2p+1)/(2P)); Berrut & Trefethen, SIAM Review 46, 2004).
+// Level k < d evaluates the cluster of the sweep,
+//     G_k(xi_p) = (1/a) sum_{q<a} phi_k(u_qp) G_{k-1}(u_qp),  u_qp = (q + xi_p)/a,
+// and the last level sums over the n_last points s/n_last of the last axis.
+//
+// GB300 mapping.  Integrals are independent, so a persistent grid of CTAs pulls
+// them from an atomic counter (no waiting: a CTA that finds the queue empty
+// exits).  A CTA sweeps its integral's d levels with the state in shared memory.
+// Inside a level, thread t owns node p = t mod P and cluster points q = t/P,
+// t/P + B/P, ...; each point interpolates G_{k-1} (P FMAs against the basis table
+// L_a[t][q*P+p] = l_t(u_qp), staged in shared memory), multiplies by phi_k, and
+// accumulates; the B/P partial rows are then added in a fixed order by P threads.
+// The basis tables depend only on (a, P): one small kernel builds them for
+// a = 1..64 at the start of every call, spread over the whole GPU.
+//
+// Precision modes (mdi_precision): FP64 everywhere; phi in float with FP64
+// interpolation and sums; phi in float with interpolation and the cluster sum in
+// double-float pairs, the state kept in FP64 between levels.
+#include <algorithm>
+
+#include "mdi_common.cuh"
+#include "mdi_internal.h"
+
+namespace mdi {
+
+constexpr int kNodesAMax = 64;              // largest a with a basis table
+constexpr int kNodesPMax = 32;
+constexpr int kNodesMaxBlock = 512;
+constexpr int kNodesSmemTable = 64 * 1024;  // table bytes staged in shared memory
+
+// Fixed part of the dynamic shared memory.  The partial rows (rows x P x 16 B)
+// and the staged table follow it.
+struct NodesShared {
+  double xi[kNodesPMax], bw[kNodesPMax];
+  double2 G[kNodesPMax];   // state at the nodes (imaginary part 0 for real families)
+  float4 Gdf[kNodesPMax];  // the same state as float pairs (re.hi, re.lo, im.hi, im.lo)
+  double2 red[kNodesMaxBlock / kWarp];
+  int inst;
+  int pad[3];
+};
+
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) / 16 * 16; }
+__host__ __device__ inline size_t rows_bytes(int block, int P) { return align16((size_t)(block / P) * P * 16); }
+static size_t nodes_smem_bytes(int block, int P) {
+  return align16(sizeof(NodesShared)) + rows_bytes(block, P) + kNodesSmemTable;
+}
+
+// Offset (in 8-byte entries) of the table of parameter a (1-based) for P nodes.
+__host__ __device__ __forceinline__ size_t table_offset(int a, int P) {
+  return (size_t)P * P * (size_t)a * (size_t)(a - 1) / 2;
+}
+static size_t table_bytes(int P) { return 8 * table_offset(kNodesAMax + 1, P); }
+
+__device__ __forceinline__ double cheb_node(int p, int P) { return 0.5 * (1.0 + cospi((2.0 * p + 1.0) / (2.0 * P))); }
+__device__ __forceinline__ double cheb_weight(int p, int P) {
+  return ((p & 1) ? -1.0 : 1.0) * sinpi((2.0 * p + 1.0) / (2.0 * P));
+}
+
+// Basis tables L_a[t][q*P + p] = l_t((q + xi_p)/a) for a = 1..64, stored as double
+// (DF = false) or as a float pair hi + lo (DF = true); 8 bytes per entry either way.
+template <bool DF>
+__global__ void nodes_table_kernel(int P, void *__restrict__ table) {
+  const size_t total_pts = (size_t)P * kNodesAMax * (kNodesAMax + 1) / 2;  // sum_a a*P points
+  for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total_pts;
+       g += (size_t)gridDim.x * blockDim.x) {
+    int a = 1;
+    size_t base = 0;
+    while (base + (size_t)a * P <= g) {
+      base += (size_t)a * P;
+      ++a;
+    }
+    const int i = (int)(g - base);  // i = q*P + p
+    const int q = i / P, p = i % P;
+    const double u = ((double)q + cheb_node(p, P)) / (double)a;
+    double den = 0.0;
+    int hit = -1;
+    for (int t = 0; t < P; ++t) {
+      const double xt = cheb_node(t, P);
+      if (u == xt) hit = t;
+      else den += cheb_weight(t, P) / (u - xt);
+    }
+    const size_t off = table_offset(a, P);
+    for (int t = 0; t < P; ++t) {
+      double l;
+      if (hit >= 0) l = (t == hit) ? 1.0 : 0.0;
+      else l = (cheb_weight(t, P) / (u - cheb_node(t, P))) / den;
+      const size_t idx = off + (size_t)t * a * P + i;
+      if constexpr (DF) {
+        const float h = (float)l;
+        ((float2 *)table)[idx] = make_float2(h, (float)(l - (double)h));
+      } else {
+        ((double *)table)[idx] = l;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ double2 as2(double v) { return make_double2(v, 0.0); }
+__device__ __forceinline__ double2 as2(double2 v) { return v; }
+template <typename V> __device__ __forceinline__ V from2(double2 v);
+template <> __device__ __forceinline__ double from2<double>(double2 v) { return v.x; }
+template <> __device__ __forceinline__ double2 from2<double2>(double2 v) { return v; }
+
+__device__ __forceinline__ void set_state(NodesShared &sh, int t, double2 g) {
+  sh.G[t] = g;
+  const float rh = (float)g.x, ih = (float)g.y;
+  sh.Gdf[t] = make_float4(rh, (float)(g.x - (double)rh), ih, (float)(g.y - (double)ih));
+}
+
+// ---------------------------------------------------------------------------
+// One integral, swept by one CTA.  Ltab: the basis table of this a (shared or
+// global memory); rowsum: rows x P slots of 16 bytes in shared memory.
+// ---------------------------------------------------------------------------
+template <int FAM, int PREC>
+__device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, void *__restrict__ rowsum, int P, int d,
+                          int a, int n_last, const double *__restrict__ prm, double *__restrict__ out_slot) {
+  using V = typename FamTraits<FAM>::V;
+  constexpr bool F32 = (PREC != MDI_PREC_FP64);
+  constexpr bool DF = (PREC == MDI_PREC_FP32_EVAL_DF32);
+  constexpr bool CPLX = (FAM == MDI_FAM_OSC);
+  const int tid = threadIdx.x, B = blockDim.x;
+  const int p = tid % P, row = tid / P, rows = B / P;
+  const bool active = row < rows;  // threads beyond rows*P only join barriers
+  const int npts = a * P;
+  const double inv_a = 1.0 / (double)a;
+  const double xi_p = sh.xi[p];
+
+  if (tid < P) set_state(sh, tid, make_double2(1.0, 0.0));
+  __syncthreads();
+
+  for (int k = 1; k < d; ++k) {
+    const AxisParams ap = load_axis(prm, d, k - 1);
+    double2 acc = make_double2(0.0, 0.0);
+    df32 dre{0.f, 0.f}, dim{0.f, 0.f};
+    for (int i = active ? tid : npts; i < npts; i += rows * P) {
+      const int q = i / P;
+      const double u = ((double)q + xi_p) * inv_a;
+      const V f = phi<FAM, F32>(u, ap);
+      if constexpr (!DF) {
+        V g;
+        if (k == 1) {
+          g = VOps<V>::one();
+        } else {
+          const double *L = (const double *)Ltab + i;
+          g = VOps<V>::zero();
+#pragma unroll 4
+          for (int t = 0; t < P; ++t) g = VOps<V>::fma_s(L[(size_t)t * npts], from2<V>(sh.G[t]), g);
+        }
+        acc = c_add(acc, as2(VOps<V>::mul(f, g)));
+      } else {
+        const float2 *L = (const float2 *)Ltab + i;
+        df32 gr{1.f, 0.f}, gi{0.f, 0.f};
+        if (k > 1) {
+          gr = df32{0.f, 0.f};
+#pragma unroll 4
+          for (int t = 0; t < P; ++t) {
+            const float2 l = L[(size_t)t * npts];
+            const float4 gt = sh.Gdf[t];
+            gr = df_add(gr, df_mul(df32{l.x, l.y}, df32{gt.x, gt.y}));
+            if constexpr (CPLX) gi = df_add(gi, df_mul(df32{l.x, l.y}, df32{gt.z, gt.w}));
+          }
+        }
+        if constexpr (CPLX) {
+          const float fr = (float)as2(f).x, fi = (float)as2(f).y;
+          dre = df_add(dre, df_add(df_mul(df32{fr, 0.f}, gr), df_mul(df32{-fi, 0.f}, gi)));
+          dim = df_add(dim, df_add(df_mul(df32{fr, 0.f}, gi), df_mul(df32{fi, 0.f}, gr)));
+        } else {
+          dre = df_add(dre, df_mul(df32{(float)as2(f).x, 0.f}, gr));
+        }
+      }
+    }
+    // Partial rows -> new state at node p, added in row order.
+    if (active) {
+      if constexpr (DF) ((float4 *)rowsum)[row * P + p] = make_float4(dre.hi, dre.lo, dim.hi, dim.lo);
+      else ((double2 *)rowsum)[row * P + p] = acc;
+    }
+    __syncthreads();
+    if (tid < P) {
+      double2 g;
+      if constexpr (DF) {
+        df32 sr{0.f, 0.f}, si{0.f, 0.f};
+        for (int r = 0; r < rows; ++r) {
+          const float4 v = ((const float4 *)rowsum)[r * P + tid];
+          sr = df_add(sr, df32{v.x, v.y});
+          si = df_add(si, df32{v.z, v.w});
+        }
+        g = make_double2(df_to_double(sr) * inv_a, df_to_double(si) * inv_a);
+      } else {
+        double2 s = make_double2(0.0, 0.0);
+        for (int r = 0; r < rows; ++r) s = c_add(s, ((const double2 *)rowsum)[r * P + tid]);
+        g = c_scale(s, inv_a);
+      }
+      set_state(sh, tid, g);
+    }
+    __syncthreads();
+  }
+
+  // Last level: Q = (1/n_last) sum_s phi_d(s/n_last) G_{d-1}(s/n_last).
+  const AxisParams ap = load_axis(prm, d, d - 1);
+  const double inv_n = 1.0 / (double)n_last;
+  V acc = VOps<V>::zero();
+  for (int s = tid; s < n_last; s += B) {
+    const double u = (double)s * inv_n;
+    V g;
+    if (d == 1) {
+      g = VOps<V>::one();
+    } else {
+      double den = 0.0;
+      double2 num = make_double2(0.0, 0.0);
+      int hit = -1;
+      for (int t = 0; t < P; ++t) {
+        if (u == sh.xi[t]) {
+          hit = t;
+          continue;
+        }
+        const double wt = sh.bw[t] / (u - sh.xi[t]);
+        den += wt;
+        num = make_double2(fma(wt, sh.G[t].x, num.x), fma(wt, sh.G[t].y, num.y));
+      }
+      g = hit >= 0 ? from2<V>(sh.G[hit]) : from2<V>(c_scale(num, 1.0 / den));
+    }
+    acc = VOps<V>::add(acc, VOps<V>::mul(phi<FAM, F32>(u, ap), g));
+  }
+  const V tot = block_sum(acc, (V *)sh.red);
+  if (tid == 0) {
+    if constexpr (CPLX) {
+      double sn, cs;
+      sincos(kTwoPi * prm[d], &sn, &cs);
+      *out_slot = (cs * tot.x - sn * tot.y) * inv_n;
+    } else {
+      *out_slot = tot * inv_n;
+    }
+  }
+  __syncthreads();
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi_batch_desc *__restrict__ descs,
+                                                                       const int32_t *__restrict__ order, int count,
+                                                                       mdi_batch_desc single,
+                                                                       const double *__restrict__ pool,
+                                                                       const void *__restrict__ tables, int P,
+                                                                       double *__restrict__ out,
+                                                                       unsigned *__restrict__ counter,
+                                                                       unsigned expect_tag) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  NodesShared &sh = *reinterpret_cast<NodesShared *>(dyn_smem);
+  unsigned char *rowsum = dyn_smem + align16(sizeof(NodesShared));
+  unsigned char *tab_smem = rowsum + rows_bytes(blockDim.x, P);
+  for (int t = threadIdx.x; t < P; t += blockDim.x) {
+    sh.xi[t] = cheb_node(t, P);
+    sh.bw[t] = cheb_weight(t, P);
+  }
+  int staged_a = -1;
+  // counter[0]: next work item; counter[1]: CTAs finished; counter[2]: preparation tag.
+  const bool prepared = counter[2] == expect_tag;
+  while (true) {
+    if (threadIdx.x == 0) sh.inst = (int)atomicAdd(&counter[0], 1u);
+    __syncthreads();
+    const int slot = sh.inst;
+    __syncthreads();
+    if (slot >= count) break;
+    const int inst = order ? order[slot] : slot;
+    if (inst < 0 || inst >= count) continue;  // an order entry outside the batch is skipped
+    const mdi_batch_desc ds = descs ? descs[inst] : single;
+    const int a = ds.a;
+    if (!prepared || ds.family < MDI_FAM_EXP || ds.family > MDI_FAM_PEAK || ds.d < 1 || ds.d > MDI_BATCH_MAX_D ||
+        a < 1 || a > kNodesAMax || ds.n_last < 1 || ds.n_last > 4096 || ds.param_offset < 0) {
+      if (threadIdx.x == 0) out[inst] = __longlong_as_double(0x7ff8000000000000ll);  // NaN marks a bad descriptor
+      continue;
+    }
+    const size_t tbytes = (size_t)a * P * P * 8;
+    const unsigned char *gtab = (const unsigned char *)tables + table_offset(a, P) * 8;
+    const void *Ltab = gtab;
+    if (tbytes <= (size_t)kNodesSmemTable && ds.d > 1) {
+      if (staged_a != a) {
+        const double2 *src = (const double2 *)gtab;  // tbytes is a multiple of 16 (P*P*8, P even or a*P*P even)
+        double2 *dst = (double2 *)tab_smem;
+        for (size_t i = threadIdx.x; i < tbytes / 16; i += blockDim.x) dst[i] = src[i];
+        if ((tbytes & 15) && threadIdx.x == 0) ((double *)tab_smem)[tbytes / 8 - 1] = ((const double *)gtab)[tbytes / 8 - 1];
+        staged_a = a;
+        __syncthreads();
+      }
+      Ltab = tab_smem;
+    }
+    const double *prm = pool + ds.param_offset;
+    switch (ds.family) {
+      case MDI_FAM_EXP: sweep_one<MDI_FAM_EXP, PREC>(sh, Ltab, rowsum, P, ds.d, a, ds.n_last, prm, out + inst); break;
+      case MDI_FAM_OSC: sweep_one<MDI_FAM_OSC, PREC>(sh, Ltab, rowsum, P, ds.d, a, ds.n_last, prm, out + inst); break;
+      case MDI_FAM_GAUSS: sweep_one<MDI_FAM_GAUSS, PREC>(sh, Ltab, rowsum, P, ds.d, a, ds.n_last, prm, out + inst); break;
+      default: sweep_one<MDI_FAM_PEAK, PREC>(sh, Ltab, rowsum, P, ds.d, a, ds.n_last, prm, out + inst); break;
+    }
+  }
+  // The last CTA to finish re-arms the queue for the next call on this workspace.
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&counter[1], 1u) == gridDim.x - 1) {
+      atomicExch(&counter[0], 0u);
+      atomicExch(&counter[1], 0u);
+    }
+  }
+}
+
+// Zeroes the queue counters and stamps the preparation tag.
+__global__ void nodes_arm_kernel(unsigned *counter, unsigned tag) {
+  counter[0] = 0u;
+  counter[1] = 0u;
+  counter[2] = tag;
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+NodesConfig nodes_config(const mdi_opts *opts) {
+  NodesConfig c{16, 256, 0, MDI_PREC_FP64};
+  if (opts) {
+    if (opts->nodes) c.P = opts->nodes;
+    if (opts->block) c.block = opts->block;
+    c.ctas_per_sm = opts->ctas_per_sm;
+    c.precision = opts->precision;
+  }
+  return c;
+}
+
+static bool config_ok(const NodesConfig &c) {
+  if (c.P < 2 || c.P > kNodesPMax || (c.P & 1)) return false;  // even P keeps tables 16-byte aligned
+  if (c.block < 32 || c.block > kNodesMaxBlock || c.block % 32 || c.block < c.P) return false;
+  if (c.precision < MDI_PREC_FP64 || c.precision > MDI_PREC_FP32_EVAL_DF32) return false;
+  return c.ctas_per_sm >= 0 && c.ctas_per_sm <= 32;
+}
+
+static size_t counter_bytes() { return align_up(4 * sizeof(unsigned)); }
+
+// Tag stamped by the preparation: node count and table format.
+static unsigned nodes_tag(const NodesConfig &c) {
+  return 0x4D440000u | ((unsigned)c.P << 4) | (c.precision == MDI_PREC_FP32_EVAL_DF32 ? 1u : 0u);
+}
+
+size_t nodes_batched_workspace_bytes(int count, const NodesConfig &cfg) {
+  (void)count;
+  return counter_bytes() + align_up(table_bytes(cfg.P));
+}
+size_t nodes_single_workspace_bytes(const NodesConfig &cfg) { return nodes_batched_workspace_bytes(1, cfg); }
+
+static bool ws_ok(const void *ws, size_t bytes, const NodesConfig &cfg) {
+  return ws && ((uintptr_t)ws % kAlign) == 0 && bytes >= nodes_batched_workspace_bytes(1, cfg);
+}
+
+mdi_status nodes_prepare(const NodesConfig &cfg, void *workspace, size_t ws_bytes, cudaStream_t stream) {
+  if (!config_ok(cfg)) return MDI_EINVAL;
+  if (!ws_ok(workspace, ws_bytes, cfg)) return MDI_EWORKSPACE;
+  unsigned *counter = (unsigned *)workspace;
+  void *tables = (char *)workspace + counter_bytes();
+  const int table_grid = sm_count() * 2;
+  if (cfg.precision == MDI_PREC_FP32_EVAL_DF32) nodes_table_kernel<true><<<table_grid, 256, 0, stream>>>(cfg.P, tables);
+  else nodes_table_kernel<false><<<table_grid, 256, 0, stream>>>(cfg.P, tables);
+  mdi_status st = check_launch();
+  if (st != MDI_OK) return st;
+  nodes_arm_kernel<<<1, 1, 0, stream>>>(counter, nodes_tag(cfg));
+  return check_launch();
+}
+
+template <int PREC>
+static mdi_status launch_nodes(const mdi_batch_desc *descs, const int32_t *order, int count,
+                               const mdi_batch_desc &single, const double *pool, const NodesConfig &cfg, double *out,
+                               void *ws, cudaStream_t stream) {
+  unsigned *counter = (unsigned *)ws;
+  void *tables = (char *)ws + counter_bytes();
+  const size_t smem = nodes_smem_bytes(cfg.block, cfg.P);
+  static thread_local bool attr_set[3] = {false, false, false};
+  if (!attr_set[PREC]) {
+    cudaError_t e = cudaFuncSetAttribute(nodes_batched_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)nodes_smem_bytes(kNodesMaxBlock, 2));
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      return MDI_ECUDA;
+    }
+    attr_set[PREC] = true;
+  }
+  int per_sm = cfg.ctas_per_sm;
+  if (per_sm == 0) {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, nodes_batched_kernel<PREC>, cfg.block, smem);
+    per_sm = std::max(1, occ);
+  }
+  const int grid = std::max(1, std::min(count, sm_count() * per_sm));
+  nodes_batched_kernel<PREC><<<grid, cfg.block, smem, stream>>>(descs, order, count, single, pool, tables, cfg.P,
+                                                                 out, counter, nodes_tag(cfg));
+  return check_launch();
+}
+
+static mdi_status dispatch_nodes(const mdi_batch_desc *descs, const int32_t *order, int count,
+                                 const mdi_batch_desc &single, const double *pool, const NodesConfig &cfg,
+                                 double *out, void *ws, cudaStream_t stream) {
+  switch (cfg.precision) {
+    case MDI_PREC_FP64: return launch_nodes<MDI_PREC_FP64>(descs, order, count, single, pool, cfg, out, ws, stream);
+    case MDI_PREC_FP32_EVAL_FP64:
+      return launch_nodes<MDI_PREC_FP32_EVAL_FP64>(descs, order, count, single, pool, cfg, out, ws, stream);
+    default: return launch_nodes<MDI_PREC_FP32_EVAL_DF32>(descs, order, count, single, pool, cfg, out, ws, stream);
+  }
+}
+
+mdi_status nodes_batched_launch(const mdi_batch_desc *descs, const int32_t *order, int count,
+                                const double *param_pool, const NodesConfig &cfg, double *out, void *workspace,
+                                size_t ws_bytes, cudaStream_t stream) {
+  if (!descs || !param_pool || !out || count < 1) return MDI_EINVAL;
+  if (!config_ok(cfg)) return MDI_EINVAL;
+  if (!ws_ok(workspace, ws_bytes, cfg)) return MDI_EWORKSPACE;
+  mdi_batch_desc none{};
+  return dispatch_nodes(descs, order, count, none, param_pool, cfg, out, workspace, stream);
+}
+
+mdi_status nodes_single_launch(int family, int d, int64_t a, int64_t n_last, const double *params,
+                               const NodesConfig &cfg, double *out, void *workspace, size_t ws_bytes,
+                               cudaStream_t stream) {
+  if (d < 1 || d > MDI_BATCH_MAX_D || a < 1 || a > kNodesAMax || n_last < 1 || n_last > 4096) return MDI_EUNSUPPORTED;
+  mdi_status st = nodes_prepare(cfg, workspace, ws_bytes, stream);
+  if (st != MDI_OK) return st;
+  mdi_batch_desc one{family, d, (int32_t)a, (int32_t)n_last, 0, 0};
+  return dispatch_nodes(nullptr, nullptr, 1, one, params, cfg, out, workspace, stream);
+}
+
+}  // namespace mdi

@@ -1,0 +1,236 @@
+// slr.cu -- the standard lattice rule (SLR), eq. (1.2) over the rank-1 points of
+// eq. (2.1): Q = (1/n) sum_{j<n} f({j z / n}).
+//
+// Every point is generated and evaluated: this is the paper's baseline method and
+// the parity partner of the MDI-LR sweep.  Each thread owns a contiguous run of
+// indices j; it forms r_i = j0 z_i mod n once (exact 64-bit double-and-add) and
+// then steps r_i <- r_i + z_i (mod n), so every coordinate numerator is an exact
+// integer (n < 2^63 keeps r_i + z_i below 2^64).  Coordinates x_i = r_i / n are
+// formed in FP64.  Per-thread FP64 partial sums are reduced by a fixed tree into
+// one partial per CTA, and a second one-CTA kernel adds the partials in index
+// order, so the result is bitwise reproducible.
+#include <algorithm>
+
+#include "mdi_common.cuh"
+#include "mdi_internal.h"
+
+namespace mdi {
+
+constexpr int kSlrMaxD = 256;
+constexpr int kSlrThreads = 256;
+constexpr int kSlrMinRun = 32;  // minimum indices per thread (amortises the set-up)
+
+struct SlrArgs {
+  uint64_t n;
+  double inv_n;
+  int d;
+  int pad;
+  uint64_t z[kSlrMaxD];  // reduced mod n
+};
+
+// (x * y) mod n for x, y < n < 2^63 by binary double-and-add: exact, no 128-bit type.
+__device__ __forceinline__ uint64_t mulmod_u63(uint64_t x, uint64_t y, uint64_t n) {
+  uint64_t r = 0;
+  while (y) {
+    if (y & 1ull) {
+      r += x;
+      if (r >= n) r -= n;
+    }
+    x += x;
+    if (x >= n) x -= n;
+    y >>= 1;
+  }
+  return r;
+}
+
+// Index run of thread `tid` out of `nthreads` covering [0, n).
+__device__ __forceinline__ void thread_run(uint64_t n, uint64_t tid, uint64_t nthreads, uint64_t &j0,
+                                           uint64_t &j1) {
+  uint64_t per = n / nthreads, extra = n % nthreads;
+  j0 = tid * per + (tid < extra ? tid : extra);
+  j1 = j0 + per + (tid < extra ? 1 : 0);
+}
+
+template <int FAM, bool FP32EVAL, int MAXD>
+__global__ void __launch_bounds__(kSlrThreads) slr_kernel(const __grid_constant__ SlrArgs args,
+                                                          const double *__restrict__ params,
+                                                          double *__restrict__ partials) {
+  __shared__ double s_c[MAXD], s_w[MAXD], s_ic2[MAXD];
+  __shared__ double s_red[kSlrThreads / kWarp];
+  constexpr int kUnroll = MAXD <= 32 ? MAXD : 1;  // the wide bucket keeps r[] in local memory
+  const int d = args.d;
+  for (int i = threadIdx.x; i < d; i += blockDim.x) {
+    s_c[i] = params[i];
+    s_w[i] = params[d + i];
+    s_ic2[i] = 1.0 / (params[i] * params[i]);
+  }
+  __syncthreads();
+  const double u2pi = (FAM == MDI_FAM_OSC) ? kTwoPi * params[d] : 0.0;
+
+  const uint64_t n = args.n;
+  const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t j0, j1;
+  thread_run(n, tid, nthreads, j0, j1);
+
+  uint64_t r[MAXD];
+#pragma unroll(kUnroll)
+  for (int i = 0; i < MAXD; ++i)
+    if (i < d) r[i] = (j0 < j1) ? mulmod_u63(j0, args.z[i], n) : 0;
+
+  double acc = 0.0;
+  for (uint64_t j = j0; j < j1; ++j) {
+    double f;
+    if constexpr (FAM == MDI_FAM_PEAK) {
+      double p = 1.0, den = 1.0;
+#pragma unroll(kUnroll)
+      for (int i = 0; i < MAXD; ++i) {
+        if (i < d) {
+          double t = fma((double)r[i], args.inv_n, -s_w[i]);
+          den *= fma(t, t, s_ic2[i]);
+          if ((i & 7) == 7) { p /= den; den = 1.0; }
+        }
+      }
+      f = p / den;
+      if constexpr (FP32EVAL) f = (double)(float)f;
+    } else {
+      double s = 0.0;
+      float sf = 0.0f;
+#pragma unroll(kUnroll)
+      for (int i = 0; i < MAXD; ++i) {
+        if (i < d) {
+          double x = (double)r[i] * args.inv_n;
+          if constexpr (FAM == MDI_FAM_GAUSS) {
+            if constexpr (FP32EVAL) {
+              float t = (float)s_c[i] * ((float)x - (float)s_w[i]);
+              sf = fmaf(t, t, sf);
+            } else {
+              double t = s_c[i] * (x - s_w[i]);
+              s = fma(t, t, s);
+            }
+          } else {
+            if constexpr (FP32EVAL) sf = fmaf((float)s_c[i], (float)x, sf);
+            else s = fma(s_c[i], x, s);
+          }
+        }
+      }
+      if constexpr (FAM == MDI_FAM_EXP) f = FP32EVAL ? (double)expf(sf) : exp(s);
+      else if constexpr (FAM == MDI_FAM_GAUSS) f = FP32EVAL ? (double)expf(-sf) : exp(-s);
+      else f = FP32EVAL ? (double)cosf((float)u2pi + sf) : cos(u2pi + s);
+    }
+    acc += f;
+#pragma unroll(kUnroll)
+    for (int i = 0; i < MAXD; ++i) {
+      if (i < d) {
+        uint64_t v = r[i] + args.z[i];
+        r[i] = (v >= n) ? v - n : v;
+      }
+    }
+  }
+  double b = block_sum(acc, s_red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = b;
+}
+
+// Adds `count` partials in a fixed order and writes scale * sum.
+__global__ void __launch_bounds__(kSlrThreads) sum_partials_kernel(const double *__restrict__ partials, int count,
+                                                                   double inv_count_scale, double *__restrict__ out) {
+  __shared__ double s_red[kSlrThreads / kWarp];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) acc += partials[i];
+  double b = block_sum(acc, s_red);
+  if (threadIdx.x == 0) out[0] = b * inv_count_scale;
+}
+
+__global__ void lattice_indices_kernel(const __grid_constant__ SlrArgs args, uint64_t j0, uint64_t count,
+                                       uint64_t runs, int64_t *__restrict__ r_out) {
+  // Same generator as slr_kernel: run `tid` covers a contiguous slice of [0, count).
+  uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= runs) return;
+  uint64_t t0, t1;
+  thread_run(count, tid, runs, t0, t1);
+  const uint64_t n = args.n;
+  for (int i = 0; i < args.d; ++i) {
+    uint64_t jj = (j0 + t0) % n;
+    uint64_t r = mulmod_u63(jj, args.z[i], n);
+    for (uint64_t t = t0; t < t1; ++t) {
+      r_out[t * (uint64_t)args.d + i] = (int64_t)r;
+      uint64_t v = r + args.z[i];
+      r = (v >= n) ? v - n : v;
+    }
+  }
+}
+
+static int slr_grid(uint64_t n) {
+  uint64_t max_threads = (uint64_t)sm_count() * 8 * kSlrThreads;
+  uint64_t want = (n + kSlrMinRun - 1) / kSlrMinRun;
+  uint64_t threads = std::min(max_threads, want);
+  return (int)std::max<uint64_t>(1, (threads + kSlrThreads - 1) / kSlrThreads);
+}
+
+size_t slr_workspace_bytes(int d, int64_t n) {
+  (void)d;
+  return align_up(sizeof(double) * (size_t)slr_grid((uint64_t)n));
+}
+
+template <int FAM, bool F32, int MAXD>
+static void launch_slr(int grid, const SlrArgs &args, const double *params, double *partials, cudaStream_t s) {
+  slr_kernel<FAM, F32, MAXD><<<grid, kSlrThreads, 0, s>>>(args, params, partials);
+}
+
+template <int FAM, bool F32>
+static void launch_slr_d(int grid, const SlrArgs &args, const double *params, double *partials, cudaStream_t s) {
+  if (args.d <= 8) launch_slr<FAM, F32, 8>(grid, args, params, partials, s);
+  else if (args.d <= 32) launch_slr<FAM, F32, 32>(grid, args, params, partials, s);
+  else launch_slr<FAM, F32, kSlrMaxD>(grid, args, params, partials, s);
+}
+
+mdi_status slr_launch(int family, int d, int64_t n, const int64_t *z, const double *params, int precision,
+                      double *out, void *workspace, size_t ws_bytes, cudaStream_t stream) {
+  if (d < 1 || d > kSlrMaxD || n < 1 || !z || !params || !out) return MDI_EINVAL;
+  if (family < MDI_FAM_EXP || family > MDI_FAM_PEAK) return MDI_EINVAL;
+  if (precision != MDI_PREC_FP64 && precision != MDI_PREC_FP32_EVAL_FP64) return MDI_EUNSUPPORTED;
+  for (int i = 0; i < d; ++i)
+    if (z[i] < 0 || z[i] >= n) return MDI_EINVAL;
+  if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < slr_workspace_bytes(d, n)) return MDI_EWORKSPACE;
+  SlrArgs args{};
+  args.n = (uint64_t)n;
+  args.inv_n = 1.0 / (double)n;
+  args.d = d;
+  for (int i = 0; i < d; ++i) args.z[i] = (uint64_t)z[i];
+  const int grid = slr_grid((uint64_t)n);
+  double *partials = (double *)workspace;
+  const bool f32 = precision == MDI_PREC_FP32_EVAL_FP64;
+  switch (family) {
+    case MDI_FAM_EXP: f32 ? launch_slr_d<MDI_FAM_EXP, true>(grid, args, params, partials, stream)
+                          : launch_slr_d<MDI_FAM_EXP, false>(grid, args, params, partials, stream); break;
+    case MDI_FAM_OSC: f32 ? launch_slr_d<MDI_FAM_OSC, true>(grid, args, params, partials, stream)
+                          : launch_slr_d<MDI_FAM_OSC, false>(grid, args, params, partials, stream); break;
+    case MDI_FAM_GAUSS: f32 ? launch_slr_d<MDI_FAM_GAUSS, true>(grid, args, params, partials, stream)
+                            : launch_slr_d<MDI_FAM_GAUSS, false>(grid, args, params, partials, stream); break;
+    default: f32 ? launch_slr_d<MDI_FAM_PEAK, true>(grid, args, params, partials, stream)
+                 : launch_slr_d<MDI_FAM_PEAK, false>(grid, args, params, partials, stream); break;
+  }
+  mdi_status st = check_launch();
+  if (st != MDI_OK) return st;
+  sum_partials_kernel<<<1, kSlrThreads, 0, stream>>>(partials, grid, 1.0 / (double)n, out);
+  return check_launch();
+}
+
+mdi_status lattice_indices_launch(int d, int64_t n, const int64_t *z, int64_t j0, int64_t count, int64_t *r_out,
+                                  cudaStream_t stream) {
+  if (d < 1 || d > kSlrMaxD || n < 1 || !z || !r_out || j0 < 0 || count < 1) return MDI_EINVAL;
+  SlrArgs args{};
+  args.n = (uint64_t)n;
+  args.inv_n = 1.0 / (double)n;
+  args.d = d;
+  for (int i = 0; i < d; ++i) {
+    if (z[i] < 0 || z[i] >= n) return MDI_EINVAL;
+    args.z[i] = (uint64_t)z[i];
+  }
+  uint64_t runs = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)count / 4, 65536));
+  int blocks = (int)((runs + 255) / 256);
+  lattice_indices_kernel<<<blocks, 256, 0, stream>>>(args, (uint64_t)j0, (uint64_t)count, runs, r_out);
+  return check_launch();
+}
+
+}  // namespace mdi

@@ -1,0 +1,123 @@
+"""Host-side checks of the C ABI: the library loads, exports every symbol that
+include/mdi_lr.h declares, validates arguments before touching the GPU, and its
+scheduler orders work longest-first.  No kernel runs here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2404_08867_gb300 import _ffi
+import paper_2404_08867_gb300 as mdi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mdi_lr.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2404_08867_gb300 import build
+    build.build()
+    return _ffi.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+char\s*\*|mdi_status|int32_t)\s*(\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_expected_entry_points():
+    names = declared_functions()
+    for must in ("lattice_rule_integrate", "mdi_lr_integrate", "mdi_lr_integrate_batched", "mdi_batch_plan"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert names, "no declarations parsed"
+    for name in names:
+        assert hasattr(lib, name), f"libmdilr.so does not export {name}"
+        assert name in _ffi.SIGNATURES, f"binding has no signature for {name}"
+
+
+def test_abi_version_and_status_strings(lib):
+    assert lib.mdi_abi_version() == 1
+    for code in range(6):
+        s = lib.mdi_status_string(code).decode()
+        assert s.startswith("MDI_")
+    assert b"unknown" in lib.mdi_status_string(99)
+
+
+def test_batch_desc_layout():
+    assert _ffi.BATCH_DESC_DTYPE.itemsize == 32
+    assert ctypes.sizeof(_ffi.MdiOpts) == 32
+
+
+def _null():
+    return ctypes.c_void_p(0)
+
+
+def test_lattice_rule_rejects_bad_arguments(lib):
+    z = np.array([1, 5, 25], dtype=np.int64)
+    zp = z.ctypes.data_as(ctypes.c_void_p)
+    fake = ctypes.c_void_p(0x1000)
+    # d out of range, n < 1, null device pointers, z_i >= n, unknown family
+    assert lib.lattice_rule_integrate(0, 0, 100, zp, fake, 0, fake, fake, 4096, _null()) == _ffi.MDI_EINVAL
+    assert lib.lattice_rule_integrate(0, 3, 0, zp, fake, 0, fake, fake, 4096, _null()) == _ffi.MDI_EINVAL
+    assert lib.lattice_rule_integrate(0, 3, 100, zp, _null(), 0, fake, fake, 4096, _null()) == _ffi.MDI_EINVAL
+    assert lib.lattice_rule_integrate(0, 3, 20, zp, fake, 0, fake, fake, 4096, _null()) == _ffi.MDI_EINVAL
+    assert lib.lattice_rule_integrate(7, 3, 100, zp, fake, 0, fake, fake, 4096, _null()) == _ffi.MDI_EINVAL
+    assert lib.lattice_rule_integrate(0, 3, 100, zp, fake, 2, fake, fake, 4096, _null()) == _ffi.MDI_EUNSUPPORTED
+    # workspace missing or misaligned
+    assert lib.lattice_rule_integrate(0, 3, 100, zp, fake, 0, fake, _null(), 4096, _null()) == _ffi.MDI_EWORKSPACE
+    assert lib.lattice_rule_integrate(0, 3, 100, zp, fake, 0, fake, ctypes.c_void_p(0x1008), 4096,
+                                      _null()) == _ffi.MDI_EWORKSPACE
+
+
+def test_mdi_rejects_bad_arguments(lib):
+    fake = ctypes.c_void_p(0x1000)
+    o = _ffi.MdiOpts()
+    assert lib.mdi_lr_integrate(0, 0, 16, 16, fake, ctypes.byref(o), fake, fake, 1 << 20, _null()) == _ffi.MDI_EINVAL
+    assert lib.mdi_lr_integrate(0, 4, 0, 16, fake, ctypes.byref(o), fake, fake, 1 << 20, _null()) == _ffi.MDI_EINVAL
+    o.reserved[0] = 1
+    assert lib.mdi_lr_integrate(0, 4, 16, 16, fake, ctypes.byref(o), fake, fake, 1 << 20, _null()) == _ffi.MDI_EINVAL
+    o = _ffi.MdiOpts()
+    o.state = _ffi.STATE["closed"]
+    assert lib.mdi_lr_integrate(2, 4, 16, 16, fake, ctypes.byref(o), fake, fake, 1 << 20,
+                                _null()) == _ffi.MDI_EUNSUPPORTED
+    o.state = _ffi.STATE["exact"]
+    b = ctypes.c_size_t()
+    assert lib.mdi_lr_workspace_size(2, 20, 16, 16, ctypes.byref(o), ctypes.byref(b)) == _ffi.MDI_EOVERFLOW
+    assert lib.mdi_lr_workspace_size(2, 4, 16, 16, ctypes.byref(o), ctypes.byref(b)) == _ffi.MDI_OK
+    o.state = _ffi.STATE["nodes"]
+    o.nodes = 15  # odd P is refused
+    assert lib.mdi_lr_integrate(2, 4, 16, 16, fake, ctypes.byref(o), fake, fake, 1 << 30, _null()) == _ffi.MDI_EINVAL
+    o.nodes = 16
+    assert lib.mdi_lr_integrate(2, 4, 65, 16, fake, ctypes.byref(o), fake, fake, 1 << 30,
+                                _null()) == _ffi.MDI_EUNSUPPORTED
+
+
+def test_batch_plan_is_longest_first_permutation(lib):
+    rng = np.random.default_rng(1)
+    n = 500
+    a = rng.integers(8, 33, n)
+    descs = mdi.make_batch_descs(["gauss"] * n, rng.integers(6, 21, n), a, a, np.arange(n) * 40)
+    order = mdi.mdi_batch_plan(descs)
+    assert sorted(order.tolist()) == list(range(n))
+    # one family, n_last = a: the work is dominated by the (d - 1) * a cluster points;
+    # the last axis adds less than 3 such units for a <= 32
+    work = (descs["d"][order] - 1) * descs["a"][order]
+    assert np.all(np.diff(work) <= 3)
+    assert work[0] == work.max() and work[-1] <= work.min() + 3
+    bad = descs.copy()
+    bad["a"][3] = 65
+    with pytest.raises(mdi.MdiError):
+        mdi.mdi_batch_plan(bad)
+
+
+def test_workspace_queries(lib):
+    assert mdi.lattice_rule_workspace_size(4, 65536) >= 8
+    assert mdi.mdi_lr_workspace_size("exp", 1000, 16, 16, state="closed") >= 8 * 1000
+    assert mdi.mdi_lr_batched_workspace_size(4096, nodes=16) > 4 * 2**20

@@ -1,0 +1,226 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+FP64 results must agree within 1e-12 relative (absolute 1e-12 for the
+oscillatory family, whose value can be near zero while |f| <= 1); lattice indices
+must agree bit for bit.  Float-evaluation modes are held to the error a float
+evaluation of phi allows (a few 1e-7 relative per factor, stated per test).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as o
+import paper_2404_08867_gb300 as mdi
+from paper_2404_08867_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2404_08867_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def close(got, ref, fam, tol=TOL):
+    if fam == "osc":
+        assert abs(got - ref) <= tol, (got, ref, abs(got - ref))
+    else:
+        assert abs(got - ref) <= tol * abs(ref), (got, ref, abs(got - ref) / abs(ref))
+
+
+# ----------------------------------------------------------------------------
+# Lattice indices: bit-exact
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("d,n,j0,count", [(4, 65536, 0, 70000), (5, 2**63 - 25, 2**63 - 1000, 3000),
+                                          (3, 10**18 + 9, 12345678901, 777), (1, 1, 0, 5), (7, 97, 50, 333)])
+def test_lattice_indices_bit_exact(d, n, j0, count):
+    rng = np.random.default_rng(d)
+    z = ([1] + [int(v) for v in rng.integers(1, min(n, 2**62), size=d - 1)]) if n > 1 else [0] * d
+    got = mdi.mdi_debug_lattice_indices(n, z, j0, count).cpu().numpy().astype(np.uint64)
+    np.testing.assert_array_equal(got, o.lattice_indices(d, n, z, j0, count))
+    for t in (0, count // 2, count - 1):  # Python's own integers on sampled rows
+        assert [int(v) for v in got[t]] == [((j0 + t) % n) * zi % n for zi in z]
+
+
+# ----------------------------------------------------------------------------
+# Standard lattice rule
+# ----------------------------------------------------------------------------
+def test_slr_small_workload():
+    """d = 4, n = 65536, z = z(12345), f = exp(sum x_j / j): the plain kernel."""
+    w = inputs.small_exp()
+    n = 16**4
+    z = o.korobov_z(4, inputs.SMALL_SLR_A, n)
+    got = mdi.lattice_rule_integrate("exp", dev(w.params), n, z.astype(np.int64)).item()
+    close(got, o.slr("exp", 4, n, z, w.c, w.w), "exp")
+
+
+@pytest.mark.parametrize("fam", ["exp", "osc", "gauss", "peak"])
+@pytest.mark.parametrize("d,n,a", [(1, 1, 1), (1, 1000, 1), (3, 100003, 47), (9, 65537, 3), (40, 20011, 5),
+                                   (6, 1_000_001, 10)])
+def test_slr_matches_oracle(fam, d, n, a):
+    params = inputs.random_product(fam, d, seed=d + n)
+    z = o.korobov_z(d, a, n)
+    got = mdi.lattice_rule_integrate(fam, dev(params), n, z.astype(np.int64)).item()
+    close(got, o.slr(fam, d, n, z, params[:d], params[d:]), fam)
+
+
+@pytest.mark.parametrize("fam", ["exp", "gauss", "peak", "osc"])
+def test_slr_fp32_eval_error(fam):
+    d, n, a = 5, 200003, 21
+    params = inputs.random_product(fam, d, seed=3)
+    z = o.korobov_z(d, a, n)
+    got = mdi.lattice_rule_integrate(fam, dev(params), n, z.astype(np.int64), precision="fp32_eval_fp64").item()
+    close(got, o.slr(fam, d, n, z, params[:d], params[d:]), fam, tol=2e-6)
+
+
+def test_slr_is_deterministic():
+    params = inputs.random_product("gauss", 8, seed=1)
+    z = o.korobov_z(8, 7, 3_000_017).astype(np.int64)
+    r = [mdi.lattice_rule_integrate("gauss", dev(params), 3_000_017, z).item() for _ in range(3)]
+    assert r[0] == r[1] == r[2]
+
+
+# ----------------------------------------------------------------------------
+# MDI-LR, exact state: equals the lattice rule on the same point set
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("fam", ["exp", "osc", "gauss", "peak"])
+@pytest.mark.parametrize("d,a,nd", [(4, 16, 16), (1, 7, 7), (1, 1, 9), (3, 1, 5), (5, 3, 7), (6, 16, 16),
+                                    (2, 100, 37), (8, 5, 2)])
+def test_exact_state_matches_oracle(fam, d, a, nd):
+    params = inputs.random_product(fam, d, seed=7 * d + a)
+    got = mdi.mdi_lr_integrate(fam, dev(params), d, a, nd, state="exact").item()
+    ref = o.mdi_exact(fam, d, a, nd, params[:d], params[d:])
+    close(got, ref, fam)
+    if d * math.log2(max(a, 2)) <= 20:
+        n = nd * a ** (d - 1)
+        close(got, o.slr(fam, d, n, o.korobov_z(d, a, n), params[:d], params[d:]), fam)
+
+
+def test_small_workload_mdi_equals_slr_on_same_lattice():
+    """The sweep with a = N = 16 and the plain kernel with a = 16, n = 16^4 give the
+    same number (Lemma 3.2: the transformed lattice is the full grid)."""
+    w = inputs.small_exp()
+    n = 16**4
+    mdi_val = mdi.mdi_lr_integrate("exp", dev(w.params), 4, 16, 16, state="exact").item()
+    slr_val = mdi.lattice_rule_integrate("exp", dev(w.params), n, o.korobov_z(4, 16, n).astype(np.int64)).item()
+    assert abs(mdi_val - slr_val) <= TOL * abs(slr_val)
+    close(mdi_val, o.slr("exp", 4, n, o.korobov_z(4, 16, n), w.c, w.w), "exp")
+
+
+# ----------------------------------------------------------------------------
+# MDI-LR, closed state
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("fam", ["exp", "osc"])
+@pytest.mark.parametrize("d,a,nd", [(4, 16, 16), (1, 5, 5), (7, 1, 3), (50, 32, 32), (1000, 16, 16),
+                                    (2000, 2, 5), (300, 100000, 100000)])
+def test_closed_state_matches_oracle(fam, d, a, nd):
+    params = inputs.random_product(fam, d, seed=d, c_range=(0.05, 1.0))
+    if fam == "osc":
+        params[d] = 0.3
+    got = mdi.mdi_lr_integrate(fam, dev(params), d, a, nd, state="closed").item()
+    close(got, o.mdi_closed(fam, d, a, nd, params[:d], params[d:]), fam)
+
+
+def test_closed_scale_workload():
+    w = inputs.scale_exp(1000, 16)
+    got = mdi.mdi_lr_integrate("exp", dev(w.params), 1000, 16, 16).item()
+    close(got, o.mdi_closed("exp", 1000, 16, 16, w.c, w.w), "exp")
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32_eval_fp64", 1e-5), ("fp32_eval_df32", 1e-5)])
+def test_closed_precision_modes(prec, tol):
+    w = inputs.oscillatory(50, 32, seed=0)
+    got = mdi.mdi_lr_integrate("osc", dev(w.params), 50, 32, 32, state="closed", precision=prec).item()
+    close(got, o.mdi_closed("osc", 50, 32, 32, w.c, w.w), "osc", tol=tol)
+
+
+# ----------------------------------------------------------------------------
+# MDI-LR, node state
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("fam", ["gauss", "peak", "exp", "osc"])
+@pytest.mark.parametrize("d,a,nd,P", [(4, 16, 16, 16), (1, 9, 9, 16), (2, 1, 5, 16), (12, 8, 8, 8), (6, 32, 13, 32),
+                                      (5, 64, 64, 16), (30, 20, 20, 16), (7, 3, 100, 4)])
+def test_nodes_state_matches_oracle(fam, d, a, nd, P):
+    params = inputs.random_product(fam, d, seed=3 * d + a)
+    got = mdi.mdi_lr_integrate(fam, dev(params), d, a, nd, state="nodes", nodes=P).item()
+    close(got, o.mdi_nodes(fam, d, a, nd, P, params[:d], params[d:]), fam)
+
+
+@pytest.mark.parametrize("block", [32, 64, 128, 512])
+def test_nodes_block_shapes(block):
+    w = inputs.gaussian(40, 16, seed=2)
+    got = mdi.mdi_lr_integrate("gauss", dev(w.params), 40, 16, 16, state="nodes", block=block).item()
+    close(got, o.mdi_nodes("gauss", 40, 16, 16, 16, w.c, w.w), "gauss")
+
+
+def test_nodes_differentiation_workload_forward():
+    w = inputs.gaussian(100, 16, seed=0)
+    got = mdi.mdi_lr_integrate("gauss", dev(w.params), 100, 16, 16).item()
+    close(got, o.mdi_nodes("gauss", 100, 16, 16, 16, w.c, w.w), "gauss")
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32_eval_fp64", 2e-5), ("fp32_eval_df32", 2e-5)])
+@pytest.mark.parametrize("fam", ["gauss", "peak", "osc"])
+def test_nodes_precision_modes(prec, tol, fam):
+    w = inputs.oscillatory(50, 32, seed=1) if fam == "osc" else inputs.gaussian(50, 32, seed=1)
+    params = w.params if fam == "osc" else inputs.random_product(fam, 50, seed=4)
+    got = mdi.mdi_lr_integrate(fam, dev(params), 50, 32, 32, state="nodes", precision=prec).item()
+    close(got, o.mdi_nodes(fam, 50, 32, 32, 16, params[:50], params[50:]), fam, tol=tol)
+
+
+# ----------------------------------------------------------------------------
+# Batched node state: the bench's launch configuration
+# ----------------------------------------------------------------------------
+def _batch_to_device(b):
+    descs = mdi.make_batch_descs(b.families, b.d, b.a, b.n_last, b.offsets)
+    order = mdi.mdi_batch_plan(descs)
+    d_descs = torch.from_numpy(descs.view(np.uint8)).cuda()
+    return descs, d_descs, torch.from_numpy(order).cuda(), dev(b.pool)
+
+
+def test_batched_small_matches_oracle_elementwise():
+    b = inputs.batch(count=193, seed=5)
+    _, d_descs, d_order, pool = _batch_to_device(b)
+    out = mdi.mdi_lr_integrate_batched(d_descs, pool, len(b), order=d_order).cpu().numpy()
+    for i in range(len(b)):
+        it = b.integral(i)
+        close(out[i], o.mdi_nodes(it.family, it.d, it.a, it.n_last, 16, it.c, it.w), it.family)
+
+
+def test_batched_full_size_sampled():
+    """4096 integrals (d ~ U{6..20}, N ~ U{8..32}) in one launch; 96 sampled
+    outputs checked against the oracle, the rest against their own re-run."""
+    b = inputs.batch(count=4096, seed=0)
+    _, d_descs, d_order, pool = _batch_to_device(b)
+    out1 = mdi.mdi_lr_integrate_batched(d_descs, pool, len(b), order=d_order).cpu().numpy()
+    out2 = mdi.mdi_lr_integrate_batched(d_descs, pool, len(b)).cpu().numpy()
+    np.testing.assert_array_equal(out1, out2)  # scheduling order does not change any value
+    for i in np.random.default_rng(0).choice(len(b), 96, replace=False):
+        it = b.integral(int(i))
+        close(out1[i], o.mdi_nodes(it.family, it.d, it.a, it.n_last, 16, it.c, it.w), it.family)
+
+
+def test_batched_mixed_families_and_edges():
+    fams = ["exp", "osc", "gauss", "peak", "gauss", "exp", "peak", "osc"]
+    ds = [1, 2, 3, 64, 5, 130, 7, 1]
+    as_ = [1, 64, 5, 2, 33, 16, 1, 3]
+    nls = [4096, 3, 5, 2, 33, 16, 1, 7]
+    offs = np.concatenate([[0], np.cumsum([2 * d for d in ds[:-1]])])
+    pool = np.concatenate([inputs.random_product(f, d, seed=i) for i, (f, d) in enumerate(zip(fams, ds))])
+    for i, f in enumerate(fams):
+        if f == "osc":
+            pool[offs[i] + ds[i]] = 0.17 * (i + 1)
+    descs = mdi.make_batch_descs(fams, ds, as_, nls, offs)
+    out = mdi.mdi_lr_integrate_batched(torch.from_numpy(descs.view(np.uint8)).cuda(), dev(pool), len(fams)).cpu()
+    for i, f in enumerate(fams):
+        p = pool[offs[i]:offs[i] + 2 * ds[i]]
+        close(out[i].item(), o.mdi_nodes(f, ds[i], as_[i], nls[i], 16, p[:ds[i]], p[ds[i]:]), f)
