@@ -67,6 +67,12 @@ __device__ __forceinline__ double cheb_weight(int p, int P) {
 // (DF = false) or as a float pair hi + lo (DF = true); 8 bytes per entry either way.
 template <bool DF>
 __global__ void nodes_table_kernel(int P, void *__restrict__ table) {
+  __shared__ double s_xi[kNodesPMax], s_bw[kNodesPMax];
+  for (int t = threadIdx.x; t < P; t += blockDim.x) {
+    s_xi[t] = cheb_node(t, P);
+    s_bw[t] = cheb_weight(t, P);
+  }
+  __syncthreads();
   const size_t total_pts = (size_t)P * kNodesAMax * (kNodesAMax + 1) / 2;  // sum_a a*P points
   for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total_pts;
        g += (size_t)gridDim.x * blockDim.x) {
@@ -78,19 +84,19 @@ __global__ void nodes_table_kernel(int P, void *__restrict__ table) {
     }
     const int i = (int)(g - base);  // i = q*P + p
     const int q = i / P, p = i % P;
-    const double u = ((double)q + cheb_node(p, P)) / (double)a;
+    const double u = ((double)q + s_xi[p]) / (double)a;
     double den = 0.0;
     int hit = -1;
     for (int t = 0; t < P; ++t) {
-      const double xt = cheb_node(t, P);
+      const double xt = s_xi[t];
       if (u == xt) hit = t;
-      else den += cheb_weight(t, P) / (u - xt);
+      else den += s_bw[t] / (u - xt);
     }
     const size_t off = table_offset(a, P);
     for (int t = 0; t < P; ++t) {
       double l;
       if (hit >= 0) l = (t == hit) ? 1.0 : 0.0;
-      else l = (cheb_weight(t, P) / (u - cheb_node(t, P))) / den;
+      else l = (s_bw[t] / (u - s_xi[t])) / den;
       const size_t idx = off + (size_t)t * a * P + i;
       if constexpr (DF) {
         const float h = (float)l;
@@ -386,9 +392,15 @@ static mdi_status launch_nodes(const mdi_batch_desc *descs, const int32_t *order
   }
   int per_sm = cfg.ctas_per_sm;
   if (per_sm == 0) {
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, nodes_batched_kernel<PREC>, cfg.block, smem);
-    per_sm = std::max(1, occ);
+    // Resident CTAs per SM for this (block, P), queried once per process.
+    static int occ_cache[kNodesMaxBlock / 32 + 1][kNodesPMax / 2 + 1];
+    int &occ = occ_cache[cfg.block / 32][cfg.P / 2];
+    if (occ == 0) {
+      int o = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, nodes_batched_kernel<PREC>, cfg.block, smem);
+      occ = std::max(1, o);
+    }
+    per_sm = occ;
   }
   const int grid = std::max(1, std::min(count, sm_count() * per_sm));
   nodes_batched_kernel<PREC><<<grid, cfg.block, smem, stream>>>(descs, order, count, single, pool, tables, cfg.P,
