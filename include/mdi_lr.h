@@ -111,6 +111,25 @@ mdi_status lattice_rule_integrate(int32_t family, int32_t d, int64_t n, const in
                                   void *workspace, size_t ws_bytes, mdi_stream_t stream);
 mdi_status lattice_rule_workspace_size(int32_t d, int64_t n, size_t *bytes);
 
+/* lattice_rule_integrate without a workspace, for callers that cannot allocate
+ * device memory when they call (for instance code inside an application that
+ * reserves all GPU memory at start-up and forbids later allocation, or a plug-in
+ * without access to its host's allocator).  The paper has no counterpart: this is
+ * a packaging variant of the lattice rule above, with the same arguments minus
+ * the workspace and the same result.
+ *   - Scratch: a fixed 4096-slot (32 KiB) array of partial sums built into this
+ *     library; every GPU that loads the library holds it until the process exits.
+ *     A launch that would need more slots (GPUs with more than 512 SMs) returns
+ *     MDI_EWORKSPACE.  Nothing is allocated or freed by the call.
+ *   - Set-up: the first call on each device looks up the array's device address
+ *     (with that device current); make that first call before any stream capture.
+ *   - All calls share the array.  Each call overwrites every slot it reads, so no
+ *     clearing is needed, but calls that overlap on the GPU (other streams, other
+ *     host threads) race on it and must be serialised by the caller. */
+mdi_status lattice_rule_integrate_noalloc(int32_t family, int32_t d, int64_t n, const int64_t *z,
+                                          const double *params, int32_t precision, double *out,
+                                          mdi_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * MDI-LR, Algorithm 2 (Section 4) with m = 1 on the Korobov lattice.
  *   d        dimension, >= 1 (EXACT: n <= 2^40; CLOSED: d <= 2^20; NODES: d <= 2^20)

@@ -22,7 +22,7 @@ from . import _ffi
 from ._ffi import BATCH_DESC_DTYPE, FAMILY, PRECISION, STATE, MdiError, MdiOpts
 
 __all__ = [
-    "lattice_rule_integrate", "lattice_rule_workspace_size", "mdi_lr_integrate", "mdi_lr_workspace_size",
+    "lattice_rule_integrate", "lattice_rule_workspace_size", "lattice_rule_integrate_noalloc", "mdi_lr_integrate", "mdi_lr_workspace_size",
     "mdi_lr_integrate_batched", "mdi_lr_batched_workspace_size", "mdi_lr_batched_prepare", "mdi_batch_plan", "mdi_debug_lattice_indices",
     "make_batch_descs", "MdiError", "FAMILY", "STATE", "PRECISION", "BATCH_DESC_DTYPE", "library_path",
 ]
@@ -97,6 +97,28 @@ def lattice_rule_integrate(family, params: torch.Tensor, n: int, z: Sequence[int
                                             ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
                                             ws.numel(), _stream(stream))
     _ffi.check(st, "lattice_rule_integrate")
+    return out
+
+
+def lattice_rule_integrate_noalloc(family, params: torch.Tensor, n: int, z: Sequence[int], precision="fp64",
+                                   out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """The lattice rule through the C entry point that takes no workspace: for
+    callers that cannot allocate device memory at call time.  Its scratch is a
+    fixed array inside the library shared by all calls, so calls that overlap on
+    the GPU race; the first call on a device should precede any stream capture.
+    ``out`` must be supplied by such callers (it is only allocated here when
+    omitted, for convenience)."""
+    _dev_f64(params, "params")
+    zz = np.ascontiguousarray(np.asarray(z, dtype=np.int64))
+    d = int(zz.size)
+    if params.numel() < 2 * d:
+        raise ValueError("params must hold 2*d doubles")
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=params.device)
+    st = _ffi.load().lattice_rule_integrate_noalloc(_fam(family), d, int(n), zz.ctypes.data_as(ctypes.c_void_p),
+                                                    ctypes.c_void_p(params.data_ptr()), _prec(precision),
+                                                    ctypes.c_void_p(out.data_ptr()), _stream(stream))
+    _ffi.check(st, "lattice_rule_integrate_noalloc")
     return out
 
 

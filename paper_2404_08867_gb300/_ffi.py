@@ -35,6 +35,7 @@ assert BATCH_DESC_DTYPE.itemsize == 32
 SIGNATURES = {
     "lattice_rule_integrate": (_I32, [_I32, _I32, _I64, _P, _P, _I32, _P, _P, _SZ, _P]),
     "lattice_rule_workspace_size": (_I32, [_I32, _I64, _c.POINTER(_SZ)]),
+    "lattice_rule_integrate_noalloc": (_I32, [_I32, _I32, _I64, _P, _P, _I32, _P, _P]),
     "mdi_lr_integrate": (_I32, [_I32, _I32, _I64, _I64, _P, _c.POINTER(MdiOpts), _P, _P, _SZ, _P]),
     "mdi_lr_workspace_size": (_I32, [_I32, _I32, _I64, _I64, _c.POINTER(MdiOpts), _c.POINTER(_SZ)]),
     "mdi_lr_integrate_batched": (_I32, [_P, _P, _I32, _P, _c.POINTER(MdiOpts), _P, _P, _SZ, _P]),

@@ -92,6 +92,12 @@ mdi_status lattice_rule_integrate(int32_t family, int32_t d, int64_t n, const in
   return slr_launch(family, d, n, z, params, precision, out, workspace, ws_bytes, (cudaStream_t)stream);
 }
 
+mdi_status lattice_rule_integrate_noalloc(int32_t family, int32_t d, int64_t n, const int64_t *z, const double *params,
+                                          int32_t precision, double *out, mdi_stream_t stream) {
+  if (!family_ok(family)) return MDI_EINVAL;
+  return slr_launch_noalloc(family, d, n, z, params, precision, out, (cudaStream_t)stream);
+}
+
 mdi_status mdi_lr_workspace_size(int32_t family, int32_t d, int64_t a, int64_t n_last, const mdi_opts *opts,
                                  size_t *bytes) {
   if (!bytes || !family_ok(family) || d < 1 || a < 1 || n_last < 1 || !opts_ok(opts)) return MDI_EINVAL;

@@ -13,6 +13,8 @@ namespace mdi {
 size_t slr_workspace_bytes(int d, int64_t n);
 mdi_status slr_launch(int family, int d, int64_t n, const int64_t *z, const double *params, int precision,
                       double *out, void *workspace, size_t ws_bytes, cudaStream_t stream);
+mdi_status slr_launch_noalloc(int family, int d, int64_t n, const int64_t *z, const double *params, int precision,
+                              double *out, cudaStream_t stream);
 mdi_status lattice_indices_launch(int d, int64_t n, const int64_t *z, int64_t j0, int64_t count, int64_t *r_out,
                                   cudaStream_t stream);
 

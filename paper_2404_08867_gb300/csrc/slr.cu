@@ -10,6 +10,7 @@
 // one partial per CTA, and a second one-CTA kernel adds the partials in index
 // order, so the result is bitwise reproducible.
 #include <algorithm>
+#include <mutex>
 
 #include "mdi_common.cuh"
 #include "mdi_internal.h"
@@ -230,6 +231,83 @@ mdi_status lattice_indices_launch(int d, int64_t n, const int64_t *z, int64_t j0
   uint64_t runs = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)count / 4, 65536));
   int blocks = (int)((runs + 255) / 256);
   lattice_indices_kernel<<<blocks, 256, 0, stream>>>(args, (uint64_t)j0, (uint64_t)count, runs, r_out);
+  return check_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the lattice rule (lattice_rule_integrate_noalloc).
+//
+// Some callers cannot allocate device memory at call time -- for example code
+// that runs inside a host application which reserves all GPU memory up front and
+// forbids later cudaMalloc, or a plug-in that has no access to the application's
+// allocator -- yet still want the plain lattice rule.  For them the per-CTA
+// partial sums live in a fixed array compiled into this library, reserved on
+// every GPU that loads it until the process exits.  The kernels are the same as
+// lattice_rule_integrate's, so the results are the same.
+// ---------------------------------------------------------------------------
+constexpr int kSlrNoAllocSlots = 4096;  // partial sums: 32 KiB, enough for 512 SMs x 8 CTAs
+static __device__ __align__(256) double g_slr_noalloc_partials[kSlrNoAllocSlots];
+
+// Device address of g_slr_noalloc_partials on the current device.  Host code
+// must not pass the symbol itself to a kernel (it names a host-side stand-in);
+// the address is looked up once per device, with that device current.
+static mdi_status noalloc_scratch(double **ptr) {
+  static std::mutex mu;
+  static double *cache[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return MDI_ECUDA;
+  }
+  if (dev < 0 || dev >= 64) return MDI_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!cache[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_slr_noalloc_partials);
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      return MDI_ECUDA;
+    }
+    cache[dev] = (double *)p;
+  }
+  *ptr = cache[dev];
+  return MDI_OK;
+}
+
+mdi_status slr_launch_noalloc(int family, int d, int64_t n, const int64_t *z, const double *params, int precision,
+                              double *out, cudaStream_t stream) {
+  if (d < 1 || d > kSlrMaxD || n < 1 || !z || !params || !out) return MDI_EINVAL;
+  if (family < MDI_FAM_EXP || family > MDI_FAM_PEAK) return MDI_EINVAL;
+  if (precision != MDI_PREC_FP64 && precision != MDI_PREC_FP32_EVAL_FP64) return MDI_EUNSUPPORTED;
+  for (int i = 0; i < d; ++i)
+    if (z[i] < 0 || z[i] >= n) return MDI_EINVAL;
+  const int grid = slr_grid((uint64_t)n);
+  if (grid > kSlrNoAllocSlots) return MDI_EWORKSPACE;  // more CTAs than the built-in scratch holds
+  double *partials = nullptr;
+  mdi_status st = noalloc_scratch(&partials);
+  if (st != MDI_OK) return st;
+  SlrArgs args{};
+  args.n = (uint64_t)n;
+  args.inv_n = 1.0 / (double)n;
+  args.d = d;
+  for (int i = 0; i < d; ++i) args.z[i] = (uint64_t)z[i];
+  // Every slot the sum reads (0..grid-1) is written by this call's CTAs first, so
+  // the array needs no clearing between calls.
+  const bool f32 = precision == MDI_PREC_FP32_EVAL_FP64;
+  switch (family) {
+    case MDI_FAM_EXP: f32 ? launch_slr_d<MDI_FAM_EXP, true>(grid, args, params, partials, stream)
+                          : launch_slr_d<MDI_FAM_EXP, false>(grid, args, params, partials, stream); break;
+    case MDI_FAM_OSC: f32 ? launch_slr_d<MDI_FAM_OSC, true>(grid, args, params, partials, stream)
+                          : launch_slr_d<MDI_FAM_OSC, false>(grid, args, params, partials, stream); break;
+    case MDI_FAM_GAUSS: f32 ? launch_slr_d<MDI_FAM_GAUSS, true>(grid, args, params, partials, stream)
+                            : launch_slr_d<MDI_FAM_GAUSS, false>(grid, args, params, partials, stream); break;
+    default: f32 ? launch_slr_d<MDI_FAM_PEAK, true>(grid, args, params, partials, stream)
+                 : launch_slr_d<MDI_FAM_PEAK, false>(grid, args, params, partials, stream); break;
+  }
+  st = check_launch();
+  if (st != MDI_OK) return st;
+  sum_partials_kernel<<<1, kSlrThreads, 0, stream>>>(partials, grid, 1.0 / (double)n, out);
   return check_launch();
 }
 
