@@ -148,6 +148,30 @@ mdi_status mdi_lr_workspace_size(int32_t family, int32_t d, int64_t a, int64_t n
                                  const mdi_opts *opts, size_t *bytes);
 
 /* ---------------------------------------------------------------------------
+ * Derivative of the MDI-LR value with respect to the integrand parameters
+ * (the adjoint sweep; the paper computes values only, this is an extension).
+ *   grad     DEVICE, 2*d doubles: grad[j] = dQ/dc_j, grad[d+j] = dQ/dw_j; for
+ *            MDI_FAM_EXP the w entries are 0, for MDI_FAM_OSC grad[d] = dQ/du and
+ *            the rest of the second half is 0.  Q is the rule's own value, so this
+ *            is the exact derivative of the computed number, not of the integral.
+ *   value    DEVICE, 1 double, or NULL: receives Q as well.
+ *   opts     state CLOSED (EXP, OSC) or NODES (any family; AUTO picks as in
+ *            mdi_lr_integrate); precision must be MDI_PREC_FP64.
+ * CLOSED: the levels run in reverse as an affine recurrence, dQ/dc_k =
+ * front * mu_k, mu_k = nu_k + mu_{k+1}/a, solved by a block-wide scan.
+ * NODES (d <= 65536, a <= 64, n_last <= 4096): every level's P x P operator is
+ * built in parallel, one CTA runs the forward and the reverse (adjoint) chains
+ * keeping level states only every opts->checkpoint levels (0: ceil(sqrt(d))),
+ * and each level's contribution is then formed in parallel after recomputing its
+ * states from the nearest checkpoints.
+ * ------------------------------------------------------------------------- */
+mdi_status mdi_lr_grad(int32_t family, int32_t d, int64_t a, int64_t n_last, const double *params,
+                       const mdi_opts *opts, double *value, double *grad, void *workspace, size_t ws_bytes,
+                       mdi_stream_t stream);
+mdi_status mdi_lr_grad_workspace_size(int32_t family, int32_t d, int64_t a, int64_t n_last,
+                                      const mdi_opts *opts, size_t *bytes);
+
+/* ---------------------------------------------------------------------------
  * Many independent MDI-LR integrals in one launch sequence (node state for every
  * family, or closed state for EXP/OSC instances when opts->state is
  * MDI_STATE_AUTO).  One descriptor per integral:

@@ -24,7 +24,7 @@ from ._ffi import BATCH_DESC_DTYPE, FAMILY, PRECISION, STATE, MdiError, MdiOpts
 __all__ = [
     "lattice_rule_integrate", "lattice_rule_workspace_size", "lattice_rule_integrate_noalloc", "mdi_lr_integrate", "mdi_lr_workspace_size",
     "mdi_lr_integrate_batched", "mdi_lr_batched_workspace_size", "mdi_lr_batched_prepare", "mdi_batch_plan", "mdi_debug_lattice_indices",
-    "make_batch_descs", "MdiError", "FAMILY", "STATE", "PRECISION", "BATCH_DESC_DTYPE", "library_path",
+    "mdi_lr_grad", "mdi_lr_grad_workspace_size", "MDILR", "mdi_lr", "make_batch_descs", "MdiError", "FAMILY", "STATE", "PRECISION", "BATCH_DESC_DTYPE", "library_path",
 ]
 
 
@@ -152,6 +152,61 @@ def mdi_lr_integrate(family, params: torch.Tensor, d: int, a: int, n_last: Optio
                                       ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
     _ffi.check(st, "mdi_lr_integrate")
     return out
+
+
+def mdi_lr_grad_workspace_size(family, d: int, a: int, n_last: int, **opts) -> int:
+    b = ctypes.c_size_t()
+    o = _opts(**opts)
+    _ffi.check(_ffi.load().mdi_lr_grad_workspace_size(_fam(family), d, a, n_last, ctypes.byref(o), ctypes.byref(b)),
+               "mdi_lr_grad_workspace_size")
+    return b.value
+
+
+def mdi_lr_grad(family, params: torch.Tensor, d: int, a: int, n_last: Optional[int] = None,
+                value: Optional[torch.Tensor] = None, grad: Optional[torch.Tensor] = None,
+                workspace: Optional[torch.Tensor] = None, stream=None, **opts):
+    """(value, grad): the MDI-LR value and its derivative with respect to the 2*d
+    parameters, from the adjoint sweep on the GPU (FP64).  opts: state
+    ("auto", "closed", "nodes"), nodes, checkpoint."""
+    _dev_f64(params, "params")
+    n_last = a if n_last is None else n_last
+    if value is None:
+        value = torch.empty(1, dtype=torch.float64, device=params.device)
+    if grad is None:
+        grad = torch.empty(2 * d, dtype=torch.float64, device=params.device)
+    o = _opts(**opts)
+    ws = _workspace(mdi_lr_grad_workspace_size(family, d, a, n_last, **opts), params.device, workspace)
+    st = _ffi.load().mdi_lr_grad(_fam(family), d, a, n_last, ctypes.c_void_p(params.data_ptr()), ctypes.byref(o),
+                                 ctypes.c_void_p(value.data_ptr()), ctypes.c_void_p(grad.data_ptr()),
+                                 ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
+    _ffi.check(st, "mdi_lr_grad")
+    return value, grad
+
+
+class MDILR(torch.autograd.Function):
+    """Differentiable MDI-LR value: the forward pass runs the sweep, the backward
+    pass runs the adjoint sweep (levels in reverse, states recomputed from
+    checkpoints) and scales the parameter gradient by the incoming gradient."""
+
+    @staticmethod
+    def forward(ctx, params, family, d, a, n_last, opts):
+        ctx.save_for_backward(params)
+        ctx.meta = (family, d, a, n_last, dict(opts))
+        return mdi_lr_integrate(family, params.detach().contiguous(), d, a, n_last, **opts).reshape(())
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (params,) = ctx.saved_tensors
+        family, d, a, n_last, opts = ctx.meta
+        opts = {k: v for k, v in opts.items() if k != "precision"}
+        _, g = mdi_lr_grad(family, params.detach().contiguous(), d, a, n_last, **opts)
+        return g * grad_out, None, None, None, None, None
+
+
+def mdi_lr(family, params: torch.Tensor, d: int, a: int, n_last: Optional[int] = None, **opts) -> torch.Tensor:
+    """MDI-LR value as a 0-dim tensor that autograd can differentiate with respect
+    to ``params`` (2*d float64 on the GPU)."""
+    return MDILR.apply(params, family, d, a, a if n_last is None else n_last, opts)
 
 
 # ---------------------------------------------------------------------------

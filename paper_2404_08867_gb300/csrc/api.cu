@@ -52,6 +52,12 @@ static double nodes_cost(const mdi_batch_desc &d, int P) {
   return (double)(d.d - 1) * d.a * P * (P + phi_cost) + (double)d.n_last * (2.0 * P + phi_cost);
 }
 
+// One node-state integral runs parallel over levels (mdi_levels.cu) when it has
+// enough levels to fill several SMs; short ones take one CTA of the batched kernel.
+static bool use_levels(int d, const NodesConfig &cfg) {
+  return d >= 8 && cfg.precision != MDI_PREC_FP32_EVAL_DF32;
+}
+
 static bool desc_ok(const mdi_batch_desc &d) {
   return family_ok(d.family) && d.d >= 1 && d.d <= MDI_BATCH_MAX_D && d.a >= 1 && d.a <= 64 && d.n_last >= 1 &&
          d.n_last <= 4096 && d.param_offset >= 0 && d.reserved == 0;
@@ -112,9 +118,12 @@ mdi_status mdi_lr_workspace_size(int32_t family, int32_t d, int64_t a, int64_t n
       if (family != MDI_FAM_EXP && family != MDI_FAM_OSC) return MDI_EUNSUPPORTED;
       *bytes = closed_workspace_bytes(d);
       return MDI_OK;
-    default:
-      *bytes = nodes_single_workspace_bytes(nodes_config(opts));
+    default: {
+      const NodesConfig cfg = nodes_config(opts);
+      *bytes = use_levels(d, cfg) ? levels_workspace_bytes(d, a, cfg, opts ? opts->checkpoint : 0)
+                                  : nodes_single_workspace_bytes(cfg);
       return MDI_OK;
+    }
   }
 }
 
@@ -127,7 +136,44 @@ mdi_status mdi_lr_integrate(int32_t family, int32_t d, int64_t a, int64_t n_last
   switch (resolve_state(family, opts)) {
     case MDI_STATE_EXACT: return exact_launch(family, d, a, n_last, params, precision, out, workspace, ws_bytes, s);
     case MDI_STATE_CLOSED: return closed_launch(family, d, a, n_last, params, precision, out, workspace, ws_bytes, s);
-    default: return nodes_single_launch(family, d, a, n_last, params, nodes_config(opts), out, workspace, ws_bytes, s);
+    default: {
+      const NodesConfig cfg = nodes_config(opts);
+      if (use_levels(d, cfg))
+        return levels_launch(family, d, a, n_last, params, cfg, opts ? opts->checkpoint : 0, out, nullptr, workspace,
+                             ws_bytes, s);
+      return nodes_single_launch(family, d, a, n_last, params, cfg, out, workspace, ws_bytes, s);
+    }
+  }
+}
+
+mdi_status mdi_lr_grad_workspace_size(int32_t family, int32_t d, int64_t a, int64_t n_last, const mdi_opts *opts,
+                                      size_t *bytes) {
+  if (!bytes || !family_ok(family) || d < 1 || a < 1 || n_last < 1 || !opts_ok(opts)) return MDI_EINVAL;
+  switch (resolve_state(family, opts)) {
+    case MDI_STATE_EXACT: return MDI_EUNSUPPORTED;
+    case MDI_STATE_CLOSED:
+      if (family != MDI_FAM_EXP && family != MDI_FAM_OSC) return MDI_EUNSUPPORTED;
+      *bytes = closed_grad_workspace_bytes(d);
+      return MDI_OK;
+    default:
+      *bytes = levels_workspace_bytes(d, a, nodes_config(opts), opts ? opts->checkpoint : 0);
+      return MDI_OK;
+  }
+}
+
+mdi_status mdi_lr_grad(int32_t family, int32_t d, int64_t a, int64_t n_last, const double *params,
+                       const mdi_opts *opts, double *value, double *grad, void *workspace, size_t ws_bytes,
+                       mdi_stream_t stream) {
+  if (!family_ok(family) || d < 1 || a < 1 || n_last < 1 || !params || !grad || !opts_ok(opts)) return MDI_EINVAL;
+  const int precision = opts ? opts->precision : MDI_PREC_FP64;
+  if (precision != MDI_PREC_FP64) return MDI_EUNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (resolve_state(family, opts)) {
+    case MDI_STATE_EXACT: return MDI_EUNSUPPORTED;
+    case MDI_STATE_CLOSED: return closed_grad_launch(family, d, a, n_last, params, value, grad, workspace, ws_bytes, s);
+    default:
+      return levels_launch(family, d, a, n_last, params, nodes_config(opts), opts ? opts->checkpoint : 0, value, grad,
+                           workspace, ws_bytes, s);
   }
 }
 

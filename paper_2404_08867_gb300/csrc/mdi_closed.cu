@@ -197,4 +197,176 @@ mdi_status closed_launch(int family, int d, int64_t a, int64_t n_last, const dou
   return run_closed_p<MDI_FAM_OSC>(precision, d, a, n_last, params, out, workspace, stream);
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint of the closed-state sweep.
+//
+// Q = front * prod_k S_k(gamma_k) with S_k(g) = (1/r_k) sum_q e^{iota g q / r_k}
+// (iota = 1 for EXP, i for OSC) and gamma_j depending on c_k (k <= j) through
+// dgamma_j/dc_k = a^{-(j-k)}.  With T_k = (1/r_k) sum_q (q/r_k) e^{iota gamma_k q/r_k}
+// (so dS_k/dgamma_k = iota T_k) and nu_j = iota T_j prod_{i != j} S_i,
+//     dQ/dc_k = front * mu_k,   mu_k = nu_k + mu_{k+1} / a,   mu_d = nu_d,
+// i.e. the levels run in reverse.  The products prod_{i != j} S_i are formed from
+// exclusive prefix and suffix products (no division by S_j), and the reverse
+// recurrence, like the forward one, is a block-wide scan of affine maps.
+// ---------------------------------------------------------------------------
+template <int FAM>
+__global__ void __launch_bounds__(kLevelThreads) closed_grad_level_kernel(int d, int64_t a, int64_t n_last,
+                                                                          const double *__restrict__ gamma,
+                                                                          double2 *__restrict__ S,
+                                                                          double2 *__restrict__ T) {
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
+  const int nwarps = gridDim.x * blockDim.x / kWarp;
+  for (int k = warp_global; k < d; k += nwarps) {
+    const int64_t r = (k + 1 < d) ? a : n_last;
+    const double g = gamma[k], invr = 1.0 / (double)r;
+    double2 s = make_double2(0.0, 0.0), t = make_double2(0.0, 0.0);
+    for (int64_t q = lane; q < r; q += kWarp) {
+      const double x = (double)q * invr;
+      double2 e;
+      if constexpr (FAM == MDI_FAM_OSC) {
+        double sn, cs;
+        sincos(g * x, &sn, &cs);
+        e = make_double2(cs, sn);
+      } else {
+        e = make_double2(exp(g * x), 0.0);
+      }
+      s = c_add(s, e);
+      t = c_add(t, c_scale(e, x));
+    }
+    s = warp_sum(s);
+    t = warp_sum(t);
+    if (lane == 0) {
+      S[k] = c_scale(s, invr);
+      T[k] = c_scale(t, invr);
+    }
+  }
+}
+
+template <int FAM>
+__global__ void __launch_bounds__(kScanThreads) closed_grad_final_kernel(int d, double a,
+                                                                         const double *__restrict__ params,
+                                                                         const double2 *__restrict__ S,
+                                                                         const double2 *__restrict__ T,
+                                                                         double2 *__restrict__ nu,
+                                                                         double *__restrict__ value,
+                                                                         double *__restrict__ grad) {
+  __shared__ double2 sP[kScanThreads], sR[kScanThreads];
+  __shared__ double sA[kScanThreads];
+  __shared__ double2 sB[kScanThreads];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int per = (d + nt - 1) / nt;
+  const int lo = min(d, tid * per), hi = min(d, lo + per);
+  const double2 iota = (FAM == MDI_FAM_OSC) ? make_double2(0.0, 1.0) : make_double2(1.0, 0.0);
+  double2 front = make_double2(1.0, 0.0);
+  if (FAM == MDI_FAM_OSC) {
+    double sn, cs;
+    sincos(kTwoPi * params[d], &sn, &cs);
+    front = make_double2(cs, sn);
+  }
+  // Chunk products, then exclusive prefix (left) and suffix (right) products.
+  double2 cp = make_double2(1.0, 0.0);
+  for (int j = lo; j < hi; ++j) cp = c_mul(cp, S[j]);
+  sP[tid] = cp;
+  sR[tid] = cp;
+  __syncthreads();
+  for (int off = 1; off < nt; off <<= 1) {
+    double2 pl = make_double2(1.0, 0.0), pr = make_double2(1.0, 0.0);
+    if (tid >= off) pl = sP[tid - off];
+    if (tid + off < nt) pr = sR[tid + off];
+    __syncthreads();
+    if (tid >= off) sP[tid] = c_mul(pl, sP[tid]);
+    if (tid + off < nt) sR[tid] = c_mul(sR[tid], pr);
+    __syncthreads();
+  }
+  const double2 left = tid > 0 ? sP[tid - 1] : make_double2(1.0, 0.0);
+  const double2 right = tid + 1 < nt ? sR[tid + 1] : make_double2(1.0, 0.0);
+  const double2 total = sP[nt - 1];
+  // nu_j = iota T_j prod_{i<j} S_i prod_{i>j} S_i
+  double2 R = right;
+  for (int j = hi - 1; j >= lo; --j) {
+    nu[j] = R;
+    R = c_mul(S[j], R);
+  }
+  double2 Lp = left;
+  for (int j = lo; j < hi; ++j) {
+    nu[j] = c_mul(c_mul(iota, T[j]), c_mul(Lp, nu[j]));
+    Lp = c_mul(Lp, S[j]);
+  }
+  // Reverse recurrence mu_j = nu_j + mu_{j+1}/a: composite map of the chunk, then an
+  // inclusive scan from the right (later chunks applied first).
+  const double inva = 1.0 / a;
+  double A = 1.0;
+  double2 Bc = make_double2(0.0, 0.0);
+  for (int j = hi - 1; j >= lo; --j) {
+    A *= inva;
+    Bc = c_add(nu[j], c_scale(Bc, inva));
+  }
+  sA[tid] = A;
+  sB[tid] = Bc;
+  __syncthreads();
+  for (int off = 1; off < nt; off <<= 1) {
+    double pA = 1.0;
+    double2 pB = make_double2(0.0, 0.0);
+    const bool has = tid + off < nt;
+    if (has) {
+      pA = sA[tid + off];
+      pB = sB[tid + off];
+    }
+    __syncthreads();
+    if (has) {  // this chunk's map applied after the maps to its right
+      const double cA = sA[tid];
+      const double2 cB = sB[tid];
+      sA[tid] = cA * pA;
+      sB[tid] = c_add(c_scale(pB, cA), cB);
+    }
+    __syncthreads();
+  }
+  double2 mu = tid + 1 < nt ? sB[tid + 1] : make_double2(0.0, 0.0);  // mu at hi (0 past the last level)
+  for (int j = hi - 1; j >= lo; --j) {
+    mu = c_add(nu[j], c_scale(mu, inva));
+    grad[j] = c_mul(front, mu).x;
+    grad[d + j] = 0.0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const double2 fq = c_mul(front, total);
+    if (value) *value = fq.x;
+    if (FAM == MDI_FAM_OSC) grad[d] = -kTwoPi * fq.y;
+  }
+}
+
+size_t closed_grad_workspace_bytes(int d) {
+  return align_up(sizeof(double) * (size_t)d) + 3 * align_up(sizeof(double2) * (size_t)d);
+}
+
+template <int FAM>
+static mdi_status run_closed_grad(int d, int64_t a, int64_t n_last, const double *params, double *value,
+                                  double *grad, void *ws, cudaStream_t stream) {
+  char *base = (char *)ws;
+  double *gamma = (double *)base;
+  double2 *S = (double2 *)(base + align_up(sizeof(double) * (size_t)d));
+  double2 *T = S + 0;
+  T = (double2 *)((char *)S + align_up(sizeof(double2) * (size_t)d));
+  double2 *nu = (double2 *)((char *)T + align_up(sizeof(double2) * (size_t)d));
+  closed_scan_kernel<<<1, kScanThreads, 0, stream>>>(d, (double)a, (double)n_last, params, gamma);
+  mdi_status st = check_launch();
+  if (st != MDI_OK) return st;
+  const int grid = std::max(1, std::min((d + kLevelWarps - 1) / kLevelWarps, sm_count() * 8));
+  closed_grad_level_kernel<FAM><<<grid, kLevelThreads, 0, stream>>>(d, a, n_last, gamma, S, T);
+  if ((st = check_launch()) != MDI_OK) return st;
+  closed_grad_final_kernel<FAM><<<1, kScanThreads, 0, stream>>>(d, (double)a, params, S, T, nu, value, grad);
+  return check_launch();
+}
+
+mdi_status closed_grad_launch(int family, int d, int64_t a, int64_t n_last, const double *params, double *value,
+                              double *grad, void *workspace, size_t ws_bytes, cudaStream_t stream) {
+  if (family != MDI_FAM_EXP && family != MDI_FAM_OSC) return MDI_EUNSUPPORTED;
+  if (d < 1 || d > (1 << 20) || a < 1 || n_last < 1) return MDI_EINVAL;
+  if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < closed_grad_workspace_bytes(d))
+    return MDI_EWORKSPACE;
+  if (family == MDI_FAM_EXP) return run_closed_grad<MDI_FAM_EXP>(d, a, n_last, params, value, grad, workspace, stream);
+  return run_closed_grad<MDI_FAM_OSC>(d, a, n_last, params, value, grad, workspace, stream);
+}
+
 }  // namespace mdi

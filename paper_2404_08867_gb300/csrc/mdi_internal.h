@@ -28,6 +28,10 @@ size_t closed_workspace_bytes(int d);
 mdi_status closed_launch(int family, int d, int64_t a, int64_t n_last, const double *params, int precision,
                          double *out, void *workspace, size_t ws_bytes, cudaStream_t stream);
 
+size_t closed_grad_workspace_bytes(int d);
+mdi_status closed_grad_launch(int family, int d, int64_t a, int64_t n_last, const double *params, double *value,
+                              double *grad, void *workspace, size_t ws_bytes, cudaStream_t stream);
+
 // mdi_nodes.cu
 struct NodesConfig {
   int P;            // nodes per state
@@ -46,5 +50,11 @@ size_t nodes_single_workspace_bytes(const NodesConfig &cfg);
 mdi_status nodes_single_launch(int family, int d, int64_t a, int64_t n_last, const double *params,
                                const NodesConfig &cfg, double *out, void *workspace, size_t ws_bytes,
                                cudaStream_t stream);
+
+// mdi_levels.cu: one integral, node state, parallel over levels (forward and adjoint)
+size_t levels_workspace_bytes(int d, int64_t a, const NodesConfig &cfg, int checkpoint);
+mdi_status levels_launch(int family, int d, int64_t a, int64_t n_last, const double *params, const NodesConfig &cfg,
+                         int checkpoint, double *value, double *grad, void *workspace, size_t ws_bytes,
+                         cudaStream_t stream);
 
 }  // namespace mdi

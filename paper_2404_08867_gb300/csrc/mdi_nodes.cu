@@ -27,11 +27,10 @@
 
 #include "mdi_common.cuh"
 #include "mdi_internal.h"
+#include "mdi_nodes.cuh"
 
 namespace mdi {
 
-constexpr int kNodesAMax = 64;              // largest a with a basis table
-constexpr int kNodesPMax = 32;
 constexpr int kNodesMaxBlock = 512;
 constexpr int kNodesSmemTable = 64 * 1024;  // table bytes staged in shared memory
 
@@ -58,10 +57,6 @@ __host__ __device__ __forceinline__ size_t table_offset(int a, int P) {
 }
 static size_t table_bytes(int P) { return 8 * table_offset(kNodesAMax + 1, P); }
 
-__device__ __forceinline__ double cheb_node(int p, int P) { return 0.5 * (1.0 + cospi((2.0 * p + 1.0) / (2.0 * P))); }
-__device__ __forceinline__ double cheb_weight(int p, int P) {
-  return ((p & 1) ? -1.0 : 1.0) * sinpi((2.0 * p + 1.0) / (2.0 * P));
-}
 
 // Basis tables L_a[t][q*P + p] = l_t((q + xi_p)/a) for a = 1..64, stored as double
 // (DF = false) or as a float pair hi + lo (DF = true); 8 bytes per entry either way.
@@ -108,11 +103,6 @@ __global__ void nodes_table_kernel(int P, void *__restrict__ table) {
   }
 }
 
-__device__ __forceinline__ double2 as2(double v) { return make_double2(v, 0.0); }
-__device__ __forceinline__ double2 as2(double2 v) { return v; }
-template <typename V> __device__ __forceinline__ V from2(double2 v);
-template <> __device__ __forceinline__ double from2<double>(double2 v) { return v.x; }
-template <> __device__ __forceinline__ double2 from2<double2>(double2 v) { return v; }
 
 __device__ __forceinline__ void set_state(NodesShared &sh, int t, double2 g) {
   sh.G[t] = g;

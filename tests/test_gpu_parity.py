@@ -157,9 +157,23 @@ def test_nodes_state_matches_oracle(fam, d, a, nd, P):
 
 @pytest.mark.parametrize("block", [32, 64, 128, 512])
 def test_nodes_block_shapes(block):
-    w = inputs.gaussian(40, 16, seed=2)
-    got = mdi.mdi_lr_integrate("gauss", dev(w.params), 40, 16, 16, state="nodes", block=block).item()
-    close(got, o.mdi_nodes("gauss", 40, 16, 16, 16, w.c, w.w), "gauss")
+    """Short integrals (d < 8) run on one CTA of the batched kernel: every block shape."""
+    w = inputs.gaussian(7, 16, seed=2)
+    got = mdi.mdi_lr_integrate("gauss", dev(w.params), 7, 16, 16, state="nodes", block=block).item()
+    close(got, o.mdi_nodes("gauss", 7, 16, 16, 16, w.c, w.w), "gauss")
+
+
+@pytest.mark.parametrize("fam", ["gauss", "peak", "osc", "exp"])
+def test_level_parallel_equals_batched_kernel(fam):
+    """A long integral runs parallel over levels; the persistent batched kernel (one
+    CTA walking the levels) must give the same value."""
+    d, a = 40, 16
+    params = inputs.random_product(fam, d, seed=21)
+    single = mdi.mdi_lr_integrate(fam, dev(params), d, a, a, state="nodes").item()
+    descs = mdi.make_batch_descs([fam], [d], [a], [a], [0])
+    batched = mdi.mdi_lr_integrate_batched(torch.from_numpy(descs.view(np.uint8)).cuda(), dev(params), 1).item()
+    close(single, batched, fam)
+    close(single, o.mdi_nodes(fam, d, a, a, 16, params[:d], params[d:]), fam)
 
 
 def test_nodes_differentiation_workload_forward():
