@@ -76,11 +76,20 @@ typedef enum { MDI_STATE_AUTO = 0, MDI_STATE_EXACT = 1, MDI_STATE_CLOSED = 2, MD
  *   MDI_PREC_FP32_EVAL_DF32   phi_j in float; level contractions (interpolation and
  *                             the sum over the cluster) in double-float pairs of
  *                             floats; level states, cross-level products, the final
- *                             sum and coordinates in double. */
+ *                             sum and coordinates in double.
+ *   MDI_PREC_DF64            FP64-class results without the FP64 pipe, for the
+ *                             node state (batched kernel and short single
+ *                             integrals): coordinates, phi (own double-float exp
+ *                             and reciprocal), interpolation and cluster sums in
+ *                             double-float pairs of floats (about 48 significant
+ *                             bits); FP64 only between levels and on the last
+ *                             axis.  OSC keeps phi in FP64.  GB300 runs FP32 64x
+ *                             faster than FP64.  Other states: MDI_EUNSUPPORTED. */
 typedef enum {
   MDI_PREC_FP64 = 0,
   MDI_PREC_FP32_EVAL_FP64 = 1,
-  MDI_PREC_FP32_EVAL_DF32 = 2
+  MDI_PREC_FP32_EVAL_DF32 = 2,
+  MDI_PREC_DF64 = 3
 } mdi_precision;
 
 typedef struct {

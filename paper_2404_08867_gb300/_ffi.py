@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(_PKG, "libmdilr.so")
 MDI_OK, MDI_EINVAL, MDI_EUNSUPPORTED, MDI_EOVERFLOW, MDI_ECUDA, MDI_EWORKSPACE = range(6)
 FAMILY = {"exp": 0, "osc": 1, "gauss": 2, "peak": 3}
 STATE = {"auto": 0, "exact": 1, "closed": 2, "nodes": 3}
-PRECISION = {"fp64": 0, "fp32_eval_fp64": 1, "fp32_eval_df32": 2}
+PRECISION = {"fp64": 0, "fp32_eval_fp64": 1, "fp32_eval_df32": 2, "df64": 3}
 
 # Every symbol include/mdi_lr.h declares, with its ctypes signature.
 _c = ctypes

@@ -35,7 +35,7 @@ static bool family_ok(int f) { return f >= MDI_FAM_EXP && f <= MDI_FAM_PEAK; }
 static bool opts_ok(const mdi_opts *o) {
   if (!o) return true;
   if (o->state < MDI_STATE_AUTO || o->state > MDI_STATE_NODES) return false;
-  if (o->precision < MDI_PREC_FP64 || o->precision > MDI_PREC_FP32_EVAL_DF32) return false;
+  if (o->precision < MDI_PREC_FP64 || o->precision > MDI_PREC_DF64) return false;
   if (o->nodes < 0 || o->block < 0 || o->ctas_per_sm < 0 || o->checkpoint < 0) return false;
   return o->reserved[0] == 0 && o->reserved[1] == 0;
 }
@@ -55,7 +55,7 @@ static double nodes_cost(const mdi_batch_desc &d, int P) {
 // One node-state integral runs parallel over levels (mdi_levels.cu) when it has
 // enough levels to fill several SMs; short ones take one CTA of the batched kernel.
 static bool use_levels(int d, const NodesConfig &cfg) {
-  return d >= 8 && cfg.precision != MDI_PREC_FP32_EVAL_DF32;
+  return d >= 8 && (cfg.precision == MDI_PREC_FP64 || cfg.precision == MDI_PREC_FP32_EVAL_FP64);
 }
 
 static bool desc_ok(const mdi_batch_desc &d) {

@@ -192,6 +192,7 @@ mdi_status closed_launch(int family, int d, int64_t a, int64_t n_last, const dou
                          double *out, void *workspace, size_t ws_bytes, cudaStream_t stream) {
   if (family != MDI_FAM_EXP && family != MDI_FAM_OSC) return MDI_EUNSUPPORTED;
   if (d < 1 || d > (1 << 20) || a < 1 || n_last < 1) return MDI_EINVAL;
+  if (precision == MDI_PREC_DF64) return MDI_EUNSUPPORTED;
   if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < closed_workspace_bytes(d)) return MDI_EWORKSPACE;
   if (family == MDI_FAM_EXP) return run_closed_p<MDI_FAM_EXP>(precision, d, a, n_last, params, out, workspace, stream);
   return run_closed_p<MDI_FAM_OSC>(precision, d, a, n_last, params, out, workspace, stream);

@@ -169,6 +169,107 @@ __device__ __forceinline__ double df_to_double(df32 v) { return (double)v.hi + (
 __device__ __forceinline__ df32 df_shfl_down(df32 v, int off) {
   return df32{__shfl_down_sync(0xffffffffu, v.hi, off), __shfl_down_sync(0xffffffffu, v.lo, off)};
 }
+__device__ __forceinline__ df32 df_neg(df32 x) { return df32{-x.hi, -x.lo}; }
+
+// Accumulator for sums of double-float products: Algorithm Dot2 of Ogita, Rump &
+// Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26 (2005), extended
+// to double-float operands.  The product of the high parts is split exactly
+// (TwoProd), the high parts are added with TwoSum, and every low-order part (the
+// product errors, the cross terms hi*lo, the TwoSum errors) is collected in one
+// float, which is folded in once at the end.  About 12 float operations per term
+// instead of about 30 for a renormalised double-float add after each product.
+struct DfAcc {
+  float s = 0.0f, c = 0.0f;
+};
+__device__ __forceinline__ void dacc_prod(DfAcc &a, df32 x, df32 y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  const float e = __fmaf_rn(x.hi, y.hi, -p);
+  const df32 t = two_sum(a.s, p);
+  a.s = t.hi;
+  float c = __fmaf_rn(x.hi, y.lo, a.c);
+  c = __fmaf_rn(x.lo, y.hi, c);
+  a.c = __fadd_rn(c, __fadd_rn(e, t.lo));
+}
+__device__ __forceinline__ void dacc_add(DfAcc &a, df32 x) {
+  const df32 t = two_sum(a.s, x.hi);
+  a.s = t.hi;
+  a.c = __fadd_rn(a.c, __fadd_rn(x.lo, t.lo));
+}
+__device__ __forceinline__ df32 dacc_value(const DfAcc &a) { return two_sum(a.s, a.c); }
+// x * f for a double-float x and a float f (Joldes et al. 2017, Algorithm 9 without
+// the final renormalisation of the error term).
+__device__ __forceinline__ df32 df_mul_f(df32 x, float f) {
+  df32 c = two_prod(x.hi, f);
+  float cl = __fmaf_rn(x.lo, f, c.lo);
+  return fast_two_sum(c.hi, cl);
+}
+__device__ __forceinline__ df32 df_sqr(df32 x) {
+  df32 c = two_prod(x.hi, x.hi);
+  float t = __fmul_rn(__fadd_rn(x.hi, x.hi), x.lo);
+  return fast_two_sum(c.hi, __fadd_rn(c.lo, t));
+}
+__device__ __forceinline__ df32 df_from_float(float f) { return df32{f, 0.0f}; }
+
+// exp(x) for a double-float x with -80 <= x <= 87 (below, the result flushes
+// towards 0 as the float range does).  Table-driven reduction after P. T. P. Tang,
+// "Table-driven implementation of the exponential function in IEEE
+// floating-point arithmetic", ACM TOMS 15 (1989): x = (256 k + j) ln2/256 + r with
+// |r| <= ln2/512, the constant ln2/256 split Cody-Waite style into three floats
+// (C1 with 9 significant bits, so n * C1 is exact for |n| < 2^15), then
+// exp(r) = 1 + r + r^2/2 + r^3/6 (1 + r/4) with the last term (< 5e-10) in float,
+// 2^(j/256) read as a float pair from `tab` (kExpTable entries built by
+// exp2_table_entry), and the power 2^k applied exactly.
+constexpr int kExpTable = 256;
+struct DfExpConsts {
+  // ln2/256 = C1 + C2 + C3 (residual 4.5e-23).
+  static constexpr float C1 = 0.00270843505859375f;
+  static constexpr float C2 = -8.2888453789564664476e-07f;
+  static constexpr float C3 = 6.4320116005783627144e-15f;
+  static constexpr float INV = 369.32993046757463f;  // 256 / ln2, only used to pick n
+};
+__device__ __forceinline__ float2 exp2_table_entry(int j) {
+  const double v = exp2((double)j / (double)kExpTable);
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+__device__ __forceinline__ df32 df_exp(df32 x, const float2 *__restrict__ tab) {
+  const float n = rintf(x.hi * DfExpConsts::INV);
+  // r = x - n ln2/256, accurate to about 2^-50 absolute
+  const float t = __fmaf_rn(-n, DfExpConsts::C1, x.hi);  // exact: n*C1 exact, Sterbenz
+  df32 r = two_sum(t, x.lo);
+  r = df_add(r, two_prod(-n, DfExpConsts::C2));
+  r = fast_two_sum(r.hi, __fmaf_rn(-n, DfExpConsts::C3, r.lo));
+  // exp(r): 1 + r (TwoSum) + r^2/2 (exact product of the high part plus cross term)
+  const float h = 0.5f * r.hi;
+  const float p2 = __fmul_rn(r.hi, h);
+  const float e2 = __fmaf_rn(r.hi, h, -p2);
+  const float cross = __fmul_rn(r.hi, r.lo);
+  const float t3 = __fmul_rn(__fmul_rn(p2, r.hi), __fmaf_rn(r.hi, 1.0f / 12.0f, 1.0f / 3.0f));
+  const df32 s1 = two_sum(1.0f, r.hi);
+  const df32 s2 = two_sum(s1.hi, p2);
+  float lo = __fadd_rn(s1.lo, s2.lo);
+  lo = __fadd_rn(lo, r.lo);
+  lo = __fadd_rn(lo, __fadd_rn(e2, cross));
+  lo = __fadd_rn(lo, t3);
+  df32 e = fast_two_sum(s2.hi, lo);
+  const int ni = (int)n;
+  const int j = ni & (kExpTable - 1), k = ni >> 8;  // floor division for negative n
+  const float2 tj = tab[j];
+  e = df_mul(e, df32{tj.x, tj.y});
+  const float sc = __int_as_float((max(k, -126) + 127) << 23);  // 2^k
+  return df32{e.hi * sc, e.lo * sc};
+}
+
+// 1/x for a positive double-float x: float reciprocal refined by one
+// Newton-Raphson step, y = y0 + y0 (1 - x y0) (quadratic convergence: the
+// residual 2^-24 squares to 2^-48).
+__device__ __forceinline__ df32 df_rcp(df32 x) {
+  const float y0 = __frcp_rn(x.hi);
+  const df32 t = df_mul_f(x, y0);
+  const df32 e = df_add(df32{1.0f, 0.0f}, df_neg(t));
+  const float corr = __fmul_rn(y0, __fadd_rn(e.hi, e.lo));
+  return fast_two_sum(y0, corr);
+}
 
 // ---------------------------------------------------------------------------
 // Reductions with a fixed tree (deterministic).

@@ -402,7 +402,7 @@ mdi_status levels_launch(int family, int d, int64_t a, int64_t n_last, const dou
   if (d < 1 || d > (1 << 16) || a < 1 || a > kNodesAMax || n_last < 1 || n_last > 4096) return MDI_EUNSUPPORTED;
   if (cfg.P < 2 || cfg.P > kNodesPMax || (cfg.P & 1)) return MDI_EINVAL;
   if (grad && cfg.precision != MDI_PREC_FP64) return MDI_EUNSUPPORTED;
-  if (cfg.precision == MDI_PREC_FP32_EVAL_DF32) return MDI_EUNSUPPORTED;
+  if (cfg.precision == MDI_PREC_FP32_EVAL_DF32 || cfg.precision == MDI_PREC_DF64) return MDI_EUNSUPPORTED;
   const int C = checkpoint > 0 ? checkpoint : default_checkpoint(d);
   if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < levels_layout(d, a, cfg.P, C).total)
     return MDI_EWORKSPACE;

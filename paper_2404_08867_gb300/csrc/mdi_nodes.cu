@@ -41,6 +41,8 @@ struct NodesShared {
   double2 G[kNodesPMax];   // state at the nodes (imaginary part 0 for real families)
   float4 Gdf[kNodesPMax];  // the same state as float pairs (re.hi, re.lo, im.hi, im.lo)
   double2 red[kNodesMaxBlock / kWarp];
+  float2 exp2tab[kExpTable];  // 2^(j/256) as float pairs (double-float exp)
+  float4 lvl[2][2];        // double-float c, w, 1/c^2 of the current/next level
   int inst;
   int pad[3];
 };
@@ -104,6 +106,28 @@ __global__ void nodes_table_kernel(int P, void *__restrict__ table) {
 }
 
 
+// Double-float constants of axis j (0-based): (c, w) and (1/c^2, 0).
+__device__ __forceinline__ void make_level_df(const double *__restrict__ prm, int d, int j, float4 *dst) {
+  const double c = prm[j], w = prm[d + j], ic2 = 1.0 / (c * c);
+  const df32 cd = df_from_double(c), wd = df_from_double(w), id = df_from_double(ic2);
+  dst[0] = make_float4(cd.hi, cd.lo, wd.hi, wd.lo);
+  dst[1] = make_float4(id.hi, id.lo, 0.f, 0.f);
+}
+
+// phi_j(u) in double-float arithmetic (EXP, GAUSS, PEAK).
+template <int FAM> __device__ __forceinline__ df32 phi_df(df32 u, float4 cw, float4 ic, const float2 *tab) {
+  const df32 c{cw.x, cw.y}, w{cw.z, cw.w};
+  if constexpr (FAM == MDI_FAM_EXP) {
+    return df_exp(df_mul(c, u), tab);
+  } else if constexpr (FAM == MDI_FAM_GAUSS) {
+    const df32 t = df_mul(c, df_add(u, df_neg(w)));
+    return df_exp(df_neg(df_sqr(t)), tab);
+  } else {
+    const df32 t = df_add(u, df_neg(w));
+    return df_rcp(df_add(df_sqr(t), df32{ic.x, ic.y}));
+  }
+}
+
 __device__ __forceinline__ void set_state(NodesShared &sh, int t, double2 g) {
   sh.G[t] = g;
   const float rh = (float)g.x, ih = (float)g.y;
@@ -118,9 +142,10 @@ template <int FAM, int PREC>
 __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, void *__restrict__ rowsum, int P, int d,
                           int a, int n_last, const double *__restrict__ prm, double *__restrict__ out_slot) {
   using V = typename FamTraits<FAM>::V;
-  constexpr bool F32 = (PREC != MDI_PREC_FP64);
-  constexpr bool DF = (PREC == MDI_PREC_FP32_EVAL_DF32);
+  constexpr bool F32 = (PREC == MDI_PREC_FP32_EVAL_FP64 || PREC == MDI_PREC_FP32_EVAL_DF32);
+  constexpr bool DF = (PREC == MDI_PREC_FP32_EVAL_DF32 || PREC == MDI_PREC_DF64);
   constexpr bool CPLX = (FAM == MDI_FAM_OSC);
+  constexpr bool DF64 = (PREC == MDI_PREC_DF64) && !CPLX;  // OSC keeps FP64 phi in this mode
   const int tid = threadIdx.x, B = blockDim.x;
   const int p = tid % P, row = tid / P, rows = B / P;
   const bool active = row < rows;  // threads beyond rows*P only join barriers
@@ -128,17 +153,28 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, void *
   const double inv_a = 1.0 / (double)a;
   const double xi_p = sh.xi[p];
 
+  // Double-float coordinates: u = q/a + xi_p/a.
+  const df32 ia = df_from_double(inv_a), xa = df_from_double(xi_p * inv_a);
   if (tid < P) set_state(sh, tid, make_double2(1.0, 0.0));
+  if (DF64 && tid == 0 && d > 1) make_level_df(prm, d, 0, sh.lvl[1]);
   __syncthreads();
 
   for (int k = 1; k < d; ++k) {
-    const AxisParams ap = load_axis(prm, d, k - 1);
+    const AxisParams ap = DF64 ? AxisParams{} : load_axis(prm, d, k - 1);
+    const float4 lc0 = sh.lvl[k & 1][0], lc1 = sh.lvl[k & 1][1];
     double2 acc = make_double2(0.0, 0.0);
-    df32 dre{0.f, 0.f}, dim{0.f, 0.f};
+    DfAcc dre, dim;
     for (int i = active ? tid : npts; i < npts; i += rows * P) {
       const int q = i / P;
-      const double u = ((double)q + xi_p) * inv_a;
-      const V f = phi<FAM, F32>(u, ap);
+      V f;
+      df32 fdf{0.f, 0.f};
+      if constexpr (DF64) {
+        const df32 u = df_add(df_mul_f(ia, (float)q), xa);
+        fdf = phi_df<FAM>(u, lc0, lc1, sh.exp2tab);
+      } else {
+        const double u = ((double)q + xi_p) * inv_a;
+        f = phi<FAM, F32>(u, ap);
+      }
       if constexpr (!DF) {
         V g;
         if (k == 1) {
@@ -151,31 +187,44 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, void *
         }
         acc = c_add(acc, as2(VOps<V>::mul(f, g)));
       } else {
+        // Interpolation and cluster sum in double-float, Dot2-style accumulation.
         const float2 *L = (const float2 *)Ltab + i;
         df32 gr{1.f, 0.f}, gi{0.f, 0.f};
         if (k > 1) {
-          gr = df32{0.f, 0.f};
+          DfAcc ar, ai;
 #pragma unroll 4
           for (int t = 0; t < P; ++t) {
             const float2 l = L[(size_t)t * npts];
             const float4 gt = sh.Gdf[t];
-            gr = df_add(gr, df_mul(df32{l.x, l.y}, df32{gt.x, gt.y}));
-            if constexpr (CPLX) gi = df_add(gi, df_mul(df32{l.x, l.y}, df32{gt.z, gt.w}));
+            dacc_prod(ar, df32{l.x, l.y}, df32{gt.x, gt.y});
+            if constexpr (CPLX) dacc_prod(ai, df32{l.x, l.y}, df32{gt.z, gt.w});
           }
+          gr = dacc_value(ar);
+          if constexpr (CPLX) gi = dacc_value(ai);
         }
         if constexpr (CPLX) {
-          const float fr = (float)as2(f).x, fi = (float)as2(f).y;
-          dre = df_add(dre, df_add(df_mul(df32{fr, 0.f}, gr), df_mul(df32{-fi, 0.f}, gi)));
-          dim = df_add(dim, df_add(df_mul(df32{fr, 0.f}, gi), df_mul(df32{fi, 0.f}, gr)));
+          const double2 f2 = as2(f);
+          const df32 fr = (PREC == MDI_PREC_DF64) ? df_from_double(f2.x) : df32{(float)f2.x, 0.f};
+          const df32 fi = (PREC == MDI_PREC_DF64) ? df_from_double(f2.y) : df32{(float)f2.y, 0.f};
+          dacc_prod(dre, fr, gr);
+          dacc_prod(dre, df_neg(fi), gi);
+          dacc_prod(dim, fr, gi);
+          dacc_prod(dim, fi, gr);
+        } else if constexpr (DF64) {
+          dacc_prod(dre, fdf, gr);
         } else {
-          dre = df_add(dre, df_mul(df32{(float)as2(f).x, 0.f}, gr));
+          dacc_prod(dre, df32{(float)as2(f).x, 0.f}, gr);
         }
       }
     }
     // Partial rows -> new state at node p, added in row order.
     if (active) {
-      if constexpr (DF) ((float4 *)rowsum)[row * P + p] = make_float4(dre.hi, dre.lo, dim.hi, dim.lo);
-      else ((double2 *)rowsum)[row * P + p] = acc;
+      if constexpr (DF) {
+        const df32 vr = dacc_value(dre), vi = dacc_value(dim);
+        ((float4 *)rowsum)[row * P + p] = make_float4(vr.hi, vr.lo, vi.hi, vi.lo);
+      } else {
+        ((double2 *)rowsum)[row * P + p] = acc;
+      }
     }
     __syncthreads();
     if (tid < P) {
@@ -194,6 +243,7 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, void *
         g = c_scale(s, inv_a);
       }
       set_state(sh, tid, g);
+      if (DF64 && tid == 0 && k + 1 < d) make_level_df(prm, d, k, sh.lvl[(k + 1) & 1]);
     }
     __syncthreads();
   }
@@ -254,6 +304,8 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
     sh.xi[t] = cheb_node(t, P);
     sh.bw[t] = cheb_weight(t, P);
   }
+  if (PREC == MDI_PREC_DF64)
+    for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) sh.exp2tab[j] = exp2_table_entry(j);
   int staged_a = -1;
   // counter[0]: next work item; counter[1]: CTAs finished; counter[2]: preparation tag.
   const bool prepared = counter[2] == expect_tag;
@@ -328,15 +380,20 @@ NodesConfig nodes_config(const mdi_opts *opts) {
 static bool config_ok(const NodesConfig &c) {
   if (c.P < 2 || c.P > kNodesPMax || (c.P & 1)) return false;  // even P keeps tables 16-byte aligned
   if (c.block < 32 || c.block > kNodesMaxBlock || c.block % 32 || c.block < c.P) return false;
-  if (c.precision < MDI_PREC_FP64 || c.precision > MDI_PREC_FP32_EVAL_DF32) return false;
+  if (c.precision < MDI_PREC_FP64 || c.precision > MDI_PREC_DF64) return false;
   return c.ctas_per_sm >= 0 && c.ctas_per_sm <= 32;
+}
+
+// Double-float precision modes read the basis tables as float pairs.
+static bool df_tables(const NodesConfig &c) {
+  return c.precision == MDI_PREC_FP32_EVAL_DF32 || c.precision == MDI_PREC_DF64;
 }
 
 static size_t counter_bytes() { return align_up(4 * sizeof(unsigned)); }
 
 // Tag stamped by the preparation: node count and table format.
 static unsigned nodes_tag(const NodesConfig &c) {
-  return 0x4D440000u | ((unsigned)c.P << 4) | (c.precision == MDI_PREC_FP32_EVAL_DF32 ? 1u : 0u);
+  return 0x4D440000u | ((unsigned)c.P << 4) | (df_tables(c) ? 1u : 0u);
 }
 
 size_t nodes_batched_workspace_bytes(int count, const NodesConfig &cfg) {
@@ -355,7 +412,7 @@ mdi_status nodes_prepare(const NodesConfig &cfg, void *workspace, size_t ws_byte
   unsigned *counter = (unsigned *)workspace;
   void *tables = (char *)workspace + counter_bytes();
   const int table_grid = sm_count() * 2;
-  if (cfg.precision == MDI_PREC_FP32_EVAL_DF32) nodes_table_kernel<true><<<table_grid, 256, 0, stream>>>(cfg.P, tables);
+  if (df_tables(cfg)) nodes_table_kernel<true><<<table_grid, 256, 0, stream>>>(cfg.P, tables);
   else nodes_table_kernel<false><<<table_grid, 256, 0, stream>>>(cfg.P, tables);
   mdi_status st = check_launch();
   if (st != MDI_OK) return st;
@@ -370,7 +427,7 @@ static mdi_status launch_nodes(const mdi_batch_desc *descs, const int32_t *order
   unsigned *counter = (unsigned *)ws;
   void *tables = (char *)ws + counter_bytes();
   const size_t smem = nodes_smem_bytes(cfg.block, cfg.P);
-  static thread_local bool attr_set[3] = {false, false, false};
+  static thread_local bool attr_set[4] = {false, false, false, false};
   if (!attr_set[PREC]) {
     cudaError_t e = cudaFuncSetAttribute(nodes_batched_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)nodes_smem_bytes(kNodesMaxBlock, 2));
@@ -405,7 +462,9 @@ static mdi_status dispatch_nodes(const mdi_batch_desc *descs, const int32_t *ord
     case MDI_PREC_FP64: return launch_nodes<MDI_PREC_FP64>(descs, order, count, single, pool, cfg, out, ws, stream);
     case MDI_PREC_FP32_EVAL_FP64:
       return launch_nodes<MDI_PREC_FP32_EVAL_FP64>(descs, order, count, single, pool, cfg, out, ws, stream);
-    default: return launch_nodes<MDI_PREC_FP32_EVAL_DF32>(descs, order, count, single, pool, cfg, out, ws, stream);
+    case MDI_PREC_FP32_EVAL_DF32:
+      return launch_nodes<MDI_PREC_FP32_EVAL_DF32>(descs, order, count, single, pool, cfg, out, ws, stream);
+    default: return launch_nodes<MDI_PREC_DF64>(descs, order, count, single, pool, cfg, out, ws, stream);
   }
 }
 

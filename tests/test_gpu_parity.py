@@ -238,3 +238,37 @@ def test_batched_mixed_families_and_edges():
     for i, f in enumerate(fams):
         p = pool[offs[i]:offs[i] + 2 * ds[i]]
         close(out[i].item(), o.mdi_nodes(f, ds[i], as_[i], nls[i], 16, p[:ds[i]], p[ds[i]:]), f)
+
+
+# ----------------------------------------------------------------------------
+# Double-float mode (MDI_PREC_DF64): FP64-class results from the FP32 pipes,
+# held to the same 1e-12 as the FP64 path.
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("fam", ["gauss", "peak", "exp", "osc"])
+@pytest.mark.parametrize("d,a,nd,P", [(4, 16, 16, 16), (1, 9, 9, 16), (2, 1, 5, 16), (12, 8, 8, 8), (6, 32, 13, 32),
+                                      (5, 64, 64, 16), (30, 20, 20, 16), (20, 32, 32, 16)])
+def test_df64_nodes_matches_fp64_oracle(fam, d, a, nd, P):
+    params = inputs.random_product(fam, d, seed=3 * d + a)
+    got = mdi.mdi_lr_integrate(fam, dev(params), d, a, nd, state="nodes", nodes=P, precision="df64").item()
+    close(got, o.mdi_nodes(fam, d, a, nd, P, params[:d], params[d:]), fam)
+
+
+def test_df64_batched_full_size_sampled():
+    b = inputs.batch(count=4096, seed=0)
+    _, d_descs, d_order, pool = _batch_to_device(b)
+    out = mdi.mdi_lr_integrate_batched(d_descs, pool, len(b), order=d_order, precision="df64").cpu().numpy()
+    worst = 0.0
+    for i in np.random.default_rng(1).choice(len(b), 128, replace=False):
+        it = b.integral(int(i))
+        ref = o.mdi_nodes(it.family, it.d, it.a, it.n_last, 16, it.c, it.w)
+        worst = max(worst, abs(out[i] - ref) / abs(ref))
+    assert worst <= TOL, worst
+
+
+def test_df64_wide_parameter_range():
+    """Larger c (steeper Gaussians and peaks) than the batch draws: the double-float
+    exp and reciprocal keep 1e-12 over the state's wider dynamic range."""
+    for fam, seed in (("gauss", 1), ("peak", 2), ("exp", 3)):
+        params = inputs.random_product(fam, 15, seed=seed, c_range=(0.5, 4.0))
+        got = mdi.mdi_lr_integrate(fam, dev(params), 15, 24, 24, state="nodes", precision="df64").item()
+        close(got, o.mdi_nodes(fam, 15, 24, 24, 16, params[:15], params[15:]), fam)
