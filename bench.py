@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--count", type=int, default=COUNT)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_eval_fp64", "fp32_eval_df32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_eval_fp64", "fp32_eval_df32", "df64"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="budget of the CPU oracle sample")
     ap.add_argument("--no-extras", action="store_true", help="skip the small-workload comparison")
     return ap.parse_args()

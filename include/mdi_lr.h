@@ -100,7 +100,10 @@ typedef struct {
                           multiple of 32 and of P); 0 selects the library default */
   int32_t ctas_per_sm; /* resident CTAs per SM for persistent grids; 0 = default */
   int32_t checkpoint;  /* level-checkpoint interval of the adjoint; 0 = ceil(sqrt(d)) */
-  int32_t reserved[2]; /* must be 0 */
+  int32_t table_in_l1; /* node-state kernels: 0 = stage each integral's basis table in
+                          shared memory (when it fits 64 KiB), 1 = read it through L1
+                          (less shared memory, more resident CTAs) */
+  int32_t reserved;    /* must be 0 */
 } mdi_opts;
 
 /* ---------------------------------------------------------------------------

@@ -55,10 +55,10 @@ def _dev_f64(t: torch.Tensor, name: str) -> torch.Tensor:
     return t
 
 
-def _opts(state="auto", precision="fp64", nodes=0, block=0, ctas_per_sm=0, checkpoint=0) -> MdiOpts:
+def _opts(state="auto", precision="fp64", nodes=0, block=0, ctas_per_sm=0, checkpoint=0, table_in_l1=0) -> MdiOpts:
     o = MdiOpts()
     o.state, o.precision, o.nodes, o.block = _state(state), _prec(precision), int(nodes), int(block)
-    o.ctas_per_sm, o.checkpoint = int(ctas_per_sm), int(checkpoint)
+    o.ctas_per_sm, o.checkpoint, o.table_in_l1 = int(ctas_per_sm), int(checkpoint), int(bool(table_in_l1))
     return o
 
 

@@ -37,7 +37,8 @@ static bool opts_ok(const mdi_opts *o) {
   if (o->state < MDI_STATE_AUTO || o->state > MDI_STATE_NODES) return false;
   if (o->precision < MDI_PREC_FP64 || o->precision > MDI_PREC_DF64) return false;
   if (o->nodes < 0 || o->block < 0 || o->ctas_per_sm < 0 || o->checkpoint < 0) return false;
-  return o->reserved[0] == 0 && o->reserved[1] == 0;
+  if (o->table_in_l1 != 0 && o->table_in_l1 != 1) return false;
+  return o->reserved == 0;
 }
 
 static int resolve_state(int family, const mdi_opts *o) {

@@ -38,6 +38,7 @@ struct NodesConfig {
   int block;        // threads per CTA
   int ctas_per_sm;  // persistent CTAs per SM
   int precision;    // mdi_precision
+  int stage;        // 1: stage each integral's basis table in shared memory; 0: read it through L1
 };
 NodesConfig nodes_config(const mdi_opts *opts);
 size_t nodes_batched_workspace_bytes(int count, const NodesConfig &cfg);

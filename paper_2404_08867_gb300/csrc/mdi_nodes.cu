@@ -14,15 +14,23 @@
 // them from an atomic counter (no waiting: a CTA that finds the queue empty
 // exits).  A CTA sweeps its integral's d levels with the state in shared memory.
 // Inside a level, thread t owns node p = t mod P and cluster points q = t/P,
-// t/P + B/P, ...; each point interpolates G_{k-1} (P FMAs against the basis table
-// L_a[t][q*P+p] = l_t(u_qp), staged in shared memory), multiplies by phi_k, and
-// accumulates; the B/P partial rows are then added in a fixed order by P threads.
-// The basis tables depend only on (a, P): one small kernel builds them for
-// a = 1..64 at the start of every call, spread over the whole GPU.
+// t/P + B/P, ...; each point interpolates G_{k-1} (P multiply-adds against the
+// basis table L_a[t][q*P+p] = l_t(u_qp)), multiplies by phi_k, and accumulates;
+// the B/P partial rows are then added in a fixed order by P threads.  The basis
+// tables depend only on (a, P) and are built once per workspace
+// (mdi_lr_batched_prepare) for a = 1..64, together with the basis at the last
+// axis' points s/a (used when n_last = a).  A CTA may stage its table in shared
+// memory (fewer resident CTAs) or read it through L1 (more resident CTAs to hide
+// the level barriers); the autotuner picks.
 //
-// Precision modes (mdi_precision): FP64 everywhere; phi in float with FP64
-// interpolation and sums; phi in float with interpolation and the cluster sum in
-// double-float pairs, the state kept in FP64 between levels.
+// Precision modes (mdi_precision):
+//   FP64             everything in double;
+//   FP32_EVAL_FP64   phi in float, interpolation and sums in double;
+//   FP32_EVAL_DF32   phi in float, interpolation and the cluster sum in
+//                    double-float, the state in double between levels;
+//   DF64             coordinates, phi, interpolation, sums and the state in
+//                    double-float (no FP64 instruction per cluster point or per
+//                    level); OSC keeps phi in double.
 #include <algorithm>
 
 #include "mdi_common.cuh"
@@ -35,33 +43,35 @@ constexpr int kNodesMaxBlock = 512;
 constexpr int kNodesSmemTable = 64 * 1024;  // table bytes staged in shared memory
 
 // Fixed part of the dynamic shared memory.  The partial rows (rows x P x 16 B)
-// and the staged table follow it.
+// and, when staging, the table follow it.
 struct NodesShared {
   double xi[kNodesPMax], bw[kNodesPMax];
-  double2 G[kNodesPMax];   // state at the nodes (imaginary part 0 for real families)
-  float4 Gdf[kNodesPMax];  // the same state as float pairs (re.hi, re.lo, im.hi, im.lo)
+  double2 G[kNodesPMax];   // state at the nodes in double (imaginary part 0 for real families)
+  float4 Gdf[kNodesPMax];  // the state as float pairs (re.hi, re.lo, im.hi, im.lo)
+  float2 xadf[kNodesPMax]; // xi_p / a as float pairs (DF64), per integral
   double2 red[kNodesMaxBlock / kWarp];
+  float4 redf[kNodesMaxBlock / kWarp];
   float2 exp2tab[kExpTable];  // 2^(j/256) as float pairs (double-float exp)
-  float4 lvl[2][2];        // double-float c, w, 1/c^2 of the current/next level
+  float4 lvl[2][2];           // double-float c, w, 1/c^2 of the current/next level
+  float2 iadf;                // 1/a as a float pair (DF64)
   int inst;
-  int pad[3];
+  int pad;
 };
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 __host__ __device__ inline size_t rows_bytes(int block, int P) { return align16((size_t)(block / P) * P * 16); }
-static size_t nodes_smem_bytes(int block, int P) {
-  return align16(sizeof(NodesShared)) + rows_bytes(block, P) + kNodesSmemTable;
+static size_t nodes_smem_bytes(int block, int P, bool stage) {
+  return align16(sizeof(NodesShared)) + rows_bytes(block, P) + (stage ? kNodesSmemTable : 0);
 }
 
-// Offset (in 8-byte entries) of the table of parameter a (1-based) for P nodes.
+// Table of parameter a (1-based) for P nodes, in 8-byte entries: the cluster basis
+// L_a[t][q*P + p] (a*P*P entries) followed by the last-axis basis F_a[t][s] =
+// l_t(s/a) (a*P entries).  Even P keeps every block 16-byte aligned.
 __host__ __device__ __forceinline__ size_t table_offset(int a, int P) {
-  return (size_t)P * P * (size_t)a * (size_t)(a - 1) / 2;
+  return (size_t)P * (P + 1) * (size_t)a * (size_t)(a - 1) / 2;
 }
 static size_t table_bytes(int P) { return 8 * table_offset(kNodesAMax + 1, P); }
 
-
-// Basis tables L_a[t][q*P + p] = l_t((q + xi_p)/a) for a = 1..64, stored as double
-// (DF = false) or as a float pair hi + lo (DF = true); 8 bytes per entry either way.
 template <bool DF>
 __global__ void nodes_table_kernel(int P, void *__restrict__ table) {
   __shared__ double s_xi[kNodesPMax], s_bw[kNodesPMax];
@@ -70,31 +80,31 @@ __global__ void nodes_table_kernel(int P, void *__restrict__ table) {
     s_bw[t] = cheb_weight(t, P);
   }
   __syncthreads();
-  const size_t total_pts = (size_t)P * kNodesAMax * (kNodesAMax + 1) / 2;  // sum_a a*P points
-  for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total_pts;
+  const size_t total_rows = (size_t)(P + 1) * kNodesAMax * (kNodesAMax + 1) / 2;  // sum_a a*(P+1)
+  for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total_rows;
        g += (size_t)gridDim.x * blockDim.x) {
     int a = 1;
     size_t base = 0;
-    while (base + (size_t)a * P <= g) {
-      base += (size_t)a * P;
+    while (base + (size_t)a * (P + 1) <= g) {
+      base += (size_t)a * (P + 1);
       ++a;
     }
-    const int i = (int)(g - base);  // i = q*P + p
-    const int q = i / P, p = i % P;
-    const double u = ((double)q + s_xi[p]) / (double)a;
+    const int i = (int)(g - base);
+    const bool last_axis = i >= a * P;
+    double u;
+    if (last_axis) u = (double)(i - a * P) / (double)a;                 // s / a
+    else u = ((double)(i / P) + s_xi[i % P]) / (double)a;              // (q + xi_p) / a
     double den = 0.0;
     int hit = -1;
     for (int t = 0; t < P; ++t) {
-      const double xt = s_xi[t];
-      if (u == xt) hit = t;
-      else den += s_bw[t] / (u - xt);
+      if (u == s_xi[t]) hit = t;
+      else den += s_bw[t] / (u - s_xi[t]);
     }
     const size_t off = table_offset(a, P);
     for (int t = 0; t < P; ++t) {
-      double l;
-      if (hit >= 0) l = (t == hit) ? 1.0 : 0.0;
-      else l = (s_bw[t] / (u - s_xi[t])) / den;
-      const size_t idx = off + (size_t)t * a * P + i;
+      const double l = hit >= 0 ? (t == hit ? 1.0 : 0.0) : (s_bw[t] / (u - s_xi[t])) / den;
+      const size_t idx = last_axis ? off + (size_t)a * P * P + (size_t)t * a + (i - a * P)
+                                   : off + (size_t)t * a * P + i;
       if constexpr (DF) {
         const float h = (float)l;
         ((float2 *)table)[idx] = make_float2(h, (float)(l - (double)h));
@@ -104,7 +114,6 @@ __global__ void nodes_table_kernel(int P, void *__restrict__ table) {
     }
   }
 }
-
 
 // Double-float constants of axis j (0-based): (c, w) and (1/c^2, 0).
 __device__ __forceinline__ void make_level_df(const double *__restrict__ prm, int d, int j, float4 *dst) {
@@ -128,40 +137,81 @@ template <int FAM> __device__ __forceinline__ df32 phi_df(df32 u, float4 cw, flo
   }
 }
 
-__device__ __forceinline__ void set_state(NodesShared &sh, int t, double2 g) {
-  sh.G[t] = g;
+__device__ __forceinline__ float4 split2(double2 g) {
   const float rh = (float)g.x, ih = (float)g.y;
-  sh.Gdf[t] = make_float4(rh, (float)(g.x - (double)rh), ih, (float)(g.y - (double)ih));
+  return make_float4(rh, (float)(g.x - (double)rh), ih, (float)(g.y - (double)ih));
+}
+__device__ __forceinline__ double2 join2(float4 v) {
+  return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+}
+
+// Block sum of double-float pairs (re, im); result valid in thread 0.
+__device__ __forceinline__ float4 block_sum_df(df32 re, df32 im, float4 *scratch) {
+  const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x / kWarp;
+  const int nwarps = (blockDim.x + kWarp - 1) / kWarp;
+#pragma unroll
+  for (int off = kWarp / 2; off > 0; off >>= 1) {
+    re = df_add(re, df_shfl_down(re, off));
+    im = df_add(im, df_shfl_down(im, off));
+  }
+  if (lane == 0) scratch[warp] = make_float4(re.hi, re.lo, im.hi, im.lo);
+  __syncthreads();
+  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (threadIdx.x == 0) {
+    df32 sr{0.f, 0.f}, si{0.f, 0.f};
+    for (int w = 0; w < nwarps; ++w) {
+      sr = df_add(sr, df32{scratch[w].x, scratch[w].y});
+      si = df_add(si, df32{scratch[w].z, scratch[w].w});
+    }
+    r = make_float4(sr.hi, sr.lo, si.hi, si.lo);
+  }
+  __syncthreads();
+  return r;
 }
 
 // ---------------------------------------------------------------------------
-// One integral, swept by one CTA.  Ltab: the basis table of this a (shared or
-// global memory); rowsum: rows x P slots of 16 bytes in shared memory.
+// One integral, swept by one CTA.  Ltab: the cluster basis of this a (shared or
+// global memory); Ftab: the last-axis basis (global); rowsum: rows x P slots of
+// 16 bytes in shared memory.
 // ---------------------------------------------------------------------------
 template <int FAM, int PREC>
-__device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, void *__restrict__ rowsum, int P, int d,
-                          int a, int n_last, const double *__restrict__ prm, double *__restrict__ out_slot) {
+__device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, const void *__restrict__ Ftab,
+                          void *__restrict__ rowsum, int P, int d, int a, int n_last, const double *__restrict__ prm,
+                          double *__restrict__ out_slot) {
   using V = typename FamTraits<FAM>::V;
   constexpr bool F32 = (PREC == MDI_PREC_FP32_EVAL_FP64 || PREC == MDI_PREC_FP32_EVAL_DF32);
   constexpr bool DF = (PREC == MDI_PREC_FP32_EVAL_DF32 || PREC == MDI_PREC_DF64);
   constexpr bool CPLX = (FAM == MDI_FAM_OSC);
-  constexpr bool DF64 = (PREC == MDI_PREC_DF64) && !CPLX;  // OSC keeps FP64 phi in this mode
+  constexpr bool DF64 = (PREC == MDI_PREC_DF64) && !CPLX;  // OSC keeps phi in FP64 in this mode
+  constexpr bool DFSTATE = (PREC == MDI_PREC_DF64);        // state kept as float pairs only
   const int tid = threadIdx.x, B = blockDim.x;
   const int p = tid % P, row = tid / P, rows = B / P;
   const bool active = row < rows;  // threads beyond rows*P only join barriers
   const int npts = a * P;
-  const double inv_a = 1.0 / (double)a;
-  const double xi_p = sh.xi[p];
 
-  // Double-float coordinates: u = q/a + xi_p/a.
-  const df32 ia = df_from_double(inv_a), xa = df_from_double(xi_p * inv_a);
-  if (tid < P) set_state(sh, tid, make_double2(1.0, 0.0));
-  if (DF64 && tid == 0 && d > 1) make_level_df(prm, d, 0, sh.lvl[1]);
+  if (tid < P) {
+    sh.Gdf[tid] = make_float4(1.f, 0.f, 0.f, 0.f);
+    sh.G[tid] = make_double2(1.0, 0.0);
+    if (DFSTATE) {
+      const double xa = sh.xi[tid] / (double)a;
+      const float h = (float)xa;
+      sh.xadf[tid] = make_float2(h, (float)(xa - (double)h));
+    }
+  }
+  if (tid == 0 && DFSTATE) {
+    const double ia = 1.0 / (double)a;
+    const float h = (float)ia;
+    sh.iadf = make_float2(h, (float)(ia - (double)h));
+    if (DF64) make_level_df(prm, d, 0, sh.lvl[1]);
+  }
   __syncthreads();
+  const double inv_a = DF64 ? 0.0 : 1.0 / (double)a;
+  const double xi_p = sh.xi[p];
 
   for (int k = 1; k < d; ++k) {
     const AxisParams ap = DF64 ? AxisParams{} : load_axis(prm, d, k - 1);
     const float4 lc0 = sh.lvl[k & 1][0], lc1 = sh.lvl[k & 1][1];
+    const df32 ia{sh.iadf.x, sh.iadf.y}, xa{sh.xadf[p].x, sh.xadf[p].y};
     double2 acc = make_double2(0.0, 0.0);
     DfAcc dre, dim;
     for (int i = active ? tid : npts; i < npts; i += rows * P) {
@@ -228,7 +278,6 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, void *
     }
     __syncthreads();
     if (tid < P) {
-      double2 g;
       if constexpr (DF) {
         df32 sr{0.f, 0.f}, si{0.f, 0.f};
         for (int r = 0; r < rows; ++r) {
@@ -236,19 +285,54 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, void *
           sr = df_add(sr, df32{v.x, v.y});
           si = df_add(si, df32{v.z, v.w});
         }
-        g = make_double2(df_to_double(sr) * inv_a, df_to_double(si) * inv_a);
+        if constexpr (DFSTATE) {
+          const df32 ia{sh.iadf.x, sh.iadf.y};
+          const df32 gr = df_mul(sr, ia), gi = df_mul(si, ia);
+          sh.Gdf[tid] = make_float4(gr.hi, gr.lo, gi.hi, gi.lo);
+        } else {
+          const double2 g = make_double2(df_to_double(sr) * inv_a, df_to_double(si) * inv_a);
+          sh.G[tid] = g;
+          sh.Gdf[tid] = split2(g);
+        }
       } else {
         double2 s = make_double2(0.0, 0.0);
         for (int r = 0; r < rows; ++r) s = c_add(s, ((const double2 *)rowsum)[r * P + tid]);
-        g = c_scale(s, inv_a);
+        sh.G[tid] = c_scale(s, inv_a);
       }
-      set_state(sh, tid, g);
-      if (DF64 && tid == 0 && k + 1 < d) make_level_df(prm, d, k, sh.lvl[(k + 1) & 1]);
+      if (DF64 && tid == 0) make_level_df(prm, d, k, sh.lvl[(k + 1) & 1]);  // axis k = level k+1 (<= d)
     }
     __syncthreads();
   }
 
   // Last level: Q = (1/n_last) sum_s phi_d(s/n_last) G_{d-1}(s/n_last).
+  const bool tabulated = (n_last == a) && d > 1;
+  if constexpr (DF64) {
+    if (tabulated) {
+      const float4 lc0 = sh.lvl[d & 1][0], lc1 = sh.lvl[d & 1][1];
+      const df32 ia{sh.iadf.x, sh.iadf.y};
+      DfAcc acc;
+      for (int s = tid; s < n_last; s += B) {
+        const float2 *F = (const float2 *)Ftab + s;
+        DfAcc ag;
+#pragma unroll 4
+        for (int t = 0; t < P; ++t) {
+          const float2 l = F[(size_t)t * a];
+          const float4 gt = sh.Gdf[t];
+          dacc_prod(ag, df32{l.x, l.y}, df32{gt.x, gt.y});
+        }
+        const df32 u = df_mul_f(ia, (float)s);
+        dacc_prod(acc, phi_df<FAM>(u, lc0, lc1, sh.exp2tab), dacc_value(ag));
+      }
+      const float4 tot = block_sum_df(dacc_value(acc), df32{0.f, 0.f}, sh.redf);
+      if (tid == 0) *out_slot = ((double)tot.x + (double)tot.y) / (double)n_last;
+      __syncthreads();
+      return;
+    }
+  }
+  if constexpr (DFSTATE) {  // double view of the state for the general last level
+    if (tid < P) sh.G[tid] = join2(sh.Gdf[tid]);
+    __syncthreads();
+  }
   const AxisParams ap = load_axis(prm, d, d - 1);
   const double inv_n = 1.0 / (double)n_last;
   V acc = VOps<V>::zero();
@@ -257,6 +341,18 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, void *
     V g;
     if (d == 1) {
       g = VOps<V>::one();
+    } else if (tabulated) {
+      g = VOps<V>::zero();
+      if constexpr (DF) {
+        const float2 *F = (const float2 *)Ftab + s;
+        for (int t = 0; t < P; ++t) {
+          const float2 l = F[(size_t)t * a];
+          g = VOps<V>::fma_s((double)l.x + (double)l.y, from2<V>(sh.G[t]), g);
+        }
+      } else {
+        const double *F = (const double *)Ftab + s;
+        for (int t = 0; t < P; ++t) g = VOps<V>::fma_s(F[(size_t)t * a], from2<V>(sh.G[t]), g);
+      }
     } else {
       double den = 0.0;
       double2 num = make_double2(0.0, 0.0);
@@ -272,7 +368,7 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, void *
       }
       g = hit >= 0 ? from2<V>(sh.G[hit]) : from2<V>(c_scale(num, 1.0 / den));
     }
-    acc = VOps<V>::add(acc, VOps<V>::mul(phi<FAM, F32>(u, ap), g));
+    acc = VOps<V>::add(acc, VOps<V>::mul(phi<FAM, F32 && !DFSTATE>(u, ap), g));
   }
   const V tot = block_sum(acc, (V *)sh.red);
   if (tid == 0) {
@@ -293,7 +389,7 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
                                                                        mdi_batch_desc single,
                                                                        const double *__restrict__ pool,
                                                                        const void *__restrict__ tables, int P,
-                                                                       double *__restrict__ out,
+                                                                       int stage, double *__restrict__ out,
                                                                        unsigned *__restrict__ counter,
                                                                        unsigned expect_tag) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
@@ -324,15 +420,15 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
       if (threadIdx.x == 0) out[inst] = __longlong_as_double(0x7ff8000000000000ll);  // NaN marks a bad descriptor
       continue;
     }
-    const size_t tbytes = (size_t)a * P * P * 8;
+    const size_t tbytes = (size_t)a * P * P * 8;  // cluster part; a multiple of 16 for even P
     const unsigned char *gtab = (const unsigned char *)tables + table_offset(a, P) * 8;
     const void *Ltab = gtab;
-    if (tbytes <= (size_t)kNodesSmemTable && ds.d > 1) {
+    const void *Ftab = gtab + tbytes;
+    if (stage && tbytes <= (size_t)kNodesSmemTable && ds.d > 1) {
       if (staged_a != a) {
-        const double2 *src = (const double2 *)gtab;  // tbytes is a multiple of 16 (P*P*8, P even or a*P*P even)
+        const double2 *src = (const double2 *)gtab;
         double2 *dst = (double2 *)tab_smem;
         for (size_t i = threadIdx.x; i < tbytes / 16; i += blockDim.x) dst[i] = src[i];
-        if ((tbytes & 15) && threadIdx.x == 0) ((double *)tab_smem)[tbytes / 8 - 1] = ((const double *)gtab)[tbytes / 8 - 1];
         staged_a = a;
         __syncthreads();
       }
@@ -340,10 +436,18 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
     }
     const double *prm = pool + ds.param_offset;
     switch (ds.family) {
-      case MDI_FAM_EXP: sweep_one<MDI_FAM_EXP, PREC>(sh, Ltab, rowsum, P, ds.d, a, ds.n_last, prm, out + inst); break;
-      case MDI_FAM_OSC: sweep_one<MDI_FAM_OSC, PREC>(sh, Ltab, rowsum, P, ds.d, a, ds.n_last, prm, out + inst); break;
-      case MDI_FAM_GAUSS: sweep_one<MDI_FAM_GAUSS, PREC>(sh, Ltab, rowsum, P, ds.d, a, ds.n_last, prm, out + inst); break;
-      default: sweep_one<MDI_FAM_PEAK, PREC>(sh, Ltab, rowsum, P, ds.d, a, ds.n_last, prm, out + inst); break;
+      case MDI_FAM_EXP:
+        sweep_one<MDI_FAM_EXP, PREC>(sh, Ltab, Ftab, rowsum, P, ds.d, a, ds.n_last, prm, out + inst);
+        break;
+      case MDI_FAM_OSC:
+        sweep_one<MDI_FAM_OSC, PREC>(sh, Ltab, Ftab, rowsum, P, ds.d, a, ds.n_last, prm, out + inst);
+        break;
+      case MDI_FAM_GAUSS:
+        sweep_one<MDI_FAM_GAUSS, PREC>(sh, Ltab, Ftab, rowsum, P, ds.d, a, ds.n_last, prm, out + inst);
+        break;
+      default:
+        sweep_one<MDI_FAM_PEAK, PREC>(sh, Ltab, Ftab, rowsum, P, ds.d, a, ds.n_last, prm, out + inst);
+        break;
     }
   }
   // The last CTA to finish re-arms the queue for the next call on this workspace.
@@ -367,12 +471,13 @@ __global__ void nodes_arm_kernel(unsigned *counter, unsigned tag) {
 // Host side
 // ---------------------------------------------------------------------------
 NodesConfig nodes_config(const mdi_opts *opts) {
-  NodesConfig c{16, 256, 0, MDI_PREC_FP64};
+  NodesConfig c{16, 256, 0, MDI_PREC_FP64, 1};
   if (opts) {
     if (opts->nodes) c.P = opts->nodes;
     if (opts->block) c.block = opts->block;
     c.ctas_per_sm = opts->ctas_per_sm;
     c.precision = opts->precision;
+    c.stage = opts->table_in_l1 ? 0 : 1;
   }
   return c;
 }
@@ -426,11 +531,11 @@ static mdi_status launch_nodes(const mdi_batch_desc *descs, const int32_t *order
                                void *ws, cudaStream_t stream) {
   unsigned *counter = (unsigned *)ws;
   void *tables = (char *)ws + counter_bytes();
-  const size_t smem = nodes_smem_bytes(cfg.block, cfg.P);
+  const size_t smem = nodes_smem_bytes(cfg.block, cfg.P, cfg.stage != 0);
   static thread_local bool attr_set[4] = {false, false, false, false};
   if (!attr_set[PREC]) {
     cudaError_t e = cudaFuncSetAttribute(nodes_batched_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)nodes_smem_bytes(kNodesMaxBlock, 2));
+                                         (int)nodes_smem_bytes(kNodesMaxBlock, 2, true));
     if (e != cudaSuccess) {
       set_cuda_error(e);
       return MDI_ECUDA;
@@ -439,9 +544,9 @@ static mdi_status launch_nodes(const mdi_batch_desc *descs, const int32_t *order
   }
   int per_sm = cfg.ctas_per_sm;
   if (per_sm == 0) {
-    // Resident CTAs per SM for this (block, P), queried once per process.
-    static int occ_cache[kNodesMaxBlock / 32 + 1][kNodesPMax / 2 + 1];
-    int &occ = occ_cache[cfg.block / 32][cfg.P / 2];
+    // Resident CTAs per SM for this (block, P, staging), queried once per process.
+    static int occ_cache[4][kNodesMaxBlock / 32 + 1][kNodesPMax / 2 + 1][2];
+    int &occ = occ_cache[PREC][cfg.block / 32][cfg.P / 2][cfg.stage ? 1 : 0];
     if (occ == 0) {
       int o = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, nodes_batched_kernel<PREC>, cfg.block, smem);
@@ -451,7 +556,7 @@ static mdi_status launch_nodes(const mdi_batch_desc *descs, const int32_t *order
   }
   const int grid = std::max(1, std::min(count, sm_count() * per_sm));
   nodes_batched_kernel<PREC><<<grid, cfg.block, smem, stream>>>(descs, order, count, single, pool, tables, cfg.P,
-                                                                 out, counter, nodes_tag(cfg));
+                                                                 cfg.stage, out, counter, nodes_tag(cfg));
   return check_launch();
 }
 

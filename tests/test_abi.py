@@ -81,7 +81,7 @@ def test_mdi_rejects_bad_arguments(lib):
     o = _ffi.MdiOpts()
     assert lib.mdi_lr_integrate(0, 0, 16, 16, fake, ctypes.byref(o), fake, fake, 1 << 20, _null()) == _ffi.MDI_EINVAL
     assert lib.mdi_lr_integrate(0, 4, 0, 16, fake, ctypes.byref(o), fake, fake, 1 << 20, _null()) == _ffi.MDI_EINVAL
-    o.reserved[0] = 1
+    o.reserved = 1
     assert lib.mdi_lr_integrate(0, 4, 16, 16, fake, ctypes.byref(o), fake, fake, 1 << 20, _null()) == _ffi.MDI_EINVAL
     o = _ffi.MdiOpts()
     o.state = _ffi.STATE["closed"]
