@@ -1,17 +1,21 @@
 """Benchmark of the MDI-LR hot path on GB300.
 
-Workload (one "step"): one batched MDI-LR call over 4096 synthetic integrals of
+Workload (one "step"): one batched MDI-LR launch over 4096 synthetic integrals of
 uneven size -- d ~ U{6..20}, N ~ U{8..32} points per transformed axis (a = n_last
 = N), product-peak and Gaussian integrands alternating, c_j ~ U(0.5, 2),
-w_j ~ U(0, 1), node state with P = 16, FP64.  Every level of every integral runs
-in one persistent kernel launch.
+w_j ~ U(0, 1), node state with P = 16.  Every level of every integral runs in one
+persistent kernel launch, autotuned (CTA size, table placement) and replayed from
+a CUDA graph.  The default arithmetic is the double-float mode (FP64-class, held to
+1e-12 of the FP64 oracle by the tests); --precision fp64 times the FP64 path.
 
 Printed (rank 0, one JSON line): integrals/s over the timed steps (device time,
 inputs resident in HBM, L2 flushed between steps), the same metric end to end
-through the C ABI from pinned host buffers, the roofline of the batched kernel,
-the CPU oracle's throughput on a bounded sample, the small-workload comparison of
-MDI-LR and the plain lattice kernel, and SM clocks sampled during the timed
-region.
+(pinned host inputs copied in and results copied out inside the timed region),
+the roofline of the batched kernel, the CPU oracle on a bounded sample, SM clocks
+sampled during the timed region, and (unless --no-extras) the other workloads:
+the FP64 mode of the same batch, the d = 4 comparison of MDI-LR with the plain
+lattice kernel including time to 1e-6, the precision modes on the oscillatory
+d = 50 integral, the adjoint on the d = 100 Gaussian, and the cost-vs-d sweep.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank sweeps its own batch (weak scaling, no collective on
@@ -21,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -38,8 +43,13 @@ BASELINE_METRIC = "time to 1e-6 rel err, MDI-LR vs plain lattice kernel; integra
 COUNT = 4096
 P_NODES = 16
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
-# FP64 peak derived from unit counts and clocks: 152 SMs x 2 DFMA/clk (4 flop) x 2.07 GHz.
-FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+# Peaks derived from unit counts and the maximum SM clock (2.07 GHz, 152 SMs):
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12    # 2 DFMA lanes per SM per clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 128 FFMA lanes per SM per clock
+
+# Float operations (an FMA counts 2) of the double-float primitives, by construction.
+DF_FLOPS = {"u": 28, "dot_term": 15, "dot_value": 6, "acc": 15,
+            "phi": {"gauss": 122, "peak": 83, "exp": 93, "osc": 0}}
 
 
 def parse():
@@ -49,9 +59,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--count", type=int, default=COUNT)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_eval_fp64", "fp32_eval_df32", "df64"])
+    ap.add_argument("--precision", default="df64", choices=["df64", "fp64", "fp32_eval_fp64", "fp32_eval_df32"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="budget of the CPU oracle sample")
-    ap.add_argument("--no-extras", action="store_true", help="skip the small-workload comparison")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other workloads")
+    ap.add_argument("--no-tune", action="store_true", help="default launch shape, no autotuning")
     return ap.parse_args()
 
 
@@ -62,18 +73,28 @@ def workload_config(count, precision):
             "state": "nodes", "l2": "flushed between timed steps (256 MiB write)", "seed": "rank"}
 
 
-def algorithmic_flops(b, P=P_NODES):
-    """FP64 operations the sweep formula itself needs, counting exp and division as
-    one each: per cluster point of level k >= 2: P multiply-adds of the
-    interpolation (2P), u = (q + xi)/a (2), phi (4), product and sum (2); level 1:
-    no interpolation; last level per point: P weights (2P: subtract, divide), the
-    weighted sums (4P), normalisation (2), phi (4), product and sum (2)."""
-    d = b.d.astype(np.float64)
-    a = b.a.astype(np.float64)
-    nl = b.n_last.astype(np.float64)
-    pts_interp = np.maximum(d - 2, 0) * a * P
-    pts_first = np.where(d >= 2, a * P, 0)
-    return float((pts_interp * (2 * P + 8) + pts_first * 8 + nl * (6 * P + 8)).sum())
+def fp64_flops(b, P=P_NODES):
+    """FP64 operations the sweep formula needs (exp and division count one): per
+    cluster point of level k >= 2: interpolation 2P, u 2, phi 4, product and sum 2;
+    level 1 without interpolation; last level per point: 2P (tabulated basis) + 8."""
+    d, a, nl = (x.astype(np.float64) for x in (b.d, b.a, b.n_last))
+    interp = np.maximum(d - 2, 0) * a * P
+    first = np.where(d >= 2, a * P, 0)
+    return float((interp * (2 * P + 8) + first * 8 + nl * (2 * P + 8)).sum())
+
+
+def df_flops(b, P=P_NODES):
+    """Float operations of the double-float formulation (FMA = 2), by construction:
+    per cluster point of level k >= 2: coordinate, phi, P Dot2 terms, their value
+    and the accumulation; level 1 without interpolation; last axis likewise."""
+    total = 0.0
+    interp = P * DF_FLOPS["dot_term"] + DF_FLOPS["dot_value"]
+    for i, fam in enumerate(b.families):
+        d, a, nl = int(b.d[i]), int(b.a[i]), int(b.n_last[i])
+        phi = DF_FLOPS["phi"][fam]
+        pt = DF_FLOPS["u"] + phi + DF_FLOPS["acc"]
+        total += max(d - 2, 0) * a * P * (pt + interp) + (a * P * pt if d >= 2 else 0) + nl * (pt + interp)
+    return total
 
 
 class ClockSampler:
@@ -91,7 +112,7 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -99,7 +120,7 @@ class ClockSampler:
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
+        time.sleep(0.3)
         self.proc.terminate()
         self.proc.wait()
         rows = []
@@ -124,24 +145,22 @@ class ClockSampler:
 
 def cpu_oracle_sample(b, budget_s, P=P_NODES, limit=None):
     """Times the FP64 CPU oracle (node state) on consecutive integrals of the batch
-    until `budget_s` seconds of work are done; returns (integrals/s, how many)."""
+    until `budget_s` seconds (or `limit` integrals) are done."""
     from oracle import oracle as o
     o.build()
     t0 = time.perf_counter()
     done = 0
-    i = 0
     while True:
-        it = b.integral(i % len(b))
+        it = b.integral(done % len(b))
         o.mdi_nodes(it.family, it.d, it.a, it.n_last, P, it.c, it.w)
         done += 1
-        i += 1
         el = time.perf_counter() - t0
         if (limit is None and el >= budget_s) or (limit is not None and done >= limit):
             return done / el, done, el
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the CPU oracle, as it stands, on the host cores."""
+    """Reference arm: the CPU oracle, as it stands, on one host core."""
     if rank != 0:
         return
     from paper_2404_08867_gb300 import inputs
@@ -167,51 +186,108 @@ def run_reference(args, rank, world):
     print(json.dumps(line))
 
 
-def small_workload_extras(torch, mdi, o, inputs):
-    """d = 4, N = 16, f = exp(sum x_j / j): MDI-LR and the plain lattice kernel on the
-    GPU, their relative errors against the closed form, and the time each needs to
-    reach 1e-6 (MDI-LR: closed state with a growing a; plain kernel: Korobov a = 12345,
-    n = 2^m), measured here with CUDA events."""
+def event_ms(torch, fn, reps=5):
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return r, statistics.median(ts)
+
+
+def extra_small_workload(torch, mdi, o, inputs):
+    """d = 4, N = 16, f = exp(sum x_j/j): MDI-LR and the plain lattice kernel on the
+    GPU, and the time each needs to reach 1e-6 relative error against the closed
+    form (MDI-LR: closed state, a doubling; plain kernel: a = 12345, n = 2^m)."""
     w = inputs.small_exp()
     c = torch.as_tensor(w.params).cuda()
     exact = o.closed_form("exp", 4, w.c, w.w)
-
-    def timed(fn, reps=20):
-        fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            r = fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return r.item(), e0.elapsed_time(e1) / reps
-
     n = 16**4
     z = o.korobov_z(4, inputs.SMALL_SLR_A, n).astype(np.int64)
-    slr_val, slr_ms = timed(lambda: mdi.lattice_rule_integrate("exp", c, n, z))
-    mdi_val, mdi_ms = timed(lambda: mdi.mdi_lr_integrate("exp", c, 4, 16, 16, state="exact"))
-    res = {"workload": "d=4, N=16, f=exp(sum x_j/j)", "slr_a12345_n65536": {"rel_err": abs(slr_val - exact) / exact,
-                                                                         "ms": slr_ms},
-           "mdi_lr_exact_N16": {"rel_err": abs(mdi_val - exact) / exact, "ms": mdi_ms}}
-    # time to 1e-6 relative error
+    slr, slr_ms = event_ms(torch, lambda: mdi.lattice_rule_integrate("exp", c, n, z))
+    mv, m_ms = event_ms(torch, lambda: mdi.mdi_lr_integrate("exp", c, 4, 16, 16, state="exact"))
+    res = {"workload": "d=4, N=16, f=exp(sum x_j/j)",
+           "slr_a12345_n65536": {"rel_err": abs(slr.item() - exact) / exact, "ms": slr_ms},
+           "mdi_lr_exact_N16": {"rel_err": abs(mv.item() - exact) / exact, "ms": m_ms}}
     a = 16
     while True:
-        v, ms = timed(lambda: mdi.mdi_lr_integrate("exp", c, 4, a, a, state="closed"))
-        if abs(v - exact) / exact <= 1e-6 or a > 1 << 24:
-            res["mdi_lr_to_1e-6"] = {"a": a, "rel_err": abs(v - exact) / exact, "ms": ms}
+        v, ms = event_ms(torch, lambda: mdi.mdi_lr_integrate("exp", c, 4, a, a, state="closed"))
+        if abs(v.item() - exact) / exact <= 1e-6 or a > 1 << 24:
+            res["mdi_lr_to_1e-6"] = {"a": a, "rel_err": abs(v.item() - exact) / exact, "ms": ms}
             break
         a *= 2
-    reached = None
+    reached, last = None, None
     for m in range(16, 31):
-        n = 1 << m
-        z = o.korobov_z(4, inputs.SMALL_SLR_A, n).astype(np.int64)
-        v, ms = timed(lambda: mdi.lattice_rule_integrate("exp", c, n, z), reps=3)
-        if abs(v - exact) / exact <= 1e-6:
-            reached = {"n": n, "a": inputs.SMALL_SLR_A, "rel_err": abs(v - exact) / exact, "ms": ms}
+        nn = 1 << m
+        zz = o.korobov_z(4, inputs.SMALL_SLR_A, nn).astype(np.int64)
+        v, ms = event_ms(torch, lambda: mdi.lattice_rule_integrate("exp", c, nn, zz), reps=2)
+        last = {"n": nn, "a": inputs.SMALL_SLR_A, "rel_err": abs(v.item() - exact) / exact, "ms": ms}
+        if last["rel_err"] <= 1e-6:
+            reached = last
             break
-        last = {"n": n, "rel_err": abs(v - exact) / exact, "ms": ms}
     res["slr_to_1e-6"] = reached if reached else {"reached": False, "largest_tried": last}
+    return res
+
+
+def extra_precision(torch, mdi, o, inputs):
+    """d = 50, N = 32, f = cos(2 pi u + sum a_j x_j): every precision mode, closed and
+    node state, error against the FP64 oracle and against the exact integral."""
+    w = inputs.oscillatory(50, 32, seed=0)
+    p = torch.as_tensor(w.params).cuda()
+    exact = o.closed_form("osc", 50, w.c, w.w)
+    res = {"workload": "d=50, N=32, cos(2 pi u + sum a_j x_j)", "exact": exact}
+    for state, ref in (("closed", o.mdi_closed("osc", 50, 32, 32, w.c, w.w)),
+                       ("nodes", o.mdi_nodes("osc", 50, 32, 32, 16, w.c, w.w))):
+        for prec in ("fp64", "fp32_eval_fp64", "fp32_eval_df32", "df64"):
+            if state == "closed" and prec == "df64":
+                continue
+            v, ms = event_ms(torch, lambda: mdi.mdi_lr_integrate("osc", p, 50, 32, state=state, precision=prec))
+            res[f"{state}/{prec}"] = {"abs_err_vs_oracle": abs(v.item() - ref), "abs_err_vs_exact": abs(v.item() - exact),
+                                      "ms": ms}
+    return res
+
+
+def extra_differentiation(torch, mdi, o, inputs):
+    """d = 100, N = 16 Gaussian: value and 200-parameter gradient by the adjoint
+    sweep (checkpoints every 10 levels) against the oracle and the exact gradient."""
+    w = inputs.gaussian(100, 16, seed=0)
+    p = torch.as_tensor(w.params).cuda()
+    (val, g), ms = event_ms(torch, lambda: mdi.mdi_lr_grad("gauss", p, 100, 16, 16, state="nodes", checkpoint=10))
+    _, fwd_ms = event_ms(torch, lambda: mdi.mdi_lr_integrate("gauss", p, 100, 16, state="nodes"))
+    g = g.cpu().numpy()
+    ref = o.mdi_nodes_grad("gauss", 100, 16, 16, 16, w.c, w.w)
+    exact = o.closed_form_grad("gauss", 100, w.c, w.w)
+    return {"workload": "d=100, N=16 Gaussian, 200 parameters, checkpoint 10", "adjoint_ms": ms, "forward_ms": fwd_ms,
+            "grad_err_vs_oracle_normwise": float(np.max(np.abs(g - ref)) / np.max(np.abs(ref))),
+            "grad_diff_vs_exact_normwise": float(np.max(np.abs(g - exact)) / np.max(np.abs(exact))),
+            "value_rel_err_vs_exact": abs(val.item() - o.closed_form("gauss", 100, w.c, w.w)) /
+            o.closed_form("gauss", 100, w.c, w.w)}
+
+
+def extra_scale(torch, mdi, o, inputs):
+    """d in {100, 250, 500, 1000}, N = 16, f = exp(sum x_j/j^2): forward and adjoint
+    in the closed and node states; fitted exponent of time ~ d^beta."""
+    res = {"workload": "N=16, f=exp(sum x_j/j^2)"}
+    for state in ("closed", "nodes"):
+        ds, fw, ad = [], [], []
+        for d in (100, 250, 500, 1000):
+            w = inputs.scale_exp(d, 16)
+            p = torch.as_tensor(w.params).cuda()
+            v, f_ms = event_ms(torch, lambda: mdi.mdi_lr_integrate("exp", p, d, 16, state=state))
+            _, a_ms = event_ms(torch, lambda: mdi.mdi_lr_grad("exp", p, d, 16, 16, state=state))
+            ds.append(d)
+            fw.append(f_ms)
+            ad.append(a_ms)
+            if d == 1000:
+                exact = o.closed_form("exp", d, w.c, w.w)
+                res[f"{state}/d1000_rel_err_vs_exact"] = abs(v.item() - exact) / exact
+        beta = lambda t: float(np.polyfit(np.log(ds), np.log(t), 1)[0])
+        res[state] = {"d": ds, "forward_ms": fw, "adjoint_ms": ad, "forward_beta": beta(fw), "adjoint_beta": beta(ad)}
     return res
 
 
@@ -228,6 +304,7 @@ def main():
     import torch.distributed as dist
     import paper_2404_08867_gb300 as mdi
     from paper_2404_08867_gb300 import inputs
+    from paper_2404_08867_gb300.tuning import BatchedMDILR
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -237,30 +314,29 @@ def main():
         if world > 1:
             dist.barrier()
 
-    b = inputs.batch(count=args.count, seed=rank)
-    descs = mdi.make_batch_descs(b.families, b.d, b.a, b.n_last, b.offsets)
-    order = mdi.mdi_batch_plan(descs, nodes=P_NODES)
-    opts = dict(nodes=P_NODES, precision=args.precision)
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item()
 
-    # Device-resident inputs.
-    d_descs = torch.from_numpy(descs.view(np.uint8).copy()).cuda()
-    d_order = torch.from_numpy(order).cuda()
-    d_pool = torch.from_numpy(b.pool.copy()).cuda()
-    d_out = torch.empty(len(b), dtype=torch.float64, device="cuda")
-    ws = mdi.mdi_lr_batched_prepare(device="cuda", **opts)
+    b = inputs.batch(count=args.count, seed=rank)
+    plan = BatchedMDILR(b.families, b.d, b.a, b.n_last, b.offsets, b.pool, precision=args.precision, nodes=P_NODES)
+    tuning = {"block": 256, "table_in_l1": 0} if args.no_tune else plan.tune()
+    if args.no_tune:
+        plan.opts.update(block=256, table_in_l1=0)
+    plan.capture()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step():
-        mdi.mdi_lr_integrate_batched(d_descs, d_pool, len(b), order=d_order, out=d_out, workspace=ws, **opts)
-
     for _ in range(max(3, args.warmup)):
-        step()
+        plan.run()
     torch.cuda.synchronize()
 
     sampler = ClockSampler(local)
     sampler.start()
-    time.sleep(0.3)
+    time.sleep(0.4)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier()
@@ -269,34 +345,29 @@ def main():
     for k in range(args.steps):
         flush.zero_()  # evict L2 between timed steps (outside the events)
         starts[k].record(stream)
-        step()
+        plan.run()
         ends[k].record(stream)
     torch.cuda.synchronize()
     barrier()
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
+    total_ms = max_over_ranks(sum(step_ms))
     value = len(b) * world * args.steps / (total_ms / 1e3)
+    device_out = plan.out.clone()
 
-    # End to end through the C ABI from pinned host buffers: H2D inputs, kernel, D2H results.
-    h_descs = torch.from_numpy(descs.view(np.uint8).copy()).pin_memory()
-    h_order = torch.from_numpy(order.copy()).pin_memory()
-    h_pool = torch.from_numpy(b.pool.copy()).pin_memory()
+    # End to end: pinned host inputs -> device, the launch, results -> pinned host.
+    h_descs = plan.descs.cpu().pin_memory()
+    h_order = plan.order.cpu().pin_memory()
+    h_pool = plan.pool.cpu().pin_memory()
     h_out = torch.empty(len(b), dtype=torch.float64).pin_memory()
-    e_descs, e_order, e_pool = torch.empty_like(d_descs), torch.empty_like(d_order), torch.empty_like(d_pool)
-    e_out = torch.empty_like(d_out)
 
     def e2e_step():
-        e_descs.copy_(h_descs, non_blocking=True)
-        e_order.copy_(h_order, non_blocking=True)
-        e_pool.copy_(h_pool, non_blocking=True)
-        mdi.mdi_lr_integrate_batched(e_descs, e_pool, len(b), order=e_order, out=e_out, workspace=ws, **opts)
-        h_out.copy_(e_out, non_blocking=True)
+        plan.descs.copy_(h_descs, non_blocking=True)
+        plan.order.copy_(h_order, non_blocking=True)
+        plan.pool.copy_(h_pool, non_blocking=True)
+        plan.run()
+        h_out.copy_(plan.out, non_blocking=True)
 
     for _ in range(3):
         e2e_step()
@@ -311,34 +382,57 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         e_ms.append(e0.elapsed_time(e1))
-    e2e_total = sum(e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = t.item()
+    e2e_total = max_over_ranks(sum(e_ms))
     e2e_value = len(b) * world * args.steps / (e2e_total / 1e3)
-    assert np.allclose(h_out.numpy(), d_out.cpu().numpy(), rtol=0, atol=0), "e2e result differs from device run"
+    assert torch.equal(h_out, device_out.cpu()), "end-to-end result differs from the device-timed run"
 
     if rank == 0:
-        flops = algorithmic_flops(b)
         kernel_ms = statistics.mean(step_ms)
-        achieved = flops / (kernel_ms / 1e3) / 1e12
+        if args.precision in ("df64", "fp32_eval_df32"):
+            flops = df_flops(b)
+            achieved = flops / (kernel_ms / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "nodes_batched_kernel",
+                    "pipe": "FP32 (double-float arithmetic)",
+                    "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2 x 2.07 GHz",
+                    "flops_per_launch": flops, "kernel_ms": kernel_ms,
+                    "fp64_equivalent_tflops": fp64_flops(b) / (kernel_ms / 1e3) / 1e12,
+                    "fp64_peak_tflops": FP64_PEAK_TFLOPS}
+        else:
+            flops = fp64_flops(b)
+            achieved = flops / (kernel_ms / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "nodes_batched_kernel",
+                    "pipe": "FP64", "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
+                    "flops_per_launch": flops, "kernel_ms": kernel_ms}
+        dtype = {"df64": "f32x2 (double-float, FP64-class)", "fp64": "f64", "fp32_eval_fp64": "f32 eval + f64",
+                 "fp32_eval_df32": "f32 eval + f32x2"}[args.precision]
         line = {"metric": METRIC, "value": value, "unit": "integrals/s", "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else args.precision,
-                "data": "synthetic", "config": workload_config(len(b), args.precision),
-                "baseline_metric": BASELINE_METRIC, "gpu_launches": args.steps,
+                "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+                "config": workload_config(len(b), args.precision), "baseline_metric": BASELINE_METRIC,
+                "gpu_launches": args.steps, "launch": {"cuda_graph": True, **{k: v for k, v in tuning.items()
+                                                                              if k != "candidates"}},
                 "e2e": {"value": e2e_value, "unit": "integrals/s",
                         "h2d_bytes_per_step": int(h_descs.numel() + 4 * h_order.numel() + 8 * h_pool.numel()),
                         "d2h_bytes_per_step": int(8 * h_out.numel())},
-                "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                             "kernel": "nodes_batched_kernel", "peak_source": "derived: 152 SMs x 4 FP64 flop/clk "
-                             "x 2.07 GHz", "flops_per_launch": flops, "kernel_ms": kernel_ms},
-                "clocks": clocks, "wall_s_timed_region": wall}
+                "roofline": roof, "clocks": clocks, "wall_s_timed_region": wall}
         if not args.no_extras:
             from oracle import oracle as o
-            line["small_workload"] = small_workload_extras(torch, mdi, o, inputs)
+            if args.precision != "fp64":
+                fp = BatchedMDILR(b.families, b.d, b.a, b.n_last, b.offsets, b.pool, precision="fp64", nodes=P_NODES)
+                ft = fp.tune()
+                fp.capture()
+                _, fms = event_ms(torch, fp.run, reps=10)
+                fl = fp64_flops(b) / (fms / 1e3) / 1e12
+                line["fp64_mode"] = {"ms_per_step": fms, "integrals_per_s": len(b) / (fms / 1e3),
+                                     "fp64_tflops": fl, "frac_of_fp64_peak": fl / FP64_PEAK_TFLOPS,
+                                     "block": ft["block"], "table_in_l1": ft["table_in_l1"],
+                                     "max_abs_diff_vs_headline": float((fp.out - device_out).abs().max())}
+            line["small_workload"] = extra_small_workload(torch, mdi, o, inputs)
+            line["precision_workload"] = extra_precision(torch, mdi, o, inputs)
+            line["differentiation_workload"] = extra_differentiation(torch, mdi, o, inputs)
+            line["scale_workload"] = extra_scale(torch, mdi, o, inputs)
         rate, n_done, secs = cpu_oracle_sample(b, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "integrals/s", "cores": 1, "kind": "oracle",
                                 "sample": f"first {n_done} integrals of the batch, {secs:.1f} s single-threaded"}

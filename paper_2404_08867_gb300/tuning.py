@@ -1,0 +1,106 @@
+"""Autotuned, CUDA-graph-captured batched MDI-LR launches.
+
+``BatchedMDILR`` owns the device copies of a batch (descriptors, processing
+order from the library's longest-first planner, parameter pool), a prepared
+workspace, and the launch shape.  ``tune()`` times the candidate shapes -- CTA
+size and whether each integral's basis table is staged in shared memory or read
+through L1 -- on the batch itself with CUDA events and keeps the fastest (cached
+per batch signature for the process).  ``capture()`` records the one-kernel
+launch into a CUDA graph; ``run()`` replays it.  Nothing here computes: every
+launch goes through the C ABI.
+"""
+from __future__ import annotations
+
+import statistics
+from typing import Dict, Optional, Tuple
+
+import numpy as np
+import torch
+
+from . import make_batch_descs, mdi_batch_plan, mdi_lr_batched_prepare, mdi_lr_integrate_batched
+
+CANDIDATE_BLOCKS = (64, 128, 256)
+CANDIDATE_TABLE_IN_L1 = (1, 0)
+_cache: Dict[Tuple, Dict] = {}
+
+
+class BatchedMDILR:
+    def __init__(self, families, d, a, n_last, offsets, pool, precision: str = "df64", nodes: int = 16,
+                 device="cuda"):
+        self.count = len(d)
+        self.precision, self.nodes = precision, nodes
+        descs = make_batch_descs(families, d, a, n_last, offsets)
+        self.descs_host = descs
+        order = mdi_batch_plan(descs, nodes=nodes)
+        self.descs = torch.from_numpy(descs.view(np.uint8).copy()).to(device)
+        self.order = torch.from_numpy(order).to(device)
+        pool_t = pool if isinstance(pool, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(pool))
+        self.pool = pool_t.to(device=device, dtype=torch.float64).contiguous()
+        self.out = torch.empty(self.count, dtype=torch.float64, device=device)
+        self.workspace = mdi_lr_batched_prepare(device=device, nodes=nodes, precision=precision)
+        self.opts = {"nodes": nodes, "precision": precision}
+        self.graph: Optional[torch.cuda.CUDAGraph] = None
+        self.tuning: Dict = {}
+
+    def signature(self) -> Tuple:
+        d = self.descs_host["d"].astype(np.int64)
+        a = self.descs_host["a"].astype(np.int64)
+        return (self.precision, self.nodes, self.count, int(d.sum()), int((d * a).sum()), int(a.max()),
+                int(d.max()), torch.cuda.get_device_name())
+
+    def launch(self, **shape) -> torch.Tensor:
+        return mdi_lr_integrate_batched(self.descs, self.pool, self.count, order=self.order, out=self.out,
+                                        workspace=self.workspace, **self.opts, **shape)
+
+    def _time(self, reps: int = 5, **shape) -> float:
+        for _ in range(2):
+            self.launch(**shape)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            self.launch(**shape)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    def tune(self, reps: int = 5) -> Dict:
+        """Times every candidate shape on this batch and keeps the fastest."""
+        key = self.signature()
+        if key not in _cache:
+            results = {}
+            for block in CANDIDATE_BLOCKS:
+                if block % self.nodes:
+                    continue
+                for l1 in CANDIDATE_TABLE_IN_L1:
+                    results[(block, l1)] = self._time(reps, block=block, table_in_l1=l1)
+            (block, l1), best = min(results.items(), key=lambda kv: kv[1])
+            _cache[key] = {"block": block, "table_in_l1": l1, "ms": best,
+                           "candidates": {f"block={b},table_in_l1={t}": ms for (b, t), ms in results.items()}}
+        self.tuning = _cache[key]
+        self.opts.update(block=self.tuning["block"], table_in_l1=self.tuning["table_in_l1"])
+        self.graph = None
+        return self.tuning
+
+    def capture(self) -> torch.cuda.CUDAGraph:
+        """Records one launch (with the current shape) into a CUDA graph."""
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.launch()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.launch()
+        self.graph = g
+        return g
+
+    def run(self) -> torch.Tensor:
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.launch()
+        return self.out
