@@ -187,13 +187,25 @@ def run_reference(args, rank, world):
 
 
 def event_ms(torch, fn, reps=5):
+    """Device time of fn: its launches are captured once into a CUDA graph and the
+    graph is replayed between CUDA events (median), so host-side marshalling of
+    the Python binding is not counted for microsecond-scale calls."""
     fn()
     torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fn()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        r = fn()
     ts = []
     for _ in range(reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        r = fn()
+        g.replay()
         e1.record()
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
@@ -230,7 +242,31 @@ def extra_small_workload(torch, mdi, o, inputs):
         if last["rel_err"] <= 1e-6:
             reached = last
             break
-    res["slr_to_1e-6"] = reached if reached else {"reached": False, "largest_tried": last}
+    res["slr_a12345_to_1e-6"] = reached if reached else {"reached": False, "largest_tried": last}
+    # The plain kernel with a searched generating vector: for n = 2^m, 64 seeded odd
+    # Korobov parameters (and 12345) are tried on the GPU (search untimed, reported
+    # separately); the first n whose best parameter reaches 1e-6 is timed.
+    rng = np.random.default_rng(2024)
+    found, search_s = None, 0.0
+    for m in range(16, 27):
+        nn = 1 << m
+        cands = [inputs.SMALL_SLR_A % nn] + [int(x) | 1 for x in rng.integers(3, nn, 64)]
+        t0 = time.perf_counter()
+        errs = []
+        for a_c in cands:
+            zz = o.korobov_z(4, a_c, nn).astype(np.int64)
+            errs.append(abs(mdi.lattice_rule_integrate("exp", c, nn, zz).item() - exact) / exact)
+        search_s += time.perf_counter() - t0
+        best = int(np.argmin(errs))
+        if errs[best] <= 1e-6:
+            zz = o.korobov_z(4, cands[best], nn).astype(np.int64)
+            _, ms = event_ms(torch, lambda: mdi.lattice_rule_integrate("exp", c, nn, zz), reps=5)
+            found = {"n": nn, "a": cands[best], "rel_err": errs[best], "ms": ms}
+            break
+    res["slr_searched_a_to_1e-6"] = found if found else {"reached": False, "n_max": 1 << 26}
+    res["slr_a_search_s_untimed"] = search_s
+    if found:
+        res["time_to_1e-6_ratio_slr_over_mdi"] = found["ms"] / res["mdi_lr_to_1e-6"]["ms"]
     return res
 
 
@@ -423,7 +459,16 @@ def main():
                 fp = BatchedMDILR(b.families, b.d, b.a, b.n_last, b.offsets, b.pool, precision="fp64", nodes=P_NODES)
                 ft = fp.tune()
                 fp.capture()
-                _, fms = event_ms(torch, fp.run, reps=10)
+                fms_list = []
+                for _ in range(10):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    fp.run()
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    fms_list.append(e0.elapsed_time(e1))
+                fms = statistics.median(fms_list)
                 fl = fp64_flops(b) / (fms / 1e3) / 1e12
                 line["fp64_mode"] = {"ms_per_step": fms, "integrals_per_s": len(b) / (fms / 1e3),
                                      "fp64_tflops": fl, "frac_of_fp64_peak": fl / FP64_PEAK_TFLOPS,

@@ -117,7 +117,8 @@ mdi_status mdi_lr_workspace_size(int32_t family, int32_t d, int64_t a, int64_t n
     }
     case MDI_STATE_CLOSED:
       if (family != MDI_FAM_EXP && family != MDI_FAM_OSC) return MDI_EUNSUPPORTED;
-      *bytes = closed_workspace_bytes(d);
+      *bytes = closed_workspace_bytes(d, a, n_last);
+      if (*bytes == 0) return MDI_EINVAL;
       return MDI_OK;
     default: {
       const NodesConfig cfg = nodes_config(opts);
@@ -154,7 +155,8 @@ mdi_status mdi_lr_grad_workspace_size(int32_t family, int32_t d, int64_t a, int6
     case MDI_STATE_EXACT: return MDI_EUNSUPPORTED;
     case MDI_STATE_CLOSED:
       if (family != MDI_FAM_EXP && family != MDI_FAM_OSC) return MDI_EUNSUPPORTED;
-      *bytes = closed_grad_workspace_bytes(d);
+      *bytes = closed_grad_workspace_bytes(d, a, n_last);
+      if (*bytes == 0) return MDI_EINVAL;
       return MDI_OK;
     default:
       *bytes = levels_workspace_bytes(d, a, nodes_config(opts), opts ? opts->checkpoint : 0);

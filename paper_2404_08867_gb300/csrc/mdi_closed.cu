@@ -1,5 +1,6 @@
 // mdi_closed.cu -- MDI-LR with the closed level state (MDI_STATE_CLOSED) for the
-// exponential families EXP (phi_j = exp(c_j x)) and OSC (phi_j = exp(i c_j x)).
+// exponential families EXP (phi_j = exp(c_j x)) and OSC (phi_j = exp(i c_j x)),
+// and its adjoint.
 //
 // With phi_k(x) = exp(c~_k x) (c~ = c or i c) the level recursion of Algorithm 1,
 //     G_k(x) = (1/r_k) sum_{q<r_k} phi_k(u) G_{k-1}(u),   u = (q + x) / r_k,
@@ -9,13 +10,15 @@
 // and the rule is front * K_d (front = exp(2 pi i u) for OSC).  The cluster
 // evaluation of level k is the sum S_k over its r_k points.
 //
-// GB300 mapping.  beta is an affine recurrence (beta_k = beta_{k-1}/r_k + c_k/r_k;
+// GB300 mapping.  beta is an affine recurrence (beta_k = beta_{k-1}/a + c_k/a;
 // for OSC the same real recurrence gives the imaginary part), so instead of
-// walking the d levels one after the other on one SM, one CTA solves it with a
-// block-wide scan of affine maps; then the cluster sums of all levels run at
-// once across the whole GPU (one warp per level, lanes over q, shuffle
-// reduction), each CTA multiplies its levels' S_k in level order, and one CTA
-// multiplies the CTA partial products in order.  Three launches, independent of d.
+// walking the d levels one after the other on one SM:
+//   1. one CTA solves it with a block-wide scan of affine maps (gamma_k, all k);
+//   2. the cluster sums of all levels run at once across the GPU: every level's
+//      r_k points are cut into chunks of up to 1024, one warp per chunk;
+//   3. the chunk sums of each level are added in chunk order (S_k);
+//   4. one CTA multiplies the S_k in level order.
+// Launch count does not depend on d or on a.
 #include <algorithm>
 
 #include "mdi_common.cuh"
@@ -24,17 +27,16 @@
 namespace mdi {
 
 constexpr int kScanThreads = 1024;
-constexpr int kLevelThreads = 256;
-constexpr int kLevelWarps = kLevelThreads / kWarp;
+constexpr int kChunkThreads = 256;
+constexpr int64_t kChunkQ = 1024;  // cluster points per warp chunk
 
 // gamma_k (real: the exponent rate, or its imaginary part for OSC) for k = 1..d.
-__global__ void __launch_bounds__(kScanThreads) closed_scan_kernel(int d, double a, double n_last,
-                                                                   const double *__restrict__ params,
+__global__ void __launch_bounds__(kScanThreads) closed_scan_kernel(int d, double a, const double *__restrict__ params,
                                                                    double *__restrict__ gamma) {
   __shared__ double sA[kScanThreads], sB[kScanThreads];
   const int per = (d + blockDim.x - 1) / blockDim.x;
   const int lo = threadIdx.x * per, hi = min(d - 1, lo + per);  // maps for levels lo+1..hi (k < d)
-  // Composite of beta_k = beta_{k-1}/r + c_k/r over this thread's levels.
+  // Composite of beta_k = beta_{k-1}/a + c_k/a over this thread's levels.
   double A = 1.0, B = 0.0;
   const double inva = 1.0 / a;
   for (int k = lo; k < hi; ++k) {  // 0-based level k <-> paper's level k+1
@@ -53,7 +55,7 @@ __global__ void __launch_bounds__(kScanThreads) closed_scan_kernel(int d, double
     }
     __syncthreads();
     if ((int)threadIdx.x >= off) {
-      double cA = sA[threadIdx.x], cB = sB[threadIdx.x];
+      const double cA = sA[threadIdx.x], cB = sB[threadIdx.x];
       sA[threadIdx.x] = cA * pA;
       sB[threadIdx.x] = cA * pB + cB;
     }
@@ -61,120 +63,210 @@ __global__ void __launch_bounds__(kScanThreads) closed_scan_kernel(int d, double
   }
   double beta = threadIdx.x == 0 ? 0.0 : sB[threadIdx.x - 1];  // beta at the start of the chunk
   for (int k = lo; k < min(d, lo + per); ++k) {
-    double g = beta + params[k];
+    const double g = beta + params[k];
     gamma[k] = g;
     beta = g * inva;
   }
-  (void)n_last;
 }
 
-template <int FAM, int PREC>
-__global__ void __launch_bounds__(kLevelThreads) closed_level_kernel(int d, int64_t a, int64_t n_last,
+// Chunks: levels k < d-1 have a points, cut into cpl chunks; the last level has
+// n_last points in cpl_last chunks.
+struct Chunks {
+  int cpl, cpl_last, total;
+};
+static Chunks make_chunks(int d, int64_t a, int64_t n_last) {
+  Chunks c;
+  c.cpl = (int)((a + kChunkQ - 1) / kChunkQ);
+  c.cpl_last = (int)((n_last + kChunkQ - 1) / kChunkQ);
+  c.total = (d - 1) * c.cpl + c.cpl_last;
+  return c;
+}
+__device__ __forceinline__ int chunk_base(int k, int d, int cpl) { return k < d - 1 ? k * cpl : (d - 1) * cpl; }
+
+// Sum of exp(iota gamma_k q / r_k) (and of (q/r_k) times it, WITH_T) over one chunk
+// of one level's cluster, per warp.
+template <int FAM, int PREC, bool WITH_T>
+__global__ void __launch_bounds__(kChunkThreads) closed_chunk_kernel(int d, int64_t a, int64_t n_last, Chunks ch,
                                                                      const double *__restrict__ gamma,
-                                                                     typename FamTraits<FAM>::V *__restrict__ partial) {
-  using V = typename FamTraits<FAM>::V;
-  __shared__ V sS[kLevelWarps * 8];
-  const int per_block = (d + gridDim.x - 1) / gridDim.x;
-  const int k_lo = blockIdx.x * per_block, k_hi = min(d, k_lo + per_block);
-  const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x / kWarp;
-  V prod = VOps<V>::one();
-  // Levels of this block in chunks of kLevelWarps*8, product kept in level order.
-  for (int base = k_lo; base < k_hi; base += kLevelWarps * 8) {
-    const int cnt = min(kLevelWarps * 8, k_hi - base);
-    for (int s = warp; s < cnt; s += kLevelWarps) {
-      const int k = base + s;
-      const int64_t r = (k + 1 < d) ? a : n_last;
-      const double g = gamma[k], invr = 1.0 / (double)r;
-      V acc = VOps<V>::zero();
-      df32 acc_hi{0.f, 0.f}, acc_im{0.f, 0.f};
-      for (int64_t q = lane; q < r; q += kWarp) {
-        const double arg = g * (double)q * invr;
-        if constexpr (FAM == MDI_FAM_OSC) {
+                                                                     double2 *__restrict__ partS,
+                                                                     double2 *__restrict__ partT) {
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
+  const int nwarps = gridDim.x * blockDim.x / kWarp;
+  for (int c = warp_global; c < ch.total; c += nwarps) {
+    int k, j;
+    if (c < (d - 1) * ch.cpl) {
+      k = c / ch.cpl;
+      j = c % ch.cpl;
+    } else {
+      k = d - 1;
+      j = c - (d - 1) * ch.cpl;
+    }
+    const int64_t r = (k + 1 < d) ? a : n_last;
+    const int64_t q0 = (int64_t)j * kChunkQ, q1 = min(r, q0 + kChunkQ);
+    const double g = gamma[k], invr = 1.0 / (double)r;
+    double2 s = make_double2(0.0, 0.0), t = make_double2(0.0, 0.0);
+    df32 sr{0.f, 0.f}, si{0.f, 0.f};
+    for (int64_t q = q0 + lane; q < q1; q += kWarp) {
+      const double x = (double)q * invr;
+      const double arg = g * x;
+      double2 e;
+      if constexpr (FAM == MDI_FAM_OSC) {
+        if constexpr (PREC == MDI_PREC_FP64) {
           double sn, cs;
-          if constexpr (PREC == MDI_PREC_FP64) {
-            sincos(arg, &sn, &cs);
-          } else {
-            float fs, fc;
-            sincosf((float)arg, &fs, &fc);
-            sn = fs;
-            cs = fc;
-          }
-          if constexpr (PREC == MDI_PREC_FP32_EVAL_DF32) {
-            acc_hi = df_add(acc_hi, df32{(float)cs, 0.f});
-            acc_im = df_add(acc_im, df32{(float)sn, 0.f});
-          } else {
-            acc = VOps<V>::add(acc, make_double2(cs, sn));
-          }
+          sincos(arg, &sn, &cs);
+          e = make_double2(cs, sn);
         } else {
-          if constexpr (PREC == MDI_PREC_FP64) {
-            acc = VOps<V>::add(acc, exp(arg));
-          } else if constexpr (PREC == MDI_PREC_FP32_EVAL_FP64) {
-            acc = VOps<V>::add(acc, (double)expf((float)arg));
-          } else {
-            acc_hi = df_add(acc_hi, df32{expf((float)arg), 0.f});
-          }
+          float fs, fc;
+          sincosf((float)arg, &fs, &fc);
+          e = make_double2((double)fc, (double)fs);
         }
+      } else {
+        e = make_double2(PREC == MDI_PREC_FP64 ? exp(arg) : (double)expf((float)arg), 0.0);
       }
       if constexpr (PREC == MDI_PREC_FP32_EVAL_DF32) {
-#pragma unroll
-        for (int off = kWarp / 2; off > 0; off >>= 1) {
-          acc_hi = df_add(acc_hi, df_shfl_down(acc_hi, off));
-          if constexpr (FAM == MDI_FAM_OSC) acc_im = df_add(acc_im, df_shfl_down(acc_im, off));
-        }
-        if constexpr (FAM == MDI_FAM_OSC) acc = make_double2(df_to_double(acc_hi), df_to_double(acc_im));
-        else acc = df_to_double(acc_hi);
+        sr = df_add(sr, df32{(float)e.x, 0.f});
+        si = df_add(si, df32{(float)e.y, 0.f});
       } else {
-        acc = warp_sum(acc);
+        s = c_add(s, e);
       }
-      if (lane == 0) sS[s] = VOps<V>::scale(acc, invr);
+      if constexpr (WITH_T) t = c_add(t, c_scale(e, x));
     }
-    __syncthreads();
-    if (threadIdx.x == 0)
-      for (int s = 0; s < cnt; ++s) prod = VOps<V>::mul(prod, sS[s]);
-    __syncthreads();
+    if constexpr (PREC == MDI_PREC_FP32_EVAL_DF32) {
+#pragma unroll
+      for (int off = kWarp / 2; off > 0; off >>= 1) {
+        sr = df_add(sr, df_shfl_down(sr, off));
+        si = df_add(si, df_shfl_down(si, off));
+      }
+      s = make_double2(df_to_double(sr), df_to_double(si));
+    } else {
+      s = warp_sum(s);
+    }
+    if constexpr (WITH_T) t = warp_sum(t);
+    if (lane == 0) {
+      partS[c] = s;
+      if constexpr (WITH_T) partT[c] = t;
+    }
   }
-  if (threadIdx.x == 0) partial[blockIdx.x] = prod;
 }
 
+// S_k (and T_k) = (1/r_k) * (chunk sums of level k added in chunk order).
+template <bool WITH_T>
+__global__ void closed_reduce_kernel(int d, int64_t a, int64_t n_last, Chunks ch, const double2 *__restrict__ partS,
+                                     const double2 *__restrict__ partT, double2 *__restrict__ S,
+                                     double2 *__restrict__ T) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < d; k += gridDim.x * blockDim.x) {
+    const int n = k < d - 1 ? ch.cpl : ch.cpl_last, base = chunk_base(k, d, ch.cpl);
+    const double invr = 1.0 / (double)((k + 1 < d) ? a : n_last);
+    double2 s = make_double2(0.0, 0.0), t = make_double2(0.0, 0.0);
+    for (int j = 0; j < n; ++j) {
+      s = c_add(s, partS[base + j]);
+      if constexpr (WITH_T) t = c_add(t, partT[base + j]);
+    }
+    S[k] = c_scale(s, invr);
+    if constexpr (WITH_T) T[k] = c_scale(t, invr);
+  }
+}
+
+// out = Re(front * prod_k S_k), the product taken in level order.
 template <int FAM>
-__global__ void closed_final_kernel(int nparts, int d, const double *__restrict__ params,
-                                    const typename FamTraits<FAM>::V *__restrict__ partial, double *__restrict__ out) {
-  using V = typename FamTraits<FAM>::V;
-  if (threadIdx.x != 0) return;
-  V K = VOps<V>::one();
-  for (int i = 0; i < nparts; ++i) K = VOps<V>::mul(K, partial[i]);
-  if constexpr (FAM == MDI_FAM_OSC) {
-    double s, c;
-    sincos(kTwoPi * params[d], &s, &c);
-    out[0] = c * K.x - s * K.y;
-  } else {
-    out[0] = K;
+__global__ void __launch_bounds__(kScanThreads) closed_product_kernel(int d, const double *__restrict__ params,
+                                                                      const double2 *__restrict__ S,
+                                                                      double *__restrict__ out) {
+  __shared__ double2 sP[kScanThreads];
+  const int per = (d + blockDim.x - 1) / blockDim.x;
+  const int lo = min(d, (int)threadIdx.x * per), hi = min(d, lo + per);
+  double2 p = make_double2(1.0, 0.0);
+  for (int k = lo; k < hi; ++k) p = c_mul(p, S[k]);
+  sP[threadIdx.x] = p;
+  __syncthreads();
+  // Fixed pairwise tree (blockDim is a power of two): deterministic, log depth.
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sP[threadIdx.x] = c_mul(sP[threadIdx.x], sP[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double2 K = sP[0];
+    if constexpr (FAM == MDI_FAM_OSC) {
+      double sn, cs;
+      sincos(kTwoPi * params[d], &sn, &cs);
+      out[0] = cs * K.x - sn * K.y;
+    } else {
+      out[0] = K.x;
+    }
   }
 }
 
-static int closed_grid(int d) {
-  // One warp per level; at least a few levels per warp before adding CTAs.
-  int want = (d + kLevelWarps * 2 - 1) / (kLevelWarps * 2);
-  return std::max(1, std::min(want, sm_count() * 4));
+// ---------------------------------------------------------------------------
+// Workspace: gamma[d] | partS[chunks] | partT[chunks] | S[d] | T[d] | nu[d]
+// ---------------------------------------------------------------------------
+struct ClosedLayout {
+  size_t gamma, partS, partT, S, T, nu, total;
+};
+static ClosedLayout closed_layout(int d, int64_t a, int64_t n_last, bool grad) {
+  const Chunks ch = make_chunks(d, a, n_last);
+  ClosedLayout L{};
+  size_t off = 0;
+  L.gamma = off;
+  off += align_up(sizeof(double) * (size_t)d);
+  L.partS = off;
+  off += align_up(sizeof(double2) * (size_t)ch.total);
+  L.partT = off;
+  if (grad) off += align_up(sizeof(double2) * (size_t)ch.total);
+  L.S = off;
+  off += align_up(sizeof(double2) * (size_t)d);
+  L.T = off;
+  L.nu = off;
+  if (grad) {
+    off += align_up(sizeof(double2) * (size_t)d);
+    L.nu = off;
+    off += align_up(sizeof(double2) * (size_t)d);
+  }
+  L.total = off;
+  return L;
 }
 
-size_t closed_workspace_bytes(int d) {
-  return align_up(sizeof(double) * (size_t)d) + align_up(16 * (size_t)closed_grid(d));
+static bool closed_sizes_ok(int d, int64_t a, int64_t n_last) {
+  if (d < 1 || d > (1 << 20) || a < 1 || n_last < 1) return false;
+  // chunk count must fit an int
+  return (double)(d - 1) * (double)((a + kChunkQ - 1) / kChunkQ) + (double)((n_last + kChunkQ - 1) / kChunkQ) <
+         (double)(1 << 30);
+}
+
+size_t closed_workspace_bytes(int d, int64_t a, int64_t n_last) {
+  return closed_sizes_ok(d, a, n_last) ? closed_layout(d, a, n_last, false).total : 0;
+}
+
+static int chunk_grid(const Chunks &ch) {
+  const int warps_per_cta = kChunkThreads / kWarp;
+  return std::max(1, std::min((ch.total + warps_per_cta - 1) / warps_per_cta, sm_count() * 8));
+}
+
+template <int FAM, int PREC, bool WITH_T>
+static mdi_status run_levels_sums(int d, int64_t a, int64_t n_last, const double *params, char *base,
+                                  const ClosedLayout &L, cudaStream_t stream) {
+  double *gamma = (double *)(base + L.gamma);
+  double2 *partS = (double2 *)(base + L.partS), *partT = (double2 *)(base + L.partT);
+  double2 *S = (double2 *)(base + L.S), *T = (double2 *)(base + L.T);
+  const Chunks ch = make_chunks(d, a, n_last);
+  closed_scan_kernel<<<1, kScanThreads, 0, stream>>>(d, (double)a, params, gamma);
+  mdi_status st = check_launch();
+  if (st != MDI_OK) return st;
+  closed_chunk_kernel<FAM, PREC, WITH_T><<<chunk_grid(ch), kChunkThreads, 0, stream>>>(d, a, n_last, ch, gamma, partS,
+                                                                                     partT);
+  if ((st = check_launch()) != MDI_OK) return st;
+  closed_reduce_kernel<WITH_T><<<std::max(1, std::min((d + 255) / 256, sm_count() * 4)), 256, 0, stream>>>(
+      d, a, n_last, ch, partS, partT, S, T);
+  return check_launch();
 }
 
 template <int FAM, int PREC>
 static mdi_status run_closed(int d, int64_t a, int64_t n_last, const double *params, double *out, void *ws,
                              cudaStream_t stream) {
-  using V = typename FamTraits<FAM>::V;
-  double *gamma = (double *)ws;
-  V *partial = (V *)((char *)ws + align_up(sizeof(double) * (size_t)d));
-  closed_scan_kernel<<<1, kScanThreads, 0, stream>>>(d, (double)a, (double)n_last, params, gamma);
-  mdi_status st = check_launch();
+  const ClosedLayout L = closed_layout(d, a, n_last, false);
+  mdi_status st = run_levels_sums<FAM, PREC, false>(d, a, n_last, params, (char *)ws, L, stream);
   if (st != MDI_OK) return st;
-  const int grid = closed_grid(d);
-  closed_level_kernel<FAM, PREC><<<grid, kLevelThreads, 0, stream>>>(d, a, n_last, gamma, partial);
-  if ((st = check_launch()) != MDI_OK) return st;
-  closed_final_kernel<FAM><<<1, 32, 0, stream>>>(grid, d, params, partial, out);
+  closed_product_kernel<FAM><<<1, kScanThreads, 0, stream>>>(d, params, (const double2 *)((char *)ws + L.S), out);
   return check_launch();
 }
 
@@ -191,9 +283,10 @@ static mdi_status run_closed_p(int precision, int d, int64_t a, int64_t n_last, 
 mdi_status closed_launch(int family, int d, int64_t a, int64_t n_last, const double *params, int precision,
                          double *out, void *workspace, size_t ws_bytes, cudaStream_t stream) {
   if (family != MDI_FAM_EXP && family != MDI_FAM_OSC) return MDI_EUNSUPPORTED;
-  if (d < 1 || d > (1 << 20) || a < 1 || n_last < 1) return MDI_EINVAL;
+  if (!closed_sizes_ok(d, a, n_last)) return MDI_EINVAL;
   if (precision == MDI_PREC_DF64) return MDI_EUNSUPPORTED;
-  if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < closed_workspace_bytes(d)) return MDI_EWORKSPACE;
+  if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < closed_workspace_bytes(d, a, n_last))
+    return MDI_EWORKSPACE;
   if (family == MDI_FAM_EXP) return run_closed_p<MDI_FAM_EXP>(precision, d, a, n_last, params, out, workspace, stream);
   return run_closed_p<MDI_FAM_OSC>(precision, d, a, n_last, params, out, workspace, stream);
 }
@@ -210,40 +303,6 @@ mdi_status closed_launch(int family, int d, int64_t a, int64_t n_last, const dou
 // exclusive prefix and suffix products (no division by S_j), and the reverse
 // recurrence, like the forward one, is a block-wide scan of affine maps.
 // ---------------------------------------------------------------------------
-template <int FAM>
-__global__ void __launch_bounds__(kLevelThreads) closed_grad_level_kernel(int d, int64_t a, int64_t n_last,
-                                                                          const double *__restrict__ gamma,
-                                                                          double2 *__restrict__ S,
-                                                                          double2 *__restrict__ T) {
-  const int lane = threadIdx.x & (kWarp - 1);
-  const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
-  const int nwarps = gridDim.x * blockDim.x / kWarp;
-  for (int k = warp_global; k < d; k += nwarps) {
-    const int64_t r = (k + 1 < d) ? a : n_last;
-    const double g = gamma[k], invr = 1.0 / (double)r;
-    double2 s = make_double2(0.0, 0.0), t = make_double2(0.0, 0.0);
-    for (int64_t q = lane; q < r; q += kWarp) {
-      const double x = (double)q * invr;
-      double2 e;
-      if constexpr (FAM == MDI_FAM_OSC) {
-        double sn, cs;
-        sincos(g * x, &sn, &cs);
-        e = make_double2(cs, sn);
-      } else {
-        e = make_double2(exp(g * x), 0.0);
-      }
-      s = c_add(s, e);
-      t = c_add(t, c_scale(e, x));
-    }
-    s = warp_sum(s);
-    t = warp_sum(t);
-    if (lane == 0) {
-      S[k] = c_scale(s, invr);
-      T[k] = c_scale(t, invr);
-    }
-  }
-}
-
 template <int FAM>
 __global__ void __launch_bounds__(kScanThreads) closed_grad_final_kernel(int d, double a,
                                                                          const double *__restrict__ params,
@@ -337,34 +396,28 @@ __global__ void __launch_bounds__(kScanThreads) closed_grad_final_kernel(int d, 
   }
 }
 
-size_t closed_grad_workspace_bytes(int d) {
-  return align_up(sizeof(double) * (size_t)d) + 3 * align_up(sizeof(double2) * (size_t)d);
+size_t closed_grad_workspace_bytes(int d, int64_t a, int64_t n_last) {
+  return closed_sizes_ok(d, a, n_last) ? closed_layout(d, a, n_last, true).total : 0;
 }
 
 template <int FAM>
 static mdi_status run_closed_grad(int d, int64_t a, int64_t n_last, const double *params, double *value,
                                   double *grad, void *ws, cudaStream_t stream) {
+  const ClosedLayout L = closed_layout(d, a, n_last, true);
   char *base = (char *)ws;
-  double *gamma = (double *)base;
-  double2 *S = (double2 *)(base + align_up(sizeof(double) * (size_t)d));
-  double2 *T = S + 0;
-  T = (double2 *)((char *)S + align_up(sizeof(double2) * (size_t)d));
-  double2 *nu = (double2 *)((char *)T + align_up(sizeof(double2) * (size_t)d));
-  closed_scan_kernel<<<1, kScanThreads, 0, stream>>>(d, (double)a, (double)n_last, params, gamma);
-  mdi_status st = check_launch();
+  mdi_status st = run_levels_sums<FAM, MDI_PREC_FP64, true>(d, a, n_last, params, base, L, stream);
   if (st != MDI_OK) return st;
-  const int grid = std::max(1, std::min((d + kLevelWarps - 1) / kLevelWarps, sm_count() * 8));
-  closed_grad_level_kernel<FAM><<<grid, kLevelThreads, 0, stream>>>(d, a, n_last, gamma, S, T);
-  if ((st = check_launch()) != MDI_OK) return st;
-  closed_grad_final_kernel<FAM><<<1, kScanThreads, 0, stream>>>(d, (double)a, params, S, T, nu, value, grad);
+  closed_grad_final_kernel<FAM><<<1, kScanThreads, 0, stream>>>(d, (double)a, params, (const double2 *)(base + L.S),
+                                                                (const double2 *)(base + L.T), (double2 *)(base + L.nu),
+                                                                value, grad);
   return check_launch();
 }
 
 mdi_status closed_grad_launch(int family, int d, int64_t a, int64_t n_last, const double *params, double *value,
                               double *grad, void *workspace, size_t ws_bytes, cudaStream_t stream) {
   if (family != MDI_FAM_EXP && family != MDI_FAM_OSC) return MDI_EUNSUPPORTED;
-  if (d < 1 || d > (1 << 20) || a < 1 || n_last < 1) return MDI_EINVAL;
-  if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < closed_grad_workspace_bytes(d))
+  if (!closed_sizes_ok(d, a, n_last)) return MDI_EINVAL;
+  if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < closed_grad_workspace_bytes(d, a, n_last))
     return MDI_EWORKSPACE;
   if (family == MDI_FAM_EXP) return run_closed_grad<MDI_FAM_EXP>(d, a, n_last, params, value, grad, workspace, stream);
   return run_closed_grad<MDI_FAM_OSC>(d, a, n_last, params, value, grad, workspace, stream);

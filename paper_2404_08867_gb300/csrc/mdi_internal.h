@@ -24,11 +24,11 @@ mdi_status exact_launch(int family, int d, int64_t a, int64_t n_last, const doub
                         double *out, void *workspace, size_t ws_bytes, cudaStream_t stream);
 
 // mdi_closed.cu
-size_t closed_workspace_bytes(int d);
+size_t closed_workspace_bytes(int d, int64_t a, int64_t n_last);  // 0 when the sizes are out of range
 mdi_status closed_launch(int family, int d, int64_t a, int64_t n_last, const double *params, int precision,
                          double *out, void *workspace, size_t ws_bytes, cudaStream_t stream);
 
-size_t closed_grad_workspace_bytes(int d);
+size_t closed_grad_workspace_bytes(int d, int64_t a, int64_t n_last);
 mdi_status closed_grad_launch(int family, int d, int64_t a, int64_t n_last, const double *params, double *value,
                               double *grad, void *workspace, size_t ws_bytes, cudaStream_t stream);
 

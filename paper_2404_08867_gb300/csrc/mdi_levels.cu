@@ -169,31 +169,120 @@ __global__ void __launch_bounds__(kLvThreads) levels_build_kernel(int d, int a, 
 }
 
 // K2: forward chain with checkpoints and the value; backward chain for the adjoint.
-// One CTA of P threads.  misc[0] = complex Q before the front factor.
+// One CTA: P threads do the P x P products while all threads stage the operators
+// of the next kChainLevels levels into shared memory with cp.async (hardware
+// wait_group, double-buffered), so no level waits on an L2 round trip.  Real
+// families use real arithmetic on the real parts.  misc[0] = Q before the front
+// factor.
+constexpr int kChainMaxThreads = 1024;  // P x G thread grid, G = the power of two >= P
+constexpr int kChainSmem = 64 * 1024;  // two buffers of operators
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Operators M_first .. M_first+cnt-1 (1-based levels) -> dst, one 16-byte copy each.
+// M is stored [t][p]; `transpose` stages each operator as [p][t].
+__device__ __forceinline__ void stage_ops(double2 *dst, const double2 *M, int first, int cnt, int P, bool transpose) {
+  const int n = cnt * P * P, pp = P * P;
+  const double2 *src = M + (size_t)(first - 1) * pp;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int j = i;
+    if (transpose) {
+      const int lev = i / pp, e = i % pp;  // e = t*P + p
+      j = lev * pp + (e % P) * P + e / P;
+    }
+    cp_async16(dst + j, src + i);
+  }
+  cp_async_commit();
+}
+
+// Sum of v over aligned groups of G lanes (G a power of two <= 32); the result is
+// valid in every lane of the group.
+template <typename V> __device__ __forceinline__ V group_sum(V v, int G);
+template <> __device__ __forceinline__ double group_sum<double>(double v, int G) {
+  for (int off = 1; off < G; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off, G);
+  return v;
+}
+template <> __device__ __forceinline__ double2 group_sum<double2>(double2 v, int G) {
+  for (int off = 1; off < G; off <<= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, off, G);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, off, G);
+  }
+  return v;
+}
+
+// Lanes per row of the chain's thread grid: the power of two >= P.
+__host__ __device__ __forceinline__ int chain_group(int P) {
+  int g = 1;
+  while (g < P) g <<= 1;
+  return g;
+}
+
+static int chain_levels_per_chunk(int P) {
+  return std::max(1, std::min(8, kChainSmem / 2 / (P * P * (int)sizeof(double2))));
+}
+
 template <int FAM>
-__global__ void levels_chain_kernel(int d, int P, int C, const double *__restrict__ prm,
-                                    const double2 *__restrict__ M, const double2 *__restrict__ w,
-                                    double2 *__restrict__ gck, double2 *__restrict__ lck, double2 *__restrict__ misc,
-                                    double *__restrict__ value, double *__restrict__ grad, int adjoint) {
-  __shared__ double2 s_v[kNodesPMax], s_n[kNodesPMax];
+__global__ void __launch_bounds__(kChainMaxThreads) levels_chain_kernel(int d, int P, int C, int LC,
+                                                                     const double *__restrict__ prm,
+                                                                     const double2 *__restrict__ M,
+                                                                     const double2 *__restrict__ w,
+                                                                     double2 *__restrict__ gck,
+                                                                     double2 *__restrict__ lck,
+                                                                     double2 *__restrict__ misc,
+                                                                     double *__restrict__ value,
+                                                                     double *__restrict__ grad, int adjoint) {
+  using V = typename FamTraits<FAM>::V;
+  extern __shared__ __align__(16) unsigned char chain_smem[];
+  double2 *buf[2] = {(double2 *)chain_smem, (double2 *)chain_smem + (size_t)LC * P * P};
+  __shared__ V s_v[kNodesPMax], s_n[kNodesPMax];
+  // Thread grid: row = threadIdx.x / G, col = threadIdx.x % G; one product per thread,
+  // summed over the G lanes of a row.
+  const int G = chain_group(P);
+  const int row = threadIdx.x / G, col = threadIdx.x % G;
+  const bool cell = row < P && col < P;
   const int p = threadIdx.x;
   const bool on = p < P;
-  if (on) s_v[p] = make_double2(1.0, 0.0);
+  auto mul = [](double2 m, V v) -> V {
+    if constexpr (FAM == MDI_FAM_OSC) return c_mul(m, v);
+    else return m.x * v;
+  };
+  if (on) s_v[p] = VOps<V>::one();
   __syncthreads();
-  if (on) gck[p] = s_v[p];
-  for (int k = 1; k < d; ++k) {
-    const double2 *Mk = M + (size_t)(k - 1) * P * P;
-    if (on) {
-      double2 acc = make_double2(0.0, 0.0);
-      for (int t = 0; t < P; ++t) acc = c_add(acc, c_mul(Mk[t * P + p], s_v[t]));
-      s_n[p] = acc;
+  if (on) gck[p] = as2(s_v[p]);
+  const int nlev = d - 1;
+  const int nchunks = (nlev + LC - 1) / LC;
+  // Forward: chunk c holds levels 1 + c*LC .. min(d-1, (c+1)*LC), staged as [p][t].
+  // G_k[p] = sum_t M_k[p][t] G_{k-1}[t]: row = p, col = t.
+  if (nchunks > 0) stage_ops(buf[0], M, 1, std::min(LC, nlev), P, true);
+  for (int c = 0; c < nchunks; ++c) {
+    const int k0 = 1 + c * LC, k1 = std::min(nlev, (c + 1) * LC);
+    if (c + 1 < nchunks) {
+      const int n0 = k1 + 1;
+      stage_ops(buf[(c + 1) & 1], M, n0, std::min(LC, nlev - n0 + 1), P, true);
+      cp_async_wait_prev();
+    } else {
+      cp_async_wait_all();
     }
     __syncthreads();
-    if (on) {
-      s_v[p] = s_n[p];
-      if (k % C == 0) gck[(size_t)(k / C) * P + p] = s_n[p];
+    const double2 *B = buf[c & 1];
+    for (int k = k0; k <= k1; ++k) {
+      const double2 *Mk = B + (size_t)(k - k0) * P * P;
+      V prod = cell ? mul(Mk[row * P + col], s_v[col]) : VOps<V>::zero();
+      prod = group_sum(prod, G);
+      if (cell && col == 0) {
+        s_n[row] = prod;
+        if (k % C == 0) gck[(size_t)(k / C) * P + row] = as2(prod);
+      }
+      __syncthreads();
+      if (on) s_v[p] = s_n[p];
+      __syncthreads();
     }
-    __syncthreads();
   }
   // Q = front * sum_t w[t] G_{d-1}[t]
   double2 front = make_double2(1.0, 0.0);
@@ -204,7 +293,7 @@ __global__ void levels_chain_kernel(int d, int P, int C, const double *__restric
   }
   if (threadIdx.x == 0) {
     double2 q = make_double2(0.0, 0.0);
-    for (int t = 0; t < P; ++t) q = c_add(q, c_mul(w[t], s_v[t]));
+    for (int t = 0; t < P; ++t) q = c_add(q, c_mul(w[t], as2(s_v[t])));
     misc[0] = q;
     const double2 fq = c_mul(front, q);
     if (value) *value = fq.x;
@@ -215,27 +304,46 @@ __global__ void levels_chain_kernel(int d, int P, int C, const double *__restric
   }
   if (!adjoint) return;
   __syncthreads();
-  // lambda_{d-1} = front * w; lck[nck] holds it, lck[j] holds lambda_{jC}.
+  // lambda_{d-1} = front * w; lck[nck] holds it, lck[j] holds lambda_{jC}.  The
+  // adjoint of a real family is real (front = 1, w real).
   const int nck = (d - 1) / C + 1;
   if (on) {
-    s_v[p] = c_mul(front, w[p]);
-    lck[(size_t)nck * P + p] = s_v[p];
-    if ((d - 1) % C == 0) lck[(size_t)((d - 1) / C) * P + p] = s_v[p];
+    const double2 l = c_mul(front, w[p]);
+    s_v[p] = from2<V>(l);
+    lck[(size_t)nck * P + p] = l;
+    if ((d - 1) % C == 0) lck[(size_t)((d - 1) / C) * P + p] = l;
   }
   __syncthreads();
-  for (int k = d - 1; k >= 1; --k) {  // lambda_{k-1} = lambda_k M_k
-    const double2 *Mk = M + (size_t)(k - 1) * P * P;
-    if (on) {
-      double2 acc = make_double2(0.0, 0.0);
-      for (int q = 0; q < P; ++q) acc = c_add(acc, c_mul(s_v[q], Mk[p * P + q]));
-      s_n[p] = acc;
+  // Backward: chunk c holds levels max(1, top - LC + 1) .. top, top = d-1 - c*LC,
+  // staged as stored ([t][p]).  lambda_{k-1}[t] = sum_p lambda_k[p] M_k[p][t]:
+  // row = t, col = p.
+  if (nchunks > 0) {
+    const int top = nlev, bot = std::max(1, top - LC + 1);
+    stage_ops(buf[0], M, bot, top - bot + 1, P, false);
+  }
+  for (int c = 0; c < nchunks; ++c) {
+    const int top = nlev - c * LC, bot = std::max(1, top - LC + 1);
+    if (c + 1 < nchunks) {
+      const int ntop = bot - 1, nbot = std::max(1, ntop - LC + 1);
+      stage_ops(buf[(c + 1) & 1], M, nbot, ntop - nbot + 1, P, false);
+      cp_async_wait_prev();
+    } else {
+      cp_async_wait_all();
     }
     __syncthreads();
-    if (on) {
-      s_v[p] = s_n[p];
-      if ((k - 1) % C == 0) lck[(size_t)((k - 1) / C) * P + p] = s_n[p];
+    const double2 *B = buf[c & 1];
+    for (int k = top; k >= bot; --k) {
+      const double2 *Mk = B + (size_t)(k - bot) * P * P;
+      V prod = cell ? mul(Mk[row * P + col], s_v[col]) : VOps<V>::zero();
+      prod = group_sum(prod, G);
+      if (cell && col == 0) {
+        s_n[row] = prod;
+        if ((k - 1) % C == 0) lck[(size_t)((k - 1) / C) * P + row] = as2(prod);
+      }
+      __syncthreads();
+      if (on) s_v[p] = s_n[p];
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
@@ -386,7 +494,21 @@ static mdi_status run_levels(int d, int a, int n_last, const double *params, con
   const int grid = std::min(d, sm_count() * 8);
   levels_build_kernel<FAM, F32><<<grid, kLvThreads, 0, stream>>>(d, a, n_last, P, params, L, M, w);
   if ((st = check_launch()) != MDI_OK) return st;
-  levels_chain_kernel<FAM><<<1, 32, 0, stream>>>(d, P, C, params, M, w, gck, lck, misc, value, grad, grad ? 1 : 0);
+  static bool chain_attr = false;
+  if (!chain_attr) {
+    cudaError_t e = cudaFuncSetAttribute(levels_chain_kernel<FAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kChainSmem);
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      return MDI_ECUDA;
+    }
+    chain_attr = true;
+  }
+  const int LC = chain_levels_per_chunk(P);
+  const size_t chain_smem = 2 * (size_t)LC * P * P * sizeof(double2);
+  const int chain_threads = std::max(32, (P * chain_group(P) + 31) / 32 * 32);
+  levels_chain_kernel<FAM><<<1, chain_threads, chain_smem, stream>>>(d, P, C, LC, params, M, w, gck, lck, misc, value,
+                                                                     grad, grad ? 1 : 0);
   if ((st = check_launch()) != MDI_OK) return st;
   if (grad) {
     levels_grad_kernel<FAM><<<std::min(d, sm_count() * 8), kLvThreads, 0, stream>>>(d, a, n_last, P, C, params, L, M,
