@@ -62,7 +62,9 @@ def parse():
     ap.add_argument("--precision", default="df64", choices=["df64", "fp64", "fp32_eval_fp64", "fp32_eval_df32"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="budget of the CPU oracle sample")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads")
-    ap.add_argument("--no-tune", action="store_true", help="default launch shape, no autotuning")
+    ap.add_argument("--no-tune", action="store_true", help="fixed launch shape (--block, --table-in-l1), no autotuning")
+    ap.add_argument("--block", type=int, default=128, help="CTA size with --no-tune")
+    ap.add_argument("--table-in-l1", type=int, default=1, choices=[0, 1], help="table placement with --no-tune")
     return ap.parse_args()
 
 
@@ -359,9 +361,9 @@ def main():
 
     b = inputs.batch(count=args.count, seed=rank)
     plan = BatchedMDILR(b.families, b.d, b.a, b.n_last, b.offsets, b.pool, precision=args.precision, nodes=P_NODES)
-    tuning = {"block": 256, "table_in_l1": 0} if args.no_tune else plan.tune()
+    tuning = {"block": args.block, "table_in_l1": args.table_in_l1} if args.no_tune else plan.tune()
     if args.no_tune:
-        plan.opts.update(block=256, table_in_l1=0)
+        plan.opts.update(block=args.block, table_in_l1=args.table_in_l1)
     plan.capture()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()

@@ -13,11 +13,13 @@
 // GB300 mapping.  Integrals are independent, so a persistent grid of CTAs pulls
 // them from an atomic counter (no waiting: a CTA that finds the queue empty
 // exits).  A CTA sweeps its integral's d levels with the state in shared memory.
-// Inside a level, thread t owns node p = t mod P and cluster points q = t/P,
-// t/P + B/P, ...; each point interpolates G_{k-1} (P multiply-adds against the
-// basis table L_a[t][q*P+p] = l_t(u_qp)), multiplies by phi_k, and accumulates;
-// the B/P partial rows are then added in a fixed order by P threads.  The basis
-// tables depend only on (a, P) and are built once per workspace
+// Lanes are node-major: Q consecutive lanes serve node p and take the cluster
+// points q = qs, qs + Q, ...; each point interpolates G_{k-1} (P multiply-adds
+// against the basis table L_a[t][p*a + q] = l_t(u_qp), contiguous in q), multiplies
+// by phi_k and accumulates; the Q lanes add their sums with shuffles and one lane
+// writes G_k[p] into the other half of a double-buffered state, so a level costs
+// one barrier.  The constants of 64 levels at a time are prepared by all threads
+// together.  The basis tables depend only on (a, P) and are built once per workspace
 // (mdi_lr_batched_prepare) for a = 1..64, together with the basis at the last
 // axis' points s/a (used when n_last = a).  A CTA may stage its table in shared
 // memory (fewer resident CTAs) or read it through L1 (more resident CTAs to hide
@@ -42,31 +44,48 @@ namespace mdi {
 constexpr int kNodesMaxBlock = 512;
 constexpr int kNodesSmemTable = 64 * 1024;  // table bytes staged in shared memory
 
-// Fixed part of the dynamic shared memory.  The partial rows (rows x P x 16 B)
-// and, when staging, the table follow it.
+constexpr int kLvChunk = 64;  // levels whose constants are held in shared memory at once
+
+// Per-axis constants of a level: c, w, 1/c^2 in double and as float pairs.
+struct LevelConst {
+  double c, w, ic2;
+  float4 cw;   // (c.hi, c.lo, w.hi, w.lo)
+  float2 ic;   // 1/c^2 as a float pair
+};
+
+// Fixed part of the dynamic shared memory; the staged table (if any) follows it.
 struct NodesShared {
   double xi[kNodesPMax], bw[kNodesPMax];
-  double2 G[kNodesPMax];   // state at the nodes in double (imaginary part 0 for real families)
-  float4 Gdf[kNodesPMax];  // the state as float pairs (re.hi, re.lo, im.hi, im.lo)
-  float2 xadf[kNodesPMax]; // xi_p / a as float pairs (DF64), per integral
+  double2 G[2][kNodesPMax];   // state at the nodes in double, double-buffered by level
+  float4 Gdf[2][kNodesPMax];  // the state as float pairs (re.hi, re.lo, im.hi, im.lo)
+  float2 xadf[kNodesPMax];    // xi_p / a as float pairs (DF64), per integral
   double2 red[kNodesMaxBlock / kWarp];
   float4 redf[kNodesMaxBlock / kWarp];
   float2 exp2tab[kExpTable];  // 2^(j/256) as float pairs (double-float exp)
-  float4 lvl[2][2];           // double-float c, w, 1/c^2 of the current/next level
+  LevelConst lc[kLvChunk];    // constants of axes base .. base+63
   float2 iadf;                // 1/a as a float pair (DF64)
   int inst;
   int pad;
 };
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) / 16 * 16; }
-__host__ __device__ inline size_t rows_bytes(int block, int P) { return align16((size_t)(block / P) * P * 16); }
 static size_t nodes_smem_bytes(int block, int P, bool stage) {
-  return align16(sizeof(NodesShared)) + rows_bytes(block, P) + (stage ? kNodesSmemTable : 0);
+  (void)block;
+  (void)P;
+  return align16(sizeof(NodesShared)) + (stage ? kNodesSmemTable : 0);
+}
+
+// Lanes per node: the largest power of two Q <= 32 with P*Q <= blockDim.
+__device__ __forceinline__ int node_lanes(int B, int P) {
+  int Q = 1;
+  while (Q < kWarp && P * 2 * Q <= B) Q <<= 1;
+  return Q;
 }
 
 // Table of parameter a (1-based) for P nodes, in 8-byte entries: the cluster basis
-// L_a[t][q*P + p] (a*P*P entries) followed by the last-axis basis F_a[t][s] =
-// l_t(s/a) (a*P entries).  Even P keeps every block 16-byte aligned.
+// L_a[t][p*a + q] = l_t((q + xi_p)/a) (a*P*P entries) followed by the last-axis
+// basis F_a[t][s] = l_t(s/a) (a*P entries).  Even P keeps every block 16-byte
+// aligned.
 __host__ __device__ __forceinline__ size_t table_offset(int a, int P) {
   return (size_t)P * (P + 1) * (size_t)a * (size_t)(a - 1) / 2;
 }
@@ -89,11 +108,11 @@ __global__ void nodes_table_kernel(int P, void *__restrict__ table) {
       base += (size_t)a * (P + 1);
       ++a;
     }
-    const int i = (int)(g - base);
+    const int i = (int)(g - base);  // i = p*a + q on the cluster part
     const bool last_axis = i >= a * P;
     double u;
     if (last_axis) u = (double)(i - a * P) / (double)a;                 // s / a
-    else u = ((double)(i / P) + s_xi[i % P]) / (double)a;              // (q + xi_p) / a
+    else u = ((double)(i % a) + s_xi[i / a]) / (double)a;              // (q + xi_p) / a
     double den = 0.0;
     int hit = -1;
     for (int t = 0; t < P; ++t) {
@@ -115,16 +134,25 @@ __global__ void nodes_table_kernel(int P, void *__restrict__ table) {
   }
 }
 
-// Double-float constants of axis j (0-based): (c, w) and (1/c^2, 0).
-__device__ __forceinline__ void make_level_df(const double *__restrict__ prm, int d, int j, float4 *dst) {
+// Constants of axis j (0-based) for the level loop.
+__device__ __forceinline__ void make_level_const(const double *__restrict__ prm, int d, int j, LevelConst &L) {
   const double c = prm[j], w = prm[d + j], ic2 = 1.0 / (c * c);
+  L.c = c;
+  L.w = w;
+  L.ic2 = ic2;
   const df32 cd = df_from_double(c), wd = df_from_double(w), id = df_from_double(ic2);
-  dst[0] = make_float4(cd.hi, cd.lo, wd.hi, wd.lo);
-  dst[1] = make_float4(id.hi, id.lo, 0.f, 0.f);
+  L.cw = make_float4(cd.hi, cd.lo, wd.hi, wd.lo);
+  L.ic = make_float2(id.hi, id.lo);
+}
+
+// Fills sh.lc with the constants of axes base .. base+kLvChunk-1 (all threads).
+__device__ __forceinline__ void load_level_chunk(LevelConst *lc, const double *__restrict__ prm, int d, int base) {
+  const int n = min(kLvChunk, d - base);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) make_level_const(prm, d, base + j, lc[j]);
 }
 
 // phi_j(u) in double-float arithmetic (EXP, GAUSS, PEAK).
-template <int FAM> __device__ __forceinline__ df32 phi_df(df32 u, float4 cw, float4 ic, const float2 *tab) {
+template <int FAM> __device__ __forceinline__ df32 phi_df(df32 u, float4 cw, float2 ic, const float2 *tab) {
   const df32 c{cw.x, cw.y}, w{cw.z, cw.w};
   if constexpr (FAM == MDI_FAM_EXP) {
     return df_exp(df_mul(c, u), tab);
@@ -169,15 +197,31 @@ __device__ __forceinline__ float4 block_sum_df(df32 re, df32 im, float4 *scratch
   return r;
 }
 
+// Sums over aligned groups of Q lanes (Q a power of two <= 32), valid in every lane.
+__device__ __forceinline__ double2 lanes_sum(double2 v, int Q) {
+  for (int off = 1; off < Q; off <<= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, off, Q);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, off, Q);
+  }
+  return v;
+}
+__device__ __forceinline__ df32 lanes_sum_df(df32 v, int Q) {
+  for (int off = 1; off < Q; off <<= 1)
+    v = df_add(v, df32{__shfl_xor_sync(0xffffffffu, v.hi, off, Q), __shfl_xor_sync(0xffffffffu, v.lo, off, Q)});
+  return v;
+}
+
 // ---------------------------------------------------------------------------
 // One integral, swept by one CTA.  Ltab: the cluster basis of this a (shared or
-// global memory); Ftab: the last-axis basis (global); rowsum: rows x P slots of
-// 16 bytes in shared memory.
+// global memory); Ftab: the last-axis basis (global).
+//
+// Lanes are node-major: the Q = node_lanes(B, P) consecutive lanes of node p take
+// the cluster points q = qs, qs + Q, ... and add their sums with shuffles, so a
+// level ends with one barrier; the state is double-buffered by level parity.
 // ---------------------------------------------------------------------------
 template <int FAM, int PREC>
-__device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, const void *__restrict__ Ftab,
-                          void *__restrict__ rowsum, int P, int d, int a, int n_last, const double *__restrict__ prm,
-                          double *__restrict__ out_slot) {
+__device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, const void *__restrict__ Ftab, int P, int d,
+                          int a, int n_last, const double *__restrict__ prm, double *__restrict__ out_slot) {
   using V = typename FamTraits<FAM>::V;
   constexpr bool F32 = (PREC == MDI_PREC_FP32_EVAL_FP64 || PREC == MDI_PREC_FP32_EVAL_DF32);
   constexpr bool DF = (PREC == MDI_PREC_FP32_EVAL_DF32 || PREC == MDI_PREC_DF64);
@@ -185,13 +229,15 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, const 
   constexpr bool DF64 = (PREC == MDI_PREC_DF64) && !CPLX;  // OSC keeps phi in FP64 in this mode
   constexpr bool DFSTATE = (PREC == MDI_PREC_DF64);        // state kept as float pairs only
   const int tid = threadIdx.x, B = blockDim.x;
-  const int p = tid % P, row = tid / P, rows = B / P;
-  const bool active = row < rows;  // threads beyond rows*P only join barriers
+  const int Q = node_lanes(B, P);
+  const int p = min(tid / Q, P - 1), qs = tid % Q;
+  const bool act = tid < P * Q;
+  const bool warp_act = (tid & ~(kWarp - 1)) < P * Q;  // this warp holds active lanes
   const int npts = a * P;
 
   if (tid < P) {
-    sh.Gdf[tid] = make_float4(1.f, 0.f, 0.f, 0.f);
-    sh.G[tid] = make_double2(1.0, 0.0);
+    sh.Gdf[0][tid] = make_float4(1.f, 0.f, 0.f, 0.f);
+    sh.G[0][tid] = make_double2(1.0, 0.0);
     if (DFSTATE) {
       const double xa = sh.xi[tid] / (double)a;
       const float h = (float)xa;
@@ -202,113 +248,112 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, const 
     const double ia = 1.0 / (double)a;
     const float h = (float)ia;
     sh.iadf = make_float2(h, (float)(ia - (double)h));
-    if (DF64) make_level_df(prm, d, 0, sh.lvl[1]);
   }
+  load_level_chunk(sh.lc, prm, d, 0);
   __syncthreads();
-  const double inv_a = DF64 ? 0.0 : 1.0 / (double)a;
+  const double inv_a = 1.0 / (double)a;  // FP64 modes only (folded away in DF64)
   const double xi_p = sh.xi[p];
 
   for (int k = 1; k < d; ++k) {
-    const AxisParams ap = DF64 ? AxisParams{} : load_axis(prm, d, k - 1);
-    const float4 lc0 = sh.lvl[k & 1][0], lc1 = sh.lvl[k & 1][1];
-    const df32 ia{sh.iadf.x, sh.iadf.y}, xa{sh.xadf[p].x, sh.xadf[p].y};
+    const int j = k - 1;  // axis of this level
+    if (j > 0 && j % kLvChunk == 0) {  // next chunk of level constants
+      load_level_chunk(sh.lc, prm, d, j);
+      __syncthreads();
+    }
+    const LevelConst &L = sh.lc[j % kLvChunk];
+    const int rb = (k - 1) & 1, wb = k & 1;
     double2 acc = make_double2(0.0, 0.0);
     DfAcc dre, dim;
-    for (int i = active ? tid : npts; i < npts; i += rows * P) {
-      const int q = i / P;
-      V f;
-      df32 fdf{0.f, 0.f};
-      if constexpr (DF64) {
-        const df32 u = df_add(df_mul_f(ia, (float)q), xa);
-        fdf = phi_df<FAM>(u, lc0, lc1, sh.exp2tab);
-      } else {
-        const double u = ((double)q + xi_p) * inv_a;
-        f = phi<FAM, F32>(u, ap);
-      }
-      if constexpr (!DF) {
-        V g;
-        if (k == 1) {
-          g = VOps<V>::one();
+    if (act) {
+      const df32 ia{sh.iadf.x, sh.iadf.y}, xa{sh.xadf[p].x, sh.xadf[p].y};
+      const AxisParams ap{L.c, L.w, L.ic2};
+      for (int q = qs; q < a; q += Q) {
+        const int i = p * a + q;
+        V f;
+        df32 fdf{0.f, 0.f};
+        if constexpr (DF64) {
+          const df32 u = df_add(df_mul_f(ia, (float)q), xa);
+          fdf = phi_df<FAM>(u, L.cw, L.ic, sh.exp2tab);
         } else {
-          const double *L = (const double *)Ltab + i;
-          g = VOps<V>::zero();
-#pragma unroll 4
-          for (int t = 0; t < P; ++t) g = VOps<V>::fma_s(L[(size_t)t * npts], from2<V>(sh.G[t]), g);
+          f = phi<FAM, F32>(((double)q + xi_p) * inv_a, ap);
         }
-        acc = c_add(acc, as2(VOps<V>::mul(f, g)));
-      } else {
-        // Interpolation and cluster sum in double-float, Dot2-style accumulation.
-        const float2 *L = (const float2 *)Ltab + i;
-        df32 gr{1.f, 0.f}, gi{0.f, 0.f};
-        if (k > 1) {
-          DfAcc ar, ai;
+        if constexpr (!DF) {
+          V g;
+          if (k == 1) {
+            g = VOps<V>::one();
+          } else {
+            const double *Lt = (const double *)Ltab + i;
+            g = VOps<V>::zero();
 #pragma unroll 4
-          for (int t = 0; t < P; ++t) {
-            const float2 l = L[(size_t)t * npts];
-            const float4 gt = sh.Gdf[t];
-            dacc_prod(ar, df32{l.x, l.y}, df32{gt.x, gt.y});
-            if constexpr (CPLX) dacc_prod(ai, df32{l.x, l.y}, df32{gt.z, gt.w});
+            for (int t = 0; t < P; ++t) g = VOps<V>::fma_s(Lt[(size_t)t * npts], from2<V>(sh.G[rb][t]), g);
           }
-          gr = dacc_value(ar);
-          if constexpr (CPLX) gi = dacc_value(ai);
-        }
-        if constexpr (CPLX) {
-          const double2 f2 = as2(f);
-          const df32 fr = (PREC == MDI_PREC_DF64) ? df_from_double(f2.x) : df32{(float)f2.x, 0.f};
-          const df32 fi = (PREC == MDI_PREC_DF64) ? df_from_double(f2.y) : df32{(float)f2.y, 0.f};
-          dacc_prod(dre, fr, gr);
-          dacc_prod(dre, df_neg(fi), gi);
-          dacc_prod(dim, fr, gi);
-          dacc_prod(dim, fi, gr);
-        } else if constexpr (DF64) {
-          dacc_prod(dre, fdf, gr);
+          acc = c_add(acc, as2(VOps<V>::mul(f, g)));
         } else {
-          dacc_prod(dre, df32{(float)as2(f).x, 0.f}, gr);
+          // Interpolation and cluster sum in double-float, Dot2-style accumulation.
+          const float2 *Lt = (const float2 *)Ltab + i;
+          df32 gr{1.f, 0.f}, gi{0.f, 0.f};
+          if (k > 1) {
+            DfAcc ar, ai;
+#pragma unroll 4
+            for (int t = 0; t < P; ++t) {
+              const float2 l = Lt[(size_t)t * npts];
+              const float4 gt = sh.Gdf[rb][t];
+              dacc_prod(ar, df32{l.x, l.y}, df32{gt.x, gt.y});
+              if constexpr (CPLX) dacc_prod(ai, df32{l.x, l.y}, df32{gt.z, gt.w});
+            }
+            gr = dacc_value(ar);
+            if constexpr (CPLX) gi = dacc_value(ai);
+          }
+          if constexpr (CPLX) {
+            const double2 f2 = as2(f);
+            const df32 fr = (PREC == MDI_PREC_DF64) ? df_from_double(f2.x) : df32{(float)f2.x, 0.f};
+            const df32 fi = (PREC == MDI_PREC_DF64) ? df_from_double(f2.y) : df32{(float)f2.y, 0.f};
+            dacc_prod(dre, fr, gr);
+            dacc_prod(dre, df_neg(fi), gi);
+            dacc_prod(dim, fr, gi);
+            dacc_prod(dim, fi, gr);
+          } else if constexpr (DF64) {
+            dacc_prod(dre, fdf, gr);
+          } else {
+            dacc_prod(dre, df32{(float)as2(f).x, 0.f}, gr);
+          }
         }
       }
     }
-    // Partial rows -> new state at node p, added in row order.
-    if (active) {
+    // The Q lanes of node p add their sums; lane qs = 0 writes the new state.
+    if (warp_act) {
       if constexpr (DF) {
-        const df32 vr = dacc_value(dre), vi = dacc_value(dim);
-        ((float4 *)rowsum)[row * P + p] = make_float4(vr.hi, vr.lo, vi.hi, vi.lo);
-      } else {
-        ((double2 *)rowsum)[row * P + p] = acc;
-      }
-    }
-    __syncthreads();
-    if (tid < P) {
-      if constexpr (DF) {
-        df32 sr{0.f, 0.f}, si{0.f, 0.f};
-        for (int r = 0; r < rows; ++r) {
-          const float4 v = ((const float4 *)rowsum)[r * P + tid];
-          sr = df_add(sr, df32{v.x, v.y});
-          si = df_add(si, df32{v.z, v.w});
-        }
-        if constexpr (DFSTATE) {
-          const df32 ia{sh.iadf.x, sh.iadf.y};
-          const df32 gr = df_mul(sr, ia), gi = df_mul(si, ia);
-          sh.Gdf[tid] = make_float4(gr.hi, gr.lo, gi.hi, gi.lo);
-        } else {
-          const double2 g = make_double2(df_to_double(sr) * inv_a, df_to_double(si) * inv_a);
-          sh.G[tid] = g;
-          sh.Gdf[tid] = split2(g);
+        const df32 sr = lanes_sum_df(dacc_value(dre), Q);
+        const df32 si = CPLX ? lanes_sum_df(dacc_value(dim), Q) : df32{0.f, 0.f};
+        if (act && qs == 0) {
+          if constexpr (DFSTATE) {
+            const df32 ia{sh.iadf.x, sh.iadf.y};
+            const df32 gr = df_mul(sr, ia), gi = df_mul(si, ia);
+            sh.Gdf[wb][p] = make_float4(gr.hi, gr.lo, gi.hi, gi.lo);
+          } else {
+            const double2 g = make_double2(df_to_double(sr) * inv_a, df_to_double(si) * inv_a);
+            sh.G[wb][p] = g;
+            sh.Gdf[wb][p] = split2(g);
+          }
         }
       } else {
-        double2 s = make_double2(0.0, 0.0);
-        for (int r = 0; r < rows; ++r) s = c_add(s, ((const double2 *)rowsum)[r * P + tid]);
-        sh.G[tid] = c_scale(s, inv_a);
+        const double2 s = lanes_sum(acc, Q);
+        if (act && qs == 0) sh.G[wb][p] = c_scale(s, inv_a);
       }
-      if (DF64 && tid == 0) make_level_df(prm, d, k, sh.lvl[(k + 1) & 1]);  // axis k = level k+1 (<= d)
     }
     __syncthreads();
   }
 
   // Last level: Q = (1/n_last) sum_s phi_d(s/n_last) G_{d-1}(s/n_last).
+  const int sb = (d - 1) & 1;  // buffer holding G_{d-1}
+  if (d > 1 && (d - 1) % kLvChunk == 0) {
+    load_level_chunk(sh.lc, prm, d, d - 1);
+    __syncthreads();
+  }
+  const LevelConst &LL = sh.lc[(d - 1) % kLvChunk];
   const bool tabulated = (n_last == a) && d > 1;
   if constexpr (DF64) {
     if (tabulated) {
-      const float4 lc0 = sh.lvl[d & 1][0], lc1 = sh.lvl[d & 1][1];
       const df32 ia{sh.iadf.x, sh.iadf.y};
       DfAcc acc;
       for (int s = tid; s < n_last; s += B) {
@@ -317,11 +362,11 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, const 
 #pragma unroll 4
         for (int t = 0; t < P; ++t) {
           const float2 l = F[(size_t)t * a];
-          const float4 gt = sh.Gdf[t];
+          const float4 gt = sh.Gdf[sb][t];
           dacc_prod(ag, df32{l.x, l.y}, df32{gt.x, gt.y});
         }
         const df32 u = df_mul_f(ia, (float)s);
-        dacc_prod(acc, phi_df<FAM>(u, lc0, lc1, sh.exp2tab), dacc_value(ag));
+        dacc_prod(acc, phi_df<FAM>(u, LL.cw, LL.ic, sh.exp2tab), dacc_value(ag));
       }
       const float4 tot = block_sum_df(dacc_value(acc), df32{0.f, 0.f}, sh.redf);
       if (tid == 0) *out_slot = ((double)tot.x + (double)tot.y) / (double)n_last;
@@ -330,10 +375,10 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, const 
     }
   }
   if constexpr (DFSTATE) {  // double view of the state for the general last level
-    if (tid < P) sh.G[tid] = join2(sh.Gdf[tid]);
+    if (tid < P) sh.G[sb][tid] = join2(sh.Gdf[sb][tid]);
     __syncthreads();
   }
-  const AxisParams ap = load_axis(prm, d, d - 1);
+  const AxisParams ap{LL.c, LL.w, LL.ic2};
   const double inv_n = 1.0 / (double)n_last;
   V acc = VOps<V>::zero();
   for (int s = tid; s < n_last; s += B) {
@@ -347,11 +392,11 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, const 
         const float2 *F = (const float2 *)Ftab + s;
         for (int t = 0; t < P; ++t) {
           const float2 l = F[(size_t)t * a];
-          g = VOps<V>::fma_s((double)l.x + (double)l.y, from2<V>(sh.G[t]), g);
+          g = VOps<V>::fma_s((double)l.x + (double)l.y, from2<V>(sh.G[sb][t]), g);
         }
       } else {
         const double *F = (const double *)Ftab + s;
-        for (int t = 0; t < P; ++t) g = VOps<V>::fma_s(F[(size_t)t * a], from2<V>(sh.G[t]), g);
+        for (int t = 0; t < P; ++t) g = VOps<V>::fma_s(F[(size_t)t * a], from2<V>(sh.G[sb][t]), g);
       }
     } else {
       double den = 0.0;
@@ -364,9 +409,9 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, const 
         }
         const double wt = sh.bw[t] / (u - sh.xi[t]);
         den += wt;
-        num = make_double2(fma(wt, sh.G[t].x, num.x), fma(wt, sh.G[t].y, num.y));
+        num = make_double2(fma(wt, sh.G[sb][t].x, num.x), fma(wt, sh.G[sb][t].y, num.y));
       }
-      g = hit >= 0 ? from2<V>(sh.G[hit]) : from2<V>(c_scale(num, 1.0 / den));
+      g = hit >= 0 ? from2<V>(sh.G[sb][hit]) : from2<V>(c_scale(num, 1.0 / den));
     }
     acc = VOps<V>::add(acc, VOps<V>::mul(phi<FAM, F32 && !DFSTATE>(u, ap), g));
   }
@@ -394,8 +439,7 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
                                                                        unsigned expect_tag) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   NodesShared &sh = *reinterpret_cast<NodesShared *>(dyn_smem);
-  unsigned char *rowsum = dyn_smem + align16(sizeof(NodesShared));
-  unsigned char *tab_smem = rowsum + rows_bytes(blockDim.x, P);
+  unsigned char *tab_smem = dyn_smem + align16(sizeof(NodesShared));
   for (int t = threadIdx.x; t < P; t += blockDim.x) {
     sh.xi[t] = cheb_node(t, P);
     sh.bw[t] = cheb_weight(t, P);
@@ -437,16 +481,16 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
     const double *prm = pool + ds.param_offset;
     switch (ds.family) {
       case MDI_FAM_EXP:
-        sweep_one<MDI_FAM_EXP, PREC>(sh, Ltab, Ftab, rowsum, P, ds.d, a, ds.n_last, prm, out + inst);
+        sweep_one<MDI_FAM_EXP, PREC>(sh, Ltab, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
         break;
       case MDI_FAM_OSC:
-        sweep_one<MDI_FAM_OSC, PREC>(sh, Ltab, Ftab, rowsum, P, ds.d, a, ds.n_last, prm, out + inst);
+        sweep_one<MDI_FAM_OSC, PREC>(sh, Ltab, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
         break;
       case MDI_FAM_GAUSS:
-        sweep_one<MDI_FAM_GAUSS, PREC>(sh, Ltab, Ftab, rowsum, P, ds.d, a, ds.n_last, prm, out + inst);
+        sweep_one<MDI_FAM_GAUSS, PREC>(sh, Ltab, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
         break;
       default:
-        sweep_one<MDI_FAM_PEAK, PREC>(sh, Ltab, Ftab, rowsum, P, ds.d, a, ds.n_last, prm, out + inst);
+        sweep_one<MDI_FAM_PEAK, PREC>(sh, Ltab, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
         break;
     }
   }
