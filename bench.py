@@ -68,6 +68,18 @@ def parse():
     return ap.parse_args()
 
 
+def combine_ranks(total_ms, units_per_rank, steps, world, dist=None, device="cpu"):
+    """Whole-job throughput under weak scaling: every rank processes its own
+    `units_per_rank` per step; the job's time is the slowest rank's (max over
+    ranks, no data-path collective).  Returns (units per second, max ms)."""
+    if world > 1:
+        import torch
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    return units_per_rank * world * steps / (total_ms / 1e3), total_ms
+
+
 def workload_config(count, precision):
     return {"workload": f"batch of {count} MDI-LR integrals, d~U{{6..20}}, N~U{{8..32}} per transformed axis, "
                         f"product-peak/Gaussian alternating, node state P={P_NODES}",
@@ -352,13 +364,6 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return t.item()
-
     b = inputs.batch(count=args.count, seed=rank)
     plan = BatchedMDILR(b.families, b.d, b.a, b.n_last, b.offsets, b.pool, precision=args.precision, nodes=P_NODES)
     tuning = {"block": args.block, "table_in_l1": args.table_in_l1} if args.no_tune else plan.tune()
@@ -390,8 +395,7 @@ def main():
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = max_over_ranks(sum(step_ms))
-    value = len(b) * world * args.steps / (total_ms / 1e3)
+    value, total_ms = combine_ranks(sum(step_ms), len(b), args.steps, world, dist, "cuda")
     device_out = plan.out.clone()
 
     # End to end: pinned host inputs -> device, the launch, results -> pinned host.
@@ -420,8 +424,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         e_ms.append(e0.elapsed_time(e1))
-    e2e_total = max_over_ranks(sum(e_ms))
-    e2e_value = len(b) * world * args.steps / (e2e_total / 1e3)
+    e2e_value, e2e_total = combine_ranks(sum(e_ms), len(b), args.steps, world, dist, "cuda")
     assert torch.equal(h_out, device_out.cpu()), "end-to-end result differs from the device-timed run"
 
     if rank == 0:
