@@ -170,6 +170,14 @@ __device__ __forceinline__ df32 df_shfl_down(df32 v, int off) {
   return df32{__shfl_down_sync(0xffffffffu, v.hi, off), __shfl_down_sync(0xffffffffu, v.lo, off)};
 }
 __device__ __forceinline__ df32 df_neg(df32 x) { return df32{-x.hi, -x.lo}; }
+// x + y with the error bounded relative to |x| + |y| rather than |x + y|
+// (Joldes, Muller & Popescu 2017, Algorithm 5, "sloppy" double-word addition):
+// used where only the absolute error of the sum matters.
+__device__ __forceinline__ df32 df_add_sloppy(df32 x, df32 y) {
+  const df32 s = two_sum(x.hi, y.hi);
+  const float v = __fadd_rn(x.lo, y.lo);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, v));
+}
 
 // Accumulator for sums of double-float products: Algorithm Dot2 of Ogita, Rump &
 // Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26 (2005), extended
@@ -237,7 +245,7 @@ __device__ __forceinline__ df32 df_exp(df32 x, const float2 *__restrict__ tab) {
   // r = x - n ln2/256, accurate to about 2^-50 absolute
   const float t = __fmaf_rn(-n, DfExpConsts::C1, x.hi);  // exact: n*C1 exact, Sterbenz
   df32 r = two_sum(t, x.lo);
-  r = df_add(r, two_prod(-n, DfExpConsts::C2));
+  r = df_add_sloppy(r, two_prod(-n, DfExpConsts::C2));  // absolute error ~2^-48 |n C2|
   r = fast_two_sum(r.hi, __fmaf_rn(-n, DfExpConsts::C3, r.lo));
   // exp(r): 1 + r (TwoSum) + r^2/2 (exact product of the high part plus cross term)
   const float h = 0.5f * r.hi;

@@ -165,6 +165,36 @@ template <int FAM> __device__ __forceinline__ df32 phi_df(df32 u, float4 cw, flo
   }
 }
 
+// The argument of phi at the cluster points u = q/a + x0 of one node is affine in
+// q: t = s1 q + s0.  Per level and node:
+//   GAUSS  t = c (u - w)  ->  s1 = c/a, s0 = c (x0 - w);   phi = exp(-t^2)
+//   PEAK   t = u - w      ->  s1 = 1/a, s0 = x0 - w;       phi = 1 / (t^2 + 1/c^2)
+//   EXP    t = c u        ->  s1 = c/a, s0 = c x0;         phi = exp(t)
+template <int FAM>
+__device__ __forceinline__ void phi_affine_coeffs(float4 cw, df32 ia, df32 x0, df32 &s1, df32 &s0) {
+  const df32 c{cw.x, cw.y}, w{cw.z, cw.w};
+  if constexpr (FAM == MDI_FAM_GAUSS) {
+    s1 = df_mul(c, ia);
+    s0 = df_mul(c, df_add(x0, df_neg(w)));
+  } else if constexpr (FAM == MDI_FAM_PEAK) {
+    s1 = ia;
+    s0 = df_add(x0, df_neg(w));
+  } else {
+    s1 = df_mul(c, ia);
+    s0 = df_mul(c, x0);
+  }
+}
+// phi at the point q: one double-float multiply-add forms the argument.  The
+// sloppy add suffices: phi depends on t through t^2 or exp(t), so only the
+// absolute error of t (about 2^-48 |t| terms) matters.
+template <int FAM>
+__device__ __forceinline__ df32 phi_df_affine(df32 s1, df32 s0, float q, float2 ic, const float2 *tab) {
+  const df32 t = df_add_sloppy(df_mul_f(s1, q), s0);
+  if constexpr (FAM == MDI_FAM_GAUSS) return df_exp(df_neg(df_sqr(t)), tab);
+  else if constexpr (FAM == MDI_FAM_PEAK) return df_rcp(df_add_sloppy(df_sqr(t), df32{ic.x, ic.y}));
+  else return df_exp(t, tab);
+}
+
 __device__ __forceinline__ float4 split2(double2 g) {
   const float rh = (float)g.x, ih = (float)g.y;
   return make_float4(rh, (float)(g.x - (double)rh), ih, (float)(g.y - (double)ih));
@@ -267,13 +297,14 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, const 
     if (act) {
       const df32 ia{sh.iadf.x, sh.iadf.y}, xa{sh.xadf[p].x, sh.xadf[p].y};
       const AxisParams ap{L.c, L.w, L.ic2};
+      df32 s1{0.f, 0.f}, s0{0.f, 0.f};
+      if constexpr (DF64) phi_affine_coeffs<FAM>(L.cw, ia, xa, s1, s0);
       for (int q = qs; q < a; q += Q) {
         const int i = p * a + q;
         V f;
         df32 fdf{0.f, 0.f};
         if constexpr (DF64) {
-          const df32 u = df_add(df_mul_f(ia, (float)q), xa);
-          fdf = phi_df<FAM>(u, L.cw, L.ic, sh.exp2tab);
+          fdf = phi_df_affine<FAM>(s1, s0, (float)q, L.ic, sh.exp2tab);
         } else {
           f = phi<FAM, F32>(((double)q + xi_p) * inv_a, ap);
         }
@@ -355,6 +386,8 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, const 
   if constexpr (DF64) {
     if (tabulated) {
       const df32 ia{sh.iadf.x, sh.iadf.y};
+      df32 s1, s0;  // the last axis' points are s/a: no node offset
+      phi_affine_coeffs<FAM>(LL.cw, ia, df32{0.f, 0.f}, s1, s0);
       DfAcc acc;
       for (int s = tid; s < n_last; s += B) {
         const float2 *F = (const float2 *)Ftab + s;
@@ -365,8 +398,7 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, const 
           const float4 gt = sh.Gdf[sb][t];
           dacc_prod(ag, df32{l.x, l.y}, df32{gt.x, gt.y});
         }
-        const df32 u = df_mul_f(ia, (float)s);
-        dacc_prod(acc, phi_df<FAM>(u, LL.cw, LL.ic, sh.exp2tab), dacc_value(ag));
+        dacc_prod(acc, phi_df_affine<FAM>(s1, s0, (float)s, LL.ic, sh.exp2tab), dacc_value(ag));
       }
       const float4 tot = block_sum_df(dacc_value(acc), df32{0.f, 0.f}, sh.redf);
       if (tid == 0) *out_slot = ((double)tot.x + (double)tot.y) / (double)n_last;
