@@ -14,17 +14,20 @@
 // GB300 mapping (instead of walking the levels one by one on one SM):
 //   K0  basis table l_t(u_qp) of this a (a*P*P entries).
 //   K1  every M_k (and w) at once, one CTA per level, across the whole GPU.
-//   K2  one CTA runs the P x P chain forward (G_k, checkpointed every C levels,
-//       and the value) and, for the adjoint, backward:
-//           lambda_{d-1} = front * w,   lambda_{k-1} = lambda_k M_k
-//       (lambda_k = dQ/dG_k, checkpointed every C levels).
-//   K3  (adjoint) one CTA per level k recomputes G_{k-1} from the checkpoint
+//   K2  the levels are cut into groups of C (the checkpoint interval); one CTA
+//       per group multiplies its operators, R_g = M_top ... M_{gC+1}, so the
+//       P^3-per-level work runs on many SMs at once.
+//   K3  one CTA runs the short chain over the groups forward (G at every group
+//       boundary -- the checkpoints -- and the value) and, for the adjoint,
+//       backward: lambda_{d-1} = front * w, lambda_{gC} = lambda_{top} R_g
+//       (lambda_k = dQ/dG_k).  The sequential part is ceil((d-1)/C) steps, not d.
+//   K4  (adjoint) one CTA per level k recomputes G_{k-1} from the checkpoint
 //       below and lambda_k from the checkpoint above -- the level states are not
 //       all stored -- and contracts
 //           dQ/dtheta_k = lambda_k (dM_k/dtheta_k) G_{k-1}
 //                       = (1/a) sum_{q,p} lambda_k[p] dphi_k(u_qp)/dtheta G~_{k-1}(u_qp),
 //       theta_k = (c_k, w_k); level d uses the points s/n_last.  For OSC the
-//       phase derivative dQ/du = Re(2 pi i Q) comes from K2.
+//       phase derivative dQ/du = Re(2 pi i Q) comes from K3.
 #include <algorithm>
 
 #include "mdi_common.cuh"
@@ -36,26 +39,30 @@ namespace mdi {
 constexpr int kLvThreads = 256;
 constexpr int kLvMaxPts = kNodesAMax * kNodesPMax;  // a*P <= 2048
 
+// Groups: g = 0..ng-1 covers levels gC+1 .. min((g+1)C, d-1); boundary b_g = gC
+// for g < ng and b_ng = d-1.  gck[g] = G at b_g, lck[g] = lambda at b_g.
 struct LevelsLayout {
-  size_t table, M, w, gck, lck, misc, total;
-  int C, nck;  // checkpoint interval and slots
+  size_t table, M, R, w, gck, lck, misc, total;
+  int C, ng;  // checkpoint interval (= group length) and number of groups
 };
 
 static LevelsLayout levels_layout(int d, int64_t a, int P, int C) {
   LevelsLayout L{};
   L.C = C;
-  L.nck = (d - 1) / C + 1;
+  L.ng = (d - 1 + C - 1) / C;
   size_t off = 0;
   L.table = off;
   off += align_up(sizeof(double) * (size_t)a * P * P);
   L.M = off;
   off += align_up(sizeof(double2) * (size_t)std::max(d - 1, 1) * P * P);
+  L.R = off;
+  if (C > 1) off += align_up(sizeof(double2) * (size_t)std::max(L.ng, 1) * P * P);
   L.w = off;
   off += align_up(sizeof(double2) * P);
   L.gck = off;
-  off += align_up(sizeof(double2) * (size_t)L.nck * P);
+  off += align_up(sizeof(double2) * (size_t)(L.ng + 1) * P);
   L.lck = off;
-  off += align_up(sizeof(double2) * (size_t)(L.nck + 1) * P);
+  off += align_up(sizeof(double2) * (size_t)(L.ng + 1) * P);
   L.misc = off;
   off += align_up(4 * sizeof(double2));
   L.total = off;
@@ -68,27 +75,23 @@ static int default_checkpoint(int d) {
   return c;
 }
 
-// K0: L[t][q*P + p] = l_t((q + xi_p)/a) for one a.
+// K0: L[t][q*P + p] = l_t((q + xi_p)/a) for one a.  One warp per point u: lane t
+// forms bw_t / (u - xi_t), a shuffle sum gives the denominator, so each lane
+// does two FP64 divisions (the FP64 unit is the scarce one on this chip).
 __global__ void levels_table_kernel(int P, int a, double *__restrict__ L) {
-  __shared__ double s_xi[kNodesPMax], s_bw[kNodesPMax];
-  for (int t = threadIdx.x; t < P; t += blockDim.x) {
-    s_xi[t] = cheb_node(t, P);
-    s_bw[t] = cheb_weight(t, P);
-  }
-  __syncthreads();
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int pt = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
   const int npts = a * P;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npts; i += gridDim.x * blockDim.x) {
-    const int q = i / P, p = i % P;
-    const double u = ((double)q + s_xi[p]) / (double)a;
-    double den = 0.0;
-    int hit = -1;
-    for (int t = 0; t < P; ++t) {
-      if (u == s_xi[t]) hit = t;
-      else den += s_bw[t] / (u - s_xi[t]);
-    }
-    for (int t = 0; t < P; ++t)
-      L[(size_t)t * npts + i] = hit >= 0 ? (t == hit ? 1.0 : 0.0) : (s_bw[t] / (u - s_xi[t])) / den;
-  }
+  if (pt >= npts) return;  // whole warps
+  const int q = pt / P, p = pt % P;
+  const double u = ((double)q + cheb_node(p, P)) / (double)a;
+  const bool on = lane < P;
+  const double xi = on ? cheb_node(lane, P) : 0.0;
+  const unsigned hit = __ballot_sync(0xffffffffu, on && u == xi);
+  const double r = (on && !hit) ? cheb_weight(lane, P) / (u - xi) : 0.0;
+  double den = r;
+  for (int off = kWarp / 2; off > 0; off >>= 1) den += __shfl_xor_sync(0xffffffffu, den, off);
+  if (on) L[(size_t)lane * npts + pt] = hit ? (lane == __ffs(hit) - 1 ? 1.0 : 0.0) : r / den;
 }
 
 // Barycentric basis value l_t(u) with the nodes and weights in shared memory.
@@ -136,7 +139,7 @@ __global__ void __launch_bounds__(kLvThreads) levels_build_kernel(int d, int a, 
           const double l = Lt[q * P];
           const double2 f = s_f[q * P + p];
           acc.x = fma(l, f.x, acc.x);
-          acc.y = fma(l, f.y, acc.y);
+          if constexpr (FAM == MDI_FAM_OSC) acc.y = fma(l, f.y, acc.y);
         }
         Mk[o] = c_scale(acc, inv_a);
       }
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(kLvThreads) levels_build_kernel(int d, int a, 
           const double2 f = as2(phi<FAM, F32>(u, ap));
           const double l = (d == 1) ? (t == 0 ? 1.0 : 0.0) : basis_at(s_xi, s_bw, P, t, u);
           acc.x = fma(l, f.x, acc.x);
-          acc.y = fma(l, f.y, acc.y);
+          if constexpr (FAM == MDI_FAM_OSC) acc.y = fma(l, f.y, acc.y);
         }
       }
       s_part[threadIdx.x] = acc;
@@ -168,12 +171,8 @@ __global__ void __launch_bounds__(kLvThreads) levels_build_kernel(int d, int a, 
   (void)sizeof(V);
 }
 
-// K2: forward chain with checkpoints and the value; backward chain for the adjoint.
-// One CTA: P threads do the P x P products while all threads stage the operators
-// of the next kChainLevels levels into shared memory with cp.async (hardware
-// wait_group, double-buffered), so no level waits on an L2 round trip.  Real
-// families use real arithmetic on the real parts.  misc[0] = Q before the front
-// factor.
+// cp.async helpers for staging operators into shared memory (hardware
+// wait_group, double-buffered), so no product waits on an L2 round trip.
 constexpr int kChainMaxThreads = 1024;  // P x G thread grid, G = the power of two >= P
 constexpr int kChainSmem = 64 * 1024;  // two buffers of operators
 
@@ -185,11 +184,11 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// Operators M_first .. M_first+cnt-1 (1-based levels) -> dst, one 16-byte copy each.
-// M is stored [t][p]; `transpose` stages each operator as [p][t].
-__device__ __forceinline__ void stage_ops(double2 *dst, const double2 *M, int first, int cnt, int P, bool transpose) {
+// Operators ops_first .. ops_first+cnt-1 (1-based) -> dst, one 16-byte copy each.
+// Operators are stored [t][p]; `transpose` stages each one as [p][t].
+__device__ __forceinline__ void stage_ops(double2 *dst, const double2 *ops, int first, int cnt, int P, bool transpose) {
   const int n = cnt * P * P, pp = P * P;
-  const double2 *src = M + (size_t)(first - 1) * pp;
+  const double2 *src = ops + (size_t)(first - 1) * pp;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     int j = i;
     if (transpose) {
@@ -199,6 +198,54 @@ __device__ __forceinline__ void stage_ops(double2 *dst, const double2 *M, int fi
     cp_async16(dst + j, src + i);
   }
   cp_async_commit();
+}
+
+// K2: R_g = M_hi ... M_lo for the levels lo = gC+1 .. hi = min((g+1)C, d-1) of
+// group g = blockIdx.x.  Thread (p, t) forms entry (p, t) of each partial product
+// R' = M_k R, R'[p][t] = sum_s M_k[p][s] R[s][t], from the operator staged in
+// shared memory (the next one is in flight meanwhile) and R in shared memory,
+// [s][t] row-major.  R_g is written [t][p] like the operators.
+constexpr int kGroupMaxThreads = kNodesPMax * kNodesPMax;
+
+template <int FAM>
+__global__ void __launch_bounds__(kGroupMaxThreads) levels_group_kernel(int d, int P, int C,
+                                                                     const double2 *__restrict__ M,
+                                                                     double2 *__restrict__ R) {
+  extern __shared__ __align__(16) unsigned char group_smem[];
+  const int pp = P * P;
+  double2 *const sM = (double2 *)group_smem;  // two staged operators
+  double2 *const sR = sM + 2 * pp;             // two partial products
+  const int g = blockIdx.x;
+  const int lo = g * C + 1, hi = min((g + 1) * C, d - 1);
+  const int i = threadIdx.x, p = i / P, t = i % P;
+  const bool on = i < pp;
+  if (on) sR[p * P + t] = M[(size_t)(lo - 1) * pp + t * P + p];  // R = M_lo
+  if (lo + 1 <= hi) stage_ops(sM, M, lo + 1, 1, P, false);
+  int cur = 0;
+  for (int k = lo + 1; k <= hi; ++k) {
+    const int j = (k - lo - 1) & 1;
+    if (k + 1 <= hi) {
+      stage_ops(sM + (j ^ 1) * pp, M, k + 1, 1, P, false);
+      cp_async_wait_prev();
+    } else {
+      cp_async_wait_all();
+    }
+    __syncthreads();
+    if (on) {
+      const double2 *Mk = sM + j * pp;
+      const double2 *Rc = sR + cur * pp;
+      double2 acc = make_double2(0.0, 0.0);
+      if constexpr (FAM == MDI_FAM_OSC) {
+        for (int s = 0; s < P; ++s) acc = c_add(acc, c_mul(Mk[s * P + p], Rc[s * P + t]));
+      } else {
+        for (int s = 0; s < P; ++s) acc.x = fma(Mk[s * P + p].x, Rc[s * P + t].x, acc.x);
+      }
+      sR[(cur ^ 1) * pp + p * P + t] = acc;
+    }
+    cur ^= 1;
+    __syncthreads();
+  }
+  if (on) R[(size_t)g * pp + t * P + p] = sR[cur * pp + p * P + t];
 }
 
 // Sum of v over aligned groups of G lanes (G a power of two <= 32); the result is
@@ -227,10 +274,16 @@ static int chain_levels_per_chunk(int P) {
   return std::max(1, std::min(8, kChainSmem / 2 / (P * P * (int)sizeof(double2))));
 }
 
+// K3: the chain over the ng group operators (R_g, or M_k when C = 1), forward
+// with a checkpoint at every group boundary and the value, backward for the
+// adjoint.  One CTA: a P x G thread grid does each matrix-vector product (one
+// multiply per thread, summed over the G lanes of a row) while all threads stage
+// the next chunk of operators with cp.async.  Real families use real arithmetic
+// on the real parts.  misc[0] = Q before the front factor.
 template <int FAM>
-__global__ void __launch_bounds__(kChainMaxThreads) levels_chain_kernel(int d, int P, int C, int LC,
+__global__ void __launch_bounds__(kChainMaxThreads) levels_chain_kernel(int d, int ng, int P, int LC,
                                                                      const double *__restrict__ prm,
-                                                                     const double2 *__restrict__ M,
+                                                                     const double2 *__restrict__ ops,
                                                                      const double2 *__restrict__ w,
                                                                      double2 *__restrict__ gck,
                                                                      double2 *__restrict__ lck,
@@ -239,10 +292,9 @@ __global__ void __launch_bounds__(kChainMaxThreads) levels_chain_kernel(int d, i
                                                                      double *__restrict__ grad, int adjoint) {
   using V = typename FamTraits<FAM>::V;
   extern __shared__ __align__(16) unsigned char chain_smem[];
-  double2 *buf[2] = {(double2 *)chain_smem, (double2 *)chain_smem + (size_t)LC * P * P};
+  double2 *const buf0 = (double2 *)chain_smem;  // two chunks of LC operators
+  const size_t bstride = (size_t)LC * P * P;
   __shared__ V s_v[kNodesPMax], s_n[kNodesPMax];
-  // Thread grid: row = threadIdx.x / G, col = threadIdx.x % G; one product per thread,
-  // summed over the G lanes of a row.
   const int G = chain_group(P);
   const int row = threadIdx.x / G, col = threadIdx.x % G;
   const bool cell = row < P && col < P;
@@ -255,29 +307,28 @@ __global__ void __launch_bounds__(kChainMaxThreads) levels_chain_kernel(int d, i
   if (on) s_v[p] = VOps<V>::one();
   __syncthreads();
   if (on) gck[p] = as2(s_v[p]);
-  const int nlev = d - 1;
-  const int nchunks = (nlev + LC - 1) / LC;
-  // Forward: chunk c holds levels 1 + c*LC .. min(d-1, (c+1)*LC), staged as [p][t].
-  // G_k[p] = sum_t M_k[p][t] G_{k-1}[t]: row = p, col = t.
-  if (nchunks > 0) stage_ops(buf[0], M, 1, std::min(LC, nlev), P, true);
+  const int nchunks = (ng + LC - 1) / LC;
+  // Forward: chunk c holds operators 1 + c*LC .. min(ng, (c+1)*LC), staged as [p][t].
+  // S_k[p] = sum_t R_k[p][t] S_{k-1}[t]: row = p, col = t.
+  if (nchunks > 0) stage_ops(buf0, ops, 1, std::min(LC, ng), P, true);
   for (int c = 0; c < nchunks; ++c) {
-    const int k0 = 1 + c * LC, k1 = std::min(nlev, (c + 1) * LC);
+    const int k0 = 1 + c * LC, k1 = std::min(ng, (c + 1) * LC);
     if (c + 1 < nchunks) {
       const int n0 = k1 + 1;
-      stage_ops(buf[(c + 1) & 1], M, n0, std::min(LC, nlev - n0 + 1), P, true);
+      stage_ops(buf0 + ((c + 1) & 1) * bstride, ops, n0, std::min(LC, ng - n0 + 1), P, true);
       cp_async_wait_prev();
     } else {
       cp_async_wait_all();
     }
     __syncthreads();
-    const double2 *B = buf[c & 1];
+    const double2 *B = buf0 + (c & 1) * bstride;
     for (int k = k0; k <= k1; ++k) {
-      const double2 *Mk = B + (size_t)(k - k0) * P * P;
-      V prod = cell ? mul(Mk[row * P + col], s_v[col]) : VOps<V>::zero();
+      const double2 *Rk = B + (size_t)(k - k0) * P * P;
+      V prod = cell ? mul(Rk[row * P + col], s_v[col]) : VOps<V>::zero();
       prod = group_sum(prod, G);
       if (cell && col == 0) {
         s_n[row] = prod;
-        if (k % C == 0) gck[(size_t)(k / C) * P + row] = as2(prod);
+        gck[(size_t)k * P + row] = as2(prod);
       }
       __syncthreads();
       if (on) s_v[p] = s_n[p];
@@ -304,41 +355,38 @@ __global__ void __launch_bounds__(kChainMaxThreads) levels_chain_kernel(int d, i
   }
   if (!adjoint) return;
   __syncthreads();
-  // lambda_{d-1} = front * w; lck[nck] holds it, lck[j] holds lambda_{jC}.  The
-  // adjoint of a real family is real (front = 1, w real).
-  const int nck = (d - 1) / C + 1;
+  // lambda at b_ng = d-1 is front * w (real for real families: front = 1, w real).
   if (on) {
     const double2 l = c_mul(front, w[p]);
     s_v[p] = from2<V>(l);
-    lck[(size_t)nck * P + p] = l;
-    if ((d - 1) % C == 0) lck[(size_t)((d - 1) / C) * P + p] = l;
+    lck[(size_t)ng * P + p] = l;
   }
   __syncthreads();
-  // Backward: chunk c holds levels max(1, top - LC + 1) .. top, top = d-1 - c*LC,
-  // staged as stored ([t][p]).  lambda_{k-1}[t] = sum_p lambda_k[p] M_k[p][t]:
+  // Backward: chunk c holds operators max(1, top - LC + 1) .. top, top = ng - c*LC,
+  // staged as stored ([t][p]).  Lambda_{k-1}[t] = sum_p Lambda_k[p] R_k[p][t]:
   // row = t, col = p.
   if (nchunks > 0) {
-    const int top = nlev, bot = std::max(1, top - LC + 1);
-    stage_ops(buf[0], M, bot, top - bot + 1, P, false);
+    const int top = ng, bot = std::max(1, top - LC + 1);
+    stage_ops(buf0, ops, bot, top - bot + 1, P, false);
   }
   for (int c = 0; c < nchunks; ++c) {
-    const int top = nlev - c * LC, bot = std::max(1, top - LC + 1);
+    const int top = ng - c * LC, bot = std::max(1, top - LC + 1);
     if (c + 1 < nchunks) {
       const int ntop = bot - 1, nbot = std::max(1, ntop - LC + 1);
-      stage_ops(buf[(c + 1) & 1], M, nbot, ntop - nbot + 1, P, false);
+      stage_ops(buf0 + ((c + 1) & 1) * bstride, ops, nbot, ntop - nbot + 1, P, false);
       cp_async_wait_prev();
     } else {
       cp_async_wait_all();
     }
     __syncthreads();
-    const double2 *B = buf[c & 1];
+    const double2 *B = buf0 + (c & 1) * bstride;
     for (int k = top; k >= bot; --k) {
-      const double2 *Mk = B + (size_t)(k - bot) * P * P;
-      V prod = cell ? mul(Mk[row * P + col], s_v[col]) : VOps<V>::zero();
+      const double2 *Rk = B + (size_t)(k - bot) * P * P;
+      V prod = cell ? mul(Rk[row * P + col], s_v[col]) : VOps<V>::zero();
       prod = group_sum(prod, G);
       if (cell && col == 0) {
         s_n[row] = prod;
-        if ((k - 1) % C == 0) lck[(size_t)((k - 1) / C) * P + row] = as2(prod);
+        lck[(size_t)(k - 1) * P + row] = as2(prod);
       }
       __syncthreads();
       if (on) s_v[p] = s_n[p];
@@ -347,7 +395,30 @@ __global__ void __launch_bounds__(kChainMaxThreads) levels_chain_kernel(int d, i
   }
 }
 
-// K3: gradient of level k (block k-1, k = 1..d).
+// Product of a level operator (stored [t][p]: entry (p, t) at t*P + p) with a
+// vector in shared memory: out[p] = sum_t Op[p][t] in[t], or with TRANSPOSE
+// out[t] = sum_p in[p] Op[p][t].  Eight lanes per output, each summing every
+// eighth term, then three shuffle rounds; the outputs are spread over P/4 warps
+// so every SM sub-partition's FP64 unit takes a share (the FP64 rate of one warp
+// is the bottleneck otherwise).  Threads past the last whole warp skip.
+template <typename V, bool TRANSPOSE>
+__device__ __forceinline__ void matvec8(const double2 *__restrict__ Op, const V *in, V *out, int P) {
+  const int i = threadIdx.x, row = i >> 3, part = i & 7;
+  if (i >= ((P * 8 + kWarp - 1) & ~(kWarp - 1))) return;
+  V acc = VOps<V>::zero();
+  if (row < P) {
+    for (int t = part; t < P; t += 8) {
+      const double2 m = TRANSPOSE ? Op[row * P + t] : Op[t * P + row];
+      if constexpr (sizeof(V) == sizeof(double2)) acc = c_add(acc, c_mul(m, in[t]));
+      else acc = fma(m.x, in[t], acc);
+    }
+  }
+  acc = group_sum(acc, 8);
+  if (row < P && part == 0) out[row] = acc;
+}
+
+// K4: gradient of level k (block k-1, k = 1..d).  Real families run in real
+// arithmetic (the operators' imaginary parts are zero).
 template <int FAM>
 __global__ void __launch_bounds__(kLvThreads) levels_grad_kernel(int d, int a, int n_last, int P, int C,
                                                                  const double *__restrict__ prm,
@@ -356,14 +427,15 @@ __global__ void __launch_bounds__(kLvThreads) levels_grad_kernel(int d, int a, i
                                                                  const double2 *__restrict__ gck,
                                                                  const double2 *__restrict__ lck,
                                                                  double *__restrict__ grad) {
+  using V = typename FamTraits<FAM>::V;
   __shared__ double s_xi[kNodesPMax], s_bw[kNodesPMax];
-  __shared__ double2 s_g[kNodesPMax], s_l[kNodesPMax], s_n[kNodesPMax];
-  __shared__ double2 s_red[kLvThreads / kWarp];
+  __shared__ V s_g[2][kNodesPMax], s_l[2][kNodesPMax];
+  __shared__ V s_red[kLvThreads / kWarp];
   for (int t = threadIdx.x; t < P; t += blockDim.x) {
     s_xi[t] = cheb_node(t, P);
     s_bw[t] = cheb_weight(t, P);
   }
-  const int nck = (d - 1) / C + 1;
+  const int ng = (d - 1 + C - 1) / C;
   const int npts = a * P;
   const double inv_a = 1.0 / (double)a;
   double2 front = make_double2(1.0, 0.0);
@@ -372,24 +444,20 @@ __global__ void __launch_bounds__(kLvThreads) levels_grad_kernel(int d, int a, i
     sincos(kTwoPi * prm[d], &sn, &cs);
     front = make_double2(cs, sn);
   }
+  const int tid = threadIdx.x;
   for (int k = blockIdx.x + 1; k <= d; k += gridDim.x) {
-    // G_{k-1} from the checkpoint at or below it.
+    // G_{k-1} from the checkpoint at or below it (ping-pong buffers).
     const int j0 = (k - 1) / C;
-    if (threadIdx.x < P) s_g[threadIdx.x] = gck[(size_t)j0 * P + threadIdx.x];
+    int cg = 0;
+    if (tid < P) s_g[0][tid] = from2<V>(gck[(size_t)j0 * P + tid]);
     __syncthreads();
     for (int m = j0 * C + 1; m <= k - 1; ++m) {
-      const double2 *Mm = M + (size_t)(m - 1) * P * P;
-      if (threadIdx.x < P) {
-        double2 acc = make_double2(0.0, 0.0);
-        for (int t = 0; t < P; ++t) acc = c_add(acc, c_mul(Mm[t * P + threadIdx.x], s_g[t]));
-        s_n[threadIdx.x] = acc;
-      }
-      __syncthreads();
-      if (threadIdx.x < P) s_g[threadIdx.x] = s_n[threadIdx.x];
+      matvec8<V, false>(M + (size_t)(m - 1) * P * P, s_g[cg], s_g[cg ^ 1], P);
+      cg ^= 1;
       __syncthreads();
     }
-    const int tid = threadIdx.x;
-    double2 acc_c = make_double2(0.0, 0.0), acc_w = make_double2(0.0, 0.0);
+    const V *g_k = s_g[cg];
+    V acc_c = VOps<V>::zero(), acc_w = VOps<V>::zero();
     const AxisParams ap = load_axis(prm, d, k - 1);
     if (k < d) {
       // lambda_k from the checkpoint at or above it.
@@ -397,50 +465,40 @@ __global__ void __launch_bounds__(kLvThreads) levels_grad_kernel(int d, int a, i
       const double2 *src;
       if (top > d - 1) {
         top = d - 1;
-        src = lck + (size_t)nck * P;
+        src = lck + (size_t)ng * P;
       } else {
         src = lck + (size_t)(top / C) * P;
       }
-      if (tid < P) s_l[tid] = src[tid];
+      int cl = 0;
+      if (tid < P) s_l[0][tid] = from2<V>(src[tid]);
       __syncthreads();
       for (int m = top; m >= k + 1; --m) {
-        const double2 *Mm = M + (size_t)(m - 1) * P * P;
-        if (tid < P) {
-          double2 acc = make_double2(0.0, 0.0);
-          for (int q = 0; q < P; ++q) acc = c_add(acc, c_mul(s_l[q], Mm[tid * P + q]));
-          s_n[tid] = acc;
-        }
-        __syncthreads();
-        if (tid < P) s_l[tid] = s_n[tid];
+        matvec8<V, true>(M + (size_t)(m - 1) * P * P, s_l[cl], s_l[cl ^ 1], P);
+        cl ^= 1;
         __syncthreads();
       }
+      const V *l_k = s_l[cl];
       for (int i = tid; i < npts; i += blockDim.x) {
         const int q = i / P, p = i % P;
         const double u = ((double)q + s_xi[p]) * inv_a;
         const PhiGrad<FAM> pg = phi_grad64<FAM>(u, ap);
-        double2 g = make_double2(0.0, 0.0);
-        if (k == 1) {
-          g = make_double2(1.0, 0.0);
-        } else {
-          for (int t = 0; t < P; ++t) {
-            const double l = L[(size_t)t * npts + i];
-            g.x = fma(l, s_g[t].x, g.x);
-            g.y = fma(l, s_g[t].y, g.y);
-          }
+        V g = VOps<V>::one();
+        if (k > 1) {
+          g = VOps<V>::zero();
+          for (int t = 0; t < P; ++t) g = VOps<V>::fma_s(L[(size_t)t * npts + i], g_k[t], g);
         }
-        const double2 lg = c_mul(s_l[p], g);
-        acc_c = c_add(acc_c, c_mul(lg, as2(pg.dc)));
-        acc_w = c_add(acc_w, c_mul(lg, as2(pg.dw)));
+        const V lg = VOps<V>::mul(l_k[p], g);
+        acc_c = VOps<V>::add(acc_c, VOps<V>::mul(lg, pg.dc));
+        acc_w = VOps<V>::add(acc_w, VOps<V>::mul(lg, pg.dw));
       }
     } else {
       // last level: dQ/dtheta_d = Re(front (1/n_last) sum_s dphi_d(s/n_last) G~_{d-1}(s/n_last))
       for (int s = tid; s < n_last; s += blockDim.x) {
         const double u = (double)s / (double)n_last;
         const PhiGrad<FAM> pg = phi_grad64<FAM>(u, ap);
-        double2 g = make_double2(0.0, 0.0);
-        if (d == 1) {
-          g = make_double2(1.0, 0.0);
-        } else {
+        V g = VOps<V>::one();
+        if (d > 1) {
+          V num = VOps<V>::zero();
           double den = 0.0;
           int hit = -1;
           for (int t = 0; t < P; ++t) {
@@ -450,22 +508,21 @@ __global__ void __launch_bounds__(kLvThreads) levels_grad_kernel(int d, int a, i
             }
             const double wt = s_bw[t] / (u - s_xi[t]);
             den += wt;
-            g.x = fma(wt, s_g[t].x, g.x);
-            g.y = fma(wt, s_g[t].y, g.y);
+            num = VOps<V>::fma_s(wt, g_k[t], num);
           }
-          g = hit >= 0 ? s_g[hit] : c_scale(g, 1.0 / den);
+          g = hit >= 0 ? g_k[hit] : VOps<V>::scale(num, 1.0 / den);
         }
-        const double2 fg = c_mul(front, g);
-        acc_c = c_add(acc_c, c_mul(fg, as2(pg.dc)));
-        acc_w = c_add(acc_w, c_mul(fg, as2(pg.dw)));
+        const V fg = from2<V>(c_mul(front, as2(g)));
+        acc_c = VOps<V>::add(acc_c, VOps<V>::mul(fg, pg.dc));
+        acc_w = VOps<V>::add(acc_w, VOps<V>::mul(fg, pg.dw));
       }
     }
-    const double2 tc = block_sum(acc_c, s_red);
-    const double2 tw = block_sum(acc_w, s_red);
+    const V tc = block_sum(acc_c, s_red);
+    const V tw = block_sum(acc_w, s_red);
     if (tid == 0) {
       const double scale = (k < d) ? inv_a : 1.0 / (double)n_last;
-      grad[k - 1] = tc.x * scale;
-      if (FAM != MDI_FAM_OSC) grad[d + k - 1] = tw.x * scale;
+      grad[k - 1] = as2(tc).x * scale;
+      if (FAM != MDI_FAM_OSC) grad[d + k - 1] = as2(tw).x * scale;
     }
     __syncthreads();
   }
@@ -488,27 +545,39 @@ static mdi_status run_levels(int d, int a, int n_last, const double *params, con
   double2 *M = (double2 *)(base + Lo.M), *w = (double2 *)(base + Lo.w);
   double2 *gck = (double2 *)(base + Lo.gck), *lck = (double2 *)(base + Lo.lck), *misc = (double2 *)(base + Lo.misc);
   const int P = cfg.P;
-  levels_table_kernel<<<std::max(1, (a * P + 255) / 256), 256, 0, stream>>>(P, a, L);
+  levels_table_kernel<<<(a * P + 7) / 8, 8 * kWarp, 0, stream>>>(P, a, L);
   mdi_status st = check_launch();
   if (st != MDI_OK) return st;
   const int grid = std::min(d, sm_count() * 8);
   levels_build_kernel<FAM, F32><<<grid, kLvThreads, 0, stream>>>(d, a, n_last, P, params, L, M, w);
   if ((st = check_launch()) != MDI_OK) return st;
-  static bool chain_attr = false;
-  if (!chain_attr) {
+  static bool attrs = false;
+  if (!attrs) {
     cudaError_t e = cudaFuncSetAttribute(levels_chain_kernel<FAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kChainSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(levels_group_kernel<FAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(4 * sizeof(double2) * kNodesPMax * kNodesPMax));
     if (e != cudaSuccess) {
       set_cuda_error(e);
       return MDI_ECUDA;
     }
-    chain_attr = true;
+    attrs = true;
+  }
+  // Group products (skipped when every group is one level: the operators are M).
+  const double2 *ops = M;
+  if (C > 1 && Lo.ng > 0) {
+    double2 *R = (double2 *)(base + Lo.R);
+    const size_t group_smem = 4 * sizeof(double2) * (size_t)P * P;
+    levels_group_kernel<FAM><<<Lo.ng, std::max(32, (P * P + 31) / 32 * 32), group_smem, stream>>>(d, P, C, M, R);
+    if ((st = check_launch()) != MDI_OK) return st;
+    ops = R;
   }
   const int LC = chain_levels_per_chunk(P);
   const size_t chain_smem = 2 * (size_t)LC * P * P * sizeof(double2);
   const int chain_threads = std::max(32, (P * chain_group(P) + 31) / 32 * 32);
-  levels_chain_kernel<FAM><<<1, chain_threads, chain_smem, stream>>>(d, P, C, LC, params, M, w, gck, lck, misc, value,
-                                                                     grad, grad ? 1 : 0);
+  levels_chain_kernel<FAM><<<1, chain_threads, chain_smem, stream>>>(d, Lo.ng, P, LC, params, ops, w, gck, lck, misc,
+                                                                     value, grad, grad ? 1 : 0);
   if ((st = check_launch()) != MDI_OK) return st;
   if (grad) {
     levels_grad_kernel<FAM><<<std::min(d, sm_count() * 8), kLvThreads, 0, stream>>>(d, a, n_last, P, C, params, L, M,
