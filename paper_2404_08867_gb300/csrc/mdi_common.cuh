@@ -194,9 +194,10 @@ __device__ __forceinline__ void dacc_prod(DfAcc &a, df32 x, df32 y) {
   const float e = __fmaf_rn(x.hi, y.hi, -p);
   const df32 t = two_sum(a.s, p);
   a.s = t.hi;
-  float c = __fmaf_rn(x.hi, y.lo, a.c);
-  c = __fmaf_rn(x.lo, y.hi, c);
-  a.c = __fadd_rn(c, __fadd_rn(e, t.lo));
+  // The term's low-order part first, then one addition into the running low sum,
+  // so the chain carried from term to term is one add on each of s and c.
+  const float lo = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, __fadd_rn(e, t.lo)));
+  a.c = __fadd_rn(a.c, lo);
 }
 __device__ __forceinline__ void dacc_add(DfAcc &a, df32 x) {
   const df32 t = two_sum(a.s, x.hi);
