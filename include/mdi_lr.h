@@ -231,6 +231,27 @@ mdi_status mdi_batch_plan(const mdi_batch_desc *descs, int32_t count, const mdi_
                           int32_t *order);
 
 /* ---------------------------------------------------------------------------
+ * Paper-table mode: the tensor midpoint rule on the grid of eq. (3.5),
+ *     Q = Re(front * prod_{i=1}^{d} (1/n_i) sum_{k<n_i} phi_i((k + 1/2)/n_i)),
+ * n_1 = ... = n_{d-1} = N, n_d = n_last, front = exp(2 pi i u) for OSC.  This is
+ * the rule whose relative errors the MDI-LR columns of Section 5 (Tables 2-1 to
+ * 3-3) print, with n_last = N or N + 1; the text's reading of MDI-LR (the
+ * transformed-lattice sum) is mdi_lr_integrate.  FP64.
+ *   family     EXP, OSC, GAUSS or PEAK (params as for mdi_lr_integrate)
+ *   params     DEVICE, 2*d doubles
+ *   out        DEVICE, one double
+ *   workspace  DEVICE, >= mdi_midpoint_workspace_size bytes, 256-byte aligned
+ * Three launches on `stream` (per-axis chunk sums across the GPU, per-axis
+ * reduction in chunk order, one fixed-tree product); no allocation.
+ * MDI_EINVAL for a bad family, d < 1, N < 1, n_last < 1 or a grid whose chunk
+ * count exceeds 2^30; MDI_EWORKSPACE for a missing, misaligned or short
+ * workspace.
+ * ------------------------------------------------------------------------- */
+mdi_status mdi_midpoint_integrate(int32_t family, int32_t d, int64_t N, int64_t n_last, const double *params,
+                                  double *out, void *workspace, size_t ws_bytes, mdi_stream_t stream);
+mdi_status mdi_midpoint_workspace_size(int32_t d, int64_t N, int64_t n_last, size_t *bytes);
+
+/* ---------------------------------------------------------------------------
  * Bit-exact view of the on-the-fly index generator used by the lattice kernel:
  * r_out[t*d + i] = (j0 + t) z_i mod n for t < count (DEVICE, count*d int64),
  * produced by the same incremental exact arithmetic the kernel uses.

@@ -25,6 +25,7 @@ __all__ = [
     "lattice_rule_integrate", "lattice_rule_workspace_size", "lattice_rule_integrate_noalloc", "mdi_lr_integrate", "mdi_lr_workspace_size",
     "mdi_lr_integrate_batched", "mdi_lr_batched_workspace_size", "mdi_lr_batched_prepare", "mdi_batch_plan", "mdi_debug_lattice_indices",
     "mdi_lr_grad", "mdi_lr_grad_workspace_size", "MDILR", "mdi_lr", "make_batch_descs", "MdiError", "FAMILY", "STATE", "PRECISION", "BATCH_DESC_DTYPE", "library_path",
+    "mdi_midpoint_integrate", "mdi_midpoint_workspace_size",
 ]
 
 
@@ -286,4 +287,33 @@ def mdi_debug_lattice_indices(n: int, z: Sequence[int], j0: int, count: int, dev
     st = _ffi.load().mdi_debug_lattice_indices(d, int(n), zz.ctypes.data_as(ctypes.c_void_p), int(j0), int(count),
                                                ctypes.c_void_p(out.data_ptr()), _stream(stream))
     _ffi.check(st, "mdi_debug_lattice_indices")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Paper-table mode: tensor midpoint rule on the grid (N, ..., N, n_last)
+# ---------------------------------------------------------------------------
+def mdi_midpoint_workspace_size(d: int, N: int, n_last: int) -> int:
+    b = ctypes.c_size_t()
+    _ffi.check(_ffi.load().mdi_midpoint_workspace_size(d, N, n_last, ctypes.byref(b)), "mdi_midpoint_workspace_size")
+    return b.value
+
+
+def mdi_midpoint_integrate(family, params: torch.Tensor, d: int, N: int, n_last: Optional[int] = None,
+                           out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
+                           stream=None) -> torch.Tensor:
+    """prod_i (1/n_i) sum_k phi_i((k + 1/2)/n_i) (real part, times exp(2 pi i u) for
+    OSC) on the grid n_1 = ... = n_{d-1} = N, n_d = n_last (default N): the rule
+    the paper's tables print.  Returns a 1-element float64 CUDA tensor."""
+    _dev_f64(params, "params")
+    n_last = N if n_last is None else n_last
+    if params.numel() < 2 * d:
+        raise ValueError("params must hold 2*d doubles")
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=params.device)
+    ws = _workspace(mdi_midpoint_workspace_size(d, N, n_last), params.device, workspace)
+    st = _ffi.load().mdi_midpoint_integrate(_fam(family), d, N, n_last, ctypes.c_void_p(params.data_ptr()),
+                                            ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                                            ws.numel(), _stream(stream))
+    _ffi.check(st, "mdi_midpoint_integrate")
     return out

@@ -45,6 +45,8 @@ SIGNATURES = {
     "mdi_lr_batched_prepare": (_I32, [_c.POINTER(MdiOpts), _P, _SZ, _P]),
     "mdi_batch_plan": (_I32, [_P, _I32, _c.POINTER(MdiOpts), _P]),
     "mdi_debug_lattice_indices": (_I32, [_I32, _I64, _P, _I64, _I64, _P, _P]),
+    "mdi_midpoint_integrate": (_I32, [_I32, _I32, _I64, _I64, _P, _P, _P, _SZ, _P]),
+    "mdi_midpoint_workspace_size": (_I32, [_I32, _I64, _I64, _c.POINTER(_SZ)]),
     "mdi_status_string": (_c.c_char_p, [_I32]),
     "mdi_last_cuda_error": (_c.c_char_p, []),
     "mdi_abi_version": (_I32, []),

@@ -219,6 +219,18 @@ mdi_status mdi_batch_plan(const mdi_batch_desc *descs, int32_t count, const mdi_
   return MDI_OK;
 }
 
+mdi_status mdi_midpoint_workspace_size(int32_t d, int64_t N, int64_t n_last, size_t *bytes) {
+  if (!bytes || d < 1 || N < 1 || n_last < 1) return MDI_EINVAL;
+  *bytes = midpoint_workspace_bytes(d, N, n_last);
+  return *bytes ? MDI_OK : MDI_EINVAL;
+}
+
+mdi_status mdi_midpoint_integrate(int32_t family, int32_t d, int64_t N, int64_t n_last, const double *params,
+                                  double *out, void *workspace, size_t ws_bytes, mdi_stream_t stream) {
+  if (!family_ok(family) || d < 1 || N < 1 || n_last < 1 || !params || !out) return MDI_EINVAL;
+  return midpoint_launch(family, d, N, n_last, params, out, workspace, ws_bytes, (cudaStream_t)stream);
+}
+
 mdi_status mdi_debug_lattice_indices(int32_t d, int64_t n, const int64_t *z, int64_t j0, int64_t count,
                                      int64_t *r_out, mdi_stream_t stream) {
   return lattice_indices_launch(d, n, z, j0, count, r_out, (cudaStream_t)stream);

@@ -23,6 +23,7 @@
 
 #include "mdi_common.cuh"
 #include "mdi_internal.h"
+#include "mdi_nodes.cuh"
 
 namespace mdi {
 
@@ -289,6 +290,75 @@ mdi_status closed_launch(int family, int d, int64_t a, int64_t n_last, const dou
     return MDI_EWORKSPACE;
   if (family == MDI_FAM_EXP) return run_closed_p<MDI_FAM_EXP>(precision, d, a, n_last, params, out, workspace, stream);
   return run_closed_p<MDI_FAM_OSC>(precision, d, a, n_last, params, out, workspace, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Paper-table mode: the tensor midpoint rule on the grid of eq. (3.5),
+//     Q = Re(front * prod_i (1/n_i) sum_{k<n_i} phi_i((k + 1/2)/n_i)),
+// with n_1 = ... = n_{d-1} = N and n_d = n_last: the rule whose errors the MDI-LR
+// columns of the paper's Section 5 tables print (Tests 3-6).  Any product-form
+// family.  Each axis factor is a level factor S_k of the pipeline above, so the
+// chunking, the per-level reduction in chunk order and the fixed-tree product are
+// shared; only the chunk sums differ.
+// ---------------------------------------------------------------------------
+template <int FAM>
+__global__ void __launch_bounds__(kChunkThreads) midpoint_chunk_kernel(int d, int64_t N, int64_t n_last, Chunks ch,
+                                                                       const double *__restrict__ params,
+                                                                       double2 *__restrict__ partS) {
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
+  const int nwarps = gridDim.x * blockDim.x / kWarp;
+  for (int c = warp_global; c < ch.total; c += nwarps) {
+    int k, j;
+    if (c < (d - 1) * ch.cpl) {
+      k = c / ch.cpl;
+      j = c % ch.cpl;
+    } else {
+      k = d - 1;
+      j = c - (d - 1) * ch.cpl;
+    }
+    const int64_t r = (k + 1 < d) ? N : n_last;
+    const int64_t q0 = (int64_t)j * kChunkQ, q1 = min(r, q0 + kChunkQ);
+    const double invr = 1.0 / (double)r;
+    const AxisParams ap = load_axis(params, d, k);
+    double2 s = make_double2(0.0, 0.0);
+    for (int64_t q = q0 + lane; q < q1; q += kWarp) s = c_add(s, as2(phi<FAM, false>(((double)q + 0.5) * invr, ap)));
+    s = warp_sum(s);
+    if (lane == 0) partS[c] = s;
+  }
+}
+
+size_t midpoint_workspace_bytes(int d, int64_t N, int64_t n_last) { return closed_workspace_bytes(d, N, n_last); }
+
+template <int FAM>
+static mdi_status run_midpoint(int d, int64_t N, int64_t n_last, const double *params, double *out, void *ws,
+                               cudaStream_t stream) {
+  const ClosedLayout L = closed_layout(d, N, n_last, false);
+  char *base = (char *)ws;
+  double2 *partS = (double2 *)(base + L.partS), *S = (double2 *)(base + L.S);
+  const Chunks ch = make_chunks(d, N, n_last);
+  midpoint_chunk_kernel<FAM><<<chunk_grid(ch), kChunkThreads, 0, stream>>>(d, N, n_last, ch, params, partS);
+  mdi_status st = check_launch();
+  if (st != MDI_OK) return st;
+  closed_reduce_kernel<false><<<std::max(1, std::min((d + 255) / 256, sm_count() * 4)), 256, 0, stream>>>(
+      d, N, n_last, ch, partS, partS, S, S);
+  if ((st = check_launch()) != MDI_OK) return st;
+  closed_product_kernel<FAM><<<1, kScanThreads, 0, stream>>>(d, params, S, out);
+  return check_launch();
+}
+
+mdi_status midpoint_launch(int family, int d, int64_t N, int64_t n_last, const double *params, double *out,
+                           void *workspace, size_t ws_bytes, cudaStream_t stream) {
+  if (!closed_sizes_ok(d, N, n_last)) return MDI_EINVAL;
+  if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < midpoint_workspace_bytes(d, N, n_last))
+    return MDI_EWORKSPACE;
+  switch (family) {
+    case MDI_FAM_EXP: return run_midpoint<MDI_FAM_EXP>(d, N, n_last, params, out, workspace, stream);
+    case MDI_FAM_OSC: return run_midpoint<MDI_FAM_OSC>(d, N, n_last, params, out, workspace, stream);
+    case MDI_FAM_GAUSS: return run_midpoint<MDI_FAM_GAUSS>(d, N, n_last, params, out, workspace, stream);
+    case MDI_FAM_PEAK: return run_midpoint<MDI_FAM_PEAK>(d, N, n_last, params, out, workspace, stream);
+    default: return MDI_EINVAL;
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -28,6 +28,11 @@ size_t closed_workspace_bytes(int d, int64_t a, int64_t n_last);  // 0 when the 
 mdi_status closed_launch(int family, int d, int64_t a, int64_t n_last, const double *params, int precision,
                          double *out, void *workspace, size_t ws_bytes, cudaStream_t stream);
 
+// Paper-table mode: tensor midpoint rule on the grid (N, ..., N, n_last).
+size_t midpoint_workspace_bytes(int d, int64_t N, int64_t n_last);  // 0 when the sizes are out of range
+mdi_status midpoint_launch(int family, int d, int64_t N, int64_t n_last, const double *params, double *out,
+                           void *workspace, size_t ws_bytes, cudaStream_t stream);
+
 size_t closed_grad_workspace_bytes(int d, int64_t a, int64_t n_last);
 mdi_status closed_grad_launch(int family, int d, int64_t a, int64_t n_last, const double *params, double *value,
                               double *grad, void *workspace, size_t ws_bytes, cudaStream_t stream);

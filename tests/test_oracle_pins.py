@@ -15,22 +15,9 @@ from scipy.special import fresnel
 
 from oracle import oracle as o
 
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-
-
-def _rows(name):
-    with open(os.path.join(GOLDEN, name)) as fh:
-        for line in fh:
-            line = line.split("#", 1)[0].strip()
-            if line:
-                yield line.split()
-
-
-def _one_unit(printed: str) -> float:
-    """One unit in the last printed digit of a value such as '7.7798e-3'."""
-    mant, exp = printed.lower().split("e")
-    decimals = len(mant.split(".")[1]) if "." in mant else 0
-    return 10.0 ** (int(exp) - decimals)
+from paper_tables import midpoint_case as _midpoint_case
+from paper_tables import one_unit as _one_unit
+from paper_tables import rows as _rows
 
 
 def _fresnel_unit():
@@ -99,20 +86,6 @@ def test_slr_reproduces_printed_errors(row):
 # ----------------------------------------------------------------------------
 # Tensor midpoint mode against the printed MDI-LR errors (Tables 2-1..3-3)
 # ----------------------------------------------------------------------------
-
-def _midpoint_case(integrand, d):
-    if integrand == "gauss":
-        return "gauss", np.full(d, 1.0 / math.sqrt(2.0)), np.zeros(d)
-    if integrand == "expalt":
-        return "exp", np.array([(-1.0) ** i for i in range(d)]), np.zeros(d)
-    if integrand == "peak":
-        return "peak", np.full(d, 1.0 / 0.9), np.full(d, 0.6)
-    if integrand == "cos2":
-        w = np.zeros(d)
-        w[0] = 1.0  # cos(2 pi u + ...) with u = 1
-        return "osc", np.full(d, 2.0), w
-    raise KeyError(integrand)
-
 
 @pytest.mark.parametrize("row", list(_rows("midpoint_printed.txt")),
                          ids=lambda r: f"T{r[0]}-{r[1]}-d{r[2]}-N{r[3]}")
