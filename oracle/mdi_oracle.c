@@ -627,3 +627,108 @@ int or_closed_form_grad(int fam, int d, const double *c, const double *w, double
   }
   return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Generating-vector criteria and searches (Section 2.2)                      */
+/* ------------------------------------------------------------------------- */
+
+/* Bernoulli polynomials on [0, 1] for the even alpha the criteria use. */
+static double bernoulli_poly(int alpha, double x) {
+  if (alpha == 2) return x * x - x + 1.0 / 6.0;
+  if (alpha == 4) return x * x * x * x - 2.0 * x * x * x + x * x - 1.0 / 30.0;
+  return NAN;
+}
+
+/* (-1)^(alpha/2 + 1) (2 pi)^alpha / alpha!, the coefficient of B_alpha in eq. (2.4). */
+static double p_alpha_coef(int alpha) {
+  double fact = 1.0;
+  for (int i = 2; i <= alpha; ++i) fact *= (double)i;
+  const double sign = ((alpha / 2 + 1) % 2 == 0) ? 1.0 : -1.0;
+  return sign * pow(2.0 * M_PI, (double)alpha) / fact;
+}
+
+/* P_alpha(z) by the finite form of eq. (2.4),
+ *   -1 + (1/n) sum_{k<n} prod_j (1 + C_alpha B_alpha({k z_j / n})),
+ * for alpha = 2 or 4.  The paper writes the k = 0 term apart as
+ * (1/n) prod_j (1 + 2 zeta(alpha)); it is the same term, C_alpha B_alpha(0) = 2 zeta(alpha). */
+double or_p_alpha(int alpha, int d, uint64_t n, const uint64_t *z) {
+  if ((alpha != 2 && alpha != 4) || d < 1 || n < 1) return NAN;
+  const double C = p_alpha_coef(alpha);
+  double sum = 0.0;
+  for (uint64_t k = 0; k < n; ++k) {
+    double prod = 1.0;
+    for (int j = 0; j < d; ++j)
+      prod *= 1.0 + C * bernoulli_poly(alpha, (double)mulmod(k, z[j] % n, n) / (double)n);
+    sum += prod;
+  }
+  return -1.0 + sum / (double)n;
+}
+
+/* Example 2's search: values[t] = P_alpha(z(a)) for a = a_first + t, t < count.  A
+ * candidate outside 1 <= a <= n-1 or with gcd(a, n) != 1 is not admissible and gets
+ * +inf.  *best_a = the first a attaining the smallest value (0 if none is admissible). */
+int or_korobov_search(int alpha, int d, uint64_t n, uint64_t a_first, uint64_t count, double *values,
+                      uint64_t *best_a) {
+  if (d < 1 || n < 1) return -1;
+  uint64_t *z = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)d);
+  double best = INFINITY;
+  *best_a = 0;
+  for (uint64_t t = 0; t < count; ++t) {
+    const uint64_t a = a_first + t;
+    if (a < 1 || a >= n || gcd_u64(a, n) != 1) {
+      values[t] = INFINITY;
+      continue;
+    }
+    or_korobov_z(d, a, n, z);
+    values[t] = or_p_alpha(alpha, d, n, z);
+    if (values[t] < best) {
+      best = values[t];
+      *best_a = a;
+    }
+  }
+  free(z);
+  return 0;
+}
+
+/* Squared shift-averaged worst-case error of a rank-1 lattice, eq. (2.12) in its
+ * second (product-weight) form,
+ *   -prod_j (1 + gamma_j beta) + (1/n) sum_{k<n} prod_j (1 + gamma_j [B_2({k z_j / n}) + beta]),
+ * beta = 0 for the unanchored Sobolev space, c^2 - c + 1/3 for the one anchored at c. */
+double or_wce2_shift(int d, uint64_t n, const uint64_t *z, const double *gamma, double beta) {
+  if (d < 1 || n < 1) return NAN;
+  double prod0 = 1.0, sum = 0.0;
+  for (int j = 0; j < d; ++j) prod0 *= 1.0 + gamma[j] * beta;
+  for (uint64_t k = 0; k < n; ++k) {
+    double prod = 1.0;
+    for (int j = 0; j < d; ++j)
+      prod *= 1.0 + gamma[j] * (bernoulli_poly(2, (double)mulmod(k, z[j] % n, n) / (double)n) + beta);
+    sum += prod;
+  }
+  return -prod0 + sum / (double)n;
+}
+
+/* Component-by-component construction of Example 3 with product weights: z_1 = 1; for
+ * s = 2..d, with z_1..z_{s-1} held fixed, z_s is the z in N_n = {1 <= z <= n-1,
+ * gcd(z, n) = 1} minimising the s-dimensional [E^(sh)]^2 of eq. (2.12) (the first such z
+ * on ties).  e2[s-1] receives that minimum; e2[0] is the value of z_1 = 1 alone. */
+int or_cbc(int d, uint64_t n, const double *gamma, double beta, uint64_t *z, double *e2) {
+  if (d < 1 || n < 2) return -1;
+  z[0] = 1;
+  e2[0] = or_wce2_shift(1, n, z, gamma, beta);
+  for (int s = 1; s < d; ++s) {
+    double best = INFINITY;
+    uint64_t best_z = 0;
+    for (uint64_t c = 1; c < n; ++c) {
+      if (gcd_u64(c, n) != 1) continue;
+      z[s] = c;
+      const double v = or_wce2_shift(s + 1, n, z, gamma, beta);
+      if (v < best) {
+        best = v;
+        best_z = c;
+      }
+    }
+    z[s] = best_z;
+    e2[s] = best;
+  }
+  return 0;
+}

@@ -4,7 +4,10 @@ The oracle (``mdi_oracle.c``) is a slow, obviously-correct restatement of the
 MDI-LR method of Zhong & Feng: the standard lattice rule of eq. (2.1)/(1.2), the
 transformed-grid rule of Lemma 3.2, the level sweeps of Algorithm 1 (m = 1)
 inside Algorithm 2, the tensor midpoint rule that reproduces the paper's printed
-MDI-LR error columns, and the exact integrals of the test integrands.  Only
+MDI-LR error columns, the exact integrals of the test integrands, and the
+generating-vector criteria of Section 2.2 (P_alpha of eq. (2.4) with the Korobov
+search of Example 2, the shift-averaged worst-case error of eq. (2.12) with the
+component-by-component construction of Example 3).  Only
 ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
 may import this module.  It shares no code with the CUDA library.
 
@@ -72,6 +75,10 @@ def _load():
                 "or_midpoint_product": (D, [I, I, P, P, P]),
                 "or_closed_form": (D, [I, I, P, P]),
                 "or_closed_form_grad": (I, [I, I, P, P, P]),
+                "or_p_alpha": (D, [I, I, U, P]),
+                "or_korobov_search": (I, [I, I, U, U, U, P, P]),
+                "or_wce2_shift": (D, [I, U, P, P, D]),
+                "or_cbc": (I, [I, U, P, D, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -225,3 +232,35 @@ def mdi_lr(family, d, a, nd, c, w=None, state="auto", P=16) -> float:
     if family in ("exp", "osc"):
         return mdi_closed(family, d, a, nd, c, w)
     return mdi_nodes(family, d, a, nd, P, c, w)
+
+
+# ---------------------------------------------------------------------------
+# Generating-vector criteria and searches (Section 2.2)
+# ---------------------------------------------------------------------------
+def p_alpha(alpha, d, n, z) -> float:
+    z = _u64(z)
+    return _load().or_p_alpha(alpha, d, n, _p(z))
+
+
+def korobov_search(alpha, d, n, a_first, count):
+    """(values, best_a): P_alpha(z(a)) for a = a_first .. a_first + count - 1 (+inf for
+    inadmissible a) and the first a attaining the minimum."""
+    vals = np.zeros(count)
+    best = np.zeros(1, dtype=np.uint64)
+    assert _load().or_korobov_search(alpha, d, n, a_first, count, _p(vals), _p(best)) == 0
+    return vals, int(best[0])
+
+
+def wce2_shift(d, n, z, gamma, beta=0.0) -> float:
+    z, g = _u64(z), _f64(gamma, d)
+    return _load().or_wce2_shift(d, n, _p(z), _p(g), beta)
+
+
+def cbc(d, n, gamma, beta=0.0):
+    """(z, e2): the component-by-component vector and the squared shift-averaged
+    worst-case error after each component."""
+    g = _f64(gamma, d)
+    z = np.zeros(d, dtype=np.uint64)
+    e2 = np.zeros(d)
+    assert _load().or_cbc(d, n, _p(g), beta, _p(z), _p(e2)) == 0
+    return z, e2

@@ -340,3 +340,107 @@ def test_nodes_grad_large_d_matches_central_difference():
             wp[t - d] += h; wm[t - d] -= h
         fd = (o.mdi_nodes("gauss", d, a, a, 16, cp, wp) - o.mdi_nodes("gauss", d, a, a, 16, cm, wm)) / (2 * h)
         assert gv == pytest.approx(fd, rel=1e-6, abs=1e-10)
+
+
+# ----------------------------------------------------------------------------
+# Generating-vector criteria of Section 2.2: P_alpha (eq. 2.4) and the
+# shift-averaged worst-case error (eq. 2.12), the Korobov search (Example 2) and
+# the CBC construction (Example 3)
+# ----------------------------------------------------------------------------
+ZETA = {2: math.pi ** 2 / 6.0, 4: math.pi ** 4 / 90.0}
+
+
+@pytest.mark.parametrize("alpha", [2, 4])
+@pytest.mark.parametrize("n", [1, 2, 7, 64, 1001])
+def test_p_alpha_one_dimension_closed_form(alpha, n):
+    """d = 1, z = (1): the dual lattice is nZ, so the defining sum is 2 zeta(alpha) / n^alpha."""
+    assert o.p_alpha(alpha, 1, n, [1]) == pytest.approx(2.0 * ZETA[alpha] / n ** alpha, rel=1e-12)
+
+
+@pytest.mark.parametrize("alpha", [2, 4])
+def test_p_alpha_degenerate_second_component(alpha):
+    """z = (1, 0): h . z = h_1, so the dual lattice is nZ x Z and the defining sum
+    factorises to (1 + 2 zeta / n^alpha)(1 + 2 zeta) - 1."""
+    n = 13
+    expect = (1.0 + 2.0 * ZETA[alpha] / n ** alpha) * (1.0 + 2.0 * ZETA[alpha]) - 1.0
+    assert o.p_alpha(alpha, 2, n, [1, 0]) == pytest.approx(expect, rel=1e-12)
+
+
+@pytest.mark.parametrize("n,z", [(5, [1, 2]), (7, [1, 3]), (11, [1, 4])])
+def test_p_alpha_equals_its_dual_lattice_definition(n, z):
+    """The finite form of eq. (2.4) against the definition, the sum of
+    1/(hbar_1 hbar_2)^4 over the nonzero h with h . z = 0 (mod n), taken over
+    |h_i| <= 300 (the omitted tail is below 2e-7)."""
+    H = 300
+    h = np.arange(-H, H + 1)
+    hb = np.maximum(1, np.abs(h)).astype(np.float64) ** -4
+    h1, h2 = np.meshgrid(h, h, indexing="ij")
+    mask = ((h1 * z[0] + h2 * z[1]) % n == 0) & ~((h1 == 0) & (h2 == 0))
+    brute = float((np.outer(hb, hb) * mask).sum())
+    assert abs(o.p_alpha(4, 2, n, z) - brute) < 5e-7
+
+
+def test_korobov_search_symmetries_and_argmin():
+    """P_alpha(z(a)) = P_alpha(z(n - a)) (B_alpha(1 - x) = B_alpha(x)) and
+    = P_alpha(z(a^-1 mod n)) (the same points with the coordinates reversed);
+    inadmissible a (gcd(a, n) > 1) are +inf; best_a attains the minimum."""
+    n, d = 210, 4
+    vals, best = o.korobov_search(2, d, n, 1, n - 1)
+    for a in range(1, n):
+        v = vals[a - 1]
+        if math.gcd(a, n) != 1:
+            assert v == math.inf
+            continue
+        assert v == pytest.approx(vals[n - a - 1], rel=1e-12, abs=1e-15)
+        assert v == pytest.approx(vals[pow(a, -1, n) - 1], rel=1e-12, abs=1e-15)
+    assert vals[best - 1] == vals[np.isfinite(vals)].min()
+
+
+@pytest.mark.parametrize("beta", [0.0, 1.0 / 12.0])
+def test_wce2_one_dimension_closed_form(beta):
+    """d = 1, z = (1): sum_{k<n} B_2(k/n) = 1/(6n), so [E^(sh)]^2 = gamma / (6 n^2) for
+    any beta (beta cancels against the leading product)."""
+    for n in (1, 3, 50, 997):
+        assert o.wce2_shift(1, n, [1], [0.7], beta) == pytest.approx(0.7 / (6.0 * n * n), rel=1e-11)
+
+
+@pytest.mark.parametrize("beta", [0.0, 0.25 - 0.5 + 1.0 / 3.0])
+def test_wce2_product_form_equals_subset_form(beta):
+    """The two sides of eq. (2.12): the sum over nonempty subsets nu of
+    gamma_nu ((1/n) sum_k prod_{j in nu} [B_2({k z_j/n}) + beta] - beta^|nu|), with
+    product weights gamma_nu = prod_{j in nu} gamma_j, equals the product form."""
+    n, z, gamma = 31, [1, 12, 7], [0.9, 0.6, 0.3]
+    k = np.arange(n)
+    x = [((k * zj) % n) / n for zj in z]
+    b2 = [xi * xi - xi + 1.0 / 6.0 for xi in x]
+    total = 0.0
+    for mask in range(1, 8):
+        nu = [j for j in range(3) if mask >> j & 1]
+        g = np.prod([gamma[j] for j in nu])
+        total += g * (np.mean(np.prod([b2[j] + beta for j in nu], axis=0)) - beta ** len(nu))
+    assert o.wce2_shift(3, n, z, gamma, beta) == pytest.approx(total, rel=1e-12)
+
+
+def test_cbc_components_minimise_against_exhaustive_subset_form():
+    """Each CBC component attains the minimum of the s-dimensional error over all
+    admissible z, evaluated here with the subset form of eq. (2.12); e2 holds those
+    minima; the error of the mirrored choice n - z_s is the same."""
+    n, d, beta = 53, 4, 0.0
+    gamma = [0.8 ** j for j in range(d)]
+    z, e2 = o.cbc(d, n, gamma, beta)
+    assert z[0] == 1
+    k = np.arange(n)
+    for s in range(1, d):
+        best = math.inf
+        for c in range(1, n):
+            zz = [int(v) for v in z[:s]] + [c]
+            x = [((k * zj) % n) / n for zj in zz]
+            b2 = [xi * xi - xi + 1.0 / 6.0 for xi in x]
+            tot = 0.0
+            for mask in range(1, 1 << (s + 1)):
+                nu = [j for j in range(s + 1) if mask >> j & 1]
+                tot += np.prod([gamma[j] for j in nu]) * np.mean(np.prod([b2[j] for j in nu], axis=0))
+            best = min(best, tot)
+        assert e2[s] == pytest.approx(best, rel=1e-10)
+        mirrored = [int(v) for v in z[:s]] + [n - int(z[s])]
+        assert o.wce2_shift(s + 1, n, mirrored, gamma, beta) == pytest.approx(e2[s], rel=1e-12)
