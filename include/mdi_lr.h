@@ -231,6 +231,41 @@ mdi_status mdi_batch_plan(const mdi_batch_desc *descs, int32_t count, const mdi_
                           int32_t *order);
 
 /* ---------------------------------------------------------------------------
+ * Generating-vector construction (Section 2.2), FP64.
+ *
+ * Korobov search, Example 2: for a = a_first .. a_first + count - 1,
+ *     values[t] = P_alpha(z(a)) = -1 + (1/n) sum_{k<n} prod_{j<d} (1 + C B_alpha({k a^j / n})),
+ * the finite form of eq. (2.4), C = (-1)^(alpha/2+1) (2 pi)^alpha / alpha!,
+ * alpha = 2 (B_2 = x^2 - x + 1/6) or 4 (B_4 = x^4 - 2x^3 + x^2 - 1/30).  A candidate
+ * with a < 1, a >= n or gcd(a, n) > 1 is not admissible: +inf.  best_a[0] = the
+ * smallest a attaining the least value (0 if none is admissible).  P_alpha is the
+ * same for a and n - a, and for a and its inverse mod n.
+ *   values  DEVICE, count doubles;  best_a  DEVICE, one int64.
+ * Two launches on `stream`, no workspace.  MDI_EINVAL unless alpha is 2 or 4,
+ * 1 <= d <= 256, 1 <= n <= 2^62, a_first >= 0 and count >= 1.  Work: count * n * d / 2.
+ * ------------------------------------------------------------------------- */
+mdi_status lattice_korobov_search(int32_t alpha, int32_t d, int64_t n, int64_t a_first, int64_t count,
+                                  double *values, int64_t *best_a, mdi_stream_t stream);
+
+/* Component-by-component construction, Example 3, with product weights: z[0] = 1
+ * and, for s = 1..d-1, z[s] = the z in {1 <= z <= n-1, gcd(z, n) = 1} minimising the
+ * (s+1)-dimensional squared shift-averaged worst-case error of eq. (2.12),
+ *     -prod_j (1 + gamma_j beta) + (1/n) sum_{k<n} prod_j (1 + gamma_j [B_2({k z_j/n}) + beta]),
+ * with the earlier components held fixed; e2[s] = that minimum (e2[0]: z_1 = 1
+ * alone).  beta = 0 for the unanchored weighted Sobolev space, c^2 - c + 1/3 for the
+ * one anchored at c (Remark after eq. 2.12).  The error of n - z equals that of z;
+ * the search takes z <= n/2 and, among equal values, the smallest z.
+ *   gamma      DEVICE, d doubles;  z  DEVICE, d int64;  e2  DEVICE, d doubles
+ *   workspace  DEVICE, >= lattice_cbc_workspace_size(n) bytes, 256-byte aligned
+ * 3d - 1 launches on `stream`, no host synchronisation.  MDI_EINVAL unless d >= 1,
+ * 2 <= n <= 2^31 and beta is finite; MDI_EWORKSPACE for a bad workspace.
+ * Work: d * n^2 / 4.
+ * ------------------------------------------------------------------------- */
+mdi_status lattice_cbc(int32_t d, int64_t n, const double *gamma, double beta, int64_t *z, double *e2,
+                       void *workspace, size_t ws_bytes, mdi_stream_t stream);
+mdi_status lattice_cbc_workspace_size(int64_t n, size_t *bytes);
+
+/* ---------------------------------------------------------------------------
  * Paper-table mode: the tensor midpoint rule on the grid of eq. (3.5),
  *     Q = Re(front * prod_{i=1}^{d} (1/n_i) sum_{k<n_i} phi_i((k + 1/2)/n_i)),
  * n_1 = ... = n_{d-1} = N, n_d = n_last, front = exp(2 pi i u) for OSC.  This is

@@ -46,6 +46,9 @@ SIGNATURES = {
     "mdi_batch_plan": (_I32, [_P, _I32, _c.POINTER(MdiOpts), _P]),
     "mdi_debug_lattice_indices": (_I32, [_I32, _I64, _P, _I64, _I64, _P, _P]),
     "mdi_midpoint_integrate": (_I32, [_I32, _I32, _I64, _I64, _P, _P, _P, _SZ, _P]),
+    "lattice_korobov_search": (_I32, [_I32, _I32, _I64, _I64, _I64, _P, _P, _P]),
+    "lattice_cbc": (_I32, [_I32, _I64, _P, _c.c_double, _P, _P, _P, _SZ, _P]),
+    "lattice_cbc_workspace_size": (_I32, [_I64, _c.POINTER(_SZ)]),
     "mdi_midpoint_workspace_size": (_I32, [_I32, _I64, _I64, _c.POINTER(_SZ)]),
     "mdi_status_string": (_c.c_char_p, [_I32]),
     "mdi_last_cuda_error": (_c.c_char_p, []),

@@ -281,6 +281,32 @@ __device__ __forceinline__ df32 df_rcp(df32 x) {
 }
 
 // ---------------------------------------------------------------------------
+// Exact lattice index arithmetic.
+// ---------------------------------------------------------------------------
+// (x * y) mod n for x, y < n < 2^63 by binary double-and-add: exact, no 128-bit type.
+__device__ __forceinline__ uint64_t mulmod_u63(uint64_t x, uint64_t y, uint64_t n) {
+  uint64_t r = 0;
+  while (y) {
+    if (y & 1ull) {
+      r += x;
+      if (r >= n) r -= n;
+    }
+    x += x;
+    if (x >= n) x -= n;
+    y >>= 1;
+  }
+  return r;
+}
+
+// Index run [j0, j1) of thread `tid` out of `nthreads` covering [0, n).
+__device__ __forceinline__ void thread_run(uint64_t n, uint64_t tid, uint64_t nthreads, uint64_t &j0,
+                                           uint64_t &j1) {
+  uint64_t per = n / nthreads, extra = n % nthreads;
+  j0 = tid * per + (tid < extra ? tid : extra);
+  j1 = j0 + per + (tid < extra ? 1 : 0);
+}
+
+// ---------------------------------------------------------------------------
 // Reductions with a fixed tree (deterministic).
 // ---------------------------------------------------------------------------
 template <typename V> __device__ __forceinline__ V warp_sum(V v) {

@@ -28,6 +28,13 @@ size_t closed_workspace_bytes(int d, int64_t a, int64_t n_last);  // 0 when the 
 mdi_status closed_launch(int family, int d, int64_t a, int64_t n_last, const double *params, int precision,
                          double *out, void *workspace, size_t ws_bytes, cudaStream_t stream);
 
+// lattice_search.cu
+mdi_status korobov_search_launch(int alpha, int d, int64_t n, int64_t a_first, int64_t count, double *values,
+                                 int64_t *best_a, cudaStream_t stream);
+size_t cbc_workspace_bytes(int64_t n);  // 0 when n is out of range
+mdi_status cbc_launch(int d, int64_t n, const double *gamma, double beta, int64_t *z, double *e2, void *workspace,
+                      size_t ws_bytes, cudaStream_t stream);
+
 // Paper-table mode: tensor midpoint rule on the grid (N, ..., N, n_last).
 size_t midpoint_workspace_bytes(int d, int64_t N, int64_t n_last);  // 0 when the sizes are out of range
 mdi_status midpoint_launch(int family, int d, int64_t N, int64_t n_last, const double *params, double *out,

@@ -29,29 +29,6 @@ struct SlrArgs {
   uint64_t z[kSlrMaxD];  // reduced mod n
 };
 
-// (x * y) mod n for x, y < n < 2^63 by binary double-and-add: exact, no 128-bit type.
-__device__ __forceinline__ uint64_t mulmod_u63(uint64_t x, uint64_t y, uint64_t n) {
-  uint64_t r = 0;
-  while (y) {
-    if (y & 1ull) {
-      r += x;
-      if (r >= n) r -= n;
-    }
-    x += x;
-    if (x >= n) x -= n;
-    y >>= 1;
-  }
-  return r;
-}
-
-// Index run of thread `tid` out of `nthreads` covering [0, n).
-__device__ __forceinline__ void thread_run(uint64_t n, uint64_t tid, uint64_t nthreads, uint64_t &j0,
-                                           uint64_t &j1) {
-  uint64_t per = n / nthreads, extra = n % nthreads;
-  j0 = tid * per + (tid < extra ? tid : extra);
-  j1 = j0 + per + (tid < extra ? 1 : 0);
-}
-
 template <int FAM, bool FP32EVAL, int MAXD>
 __global__ void __launch_bounds__(kSlrThreads) slr_kernel(const __grid_constant__ SlrArgs args,
                                                           const double *__restrict__ params,
