@@ -1,0 +1,69 @@
+"""Named workloads, each run a fixed number of times through the public API, for
+profiling one kernel at a time (``python -m paper_2404_08867_gb300.cases NAME
+[REPEATS]``).  Inputs are the seeded synthetic ones of ``inputs``; nothing here
+computes: every launch goes through the C ABI.
+
+  batch-df64      4096-integral batch, double-float node state (block 64, table via L1)
+  batch-fp64      the same batch in FP64
+  levels-d1000    one integral, node state parallel over levels, d = 1000, N = 16:
+                  forward and adjoint
+  korobov         P_2 Korobov search, n = 65536, d = 4, every a in 1..n/2
+  cbc             CBC, n = 65536, d = 4, gamma_j = 1/j^2, unanchored
+  midpoint-d1000  paper-table mode, d = 1000, N = 20, n_last = 21 (Gaussian)
+"""
+from __future__ import annotations
+
+import sys
+
+import numpy as np
+import torch
+
+import paper_2404_08867_gb300 as mdi
+from paper_2404_08867_gb300 import inputs
+
+
+def _batch(precision: str):
+    from paper_2404_08867_gb300.tuning import BatchedMDILR
+    b = inputs.batch(count=4096, seed=0)
+    plan = BatchedMDILR(b.families, b.d, b.a, b.n_last, b.offsets, b.pool, precision=precision, nodes=16)
+    plan.opts.update(block=64, table_in_l1=1)
+    return plan.launch
+
+
+def build_case(name: str):
+    if name == "batch-df64":
+        return _batch("df64")
+    if name == "batch-fp64":
+        return _batch("fp64")
+    if name == "levels-d1000":
+        w = inputs.scale_exp(1000, 16)
+        p = torch.as_tensor(w.params).cuda()
+        return lambda: (mdi.mdi_lr_integrate("exp", p, 1000, 16, state="nodes"),
+                        mdi.mdi_lr_grad("exp", p, 1000, 16, 16, state="nodes"))
+    if name == "korobov":
+        vals = torch.empty(32768, dtype=torch.float64, device="cuda")
+        return lambda: mdi.lattice_korobov_search(65536, 4, a_first=1, count=32768, values=vals)
+    if name == "cbc":
+        g = torch.as_tensor(1.0 / np.arange(1, 5) ** 2).cuda()
+        ws = torch.empty(mdi.lattice_cbc_workspace_size(65536), dtype=torch.uint8, device="cuda")
+        return lambda: mdi.lattice_cbc(65536, g, 0.0, workspace=ws)
+    if name == "midpoint-d1000":
+        w = inputs.gaussian(1000, 20, seed=0)
+        p = torch.as_tensor(w.params).cuda()
+        return lambda: mdi.mdi_midpoint_integrate("gauss", p, 1000, 20, 21)
+    raise SystemExit(f"unknown case {name!r}; see the module docstring")
+
+
+def main(argv):
+    if len(argv) < 2:
+        raise SystemExit(__doc__)
+    run = build_case(argv[1])
+    repeats = int(argv[2]) if len(argv) > 2 else 5
+    for _ in range(repeats):
+        run()
+    torch.cuda.synchronize()
+    print(f"{argv[1]}: {repeats} runs ok")
+
+
+if __name__ == "__main__":
+    main(sys.argv)

@@ -169,31 +169,40 @@ __global__ void closed_reduce_kernel(int d, int64_t a, int64_t n_last, Chunks ch
   }
 }
 
-// out = Re(front * prod_k S_k), the product taken in level order.
+// out = Re(front * prod_k S_k) by a fixed tree: each thread multiplies a run of
+// consecutive factors, the 32 runs of a warp are combined by an xor butterfly
+// (IEEE multiplication commutes exactly, so every lane holds the same value), and
+// thread 0 multiplies the warps' products in order.  Real families multiply reals.
+constexpr int kProdThreads = 256;
 template <int FAM>
-__global__ void __launch_bounds__(kScanThreads) closed_product_kernel(int d, const double *__restrict__ params,
+__global__ void __launch_bounds__(kProdThreads) closed_product_kernel(int d, const double *__restrict__ params,
                                                                       const double2 *__restrict__ S,
                                                                       double *__restrict__ out) {
-  __shared__ double2 sP[kScanThreads];
+  using V = typename FamTraits<FAM>::V;
+  __shared__ V sW[kProdThreads / kWarp];
   const int per = (d + blockDim.x - 1) / blockDim.x;
   const int lo = min(d, (int)threadIdx.x * per), hi = min(d, lo + per);
-  double2 p = make_double2(1.0, 0.0);
-  for (int k = lo; k < hi; ++k) p = c_mul(p, S[k]);
-  sP[threadIdx.x] = p;
-  __syncthreads();
-  // Fixed pairwise tree (blockDim is a power of two): deterministic, log depth.
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) sP[threadIdx.x] = c_mul(sP[threadIdx.x], sP[threadIdx.x + s]);
-    __syncthreads();
+  V p = VOps<V>::one();
+  for (int k = lo; k < hi; ++k) p = VOps<V>::mul(p, from2<V>(S[k]));
+  for (int off = 1; off < kWarp; off <<= 1) {
+    if constexpr (FAM == MDI_FAM_OSC) {
+      const double2 o = make_double2(__shfl_xor_sync(0xffffffffu, p.x, off), __shfl_xor_sync(0xffffffffu, p.y, off));
+      p = c_mul(p, o);
+    } else {
+      p *= __shfl_xor_sync(0xffffffffu, p, off);
+    }
   }
+  if ((threadIdx.x & (kWarp - 1)) == 0) sW[threadIdx.x / kWarp] = p;
+  __syncthreads();
   if (threadIdx.x == 0) {
-    const double2 K = sP[0];
+    V K = sW[0];
+    for (int w = 1; w < (int)(blockDim.x / kWarp); ++w) K = VOps<V>::mul(K, sW[w]);
     if constexpr (FAM == MDI_FAM_OSC) {
       double sn, cs;
       sincos(kTwoPi * params[d], &sn, &cs);
       out[0] = cs * K.x - sn * K.y;
     } else {
-      out[0] = K.x;
+      out[0] = K;
     }
   }
 }
@@ -267,7 +276,7 @@ static mdi_status run_closed(int d, int64_t a, int64_t n_last, const double *par
   const ClosedLayout L = closed_layout(d, a, n_last, false);
   mdi_status st = run_levels_sums<FAM, PREC, false>(d, a, n_last, params, (char *)ws, L, stream);
   if (st != MDI_OK) return st;
-  closed_product_kernel<FAM><<<1, kScanThreads, 0, stream>>>(d, params, (const double2 *)((char *)ws + L.S), out);
+  closed_product_kernel<FAM><<<1, kProdThreads, 0, stream>>>(d, params, (const double2 *)((char *)ws + L.S), out);
   return check_launch();
 }
 
@@ -343,7 +352,7 @@ static mdi_status run_midpoint(int d, int64_t N, int64_t n_last, const double *p
   closed_reduce_kernel<false><<<std::max(1, std::min((d + 255) / 256, sm_count() * 4)), 256, 0, stream>>>(
       d, N, n_last, ch, partS, partS, S, S);
   if ((st = check_launch()) != MDI_OK) return st;
-  closed_product_kernel<FAM><<<1, kScanThreads, 0, stream>>>(d, params, S, out);
+  closed_product_kernel<FAM><<<1, kProdThreads, 0, stream>>>(d, params, S, out);
   return check_launch();
 }
 

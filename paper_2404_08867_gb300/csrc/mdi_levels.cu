@@ -76,19 +76,26 @@ static int default_checkpoint(int d) {
 }
 
 // K0: L[t][q*P + p] = l_t((q + xi_p)/a) for one a.  One warp per point u: lane t
-// forms bw_t / (u - xi_t), a shuffle sum gives the denominator, so each lane
-// does two FP64 divisions (the FP64 unit is the scarce one on this chip).
+// forms bw_t / (u - xi_t), a shuffle sum gives the denominator, so each lane does
+// two FP64 divisions (the FP64 unit is the scarce one on this chip); the nodes and
+// weights are computed once per CTA.
 __global__ void levels_table_kernel(int P, int a, double *__restrict__ L) {
+  __shared__ double s_xi[kNodesPMax], s_bw[kNodesPMax];
+  for (int t = threadIdx.x; t < P; t += blockDim.x) {
+    s_xi[t] = cheb_node(t, P);
+    s_bw[t] = cheb_weight(t, P);
+  }
+  __syncthreads();
   const int lane = threadIdx.x & (kWarp - 1);
   const int pt = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
   const int npts = a * P;
   if (pt >= npts) return;  // whole warps
   const int q = pt / P, p = pt % P;
-  const double u = ((double)q + cheb_node(p, P)) / (double)a;
+  const double u = ((double)q + s_xi[p]) / (double)a;
   const bool on = lane < P;
-  const double xi = on ? cheb_node(lane, P) : 0.0;
+  const double xi = on ? s_xi[lane] : 0.0;
   const unsigned hit = __ballot_sync(0xffffffffu, on && u == xi);
-  const double r = (on && !hit) ? cheb_weight(lane, P) / (u - xi) : 0.0;
+  const double r = (on && !hit) ? s_bw[lane] / (u - xi) : 0.0;
   double den = r;
   for (int off = kWarp / 2; off > 0; off >>= 1) den += __shfl_xor_sync(0xffffffffu, den, off);
   if (on) L[(size_t)lane * npts + pt] = hit ? (lane == __ffs(hit) - 1 ? 1.0 : 0.0) : r / den;
