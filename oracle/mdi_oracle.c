@@ -629,6 +629,25 @@ int or_closed_form_grad(int fam, int d, const double *c, const double *w, double
 }
 
 /* ------------------------------------------------------------------------- */
+/* Randomly shifted lattice rule (Section 2.1): P + Delta = {{t + Delta} : t in P} */
+/* ------------------------------------------------------------------------- */
+
+/* (1/n) sum_{j<n} f({j z / n + Delta}), {x} = x - floor(x) componentwise. */
+double or_slr_shifted(int fam, int d, uint64_t n, const uint64_t *z, const double *c, const double *w,
+                      const double *shift) {
+  double *x = (double *)malloc(sizeof(double) * (size_t)d), sum = 0.0;
+  for (uint64_t j = 0; j < n; ++j) {
+    for (int i = 0; i < d; ++i) {
+      const double v = (double)mulmod(j, z[i] % n, n) / (double)n + shift[i];
+      x[i] = v - floor(v);
+    }
+    sum += f_eval(fam, d, x, c, w);
+  }
+  free(x);
+  return sum / (double)n;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Generating-vector criteria and searches (Section 2.2)                      */
 /* ------------------------------------------------------------------------- */
 

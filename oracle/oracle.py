@@ -75,6 +75,7 @@ def _load():
                 "or_midpoint_product": (D, [I, I, P, P, P]),
                 "or_closed_form": (D, [I, I, P, P]),
                 "or_closed_form_grad": (I, [I, I, P, P, P]),
+                "or_slr_shifted": (D, [I, I, U, P, P, P, P]),
                 "or_p_alpha": (D, [I, I, U, P]),
                 "or_korobov_search": (I, [I, I, U, U, U, P, P]),
                 "or_wce2_shift": (D, [I, U, P, P, D]),
@@ -232,6 +233,14 @@ def mdi_lr(family, d, a, nd, c, w=None, state="auto", P=16) -> float:
     if family in ("exp", "osc"):
         return mdi_closed(family, d, a, nd, c, w)
     return mdi_nodes(family, d, a, nd, P, c, w)
+
+
+# ---------------------------------------------------------------------------
+# Randomly shifted lattice rule (Section 2.1)
+# ---------------------------------------------------------------------------
+def slr_shifted(family, d, n, z, c, w=None, shift=None) -> float:
+    z, c, w, sh = _u64(z), _f64(c, d), _f64(w, d), _f64(shift, d)
+    return _load().or_slr_shifted(_fam(family), d, n, _p(z), _p(c), _p(w), _p(sh))
 
 
 # ---------------------------------------------------------------------------

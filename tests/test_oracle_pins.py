@@ -444,3 +444,38 @@ def test_cbc_components_minimise_against_exhaustive_subset_form():
         assert e2[s] == pytest.approx(best, rel=1e-10)
         mirrored = [int(v) for v in z[:s]] + [n - int(z[s])]
         assert o.wce2_shift(s + 1, n, mirrored, gamma, beta) == pytest.approx(e2[s], rel=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# Randomly shifted lattice rule (Section 2.1)
+# ----------------------------------------------------------------------------
+def test_shifted_rule_with_zero_shift_is_the_lattice_rule():
+    n, d = 1009, 3
+    z = o.korobov_z(d, 76, n)
+    c, w = np.array([0.7, -1.1, 0.4]), np.zeros(d)
+    assert o.slr_shifted("exp", d, n, z, c, w, np.zeros(d)) == o.slr("exp", d, n, z, c, w)
+
+
+def test_shifted_rule_on_characters():
+    """For f = cos(2 pi (u + h . x)) (the OSC family with c = 2 pi h) the shifted rule
+    is exactly cos(2 pi (u + h . Delta)) when h . z = 0 (mod n) and 0 otherwise (the
+    character sum over the lattice, eq. 2.3 with one Fourier mode)."""
+    n, z = 31, [1, 12]
+    rng = np.random.default_rng(4)
+    delta = rng.uniform(0, 1, 2)
+    for h in ([1, 18], [2, 5], [31, 0], [0, 1], [1, 1]):  # the first three are in the dual lattice
+        c = 2.0 * math.pi * np.array(h, dtype=float)
+        w = np.array([0.3, 0.0])
+        dual = (h[0] * z[0] + h[1] * z[1]) % n == 0
+        expect = math.cos(2.0 * math.pi * (0.3 + float(np.dot(h, delta)))) if dual else 0.0
+        assert o.slr_shifted("osc", 2, n, z, c, w, delta) == pytest.approx(expect, abs=1e-12)
+
+
+def test_shift_by_a_lattice_point_permutes_the_points():
+    """Delta = {k0 z / n} maps the lattice onto itself: the rule is unchanged (a
+    periodic integrand, so the wrap at 1 is invisible)."""
+    n, z, k0 = 101, [1, 37, 56], 29
+    c = 2.0 * math.pi * np.array([1.0, 2.0, -1.0])
+    w = np.array([0.1, 0.0, 0.0])
+    delta = np.array([(k0 * zi % n) / n for zi in z])
+    assert o.slr_shifted("osc", 3, n, z, c, w, delta) == pytest.approx(o.slr("osc", 3, n, z, c, w), abs=1e-13)
