@@ -299,6 +299,15 @@ def extra_small_workload(torch, mdi, o, inputs):
             break
     res["slr_p2_searched_a"] = p2
     res["slr_p2_search_ms_total"] = p2_search_ms
+    # Randomly shifted rule (Section 2.1): 16 uniform shifts of the a = 12345
+    # lattice at n = 65536 in one call; the mean estimates the integral and the
+    # replicates' spread its error.
+    shifts = torch.as_tensor(np.random.default_rng(16).uniform(0.0, 1.0, (16, 4))).cuda()
+    z16 = o.korobov_z(4, inputs.SMALL_SLR_A, n).astype(np.int64)
+    vals, sh_ms = event_ms(torch, lambda: mdi.lattice_rule_integrate_shifted("exp", c, n, z16, shifts))
+    mean, se = mdi.shifted_estimate(vals)
+    res["slr_shifted_R16_n65536"] = {"rel_err_of_mean": abs(mean.item() - exact) / exact,
+                                     "rel_std_error": se.item() / exact, "ms": sh_ms}
     return res
 
 

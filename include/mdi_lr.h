@@ -143,6 +143,25 @@ mdi_status lattice_rule_integrate_noalloc(int32_t family, int32_t d, int64_t n, 
                                           mdi_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Randomly shifted lattice rule (Section 2.1: P + Delta = {{t + Delta} : t in P}),
+ * R shifts in one call:
+ *     out[r] = (1/n) sum_{j<n} f({j z / n + Delta_r}),  r < R,
+ * the replicates of the randomly shifted rule whose mean estimates the integral and
+ * whose spread estimates its error (the mean square error over uniform shifts is
+ * bounded by the shift-averaged worst-case error, eq. 2.12).
+ *   shifts   DEVICE, R*d doubles, Delta_r = shifts[r*d .. r*d + d), each in [0, 1)
+ *   out      DEVICE, R doubles
+ *   R        1..65535
+ * FP64; other arguments and the index arithmetic as lattice_rule_integrate.  Two
+ * launches on `stream`.  MDI_EINVAL for bad sizes; MDI_EWORKSPACE for a missing,
+ * misaligned or short workspace (lattice_rule_shifted_workspace_size).
+ * ------------------------------------------------------------------------- */
+mdi_status lattice_rule_integrate_shifted(int32_t family, int32_t d, int64_t n, const int64_t *z,
+                                          const double *params, const double *shifts, int32_t R, double *out,
+                                          void *workspace, size_t ws_bytes, mdi_stream_t stream);
+mdi_status lattice_rule_shifted_workspace_size(int32_t d, int64_t n, int32_t R, size_t *bytes);
+
+/* ---------------------------------------------------------------------------
  * MDI-LR, Algorithm 2 (Section 4) with m = 1 on the Korobov lattice.
  *   d        dimension, >= 1 (EXACT: n <= 2^40; CLOSED: d <= 2^20; NODES: d <= 2^20)
  *   a        Korobov parameter = points per transformed axis 1..d-1, a >= 1

@@ -26,7 +26,8 @@ __all__ = [
     "mdi_lr_integrate_batched", "mdi_lr_batched_workspace_size", "mdi_lr_batched_prepare", "mdi_batch_plan", "mdi_debug_lattice_indices",
     "mdi_lr_grad", "mdi_lr_grad_workspace_size", "MDILR", "mdi_lr", "make_batch_descs", "MdiError", "FAMILY", "STATE", "PRECISION", "BATCH_DESC_DTYPE", "library_path",
     "mdi_midpoint_integrate", "mdi_midpoint_workspace_size", "lattice_korobov_search", "lattice_cbc",
-    "lattice_cbc_workspace_size",
+    "lattice_cbc_workspace_size", "lattice_rule_integrate_shifted", "lattice_rule_shifted_workspace_size",
+    "shifted_estimate",
 ]
 
 
@@ -100,6 +101,46 @@ def lattice_rule_integrate(family, params: torch.Tensor, n: int, z: Sequence[int
                                             ws.numel(), _stream(stream))
     _ffi.check(st, "lattice_rule_integrate")
     return out
+
+
+def lattice_rule_shifted_workspace_size(d: int, n: int, R: int) -> int:
+    b = ctypes.c_size_t()
+    _ffi.check(_ffi.load().lattice_rule_shifted_workspace_size(d, n, R, ctypes.byref(b)),
+               "lattice_rule_shifted_workspace_size")
+    return b.value
+
+
+def lattice_rule_integrate_shifted(family, params: torch.Tensor, n: int, z: Sequence[int], shifts: torch.Tensor,
+                                   out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
+                                   stream=None) -> torch.Tensor:
+    """R replicates of the randomly shifted rule, (1/n) sum_j f({j z/n + Delta_r}):
+    ``shifts`` is an (R, d) float64 CUDA tensor of shifts in [0, 1).  Returns R values."""
+    _dev_f64(params, "params")
+    _dev_f64(shifts, "shifts")
+    zz = np.ascontiguousarray(np.asarray(z, dtype=np.int64))
+    d = int(zz.size)
+    if params.numel() < 2 * d or shifts.dim() != 2 or shifts.shape[1] != d:
+        raise ValueError("params must hold 2*d doubles and shifts must be (R, d)")
+    R = int(shifts.shape[0])
+    if out is None:
+        out = torch.empty(R, dtype=torch.float64, device=params.device)
+    ws = _workspace(lattice_rule_shifted_workspace_size(d, n, R), params.device, workspace)
+    st = _ffi.load().lattice_rule_integrate_shifted(_fam(family), d, int(n), zz.ctypes.data_as(ctypes.c_void_p),
+                                                    ctypes.c_void_p(params.data_ptr()),
+                                                    ctypes.c_void_p(shifts.data_ptr()), R,
+                                                    ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                                                    ws.numel(), _stream(stream))
+    _ffi.check(st, "lattice_rule_integrate_shifted")
+    return out
+
+
+def shifted_estimate(values: torch.Tensor):
+    """(mean, standard error) of R shifted-rule replicates: the estimate of the
+    integral and of its error (sample standard deviation / sqrt(R))."""
+    R = values.numel()
+    mean = values.mean()
+    se = values.std(correction=1) / (R ** 0.5) if R > 1 else torch.zeros_like(mean)
+    return mean, se
 
 
 def lattice_rule_integrate_noalloc(family, params: torch.Tensor, n: int, z: Sequence[int], precision="fp64",

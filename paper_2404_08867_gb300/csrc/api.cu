@@ -99,6 +99,19 @@ mdi_status lattice_rule_integrate(int32_t family, int32_t d, int64_t n, const in
   return slr_launch(family, d, n, z, params, precision, out, workspace, ws_bytes, (cudaStream_t)stream);
 }
 
+mdi_status lattice_rule_shifted_workspace_size(int32_t d, int64_t n, int32_t R, size_t *bytes) {
+  if (!bytes || d < 1 || n < 1 || R < 1) return MDI_EINVAL;
+  *bytes = slr_shifted_workspace_bytes(d, n, R);
+  return *bytes ? MDI_OK : MDI_EINVAL;
+}
+
+mdi_status lattice_rule_integrate_shifted(int32_t family, int32_t d, int64_t n, const int64_t *z,
+                                          const double *params, const double *shifts, int32_t R, double *out,
+                                          void *workspace, size_t ws_bytes, mdi_stream_t stream) {
+  if (!family_ok(family)) return MDI_EINVAL;
+  return slr_shifted_launch(family, d, n, z, params, shifts, R, out, workspace, ws_bytes, (cudaStream_t)stream);
+}
+
 mdi_status lattice_rule_integrate_noalloc(int32_t family, int32_t d, int64_t n, const int64_t *z, const double *params,
                                           int32_t precision, double *out, mdi_stream_t stream) {
   if (!family_ok(family)) return MDI_EINVAL;

@@ -28,6 +28,12 @@ size_t closed_workspace_bytes(int d, int64_t a, int64_t n_last);  // 0 when the 
 mdi_status closed_launch(int family, int d, int64_t a, int64_t n_last, const double *params, int precision,
                          double *out, void *workspace, size_t ws_bytes, cudaStream_t stream);
 
+// slr.cu: randomly shifted lattice rule, R replicates
+size_t slr_shifted_workspace_bytes(int d, int64_t n, int R);  // 0 when out of range
+mdi_status slr_shifted_launch(int family, int d, int64_t n, const int64_t *z, const double *params,
+                              const double *shifts, int R, double *out, void *workspace, size_t ws_bytes,
+                              cudaStream_t stream);
+
 // lattice_search.cu
 mdi_status korobov_search_launch(int alpha, int d, int64_t n, int64_t a_first, int64_t count, double *values,
                                  int64_t *best_a, cudaStream_t stream);

@@ -29,11 +29,16 @@ struct SlrArgs {
   uint64_t z[kSlrMaxD];  // reduced mod n
 };
 
-template <int FAM, bool FP32EVAL, int MAXD>
+// SHIFT: the randomly shifted rule of Section 2.1, x = {j z / n + Delta_r} with the
+// shift Delta_r = shifts[r*d .. r*d + d) of replicate r = blockIdx.y; each
+// replicate's CTAs write their partials at partials + r * gridDim.x.
+template <int FAM, bool FP32EVAL, int MAXD, bool SHIFT = false>
 __global__ void __launch_bounds__(kSlrThreads) slr_kernel(const __grid_constant__ SlrArgs args,
                                                           const double *__restrict__ params,
-                                                          double *__restrict__ partials) {
+                                                          double *__restrict__ partials,
+                                                          const double *__restrict__ shifts = nullptr) {
   __shared__ double s_c[MAXD], s_w[MAXD], s_ic2[MAXD];
+  __shared__ double s_dx[SHIFT ? MAXD : 1];
   __shared__ double s_red[kSlrThreads / kWarp];
   constexpr int kUnroll = MAXD <= 32 ? MAXD : 1;  // the wide bucket keeps r[] in local memory
   const int d = args.d;
@@ -41,8 +46,19 @@ __global__ void __launch_bounds__(kSlrThreads) slr_kernel(const __grid_constant_
     s_c[i] = params[i];
     s_w[i] = params[d + i];
     s_ic2[i] = 1.0 / (params[i] * params[i]);
+    if constexpr (SHIFT) s_dx[i] = shifts[(size_t)blockIdx.y * d + i];
   }
+  if constexpr (SHIFT) partials += (size_t)blockIdx.y * gridDim.x;
   __syncthreads();
+  // Coordinate i of the current point: r_i / n, shifted and wrapped into [0, 1).
+  auto coord = [&](uint64_t ri, int i) -> double {
+    double x = (double)ri * args.inv_n;
+    if constexpr (SHIFT) {
+      x += s_dx[i];
+      if (x >= 1.0) x -= 1.0;
+    }
+    return x;
+  };
   const double u2pi = (FAM == MDI_FAM_OSC) ? kTwoPi * params[d] : 0.0;
 
   const uint64_t n = args.n;
@@ -64,7 +80,7 @@ __global__ void __launch_bounds__(kSlrThreads) slr_kernel(const __grid_constant_
 #pragma unroll(kUnroll)
       for (int i = 0; i < MAXD; ++i) {
         if (i < d) {
-          double t = fma((double)r[i], args.inv_n, -s_w[i]);
+          double t = SHIFT ? coord(r[i], i) - s_w[i] : fma((double)r[i], args.inv_n, -s_w[i]);
           den *= fma(t, t, s_ic2[i]);
           if ((i & 7) == 7) { p /= den; den = 1.0; }
         }
@@ -77,7 +93,7 @@ __global__ void __launch_bounds__(kSlrThreads) slr_kernel(const __grid_constant_
 #pragma unroll(kUnroll)
       for (int i = 0; i < MAXD; ++i) {
         if (i < d) {
-          double x = (double)r[i] * args.inv_n;
+          double x = coord(r[i], i);
           if constexpr (FAM == MDI_FAM_GAUSS) {
             if constexpr (FP32EVAL) {
               float t = (float)s_c[i] * ((float)x - (float)s_w[i]);
@@ -109,14 +125,16 @@ __global__ void __launch_bounds__(kSlrThreads) slr_kernel(const __grid_constant_
   if (threadIdx.x == 0) partials[blockIdx.x] = b;
 }
 
-// Adds `count` partials in a fixed order and writes scale * sum.
+// Adds `count` partials in a fixed order and writes scale * sum; CTA r handles the
+// partials of replicate r (one CTA without shifts).
 __global__ void __launch_bounds__(kSlrThreads) sum_partials_kernel(const double *__restrict__ partials, int count,
                                                                    double inv_count_scale, double *__restrict__ out) {
   __shared__ double s_red[kSlrThreads / kWarp];
+  partials += (size_t)blockIdx.x * count;
   double acc = 0.0;
   for (int i = threadIdx.x; i < count; i += blockDim.x) acc += partials[i];
   double b = block_sum(acc, s_red);
-  if (threadIdx.x == 0) out[0] = b * inv_count_scale;
+  if (threadIdx.x == 0) out[blockIdx.x] = b * inv_count_scale;
 }
 
 __global__ void lattice_indices_kernel(const __grid_constant__ SlrArgs args, uint64_t j0, uint64_t count,
@@ -191,6 +209,55 @@ mdi_status slr_launch(int family, int d, int64_t n, const int64_t *z, const doub
   mdi_status st = check_launch();
   if (st != MDI_OK) return st;
   sum_partials_kernel<<<1, kSlrThreads, 0, stream>>>(partials, grid, 1.0 / (double)n, out);
+  return check_launch();
+}
+
+// Randomly shifted rule: R replicates, one launch (grid.y = R) plus one sum launch.
+template <int FAM>
+static void launch_slr_shifted(int grid, int R, const SlrArgs &args, const double *params, double *partials,
+                               const double *shifts, cudaStream_t s) {
+  const dim3 g(grid, R);
+  if (args.d <= 8) slr_kernel<FAM, false, 8, true><<<g, kSlrThreads, 0, s>>>(args, params, partials, shifts);
+  else if (args.d <= 32) slr_kernel<FAM, false, 32, true><<<g, kSlrThreads, 0, s>>>(args, params, partials, shifts);
+  else slr_kernel<FAM, false, kSlrMaxD, true><<<g, kSlrThreads, 0, s>>>(args, params, partials, shifts);
+}
+
+static int slr_shifted_grid(uint64_t n, int R) {
+  // about the same number of resident CTAs in total as one unshifted launch
+  return std::max(1, slr_grid(n) / std::max(1, std::min(R, slr_grid(n))));
+}
+
+size_t slr_shifted_workspace_bytes(int d, int64_t n, int R) {
+  (void)d;
+  if (n < 1 || R < 1 || R > 65535) return 0;
+  return align_up(sizeof(double) * (size_t)slr_shifted_grid((uint64_t)n, R) * (size_t)R);
+}
+
+mdi_status slr_shifted_launch(int family, int d, int64_t n, const int64_t *z, const double *params,
+                              const double *shifts, int R, double *out, void *workspace, size_t ws_bytes,
+                              cudaStream_t stream) {
+  if (d < 1 || d > kSlrMaxD || n < 1 || !z || !params || !shifts || !out || R < 1 || R > 65535) return MDI_EINVAL;
+  if (family < MDI_FAM_EXP || family > MDI_FAM_PEAK) return MDI_EINVAL;
+  for (int i = 0; i < d; ++i)
+    if (z[i] < 0 || z[i] >= n) return MDI_EINVAL;
+  if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < slr_shifted_workspace_bytes(d, n, R))
+    return MDI_EWORKSPACE;
+  SlrArgs args{};
+  args.n = (uint64_t)n;
+  args.inv_n = 1.0 / (double)n;
+  args.d = d;
+  for (int i = 0; i < d; ++i) args.z[i] = (uint64_t)z[i];
+  const int grid = slr_shifted_grid((uint64_t)n, R);
+  double *partials = (double *)workspace;
+  switch (family) {
+    case MDI_FAM_EXP: launch_slr_shifted<MDI_FAM_EXP>(grid, R, args, params, partials, shifts, stream); break;
+    case MDI_FAM_OSC: launch_slr_shifted<MDI_FAM_OSC>(grid, R, args, params, partials, shifts, stream); break;
+    case MDI_FAM_GAUSS: launch_slr_shifted<MDI_FAM_GAUSS>(grid, R, args, params, partials, shifts, stream); break;
+    default: launch_slr_shifted<MDI_FAM_PEAK>(grid, R, args, params, partials, shifts, stream); break;
+  }
+  mdi_status st = check_launch();
+  if (st != MDI_OK) return st;
+  sum_partials_kernel<<<R, kSlrThreads, 0, stream>>>(partials, grid, 1.0 / (double)n, out);
   return check_launch();
 }
 
