@@ -48,7 +48,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12    # 2 DFMA lanes per SM per clo
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 128 FFMA lanes per SM per clock
 
 # Float operations (an FMA counts 2) of the double-float primitives, by construction.
-DF_FLOPS = {"u": 28, "dot_term": 15, "dot_value": 6, "acc": 15,
+DF_FLOPS = {"u": 28, "dot_term": 15, "dot_value": 6, "acc": 15, "combine": 22,
             "phi": {"gauss": 122, "peak": 83, "exp": 93, "osc": 0}}
 
 
@@ -97,17 +97,23 @@ def fp64_flops(b, P=P_NODES):
     return float((interp * (2 * P + 8) + first * 8 + nl * (2 * P + 8)).sum())
 
 
-def df_flops(b, P=P_NODES):
+def df_flops(b, P=P_NODES, paired=True):
     """Float operations of the double-float formulation (FMA = 2), by construction:
-    per cluster point of level k >= 2: coordinate, phi, P Dot2 terms, their value
-    and the accumulation; level 1 without interpolation; last axis likewise."""
+    per cluster point of level k >= 2: coordinate, phi, the interpolation and the
+    accumulation; level 1 without interpolation; last axis with a P-term Dot2 per
+    point.  Paired (DF64, real families): one pass of P Dot2 terms (P/2 for the
+    sums of the table values, P/2 for their differences) interpolates two mirrored
+    points, plus per point one Dot2 value, a double-float add and a halving;
+    otherwise P Dot2 terms and one value per point."""
     total = 0.0
-    interp = P * DF_FLOPS["dot_term"] + DF_FLOPS["dot_value"]
+    interp_one = P * DF_FLOPS["dot_term"] + DF_FLOPS["dot_value"]
+    interp_paired = P * DF_FLOPS["dot_term"] / 2 + DF_FLOPS["dot_value"] + DF_FLOPS["combine"]
     for i, fam in enumerate(b.families):
         d, a, nl = int(b.d[i]), int(b.a[i]), int(b.n_last[i])
         phi = DF_FLOPS["phi"][fam]
         pt = DF_FLOPS["u"] + phi + DF_FLOPS["acc"]
-        total += max(d - 2, 0) * a * P * (pt + interp) + (a * P * pt if d >= 2 else 0) + nl * (pt + interp)
+        interp = interp_paired if (paired and fam != "osc") else interp_one
+        total += max(d - 2, 0) * a * P * (pt + interp) + (a * P * pt if d >= 2 else 0) + nl * (pt + interp_one)
     return total
 
 
@@ -547,7 +553,7 @@ def main():
     if rank == 0:
         kernel_ms = statistics.mean(step_ms)
         if args.precision in ("df64", "fp32_eval_df32"):
-            flops = df_flops(b)
+            flops = df_flops(b, paired=args.precision == "df64")
             achieved = flops / (kernel_ms / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": profiled_traffic(args.precision),

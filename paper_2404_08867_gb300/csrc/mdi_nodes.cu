@@ -134,6 +134,57 @@ __global__ void nodes_table_kernel(int P, void *__restrict__ table) {
   }
 }
 
+// Paired cluster basis (DF64, real families).  The nodes are symmetric,
+// xi_{P-1-p} = 1 - xi_p, and the barycentric weights are too up to one common sign,
+// so l_t(1 - u) = l_{P-1-t}(u): the cluster point u = (q + xi_p)/a of node p and the
+// point 1 - u = (a-1-q + xi_{P-1-p})/a of node P-1-p interpolate with the same basis
+// values in reverse order.  For p < h = P/2 the table holds
+//     Lpm[t][p*a + q] = (l_t(u) + l_{P-1-t}(u), l_t(u) - l_{P-1-t}(u)),  t < h,
+// as two float pairs (one 16-byte entry); h*a*h entries per a, a = 1..64.
+__host__ __device__ __forceinline__ size_t paired_offset(int a, int P) {
+  const size_t h = (size_t)P / 2;
+  return h * h * (size_t)a * (size_t)(a - 1) / 2;  // in 16-byte entries
+}
+static size_t paired_bytes(int P) { return 16 * paired_offset(kNodesAMax + 1, P); }
+
+__global__ void nodes_paired_table_kernel(int P, float4 *__restrict__ table) {
+  __shared__ double s_xi[kNodesPMax], s_bw[kNodesPMax];
+  for (int t = threadIdx.x; t < P; t += blockDim.x) {
+    s_xi[t] = cheb_node(t, P);
+    s_bw[t] = cheb_weight(t, P);
+  }
+  __syncthreads();
+  const int h = P / 2;
+  const size_t total_rows = (size_t)h * kNodesAMax * (kNodesAMax + 1) / 2;  // sum_a a*h
+  for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total_rows;
+       g += (size_t)gridDim.x * blockDim.x) {
+    int a = 1;
+    size_t base = 0;
+    while (base + (size_t)a * h <= g) {
+      base += (size_t)a * h;
+      ++a;
+    }
+    const int i = (int)(g - base);  // i = p*a + q, p < h
+    const double u = ((double)(i % a) + s_xi[i / a]) / (double)a;
+    double den = 0.0;
+    int hit = -1;
+    for (int t = 0; t < P; ++t) {
+      if (u == s_xi[t]) hit = t;
+      else den += s_bw[t] / (u - s_xi[t]);
+    }
+    auto basis = [&](int t) {
+      return hit >= 0 ? (t == hit ? 1.0 : 0.0) : (s_bw[t] / (u - s_xi[t])) / den;
+    };
+    float4 *row = table + paired_offset(a, P);
+    for (int t = 0; t < h; ++t) {
+      const double lt = basis(t), lr = basis(P - 1 - t);
+      const double vp = lt + lr, vm = lt - lr;
+      const float ph = (float)vp, mh = (float)vm;
+      row[(size_t)t * a * h + i] = make_float4(ph, (float)(vp - (double)ph), mh, (float)(vm - (double)mh));
+    }
+  }
+}
+
 // Constants of axis j (0-based) for the level loop.
 __device__ __forceinline__ void make_level_const(const double *__restrict__ prm, int d, int j, LevelConst &L) {
   const double c = prm[j], w = prm[d + j], ic2 = 1.0 / (c * c);
@@ -240,6 +291,103 @@ __device__ __forceinline__ df32 lanes_sum_df(df32 v, int Q) {
     v = df_add(v, df32{__shfl_xor_sync(0xffffffffu, v.hi, off, Q), __shfl_xor_sync(0xffffffffu, v.lo, off, Q)});
   return v;
 }
+
+// The last level of one integral, Q = (1/n_last) sum_s phi_d(s/n_last) G_{d-1}(s/n_last),
+// with G_{d-1} in state buffer sb (sh.Gdf as float pairs in DF64, sh.G otherwise)
+// and the level constants of the chunk holding axis d-2 in sh.lc.
+template <int FAM, int PREC>
+__device__ void last_level(NodesShared &sh, const void *__restrict__ Ftab, int P, int d, int a, int n_last,
+                           const double *__restrict__ prm, double *__restrict__ out_slot, int sb) {
+  using V = typename FamTraits<FAM>::V;
+  constexpr bool F32 = (PREC == MDI_PREC_FP32_EVAL_FP64 || PREC == MDI_PREC_FP32_EVAL_DF32);
+  constexpr bool DF = (PREC == MDI_PREC_FP32_EVAL_DF32 || PREC == MDI_PREC_DF64);
+  constexpr bool CPLX = (FAM == MDI_FAM_OSC);
+  constexpr bool DF64 = (PREC == MDI_PREC_DF64) && !CPLX;
+  constexpr bool DFSTATE = (PREC == MDI_PREC_DF64);
+  const int tid = threadIdx.x, B = blockDim.x;
+  if (d > 1 && (d - 1) % kLvChunk == 0) {
+    load_level_chunk(sh.lc, prm, d, d - 1);
+    __syncthreads();
+  }
+  const LevelConst &LL = sh.lc[(d - 1) % kLvChunk];
+  const bool tabulated = (n_last == a) && d > 1;
+  if constexpr (DF64) {
+    if (tabulated) {
+      const df32 ia{sh.iadf.x, sh.iadf.y};
+      df32 s1, s0;  // the last axis' points are s/a: no node offset
+      phi_affine_coeffs<FAM>(LL.cw, ia, df32{0.f, 0.f}, s1, s0);
+      DfAcc acc;
+      for (int s = tid; s < n_last; s += B) {
+        const float2 *F = (const float2 *)Ftab + s;
+        DfAcc ag;
+#pragma unroll 4
+        for (int t = 0; t < P; ++t) {
+          const float2 l = F[(size_t)t * a];
+          const float4 gt = sh.Gdf[sb][t];
+          dacc_prod(ag, df32{l.x, l.y}, df32{gt.x, gt.y});
+        }
+        dacc_prod(acc, phi_df_affine<FAM>(s1, s0, (float)s, LL.ic, sh.exp2tab), dacc_value(ag));
+      }
+      const float4 tot = block_sum_df(dacc_value(acc), df32{0.f, 0.f}, sh.redf);
+      if (tid == 0) *out_slot = ((double)tot.x + (double)tot.y) / (double)n_last;
+      __syncthreads();
+      return;
+    }
+  }
+  if constexpr (DFSTATE) {  // double view of the state for the general last level
+    if (tid < P) sh.G[sb][tid] = join2(sh.Gdf[sb][tid]);
+    __syncthreads();
+  }
+  const AxisParams ap{LL.c, LL.w, LL.ic2};
+  const double inv_n = 1.0 / (double)n_last;
+  V acc = VOps<V>::zero();
+  for (int s = tid; s < n_last; s += B) {
+    const double u = (double)s * inv_n;
+    V g;
+    if (d == 1) {
+      g = VOps<V>::one();
+    } else if (tabulated) {
+      g = VOps<V>::zero();
+      if constexpr (DF) {
+        const float2 *F = (const float2 *)Ftab + s;
+        for (int t = 0; t < P; ++t) {
+          const float2 l = F[(size_t)t * a];
+          g = VOps<V>::fma_s((double)l.x + (double)l.y, from2<V>(sh.G[sb][t]), g);
+        }
+      } else {
+        const double *F = (const double *)Ftab + s;
+        for (int t = 0; t < P; ++t) g = VOps<V>::fma_s(F[(size_t)t * a], from2<V>(sh.G[sb][t]), g);
+      }
+    } else {
+      double den = 0.0;
+      double2 num = make_double2(0.0, 0.0);
+      int hit = -1;
+      for (int t = 0; t < P; ++t) {
+        if (u == sh.xi[t]) {
+          hit = t;
+          continue;
+        }
+        const double wt = sh.bw[t] / (u - sh.xi[t]);
+        den += wt;
+        num = make_double2(fma(wt, sh.G[sb][t].x, num.x), fma(wt, sh.G[sb][t].y, num.y));
+      }
+      g = hit >= 0 ? from2<V>(sh.G[sb][hit]) : from2<V>(c_scale(num, 1.0 / den));
+    }
+    acc = VOps<V>::add(acc, VOps<V>::mul(phi<FAM, F32 && !DFSTATE>(u, ap), g));
+  }
+  const V tot = block_sum(acc, (V *)sh.red);
+  if (tid == 0) {
+    if constexpr (CPLX) {
+      double sn, cs;
+      sincos(kTwoPi * prm[d], &sn, &cs);
+      *out_slot = (cs * tot.x - sn * tot.y) * inv_n;
+    } else {
+      *out_slot = tot * inv_n;
+    }
+  }
+  __syncthreads();
+}
+
 
 // ---------------------------------------------------------------------------
 // One integral, swept by one CTA.  Ltab: the cluster basis of this a (shared or
@@ -376,88 +524,101 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, const 
   }
 
   // Last level: Q = (1/n_last) sum_s phi_d(s/n_last) G_{d-1}(s/n_last).
-  const int sb = (d - 1) & 1;  // buffer holding G_{d-1}
-  if (d > 1 && (d - 1) % kLvChunk == 0) {
-    load_level_chunk(sh.lc, prm, d, d - 1);
-    __syncthreads();
+  last_level<FAM, PREC>(sh, Ftab, P, d, a, n_last, prm, out_slot, (d - 1) & 1);
+}
+
+// ---------------------------------------------------------------------------
+// One integral of a real family in DF64 with paired cluster points.  The state
+// is kept as E_t = G_t + G_{P-1-t} and O_t = G_t - G_{P-1-t} (t < h, sh.Gdf as
+// (E.hi, E.lo, O.hi, O.lo)).  With S+ = sum_t Lp[t] E_t and S- = sum_t Lm[t] O_t,
+//     G(u) = (S+ + S-)/2,   G(1 - u) = (S+ - S-)/2,
+// so one pass of h Dot2 pairs interpolates both points of a pair: P multiply-adds
+// for two cluster points instead of 2P.  Lanes are pair-major: the Q lanes of
+// pair pp take the points q of node pp (and a-1-q of node P-1-pp) and accumulate
+// both nodes' sums.  The last level unpacks E, O into G and runs last_level.
+// ---------------------------------------------------------------------------
+template <int FAM>
+__device__ void sweep_paired(NodesShared &sh, const float4 *__restrict__ Lpm, const void *__restrict__ Ftab, int P,
+                             int d, int a, int n_last, const double *__restrict__ prm, double *__restrict__ out_slot) {
+  const int h = P / 2;
+  const int tid = threadIdx.x, B = blockDim.x;
+  const int Q = node_lanes(B, h);
+  const int pp = min(tid / Q, h - 1), pb = P - 1 - pp, qs = tid % Q;
+  const bool act = tid < h * Q;
+  const bool warp_act = (tid & ~(kWarp - 1)) < h * Q;
+  const int npts_h = a * h;
+  if (tid < h) sh.Gdf[0][tid] = make_float4(2.f, 0.f, 0.f, 0.f);  // G_0 = 1: E = 2, O = 0
+  if (tid < P) {
+    const double xa = sh.xi[tid] / (double)a;
+    const float hx = (float)xa;
+    sh.xadf[tid] = make_float2(hx, (float)(xa - (double)hx));
   }
-  const LevelConst &LL = sh.lc[(d - 1) % kLvChunk];
-  const bool tabulated = (n_last == a) && d > 1;
-  if constexpr (DF64) {
-    if (tabulated) {
-      const df32 ia{sh.iadf.x, sh.iadf.y};
-      df32 s1, s0;  // the last axis' points are s/a: no node offset
-      phi_affine_coeffs<FAM>(LL.cw, ia, df32{0.f, 0.f}, s1, s0);
-      DfAcc acc;
-      for (int s = tid; s < n_last; s += B) {
-        const float2 *F = (const float2 *)Ftab + s;
-        DfAcc ag;
-#pragma unroll 4
-        for (int t = 0; t < P; ++t) {
-          const float2 l = F[(size_t)t * a];
-          const float4 gt = sh.Gdf[sb][t];
-          dacc_prod(ag, df32{l.x, l.y}, df32{gt.x, gt.y});
-        }
-        dacc_prod(acc, phi_df_affine<FAM>(s1, s0, (float)s, LL.ic, sh.exp2tab), dacc_value(ag));
-      }
-      const float4 tot = block_sum_df(dacc_value(acc), df32{0.f, 0.f}, sh.redf);
-      if (tid == 0) *out_slot = ((double)tot.x + (double)tot.y) / (double)n_last;
-      __syncthreads();
-      return;
-    }
-  }
-  if constexpr (DFSTATE) {  // double view of the state for the general last level
-    if (tid < P) sh.G[sb][tid] = join2(sh.Gdf[sb][tid]);
-    __syncthreads();
-  }
-  const AxisParams ap{LL.c, LL.w, LL.ic2};
-  const double inv_n = 1.0 / (double)n_last;
-  V acc = VOps<V>::zero();
-  for (int s = tid; s < n_last; s += B) {
-    const double u = (double)s * inv_n;
-    V g;
-    if (d == 1) {
-      g = VOps<V>::one();
-    } else if (tabulated) {
-      g = VOps<V>::zero();
-      if constexpr (DF) {
-        const float2 *F = (const float2 *)Ftab + s;
-        for (int t = 0; t < P; ++t) {
-          const float2 l = F[(size_t)t * a];
-          g = VOps<V>::fma_s((double)l.x + (double)l.y, from2<V>(sh.G[sb][t]), g);
-        }
-      } else {
-        const double *F = (const double *)Ftab + s;
-        for (int t = 0; t < P; ++t) g = VOps<V>::fma_s(F[(size_t)t * a], from2<V>(sh.G[sb][t]), g);
-      }
-    } else {
-      double den = 0.0;
-      double2 num = make_double2(0.0, 0.0);
-      int hit = -1;
-      for (int t = 0; t < P; ++t) {
-        if (u == sh.xi[t]) {
-          hit = t;
-          continue;
-        }
-        const double wt = sh.bw[t] / (u - sh.xi[t]);
-        den += wt;
-        num = make_double2(fma(wt, sh.G[sb][t].x, num.x), fma(wt, sh.G[sb][t].y, num.y));
-      }
-      g = hit >= 0 ? from2<V>(sh.G[sb][hit]) : from2<V>(c_scale(num, 1.0 / den));
-    }
-    acc = VOps<V>::add(acc, VOps<V>::mul(phi<FAM, F32 && !DFSTATE>(u, ap), g));
-  }
-  const V tot = block_sum(acc, (V *)sh.red);
   if (tid == 0) {
-    if constexpr (CPLX) {
-      double sn, cs;
-      sincos(kTwoPi * prm[d], &sn, &cs);
-      *out_slot = (cs * tot.x - sn * tot.y) * inv_n;
-    } else {
-      *out_slot = tot * inv_n;
+    const double ia = 1.0 / (double)a;
+    const float hx = (float)ia;
+    sh.iadf = make_float2(hx, (float)(ia - (double)hx));
+  }
+  load_level_chunk(sh.lc, prm, d, 0);
+  __syncthreads();
+  const df32 ia{sh.iadf.x, sh.iadf.y};
+
+  for (int k = 1; k < d; ++k) {
+    const int j = k - 1;
+    if (j > 0 && j % kLvChunk == 0) {
+      load_level_chunk(sh.lc, prm, d, j);
+      __syncthreads();
     }
+    const LevelConst &L = sh.lc[j % kLvChunk];
+    const int rb = (k - 1) & 1, wb = k & 1;
+    DfAcc acc_a, acc_b;
+    if (act) {
+      const df32 xa{sh.xadf[pp].x, sh.xadf[pp].y}, xb{sh.xadf[pb].x, sh.xadf[pb].y};
+      df32 s1a, s0a, s1b, s0b;
+      phi_affine_coeffs<FAM>(L.cw, ia, xa, s1a, s0a);
+      phi_affine_coeffs<FAM>(L.cw, ia, xb, s1b, s0b);
+      for (int q = qs; q < a; q += Q) {
+        df32 ga{1.f, 0.f}, gb{1.f, 0.f};
+        if (k > 1) {
+          const float4 *Lt = Lpm + pp * a + q;
+          DfAcc sp, sm;
+#pragma unroll 4
+          for (int t = 0; t < h; ++t) {
+            const float4 l = Lt[(size_t)t * npts_h];
+            const float4 eo = sh.Gdf[rb][t];
+            dacc_prod(sp, df32{l.x, l.y}, df32{eo.x, eo.y});
+            dacc_prod(sm, df32{l.z, l.w}, df32{eo.z, eo.w});
+          }
+          const df32 vp = dacc_value(sp), vm = dacc_value(sm);
+          const df32 ta = df_add(vp, vm), tb = df_add(vp, df_neg(vm));
+          ga = df32{0.5f * ta.hi, 0.5f * ta.lo};
+          gb = df32{0.5f * tb.hi, 0.5f * tb.lo};
+        }
+        dacc_prod(acc_a, phi_df_affine<FAM>(s1a, s0a, (float)q, L.ic, sh.exp2tab), ga);
+        dacc_prod(acc_b, phi_df_affine<FAM>(s1b, s0b, (float)(a - 1 - q), L.ic, sh.exp2tab), gb);
+      }
+    }
+    if (warp_act) {
+      const df32 sa = lanes_sum_df(dacc_value(acc_a), Q);
+      const df32 sbv = lanes_sum_df(dacc_value(acc_b), Q);
+      if (act && qs == 0) {
+        const df32 Ga = df_mul(sa, ia), Gb = df_mul(sbv, ia);
+        const df32 E = df_add(Ga, Gb), O = df_add(Ga, df_neg(Gb));
+        sh.Gdf[wb][pp] = make_float4(E.hi, E.lo, O.hi, O.lo);
+      }
+    }
+    __syncthreads();
+  }
+  // G_{d-1} from (E, O) into the other buffer, then the common last level.
+  const int eb = (d - 1) & 1, gbuf = eb ^ 1;
+  if (tid < P) {
+    const int t = tid < h ? tid : P - 1 - tid;
+    const float4 eo = sh.Gdf[eb][t];
+    const df32 E{eo.x, eo.y}, O{eo.z, eo.w};
+    const df32 v = tid < h ? df_add(E, O) : df_add(E, df_neg(O));
+    sh.Gdf[gbuf][tid] = make_float4(0.5f * v.hi, 0.5f * v.lo, 0.f, 0.f);
   }
   __syncthreads();
+  last_level<FAM, MDI_PREC_DF64>(sh, Ftab, P, d, a, n_last, prm, out_slot, gbuf);
 }
 
 template <int PREC>
@@ -465,7 +626,8 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
                                                                        const int32_t *__restrict__ order, int count,
                                                                        mdi_batch_desc single,
                                                                        const double *__restrict__ pool,
-                                                                       const void *__restrict__ tables, int P,
+                                                                       const void *__restrict__ tables,
+                                                                       const float4 *__restrict__ paired, int P,
                                                                        int stage, double *__restrict__ out,
                                                                        unsigned *__restrict__ counter,
                                                                        unsigned expect_tag) {
@@ -496,33 +658,47 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
       if (threadIdx.x == 0) out[inst] = __longlong_as_double(0x7ff8000000000000ll);  // NaN marks a bad descriptor
       continue;
     }
-    const size_t tbytes = (size_t)a * P * P * 8;  // cluster part; a multiple of 16 for even P
+    // Basis tables of a: the cluster part (the paired one for real families in
+    // DF64), staged in shared memory when asked and it fits, and the last-axis part.
+    const bool use_paired = PREC == MDI_PREC_DF64 && paired != nullptr && ds.family != MDI_FAM_OSC;
+    const size_t tbytes = (size_t)a * P * P * 8;  // plain cluster part; a multiple of 16 for even P
     const unsigned char *gtab = (const unsigned char *)tables + table_offset(a, P) * 8;
-    const void *Ltab = gtab;
     const void *Ftab = gtab + tbytes;
-    if (stage && tbytes <= (size_t)kNodesSmemTable && ds.d > 1) {
-      if (staged_a != a) {
-        const double2 *src = (const double2 *)gtab;
+    const unsigned char *csrc = use_paired ? (const unsigned char *)(paired + paired_offset(a, P)) : gtab;
+    const size_t cbytes = use_paired ? (size_t)a * P * P * 4 : tbytes;
+    const void *C = csrc;
+    if (stage && cbytes <= (size_t)kNodesSmemTable && ds.d > 1) {
+      const int key = 2 * a + (use_paired ? 1 : 0);
+      if (staged_a != key) {
+        const double2 *src = (const double2 *)csrc;
         double2 *dst = (double2 *)tab_smem;
-        for (size_t i = threadIdx.x; i < tbytes / 16; i += blockDim.x) dst[i] = src[i];
-        staged_a = a;
+        for (size_t i = threadIdx.x; i < cbytes / 16; i += blockDim.x) dst[i] = src[i];
+        staged_a = key;
         __syncthreads();
       }
-      Ltab = tab_smem;
+      C = tab_smem;
     }
     const double *prm = pool + ds.param_offset;
+    if (use_paired) {
+      const float4 *Lpm = (const float4 *)C;
+      if (ds.family == MDI_FAM_EXP) sweep_paired<MDI_FAM_EXP>(sh, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+      else if (ds.family == MDI_FAM_GAUSS)
+        sweep_paired<MDI_FAM_GAUSS>(sh, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+      else sweep_paired<MDI_FAM_PEAK>(sh, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+      continue;
+    }
     switch (ds.family) {
       case MDI_FAM_EXP:
-        sweep_one<MDI_FAM_EXP, PREC>(sh, Ltab, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+        sweep_one<MDI_FAM_EXP, PREC>(sh, C, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
         break;
       case MDI_FAM_OSC:
-        sweep_one<MDI_FAM_OSC, PREC>(sh, Ltab, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+        sweep_one<MDI_FAM_OSC, PREC>(sh, C, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
         break;
       case MDI_FAM_GAUSS:
-        sweep_one<MDI_FAM_GAUSS, PREC>(sh, Ltab, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+        sweep_one<MDI_FAM_GAUSS, PREC>(sh, C, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
         break;
       default:
-        sweep_one<MDI_FAM_PEAK, PREC>(sh, Ltab, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+        sweep_one<MDI_FAM_PEAK, PREC>(sh, C, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
         break;
     }
   }
@@ -573,13 +749,15 @@ static bool df_tables(const NodesConfig &c) {
 static size_t counter_bytes() { return align_up(4 * sizeof(unsigned)); }
 
 // Tag stamped by the preparation: node count and table format.
+static bool paired_tables(const NodesConfig &c) { return c.precision == MDI_PREC_DF64; }
+
 static unsigned nodes_tag(const NodesConfig &c) {
-  return 0x4D440000u | ((unsigned)c.P << 4) | (df_tables(c) ? 1u : 0u);
+  return 0x4D440000u | ((unsigned)c.P << 4) | (df_tables(c) ? 1u : 0u) | (paired_tables(c) ? 2u : 0u);
 }
 
 size_t nodes_batched_workspace_bytes(int count, const NodesConfig &cfg) {
   (void)count;
-  return counter_bytes() + align_up(table_bytes(cfg.P));
+  return counter_bytes() + align_up(table_bytes(cfg.P)) + (paired_tables(cfg) ? align_up(paired_bytes(cfg.P)) : 0);
 }
 size_t nodes_single_workspace_bytes(const NodesConfig &cfg) { return nodes_batched_workspace_bytes(1, cfg); }
 
@@ -597,6 +775,11 @@ mdi_status nodes_prepare(const NodesConfig &cfg, void *workspace, size_t ws_byte
   else nodes_table_kernel<false><<<table_grid, 256, 0, stream>>>(cfg.P, tables);
   mdi_status st = check_launch();
   if (st != MDI_OK) return st;
+  if (paired_tables(cfg)) {
+    float4 *paired = (float4 *)((char *)tables + align_up(table_bytes(cfg.P)));
+    nodes_paired_table_kernel<<<table_grid, 256, 0, stream>>>(cfg.P, paired);
+    if ((st = check_launch()) != MDI_OK) return st;
+  }
   nodes_arm_kernel<<<1, 1, 0, stream>>>(counter, nodes_tag(cfg));
   return check_launch();
 }
@@ -631,8 +814,9 @@ static mdi_status launch_nodes(const mdi_batch_desc *descs, const int32_t *order
     per_sm = occ;
   }
   const int grid = std::max(1, std::min(count, sm_count() * per_sm));
-  nodes_batched_kernel<PREC><<<grid, cfg.block, smem, stream>>>(descs, order, count, single, pool, tables, cfg.P,
-                                                                 cfg.stage, out, counter, nodes_tag(cfg));
+  const float4 *paired = paired_tables(cfg) ? (const float4 *)((char *)tables + align_up(table_bytes(cfg.P))) : nullptr;
+  nodes_batched_kernel<PREC><<<grid, cfg.block, smem, stream>>>(descs, order, count, single, pool, tables, paired,
+                                                                 cfg.P, cfg.stage, out, counter, nodes_tag(cfg));
   return check_launch();
 }
 

@@ -19,7 +19,7 @@ import torch
 
 from . import make_batch_descs, mdi_batch_plan, mdi_lr_batched_prepare, mdi_lr_integrate_batched
 
-CANDIDATE_BLOCKS = (64, 128, 256)
+CANDIDATE_BLOCKS = (32, 64, 128, 256)
 CANDIDATE_TABLE_IN_L1 = (1, 0)
 _cache: Dict[Tuple, Dict] = {}
 

@@ -45,7 +45,7 @@ def test_tuned_graph_replay_matches_oracle_and_direct_launch(precision):
     _check_sample(b, r1.cpu().numpy())
 
 
-@pytest.mark.parametrize("block", [64, 128, 256, 512])
+@pytest.mark.parametrize("block", [32, 64, 128, 256, 512])
 @pytest.mark.parametrize("table_in_l1", [0, 1])
 def test_every_launch_shape_gives_the_same_values(block, table_in_l1):
     b = inputs.batch(count=256, seed=4)
