@@ -3,8 +3,8 @@ profiling one kernel at a time (``python -m paper_2404_08867_gb300.cases NAME
 [REPEATS]``).  Inputs are the seeded synthetic ones of ``inputs``; nothing here
 computes: every launch goes through the C ABI.
 
-  batch-df64      4096-integral batch, double-float node state (block 64, table via L1)
-  batch-fp64      the same batch in FP64
+  batch-df64      4096-integral batch, double-float node state (block 32, table via L1)
+  batch-fp64      the same batch in FP64 (block 64, table via L1)
   levels-d1000    one integral, node state parallel over levels, d = 1000, N = 16:
                   forward and adjoint
   korobov         P_2 Korobov search, n = 65536, d = 4, every a in 1..n/2
@@ -22,19 +22,19 @@ import paper_2404_08867_gb300 as mdi
 from paper_2404_08867_gb300 import inputs
 
 
-def _batch(precision: str):
+def _batch(precision: str, block: int):
     from paper_2404_08867_gb300.tuning import BatchedMDILR
     b = inputs.batch(count=4096, seed=0)
     plan = BatchedMDILR(b.families, b.d, b.a, b.n_last, b.offsets, b.pool, precision=precision, nodes=16)
-    plan.opts.update(block=64, table_in_l1=1)
+    plan.opts.update(block=block, table_in_l1=1)
     return plan.launch
 
 
 def build_case(name: str):
     if name == "batch-df64":
-        return _batch("df64")
+        return _batch("df64", 32)
     if name == "batch-fp64":
-        return _batch("fp64")
+        return _batch("fp64", 64)
     if name == "levels-d1000":
         w = inputs.scale_exp(1000, 16)
         p = torch.as_tensor(w.params).cuda()
