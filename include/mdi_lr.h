@@ -259,12 +259,19 @@ mdi_status mdi_batch_plan(const mdi_batch_desc *descs, int32_t count, const mdi_
  * with a < 1, a >= n or gcd(a, n) > 1 is not admissible: +inf.  best_a[0] = the
  * smallest a attaining the least value (0 if none is admissible).  P_alpha is the
  * same for a and n - a, and for a and its inverse mod n.
- *   values  DEVICE, count doubles;  best_a  DEVICE, one int64.
- * Two launches on `stream`, no workspace.  MDI_EINVAL unless alpha is 2 or 4,
- * 1 <= d <= 256, 1 <= n <= 2^62, a_first >= 0 and count >= 1.  Work: count * n * d / 2.
+ *   values     DEVICE, count doubles;  best_a  DEVICE, one int64
+ *   workspace  DEVICE, >= lattice_korobov_search_workspace_size(n) bytes, 256-byte
+ *              aligned (for n <= 2^24 and d <= 16 a table of the factors
+ *              1 + C B_alpha(r/n), r <= n/2, as float pairs; the terms are then
+ *              double-float products of table entries)
+ * Two or three launches on `stream`.  MDI_EINVAL unless alpha is 2 or 4,
+ * 1 <= d <= 256, 1 <= n <= 2^62, a_first >= 0 and count >= 1; MDI_EWORKSPACE for a
+ * bad workspace.  Work: count * n * d / 2.
  * ------------------------------------------------------------------------- */
 mdi_status lattice_korobov_search(int32_t alpha, int32_t d, int64_t n, int64_t a_first, int64_t count,
-                                  double *values, int64_t *best_a, mdi_stream_t stream);
+                                  double *values, int64_t *best_a, void *workspace, size_t ws_bytes,
+                                  mdi_stream_t stream);
+mdi_status lattice_korobov_search_workspace_size(int64_t n, size_t *bytes);
 
 /* Component-by-component construction, Example 3, with product weights: z[0] = 1
  * and, for s = 1..d-1, z[s] = the z in {1 <= z <= n-1, gcd(z, n) = 1} minimising the
@@ -276,9 +283,11 @@ mdi_status lattice_korobov_search(int32_t alpha, int32_t d, int64_t n, int64_t a
  * the search takes z <= n/2 and, among equal values, the smallest z.
  *   gamma      DEVICE, d doubles;  z  DEVICE, d int64;  e2  DEVICE, d doubles
  *   workspace  DEVICE, >= lattice_cbc_workspace_size(n) bytes, 256-byte aligned
- * 3d - 1 launches on `stream`, no host synchronisation.  MDI_EINVAL unless d >= 1,
- * 2 <= n <= 2^31 and beta is finite; MDI_EWORKSPACE for a bad workspace.
- * Work: d * n^2 / 4.
+ * About 4d launches on `stream`, no host synchronisation; each component's factors
+ * 1 + gamma_s (B_2(r/n) + beta), r <= n/2, are tabulated as float pairs and the
+ * running products kept as float pairs (double-float arithmetic).  MDI_EINVAL
+ * unless d >= 1, 2 <= n <= 2^24 and beta is finite; MDI_EWORKSPACE for a bad
+ * workspace.  Work: d * n^2 / 4.
  * ------------------------------------------------------------------------- */
 mdi_status lattice_cbc(int32_t d, int64_t n, const double *gamma, double beta, int64_t *z, double *e2,
                        void *workspace, size_t ws_bytes, mdi_stream_t stream);

@@ -26,7 +26,7 @@ __all__ = [
     "mdi_lr_integrate_batched", "mdi_lr_batched_workspace_size", "mdi_lr_batched_prepare", "mdi_batch_plan", "mdi_debug_lattice_indices",
     "mdi_lr_grad", "mdi_lr_grad_workspace_size", "MDILR", "mdi_lr", "make_batch_descs", "MdiError", "FAMILY", "STATE", "PRECISION", "BATCH_DESC_DTYPE", "library_path",
     "mdi_midpoint_integrate", "mdi_midpoint_workspace_size", "lattice_korobov_search", "lattice_cbc",
-    "lattice_cbc_workspace_size", "lattice_rule_integrate_shifted", "lattice_rule_shifted_workspace_size",
+    "lattice_cbc_workspace_size", "lattice_korobov_search_workspace_size", "lattice_rule_integrate_shifted", "lattice_rule_shifted_workspace_size",
     "shifted_estimate",
 ]
 
@@ -364,8 +364,16 @@ def mdi_midpoint_integrate(family, params: torch.Tensor, d: int, N: int, n_last:
 # ---------------------------------------------------------------------------
 # Generating-vector construction (Section 2.2)
 # ---------------------------------------------------------------------------
+def lattice_korobov_search_workspace_size(n: int) -> int:
+    b = ctypes.c_size_t()
+    _ffi.check(_ffi.load().lattice_korobov_search_workspace_size(n, ctypes.byref(b)),
+               "lattice_korobov_search_workspace_size")
+    return b.value
+
+
 def lattice_korobov_search(n: int, d: int, alpha: int = 2, a_first: int = 1, count: Optional[int] = None,
-                           values: Optional[torch.Tensor] = None, device="cuda", stream=None):
+                           values: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
+                           device="cuda", stream=None):
     """(values, best_a): P_alpha(z(a)) of eq. (2.4) for a = a_first .. a_first + count - 1
     (default: every a in 1..n-1; +inf where gcd(a, n) > 1) and the smallest a attaining
     the least value, both as CUDA tensors (float64, int64[1])."""
@@ -373,8 +381,10 @@ def lattice_korobov_search(n: int, d: int, alpha: int = 2, a_first: int = 1, cou
     if values is None:
         values = torch.empty(count, dtype=torch.float64, device=device)
     best = torch.zeros(1, dtype=torch.int64, device=values.device)
+    ws = _workspace(lattice_korobov_search_workspace_size(n), values.device, workspace)
     st = _ffi.load().lattice_korobov_search(alpha, d, n, a_first, count, ctypes.c_void_p(values.data_ptr()),
-                                            ctypes.c_void_p(best.data_ptr()), _stream(stream))
+                                            ctypes.c_void_p(best.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                                            ws.numel(), _stream(stream))
     _ffi.check(st, "lattice_korobov_search")
     return values, best
 

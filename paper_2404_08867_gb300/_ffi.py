@@ -48,7 +48,8 @@ SIGNATURES = {
     "mdi_batch_plan": (_I32, [_P, _I32, _c.POINTER(MdiOpts), _P]),
     "mdi_debug_lattice_indices": (_I32, [_I32, _I64, _P, _I64, _I64, _P, _P]),
     "mdi_midpoint_integrate": (_I32, [_I32, _I32, _I64, _I64, _P, _P, _P, _SZ, _P]),
-    "lattice_korobov_search": (_I32, [_I32, _I32, _I64, _I64, _I64, _P, _P, _P]),
+    "lattice_korobov_search": (_I32, [_I32, _I32, _I64, _I64, _I64, _P, _P, _P, _SZ, _P]),
+    "lattice_korobov_search_workspace_size": (_I32, [_I64, _c.POINTER(_SZ)]),
     "lattice_cbc": (_I32, [_I32, _I64, _P, _c.c_double, _P, _P, _P, _SZ, _P]),
     "lattice_cbc_workspace_size": (_I32, [_I64, _c.POINTER(_SZ)]),
     "mdi_midpoint_workspace_size": (_I32, [_I32, _I64, _I64, _c.POINTER(_SZ)]),

@@ -244,9 +244,17 @@ mdi_status mdi_midpoint_integrate(int32_t family, int32_t d, int64_t N, int64_t 
   return midpoint_launch(family, d, N, n_last, params, out, workspace, ws_bytes, (cudaStream_t)stream);
 }
 
+mdi_status lattice_korobov_search_workspace_size(int64_t n, size_t *bytes) {
+  if (!bytes) return MDI_EINVAL;
+  *bytes = korobov_workspace_bytes(n);
+  return *bytes ? MDI_OK : MDI_EINVAL;
+}
+
 mdi_status lattice_korobov_search(int32_t alpha, int32_t d, int64_t n, int64_t a_first, int64_t count,
-                                  double *values, int64_t *best_a, mdi_stream_t stream) {
-  return korobov_search_launch(alpha, d, n, a_first, count, values, best_a, (cudaStream_t)stream);
+                                  double *values, int64_t *best_a, void *workspace, size_t ws_bytes,
+                                  mdi_stream_t stream) {
+  return korobov_search_launch(alpha, d, n, a_first, count, values, best_a, workspace, ws_bytes,
+                               (cudaStream_t)stream);
 }
 
 mdi_status lattice_cbc_workspace_size(int64_t n, size_t *bytes) {

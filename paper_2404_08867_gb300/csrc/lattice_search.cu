@@ -15,8 +15,17 @@
 // doubled, plus k = 0 and (n even) k = n/2.  CBC keeps the running products
 // p(k) = prod_{j<s} (...) of the components chosen so far in device memory (for
 // k <= n/2, by the same symmetry) and searches z <= n/2 (E^2 of n - z equals that of
-// z); each component is three launches -- candidates, a deterministic argmin
-// (smallest z among equal values), the update of p -- with no host round trip.
+// z); each component is four launches -- its factor table, the candidates, a
+// deterministic argmin (smallest z among equal values), the update of p -- with no
+// host round trip.
+//
+// Factor tables (n <= 2^24).  A term's factor depends only on its residue r, and
+// r and n - r share it, so T[r] = 1 + C B(r/n) (Korobov) or 1 + gamma_s (B_2(r/n) +
+// beta) (CBC component s) for r <= n/2 is formed once, as a float pair, and every
+// term becomes one table lookup and a double-float multiply on the FP32 pipe,
+// accumulated with Dot2-style compensated sums; the running CBC products are
+// float pairs too.  Korobov searches with larger n (or d > 16) use the direct FP64
+// kernel; CBC is limited to n <= 2^24 (its work grows as d n^2 / 4).
 #include <algorithm>
 #include <cmath>
 
@@ -160,54 +169,10 @@ __global__ void __launch_bounds__(kArgminThreads) korobov_argmin_kernel(const do
 }
 
 // ---------------------------------------------------------------------------
-// CBC with product weights.  p[k] (k = 0..n/2): products of the chosen components;
-// pref[0]: prod_{j<s} (1 + gamma_j beta).
+// CBC with product weights: the factor of a residue r for component s.
 // ---------------------------------------------------------------------------
-__global__ void cbc_init_kernel(uint64_t half, double *__restrict__ p, double *__restrict__ pref) {
-  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= half; k += (uint64_t)gridDim.x * blockDim.x)
-    p[k] = 1.0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) pref[0] = 1.0;
-}
-
 __device__ __forceinline__ double cbc_factor(double g, double beta, uint64_t r, double inv_n) {
   return fma(g, bernoulli_even<2>((double)r * inv_n) + beta, 1.0);
-}
-
-// vals[t] = [E^(sh)]^2 of (z_1..z_{s-1}, z_first + t) (+inf for gcd(z, n) > 1).
-__global__ void __launch_bounds__(kSearchThreads) cbc_candidates_kernel(int s, uint64_t n,
-                                                                        const double *__restrict__ gamma, double beta,
-                                                                        const double *__restrict__ p,
-                                                                        const double *__restrict__ pref,
-                                                                        uint64_t z_first, uint64_t count,
-                                                                        double *__restrict__ vals) {
-  __shared__ double s_red[kSearchThreads / kWarp];
-  const double inv_n = 1.0 / (double)n, g = gamma[s];
-  const uint64_t h = (n - 1) / 2;
-  for (uint64_t t = blockIdx.x; t < count; t += gridDim.x) {
-    const uint64_t z = z_first + t;
-    if (gcd_u64(z, n) != 1) {  // uniform across the CTA
-      if (threadIdx.x == 0) vals[t] = INFINITY;
-      continue;
-    }
-    uint64_t k0, k1;
-    thread_run(h, threadIdx.x, blockDim.x, k0, k1);
-    k0 += 1;
-    k1 += 1;
-    uint64_t r = (k0 < k1) ? (k0 * z) % n : 0;  // k, z < 2^31
-    double acc = 0.0;
-    for (uint64_t k = k0; k < k1; ++k) {
-      acc = fma(p[k], cbc_factor(g, beta, r, inv_n), acc);
-      r += z;
-      if (r >= n) r -= n;
-    }
-    acc = block_sum(acc, s_red);
-    if (threadIdx.x == 0) {
-      double S = p[0] * cbc_factor(g, beta, 0, inv_n) + 2.0 * acc;
-      if (n % 2 == 0 && n > 1) S += p[n / 2] * cbc_factor(g, beta, (z & 1ull) ? n / 2 : 0, inv_n);
-      vals[t] = -pref[0] * fma(g, beta, 1.0) + S * inv_n;
-    }
-    __syncthreads();
-  }
 }
 
 __global__ void __launch_bounds__(kArgminThreads) cbc_select_kernel(int s, const double *__restrict__ vals,
@@ -222,13 +187,178 @@ __global__ void __launch_bounds__(kArgminThreads) cbc_select_kernel(int s, const
   }
 }
 
-__global__ void cbc_update_kernel(int s, uint64_t n, const double *__restrict__ gamma, double beta,
-                                  const int64_t *__restrict__ z, double *__restrict__ p, double *__restrict__ pref) {
-  const uint64_t half = n / 2, zs = (uint64_t)z[s];
-  const double inv_n = 1.0 / (double)n, g = gamma[s];
+
+// ---------------------------------------------------------------------------
+// Factor-table kernels (double-float)
+// ---------------------------------------------------------------------------
+constexpr uint64_t kTableMaxN = 1ull << 24;
+
+__device__ __forceinline__ float2 split_f2(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+__device__ __forceinline__ uint64_t fold(uint64_t r, uint64_t n) { return r <= n - r ? r : n - r; }
+
+// Block sum of a double-float value in a fixed order; valid in thread 0.
+__device__ __forceinline__ df32 block_sum_df32(df32 v, float2 *scratch) {
+  const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x / kWarp;
+#pragma unroll
+  for (int off = kWarp / 2; off > 0; off >>= 1) v = df_add(v, df_shfl_down(v, off));
+  if (lane == 0) scratch[warp] = make_float2(v.hi, v.lo);
+  __syncthreads();
+  df32 t{0.f, 0.f};
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x + kWarp - 1) / kWarp; ++w) t = df_add(t, df32{scratch[w].x, scratch[w].y});
+  __syncthreads();
+  return t;
+}
+
+template <int ALPHA>
+__global__ void korobov_table_kernel(uint64_t n, float2 *__restrict__ T) {
+  constexpr double C = p_alpha_coef<ALPHA>();
+  const double inv_n = 1.0 / (double)n;
+  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= n / 2; r += (uint64_t)gridDim.x * blockDim.x)
+    T[r] = split_f2(fma(C, bernoulli_even<ALPHA>((double)r * inv_n), 1.0));
+}
+
+template <int ALPHA, int MAXD>
+__global__ void __launch_bounds__(kSearchThreads) korobov_table_criterion_kernel(int d, uint64_t n, uint64_t a_first,
+                                                                                 uint64_t count,
+                                                                                 const float2 *__restrict__ T,
+                                                                                 double *__restrict__ values) {
+  __shared__ uint64_t s_z[MAXD];
+  __shared__ float2 s_red[kSearchThreads / kWarp];
+  __shared__ int s_ok;
+  constexpr int kUnroll = MAXD <= 16 ? MAXD : 1;
+  constexpr double C = p_alpha_coef<ALPHA>();
+  const uint64_t h = (n - 1) / 2;
+  for (uint64_t t = blockIdx.x; t < count; t += gridDim.x) {
+    const uint64_t a = a_first + t;
+    if (threadIdx.x == 0) {
+      const bool ok = a >= 1 && a < n && gcd_u64(a, n) == 1;
+      if (ok) {
+        uint64_t v = 1 % n;
+        for (int j = 0; j < d; ++j) {
+          s_z[j] = v;
+          v = mulmod_u63(v, a, n);
+        }
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) {
+      if (threadIdx.x == 0) values[t] = INFINITY;
+      __syncthreads();
+      continue;
+    }
+    uint64_t k0, k1;
+    thread_run(h, threadIdx.x, blockDim.x, k0, k1);
+    k0 += 1;
+    k1 += 1;
+    uint64_t r[MAXD];
+#pragma unroll(kUnroll)
+    for (int j = 0; j < MAXD; ++j)
+      if (j < d) r[j] = (k0 < k1) ? (k0 * s_z[j]) % n : 0;  // k < 2^23, z < 2^24
+    DfAcc acc;
+    for (uint64_t k = k0; k < k1; ++k) {
+      const float2 f0 = T[fold(r[0], n)];
+      df32 prod{f0.x, f0.y};
+      r[0] += s_z[0];
+      if (r[0] >= n) r[0] -= n;
+#pragma unroll(kUnroll)
+      for (int j = 1; j < MAXD; ++j) {
+        if (j < d) {
+          const float2 f = T[fold(r[j], n)];
+          prod = df_mul(prod, df32{f.x, f.y});
+          r[j] += s_z[j];
+          if (r[j] >= n) r[j] -= n;
+        }
+      }
+      dacc_add(acc, prod);
+    }
+    const df32 tot = block_sum_df32(dacc_value(acc), s_red);
+    if (threadIdx.x == 0) {
+      double p0 = 1.0, pm = 1.0;
+      const double f0 = fma(C, bernoulli_even<ALPHA>(0.0), 1.0);
+      for (int j = 0; j < d; ++j) {
+        p0 *= f0;
+        pm *= fma(C, bernoulli_even<ALPHA>((s_z[j] & 1ull) ? 0.5 : 0.0), 1.0);
+      }
+      const double S = p0 + 2.0 * ((double)tot.hi + (double)tot.lo) + ((n % 2 == 0 && n > 1) ? pm : 0.0);
+      values[t] = -1.0 + S / (double)n;
+    }
+    __syncthreads();
+  }
+}
+
+// CBC with factor tables: T[r] = 1 + gamma_s (B_2(r/n) + beta) for component s; the
+// running products p(k) (k <= n/2) as float pairs.
+__global__ void cbc_df_init_kernel(uint64_t half, float2 *__restrict__ p, double *__restrict__ pref) {
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= half; k += (uint64_t)gridDim.x * blockDim.x)
-    p[k] *= cbc_factor(g, beta, (k * zs) % n, inv_n);
-  if (blockIdx.x == 0 && threadIdx.x == 0) pref[0] *= fma(g, beta, 1.0);
+    p[k] = make_float2(1.f, 0.f);
+  if (blockIdx.x == 0 && threadIdx.x == 0) pref[0] = 1.0;
+}
+
+__global__ void cbc_table_kernel(int s, uint64_t n, const double *__restrict__ gamma, double beta,
+                                 float2 *__restrict__ T) {
+  const double inv_n = 1.0 / (double)n, g = gamma[s];
+  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= n / 2; r += (uint64_t)gridDim.x * blockDim.x)
+    T[r] = split_f2(cbc_factor(g, beta, r, inv_n));
+}
+
+__global__ void __launch_bounds__(kSearchThreads) cbc_df_candidates_kernel(int s, uint64_t n,
+                                                                           const double *__restrict__ gamma,
+                                                                           double beta, const float2 *__restrict__ p,
+                                                                           const float2 *__restrict__ T,
+                                                                           const double *__restrict__ pref,
+                                                                           uint64_t z_first, uint64_t count,
+                                                                           double *__restrict__ vals) {
+  __shared__ float2 s_red[kSearchThreads / kWarp];
+  const uint64_t h = (n - 1) / 2;
+  for (uint64_t t = blockIdx.x; t < count; t += gridDim.x) {
+    const uint64_t z = z_first + t;
+    if (gcd_u64(z, n) != 1) {  // uniform across the CTA
+      if (threadIdx.x == 0) vals[t] = INFINITY;
+      continue;
+    }
+    uint64_t k0, k1;
+    thread_run(h, threadIdx.x, blockDim.x, k0, k1);
+    k0 += 1;
+    k1 += 1;
+    uint64_t r = (k0 < k1) ? (k0 * z) % n : 0;
+    DfAcc acc;
+    for (uint64_t k = k0; k < k1; ++k) {
+      const float2 pk = p[k], f = T[fold(r, n)];
+      dacc_prod(acc, df32{pk.x, pk.y}, df32{f.x, f.y});
+      r += z;
+      if (r >= n) r -= n;
+    }
+    const df32 tot = block_sum_df32(dacc_value(acc), s_red);
+    if (threadIdx.x == 0) {
+      const double inv_n = 1.0 / (double)n, g = gamma[s];
+      const float2 p0 = p[0];
+      double S = ((double)p0.x + (double)p0.y) * cbc_factor(g, beta, 0, inv_n) +
+                 2.0 * ((double)tot.hi + (double)tot.lo);
+      if (n % 2 == 0 && n > 1) {
+        const float2 pm = p[n / 2];
+        S += ((double)pm.x + (double)pm.y) * cbc_factor(g, beta, (z & 1ull) ? n / 2 : 0, inv_n);
+      }
+      vals[t] = -pref[0] * fma(g, beta, 1.0) + S * inv_n;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void cbc_df_update_kernel(int s, uint64_t n, const double *__restrict__ gamma, double beta,
+                                     const int64_t *__restrict__ z, const float2 *__restrict__ T,
+                                     float2 *__restrict__ p, double *__restrict__ pref) {
+  const uint64_t half = n / 2, zs = (uint64_t)z[s];
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= half; k += (uint64_t)gridDim.x * blockDim.x) {
+    const float2 pk = p[k], f = T[fold((k * zs) % n, n)];
+    const df32 v = df_mul(df32{pk.x, pk.y}, df32{f.x, f.y});
+    p[k] = make_float2(v.hi, v.lo);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) pref[0] *= fma(gamma[s], beta, 1.0);
 }
 
 // ---------------------------------------------------------------------------
@@ -245,58 +375,89 @@ static mdi_status korobov_dispatch(int d, uint64_t n, uint64_t a_first, uint64_t
   return check_launch();
 }
 
+size_t korobov_workspace_bytes(int64_t n) {
+  if (n < 1) return 0;
+  return ((uint64_t)n <= kTableMaxN) ? align_up(sizeof(float2) * (size_t)(n / 2 + 1)) : kAlign;
+}
+
 mdi_status korobov_search_launch(int alpha, int d, int64_t n, int64_t a_first, int64_t count, double *values,
-                                 int64_t *best_a, cudaStream_t stream) {
+                                 int64_t *best_a, void *workspace, size_t ws_bytes, cudaStream_t stream) {
   if ((alpha != 2 && alpha != 4) || d < 1 || d > 256 || n < 1 || n > (INT64_C(1) << 62) || a_first < 0 ||
       count < 1 || !values || !best_a)
     return MDI_EINVAL;
-  mdi_status st = alpha == 2 ? korobov_dispatch<2>(d, (uint64_t)n, (uint64_t)a_first, (uint64_t)count, values, stream)
-                             : korobov_dispatch<4>(d, (uint64_t)n, (uint64_t)a_first, (uint64_t)count, values, stream);
+  if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < korobov_workspace_bytes(n)) return MDI_EWORKSPACE;
+  const uint64_t un = (uint64_t)n, ua = (uint64_t)a_first, uc = (uint64_t)count;
+  mdi_status st;
+  if (un <= kTableMaxN && d <= 16) {
+    float2 *T = (float2 *)workspace;
+    const int tgrid = (int)std::max<uint64_t>(1, std::min<uint64_t>((un / 2 + 256) / 256, (uint64_t)sm_count() * 8));
+    if (alpha == 2) korobov_table_kernel<2><<<tgrid, 256, 0, stream>>>(un, T);
+    else korobov_table_kernel<4><<<tgrid, 256, 0, stream>>>(un, T);
+    if ((st = check_launch()) != MDI_OK) return st;
+    const int grid = (int)std::min<uint64_t>(uc, (uint64_t)sm_count() * 16);
+    if (alpha == 2) {
+      if (d <= 8) korobov_table_criterion_kernel<2, 8><<<grid, kSearchThreads, 0, stream>>>(d, un, ua, uc, T, values);
+      else korobov_table_criterion_kernel<2, 16><<<grid, kSearchThreads, 0, stream>>>(d, un, ua, uc, T, values);
+    } else {
+      if (d <= 8) korobov_table_criterion_kernel<4, 8><<<grid, kSearchThreads, 0, stream>>>(d, un, ua, uc, T, values);
+      else korobov_table_criterion_kernel<4, 16><<<grid, kSearchThreads, 0, stream>>>(d, un, ua, uc, T, values);
+    }
+    st = check_launch();
+  } else {
+    st = alpha == 2 ? korobov_dispatch<2>(d, un, ua, uc, values, stream) : korobov_dispatch<4>(d, un, ua, uc, values, stream);
+  }
   if (st != MDI_OK) return st;
-  korobov_argmin_kernel<<<1, kArgminThreads, 0, stream>>>(values, (uint64_t)count, (uint64_t)a_first, best_a);
+  korobov_argmin_kernel<<<1, kArgminThreads, 0, stream>>>(values, uc, ua, best_a);
   return check_launch();
 }
 
+// Workspace: p[n/2+1] (float pairs) | T[n/2+1] (float pairs) | vals[n/2+1] | pref.
 struct CbcLayout {
-  size_t p, vals, pref, total;
+  size_t p, T, vals, pref, total;
 };
 static CbcLayout cbc_layout(int64_t n) {
   CbcLayout L{};
+  const size_t m = (size_t)(n / 2 + 1);
   size_t off = 0;
   L.p = off;
-  off += align_up(sizeof(double) * (size_t)(n / 2 + 1));
+  off += align_up(sizeof(float2) * m);
+  L.T = off;
+  off += align_up(sizeof(float2) * m);
   L.vals = off;
-  off += align_up(sizeof(double) * (size_t)(n / 2 + 1));
+  off += align_up(sizeof(double) * m);
   L.pref = off;
   off += align_up(sizeof(double));
   L.total = off;
   return L;
 }
 
-size_t cbc_workspace_bytes(int64_t n) { return (n >= 2 && n <= (INT64_C(1) << 31)) ? cbc_layout(n).total : 0; }
+size_t cbc_workspace_bytes(int64_t n) { return (n >= 2 && (uint64_t)n <= kTableMaxN) ? cbc_layout(n).total : 0; }
 
 mdi_status cbc_launch(int d, int64_t n, const double *gamma, double beta, int64_t *z, double *e2, void *workspace,
                       size_t ws_bytes, cudaStream_t stream) {
-  if (d < 1 || n < 2 || n > (INT64_C(1) << 31) || !gamma || !z || !e2 || !std::isfinite(beta)) return MDI_EINVAL;
+  if (d < 1 || n < 2 || (uint64_t)n > kTableMaxN || !gamma || !z || !e2 || !std::isfinite(beta)) return MDI_EINVAL;
   if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < cbc_workspace_bytes(n)) return MDI_EWORKSPACE;
   const CbcLayout L = cbc_layout(n);
   char *base = (char *)workspace;
-  double *p = (double *)(base + L.p), *vals = (double *)(base + L.vals), *pref = (double *)(base + L.pref);
+  float2 *p = (float2 *)(base + L.p), *T = (float2 *)(base + L.T);
+  double *vals = (double *)(base + L.vals), *pref = (double *)(base + L.pref);
   const uint64_t un = (uint64_t)n, half = un / 2;
   const int upd_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((half + 256) / 256, (uint64_t)sm_count() * 8));
-  cbc_init_kernel<<<upd_grid, 256, 0, stream>>>(half, p, pref);
+  cbc_df_init_kernel<<<upd_grid, 256, 0, stream>>>(half, p, pref);
   mdi_status st = check_launch();
   if (st != MDI_OK) return st;
   for (int s = 0; s < d; ++s) {
     // z_1 = 1 is fixed (Example 3, step (i)); later components search 1..n/2.
     const uint64_t first = 1, count = (s == 0) ? 1 : std::max<uint64_t>(1, half);
     const int grid = (int)std::min<uint64_t>(count, (uint64_t)sm_count() * 16);
-    cbc_candidates_kernel<<<grid, kSearchThreads, 0, stream>>>(s, un, gamma, beta, p, pref, first, count, vals);
+    cbc_table_kernel<<<upd_grid, 256, 0, stream>>>(s, un, gamma, beta, T);
+    if ((st = check_launch()) != MDI_OK) return st;
+    cbc_df_candidates_kernel<<<grid, kSearchThreads, 0, stream>>>(s, un, gamma, beta, p, T, pref, first, count, vals);
     if ((st = check_launch()) != MDI_OK) return st;
     cbc_select_kernel<<<1, kArgminThreads, 0, stream>>>(s, vals, count, first, z, e2);
     if ((st = check_launch()) != MDI_OK) return st;
     if (s + 1 < d) {
-      cbc_update_kernel<<<upd_grid, 256, 0, stream>>>(s, un, gamma, beta, z, p, pref);
+      cbc_df_update_kernel<<<upd_grid, 256, 0, stream>>>(s, un, gamma, beta, z, T, p, pref);
       if ((st = check_launch()) != MDI_OK) return st;
     }
   }

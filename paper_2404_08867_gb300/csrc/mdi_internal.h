@@ -35,8 +35,9 @@ mdi_status slr_shifted_launch(int family, int d, int64_t n, const int64_t *z, co
                               cudaStream_t stream);
 
 // lattice_search.cu
+size_t korobov_workspace_bytes(int64_t n);  // 0 when n is out of range
 mdi_status korobov_search_launch(int alpha, int d, int64_t n, int64_t a_first, int64_t count, double *values,
-                                 int64_t *best_a, cudaStream_t stream);
+                                 int64_t *best_a, void *workspace, size_t ws_bytes, cudaStream_t stream);
 size_t cbc_workspace_bytes(int64_t n);  // 0 when n is out of range
 mdi_status cbc_launch(int d, int64_t n, const double *gamma, double beta, int64_t *z, double *e2, void *workspace,
                       size_t ws_bytes, cudaStream_t stream);
