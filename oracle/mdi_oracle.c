@@ -556,6 +556,44 @@ double or_midpoint_product(int fam, int d, const uint64_t *Nd, const double *c, 
   return creal(front(fam, w) * prod);
 }
 
+/* The same rule for a ridge integrand f(x) = (c0 + sum_i x_i)^(-p) on the grid
+ * n_1 = ... = n_{d-1} = N, n_d = n_last, by the dimension iteration of Algorithm 1
+ * (m = 1, eq. 2.14c): after the first i axes are summed out, the symbolic function
+ * depends on them only through the digit sum S = k_1 + ... + k_i, so its state is
+ * the weight H_i[S] of each S, H_i[S] = (1/N) sum_{k<N} H_{i-1}[S - k], H_0 = [1].
+ * Then Q = sum_S H_{d-1}[S] (1/n_last) sum_{k<n_last} f at the coordinate sum
+ * (S + (d-1)/2)/N + (k + 1/2)/n_last.  Test 7's f_6 is c0 = 1, p = d + 1. */
+double or_midpoint_ridge(int d, uint64_t N, uint64_t n_last, double c0, double p) {
+  if (d < 1 || N < 1 || n_last < 1) return NAN;
+  const uint64_t L = (uint64_t)(d - 1) * (N - 1) + 1;
+  double *h = (double *)calloc((size_t)L, sizeof(double)), *g = (double *)calloc((size_t)L, sizeof(double));
+  h[0] = 1.0;
+  uint64_t len = 1;
+  for (int i = 1; i < d; ++i) {
+    const uint64_t nlen = len + N - 1;
+    for (uint64_t S = 0; S < nlen; ++S) {
+      double acc = 0.0;
+      for (uint64_t k = 0; k < N; ++k)
+        if (S >= k && S - k < len) acc += h[S - k];
+      g[S] = acc / (double)N;
+    }
+    double *t = h;
+    h = g;
+    g = t;
+    len = nlen;
+  }
+  double q = 0.0;
+  for (uint64_t S = 0; S < len; ++S) {
+    double inner = 0.0;
+    const double base = ((double)S + 0.5 * (double)(d - 1)) / (double)N;
+    for (uint64_t k = 0; k < n_last; ++k) inner += pow(c0 + base + ((double)k + 0.5) / (double)n_last, -p);
+    q += h[S] * inner / (double)n_last;
+  }
+  free(h);
+  free(g);
+  return q;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Exact integrals over [0,1]^d (textbook antiderivatives per axis)           */
 /* ------------------------------------------------------------------------- */

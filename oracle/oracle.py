@@ -76,6 +76,7 @@ def _load():
                 "or_closed_form": (D, [I, I, P, P]),
                 "or_closed_form_grad": (I, [I, I, P, P, P]),
                 "or_slr_shifted": (D, [I, I, U, P, P, P, P]),
+                "or_midpoint_ridge": (D, [I, U, U, D, D]),
                 "or_p_alpha": (D, [I, I, U, P]),
                 "or_korobov_search": (I, [I, I, U, U, U, P, P]),
                 "or_wce2_shift": (D, [I, U, P, P, D]),
@@ -205,6 +206,12 @@ def midpoint_grid(family, d, Nd, c=None, w=None) -> float:
 def midpoint_product(family, d, Nd, c, w=None) -> float:
     Nd, c, w = _u64(Nd), _f64(c, d), _f64(w, d)
     return _load().or_midpoint_product(_fam(family), d, _p(Nd), _p(c), _p(w))
+
+
+def midpoint_ridge(d, N, n_last, c0=1.0, p=None) -> float:
+    """Tensor midpoint rule for (c0 + sum x_i)^(-p) (default p = d + 1, Test 7's f_6)
+    by the dimension iteration with a partial-sum histogram state."""
+    return _load().or_midpoint_ridge(d, N, n_last, c0, float(d + 1) if p is None else float(p))
 
 
 def closed_form(family, d, c, w=None) -> float:

@@ -479,3 +479,34 @@ def test_shift_by_a_lattice_point_permutes_the_points():
     w = np.array([0.1, 0.0, 0.0])
     delta = np.array([(k0 * zi % n) / n for zi in z])
     assert o.slr_shifted("osc", 3, n, z, c, w, delta) == pytest.approx(o.slr("osc", 3, n, z, c, w), abs=1e-13)
+
+
+# ----------------------------------------------------------------------------
+# Ridge integrand of Test 7 in the paper-table mode: histogram state
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("d,N,nl", [(1, 7, 7), (2, 5, 6), (3, 4, 5), (4, 3, 4), (5, 3, 3)])
+def test_midpoint_ridge_equals_grid_bruteforce(d, N, nl):
+    """f_6 = (1 + sum x_i)^-(d+1): the histogram recursion equals the brute-force sum
+    over the whole grid (the oracle's independent point-by-point rule)."""
+    assert o.midpoint_ridge(d, N, nl) == pytest.approx(o.midpoint_grid("ridge", d, [N] * (d - 1) + [nl]), rel=1e-13)
+
+
+@pytest.mark.parametrize("d", [2, 4, 6])
+def test_midpoint_ridge_converges_to_the_exact_integral(d):
+    """The integral of (1 + sum x_i)^-(d+1) over [0,1]^d is 1/(d+1)! (d integrations,
+    each lowering the power by one, and sum_j (-1)^j C(d,j)/(1+j) = 1/(d+1)); the
+    midpoint rule's error falls by 4 when N doubles."""
+    exact = 1.0 / math.factorial(d + 1)
+    e1 = o.midpoint_ridge(d, 12, 12) - exact
+    e2 = o.midpoint_ridge(d, 24, 24) - exact
+    assert abs(e2) < abs(e1)
+    assert 3.6 < e1 / e2 < 4.4
+
+
+def test_midpoint_ridge_general_power_against_numpy():
+    """c0 = 0.5, p = 2.5, d = 2: the direct double sum in numpy."""
+    N, nl = 6, 7
+    x = (np.arange(N) + 0.5) / N
+    y = (np.arange(nl) + 0.5) / nl
+    direct = float(np.mean((0.5 + x[:, None] + y[None, :]) ** -2.5))
+    assert o.midpoint_ridge(2, N, nl, 0.5, 2.5) == pytest.approx(direct, rel=1e-13)
