@@ -378,8 +378,19 @@ def extra_paper_tables(torch, mdi, o):
         if worst is None or d > worst["d"]:
             worst = {"table": table, "integrand": integrand, "d": d, "N": N, "printed": printed, "gpu_rel_err": rel,
                      "ms": ms}
+    # Test 7's ridge integrand f_6 = (1 + sum x_i)^-(d+1) by the histogram state:
+    # device time against d at N = 16 (the paper fits its CPU time against d,
+    # Table 4-2) and the error against the exact 1/(d+1)!.
+    ds, ts = [25, 50, 100, 150], []
+    for d in ds:
+        v, ms = event_ms(torch, lambda: mdi.mdi_midpoint_ridge(d, 16, 16), reps=3)
+        ts.append(ms)
+        if d == 50:
+            ridge50 = abs(v.item() * math.factorial(51) - 1.0)
+    ridge = {"N": 16, "d": ds, "ms": ts, "beta": float(np.polyfit(np.log(ds), np.log(ts), 1)[0]),
+             "d50_rel_err_vs_exact": ridge50}
     return {"workload": "Section 5 MDI-LR columns (tensor midpoint rule on the eq. 3.5 grid)", "rows": rows,
-            "reproduced": ok, "largest": worst}
+            "reproduced": ok, "largest": worst, "ridge_f6": ridge}
 
 
 def extra_lattice_search(torch, mdi, o):

@@ -250,6 +250,25 @@ mdi_status mdi_batch_plan(const mdi_batch_desc *descs, int32_t count, const mdi_
                           int32_t *order);
 
 /* ---------------------------------------------------------------------------
+ * Paper-table mode for the ridge integrand f(x) = (c0 + sum_i x_i)^(-power) of
+ * Test 7 (f_6: c0 = 1, power = d + 1) on the same midpoint grid (n_1 = ... =
+ * n_{d-1} = N, n_d = n_last), by the dimension iteration of Algorithm 1 with m = 1:
+ * after i axes the symbolic function depends only on the digit sum
+ * S = k_1 + ... + k_i, so its state is the weight H_i[S] of each sum,
+ * H_i[S] = (1/N) sum_{k<N} H_{i-1}[S - k]; then
+ *     Q = sum_S H_{d-1}[S] (1/n_last) sum_{k<n_last} f at (S + (d-1)/2)/N + (k + 1/2)/n_last.
+ *   out        DEVICE, one double
+ *   workspace  DEVICE, >= mdi_midpoint_ridge_workspace_size bytes, 256-byte aligned
+ * d + 2 launches on `stream`, FP64.  MDI_EINVAL unless d, N, n_last >= 1, c0 > 0
+ * and power finite, and (d-1)(N-1) + 1 <= 2^26; MDI_EWORKSPACE for a bad
+ * workspace.  f_6's integral is 1/(d+1)!, which leaves the double range near
+ * d = 170.
+ * ------------------------------------------------------------------------- */
+mdi_status mdi_midpoint_ridge(int32_t d, int64_t N, int64_t n_last, double c0, double power, double *out,
+                              void *workspace, size_t ws_bytes, mdi_stream_t stream);
+mdi_status mdi_midpoint_ridge_workspace_size(int32_t d, int64_t N, int64_t n_last, size_t *bytes);
+
+/* ---------------------------------------------------------------------------
  * Generating-vector construction (Section 2.2), FP64.
  *
  * Korobov search, Example 2: for a = a_first .. a_first + count - 1,

@@ -25,7 +25,7 @@ __all__ = [
     "lattice_rule_integrate", "lattice_rule_workspace_size", "lattice_rule_integrate_noalloc", "mdi_lr_integrate", "mdi_lr_workspace_size",
     "mdi_lr_integrate_batched", "mdi_lr_batched_workspace_size", "mdi_lr_batched_prepare", "mdi_batch_plan", "mdi_debug_lattice_indices",
     "mdi_lr_grad", "mdi_lr_grad_workspace_size", "MDILR", "mdi_lr", "make_batch_descs", "MdiError", "FAMILY", "STATE", "PRECISION", "BATCH_DESC_DTYPE", "library_path",
-    "mdi_midpoint_integrate", "mdi_midpoint_workspace_size", "lattice_korobov_search", "lattice_cbc",
+    "mdi_midpoint_integrate", "mdi_midpoint_workspace_size", "mdi_midpoint_ridge", "lattice_korobov_search", "lattice_cbc",
     "lattice_cbc_workspace_size", "lattice_korobov_search_workspace_size", "lattice_rule_integrate_shifted", "lattice_rule_shifted_workspace_size",
     "shifted_estimate",
 ]
@@ -358,6 +358,26 @@ def mdi_midpoint_integrate(family, params: torch.Tensor, d: int, N: int, n_last:
                                             ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
                                             ws.numel(), _stream(stream))
     _ffi.check(st, "mdi_midpoint_integrate")
+    return out
+
+
+def mdi_midpoint_ridge(d: int, N: int, n_last: Optional[int] = None, c0: float = 1.0,
+                       power: Optional[float] = None, out: Optional[torch.Tensor] = None,
+                       workspace: Optional[torch.Tensor] = None, device="cuda", stream=None) -> torch.Tensor:
+    """Midpoint rule on the grid (N, ..., N, n_last) for (c0 + sum x_i)^(-power)
+    (default power = d + 1: Test 7's f_6), by the dimension iteration with a
+    partial-sum histogram state.  Returns a 1-element float64 CUDA tensor."""
+    n_last = N if n_last is None else n_last
+    power = float(d + 1) if power is None else float(power)
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=device)
+    b = ctypes.c_size_t()
+    _ffi.check(_ffi.load().mdi_midpoint_ridge_workspace_size(d, N, n_last, ctypes.byref(b)),
+               "mdi_midpoint_ridge_workspace_size")
+    ws = _workspace(b.value, out.device, workspace)
+    st = _ffi.load().mdi_midpoint_ridge(d, N, n_last, float(c0), power, ctypes.c_void_p(out.data_ptr()),
+                                        ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
+    _ffi.check(st, "mdi_midpoint_ridge")
     return out
 
 

@@ -53,6 +53,8 @@ SIGNATURES = {
     "lattice_cbc": (_I32, [_I32, _I64, _P, _c.c_double, _P, _P, _P, _SZ, _P]),
     "lattice_cbc_workspace_size": (_I32, [_I64, _c.POINTER(_SZ)]),
     "mdi_midpoint_workspace_size": (_I32, [_I32, _I64, _I64, _c.POINTER(_SZ)]),
+    "mdi_midpoint_ridge": (_I32, [_I32, _I64, _I64, _c.c_double, _c.c_double, _P, _P, _SZ, _P]),
+    "mdi_midpoint_ridge_workspace_size": (_I32, [_I32, _I64, _I64, _c.POINTER(_SZ)]),
     "mdi_status_string": (_c.c_char_p, [_I32]),
     "mdi_last_cuda_error": (_c.c_char_p, []),
     "mdi_abi_version": (_I32, []),

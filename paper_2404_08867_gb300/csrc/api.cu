@@ -268,6 +268,17 @@ mdi_status lattice_cbc(int32_t d, int64_t n, const double *gamma, double beta, i
   return cbc_launch(d, n, gamma, beta, z, e2, workspace, ws_bytes, (cudaStream_t)stream);
 }
 
+mdi_status mdi_midpoint_ridge_workspace_size(int32_t d, int64_t N, int64_t n_last, size_t *bytes) {
+  if (!bytes) return MDI_EINVAL;
+  *bytes = ridge_workspace_bytes(d, N, n_last);
+  return *bytes ? MDI_OK : MDI_EINVAL;
+}
+
+mdi_status mdi_midpoint_ridge(int32_t d, int64_t N, int64_t n_last, double c0, double power, double *out,
+                              void *workspace, size_t ws_bytes, mdi_stream_t stream) {
+  return ridge_launch(d, N, n_last, c0, power, out, workspace, ws_bytes, (cudaStream_t)stream);
+}
+
 mdi_status mdi_debug_lattice_indices(int32_t d, int64_t n, const int64_t *z, int64_t j0, int64_t count,
                                      int64_t *r_out, mdi_stream_t stream) {
   return lattice_indices_launch(d, n, z, j0, count, r_out, (cudaStream_t)stream);

@@ -34,6 +34,11 @@ mdi_status slr_shifted_launch(int family, int d, int64_t n, const int64_t *z, co
                               const double *shifts, int R, double *out, void *workspace, size_t ws_bytes,
                               cudaStream_t stream);
 
+// mdi_ridge.cu: paper-table mode for (c0 + sum x_i)^(-p), histogram state
+size_t ridge_workspace_bytes(int d, int64_t N, int64_t n_last);  // 0 when out of range
+mdi_status ridge_launch(int d, int64_t N, int64_t n_last, double c0, double p, double *out, void *workspace,
+                        size_t ws_bytes, cudaStream_t stream);
+
 // lattice_search.cu
 size_t korobov_workspace_bytes(int64_t n);  // 0 when n is out of range
 mdi_status korobov_search_launch(int alpha, int d, int64_t n, int64_t a_first, int64_t count, double *values,

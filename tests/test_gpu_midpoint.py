@@ -53,3 +53,29 @@ def test_gpu_reproduces_printed_mdi_errors(row):
     exact = o.closed_form(fam, d, c, w)
     rel = abs(got - exact) / abs(exact)
     assert abs(rel - float(printed)) <= one_unit(printed), (rel, printed)
+
+
+@pytest.mark.parametrize("d,N,nl,c0,p", [(1, 7, 7, 1.0, None), (2, 5, 6, 1.0, None), (6, 10, 11, 1.0, None),
+                                         (20, 8, 9, 1.0, None), (60, 16, 16, 1.0, None), (3, 300, 301, 0.5, 2.5),
+                                         (150, 4, 5, 1.0, None), (10, 33, 2, 2.0, 7.0)])
+def test_midpoint_ridge_matches_oracle(d, N, nl, c0, p):
+    """Test 7's f_6 = (1 + sum x_i)^-(d+1) (and other c0, p): the GPU's histogram
+    sweep against the oracle's, element by element."""
+    got = mdi.mdi_midpoint_ridge(d, N, nl, c0=c0, power=p).item()
+    ref = o.midpoint_ridge(d, N, nl, c0, p)
+    assert abs(got - ref) <= TOL * abs(ref), (got, ref)
+
+
+def test_midpoint_ridge_approaches_the_exact_integral():
+    import math
+    for d in (3, 8):
+        exact = 1.0 / math.factorial(d + 1)
+        errs = [mdi.mdi_midpoint_ridge(d, N, N).item() - exact for N in (16, 32)]
+        assert 3.6 < errs[0] / errs[1] < 4.4
+
+
+def test_midpoint_ridge_rejects_bad_arguments():
+    with pytest.raises(mdi.MdiError):
+        mdi.mdi_midpoint_ridge(4, 8, 8, c0=0.0)
+    with pytest.raises(mdi.MdiError):
+        mdi.mdi_midpoint_ridge(0, 8, 8)
