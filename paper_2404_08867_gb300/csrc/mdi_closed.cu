@@ -20,6 +20,7 @@
 //   4. one CTA multiplies the S_k in level order.
 // Launch count does not depend on d or on a.
 #include <algorithm>
+#include <cmath>
 
 #include "mdi_common.cuh"
 #include "mdi_internal.h"
@@ -29,7 +30,7 @@ namespace mdi {
 
 constexpr int kScanThreads = 1024;
 constexpr int kChunkThreads = 256;
-constexpr int64_t kChunkQ = 1024;  // cluster points per warp chunk
+constexpr int64_t kChunkQ = 1024;  // most cluster points per warp chunk
 
 // gamma_k (real: the exponent rate, or its imaginary part for OSC) for k = 1..d.
 __global__ void __launch_bounds__(kScanThreads) closed_scan_kernel(int d, double a, const double *__restrict__ params,
@@ -70,15 +71,25 @@ __global__ void __launch_bounds__(kScanThreads) closed_scan_kernel(int d, double
   }
 }
 
-// Chunks: levels k < d-1 have a points, cut into cpl chunks; the last level has
-// n_last points in cpl_last chunks.
+// Chunks: levels k < d-1 have a points, cut into cpl chunks of q points; the last
+// level has n_last points in cpl_last chunks.  q (a multiple of 32, at most 1024)
+// is chosen so that about 32 warps per SM get a chunk when the levels are small.
 struct Chunks {
   int cpl, cpl_last, total;
+  int64_t q;
 };
+static int64_t chunk_q(int d, int64_t a, int64_t n_last) {
+  const double points = (double)(d - 1) * (double)a + (double)n_last;
+  const double target = (double)sm_count() * 32.0;
+  int64_t q = (int64_t)std::ceil(points / target);
+  q = (q + 31) / 32 * 32;
+  return std::max<int64_t>(32, std::min<int64_t>(kChunkQ, q));
+}
 static Chunks make_chunks(int d, int64_t a, int64_t n_last) {
   Chunks c;
-  c.cpl = (int)((a + kChunkQ - 1) / kChunkQ);
-  c.cpl_last = (int)((n_last + kChunkQ - 1) / kChunkQ);
+  c.q = chunk_q(d, a, n_last);
+  c.cpl = (int)((a + c.q - 1) / c.q);
+  c.cpl_last = (int)((n_last + c.q - 1) / c.q);
   c.total = (d - 1) * c.cpl + c.cpl_last;
   return c;
 }
@@ -104,7 +115,7 @@ __global__ void __launch_bounds__(kChunkThreads) closed_chunk_kernel(int d, int6
       j = c - (d - 1) * ch.cpl;
     }
     const int64_t r = (k + 1 < d) ? a : n_last;
-    const int64_t q0 = (int64_t)j * kChunkQ, q1 = min(r, q0 + kChunkQ);
+    const int64_t q0 = (int64_t)j * ch.q, q1 = min(r, q0 + ch.q);
     const double g = gamma[k], invr = 1.0 / (double)r;
     double2 s = make_double2(0.0, 0.0), t = make_double2(0.0, 0.0);
     df32 sr{0.f, 0.f}, si{0.f, 0.f};
@@ -151,11 +162,12 @@ __global__ void __launch_bounds__(kChunkThreads) closed_chunk_kernel(int d, int6
   }
 }
 
-// S_k (and T_k) = (1/r_k) * (chunk sums of level k added in chunk order).
+// The same sums for levels of at most a few chunks: one thread per level, chunks
+// added in order.
 template <bool WITH_T>
-__global__ void closed_reduce_kernel(int d, int64_t a, int64_t n_last, Chunks ch, const double2 *__restrict__ partS,
-                                     const double2 *__restrict__ partT, double2 *__restrict__ S,
-                                     double2 *__restrict__ T) {
+__global__ void closed_reduce_small_kernel(int d, int64_t a, int64_t n_last, Chunks ch,
+                                           const double2 *__restrict__ partS, const double2 *__restrict__ partT,
+                                           double2 *__restrict__ S, double2 *__restrict__ T) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < d; k += gridDim.x * blockDim.x) {
     const int n = k < d - 1 ? ch.cpl : ch.cpl_last, base = chunk_base(k, d, ch.cpl);
     const double invr = 1.0 / (double)((k + 1 < d) ? a : n_last);
@@ -167,6 +179,49 @@ __global__ void closed_reduce_kernel(int d, int64_t a, int64_t n_last, Chunks ch
     S[k] = c_scale(s, invr);
     if constexpr (WITH_T) T[k] = c_scale(t, invr);
   }
+}
+
+// Per-level sums (S_k, and T_k with WITH_T) of the chunk partials.
+template <bool WITH_T>
+static void launch_reduce(int d, int64_t a, int64_t n_last, const Chunks &ch, const double2 *partS,
+                          const double2 *partT, double2 *S, double2 *T, cudaStream_t stream);
+
+// S_k (and T_k) = (1/r_k) * (sum of the chunk sums of level k), one CTA per level:
+// each thread adds a strided subset of the level's chunks, then a fixed tree.
+constexpr int kReduceThreads = 128;
+template <bool WITH_T>
+__global__ void __launch_bounds__(kReduceThreads) closed_reduce_kernel(int d, int64_t a, int64_t n_last, Chunks ch,
+                                                                       const double2 *__restrict__ partS,
+                                                                       const double2 *__restrict__ partT,
+                                                                       double2 *__restrict__ S,
+                                                                       double2 *__restrict__ T) {
+  __shared__ double2 s_red[kReduceThreads / kWarp];
+  for (int k = blockIdx.x; k < d; k += gridDim.x) {
+    const int n = k < d - 1 ? ch.cpl : ch.cpl_last, base = chunk_base(k, d, ch.cpl);
+    const double invr = 1.0 / (double)((k + 1 < d) ? a : n_last);
+    double2 s = make_double2(0.0, 0.0), t = make_double2(0.0, 0.0);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      s = c_add(s, partS[base + j]);
+      if constexpr (WITH_T) t = c_add(t, partT[base + j]);
+    }
+    s = block_sum(s, s_red);
+    if constexpr (WITH_T) t = block_sum(t, s_red);
+    if (threadIdx.x == 0) {
+      S[k] = c_scale(s, invr);
+      if constexpr (WITH_T) T[k] = c_scale(t, invr);
+    }
+  }
+}
+
+template <bool WITH_T>
+static void launch_reduce(int d, int64_t a, int64_t n_last, const Chunks &ch, const double2 *partS,
+                          const double2 *partT, double2 *S, double2 *T, cudaStream_t stream) {
+  if (ch.cpl <= 8 && ch.cpl_last <= 8)
+    closed_reduce_small_kernel<WITH_T><<<std::max(1, std::min((d + 255) / 256, sm_count() * 4)), 256, 0, stream>>>(
+        d, a, n_last, ch, partS, partT, S, T);
+  else
+    closed_reduce_kernel<WITH_T><<<std::max(1, std::min(d, sm_count() * 16)), kReduceThreads, 0, stream>>>(
+        d, a, n_last, ch, partS, partT, S, T);
 }
 
 // out = Re(front * prod_k S_k) by a fixed tree: each thread multiplies a run of
@@ -239,8 +294,8 @@ static ClosedLayout closed_layout(int d, int64_t a, int64_t n_last, bool grad) {
 static bool closed_sizes_ok(int d, int64_t a, int64_t n_last) {
   if (d < 1 || d > (1 << 20) || a < 1 || n_last < 1) return false;
   // chunk count must fit an int
-  return (double)(d - 1) * (double)((a + kChunkQ - 1) / kChunkQ) + (double)((n_last + kChunkQ - 1) / kChunkQ) <
-         (double)(1 << 30);
+  const int64_t q = chunk_q(d, a, n_last);
+  return (double)(d - 1) * (double)((a + q - 1) / q) + (double)((n_last + q - 1) / q) < (double)(1 << 30);
 }
 
 size_t closed_workspace_bytes(int d, int64_t a, int64_t n_last) {
@@ -265,8 +320,7 @@ static mdi_status run_levels_sums(int d, int64_t a, int64_t n_last, const double
   closed_chunk_kernel<FAM, PREC, WITH_T><<<chunk_grid(ch), kChunkThreads, 0, stream>>>(d, a, n_last, ch, gamma, partS,
                                                                                      partT);
   if ((st = check_launch()) != MDI_OK) return st;
-  closed_reduce_kernel<WITH_T><<<std::max(1, std::min((d + 255) / 256, sm_count() * 4)), 256, 0, stream>>>(
-      d, a, n_last, ch, partS, partT, S, T);
+  launch_reduce<WITH_T>(d, a, n_last, ch, partS, partT, S, T, stream);
   return check_launch();
 }
 
@@ -327,7 +381,7 @@ __global__ void __launch_bounds__(kChunkThreads) midpoint_chunk_kernel(int d, in
       j = c - (d - 1) * ch.cpl;
     }
     const int64_t r = (k + 1 < d) ? N : n_last;
-    const int64_t q0 = (int64_t)j * kChunkQ, q1 = min(r, q0 + kChunkQ);
+    const int64_t q0 = (int64_t)j * ch.q, q1 = min(r, q0 + ch.q);
     const double invr = 1.0 / (double)r;
     const AxisParams ap = load_axis(params, d, k);
     double2 s = make_double2(0.0, 0.0);
@@ -349,8 +403,7 @@ static mdi_status run_midpoint(int d, int64_t N, int64_t n_last, const double *p
   midpoint_chunk_kernel<FAM><<<chunk_grid(ch), kChunkThreads, 0, stream>>>(d, N, n_last, ch, params, partS);
   mdi_status st = check_launch();
   if (st != MDI_OK) return st;
-  closed_reduce_kernel<false><<<std::max(1, std::min((d + 255) / 256, sm_count() * 4)), 256, 0, stream>>>(
-      d, N, n_last, ch, partS, partS, S, S);
+  launch_reduce<false>(d, N, n_last, ch, partS, partS, S, S, stream);
   if ((st = check_launch()) != MDI_OK) return st;
   closed_product_kernel<FAM><<<1, kProdThreads, 0, stream>>>(d, params, S, out);
   return check_launch();

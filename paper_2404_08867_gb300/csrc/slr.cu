@@ -19,7 +19,7 @@ namespace mdi {
 
 constexpr int kSlrMaxD = 256;
 constexpr int kSlrThreads = 256;
-constexpr int kSlrMinRun = 32;  // minimum indices per thread (amortises the set-up)
+constexpr int kSlrMinRun = 4;  // minimum indices per thread (amortises the exact set-up of the residues)
 
 struct SlrArgs {
   uint64_t n;
@@ -223,8 +223,12 @@ static void launch_slr_shifted(int grid, int R, const SlrArgs &args, const doubl
 }
 
 static int slr_shifted_grid(uint64_t n, int R) {
-  // about the same number of resident CTAs in total as one unshifted launch
-  return std::max(1, slr_grid(n) / std::max(1, std::min(R, slr_grid(n))));
+  // CTAs per replicate: the R replicates together fill the GPU as one launch over
+  // n * R points would, and none uses more CTAs than a single unshifted launch.
+  const double max_threads = (double)sm_count() * 8 * kSlrThreads;
+  const double threads = std::min(max_threads, std::ceil((double)n * (double)R / kSlrMinRun));
+  const int per = (int)std::ceil(threads / (double)R / kSlrThreads);
+  return std::max(1, std::min(per, slr_grid(n)));
 }
 
 size_t slr_shifted_workspace_bytes(int d, int64_t n, int R) {
