@@ -220,8 +220,10 @@ typedef struct {
 
 /* One-time set-up of a workspace for mdi_lr_integrate_batched: builds the
  * barycentric basis tables l_t((q + xi_p)/a) for a = 1..64 and the P of opts (they
- * depend on nothing else), zeroes the work-queue counters and stamps a tag naming
- * opts->nodes and the table format of opts->precision.  Enqueued on `stream`; a
+ * depend on nothing else) -- for MDI_PREC_DF64 also the paired table
+ * l_t +- l_{P-1-t} that the real families' sweep uses -- zeroes the work-queue
+ * counters and stamps a tag naming opts->nodes and the table format of
+ * opts->precision.  Enqueued on `stream`; a
  * prepared workspace serves any number of batched calls with the same nodes and
  * precision.  Call it again after a batched call failed to launch. */
 mdi_status mdi_lr_batched_prepare(const mdi_opts *opts, void *workspace, size_t ws_bytes, mdi_stream_t stream);

@@ -32,7 +32,12 @@
 //                    double-float, the state in double between levels;
 //   DF64             coordinates, phi, interpolation, sums and the state in
 //                    double-float (no FP64 instruction per cluster point or per
-//                    level); OSC keeps phi in double.
+//                    level); OSC keeps phi in double.  The real families use
+//                    paired cluster points (sweep_paired): by the symmetry of
+//                    the nodes, one pass over a table of sums and differences of
+//                    basis values interpolates the point u of node p and the
+//                    point 1 - u of node P-1-p, lanes are pair-major, and the
+//                    state is kept as sums and differences of mirrored nodes.
 #include <algorithm>
 
 #include "mdi_common.cuh"
