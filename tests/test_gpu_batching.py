@@ -66,3 +66,58 @@ def test_graph_replays_after_input_update():
     plan.pool.copy_(torch.from_numpy(b2.pool))
     out = plan.run().cpu().numpy()
     _check_sample(b2, out, k=24, seed=1)
+
+
+def test_bench_batch_in_the_bench_launch_configuration():
+    """The bench's own workload (4096 integrals, seed 0, DF64) through the bench's
+    path -- autotuned shape, CUDA-graph capture, replay -- with 96 sampled outputs
+    against the oracle, and the replay equal to a direct launch of the same shape."""
+    b = inputs.batch(count=4096, seed=0)
+    plan = _plan(b, "df64")
+    plan.tune(reps=2)
+    direct = plan.launch().clone()
+    plan.capture()
+    replay = plan.run().clone()
+    torch.cuda.synchronize()
+    assert torch.equal(direct, replay)
+    _check_sample(b, replay.cpu().numpy(), k=96, seed=7)
+
+
+def _descs_dev(descs):
+    return torch.from_numpy(descs.view(np.uint8).copy()).cuda()
+
+
+@pytest.mark.parametrize("precision", ["df64", "fp64"])
+def test_injected_faults_are_reported_not_run(precision):
+    """Host-side fault injection: descriptors outside the limits give NaN in their own
+    output only; a zeroed (unprepared) workspace and one prepared for another node
+    count (whose tag differs) give NaN everywhere; order entries outside the batch are
+    skipped.  Every
+    one of these is rejected before the kernel touches memory for that entry."""
+    import paper_2404_08867_gb300 as mdi
+    b = inputs.batch(count=16, seed=2)
+    descs = mdi.make_batch_descs(b.families, b.d, b.a, b.n_last, b.offsets)
+    pool = torch.as_tensor(b.pool).cuda()
+    good = mdi.mdi_lr_integrate_batched(_descs_dev(descs), pool, 16, precision=precision).cpu().numpy()
+    bad = descs.copy()
+    bad["a"][3], bad["d"][5], bad["family"][7], bad["n_last"][9], bad["param_offset"][11] = 65, 0, 9, 5000, -8
+    out = mdi.mdi_lr_integrate_batched(_descs_dev(bad), pool, 16, precision=precision).cpu().numpy()
+    hit = [3, 5, 7, 9, 11]
+    assert np.all(np.isnan(out[hit]))
+    keep = [i for i in range(16) if i not in hit]
+    np.testing.assert_array_equal(out[keep], good[keep])
+    nbytes = mdi.mdi_lr_batched_workspace_size(16, nodes=16, precision=precision)
+    zeroed = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    out = mdi.mdi_lr_integrate_batched(_descs_dev(descs), pool, 16, workspace=zeroed, precision=precision)
+    assert torch.isnan(out).all()
+    # prepared for P = 18: large enough, but its tag names another node count
+    other = mdi.mdi_lr_batched_prepare(nodes=18, precision=precision)
+    assert other.numel() >= nbytes
+    out = mdi.mdi_lr_integrate_batched(_descs_dev(descs), pool, 16, workspace=other, precision=precision)
+    assert torch.isnan(out).all()
+    order = torch.as_tensor(np.array([-1] + list(range(15)), dtype=np.int32)).cuda()
+    filled = torch.full((16,), 7.0, dtype=torch.float64, device="cuda")
+    out = mdi.mdi_lr_integrate_batched(_descs_dev(descs), pool, 16, order=order, out=filled,
+                                       precision=precision).cpu().numpy()
+    assert out[15] == 7.0
+    np.testing.assert_array_equal(out[:15], good[:15])
