@@ -199,7 +199,8 @@ def run_reference(args, rank, world):
     line = {"metric": METRIC, "value": value, "unit": "integrals/s", "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.count, "fp64"),
+            "config": workload_config(args.count, args.precision),  # the same workload as our arm
+            "reference_arithmetic": "f64 (the oracle computes every integral in double)",
             "cpu_baseline": {"value": value, "unit": "integrals/s", "cores": 1, "kind": "oracle",
                              "sample": f"{per_step} integrals of the batch per step (node state, P=16)"},
             "e2e": {"value": value, "unit": "integrals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
