@@ -14,8 +14,11 @@ inputs resident in HBM, L2 flushed between steps), the same metric end to end
 the roofline of the batched kernel, the CPU oracle on a bounded sample, SM clocks
 sampled during the timed region, and (unless --no-extras) the other workloads:
 the FP64 mode of the same batch, the d = 4 comparison of MDI-LR with the plain
-lattice kernel including time to 1e-6, the precision modes on the oscillatory
-d = 50 integral, the adjoint on the d = 100 Gaussian, and the cost-vs-d sweep.
+lattice kernel including time to 1e-6 (with a Korobov parameter from the GPU's
+P_2 search, and 16 random shifts), the precision modes on the oscillatory d = 50
+integral, the adjoint on the d = 100 Gaussian, the cost-vs-d sweep, the paper's
+printed MDI-LR errors recomputed in the paper-table mode (and Test 7's ridge
+integrand), and the Korobov search and CBC construction at n = 65536.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank sweeps its own batch (weak scaling, no collective on
