@@ -8,12 +8,24 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mdi_common.cuh"
 #include "mdi_internal.h"
 
 namespace mdi {
 
 static thread_local std::string g_last_cuda_error;
+
+// One NVTX range per compute call of the ABI, named after it, so a profiler can
+// attribute the kernels it sees to calls (header-only NVTX 3: without an attached
+// tool a push or pop is a pointer check).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 void set_cuda_error(cudaError_t e) {
   g_last_cuda_error = std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e);
@@ -95,6 +107,7 @@ mdi_status lattice_rule_workspace_size(int32_t d, int64_t n, size_t *bytes) {
 mdi_status lattice_rule_integrate(int32_t family, int32_t d, int64_t n, const int64_t *z, const double *params,
                                   int32_t precision, double *out, void *workspace, size_t ws_bytes,
                                   mdi_stream_t stream) {
+  NvtxRange nvtx_scope("lattice_rule_integrate");
   if (!family_ok(family)) return MDI_EINVAL;
   return slr_launch(family, d, n, z, params, precision, out, workspace, ws_bytes, (cudaStream_t)stream);
 }
@@ -108,12 +121,14 @@ mdi_status lattice_rule_shifted_workspace_size(int32_t d, int64_t n, int32_t R, 
 mdi_status lattice_rule_integrate_shifted(int32_t family, int32_t d, int64_t n, const int64_t *z,
                                           const double *params, const double *shifts, int32_t R, double *out,
                                           void *workspace, size_t ws_bytes, mdi_stream_t stream) {
+  NvtxRange nvtx_scope("lattice_rule_integrate_shifted");
   if (!family_ok(family)) return MDI_EINVAL;
   return slr_shifted_launch(family, d, n, z, params, shifts, R, out, workspace, ws_bytes, (cudaStream_t)stream);
 }
 
 mdi_status lattice_rule_integrate_noalloc(int32_t family, int32_t d, int64_t n, const int64_t *z, const double *params,
                                           int32_t precision, double *out, mdi_stream_t stream) {
+  NvtxRange nvtx_scope("lattice_rule_integrate_noalloc");
   if (!family_ok(family)) return MDI_EINVAL;
   return slr_launch_noalloc(family, d, n, z, params, precision, out, (cudaStream_t)stream);
 }
@@ -145,6 +160,7 @@ mdi_status mdi_lr_workspace_size(int32_t family, int32_t d, int64_t a, int64_t n
 mdi_status mdi_lr_integrate(int32_t family, int32_t d, int64_t a, int64_t n_last, const double *params,
                             const mdi_opts *opts, double *out, void *workspace, size_t ws_bytes,
                             mdi_stream_t stream) {
+  NvtxRange nvtx_scope("mdi_lr_integrate");
   if (!family_ok(family) || d < 1 || a < 1 || n_last < 1 || !params || !out || !opts_ok(opts)) return MDI_EINVAL;
   const int precision = opts ? opts->precision : MDI_PREC_FP64;
   cudaStream_t s = (cudaStream_t)stream;
@@ -180,6 +196,7 @@ mdi_status mdi_lr_grad_workspace_size(int32_t family, int32_t d, int64_t a, int6
 mdi_status mdi_lr_grad(int32_t family, int32_t d, int64_t a, int64_t n_last, const double *params,
                        const mdi_opts *opts, double *value, double *grad, void *workspace, size_t ws_bytes,
                        mdi_stream_t stream) {
+  NvtxRange nvtx_scope("mdi_lr_grad");
   if (!family_ok(family) || d < 1 || a < 1 || n_last < 1 || !params || !grad || !opts_ok(opts)) return MDI_EINVAL;
   const int precision = opts ? opts->precision : MDI_PREC_FP64;
   if (precision != MDI_PREC_FP64) return MDI_EUNSUPPORTED;
@@ -200,6 +217,7 @@ mdi_status mdi_lr_batched_workspace_size(int32_t count, const mdi_opts *opts, si
 }
 
 mdi_status mdi_lr_batched_prepare(const mdi_opts *opts, void *workspace, size_t ws_bytes, mdi_stream_t stream) {
+  NvtxRange nvtx_scope("mdi_lr_batched_prepare");
   if (!opts_ok(opts)) return MDI_EINVAL;
   return nodes_prepare(nodes_config(opts), workspace, ws_bytes, (cudaStream_t)stream);
 }
@@ -207,6 +225,7 @@ mdi_status mdi_lr_batched_prepare(const mdi_opts *opts, void *workspace, size_t 
 mdi_status mdi_lr_integrate_batched(const mdi_batch_desc *descs, const int32_t *order, int32_t count,
                                     const double *param_pool, const mdi_opts *opts, double *out, void *workspace,
                                     size_t ws_bytes, mdi_stream_t stream) {
+  NvtxRange nvtx_scope("mdi_lr_integrate_batched");
   if (!opts_ok(opts)) return MDI_EINVAL;
   if (opts && opts->state != MDI_STATE_AUTO && opts->state != MDI_STATE_NODES) return MDI_EUNSUPPORTED;
   return nodes_batched_launch(descs, order, count, param_pool, nodes_config(opts), out, workspace, ws_bytes,
@@ -240,6 +259,7 @@ mdi_status mdi_midpoint_workspace_size(int32_t d, int64_t N, int64_t n_last, siz
 
 mdi_status mdi_midpoint_integrate(int32_t family, int32_t d, int64_t N, int64_t n_last, const double *params,
                                   double *out, void *workspace, size_t ws_bytes, mdi_stream_t stream) {
+  NvtxRange nvtx_scope("mdi_midpoint_integrate");
   if (!family_ok(family) || d < 1 || N < 1 || n_last < 1 || !params || !out) return MDI_EINVAL;
   return midpoint_launch(family, d, N, n_last, params, out, workspace, ws_bytes, (cudaStream_t)stream);
 }
@@ -253,6 +273,7 @@ mdi_status lattice_korobov_search_workspace_size(int64_t n, size_t *bytes) {
 mdi_status lattice_korobov_search(int32_t alpha, int32_t d, int64_t n, int64_t a_first, int64_t count,
                                   double *values, int64_t *best_a, void *workspace, size_t ws_bytes,
                                   mdi_stream_t stream) {
+  NvtxRange nvtx_scope("lattice_korobov_search");
   return korobov_search_launch(alpha, d, n, a_first, count, values, best_a, workspace, ws_bytes,
                                (cudaStream_t)stream);
 }
@@ -265,6 +286,7 @@ mdi_status lattice_cbc_workspace_size(int64_t n, size_t *bytes) {
 
 mdi_status lattice_cbc(int32_t d, int64_t n, const double *gamma, double beta, int64_t *z, double *e2,
                        void *workspace, size_t ws_bytes, mdi_stream_t stream) {
+  NvtxRange nvtx_scope("lattice_cbc");
   return cbc_launch(d, n, gamma, beta, z, e2, workspace, ws_bytes, (cudaStream_t)stream);
 }
 
@@ -276,6 +298,7 @@ mdi_status mdi_midpoint_ridge_workspace_size(int32_t d, int64_t N, int64_t n_las
 
 mdi_status mdi_midpoint_ridge(int32_t d, int64_t N, int64_t n_last, double c0, double power, double *out,
                               void *workspace, size_t ws_bytes, mdi_stream_t stream) {
+  NvtxRange nvtx_scope("mdi_midpoint_ridge");
   return ridge_launch(d, N, n_last, c0, power, out, workspace, ws_bytes, (cudaStream_t)stream);
 }
 
