@@ -121,3 +121,39 @@ def test_workspace_queries(lib):
     assert mdi.lattice_rule_workspace_size(4, 65536) >= 8
     assert mdi.mdi_lr_workspace_size("exp", 1000, 16, 16, state="closed") >= 8 * 1000
     assert mdi.mdi_lr_batched_workspace_size(4096, nodes=16) > 4 * 2**20
+
+
+def test_new_entry_points_validate_before_launching(lib):
+    """The paper-table, ridge, shifted-rule and search entry points refuse bad
+    arguments and workspaces with status codes, before any launch (no GPU here)."""
+    fake = ctypes.c_void_p(0x1000)
+    E, W = _ffi.MDI_EINVAL, _ffi.MDI_EWORKSPACE
+    # tensor midpoint rule: family, d, N, n_last, workspace
+    assert lib.mdi_midpoint_integrate(7, 4, 8, 8, fake, fake, fake, 1 << 20, _null()) == E
+    assert lib.mdi_midpoint_integrate(2, 0, 8, 8, fake, fake, fake, 1 << 20, _null()) == E
+    assert lib.mdi_midpoint_integrate(2, 4, 0, 8, fake, fake, fake, 1 << 20, _null()) == E
+    assert lib.mdi_midpoint_integrate(2, 4, 8, 8, fake, fake, _null(), 1 << 20, _null()) == W
+    assert lib.mdi_midpoint_integrate(2, 4, 8, 8, fake, fake, ctypes.c_void_p(0x1008), 1 << 20, _null()) == W
+    # ridge: c0 > 0, finite power, sizes
+    assert lib.mdi_midpoint_ridge(4, 8, 8, 0.0, 5.0, fake, fake, 1 << 20, _null()) == E
+    assert lib.mdi_midpoint_ridge(4, 8, 8, 1.0, float("inf"), fake, fake, 1 << 20, _null()) == E
+    assert lib.mdi_midpoint_ridge(4, 8, 8, 1.0, 5.0, fake, fake, 8, _null()) == W
+    b = ctypes.c_size_t()
+    assert lib.mdi_midpoint_ridge_workspace_size(1 << 20, 1 << 20, 8, ctypes.byref(b)) == E  # histogram > 2^26
+    # shifted rule: R range, z range
+    z = (ctypes.c_int64 * 2)(1, 5)
+    zp = ctypes.cast(z, ctypes.c_void_p)
+    assert lib.lattice_rule_integrate_shifted(0, 2, 11, zp, fake, fake, 0, fake, fake, 1 << 20, _null()) == E
+    assert lib.lattice_rule_integrate_shifted(0, 2, 11, zp, fake, fake, 70000, fake, fake, 1 << 20, _null()) == E
+    assert lib.lattice_rule_integrate_shifted(0, 2, 5, zp, fake, fake, 2, fake, fake, 1 << 20, _null()) == E  # z >= n
+    # Korobov search: alpha, d, count, workspace
+    assert lib.lattice_korobov_search(3, 4, 101, 1, 10, fake, fake, fake, 1 << 20, _null()) == E
+    assert lib.lattice_korobov_search(2, 257, 101, 1, 10, fake, fake, fake, 1 << 20, _null()) == E
+    assert lib.lattice_korobov_search(2, 4, 101, 1, 0, fake, fake, fake, 1 << 20, _null()) == E
+    assert lib.lattice_korobov_search(2, 4, 101, 1, 10, fake, fake, _null(), 1 << 20, _null()) == W
+    # CBC: n range (tabulated factors, n <= 2^24), beta finite, workspace
+    assert lib.lattice_cbc(4, 1, fake, 0.0, fake, fake, fake, 1 << 20, _null()) == E
+    assert lib.lattice_cbc(4, (1 << 24) + 1, fake, 0.0, fake, fake, fake, 1 << 30, _null()) == E
+    assert lib.lattice_cbc(4, 101, fake, float("nan"), fake, fake, fake, 1 << 20, _null()) == E
+    assert lib.lattice_cbc(4, 101, fake, 0.0, fake, fake, fake, 8, _null()) == W
+    assert lib.lattice_cbc_workspace_size((1 << 24) + 1, ctypes.byref(b)) == E
