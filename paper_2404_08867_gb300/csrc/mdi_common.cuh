@@ -271,13 +271,14 @@ __device__ __forceinline__ df32 df_exp(df32 x, const float2 *__restrict__ tab) {
 
 // 1/x for a positive double-float x: float reciprocal refined by one
 // Newton-Raphson step, y = y0 + y0 (1 - x y0) (quadratic convergence: the
-// residual 2^-24 squares to 2^-48).
+// residual 2^-24 squares to 2^-48).  t = x y0 lies within 2^-22 of 1, so
+// 1 - t.hi is exact (Sterbenz), and (1 - t.hi) - t.lo rounds only at 2^-24 of a
+// residual that is itself below 2^-22.
 __device__ __forceinline__ df32 df_rcp(df32 x) {
   const float y0 = __frcp_rn(x.hi);
   const df32 t = df_mul_f(x, y0);
-  const df32 e = df_add(df32{1.0f, 0.0f}, df_neg(t));
-  const float corr = __fmul_rn(y0, __fadd_rn(e.hi, e.lo));
-  return fast_two_sum(y0, corr);
+  const float e = __fsub_rn(__fsub_rn(1.0f, t.hi), t.lo);
+  return fast_two_sum(y0, __fmul_rn(y0, e));
 }
 
 // ---------------------------------------------------------------------------
