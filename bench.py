@@ -351,6 +351,32 @@ def profiled_traffic(precision: str):
     return entry[1] if entry is not None and kernel_sources_key() == entry[0] else None
 
 
+def extra_paper_context(torch, mdi, o):
+    """The paper's own MDI-LR CPU times (Matlab on an Intel Xeon Gold 6226R at
+    2.90 GHz, one process, Section 4) beside this GPU's time for the nearest
+    workloads, context only: the paper's printed columns use the midpoint point set
+    (reading R1) where this path computes the text's transformed-lattice sum, on
+    the same integrand, d and N."""
+    import math
+    hw = "Matlab, Intel Xeon Gold 6226R @ 2.90 GHz, 32 GB (Section 4)"
+    cases = [
+        ("exp(sum (-1)^(i+1) x_i), d=1000, a=N=8", "exp", 1000, 8,
+         np.array([(-1.0) ** i for i in range(1000)]), np.zeros(1000), 69992.0, "Table 2-3"),
+        ("prod 1/(0.9^2 + (x_i - 0.6)^2), d=1000, a=N=20", "peak", 1000, 20, np.full(1000, 1.0 / 0.9),
+         np.full(1000, 0.6), 189.13, "Table 2-3"),
+        ("(2 pi)^(-1/2) exp(-|x|^2/2), d=12, N=10", "gauss", 12, 10, np.full(12, 1.0 / math.sqrt(2.0)),
+         np.zeros(12), 4.592, "Table 2-1"),
+    ]
+    out = {"hardware_of_paper": hw, "cases": []}
+    for name, fam, d, a, c, w, paper_s, table in cases:
+        p = torch.as_tensor(np.concatenate([c, w])).cuda()
+        v, ms = event_ms(torch, lambda: mdi.mdi_lr_integrate(fam, p, d, a, a), reps=3)
+        exact = o.closed_form(fam, d, c, w)
+        out["cases"].append({"workload": name, "gpu_ms": ms, "gpu_rel_err_vs_exact": abs(v.item() - exact) / abs(exact),
+                             "paper_cpu_s": paper_s, "paper_source": table, "ratio_paper_over_gpu": paper_s * 1e3 / ms})
+    return out
+
+
 PAPER_ROWS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "midpoint_printed.txt")
 
 
@@ -633,6 +659,7 @@ def main():
             line["scale_workload"] = extra_scale(torch, mdi, o, inputs)
             line["paper_table_workload"] = extra_paper_tables(torch, mdi, o)
             line["lattice_search_workload"] = extra_lattice_search(torch, mdi, o)
+            line["paper_context"] = extra_paper_context(torch, mdi, o)
         rate, n_done, secs = cpu_oracle_sample(b, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "integrals/s", "cores": 1, "kind": "oracle",
                                 "sample": f"first {n_done} integrals of the batch, {secs:.1f} s single-threaded"}
