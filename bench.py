@@ -351,6 +351,38 @@ def profiled_traffic(precision: str):
     return entry[1] if entry is not None and kernel_sources_key() == entry[0] else None
 
 
+def extra_batch_vs_plain(torch, mdi, o, inputs):
+    """The batch's integrals whose full point set is small enough for the plain
+    lattice kernel (n = N^d <= 2^27): the plain kernel on the Korobov lattice with
+    a = N and n = N^d -- by Lemma 3.2 the same sum as MDI-LR's text reading --
+    one call per integral, beside one batched MDI-LR launch (DF64) over the same
+    integrals; their values agree to the node state's approximation."""
+    from paper_2404_08867_gb300.tuning import BatchedMDILR
+    b = inputs.batch(count=COUNT, seed=0)
+    idx = [i for i in range(len(b)) if float(b.a[i]) ** int(b.d[i]) <= 2.0 ** 27]
+    fams = [b.families[i] for i in idx]
+    ds, as_ = b.d[idx], b.a[idx]
+    offs = np.concatenate([[0], np.cumsum(2 * ds[:-1])]).astype(np.int64)
+    pool = np.concatenate([b.pool[b.offsets[i]:b.offsets[i] + 2 * b.d[i]] for i in idx])
+    plan = BatchedMDILR(fams, ds, as_, as_, offs, pool, precision="df64", nodes=P_NODES)
+    plan.tune()
+    mv, mdi_ms = event_ms(torch, lambda: plan.launch(), reps=3)
+    mv = mv.cpu().numpy()
+    slr_ms, worst = 0.0, 0.0
+    for j, i in enumerate(idx):
+        d, a = int(b.d[i]), int(b.a[i])
+        n = a ** d
+        p = torch.as_tensor(pool[offs[j]:offs[j] + 2 * d]).cuda()
+        z = o.korobov_z(d, a, n).astype(np.int64)
+        v, ms = event_ms(torch, lambda: mdi.lattice_rule_integrate(fams[j], p, n, z), reps=1)
+        slr_ms += ms
+        worst = max(worst, abs(v.item() - mv[j]) / abs(mv[j]))
+    return {"workload": f"{len(idx)} integrals of the batch with N^d <= 2^27 "
+                        f"(points per integral up to {int(max(float(as_[k]) ** int(ds[k]) for k in range(len(idx))))})",
+            "mdi_lr_batched_ms": mdi_ms, "plain_kernel_ms_total": slr_ms, "ratio_plain_over_mdi": slr_ms / mdi_ms,
+            "max_rel_diff_plain_vs_mdi": worst}
+
+
 def extra_paper_context(torch, mdi, o):
     """The paper's own MDI-LR CPU times (Matlab on an Intel Xeon Gold 6226R at
     2.90 GHz, one process, Section 4) beside this GPU's time for the nearest
@@ -660,6 +692,7 @@ def main():
             line["paper_table_workload"] = extra_paper_tables(torch, mdi, o)
             line["lattice_search_workload"] = extra_lattice_search(torch, mdi, o)
             line["paper_context"] = extra_paper_context(torch, mdi, o)
+            line["batch_vs_plain_kernel"] = extra_batch_vs_plain(torch, mdi, o, inputs)
         rate, n_done, secs = cpu_oracle_sample(b, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "integrals/s", "cores": 1, "kind": "oracle",
                                 "sample": f"first {n_done} integrals of the batch, {secs:.1f} s single-threaded"}
