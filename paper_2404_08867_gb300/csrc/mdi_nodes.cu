@@ -296,6 +296,23 @@ __device__ __forceinline__ df32 lanes_sum_df(df32 v, int Q) {
     v = df_add(v, df32{__shfl_xor_sync(0xffffffffu, v.hi, off, Q), __shfl_xor_sync(0xffffffffu, v.lo, off, Q)});
   return v;
 }
+// The same over Dot2 accumulators left unnormalised: the high parts are added
+// with TwoSum, the low parts and the TwoSum errors with plain adds.
+__device__ __forceinline__ DfAcc lanes_sum_acc(DfAcc v, int Q) {
+  for (int off = 1; off < Q; off <<= 1) {
+    const float os = __shfl_xor_sync(0xffffffffu, v.s, off, Q), oc = __shfl_xor_sync(0xffffffffu, v.c, off, Q);
+    const df32 t = two_sum(v.s, os);
+    v.s = t.hi;
+    v.c = __fadd_rn(__fadd_rn(v.c, oc), t.lo);
+  }
+  return v;
+}
+// x + sg * y (sg = +1 or -1) of two Dot2 accumulators as a normalised double-float:
+// the error is bounded relative to |x| + |y| (as a sloppy double-word add).
+__device__ __forceinline__ df32 pair_combine(const DfAcc &x, const DfAcc &y, float sg) {
+  const df32 t = two_sum(x.s, sg * y.s);
+  return fast_two_sum(t.hi, __fadd_rn(__fmaf_rn(sg, y.c, x.c), t.lo));
+}
 
 // The last level of one integral, Q = (1/n_last) sum_s phi_d(s/n_last) G_{d-1}(s/n_last),
 // with G_{d-1} in state buffer sb (sh.Gdf as float pairs in DF64, sh.G otherwise)
@@ -534,11 +551,14 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, const 
 
 // ---------------------------------------------------------------------------
 // One integral of a real family in DF64 with paired cluster points.  The state
-// is kept as E_t = G_t + G_{P-1-t} and O_t = G_t - G_{P-1-t} (t < h, sh.Gdf as
-// (E.hi, E.lo, O.hi, O.lo)).  With S+ = sum_t Lp[t] E_t and S- = sum_t Lm[t] O_t,
-//     G(u) = (S+ + S-)/2,   G(1 - u) = (S+ - S-)/2,
+// is kept as E_t = (G_t + G_{P-1-t})/2 and O_t = (G_t - G_{P-1-t})/2 (t < h, sh.Gdf
+// as (E.hi, E.lo, O.hi, O.lo)).  With S+ = sum_t Lp[t] E_t and S- = sum_t Lm[t] O_t,
+//     G(u) = S+ + S-,   G(1 - u) = S+ - S-,
 // so one pass of h Dot2 pairs interpolates both points of a pair: P multiply-adds
-// for two cluster points instead of 2P.  Lanes are pair-major: the Q lanes of
+// for two cluster points instead of 2P.  The two accumulators are combined with
+// one TwoSum of their high parts and one add of their low parts (pair_combine),
+// whose error is bounded relative to |S+| + |S-| -- the bound the accumulated
+// sums carry already.  Lanes are pair-major: the Q lanes of
 // pair pp take the points q of node pp (and a-1-q of node P-1-pp) and accumulate
 // both nodes' sums.  The last level unpacks E, O into G and runs last_level.
 // ---------------------------------------------------------------------------
@@ -552,7 +572,7 @@ __device__ void sweep_paired(NodesShared &sh, const float4 *__restrict__ Lpm, co
   const bool act = tid < h * Q;
   const bool warp_act = (tid & ~(kWarp - 1)) < h * Q;
   const int npts_h = a * h;
-  if (tid < h) sh.Gdf[0][tid] = make_float4(2.f, 0.f, 0.f, 0.f);  // G_0 = 1: E = 2, O = 0
+  if (tid < h) sh.Gdf[0][tid] = make_float4(1.f, 0.f, 0.f, 0.f);  // G_0 = 1: E = 1, O = 0
   if (tid < P) {
     const double xa = sh.xi[tid] / (double)a;
     const float hx = (float)xa;
@@ -566,6 +586,7 @@ __device__ void sweep_paired(NodesShared &sh, const float4 *__restrict__ Lpm, co
   load_level_chunk(sh.lc, prm, d, 0);
   __syncthreads();
   const df32 ia{sh.iadf.x, sh.iadf.y};
+  const df32 ia2{0.5f * ia.hi, 0.5f * ia.lo};  // 1/(2a), exact halving
 
   for (int k = 1; k < d; ++k) {
     const int j = k - 1;
@@ -593,21 +614,19 @@ __device__ void sweep_paired(NodesShared &sh, const float4 *__restrict__ Lpm, co
             dacc_prod(sp, df32{l.x, l.y}, df32{eo.x, eo.y});
             dacc_prod(sm, df32{l.z, l.w}, df32{eo.z, eo.w});
           }
-          const df32 vp = dacc_value(sp), vm = dacc_value(sm);
-          const df32 ta = df_add(vp, vm), tb = df_add(vp, df_neg(vm));
-          ga = df32{0.5f * ta.hi, 0.5f * ta.lo};
-          gb = df32{0.5f * tb.hi, 0.5f * tb.lo};
+          ga = pair_combine(sp, sm, 1.0f);
+          gb = pair_combine(sp, sm, -1.0f);
         }
         dacc_prod(acc_a, phi_df_affine<FAM>(s1a, s0a, (float)q, L.ic, sh.exp2tab), ga);
         dacc_prod(acc_b, phi_df_affine<FAM>(s1b, s0b, (float)(a - 1 - q), L.ic, sh.exp2tab), gb);
       }
     }
     if (warp_act) {
-      const df32 sa = lanes_sum_df(dacc_value(acc_a), Q);
-      const df32 sbv = lanes_sum_df(dacc_value(acc_b), Q);
+      const DfAcc sa = lanes_sum_acc(acc_a, Q), sbv = lanes_sum_acc(acc_b, Q);
       if (act && qs == 0) {
-        const df32 Ga = df_mul(sa, ia), Gb = df_mul(sbv, ia);
-        const df32 E = df_add(Ga, Gb), O = df_add(Ga, df_neg(Gb));
+        // E = (G_a + G_b)/2, O = (G_a - G_b)/2 with G = (1/a) * sum: one scale by 1/(2a).
+        const df32 E = df_mul(pair_combine(sa, sbv, 1.0f), ia2);
+        const df32 O = df_mul(pair_combine(sa, sbv, -1.0f), ia2);
         sh.Gdf[wb][pp] = make_float4(E.hi, E.lo, O.hi, O.lo);
       }
     }
@@ -620,7 +639,7 @@ __device__ void sweep_paired(NodesShared &sh, const float4 *__restrict__ Lpm, co
     const float4 eo = sh.Gdf[eb][t];
     const df32 E{eo.x, eo.y}, O{eo.z, eo.w};
     const df32 v = tid < h ? df_add(E, O) : df_add(E, df_neg(O));
-    sh.Gdf[gbuf][tid] = make_float4(0.5f * v.hi, 0.5f * v.lo, 0.f, 0.f);
+    sh.Gdf[gbuf][tid] = make_float4(v.hi, v.lo, 0.f, 0.f);
   }
   __syncthreads();
   last_level<FAM, MDI_PREC_DF64>(sh, Ftab, P, d, a, n_last, prm, out_slot, gbuf);
