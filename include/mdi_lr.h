@@ -221,7 +221,9 @@ typedef struct {
 /* One-time set-up of a workspace for mdi_lr_integrate_batched: builds the
  * barycentric basis tables l_t((q + xi_p)/a) for a = 1..64 and the P of opts (they
  * depend on nothing else) -- for MDI_PREC_DF64 also the paired table
- * l_t +- l_{P-1-t} that the real families' sweep uses -- zeroes the work-queue
+ * l_t +- l_{P-1-t} that the real families' sweep uses -- and the constants every
+ * integral shares (the Chebyshev nodes and weights, xi_p/a and 1/a as float
+ * pairs, the 2^(j/256) table of the double-float exp), zeroes the work-queue
  * counters and stamps a tag naming opts->nodes and the table format of
  * opts->precision.  Enqueued on `stream`; a
  * prepared workspace serves any number of batched calls with the same nodes and

@@ -73,6 +73,37 @@ struct NodesShared {
   int pad;
 };
 
+// Constants common to every integral for P nodes, built once by the preparation
+// and copied by each CTA (FP64 evaluation of them per CTA would queue on the
+// FP64 pipe at every launch): the 2^(j/256) table of the double-float exp, the
+// Chebyshev nodes and barycentric weights, and for every a the float pairs of 1/a
+// and xi_p/a.
+struct NodesConsts {
+  float2 exp2tab[kExpTable];
+  double xi[kNodesPMax], bw[kNodesPMax];
+  float2 ia[kNodesAMax + 1];
+  float2 xa[kNodesAMax + 1][kNodesPMax];
+};
+
+__global__ void nodes_consts_kernel(int P, NodesConsts *__restrict__ kc) {
+  for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) kc->exp2tab[j] = exp2_table_entry(j);
+  for (int t = threadIdx.x; t < P; t += blockDim.x) {
+    kc->xi[t] = cheb_node(t, P);
+    kc->bw[t] = cheb_weight(t, P);
+  }
+  for (int i = threadIdx.x; i <= kNodesAMax; i += blockDim.x) {
+    const double v = i ? 1.0 / (double)i : 0.0;
+    const float h = (float)v;
+    kc->ia[i] = make_float2(h, (float)(v - (double)h));
+  }
+  for (int i = threadIdx.x; i < (kNodesAMax + 1) * P; i += blockDim.x) {
+    const int a = i / P, t = i % P;
+    const double v = a ? cheb_node(t, P) / (double)a : 0.0;
+    const float h = (float)v;
+    kc->xa[a][t] = make_float2(h, (float)(v - (double)h));
+  }
+}
+
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 static size_t nodes_smem_bytes(int block, int P, bool stage) {
   (void)block;
@@ -190,21 +221,32 @@ __global__ void nodes_paired_table_kernel(int P, float4 *__restrict__ table) {
   }
 }
 
-// Constants of axis j (0-based) for the level loop.
+// Constants of axis j (0-based) for the level loop.  With DF, 1/c^2 is formed in
+// double-float arithmetic (relative error about 2^-46) and its double copy is the
+// sum of that pair: no FP64 division per level.
+template <bool DF>
 __device__ __forceinline__ void make_level_const(const double *__restrict__ prm, int d, int j, LevelConst &L) {
-  const double c = prm[j], w = prm[d + j], ic2 = 1.0 / (c * c);
+  const double c = prm[j], w = prm[d + j];
+  const df32 cd = df_from_double(c), wd = df_from_double(w);
+  df32 id;
+  if constexpr (DF) {
+    id = df_rcp(df_sqr(cd));
+    L.ic2 = df_to_double(id);
+  } else {
+    L.ic2 = 1.0 / (c * c);
+    id = df_from_double(L.ic2);
+  }
   L.c = c;
   L.w = w;
-  L.ic2 = ic2;
-  const df32 cd = df_from_double(c), wd = df_from_double(w), id = df_from_double(ic2);
   L.cw = make_float4(cd.hi, cd.lo, wd.hi, wd.lo);
   L.ic = make_float2(id.hi, id.lo);
 }
 
 // Fills sh.lc with the constants of axes base .. base+kLvChunk-1 (all threads).
+template <bool DF = false>
 __device__ __forceinline__ void load_level_chunk(LevelConst *lc, const double *__restrict__ prm, int d, int base) {
   const int n = min(kLvChunk, d - base);
-  for (int j = threadIdx.x; j < n; j += blockDim.x) make_level_const(prm, d, base + j, lc[j]);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) make_level_const<DF>(prm, d, base + j, lc[j]);
 }
 
 // phi_j(u) in double-float arithmetic (EXP, GAUSS, PEAK).
@@ -328,7 +370,7 @@ __device__ void last_level(NodesShared &sh, const void *__restrict__ Ftab, int P
   constexpr bool DFSTATE = (PREC == MDI_PREC_DF64);
   const int tid = threadIdx.x, B = blockDim.x;
   if (d > 1 && (d - 1) % kLvChunk == 0) {
-    load_level_chunk(sh.lc, prm, d, d - 1);
+    load_level_chunk<DFSTATE>(sh.lc, prm, d, d - 1);
     __syncthreads();
   }
   const LevelConst &LL = sh.lc[(d - 1) % kLvChunk];
@@ -420,8 +462,9 @@ __device__ void last_level(NodesShared &sh, const void *__restrict__ Ftab, int P
 // level ends with one barrier; the state is double-buffered by level parity.
 // ---------------------------------------------------------------------------
 template <int FAM, int PREC>
-__device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, const void *__restrict__ Ftab, int P, int d,
-                          int a, int n_last, const double *__restrict__ prm, double *__restrict__ out_slot) {
+__device__ void sweep_one(NodesShared &sh, const NodesConsts *__restrict__ kc, const void *__restrict__ Ltab,
+                          const void *__restrict__ Ftab, int P, int d, int a, int n_last,
+                          const double *__restrict__ prm, double *__restrict__ out_slot) {
   using V = typename FamTraits<FAM>::V;
   constexpr bool F32 = (PREC == MDI_PREC_FP32_EVAL_FP64 || PREC == MDI_PREC_FP32_EVAL_DF32);
   constexpr bool DF = (PREC == MDI_PREC_FP32_EVAL_DF32 || PREC == MDI_PREC_DF64);
@@ -438,18 +481,10 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, const 
   if (tid < P) {
     sh.Gdf[0][tid] = make_float4(1.f, 0.f, 0.f, 0.f);
     sh.G[0][tid] = make_double2(1.0, 0.0);
-    if (DFSTATE) {
-      const double xa = sh.xi[tid] / (double)a;
-      const float h = (float)xa;
-      sh.xadf[tid] = make_float2(h, (float)(xa - (double)h));
-    }
+    if (DFSTATE) sh.xadf[tid] = kc->xa[a][tid];
   }
-  if (tid == 0 && DFSTATE) {
-    const double ia = 1.0 / (double)a;
-    const float h = (float)ia;
-    sh.iadf = make_float2(h, (float)(ia - (double)h));
-  }
-  load_level_chunk(sh.lc, prm, d, 0);
+  if (tid == 0 && DFSTATE) sh.iadf = kc->ia[a];
+  load_level_chunk<DFSTATE>(sh.lc, prm, d, 0);
   __syncthreads();
   const double inv_a = 1.0 / (double)a;  // FP64 modes only (folded away in DF64)
   const double xi_p = sh.xi[p];
@@ -457,7 +492,7 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, const 
   for (int k = 1; k < d; ++k) {
     const int j = k - 1;  // axis of this level
     if (j > 0 && j % kLvChunk == 0) {  // next chunk of level constants
-      load_level_chunk(sh.lc, prm, d, j);
+      load_level_chunk<DFSTATE>(sh.lc, prm, d, j);
       __syncthreads();
     }
     const LevelConst &L = sh.lc[j % kLvChunk];
@@ -563,8 +598,9 @@ __device__ void sweep_one(NodesShared &sh, const void *__restrict__ Ltab, const 
 // both nodes' sums.  The last level unpacks E, O into G and runs last_level.
 // ---------------------------------------------------------------------------
 template <int FAM>
-__device__ void sweep_paired(NodesShared &sh, const float4 *__restrict__ Lpm, const void *__restrict__ Ftab, int P,
-                             int d, int a, int n_last, const double *__restrict__ prm, double *__restrict__ out_slot) {
+__device__ void sweep_paired(NodesShared &sh, const NodesConsts *__restrict__ kc, const float4 *__restrict__ Lpm,
+                             const void *__restrict__ Ftab, int P, int d, int a, int n_last,
+                             const double *__restrict__ prm, double *__restrict__ out_slot) {
   const int h = P / 2;
   const int tid = threadIdx.x, B = blockDim.x;
   const int Q = node_lanes(B, h);
@@ -573,17 +609,9 @@ __device__ void sweep_paired(NodesShared &sh, const float4 *__restrict__ Lpm, co
   const bool warp_act = (tid & ~(kWarp - 1)) < h * Q;
   const int npts_h = a * h;
   if (tid < h) sh.Gdf[0][tid] = make_float4(1.f, 0.f, 0.f, 0.f);  // G_0 = 1: E = 1, O = 0
-  if (tid < P) {
-    const double xa = sh.xi[tid] / (double)a;
-    const float hx = (float)xa;
-    sh.xadf[tid] = make_float2(hx, (float)(xa - (double)hx));
-  }
-  if (tid == 0) {
-    const double ia = 1.0 / (double)a;
-    const float hx = (float)ia;
-    sh.iadf = make_float2(hx, (float)(ia - (double)hx));
-  }
-  load_level_chunk(sh.lc, prm, d, 0);
+  if (tid < P) sh.xadf[tid] = kc->xa[a][tid];
+  if (tid == 0) sh.iadf = kc->ia[a];
+  load_level_chunk<true>(sh.lc, prm, d, 0);
   __syncthreads();
   const df32 ia{sh.iadf.x, sh.iadf.y};
   const df32 ia2{0.5f * ia.hi, 0.5f * ia.lo};  // 1/(2a), exact halving
@@ -591,7 +619,7 @@ __device__ void sweep_paired(NodesShared &sh, const float4 *__restrict__ Lpm, co
   for (int k = 1; k < d; ++k) {
     const int j = k - 1;
     if (j > 0 && j % kLvChunk == 0) {
-      load_level_chunk(sh.lc, prm, d, j);
+      load_level_chunk<true>(sh.lc, prm, d, j);
       __syncthreads();
     }
     const LevelConst &L = sh.lc[j % kLvChunk];
@@ -651,7 +679,8 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
                                                                        mdi_batch_desc single,
                                                                        const double *__restrict__ pool,
                                                                        const void *__restrict__ tables,
-                                                                       const float4 *__restrict__ paired, int P,
+                                                                       const float4 *__restrict__ paired,
+                                                                       const NodesConsts *__restrict__ kc, int P,
                                                                        int stage, double *__restrict__ out,
                                                                        unsigned *__restrict__ counter,
                                                                        unsigned expect_tag) {
@@ -659,11 +688,11 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
   NodesShared &sh = *reinterpret_cast<NodesShared *>(dyn_smem);
   unsigned char *tab_smem = dyn_smem + align16(sizeof(NodesShared));
   for (int t = threadIdx.x; t < P; t += blockDim.x) {
-    sh.xi[t] = cheb_node(t, P);
-    sh.bw[t] = cheb_weight(t, P);
+    sh.xi[t] = kc->xi[t];
+    sh.bw[t] = kc->bw[t];
   }
   if (PREC == MDI_PREC_DF64)
-    for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) sh.exp2tab[j] = exp2_table_entry(j);
+    for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) sh.exp2tab[j] = kc->exp2tab[j];
   int staged_a = -1;
   // counter[0]: next work item; counter[1]: CTAs finished; counter[2]: preparation tag.
   const bool prepared = counter[2] == expect_tag;
@@ -705,24 +734,24 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
     const double *prm = pool + ds.param_offset;
     if (use_paired) {
       const float4 *Lpm = (const float4 *)C;
-      if (ds.family == MDI_FAM_EXP) sweep_paired<MDI_FAM_EXP>(sh, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+      if (ds.family == MDI_FAM_EXP) sweep_paired<MDI_FAM_EXP>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
       else if (ds.family == MDI_FAM_GAUSS)
-        sweep_paired<MDI_FAM_GAUSS>(sh, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-      else sweep_paired<MDI_FAM_PEAK>(sh, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+        sweep_paired<MDI_FAM_GAUSS>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+      else sweep_paired<MDI_FAM_PEAK>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
       continue;
     }
     switch (ds.family) {
       case MDI_FAM_EXP:
-        sweep_one<MDI_FAM_EXP, PREC>(sh, C, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+        sweep_one<MDI_FAM_EXP, PREC>(sh, kc, C, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
         break;
       case MDI_FAM_OSC:
-        sweep_one<MDI_FAM_OSC, PREC>(sh, C, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+        sweep_one<MDI_FAM_OSC, PREC>(sh, kc, C, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
         break;
       case MDI_FAM_GAUSS:
-        sweep_one<MDI_FAM_GAUSS, PREC>(sh, C, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+        sweep_one<MDI_FAM_GAUSS, PREC>(sh, kc, C, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
         break;
       default:
-        sweep_one<MDI_FAM_PEAK, PREC>(sh, C, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+        sweep_one<MDI_FAM_PEAK, PREC>(sh, kc, C, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
         break;
     }
   }
@@ -779,9 +808,14 @@ static unsigned nodes_tag(const NodesConfig &c) {
   return 0x4D440000u | ((unsigned)c.P << 4) | (df_tables(c) ? 1u : 0u) | (paired_tables(c) ? 2u : 0u);
 }
 
+// Workspace: queue counters | basis tables | paired tables (DF64) | NodesConsts.
+static size_t consts_offset(const NodesConfig &cfg) {
+  return counter_bytes() + align_up(table_bytes(cfg.P)) + (paired_tables(cfg) ? align_up(paired_bytes(cfg.P)) : 0);
+}
+
 size_t nodes_batched_workspace_bytes(int count, const NodesConfig &cfg) {
   (void)count;
-  return counter_bytes() + align_up(table_bytes(cfg.P)) + (paired_tables(cfg) ? align_up(paired_bytes(cfg.P)) : 0);
+  return consts_offset(cfg) + align_up(sizeof(NodesConsts));
 }
 size_t nodes_single_workspace_bytes(const NodesConfig &cfg) { return nodes_batched_workspace_bytes(1, cfg); }
 
@@ -804,6 +838,8 @@ mdi_status nodes_prepare(const NodesConfig &cfg, void *workspace, size_t ws_byte
     nodes_paired_table_kernel<<<table_grid, 256, 0, stream>>>(cfg.P, paired);
     if ((st = check_launch()) != MDI_OK) return st;
   }
+  nodes_consts_kernel<<<1, 256, 0, stream>>>(cfg.P, (NodesConsts *)((char *)workspace + consts_offset(cfg)));
+  if ((st = check_launch()) != MDI_OK) return st;
   nodes_arm_kernel<<<1, 1, 0, stream>>>(counter, nodes_tag(cfg));
   return check_launch();
 }
@@ -839,7 +875,8 @@ static mdi_status launch_nodes(const mdi_batch_desc *descs, const int32_t *order
   }
   const int grid = std::max(1, std::min(count, sm_count() * per_sm));
   const float4 *paired = paired_tables(cfg) ? (const float4 *)((char *)tables + align_up(table_bytes(cfg.P))) : nullptr;
-  nodes_batched_kernel<PREC><<<grid, cfg.block, smem, stream>>>(descs, order, count, single, pool, tables, paired,
+  const NodesConsts *kc = (const NodesConsts *)((char *)ws + consts_offset(cfg));
+  nodes_batched_kernel<PREC><<<grid, cfg.block, smem, stream>>>(descs, order, count, single, pool, tables, paired, kc,
                                                                  cfg.P, cfg.stage, out, counter, nodes_tag(cfg));
   return check_launch();
 }
