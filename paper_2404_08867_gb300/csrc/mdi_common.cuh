@@ -254,8 +254,10 @@ __device__ __forceinline__ df32 df_exp(df32 x, const float2 *__restrict__ tab) {
   const float e2 = __fmaf_rn(r.hi, h, -p2);
   const float cross = __fmul_rn(r.hi, r.lo);
   const float t3 = __fmul_rn(__fmul_rn(p2, r.hi), __fmaf_rn(r.hi, 1.0f / 12.0f, 1.0f / 3.0f));
-  const df32 s1 = two_sum(1.0f, r.hi);
-  const df32 s2 = two_sum(s1.hi, p2);
+  // |r.hi| <= ln2/512 < 1 and |p2| <= r^2/2 < |s1.hi|: both sums meet FastTwoSum's
+  // ordering condition, so their errors are exact with three operations.
+  const df32 s1 = fast_two_sum(1.0f, r.hi);
+  const df32 s2 = fast_two_sum(s1.hi, p2);
   float lo = __fadd_rn(s1.lo, s2.lo);
   lo = __fadd_rn(lo, r.lo);
   lo = __fadd_rn(lo, __fadd_rn(e2, cross));

@@ -597,11 +597,35 @@ __device__ void sweep_one(NodesShared &sh, const NodesConsts *__restrict__ kc, c
 // pair pp take the points q of node pp (and a-1-q of node P-1-pp) and accumulate
 // both nodes' sums.  The last level unpacks E, O into G and runs last_level.
 // ---------------------------------------------------------------------------
-template <int FAM>
+// S+ and S- of one cluster point: h Dot2 pairs over the paired table column Lt
+// (entries stride apart) and the state E, O.  H > 0 fixes h at compile time.
+template <int H>
+__device__ __forceinline__ void paired_dot(const float4 *__restrict__ Lt, int stride, const float4 *__restrict__ EO,
+                                           int h, DfAcc &sp, DfAcc &sm) {
+  if constexpr (H > 0) {
+#pragma unroll
+    for (int t = 0; t < H; ++t) {
+      const float4 l = Lt[t * stride];
+      const float4 eo = EO[t];
+      dacc_prod(sp, df32{l.x, l.y}, df32{eo.x, eo.y});
+      dacc_prod(sm, df32{l.z, l.w}, df32{eo.z, eo.w});
+    }
+  } else {
+#pragma unroll 4
+    for (int t = 0; t < h; ++t) {
+      const float4 l = Lt[(size_t)t * stride];
+      const float4 eo = EO[t];
+      dacc_prod(sp, df32{l.x, l.y}, df32{eo.x, eo.y});
+      dacc_prod(sm, df32{l.z, l.w}, df32{eo.z, eo.w});
+    }
+  }
+}
+
+template <int FAM, int H>
 __device__ void sweep_paired(NodesShared &sh, const NodesConsts *__restrict__ kc, const float4 *__restrict__ Lpm,
                              const void *__restrict__ Ftab, int P, int d, int a, int n_last,
                              const double *__restrict__ prm, double *__restrict__ out_slot) {
-  const int h = P / 2;
+  const int h = H > 0 ? H : P / 2;
   const int tid = threadIdx.x, B = blockDim.x;
   const int Q = node_lanes(B, h);
   const int pp = min(tid / Q, h - 1), pb = P - 1 - pp, qs = tid % Q;
@@ -633,15 +657,8 @@ __device__ void sweep_paired(NodesShared &sh, const NodesConsts *__restrict__ kc
       for (int q = qs; q < a; q += Q) {
         df32 ga{1.f, 0.f}, gb{1.f, 0.f};
         if (k > 1) {
-          const float4 *Lt = Lpm + pp * a + q;
           DfAcc sp, sm;
-#pragma unroll 4
-          for (int t = 0; t < h; ++t) {
-            const float4 l = Lt[(size_t)t * npts_h];
-            const float4 eo = sh.Gdf[rb][t];
-            dacc_prod(sp, df32{l.x, l.y}, df32{eo.x, eo.y});
-            dacc_prod(sm, df32{l.z, l.w}, df32{eo.z, eo.w});
-          }
+          paired_dot<H>(Lpm + pp * a + q, npts_h, sh.Gdf[rb], h, sp, sm);
           ga = pair_combine(sp, sm, 1.0f);
           gb = pair_combine(sp, sm, -1.0f);
         }
@@ -734,10 +751,18 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
     const double *prm = pool + ds.param_offset;
     if (use_paired) {
       const float4 *Lpm = (const float4 *)C;
-      if (ds.family == MDI_FAM_EXP) sweep_paired<MDI_FAM_EXP>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-      else if (ds.family == MDI_FAM_GAUSS)
-        sweep_paired<MDI_FAM_GAUSS>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-      else sweep_paired<MDI_FAM_PEAK>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+      // P = 16 (the default node count) runs with the pair loop fully unrolled.
+      if (P == 16) {
+        if (ds.family == MDI_FAM_EXP) sweep_paired<MDI_FAM_EXP, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+        else if (ds.family == MDI_FAM_GAUSS)
+          sweep_paired<MDI_FAM_GAUSS, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+        else sweep_paired<MDI_FAM_PEAK, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+      } else {
+        if (ds.family == MDI_FAM_EXP) sweep_paired<MDI_FAM_EXP, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+        else if (ds.family == MDI_FAM_GAUSS)
+          sweep_paired<MDI_FAM_GAUSS, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+        else sweep_paired<MDI_FAM_PEAK, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+      }
       continue;
     }
     switch (ds.family) {
