@@ -789,3 +789,57 @@ int or_cbc(int d, uint64_t n, const double *gamma, double beta, uint64_t *z, dou
   }
   return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Improved lattice rule, Definition 3.3 (Section 2.2.2), Korobov z = (1,a,..)  */
+/* ------------------------------------------------------------------------- */
+
+/* The n points {j z / n} with z = (1, a, ..., a^(d-1)) lie on the lines of the
+ * transformed grid of Theorem 3.1: the first d-1 transformed coordinates of point j
+ * are the base-a digits of L(j) = floor(j a^(d-1) / n) (eq. 3.7), and eq. (3.5)
+ * gives n_d = ceil(n / a^(d-1)) positions along the last axis.  A line holding
+ * fewer than n_d points is completed by the points that continue its arithmetic
+ * progression: the last point of the line plus k z / n, NOT reduced mod 1 (the
+ * unwrapped reading of the ghost points).  The rule is the equal-weight mean over
+ * the n lattice points and the n* added ones, 1/(n + n*) (Section 3).  Brute force:
+ * every point is generated, grouped by line and evaluated.  Returns NAN when
+ * a^(d-1) n does not fit in 63 bits or a^(d-1) exceeds 2^26 (the line table). */
+double or_improved(int fam, int d, uint64_t n, uint64_t a, const double *c, const double *w, uint64_t *nstar) {
+  uint64_t M = 1;
+  for (int i = 1; i < d; ++i) {
+    if (M > (1ull << 26) / a) return NAN;
+    M *= a;
+  }
+  if (n > (1ull << 62) / M) return NAN;
+  const uint64_t nd = (n + M - 1) / M;
+  uint64_t *count = (uint64_t *)calloc(M, sizeof(uint64_t));
+  uint64_t *last = (uint64_t *)calloc(M, sizeof(uint64_t));
+  uint64_t *z = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)d);
+  double *x = (double *)malloc(sizeof(double) * (size_t)d);
+  z[0] = 1 % n;
+  for (int i = 1; i < d; ++i) z[i] = mulmod(z[i - 1], a % n, n);
+  double sum = 0.0;
+  for (uint64_t j = 0; j < n; ++j) {
+    const uint64_t L = j * M / n;
+    count[L] += 1;
+    last[L] = j;
+    for (int i = 0; i < d; ++i) x[i] = (double)mulmod(j, z[i], n) / (double)n;
+    sum += f_eval(fam, d, x, c, w);
+  }
+  uint64_t added = 0;
+  for (uint64_t L = 0; L < M; ++L) {
+    if (count[L] == 0) continue;  /* lines without a lattice point have no progression */
+    for (uint64_t k = 1; count[L] + k <= nd; ++k) {
+      for (int i = 0; i < d; ++i)
+        x[i] = (double)mulmod(last[L], z[i], n) / (double)n + (double)k * (double)z[i] / (double)n;
+      sum += f_eval(fam, d, x, c, w);
+      added += 1;
+    }
+  }
+  free(count);
+  free(last);
+  free(z);
+  free(x);
+  if (nstar) *nstar = added;
+  return sum / (double)(n + added);
+}

@@ -60,6 +60,7 @@ def _load():
                 "or_korobov_z": (I, [I, U, U, P]),
                 "or_lattice_indices": (I, [I, U, P, U, U, P]),
                 "or_slr": (D, [I, I, U, P, P, P]),
+                "or_improved": (D, [I, I, U, U, P, P, P]),
                 "or_slr_grad": (I, [I, I, U, P, P, P, P]),
                 "or_grid_sizes": (I, [I, U, P, P]),
                 "or_affine_y": (I, [I, U, P, P]),
@@ -125,6 +126,15 @@ def lattice_indices(d, n, z, j0, count) -> np.ndarray:
 def slr(family, d, n, z, c, w=None) -> float:
     z, c, w = _u64(z), _f64(c, d), _f64(w, d)
     return _load().or_slr(_fam(family), d, n, _p(z), _p(c), _p(w))
+
+
+def improved_rule(family, d, n, a, c, w=None):
+    """Improved lattice rule of Definition 3.3 on z = (1, a, ..) by brute force:
+    (value, n*), ghosts by the unwrapped line extension."""
+    c, w = _f64(c, d), _f64(w, d)
+    ns = ctypes.c_uint64()
+    v = _load().or_improved(_fam(family), d, n, a, _p(c), _p(w), ctypes.byref(ns))
+    return v, ns.value
 
 
 def slr_grad(family, d, n, z, c, w=None) -> np.ndarray:
