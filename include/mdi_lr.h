@@ -162,6 +162,30 @@ mdi_status lattice_rule_integrate_shifted(int32_t family, int32_t d, int64_t n, 
 mdi_status lattice_rule_shifted_workspace_size(int32_t d, int64_t n, int32_t R, size_t *bytes);
 
 /* ---------------------------------------------------------------------------
+ * Improved lattice rule (Definition 3.3, Section 2.2.2) for the Korobov vector
+ * z = (1, a, ..., a^(d-1)) mod n and general n.  The transformed grid of
+ * Theorem 3.1 has M = a^(d-1) lines of n_d = ceil(n / M) positions (eq. 3.5); the
+ * n lattice points fill it except for n* = M n_d - n positions, one on each short
+ * line.  Each is filled by the point that continues its line by one lattice step
+ * z/n, not reduced mod 1 (so its last coordinate is >= 1):
+ *     out = (sum_{j<n} f({j z / n}) + sum_{ghosts} f(x_g)) / (n + n*).
+ * With a^(d-1) | n there are no ghosts and this is lattice_rule_integrate.
+ *   d        1..64;  a >= 1 with a^(d-1) * ceil(n / a^(d-1)) < 2^62
+ *   n        1 <= n < 2^62; gcd(a, n) = 1 unless a^(d-1) divides n
+ *   params   DEVICE, the family's parameters as lattice_rule_integrate
+ *   out      DEVICE, 1 double
+ *   n_ghost  HOST, optional (may be NULL): receives n*
+ * FP64.  Three launches on `stream` (lattice points, ghosts, ordered sum).
+ * MDI_EINVAL for bad sizes or a common factor of a and n with ghosts present;
+ * MDI_EWORKSPACE for a missing, misaligned or short workspace
+ * (lattice_rule_improved_workspace_size).
+ * ------------------------------------------------------------------------- */
+mdi_status lattice_rule_integrate_improved(int32_t family, int32_t d, int64_t n, int64_t a, const double *params,
+                                           double *out, int64_t *n_ghost, void *workspace, size_t ws_bytes,
+                                           mdi_stream_t stream);
+mdi_status lattice_rule_improved_workspace_size(int32_t d, int64_t n, int64_t a, size_t *bytes);
+
+/* ---------------------------------------------------------------------------
  * MDI-LR, Algorithm 2 (Section 4) with m = 1 on the Korobov lattice.
  *   d        dimension, >= 1 (EXACT: n <= 2^40; CLOSED: d <= 2^20; NODES: d <= 2^20)
  *   a        Korobov parameter = points per transformed axis 1..d-1, a >= 1

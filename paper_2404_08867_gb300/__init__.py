@@ -27,6 +27,7 @@ __all__ = [
     "mdi_lr_grad", "mdi_lr_grad_workspace_size", "MDILR", "mdi_lr", "make_batch_descs", "MdiError", "FAMILY", "STATE", "PRECISION", "BATCH_DESC_DTYPE", "library_path",
     "mdi_midpoint_integrate", "mdi_midpoint_workspace_size", "mdi_midpoint_ridge", "lattice_korobov_search", "lattice_cbc",
     "lattice_cbc_workspace_size", "lattice_korobov_search_workspace_size", "lattice_rule_integrate_shifted", "lattice_rule_shifted_workspace_size",
+    "lattice_rule_integrate_improved", "lattice_rule_improved_workspace_size",
     "shifted_estimate",
 ]
 
@@ -132,6 +133,35 @@ def lattice_rule_integrate_shifted(family, params: torch.Tensor, n: int, z: Sequ
                                                     ws.numel(), _stream(stream))
     _ffi.check(st, "lattice_rule_integrate_shifted")
     return out
+
+
+def lattice_rule_improved_workspace_size(d: int, n: int, a: int) -> int:
+    b = ctypes.c_size_t()
+    _ffi.check(_ffi.load().lattice_rule_improved_workspace_size(d, int(n), int(a), ctypes.byref(b)),
+               "lattice_rule_improved_workspace_size")
+    return b.value
+
+
+def lattice_rule_integrate_improved(family, params: torch.Tensor, d: int, n: int, a: int,
+                                    out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
+                                    stream=None):
+    """Improved lattice rule (Definition 3.3) on the Korobov lattice z = (1, a, ..)
+    for general n: the n lattice points plus the n* points completing the
+    transformed tensor grid, weight 1/(n + n*).  Returns (1-element float64 CUDA
+    tensor, n*)."""
+    _dev_f64(params, "params")
+    if params.numel() < 2 * d:
+        raise ValueError("params must hold 2*d doubles")
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=params.device)
+    ws = _workspace(lattice_rule_improved_workspace_size(d, n, a), params.device, workspace)
+    ng = ctypes.c_int64()
+    st = _ffi.load().lattice_rule_integrate_improved(_fam(family), d, int(n), int(a),
+                                                     ctypes.c_void_p(params.data_ptr()),
+                                                     ctypes.c_void_p(out.data_ptr()), ctypes.byref(ng),
+                                                     ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
+    _ffi.check(st, "lattice_rule_integrate_improved")
+    return out, ng.value
 
 
 def shifted_estimate(values: torch.Tensor):

@@ -126,6 +126,20 @@ mdi_status lattice_rule_integrate_shifted(int32_t family, int32_t d, int64_t n, 
   return slr_shifted_launch(family, d, n, z, params, shifts, R, out, workspace, ws_bytes, (cudaStream_t)stream);
 }
 
+mdi_status lattice_rule_improved_workspace_size(int32_t d, int64_t n, int64_t a, size_t *bytes) {
+  if (!bytes) return MDI_EINVAL;
+  *bytes = slr_improved_workspace_bytes(d, n, a);
+  return *bytes ? MDI_OK : MDI_EINVAL;
+}
+
+mdi_status lattice_rule_integrate_improved(int32_t family, int32_t d, int64_t n, int64_t a, const double *params,
+                                           double *out, int64_t *n_ghost, void *workspace, size_t ws_bytes,
+                                           mdi_stream_t stream) {
+  NvtxRange nvtx_scope("lattice_rule_integrate_improved");
+  if (!family_ok(family)) return MDI_EINVAL;
+  return slr_improved_launch(family, d, n, a, params, out, n_ghost, workspace, ws_bytes, (cudaStream_t)stream);
+}
+
 mdi_status lattice_rule_integrate_noalloc(int32_t family, int32_t d, int64_t n, const int64_t *z, const double *params,
                                           int32_t precision, double *out, mdi_stream_t stream) {
   NvtxRange nvtx_scope("lattice_rule_integrate_noalloc");

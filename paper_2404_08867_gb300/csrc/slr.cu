@@ -359,4 +359,214 @@ mdi_status slr_launch_noalloc(int family, int d, int64_t n, const int64_t *z, co
   return check_launch();
 }
 
+
+// ---------------------------------------------------------------------------
+// Improved lattice rule (Definition 3.3) for the Korobov vector z = (1, a, ..,
+// a^(d-1)) mod n.  With M = a^(d-1), the transformed grid of Theorem 3.1 has M
+// lines (the digit blocks of the first d-1 axes) of n_d = ceil(n / M) positions
+// (eq. 3.5), N = M n_d points, of which n are lattice points.  Indexing every
+// grid point by r = n x_d (an integer), the lattice points are r < n and, when
+// gcd(a, n) = 1, every r < N occurs exactly once: r = M s + (-n Q mod M) ties the
+// last coordinate to the line Q, so Q(r) = -r n^{-1} mod M, and the other
+// coordinates follow from the base-a digits q_0, q_1, ... of Q:
+//     x_{d-1} = (q_0 + x_d)/a,  x_{d-2} = (q_1 + x_{d-1})/a,  ...
+// The ghosts are r = n .. N-1 with x_d = r/n >= 1: each continues the progression
+// of its line by one lattice step z/n without reduction mod 1 (the unwrapped
+// reading).  The rule is (sum over the n lattice points + sum over the N - n
+// ghosts) / N.  Each line's points all have distinct last coordinates, so no MDI
+// work is shared: the lattice points run through slr_kernel and the ghosts
+// through ghost_kernel, each thread forming Q once and then stepping it by a
+// digit-wise subtraction of n^{-1} with borrow.
+// ---------------------------------------------------------------------------
+constexpr int kGhostMaxD = 64;  // a^(d-1) < 2^62 with a >= 2 bounds d - 1 by 61
+
+struct GhostArgs {
+  uint64_t n, count, M, ninv;  // count = N - n ghosts
+  double inv_n, inv_a;
+  int d, a;
+  int ninv_digit[kGhostMaxD];  // base-a digits of n^{-1} mod M, least significant first
+};
+
+template <int FAM, int MAXD>
+__global__ void __launch_bounds__(kSlrThreads) ghost_kernel(const __grid_constant__ GhostArgs g,
+                                                            const double *__restrict__ params,
+                                                            double *__restrict__ partials) {
+  __shared__ double s_c[MAXD], s_w[MAXD], s_ic2[MAXD];
+  __shared__ double s_red[kSlrThreads / kWarp];
+  const int d = g.d;
+  for (int i = threadIdx.x; i < d; i += blockDim.x) {
+    s_c[i] = params[i];
+    s_w[i] = params[d + i];
+    s_ic2[i] = 1.0 / (params[i] * params[i]);
+  }
+  __syncthreads();
+  const double u2pi = (FAM == MDI_FAM_OSC) ? kTwoPi * params[d] : 0.0;
+  const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t t0, t1;
+  thread_run(g.count, tid, nthreads, t0, t1);
+  int q[MAXD > 1 ? MAXD - 1 : 1];  // digits of Q
+  if (t0 < t1) {
+    const uint64_t r0 = g.n + t0;
+    const uint64_t m = mulmod_u63(r0 % g.M, g.ninv, g.M);
+    uint64_t Q = m ? g.M - m : 0;
+    for (int k = 0; k + 1 < d; ++k) {
+      q[k] = (int)(Q % (uint64_t)g.a);
+      Q /= (uint64_t)g.a;
+    }
+  }
+  double acc = 0.0;
+  for (uint64_t t = t0; t < t1; ++t) {
+    double x = (double)(g.n + t) * g.inv_n;  // x_d
+    double f;
+    if constexpr (FAM == MDI_FAM_PEAK) {
+      double p = 1.0, den = 1.0;
+      for (int i = d - 1, k = 0; i >= 0; --i, ++k) {
+        if (i < d - 1) x = ((double)q[k - 1] + x) * g.inv_a;
+        const double u = x - s_w[i];
+        den *= fma(u, u, s_ic2[i]);
+        if ((k & 7) == 7) {
+          p /= den;
+          den = 1.0;
+        }
+      }
+      f = p / den;
+    } else {
+      double sum = 0.0;
+      for (int i = d - 1, k = 0; i >= 0; --i, ++k) {
+        if (i < d - 1) x = ((double)q[k - 1] + x) * g.inv_a;
+        if constexpr (FAM == MDI_FAM_GAUSS) {
+          const double u = s_c[i] * (x - s_w[i]);
+          sum = fma(u, u, sum);
+        } else {
+          sum = fma(s_c[i], x, sum);
+        }
+      }
+      if constexpr (FAM == MDI_FAM_EXP) f = exp(sum);
+      else if constexpr (FAM == MDI_FAM_GAUSS) f = exp(-sum);
+      else f = cos(u2pi + sum);
+    }
+    acc += f;
+    // Q(r + 1) = Q(r) - n^{-1} mod M, digit by digit (the borrow out of the top
+    // digit is the reduction mod M).
+    int borrow = 0;
+    for (int k = 0; k + 1 < d; ++k) {
+      int v = q[k] - g.ninv_digit[k] - borrow;
+      borrow = v < 0;
+      q[k] = borrow ? v + g.a : v;
+    }
+  }
+  const double b = block_sum(acc, s_red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = b;
+}
+
+// M = a^(d-1), N = M ceil(n / M) and n^{-1} mod M, or false when out of range.
+struct ImprovedPlan {
+  uint64_t M, N, ninv;
+  int grid_lattice, grid_ghost;
+};
+static bool improved_plan(int d, int64_t n, int64_t a, ImprovedPlan &pl) {
+  if (d < 1 || d > kGhostMaxD || n < 1 || a < 1 || n >= (int64_t)(1ull << 62)) return false;
+  uint64_t M = 1;
+  for (int i = 1; i < d; ++i) {
+    if (M > ((1ull << 62) - 1) / (uint64_t)a) return false;
+    M *= (uint64_t)a;
+  }
+  const uint64_t nd = ((uint64_t)n + M - 1) / M;
+  if (nd > ((1ull << 62) - 1) / M) return false;
+  pl.M = M;
+  pl.N = nd * M;
+  pl.ninv = 0;
+  if (pl.N > (uint64_t)n) {
+    // n^{-1} mod M by the extended Euclidean algorithm; needs gcd(n, M) = 1.
+    __int128 r0 = (__int128)M, r1 = (__int128)((uint64_t)n % M), s0 = 0, s1 = 1;
+    while (r1 != 0) {
+      const __int128 qq = r0 / r1, r2 = r0 - qq * r1, s2 = s0 - qq * s1;
+      r0 = r1;
+      r1 = r2;
+      s0 = s1;
+      s1 = s2;
+    }
+    if (r0 != 1) return false;
+    __int128 inv = s0 % (__int128)M;
+    if (inv < 0) inv += (__int128)M;
+    pl.ninv = (uint64_t)inv;
+  }
+  pl.grid_lattice = slr_grid((uint64_t)n);
+  pl.grid_ghost = pl.N > (uint64_t)n ? slr_grid(pl.N - (uint64_t)n) : 0;
+  return true;
+}
+
+size_t slr_improved_workspace_bytes(int d, int64_t n, int64_t a) {
+  ImprovedPlan pl{};
+  if (!improved_plan(d, n, a, pl)) return 0;
+  return align_up(sizeof(double) * (size_t)(pl.grid_lattice + pl.grid_ghost));
+}
+
+template <int FAM, int MAXD>
+static void launch_ghost(int grid, const GhostArgs &g, const double *params, double *partials, cudaStream_t s) {
+  ghost_kernel<FAM, MAXD><<<grid, kSlrThreads, 0, s>>>(g, params, partials);
+}
+template <int FAM>
+static void launch_ghost_d(int grid, const GhostArgs &g, const double *params, double *partials, cudaStream_t s) {
+  if (g.d <= 8) launch_ghost<FAM, 8>(grid, g, params, partials, s);
+  else if (g.d <= 32) launch_ghost<FAM, 32>(grid, g, params, partials, s);
+  else launch_ghost<FAM, kGhostMaxD>(grid, g, params, partials, s);
+}
+
+mdi_status slr_improved_launch(int family, int d, int64_t n, int64_t a, const double *params, double *out,
+                               int64_t *n_ghost, void *workspace, size_t ws_bytes, cudaStream_t stream) {
+  if (!params || !out) return MDI_EINVAL;
+  if (family < MDI_FAM_EXP || family > MDI_FAM_PEAK) return MDI_EINVAL;
+  ImprovedPlan pl{};
+  if (!improved_plan(d, n, a, pl)) return MDI_EINVAL;
+  if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < slr_improved_workspace_bytes(d, n, a))
+    return MDI_EWORKSPACE;
+  SlrArgs args{};
+  args.n = (uint64_t)n;
+  args.inv_n = 1.0 / (double)n;
+  args.d = d;
+  uint64_t zi = 1 % (uint64_t)n;
+  for (int i = 0; i < d; ++i) {
+    args.z[i] = zi;
+    zi = (uint64_t)(((unsigned __int128)zi * (uint64_t)a) % (uint64_t)n);
+  }
+  double *partials = (double *)workspace;
+  switch (family) {
+    case MDI_FAM_EXP: launch_slr_d<MDI_FAM_EXP, false>(pl.grid_lattice, args, params, partials, stream); break;
+    case MDI_FAM_OSC: launch_slr_d<MDI_FAM_OSC, false>(pl.grid_lattice, args, params, partials, stream); break;
+    case MDI_FAM_GAUSS: launch_slr_d<MDI_FAM_GAUSS, false>(pl.grid_lattice, args, params, partials, stream); break;
+    default: launch_slr_d<MDI_FAM_PEAK, false>(pl.grid_lattice, args, params, partials, stream); break;
+  }
+  mdi_status st = check_launch();
+  if (st != MDI_OK) return st;
+  if (pl.grid_ghost > 0) {
+    GhostArgs g{};
+    g.n = (uint64_t)n;
+    g.count = pl.N - (uint64_t)n;
+    g.M = pl.M;
+    g.ninv = pl.ninv;
+    g.inv_n = 1.0 / (double)n;
+    g.inv_a = 1.0 / (double)a;
+    g.d = d;
+    g.a = (int)a;
+    uint64_t v = pl.ninv;
+    for (int k = 0; k + 1 < d; ++k) {
+      g.ninv_digit[k] = (int)(v % (uint64_t)a);
+      v /= (uint64_t)a;
+    }
+    double *gp = partials + pl.grid_lattice;
+    switch (family) {
+      case MDI_FAM_EXP: launch_ghost_d<MDI_FAM_EXP>(pl.grid_ghost, g, params, gp, stream); break;
+      case MDI_FAM_OSC: launch_ghost_d<MDI_FAM_OSC>(pl.grid_ghost, g, params, gp, stream); break;
+      case MDI_FAM_GAUSS: launch_ghost_d<MDI_FAM_GAUSS>(pl.grid_ghost, g, params, gp, stream); break;
+      default: launch_ghost_d<MDI_FAM_PEAK>(pl.grid_ghost, g, params, gp, stream); break;
+    }
+    if ((st = check_launch()) != MDI_OK) return st;
+  }
+  sum_partials_kernel<<<1, kSlrThreads, 0, stream>>>(partials, pl.grid_lattice + pl.grid_ghost, 1.0 / (double)pl.N,
+                                                      out);
+  if (n_ghost) *n_ghost = (int64_t)(pl.N - (uint64_t)n);
+  return check_launch();
+}
 }  // namespace mdi
