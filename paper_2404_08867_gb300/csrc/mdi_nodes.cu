@@ -176,13 +176,15 @@ __global__ void nodes_table_kernel(int P, void *__restrict__ table) {
 // point 1 - u = (a-1-q + xi_{P-1-p})/a of node P-1-p interpolate with the same basis
 // values in reverse order.  For p < h = P/2 the table holds
 //     Lpm[t][p*a + q] = (l_t(u) + l_{P-1-t}(u), l_t(u) - l_{P-1-t}(u)),  t < h,
-// as two float pairs (one 16-byte entry); h*a*h entries per a, a = 1..64.
+// as two float pairs (DF64) or two doubles (FP64), one 16-byte entry; h*a*h
+// entries per a, a = 1..64.
 __host__ __device__ __forceinline__ size_t paired_offset(int a, int P) {
   const size_t h = (size_t)P / 2;
   return h * h * (size_t)a * (size_t)(a - 1) / 2;  // in 16-byte entries
 }
 static size_t paired_bytes(int P) { return 16 * paired_offset(kNodesAMax + 1, P); }
 
+template <bool DF>
 __global__ void nodes_paired_table_kernel(int P, float4 *__restrict__ table) {
   __shared__ double s_xi[kNodesPMax], s_bw[kNodesPMax];
   for (int t = threadIdx.x; t < P; t += blockDim.x) {
@@ -215,8 +217,12 @@ __global__ void nodes_paired_table_kernel(int P, float4 *__restrict__ table) {
     for (int t = 0; t < h; ++t) {
       const double lt = basis(t), lr = basis(P - 1 - t);
       const double vp = lt + lr, vm = lt - lr;
-      const float ph = (float)vp, mh = (float)vm;
-      row[(size_t)t * a * h + i] = make_float4(ph, (float)(vp - (double)ph), mh, (float)(vm - (double)mh));
+      if constexpr (DF) {
+        const float ph = (float)vp, mh = (float)vm;
+        row[(size_t)t * a * h + i] = make_float4(ph, (float)(vp - (double)ph), mh, (float)(vm - (double)mh));
+      } else {
+        reinterpret_cast<double2 *>(row)[(size_t)t * a * h + i] = make_double2(vp, vm);
+      }
     }
   }
 }
@@ -690,6 +696,81 @@ __device__ void sweep_paired(NodesShared &sh, const NodesConsts *__restrict__ kc
   last_level<FAM, MDI_PREC_DF64>(sh, Ftab, P, d, a, n_last, prm, out_slot, gbuf);
 }
 
+// The same pairing in FP64 (real families): the state (E_t, O_t) in sh.G as
+// doubles, the paired table as (Lp, Lm) doubles, phi in FP64.  P/2 fused
+// multiply-adds per cluster point instead of P, on the FP64 pipe that bounds
+// this mode.
+template <int FAM, int H>
+__device__ void sweep_paired_fp64(NodesShared &sh, const double2 *__restrict__ Lpm, const void *__restrict__ Ftab,
+                                  int P, int d, int a, int n_last, const double *__restrict__ prm,
+                                  double *__restrict__ out_slot) {
+  const int h = H > 0 ? H : P / 2;
+  const int tid = threadIdx.x, B = blockDim.x;
+  const int Q = node_lanes(B, h);
+  const int pp = min(tid / Q, h - 1), pb = P - 1 - pp, qs = tid % Q;
+  const bool act = tid < h * Q;
+  const bool warp_act = (tid & ~(kWarp - 1)) < h * Q;
+  const int npts_h = a * h;
+  if (tid < h) sh.G[0][tid] = make_double2(1.0, 0.0);  // G_0 = 1: E = 1, O = 0
+  load_level_chunk(sh.lc, prm, d, 0);
+  __syncthreads();
+  const double inv_a = 1.0 / (double)a, half_inv_a = 0.5 * inv_a;
+  const double xa = sh.xi[pp], xb = sh.xi[pb];
+
+  for (int k = 1; k < d; ++k) {
+    const int j = k - 1;
+    if (j > 0 && j % kLvChunk == 0) {
+      load_level_chunk(sh.lc, prm, d, j);
+      __syncthreads();
+    }
+    const LevelConst &L = sh.lc[j % kLvChunk];
+    const AxisParams ap{L.c, L.w, L.ic2};
+    const int rb = (k - 1) & 1, wb = k & 1;
+    double acc_a = 0.0, acc_b = 0.0;
+    if (act) {
+      for (int q = qs; q < a; q += Q) {
+        double ga = 1.0, gb = 1.0;
+        if (k > 1) {
+          const double2 *Lt = Lpm + pp * a + q;
+          double sp = 0.0, sm = 0.0;
+          if constexpr (H > 0) {
+#pragma unroll
+            for (int t = 0; t < H; ++t) {
+              const double2 l = Lt[t * npts_h], eo = sh.G[rb][t];
+              sp = fma(l.x, eo.x, sp);
+              sm = fma(l.y, eo.y, sm);
+            }
+          } else {
+#pragma unroll 4
+            for (int t = 0; t < h; ++t) {
+              const double2 l = Lt[(size_t)t * npts_h], eo = sh.G[rb][t];
+              sp = fma(l.x, eo.x, sp);
+              sm = fma(l.y, eo.y, sm);
+            }
+          }
+          ga = sp + sm;
+          gb = sp - sm;
+        }
+        acc_a = fma(phi<FAM, false>(((double)q + xa) * inv_a, ap), ga, acc_a);
+        acc_b = fma(phi<FAM, false>(((double)(a - 1 - q) + xb) * inv_a, ap), gb, acc_b);
+      }
+    }
+    if (warp_act) {
+      const double2 s2 = lanes_sum(make_double2(acc_a, acc_b), Q);
+      if (act && qs == 0) sh.G[wb][pp] = make_double2((s2.x + s2.y) * half_inv_a, (s2.x - s2.y) * half_inv_a);
+    }
+    __syncthreads();
+  }
+  const int eb = (d - 1) & 1, gbuf = eb ^ 1;
+  if (tid < P) {
+    const int t = tid < h ? tid : P - 1 - tid;
+    const double2 eo = sh.G[eb][t];
+    sh.G[gbuf][tid] = make_double2(tid < h ? eo.x + eo.y : eo.x - eo.y, 0.0);
+  }
+  __syncthreads();
+  last_level<FAM, MDI_PREC_FP64>(sh, Ftab, P, d, a, n_last, prm, out_slot, gbuf);
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi_batch_desc *__restrict__ descs,
                                                                        const int32_t *__restrict__ order, int count,
@@ -730,7 +811,8 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
     }
     // Basis tables of a: the cluster part (the paired one for real families in
     // DF64), staged in shared memory when asked and it fits, and the last-axis part.
-    const bool use_paired = PREC == MDI_PREC_DF64 && paired != nullptr && ds.family != MDI_FAM_OSC;
+    const bool use_paired = (PREC == MDI_PREC_DF64 || PREC == MDI_PREC_FP64) && paired != nullptr &&
+                            ds.family != MDI_FAM_OSC;
     const size_t tbytes = (size_t)a * P * P * 8;  // plain cluster part; a multiple of 16 for even P
     const unsigned char *gtab = (const unsigned char *)tables + table_offset(a, P) * 8;
     const void *Ftab = gtab + tbytes;
@@ -750,18 +832,33 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
     }
     const double *prm = pool + ds.param_offset;
     if (use_paired) {
-      const float4 *Lpm = (const float4 *)C;
       // P = 16 (the default node count) runs with the pair loop fully unrolled.
-      if (P == 16) {
-        if (ds.family == MDI_FAM_EXP) sweep_paired<MDI_FAM_EXP, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-        else if (ds.family == MDI_FAM_GAUSS)
-          sweep_paired<MDI_FAM_GAUSS, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-        else sweep_paired<MDI_FAM_PEAK, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-      } else {
-        if (ds.family == MDI_FAM_EXP) sweep_paired<MDI_FAM_EXP, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-        else if (ds.family == MDI_FAM_GAUSS)
-          sweep_paired<MDI_FAM_GAUSS, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-        else sweep_paired<MDI_FAM_PEAK, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+      if constexpr (PREC == MDI_PREC_DF64) {
+        const float4 *Lpm = (const float4 *)C;
+        if (P == 16) {
+          if (ds.family == MDI_FAM_EXP) sweep_paired<MDI_FAM_EXP, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+          else if (ds.family == MDI_FAM_GAUSS)
+            sweep_paired<MDI_FAM_GAUSS, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+          else sweep_paired<MDI_FAM_PEAK, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+        } else {
+          if (ds.family == MDI_FAM_EXP) sweep_paired<MDI_FAM_EXP, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+          else if (ds.family == MDI_FAM_GAUSS)
+            sweep_paired<MDI_FAM_GAUSS, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+          else sweep_paired<MDI_FAM_PEAK, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+        }
+      } else if constexpr (PREC == MDI_PREC_FP64) {
+        const double2 *Lpm = (const double2 *)C;
+        if (P == 16) {
+          if (ds.family == MDI_FAM_EXP) sweep_paired_fp64<MDI_FAM_EXP, 8>(sh, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+          else if (ds.family == MDI_FAM_GAUSS)
+            sweep_paired_fp64<MDI_FAM_GAUSS, 8>(sh, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+          else sweep_paired_fp64<MDI_FAM_PEAK, 8>(sh, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+        } else {
+          if (ds.family == MDI_FAM_EXP) sweep_paired_fp64<MDI_FAM_EXP, 0>(sh, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+          else if (ds.family == MDI_FAM_GAUSS)
+            sweep_paired_fp64<MDI_FAM_GAUSS, 0>(sh, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+          else sweep_paired_fp64<MDI_FAM_PEAK, 0>(sh, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+        }
       }
       continue;
     }
@@ -827,7 +924,9 @@ static bool df_tables(const NodesConfig &c) {
 static size_t counter_bytes() { return align_up(4 * sizeof(unsigned)); }
 
 // Tag stamped by the preparation: node count and table format.
-static bool paired_tables(const NodesConfig &c) { return c.precision == MDI_PREC_DF64; }
+static bool paired_tables(const NodesConfig &c) {
+  return c.precision == MDI_PREC_DF64 || c.precision == MDI_PREC_FP64;
+}
 
 static unsigned nodes_tag(const NodesConfig &c) {
   return 0x4D440000u | ((unsigned)c.P << 4) | (df_tables(c) ? 1u : 0u) | (paired_tables(c) ? 2u : 0u);
@@ -860,7 +959,8 @@ mdi_status nodes_prepare(const NodesConfig &cfg, void *workspace, size_t ws_byte
   if (st != MDI_OK) return st;
   if (paired_tables(cfg)) {
     float4 *paired = (float4 *)((char *)tables + align_up(table_bytes(cfg.P)));
-    nodes_paired_table_kernel<<<table_grid, 256, 0, stream>>>(cfg.P, paired);
+    if (cfg.precision == MDI_PREC_DF64) nodes_paired_table_kernel<true><<<table_grid, 256, 0, stream>>>(cfg.P, paired);
+    else nodes_paired_table_kernel<false><<<table_grid, 256, 0, stream>>>(cfg.P, paired);
     if ((st = check_launch()) != MDI_OK) return st;
   }
   nodes_consts_kernel<<<1, 256, 0, stream>>>(cfg.P, (NodesConsts *)((char *)workspace + consts_offset(cfg)));
