@@ -90,14 +90,17 @@ def workload_config(count, precision):
             "state": "nodes", "l2": "flushed between timed steps (256 MiB write)", "seed": "rank"}
 
 
-def fp64_flops(b, P=P_NODES):
+def fp64_flops(b, P=P_NODES, paired=True):
     """FP64 operations the sweep formula needs (exp and division count one): per
-    cluster point of level k >= 2: interpolation 2P, u 2, phi 4, product and sum 2;
-    level 1 without interpolation; last level per point: 2P (tabulated basis) + 8."""
+    cluster point of level k >= 2: interpolation 2P (paired: P, the P/2 sums and
+    P/2 differences of table values shared by two mirrored points, plus one add),
+    u 2, phi 4, product and sum 2; level 1 without interpolation; last level per
+    point: 2P (tabulated basis) + 8."""
     d, a, nl = (x.astype(np.float64) for x in (b.d, b.a, b.n_last))
     interp = np.maximum(d - 2, 0) * a * P
     first = np.where(d >= 2, a * P, 0)
-    return float((interp * (2 * P + 8) + first * 8 + nl * (2 * P + 8)).sum())
+    per_point = (P + 1 if paired else 2 * P) + 8
+    return float((interp * per_point + first * 8 + nl * (2 * P + 8)).sum())
 
 
 def df_flops(b, P=P_NODES, paired=True):

@@ -10,6 +10,8 @@ computes: every launch goes through the C ABI.
   korobov         P_2 Korobov search, n = 65536, d = 4, every a in 1..n/2
   cbc             CBC, n = 65536, d = 4, gamma_j = 1/j^2, unanchored
   midpoint-d1000  paper-table mode, d = 1000, N = 20, n_last = 21 (Gaussian)
+  improved-d7     improved lattice rule, d = 7, z = (1, 16, .., 16^6), n = 1 + 16^7
+                  (16^6 - 1 ghosts), f = exp(sum x_j / j)
 """
 from __future__ import annotations
 
@@ -51,6 +53,13 @@ def build_case(name: str):
         w = inputs.gaussian(1000, 20, seed=0)
         p = torch.as_tensor(w.params).cuda()
         return lambda: mdi.mdi_midpoint_integrate("gauss", p, 1000, 20, 21)
+    if name == "improved-d7":
+        d, a = 7, 16
+        p = torch.as_tensor(np.r_[1.0 / np.arange(1, d + 1), np.zeros(d)]).cuda()
+        ws = torch.empty(mdi.lattice_rule_improved_workspace_size(d, 1 + a ** d, a), dtype=torch.uint8,
+                         device="cuda")
+        out = torch.empty(1, dtype=torch.float64, device="cuda")
+        return lambda: mdi.lattice_rule_integrate_improved("exp", p, d, 1 + a ** d, a, out=out, workspace=ws)
     raise SystemExit(f"unknown case {name!r}; see the module docstring")
 
 

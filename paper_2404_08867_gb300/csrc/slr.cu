@@ -405,41 +405,59 @@ __global__ void __launch_bounds__(kSlrThreads) ghost_kernel(const __grid_constan
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint64_t t0, t1;
   thread_run(g.count, tid, nthreads, t0, t1);
-  int q[MAXD > 1 ? MAXD - 1 : 1];  // digits of Q
+  // Digits of Q; loops run to the bucket's compile-time bound so that they stay
+  // in registers for d <= 32.
+  constexpr int kDig = MAXD > 1 ? MAXD - 1 : 1;
+  constexpr int kUnroll = MAXD <= 32 ? kDig : 1;
+  int q[kDig];
   if (t0 < t1) {
     const uint64_t r0 = g.n + t0;
     const uint64_t m = mulmod_u63(r0 % g.M, g.ninv, g.M);
     uint64_t Q = m ? g.M - m : 0;
-    for (int k = 0; k + 1 < d; ++k) {
-      q[k] = (int)(Q % (uint64_t)g.a);
-      Q /= (uint64_t)g.a;
+#pragma unroll(kUnroll)
+    for (int k = 0; k < kDig; ++k) {
+      if (k + 1 < d) {
+        q[k] = (int)(Q % (uint64_t)g.a);
+        Q /= (uint64_t)g.a;
+      }
     }
   }
   double acc = 0.0;
   for (uint64_t t = t0; t < t1; ++t) {
-    double x = (double)(g.n + t) * g.inv_n;  // x_d
+    double x = (double)(g.n + t) * g.inv_n;  // x_d, then x_{d-1}, x_{d-2}, ...
     double f;
     if constexpr (FAM == MDI_FAM_PEAK) {
-      double p = 1.0, den = 1.0;
-      for (int i = d - 1, k = 0; i >= 0; --i, ++k) {
-        if (i < d - 1) x = ((double)q[k - 1] + x) * g.inv_a;
-        const double u = x - s_w[i];
-        den *= fma(u, u, s_ic2[i]);
-        if ((k & 7) == 7) {
-          p /= den;
-          den = 1.0;
+      const double u0 = x - s_w[d - 1];
+      double p = 1.0, den = fma(u0, u0, s_ic2[d - 1]);
+#pragma unroll(kUnroll)
+      for (int k = 1; k <= kDig; ++k) {
+        if (k < d) {
+          x = ((double)q[k - 1] + x) * g.inv_a;
+          const int i = d - 1 - k;
+          const double u = x - s_w[i];
+          den *= fma(u, u, s_ic2[i]);
+          if ((k & 7) == 7) {
+            p /= den;
+            den = 1.0;
+          }
         }
       }
       f = p / den;
     } else {
-      double sum = 0.0;
-      for (int i = d - 1, k = 0; i >= 0; --i, ++k) {
-        if (i < d - 1) x = ((double)q[k - 1] + x) * g.inv_a;
+      auto term = [&](int i, double xi, double sum) {
         if constexpr (FAM == MDI_FAM_GAUSS) {
-          const double u = s_c[i] * (x - s_w[i]);
-          sum = fma(u, u, sum);
+          const double u = s_c[i] * (xi - s_w[i]);
+          return fma(u, u, sum);
         } else {
-          sum = fma(s_c[i], x, sum);
+          return fma(s_c[i], xi, sum);
+        }
+      };
+      double sum = term(d - 1, x, 0.0);
+#pragma unroll(kUnroll)
+      for (int k = 1; k <= kDig; ++k) {
+        if (k < d) {
+          x = ((double)q[k - 1] + x) * g.inv_a;
+          sum = term(d - 1 - k, x, sum);
         }
       }
       if constexpr (FAM == MDI_FAM_EXP) f = exp(sum);
@@ -450,10 +468,13 @@ __global__ void __launch_bounds__(kSlrThreads) ghost_kernel(const __grid_constan
     // Q(r + 1) = Q(r) - n^{-1} mod M, digit by digit (the borrow out of the top
     // digit is the reduction mod M).
     int borrow = 0;
-    for (int k = 0; k + 1 < d; ++k) {
-      int v = q[k] - g.ninv_digit[k] - borrow;
-      borrow = v < 0;
-      q[k] = borrow ? v + g.a : v;
+#pragma unroll(kUnroll)
+    for (int k = 0; k < kDig; ++k) {
+      if (k + 1 < d) {
+        const int v = q[k] - g.ninv_digit[k] - borrow;
+        borrow = v < 0;
+        q[k] = borrow ? v + g.a : v;
+      }
     }
   }
   const double b = block_sum(acc, s_red);
