@@ -324,6 +324,52 @@ def extra_small_workload(torch, mdi, o, inputs):
     return res
 
 
+def extra_time_to_1e6_vs_d(torch, mdi, o, inputs, dims=(4, 6, 8, 10, 12, 16, 20, 24)):
+    """Time to 1e-6 relative error against the closed form, f = exp(sum x_j / j),
+    as d grows.  MDI-LR: closed state, a = N doubling from 16.  Plain kernel: for
+    n = 2^m (m = 16..28) the best of 33 Korobov parameters (12345 and 32 seeded odd
+    ones) by an error scan against the closed form (untimed, reported separately);
+    the first n whose best parameter reaches 1e-6 is timed."""
+    rows = []
+    for d in dims:
+        w = inputs.small_exp(d)
+        c = torch.as_tensor(w.params).cuda()
+        exact = o.closed_form("exp", d, w.c, w.w)
+        row = {"d": d}
+        a = 16
+        while a <= 1 << 24:
+            v, ms = event_ms(torch, lambda: mdi.mdi_lr_integrate("exp", c, d, a, a, state="closed"), reps=3)
+            err = abs(v.item() - exact) / exact
+            if err <= 1e-6:
+                row["mdi_lr"] = {"a": a, "rel_err": err, "ms": ms}
+                break
+            a *= 2
+        rng = np.random.default_rng(1000 + d)
+        search_s, found, best_seen = 0.0, None, None
+        for m in range(16, 29):
+            nn = 1 << m
+            cands = [inputs.SMALL_SLR_A % nn] + [int(x) | 1 for x in rng.integers(3, nn, 32)]
+            t0 = time.perf_counter()
+            errs = []
+            for a_c in cands:
+                zz = o.korobov_z(d, a_c, nn).astype(np.int64)
+                errs.append(abs(mdi.lattice_rule_integrate("exp", c, nn, zz).item() - exact) / exact)
+            search_s += time.perf_counter() - t0
+            b = int(np.argmin(errs))
+            best_seen = {"n": nn, "a": cands[b], "rel_err": errs[b]}
+            if errs[b] <= 1e-6:
+                zz = o.korobov_z(d, cands[b], nn).astype(np.int64)
+                _, ms = event_ms(torch, lambda: mdi.lattice_rule_integrate("exp", c, nn, zz), reps=3)
+                found = dict(best_seen, ms=ms)
+                break
+        row["plain_searched_a"] = found if found else {"reached": False, "best_at_2^28": best_seen}
+        row["plain_search_s_untimed"] = search_s
+        if found and "mdi_lr" in row:
+            row["ratio_plain_over_mdi"] = found["ms"] / row["mdi_lr"]["ms"]
+        rows.append(row)
+    return {"workload": "f = exp(sum_j x_j / j), d in " + str(list(dims)), "rows": rows}
+
+
 # DRAM bytes per launch of the batched kernel from the ncu captures summarised in
 # profiles/ (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel
 # sources they were taken on (SHA-256 prefix of the files below, comments
@@ -720,6 +766,7 @@ def main():
             line["paper_context"] = extra_paper_context(torch, mdi, o)
             line["batch_vs_plain_kernel"] = extra_batch_vs_plain(torch, mdi, o, inputs)
             line["improved_rule"] = extra_improved_rule(torch, mdi, o)
+            line["time_to_1e-6_vs_d"] = extra_time_to_1e6_vs_d(torch, mdi, o, inputs)
         rate, n_done, secs = cpu_oracle_sample(b, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "integrals/s", "cores": 1, "kind": "oracle",
                                 "sample": f"first {n_done} integrals of the batch, {secs:.1f} s single-threaded"}
