@@ -84,7 +84,13 @@ typedef enum { MDI_STATE_AUTO = 0, MDI_STATE_EXACT = 1, MDI_STATE_CLOSED = 2, MD
  *                             double-float pairs of floats (about 48 significant
  *                             bits); FP64 only between levels and on the last
  *                             axis.  OSC keeps phi in FP64.  GB300 runs FP32 64x
- *                             faster than FP64.  Other states: MDI_EUNSUPPORTED. */
+ *                             faster than FP64.  Closed state (forward): the
+ *                             cluster sums of the exponential family in
+ *                             double-float (own exp, Dot2 sums) on levels with
+ *                             |gamma_k| <= 64, other levels and everything else
+ *                             in FP64; a and
+ *                             n_last below 2^31; OSC in FP64.  Other states and
+ *                             gradients: MDI_EUNSUPPORTED. */
 typedef enum {
   MDI_PREC_FP64 = 0,
   MDI_PREC_FP32_EVAL_FP64 = 1,

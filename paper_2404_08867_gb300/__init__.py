@@ -27,7 +27,7 @@ __all__ = [
     "mdi_lr_grad", "mdi_lr_grad_workspace_size", "MDILR", "mdi_lr", "make_batch_descs", "MdiError", "FAMILY", "STATE", "PRECISION", "BATCH_DESC_DTYPE", "library_path",
     "mdi_midpoint_integrate", "mdi_midpoint_workspace_size", "mdi_midpoint_ridge", "lattice_korobov_search", "lattice_cbc",
     "lattice_cbc_workspace_size", "lattice_korobov_search_workspace_size", "lattice_rule_integrate_shifted", "lattice_rule_shifted_workspace_size",
-    "lattice_rule_integrate_improved", "lattice_rule_improved_workspace_size",
+    "lattice_rule_integrate_improved", "lattice_rule_improved_workspace_size", "korobov_vector",
     "shifted_estimate",
 ]
 
@@ -133,6 +133,16 @@ def lattice_rule_integrate_shifted(family, params: torch.Tensor, n: int, z: Sequ
                                                     ws.numel(), _stream(stream))
     _ffi.check(st, "lattice_rule_integrate_shifted")
     return out
+
+
+def korobov_vector(d: int, a: int, n: int) -> np.ndarray:
+    """The Korobov generating vector of Example 2, z_j = a^(j-1) mod n (j = 1..d),
+    in exact integer arithmetic: the z argument of the lattice-rule calls."""
+    z, v = [], 1 % int(n)
+    for _ in range(int(d)):
+        z.append(v)
+        v = v * int(a) % int(n)
+    return np.asarray(z, dtype=np.int64)
 
 
 def lattice_rule_improved_workspace_size(d: int, n: int, a: int) -> int:

@@ -10,6 +10,7 @@ import concurrent.futures as cf
 import glob
 import os
 import shutil
+import struct
 import subprocess
 import sys
 
@@ -18,11 +19,12 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJ = os.path.join(PKG, "_build")
+GEN = os.path.join(OBJ, "gen")
 LIB = os.path.join(PKG, "libmdilr.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-                     "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
+                     "-I", INCLUDE, "-I", CSRC, "-I", GEN, "--expt-relaxed-constexpr"]
 
 
 def _nvcc() -> str:
@@ -34,7 +36,35 @@ def _nvcc() -> str:
 
 def _headers():
     return glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
-        glob.glob(os.path.join(INCLUDE, "*.h"))
+        glob.glob(os.path.join(INCLUDE, "*.h")) + glob.glob(os.path.join(GEN, "*.inc"))
+
+
+def _f32(v: float) -> float:
+    return struct.unpack("<f", struct.pack("<f", v))[0]
+
+
+def exp2_table_source() -> str:
+    """2^(j/256), j = 0..255, as float pairs (hi = v rounded to float, lo = v - hi
+    rounded to float; v - hi is exact in double), written as hex literals: the table
+    of the double-float exp, so that no kernel computes it in FP64 at run time."""
+    rows = []
+    for j in range(256):
+        v = 2.0 ** (j / 256.0)
+        hi = _f32(v)
+        lo = _f32(v - hi)
+        rows.append(f"    {{{hi.hex()}f, {lo.hex()}f}},")
+    return ("// Generated by build.py: 2^(j/256) for j = 0..255 as float pairs (hi, lo).\n"
+            "static __device__ const float2 kExp2TableGen[256] = {\n" + "\n".join(rows) + "\n};\n")
+
+
+def _write_generated():
+    os.makedirs(GEN, exist_ok=True)
+    path = os.path.join(GEN, "mdi_exp2_table.inc")
+    src = exp2_table_source()
+    if not os.path.exists(path) or open(path).read() != src:
+        with open(path + ".tmp", "w") as f:
+            f.write(src)
+        os.replace(path + ".tmp", path)
 
 
 def _stale(target: str, deps) -> bool:
@@ -57,6 +87,7 @@ def _compile(src: str, extra) -> str:
 
 def build(verbose: bool = False, extra_flags=()) -> str:
     os.makedirs(OBJ, exist_ok=True)
+    _write_generated()
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(sources), os.cpu_count() or 4))) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra_flags), sources))

@@ -10,6 +10,11 @@ computes: every launch goes through the C ABI.
   korobov         P_2 Korobov search, n = 65536, d = 4, every a in 1..n/2
   cbc             CBC, n = 65536, d = 4, gamma_j = 1/j^2, unanchored
   midpoint-d1000  paper-table mode, d = 1000, N = 20, n_last = 21 (Gaussian)
+  closed-d4       closed state forward, f = exp(sum x_j / j), d = 4, a = N = 65536,
+                  double-float cluster sums (time to 1e-6 of the small workload)
+  closed-d1000    closed state forward, exp(sum x_j / j^2), d = 1000, N = 16, FP64
+  slr-d4          plain lattice rule, f = exp(sum x_j / j), d = 4, n = 65536, Korobov
+                  a = 11119 (the small workload's error-scanned parameter)
   improved-d7     improved lattice rule, d = 7, z = (1, 16, .., 16^6), n = 1 + 16^7
                   (16^6 - 1 ghosts), f = exp(sum x_j / j)
 """
@@ -53,6 +58,16 @@ def build_case(name: str):
         w = inputs.gaussian(1000, 20, seed=0)
         p = torch.as_tensor(w.params).cuda()
         return lambda: mdi.mdi_midpoint_integrate("gauss", p, 1000, 20, 21)
+    if name == "closed-d4":
+        p = torch.as_tensor(inputs.small_exp(4).params).cuda()
+        return lambda: mdi.mdi_lr_integrate("exp", p, 4, 65536, 65536, state="closed", precision="df64")
+    if name == "closed-d1000":
+        p = torch.as_tensor(inputs.scale_exp(1000, 16).params).cuda()
+        return lambda: mdi.mdi_lr_integrate("exp", p, 1000, 16, 16, state="closed")
+    if name == "slr-d4":
+        p = torch.as_tensor(inputs.small_exp(4).params).cuda()
+        z = mdi.korobov_vector(4, 11119, 65536)
+        return lambda: mdi.lattice_rule_integrate("exp", p, 65536, z)
     if name == "improved-d7":
         d, a = 7, 16
         p = torch.as_tensor(np.r_[1.0 / np.arange(1, d + 1), np.zeros(d)]).cuda()

@@ -18,11 +18,13 @@
 //      r_k points are cut into chunks of up to 1024, one warp per chunk;
 //   3. the chunk sums of each level are added in chunk order (S_k);
 //   4. one CTA multiplies the S_k in level order.
+// When the chunk partials are few (at most 2^15), steps 3 and 4 run as one CTA.
 // Launch count does not depend on d or on a.
 #include <algorithm>
 #include <cmath>
 
 #include "mdi_common.cuh"
+#include "mdi_exp2_table.inc"
 #include "mdi_internal.h"
 #include "mdi_nodes.cuh"
 
@@ -96,12 +98,23 @@ static Chunks make_chunks(int d, int64_t a, int64_t n_last) {
 __device__ __forceinline__ int chunk_base(int k, int d, int cpl) { return k < d - 1 ? k * cpl : (d - 1) * cpl; }
 
 // Sum of exp(iota gamma_k q / r_k) (and of (q/r_k) times it, WITH_T) over one chunk
-// of one level's cluster, per warp.
+// of one level's cluster, per warp.  DF64 (exponential family): x = q (1/r) and
+// gamma x as double-float pairs, the double-float exp (table copied from the
+// generated constants into shared memory), Dot2 accumulation -- for levels with
+// |gamma| <= 64, whose terms e^(gamma x) lie in [e^-64, e^64] and whose chunk sums
+// (at most 1024 terms) stay inside the float range with normal low parts; other
+// levels are summed in FP64.
 template <int FAM, int PREC, bool WITH_T>
 __global__ void __launch_bounds__(kChunkThreads) closed_chunk_kernel(int d, int64_t a, int64_t n_last, Chunks ch,
                                                                      const double *__restrict__ gamma,
                                                                      double2 *__restrict__ partS,
                                                                      double2 *__restrict__ partT) {
+  constexpr bool DFE = (PREC == MDI_PREC_DF64) && (FAM != MDI_FAM_OSC);
+  __shared__ float2 s_exp2[DFE ? kExpTable : 1];
+  if constexpr (DFE) {
+    for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s_exp2[j] = kExp2TableGen[j];
+    __syncthreads();
+  }
   const int lane = threadIdx.x & (kWarp - 1);
   const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
   const int nwarps = gridDim.x * blockDim.x / kWarp;
@@ -119,6 +132,35 @@ __global__ void __launch_bounds__(kChunkThreads) closed_chunk_kernel(int d, int6
     const double g = gamma[k], invr = 1.0 / (double)r;
     double2 s = make_double2(0.0, 0.0), t = make_double2(0.0, 0.0);
     df32 sr{0.f, 0.f}, si{0.f, 0.f};
+    if (DFE && fabs(g) <= 64.0) {
+      const df32 gd = df_from_double(g), ird = df_from_double(invr);
+      const bool small = r <= (int64_t)(1 << 24);  // q exact in one float
+      DfAcc as, at;
+      for (int64_t q = q0 + lane; q < q1; q += kWarp) {
+        df32 x;
+        if (small) {
+          x = df_mul_f(ird, (float)(int)q);
+        } else {  // q < 2^31: q = qh + ql exactly, both floats
+          const int qi = (int)q;
+          const float qh = __int2float_rz(qi);
+          x = df_mul(ird, df32{qh, __int2float_rn(qi - __float2int_rz(qh))});
+        }
+        const df32 e = df_exp(df_mul(gd, x), s_exp2);
+        dacc_add(as, e);
+        if constexpr (WITH_T) dacc_prod(at, e, x);
+      }
+      df32 sv = dacc_value(as), tv = dacc_value(at);
+#pragma unroll
+      for (int off = kWarp / 2; off > 0; off >>= 1) {
+        sv = df_add(sv, df_shfl_down(sv, off));
+        if constexpr (WITH_T) tv = df_add(tv, df_shfl_down(tv, off));
+      }
+      if (lane == 0) {
+        partS[c] = make_double2(df_to_double(sv), 0.0);
+        if constexpr (WITH_T) partT[c] = make_double2(df_to_double(tv), 0.0);
+      }
+      continue;
+    }
     for (int64_t q = q0 + lane; q < q1; q += kWarp) {
       const double x = (double)q * invr;
       const double arg = g * x;
@@ -134,7 +176,7 @@ __global__ void __launch_bounds__(kChunkThreads) closed_chunk_kernel(int d, int6
           e = make_double2((double)fc, (double)fs);
         }
       } else {
-        e = make_double2(PREC == MDI_PREC_FP64 ? exp(arg) : (double)expf((float)arg), 0.0);
+        e = make_double2(PREC == MDI_PREC_FP64 || PREC == MDI_PREC_DF64 ? exp(arg) : (double)expf((float)arg), 0.0);
       }
       if constexpr (PREC == MDI_PREC_FP32_EVAL_DF32) {
         sr = df_add(sr, df32{(float)e.x, 0.f});
@@ -230,11 +272,9 @@ static void launch_reduce(int d, int64_t a, int64_t n_last, const Chunks &ch, co
 // thread 0 multiplies the warps' products in order.  Real families multiply reals.
 constexpr int kProdThreads = 256;
 template <int FAM>
-__global__ void __launch_bounds__(kProdThreads) closed_product_kernel(int d, const double *__restrict__ params,
-                                                                      const double2 *__restrict__ S,
-                                                                      double *__restrict__ out) {
+__device__ void product_body(int d, const double *__restrict__ params, const double2 *__restrict__ S,
+                             double *__restrict__ out, typename FamTraits<FAM>::V *sW) {
   using V = typename FamTraits<FAM>::V;
-  __shared__ V sW[kProdThreads / kWarp];
   const int per = (d + blockDim.x - 1) / blockDim.x;
   const int lo = min(d, (int)threadIdx.x * per), hi = min(d, lo + per);
   V p = VOps<V>::one();
@@ -260,6 +300,40 @@ __global__ void __launch_bounds__(kProdThreads) closed_product_kernel(int d, con
       out[0] = K;
     }
   }
+}
+template <int FAM>
+__global__ void __launch_bounds__(kProdThreads) closed_product_kernel(int d, const double *__restrict__ params,
+                                                                      const double2 *__restrict__ S,
+                                                                      double *__restrict__ out) {
+  __shared__ typename FamTraits<FAM>::V sW[kProdThreads / kWarp];
+  product_body<FAM>(d, params, S, out, sW);
+}
+
+// Small pipelines (few chunk partials): the per-level sums and the product in one
+// CTA.  Warp w sums the chunks of levels w, w + 32, ... (lanes strided over the
+// chunks, then a fixed shuffle tree), writes S_k, and after a barrier the CTA
+// multiplies the S_k as closed_product_kernel does.
+constexpr int kFusedThreads = 1024;
+constexpr int kFusedMaxChunks = 1 << 15;
+template <int FAM>
+__global__ void __launch_bounds__(kFusedThreads) closed_reduce_product_kernel(int d, int64_t a, int64_t n_last,
+                                                                              Chunks ch,
+                                                                              const double *__restrict__ params,
+                                                                              const double2 *__restrict__ partS,
+                                                                              double2 *__restrict__ S,
+                                                                              double *__restrict__ out) {
+  __shared__ typename FamTraits<FAM>::V sW[kFusedThreads / kWarp];
+  const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x / kWarp, nwarps = blockDim.x / kWarp;
+  for (int k = warp; k < d; k += nwarps) {
+    const int n = k < d - 1 ? ch.cpl : ch.cpl_last, base = chunk_base(k, d, ch.cpl);
+    double2 s = make_double2(0.0, 0.0);
+    for (int j = lane; j < n; j += kWarp) s = c_add(s, partS[base + j]);
+    s = warp_sum(s);
+    if (lane == 0) S[k] = c_scale(s, 1.0 / (double)((k + 1 < d) ? a : n_last));
+  }
+  __threadfence_block();
+  __syncthreads();
+  product_body<FAM>(d, params, S, out, sW);
 }
 
 // ---------------------------------------------------------------------------
@@ -302,6 +376,14 @@ size_t closed_workspace_bytes(int d, int64_t a, int64_t n_last) {
   return closed_sizes_ok(d, a, n_last) ? closed_layout(d, a, n_last, false).total : 0;
 }
 
+// Threads of the one-CTA scan: about 8 levels per thread, 32 to 1024.  The scan is
+// FP64 work on one SM, so a block sized to d keeps small d from paying for 1024
+// threads' tree steps.
+static int scan_threads(int d) {
+  const int t = ((d + 7) / 8 + kWarp - 1) / kWarp * kWarp;
+  return std::max(kWarp, std::min(kScanThreads, t));
+}
+
 static int chunk_grid(const Chunks &ch) {
   const int warps_per_cta = kChunkThreads / kWarp;
   return std::max(1, std::min((ch.total + warps_per_cta - 1) / warps_per_cta, sm_count() * 8));
@@ -314,7 +396,7 @@ static mdi_status run_levels_sums(int d, int64_t a, int64_t n_last, const double
   double2 *partS = (double2 *)(base + L.partS), *partT = (double2 *)(base + L.partT);
   double2 *S = (double2 *)(base + L.S), *T = (double2 *)(base + L.T);
   const Chunks ch = make_chunks(d, a, n_last);
-  closed_scan_kernel<<<1, kScanThreads, 0, stream>>>(d, (double)a, params, gamma);
+  closed_scan_kernel<<<1, scan_threads(d), 0, stream>>>(d, (double)a, params, gamma);
   mdi_status st = check_launch();
   if (st != MDI_OK) return st;
   closed_chunk_kernel<FAM, PREC, WITH_T><<<chunk_grid(ch), kChunkThreads, 0, stream>>>(d, a, n_last, ch, gamma, partS,
@@ -328,7 +410,21 @@ template <int FAM, int PREC>
 static mdi_status run_closed(int d, int64_t a, int64_t n_last, const double *params, double *out, void *ws,
                              cudaStream_t stream) {
   const ClosedLayout L = closed_layout(d, a, n_last, false);
-  mdi_status st = run_levels_sums<FAM, PREC, false>(d, a, n_last, params, (char *)ws, L, stream);
+  const Chunks ch = make_chunks(d, a, n_last);
+  char *base = (char *)ws;
+  if (ch.total <= kFusedMaxChunks) {  // three launches: scan, chunk sums, level sums and product
+    double *gamma = (double *)(base + L.gamma);
+    double2 *partS = (double2 *)(base + L.partS), *S = (double2 *)(base + L.S);
+    closed_scan_kernel<<<1, scan_threads(d), 0, stream>>>(d, (double)a, params, gamma);
+    mdi_status st = check_launch();
+    if (st != MDI_OK) return st;
+    closed_chunk_kernel<FAM, PREC, false><<<chunk_grid(ch), kChunkThreads, 0, stream>>>(d, a, n_last, ch, gamma,
+                                                                                        partS, nullptr);
+    if ((st = check_launch()) != MDI_OK) return st;
+    closed_reduce_product_kernel<FAM><<<1, kFusedThreads, 0, stream>>>(d, a, n_last, ch, params, partS, S, out);
+    return check_launch();
+  }
+  mdi_status st = run_levels_sums<FAM, PREC, false>(d, a, n_last, params, base, L, stream);
   if (st != MDI_OK) return st;
   closed_product_kernel<FAM><<<1, kProdThreads, 0, stream>>>(d, params, (const double2 *)((char *)ws + L.S), out);
   return check_launch();
@@ -340,7 +436,10 @@ static mdi_status run_closed_p(int precision, int d, int64_t a, int64_t n_last, 
   switch (precision) {
     case MDI_PREC_FP64: return run_closed<FAM, MDI_PREC_FP64>(d, a, n_last, params, out, ws, stream);
     case MDI_PREC_FP32_EVAL_FP64: return run_closed<FAM, MDI_PREC_FP32_EVAL_FP64>(d, a, n_last, params, out, ws, stream);
-    default: return run_closed<FAM, MDI_PREC_FP32_EVAL_DF32>(d, a, n_last, params, out, ws, stream);
+    case MDI_PREC_FP32_EVAL_DF32: return run_closed<FAM, MDI_PREC_FP32_EVAL_DF32>(d, a, n_last, params, out, ws, stream);
+    default:  // DF64: double-float cluster sums for the exponential family, FP64 for the oscillatory one
+      if constexpr (FAM == MDI_FAM_OSC) return run_closed<FAM, MDI_PREC_FP64>(d, a, n_last, params, out, ws, stream);
+      else return run_closed<FAM, MDI_PREC_DF64>(d, a, n_last, params, out, ws, stream);
   }
 }
 
@@ -348,7 +447,8 @@ mdi_status closed_launch(int family, int d, int64_t a, int64_t n_last, const dou
                          double *out, void *workspace, size_t ws_bytes, cudaStream_t stream) {
   if (family != MDI_FAM_EXP && family != MDI_FAM_OSC) return MDI_EUNSUPPORTED;
   if (!closed_sizes_ok(d, a, n_last)) return MDI_EINVAL;
-  if (precision == MDI_PREC_DF64) return MDI_EUNSUPPORTED;
+  if (precision < MDI_PREC_FP64 || precision > MDI_PREC_DF64) return MDI_EINVAL;
+  if (precision == MDI_PREC_DF64 && (a >= (int64_t)1 << 31 || n_last >= (int64_t)1 << 31)) return MDI_EUNSUPPORTED;
   if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < closed_workspace_bytes(d, a, n_last))
     return MDI_EWORKSPACE;
   if (family == MDI_FAM_EXP) return run_closed_p<MDI_FAM_EXP>(precision, d, a, n_last, params, out, workspace, stream);
@@ -403,6 +503,10 @@ static mdi_status run_midpoint(int d, int64_t N, int64_t n_last, const double *p
   midpoint_chunk_kernel<FAM><<<chunk_grid(ch), kChunkThreads, 0, stream>>>(d, N, n_last, ch, params, partS);
   mdi_status st = check_launch();
   if (st != MDI_OK) return st;
+  if (ch.total <= kFusedMaxChunks) {
+    closed_reduce_product_kernel<FAM><<<1, kFusedThreads, 0, stream>>>(d, N, n_last, ch, params, partS, S, out);
+    return check_launch();
+  }
   launch_reduce<false>(d, N, n_last, ch, partS, partS, S, S, stream);
   if ((st = check_launch()) != MDI_OK) return st;
   closed_product_kernel<FAM><<<1, kProdThreads, 0, stream>>>(d, params, S, out);

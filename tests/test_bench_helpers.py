@@ -1,0 +1,73 @@
+"""Host helpers outside the oracle, pinned against it: the bench's closed forms
+(its error columns' targets), the package's Korobov generating vector, and the
+boundary rule that only the bench's CPU-baseline legs and reference arm, and no
+module of the package, import the oracle."""
+import ast
+import os
+
+import numpy as np
+import pytest
+
+import bench
+import paper_2404_08867_gb300 as mdi
+from oracle import oracle as o
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.mark.parametrize("fam", ["exp", "gauss", "peak", "osc"])
+@pytest.mark.parametrize("d,seed", [(1, 0), (7, 1), (50, 2)])
+def test_exact_integral_matches_oracle(fam, d, seed):
+    rng = np.random.default_rng(seed)
+    c, w = rng.uniform(0.2, 2.0, d), rng.uniform(0.0, 1.0, d)
+    ref = o.closed_form(fam, d, c, w)
+    got = bench.exact_integral(fam, d, c, w)
+    assert abs(got - ref) <= 1e-13 * max(abs(ref), 1e-3)
+
+
+def test_exact_gauss_grad_matches_oracle():
+    rng = np.random.default_rng(5)
+    c, w = rng.uniform(0.2, 1.5, 100), rng.uniform(0.0, 1.0, 100)
+    ref = o.closed_form_grad("gauss", 100, c, w)
+    assert np.max(np.abs(bench.exact_gauss_grad(100, c, w) - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("d,a,n", [(4, 12345, 65536), (20, 3, (1 << 63) - 25), (9, (1 << 62) + 7, (1 << 63) - 25),
+                                   (1, 5, 7), (6, 16, 1 + 16 ** 7)])
+def test_korobov_vector_matches_oracle(d, a, n):
+    assert np.array_equal(mdi.korobov_vector(d, a, n).astype(np.uint64), o.korobov_z(d, a, n))
+
+
+def _oracle_importers(path):
+    tree = ast.parse(open(path).read())
+    found = []
+
+    class V(ast.NodeVisitor):
+        def __init__(self):
+            self.stack = []
+
+        def visit_FunctionDef(self, node):
+            self.stack.append(node.name)
+            self.generic_visit(node)
+            self.stack.pop()
+
+        def visit_ImportFrom(self, node):
+            if node.module and node.module.split(".")[0] == "oracle":
+                found.append(self.stack[0] if self.stack else "<module>")
+
+        def visit_Import(self, node):
+            if any(a.name.split(".")[0] == "oracle" for a in node.names):
+                found.append(self.stack[0] if self.stack else "<module>")
+
+    V().visit(tree)
+    return found
+
+
+def test_oracle_only_in_cpu_baseline_and_reference_legs():
+    users = _oracle_importers(os.path.join(ROOT, "bench.py"))
+    assert users, "the CPU baseline must still time the oracle"
+    assert all(u.startswith("cpu_") for u in users), users
+    pkg = os.path.join(ROOT, "paper_2404_08867_gb300")
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            assert not _oracle_importers(os.path.join(pkg, f)), f

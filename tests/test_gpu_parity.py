@@ -143,6 +143,29 @@ def test_closed_precision_modes(prec, tol):
     close(got, o.mdi_closed("osc", 50, 32, 32, w.c, w.w), "osc", tol=tol)
 
 
+@pytest.mark.parametrize("fam", ["exp", "osc"])
+@pytest.mark.parametrize("d,a,nd", [(4, 16, 16), (1, 5, 5), (7, 1, 3), (50, 32, 32), (1000, 16, 16),
+                                    (2000, 2, 5), (4, 65536, 65536), (300, 100000, 100000), (2, 1 << 25, 7)])
+def test_closed_df64_matches_fp64_oracle(fam, d, a, nd):
+    # Double-float cluster sums (exponential family; OSC evaluates in FP64) against
+    # the FP64 oracle; a = 2^25 takes the two-float cluster coordinate.
+    params = inputs.random_product(fam, d, seed=d + 7, c_range=(0.05, 1.0))
+    if fam == "osc":
+        params[d] = 0.3
+    got = mdi.mdi_lr_integrate(fam, dev(params), d, a, nd, state="closed", precision="df64").item()
+    close(got, o.mdi_closed(fam, d, a, nd, params[:d], params[d:]), fam)
+
+
+@pytest.mark.parametrize("d,c_range", [(3, (90.0, 120.0)), (6, (20.0, 110.0))])
+def test_closed_df64_large_exponents(d, c_range):
+    # |gamma_k| > 64 on some or all levels: those are summed in FP64 (their terms
+    # would leave the float range); the result must still be the FP64 one.
+    a, nd = 64, 64
+    params = inputs.random_product("exp", d, seed=3, c_range=c_range)
+    got = mdi.mdi_lr_integrate("exp", dev(params), d, a, nd, state="closed", precision="df64").item()
+    close(got, o.mdi_closed("exp", d, a, nd, params[:d], params[d:]), "exp")
+
+
 # ----------------------------------------------------------------------------
 # MDI-LR, node state
 # ----------------------------------------------------------------------------
