@@ -18,7 +18,6 @@
 //      r_k points are cut into chunks of up to 1024, one warp per chunk;
 //   3. the chunk sums of each level are added in chunk order (S_k);
 //   4. one CTA multiplies the S_k in level order.
-// When the chunk partials are few (at most 2^15), steps 3 and 4 run as one CTA.
 // Launch count does not depend on d or on a.
 #include <algorithm>
 #include <cmath>
@@ -309,33 +308,6 @@ __global__ void __launch_bounds__(kProdThreads) closed_product_kernel(int d, con
   product_body<FAM>(d, params, S, out, sW);
 }
 
-// Small pipelines (few chunk partials): the per-level sums and the product in one
-// CTA.  Warp w sums the chunks of levels w, w + 32, ... (lanes strided over the
-// chunks, then a fixed shuffle tree), writes S_k, and after a barrier the CTA
-// multiplies the S_k as closed_product_kernel does.
-constexpr int kFusedThreads = 1024;
-constexpr int kFusedMaxChunks = 1 << 15;
-template <int FAM>
-__global__ void __launch_bounds__(kFusedThreads) closed_reduce_product_kernel(int d, int64_t a, int64_t n_last,
-                                                                              Chunks ch,
-                                                                              const double *__restrict__ params,
-                                                                              const double2 *__restrict__ partS,
-                                                                              double2 *__restrict__ S,
-                                                                              double *__restrict__ out) {
-  __shared__ typename FamTraits<FAM>::V sW[kFusedThreads / kWarp];
-  const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x / kWarp, nwarps = blockDim.x / kWarp;
-  for (int k = warp; k < d; k += nwarps) {
-    const int n = k < d - 1 ? ch.cpl : ch.cpl_last, base = chunk_base(k, d, ch.cpl);
-    double2 s = make_double2(0.0, 0.0);
-    for (int j = lane; j < n; j += kWarp) s = c_add(s, partS[base + j]);
-    s = warp_sum(s);
-    if (lane == 0) S[k] = c_scale(s, 1.0 / (double)((k + 1 < d) ? a : n_last));
-  }
-  __threadfence_block();
-  __syncthreads();
-  product_body<FAM>(d, params, S, out, sW);
-}
-
 // ---------------------------------------------------------------------------
 // Workspace: gamma[d] | partS[chunks] | partT[chunks] | S[d] | T[d] | nu[d]
 // ---------------------------------------------------------------------------
@@ -410,21 +382,7 @@ template <int FAM, int PREC>
 static mdi_status run_closed(int d, int64_t a, int64_t n_last, const double *params, double *out, void *ws,
                              cudaStream_t stream) {
   const ClosedLayout L = closed_layout(d, a, n_last, false);
-  const Chunks ch = make_chunks(d, a, n_last);
-  char *base = (char *)ws;
-  if (ch.total <= kFusedMaxChunks) {  // three launches: scan, chunk sums, level sums and product
-    double *gamma = (double *)(base + L.gamma);
-    double2 *partS = (double2 *)(base + L.partS), *S = (double2 *)(base + L.S);
-    closed_scan_kernel<<<1, scan_threads(d), 0, stream>>>(d, (double)a, params, gamma);
-    mdi_status st = check_launch();
-    if (st != MDI_OK) return st;
-    closed_chunk_kernel<FAM, PREC, false><<<chunk_grid(ch), kChunkThreads, 0, stream>>>(d, a, n_last, ch, gamma,
-                                                                                        partS, nullptr);
-    if ((st = check_launch()) != MDI_OK) return st;
-    closed_reduce_product_kernel<FAM><<<1, kFusedThreads, 0, stream>>>(d, a, n_last, ch, params, partS, S, out);
-    return check_launch();
-  }
-  mdi_status st = run_levels_sums<FAM, PREC, false>(d, a, n_last, params, base, L, stream);
+  mdi_status st = run_levels_sums<FAM, PREC, false>(d, a, n_last, params, (char *)ws, L, stream);
   if (st != MDI_OK) return st;
   closed_product_kernel<FAM><<<1, kProdThreads, 0, stream>>>(d, params, (const double2 *)((char *)ws + L.S), out);
   return check_launch();
@@ -503,10 +461,6 @@ static mdi_status run_midpoint(int d, int64_t N, int64_t n_last, const double *p
   midpoint_chunk_kernel<FAM><<<chunk_grid(ch), kChunkThreads, 0, stream>>>(d, N, n_last, ch, params, partS);
   mdi_status st = check_launch();
   if (st != MDI_OK) return st;
-  if (ch.total <= kFusedMaxChunks) {
-    closed_reduce_product_kernel<FAM><<<1, kFusedThreads, 0, stream>>>(d, N, n_last, ch, params, partS, S, out);
-    return check_launch();
-  }
   launch_reduce<false>(d, N, n_last, ch, partS, partS, S, S, stream);
   if ((st = check_launch()) != MDI_OK) return st;
   closed_product_kernel<FAM><<<1, kProdThreads, 0, stream>>>(d, params, S, out);

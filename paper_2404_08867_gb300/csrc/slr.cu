@@ -156,10 +156,14 @@ __global__ void lattice_indices_kernel(const __grid_constant__ SlrArgs args, uin
   }
 }
 
+// CTAs for n points: runs of at least kSlrMinRun indices, but never fewer threads
+// than two CTAs per SM while n allows (the FP64 pipe of every SM is needed for
+// small n; runs then shorten down to one index), and at most 8 CTAs per SM.
 static int slr_grid(uint64_t n) {
-  uint64_t max_threads = (uint64_t)sm_count() * 8 * kSlrThreads;
-  uint64_t want = (n + kSlrMinRun - 1) / kSlrMinRun;
-  uint64_t threads = std::min(max_threads, want);
+  const uint64_t max_threads = (uint64_t)sm_count() * 8 * kSlrThreads;
+  const uint64_t want = (n + kSlrMinRun - 1) / kSlrMinRun;
+  const uint64_t floor_threads = std::min<uint64_t>(n, (uint64_t)sm_count() * 2 * kSlrThreads);
+  const uint64_t threads = std::min(max_threads, std::max(want, floor_threads));
   return (int)std::max<uint64_t>(1, (threads + kSlrThreads - 1) / kSlrThreads);
 }
 
@@ -224,9 +228,12 @@ static void launch_slr_shifted(int grid, int R, const SlrArgs &args, const doubl
 
 static int slr_shifted_grid(uint64_t n, int R) {
   // CTAs per replicate: the R replicates together fill the GPU as one launch over
-  // n * R points would, and none uses more CTAs than a single unshifted launch.
+  // n * R points would (so R = 1 is slr_grid's partition), and none uses more CTAs
+  // than a single unshifted launch.
   const double max_threads = (double)sm_count() * 8 * kSlrThreads;
-  const double threads = std::min(max_threads, std::ceil((double)n * (double)R / kSlrMinRun));
+  const double want = std::ceil((double)n * (double)R / kSlrMinRun);
+  const double floor_threads = std::min((double)n * (double)R, (double)sm_count() * 2 * kSlrThreads);
+  const double threads = std::min(max_threads, std::max(want, floor_threads));
   const int per = (int)std::ceil(threads / (double)R / kSlrThreads);
   return std::max(1, std::min(per, slr_grid(n)));
 }
