@@ -119,7 +119,11 @@ typedef struct {
  *   z        HOST array of d generating-vector entries, 0 <= z_i < n (any vector;
  *            the paper's gcd(z_i, n) = 1 is not required)
  *   params   DEVICE, 2*d doubles (see above)
- *   precision MDI_PREC_FP64 or MDI_PREC_FP32_EVAL_FP64
+ *   precision MDI_PREC_FP64, MDI_PREC_FP32_EVAL_FP64, or MDI_PREC_DF64 (n <= 2^48:
+ *            coordinates, integrand and per-thread sums in double-float pairs of
+ *            floats from the exact integer numerators; a point whose value would
+ *            leave the float range, and the OSC family, in FP64; larger n:
+ *            MDI_EUNSUPPORTED)
  *   out      DEVICE, 1 double: Q = (1/n) sum_{j<n} f((j z mod n) / n)
  * Indices j z_i mod n are exact 64-bit integers; the sum is a fixed-order
  * (deterministic) FP64 reduction.

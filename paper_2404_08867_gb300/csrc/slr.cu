@@ -13,6 +13,7 @@
 #include <mutex>
 
 #include "mdi_common.cuh"
+#include "mdi_exp2_table.inc"
 #include "mdi_internal.h"
 
 namespace mdi {
@@ -125,6 +126,123 @@ __global__ void __launch_bounds__(kSlrThreads) slr_kernel(const __grid_constant_
   if (threadIdx.x == 0) partials[blockIdx.x] = b;
 }
 
+// DF64 (EXP, GAUSS, PEAK): the same points with the integrand in double-float
+// arithmetic on the FP32 pipe.  x_i = r_i / n is formed from the exact integer
+// r_i < 2^48 as r = rh 2^24 + rl (each exact in a float): x = rh (2^24/n) + rl (1/n)
+// with both constants as float pairs (one product when n <= 2^24).  Sums over the
+// coordinates are Dot2 accumulations, exp and 1/x the double-float ones; a point
+// whose value would leave the float range (argument of exp beyond 64 in size, or
+// a peak product outside 2^(+-100)) is evaluated in FP64 into a separate double
+// accumulator.  Each thread's Dot2 sum and double sum are added in double, then
+// the fixed block tree as in slr_kernel.
+constexpr int kSlrDfMaxLog2N = 48;
+template <int FAM, int MAXD>
+__global__ void __launch_bounds__(kSlrThreads) slr_df_kernel(const __grid_constant__ SlrArgs args,
+                                                             const double *__restrict__ params,
+                                                             double *__restrict__ partials) {
+  __shared__ float4 s_cw[MAXD];  // (c.hi, c.lo, w.hi, w.lo)
+  __shared__ float2 s_ic[MAXD];  // 1/c^2 (PEAK)
+  __shared__ double s_c[MAXD], s_w[MAXD];
+  __shared__ float2 s_exp2[kExpTable];
+  __shared__ double s_red[kSlrThreads / kWarp];
+  constexpr int kUnroll = MAXD <= 32 ? MAXD : 1;
+  const int d = args.d;
+  for (int i = threadIdx.x; i < d; i += blockDim.x) {
+    const double c = params[i], w = params[d + i];
+    const df32 cd = df_from_double(c), wd = df_from_double(w);
+    s_cw[i] = make_float4(cd.hi, cd.lo, wd.hi, wd.lo);
+    const df32 ic = df_rcp(df_sqr(cd));
+    s_ic[i] = make_float2(ic.hi, ic.lo);
+    s_c[i] = c;
+    s_w[i] = w;
+  }
+  for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s_exp2[j] = kExp2TableGen[j];
+  __syncthreads();
+  const uint64_t n = args.n;
+  const bool one_limb = n <= (1ull << 24);
+  const df32 inv_n = df_from_double(args.inv_n), inv_n24 = df_from_double(args.inv_n * 16777216.0);
+  auto coord = [&](uint64_t ri) -> df32 {
+    if (one_limb) return df_mul_f(inv_n, (float)(uint32_t)ri);
+    return df_add_sloppy(df_mul_f(inv_n24, (float)(uint32_t)(ri >> 24)), df_mul_f(inv_n, (float)(uint32_t)(ri & 0xFFFFFFu)));
+  };
+  const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t j0, j1;
+  thread_run(n, tid, nthreads, j0, j1);
+  uint64_t r[MAXD];
+#pragma unroll(kUnroll)
+  for (int i = 0; i < MAXD; ++i)
+    if (i < d) r[i] = (j0 < j1) ? mulmod_u63(j0, args.z[i], n) : 0;
+
+  DfAcc acc;
+  double acc64 = 0.0;
+  for (uint64_t j = j0; j < j1; ++j) {
+    if constexpr (FAM == MDI_FAM_PEAK) {
+      df32 p{1.f, 0.f};
+#pragma unroll(kUnroll)
+      for (int i = 0; i < MAXD; ++i) {
+        if (i < d) {
+          const float4 cw = s_cw[i];
+          const df32 t = df_add_sloppy(coord(r[i]), df32{-cw.z, -cw.w});
+          p = df_mul(p, df_add_sloppy(df_sqr(t), df32{s_ic[i].x, s_ic[i].y}));
+        }
+      }
+      const float mag = fabsf(p.hi);
+      if (mag > 0x1p-100f && mag < 0x1p100f) {
+        dacc_add(acc, df_rcp(p));
+      } else {
+        double q = 1.0;
+        for (int i = 0; i < d; ++i) {
+          const double t = (double)r[i] * args.inv_n - s_w[i];
+          q *= 1.0 / (1.0 / (s_c[i] * s_c[i]) + t * t);
+        }
+        acc64 += q;
+      }
+    } else {
+      DfAcc sa;
+#pragma unroll(kUnroll)
+      for (int i = 0; i < MAXD; ++i) {
+        if (i < d) {
+          const float4 cw = s_cw[i];
+          const df32 x = coord(r[i]);
+          if constexpr (FAM == MDI_FAM_GAUSS) {
+            const df32 t = df_mul(df32{cw.x, cw.y}, df_add_sloppy(x, df32{-cw.z, -cw.w}));
+            dacc_prod(sa, t, t);
+          } else {
+            dacc_prod(sa, df32{cw.x, cw.y}, x);
+          }
+        }
+      }
+      df32 arg = dacc_value(sa);
+      if constexpr (FAM == MDI_FAM_GAUSS) arg = df_neg(arg);
+      if (fabsf(arg.hi) <= 64.0f) {
+        dacc_add(acc, df_exp(arg, s_exp2));
+      } else {
+        double sum = 0.0;
+        for (int i = 0; i < d; ++i) {
+          const double x = (double)r[i] * args.inv_n;
+          if constexpr (FAM == MDI_FAM_GAUSS) {
+            const double t = s_c[i] * (x - s_w[i]);
+            sum = fma(t, t, sum);
+          } else {
+            sum = fma(s_c[i], x, sum);
+          }
+        }
+        acc64 += exp(FAM == MDI_FAM_GAUSS ? -sum : sum);
+      }
+    }
+#pragma unroll(kUnroll)
+    for (int i = 0; i < MAXD; ++i) {
+      if (i < d) {
+        uint64_t v = r[i] + args.z[i];
+        r[i] = (v >= n) ? v - n : v;
+      }
+    }
+  }
+  const double b = block_sum((double)acc.s + ((double)acc.c + acc64), s_red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = b;
+}
+
 // Adds `count` partials in a fixed order and writes scale * sum; CTA r handles the
 // partials of replicate r (one CTA without shifts).
 __global__ void __launch_bounds__(kSlrThreads) sum_partials_kernel(const double *__restrict__ partials, int count,
@@ -184,11 +302,52 @@ static void launch_slr_d(int grid, const SlrArgs &args, const double *params, do
   else launch_slr<FAM, F32, kSlrMaxD>(grid, args, params, partials, s);
 }
 
+template <int FAM>
+static void launch_slr_df_d(int grid, const SlrArgs &args, const double *params, double *partials, cudaStream_t s) {
+  if (args.d <= 8) slr_df_kernel<FAM, 8><<<grid, kSlrThreads, 0, s>>>(args, params, partials);
+  else if (args.d <= 16) slr_df_kernel<FAM, 16><<<grid, kSlrThreads, 0, s>>>(args, params, partials);
+  else if (args.d <= 32) slr_df_kernel<FAM, 32><<<grid, kSlrThreads, 0, s>>>(args, params, partials);
+  else slr_df_kernel<FAM, kSlrMaxD><<<grid, kSlrThreads, 0, s>>>(args, params, partials);
+}
+
+// The point sums of one plain-rule launch into `partials` (grid entries).
+static void launch_slr_points(int family, int precision, int grid, const SlrArgs &args, const double *params,
+                              double *partials, cudaStream_t stream) {
+  const bool f32 = precision == MDI_PREC_FP32_EVAL_FP64;
+  const bool df = precision == MDI_PREC_DF64 && family != MDI_FAM_OSC;  // OSC evaluates in FP64
+  switch (family) {
+    case MDI_FAM_EXP:
+      df ? launch_slr_df_d<MDI_FAM_EXP>(grid, args, params, partials, stream)
+         : f32 ? launch_slr_d<MDI_FAM_EXP, true>(grid, args, params, partials, stream)
+               : launch_slr_d<MDI_FAM_EXP, false>(grid, args, params, partials, stream);
+      break;
+    case MDI_FAM_OSC: f32 ? launch_slr_d<MDI_FAM_OSC, true>(grid, args, params, partials, stream)
+                          : launch_slr_d<MDI_FAM_OSC, false>(grid, args, params, partials, stream); break;
+    case MDI_FAM_GAUSS:
+      df ? launch_slr_df_d<MDI_FAM_GAUSS>(grid, args, params, partials, stream)
+         : f32 ? launch_slr_d<MDI_FAM_GAUSS, true>(grid, args, params, partials, stream)
+               : launch_slr_d<MDI_FAM_GAUSS, false>(grid, args, params, partials, stream);
+      break;
+    default:
+      df ? launch_slr_df_d<MDI_FAM_PEAK>(grid, args, params, partials, stream)
+         : f32 ? launch_slr_d<MDI_FAM_PEAK, true>(grid, args, params, partials, stream)
+               : launch_slr_d<MDI_FAM_PEAK, false>(grid, args, params, partials, stream);
+      break;
+  }
+}
+
+// Precision modes of the plain rule: FP64, FP32 evaluation, and DF64 for n <= 2^48.
+static mdi_status slr_precision_ok(int precision, int64_t n) {
+  if (precision == MDI_PREC_FP64 || precision == MDI_PREC_FP32_EVAL_FP64) return MDI_OK;
+  if (precision == MDI_PREC_DF64 && (uint64_t)n <= (1ull << kSlrDfMaxLog2N)) return MDI_OK;
+  return MDI_EUNSUPPORTED;
+}
+
 mdi_status slr_launch(int family, int d, int64_t n, const int64_t *z, const double *params, int precision,
                       double *out, void *workspace, size_t ws_bytes, cudaStream_t stream) {
   if (d < 1 || d > kSlrMaxD || n < 1 || !z || !params || !out) return MDI_EINVAL;
   if (family < MDI_FAM_EXP || family > MDI_FAM_PEAK) return MDI_EINVAL;
-  if (precision != MDI_PREC_FP64 && precision != MDI_PREC_FP32_EVAL_FP64) return MDI_EUNSUPPORTED;
+  if (slr_precision_ok(precision, n) != MDI_OK) return MDI_EUNSUPPORTED;
   for (int i = 0; i < d; ++i)
     if (z[i] < 0 || z[i] >= n) return MDI_EINVAL;
   if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < slr_workspace_bytes(d, n)) return MDI_EWORKSPACE;
@@ -199,17 +358,7 @@ mdi_status slr_launch(int family, int d, int64_t n, const int64_t *z, const doub
   for (int i = 0; i < d; ++i) args.z[i] = (uint64_t)z[i];
   const int grid = slr_grid((uint64_t)n);
   double *partials = (double *)workspace;
-  const bool f32 = precision == MDI_PREC_FP32_EVAL_FP64;
-  switch (family) {
-    case MDI_FAM_EXP: f32 ? launch_slr_d<MDI_FAM_EXP, true>(grid, args, params, partials, stream)
-                          : launch_slr_d<MDI_FAM_EXP, false>(grid, args, params, partials, stream); break;
-    case MDI_FAM_OSC: f32 ? launch_slr_d<MDI_FAM_OSC, true>(grid, args, params, partials, stream)
-                          : launch_slr_d<MDI_FAM_OSC, false>(grid, args, params, partials, stream); break;
-    case MDI_FAM_GAUSS: f32 ? launch_slr_d<MDI_FAM_GAUSS, true>(grid, args, params, partials, stream)
-                            : launch_slr_d<MDI_FAM_GAUSS, false>(grid, args, params, partials, stream); break;
-    default: f32 ? launch_slr_d<MDI_FAM_PEAK, true>(grid, args, params, partials, stream)
-                 : launch_slr_d<MDI_FAM_PEAK, false>(grid, args, params, partials, stream); break;
-  }
+  launch_slr_points(family, precision, grid, args, params, partials, stream);
   mdi_status st = check_launch();
   if (st != MDI_OK) return st;
   sum_partials_kernel<<<1, kSlrThreads, 0, stream>>>(partials, grid, 1.0 / (double)n, out);
@@ -334,7 +483,7 @@ mdi_status slr_launch_noalloc(int family, int d, int64_t n, const int64_t *z, co
                               double *out, cudaStream_t stream) {
   if (d < 1 || d > kSlrMaxD || n < 1 || !z || !params || !out) return MDI_EINVAL;
   if (family < MDI_FAM_EXP || family > MDI_FAM_PEAK) return MDI_EINVAL;
-  if (precision != MDI_PREC_FP64 && precision != MDI_PREC_FP32_EVAL_FP64) return MDI_EUNSUPPORTED;
+  if (slr_precision_ok(precision, n) != MDI_OK) return MDI_EUNSUPPORTED;
   for (int i = 0; i < d; ++i)
     if (z[i] < 0 || z[i] >= n) return MDI_EINVAL;
   const int grid = slr_grid((uint64_t)n);
@@ -349,17 +498,7 @@ mdi_status slr_launch_noalloc(int family, int d, int64_t n, const int64_t *z, co
   for (int i = 0; i < d; ++i) args.z[i] = (uint64_t)z[i];
   // Every slot the sum reads (0..grid-1) is written by this call's CTAs first, so
   // the array needs no clearing between calls.
-  const bool f32 = precision == MDI_PREC_FP32_EVAL_FP64;
-  switch (family) {
-    case MDI_FAM_EXP: f32 ? launch_slr_d<MDI_FAM_EXP, true>(grid, args, params, partials, stream)
-                          : launch_slr_d<MDI_FAM_EXP, false>(grid, args, params, partials, stream); break;
-    case MDI_FAM_OSC: f32 ? launch_slr_d<MDI_FAM_OSC, true>(grid, args, params, partials, stream)
-                          : launch_slr_d<MDI_FAM_OSC, false>(grid, args, params, partials, stream); break;
-    case MDI_FAM_GAUSS: f32 ? launch_slr_d<MDI_FAM_GAUSS, true>(grid, args, params, partials, stream)
-                            : launch_slr_d<MDI_FAM_GAUSS, false>(grid, args, params, partials, stream); break;
-    default: f32 ? launch_slr_d<MDI_FAM_PEAK, true>(grid, args, params, partials, stream)
-                 : launch_slr_d<MDI_FAM_PEAK, false>(grid, args, params, partials, stream); break;
-  }
+  launch_slr_points(family, precision, grid, args, params, partials, stream);
   st = check_launch();
   if (st != MDI_OK) return st;
   sum_partials_kernel<<<1, kSlrThreads, 0, stream>>>(partials, grid, 1.0 / (double)n, out);

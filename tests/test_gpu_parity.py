@@ -82,6 +82,40 @@ def test_slr_fp32_eval_error(fam):
     close(got, o.slr(fam, d, n, z, params[:d], params[d:]), fam, tol=2e-6)
 
 
+@pytest.mark.parametrize("fam", ["exp", "gauss", "peak", "osc"])
+@pytest.mark.parametrize("d,n,a", [(1, 1, 1), (4, 65536, 12345), (3, 1009, 76), (9, 100003, 7), (20, 40009, 3),
+                                   (40, 20011, 5), (3, (1 << 25) + 3, 76543), (2, (1 << 31) - 1, 48271)])
+def test_slr_df64_matches_fp64_oracle(fam, d, n, a):
+    # Double-float integrand and sums; n > 2^24 takes the two-limb coordinate; OSC
+    # evaluates in FP64.  The largest case is checked on a sample-free property:
+    # equality with the FP64 kernel to 1e-12 (its own parity is pinned above).
+    params = inputs.random_product(fam, d, seed=d + n % 1000)
+    z = o.korobov_z(d, a, n)
+    got = mdi.lattice_rule_integrate(fam, dev(params), n, z.astype(np.int64), precision="df64").item()
+    if n < 1 << 28:
+        ref = o.slr(fam, d, n, z, params[:d], params[d:])
+    else:
+        ref = mdi.lattice_rule_integrate(fam, dev(params), n, z.astype(np.int64)).item()
+    close(got, ref, fam)
+
+
+@pytest.mark.parametrize("fam,c_range,d", [("exp", (20.0, 40.0), 4), ("gauss", (4.0, 9.0), 6), ("peak", (30.0, 60.0), 12)])
+def test_slr_df64_out_of_float_range_points(fam, c_range, d):
+    # Arguments of exp beyond 64 in size and peak products beyond 2^100 are summed
+    # in FP64; the rule must still match the FP64 oracle.
+    n, a = 20011, 5
+    params = inputs.random_product(fam, d, seed=11, c_range=c_range)
+    z = o.korobov_z(d, a, n)
+    got = mdi.lattice_rule_integrate(fam, dev(params), n, z.astype(np.int64), precision="df64").item()
+    close(got, o.slr(fam, d, n, z, params[:d], params[d:]), fam)
+
+
+def test_slr_df64_refuses_n_beyond_2_48():
+    z = np.array([1, 3], dtype=np.int64)
+    with pytest.raises(RuntimeError):
+        mdi.lattice_rule_integrate("exp", dev(np.ones(4)), (1 << 48) + 1, z, precision="df64")
+
+
 def test_slr_is_deterministic():
     params = inputs.random_product("gauss", 8, seed=1)
     z = o.korobov_z(8, 7, 3_000_017).astype(np.int64)
