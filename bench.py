@@ -521,6 +521,22 @@ def extra_improved_rule(torch, mdi):
             "plain_ms": ms_p, "plain_rel_err": abs(vp.item() - exact) / exact}
 
 
+def extra_batch_size_sweep(torch, mdi, inputs, counts=(4096, 16384, 65536)):
+    """The batched DF64 launch on larger batches of the same distribution (seed 0):
+    integrals/s as the persistent launch's tail (its largest integrals finishing
+    alone) weighs less.  Context beside the configured 4096-integral step."""
+    from paper_2404_08867_gb300.tuning import BatchedMDILR
+    rows = []
+    for count in counts:
+        b = inputs.batch(count=count, seed=0)
+        plan = BatchedMDILR(b.families, b.d, b.a, b.n_last, b.offsets, b.pool, precision="df64", nodes=P_NODES)
+        plan.tune()
+        _, ms = event_ms(torch, lambda: plan.launch(), reps=5)
+        rows.append({"count": count, "ms": ms, "integrals_per_s": count / (ms * 1e-3),
+                     "block": plan.opts.get("block")})
+    return {"workload": "batches of the configured distribution, DF64, tuned shape", "rows": rows}
+
+
 def extra_paper_context(torch, mdi):
     """The paper's own MDI-LR CPU times (Matlab on an Intel Xeon Gold 6226R at
     2.90 GHz, one process, Section 4) beside this GPU's time for the nearest
@@ -836,6 +852,7 @@ def main():
             line["batch_vs_plain_kernel"] = extra_batch_vs_plain(torch, mdi, inputs)
             line["improved_rule"] = extra_improved_rule(torch, mdi)
             line["time_to_1e-6_vs_d"] = extra_time_to_1e6_vs_d(torch, mdi, inputs)
+            line["batch_size_sweep"] = extra_batch_size_sweep(torch, mdi, inputs)
         rate, n_done, secs = cpu_oracle_sample(b, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "integrals/s", "cores": 1, "kind": "oracle",
                                 "sample": f"first {n_done} integrals of the batch, {secs:.1f} s single-threaded"}

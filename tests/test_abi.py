@@ -157,3 +157,40 @@ def test_new_entry_points_validate_before_launching(lib):
     assert lib.lattice_cbc(4, 101, fake, float("nan"), fake, fake, fake, 1 << 20, _null()) == E
     assert lib.lattice_cbc(4, 101, fake, 0.0, fake, fake, fake, 8, _null()) == W
     assert lib.lattice_cbc_workspace_size((1 << 24) + 1, ctypes.byref(b)) == E
+
+
+def test_improved_rule_and_df64_modes_validate_before_launching(lib):
+    """The improved lattice rule refuses bad sizes, a common factor of a and n with
+    ghosts present, and bad workspaces; the plain rule's double-float mode refuses
+    n beyond 2^48; the closed state's double-float mode refuses a >= 2^31.  All
+    before any launch (no GPU here)."""
+    fake = ctypes.c_void_p(0x1000)
+    E, W, U = _ffi.MDI_EINVAL, _ffi.MDI_EWORKSPACE, _ffi.MDI_EUNSUPPORTED
+    b = ctypes.c_size_t()
+    ng = ctypes.c_int64(-1)
+    # improved rule: family, d range, n < 1, a^(d-1) beyond 2^62, gcd(a, n) > 1 with ghosts
+    assert lib.lattice_rule_integrate_improved(7, 3, 100, 7, fake, fake, ctypes.byref(ng), fake, 1 << 20, _null()) == E
+    assert lib.lattice_rule_integrate_improved(0, 0, 100, 7, fake, fake, None, fake, 1 << 20, _null()) == E
+    assert lib.lattice_rule_integrate_improved(0, 65, 100, 2, fake, fake, None, fake, 1 << 20, _null()) == E
+    assert lib.lattice_rule_integrate_improved(0, 3, 0, 7, fake, fake, None, fake, 1 << 20, _null()) == E
+    assert lib.lattice_rule_integrate_improved(0, 41, 1000, 3, fake, fake, None, fake, 1 << 20, _null()) == E
+    assert lib.lattice_rule_integrate_improved(0, 3, 150, 10, fake, fake, None, fake, 1 << 20, _null()) == E
+    assert lib.lattice_rule_integrate_improved(0, 3, 100, 7, _null(), fake, None, fake, 1 << 20, _null()) == E
+    assert ng.value == -1  # nothing written on refusal
+    # workspace: missing, misaligned, short
+    assert lib.lattice_rule_integrate_improved(0, 3, 100, 7, fake, fake, None, _null(), 1 << 20, _null()) == W
+    assert lib.lattice_rule_integrate_improved(0, 3, 100, 7, fake, fake, None, ctypes.c_void_p(0x1008), 1 << 20,
+                                               _null()) == W
+    assert lib.lattice_rule_integrate_improved(0, 3, 100, 7, fake, fake, None, fake, 8, _null()) == W
+    assert lib.lattice_rule_improved_workspace_size(3, 150, 10, ctypes.byref(b)) == E
+    assert lib.lattice_rule_improved_workspace_size(3, 100, 10, ctypes.byref(b)) == _ffi.MDI_OK  # 10^2 | 100: no ghosts
+    # double-float plain rule beyond 2^48 points
+    z = np.array([1, 3], dtype=np.int64)
+    zp = z.ctypes.data_as(ctypes.c_void_p)
+    assert lib.lattice_rule_integrate(0, 2, (1 << 48) + 1, zp, fake, 3, fake, fake, 1 << 20, _null()) == U
+    assert lib.lattice_rule_integrate_noalloc(0, 2, (1 << 48) + 1, zp, fake, 3, fake, _null()) == U
+    # double-float closed state with a >= 2^31
+    o = _ffi.MdiOpts()
+    o.state = _ffi.STATE["closed"]
+    o.precision = 3
+    assert lib.mdi_lr_integrate(0, 2, 1 << 31, 4, fake, ctypes.byref(o), fake, fake, 1 << 30, _null()) == U
