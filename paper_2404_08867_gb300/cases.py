@@ -15,6 +15,8 @@ computes: every launch goes through the C ABI.
   closed-d1000    closed state forward, exp(sum x_j / j^2), d = 1000, N = 16, FP64
   slr-d4          plain lattice rule, f = exp(sum x_j / j), d = 4, n = 65536, Korobov
                   a = 11119 (the small workload's error-scanned parameter)
+  slr-df-d7       plain lattice rule in double-float, f = exp(sum x_j / j), d = 7,
+                  n = 2^24, Korobov a = 12345
   improved-d7     improved lattice rule, d = 7, z = (1, 16, .., 16^6), n = 1 + 16^7
                   (16^6 - 1 ghosts), f = exp(sum x_j / j)
 """
@@ -68,6 +70,10 @@ def build_case(name: str):
         p = torch.as_tensor(inputs.small_exp(4).params).cuda()
         z = mdi.korobov_vector(4, 11119, 65536)
         return lambda: mdi.lattice_rule_integrate("exp", p, 65536, z)
+    if name == "slr-df-d7":
+        p = torch.as_tensor(inputs.small_exp(7).params).cuda()
+        z = mdi.korobov_vector(7, 12345, 1 << 24)
+        return lambda: mdi.lattice_rule_integrate("exp", p, 1 << 24, z, precision="df64")
     if name == "improved-d7":
         d, a = 7, 16
         p = torch.as_tensor(np.r_[1.0 / np.arange(1, d + 1), np.zeros(d)]).cuda()

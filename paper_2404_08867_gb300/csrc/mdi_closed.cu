@@ -34,14 +34,14 @@ constexpr int kChunkThreads = 256;
 constexpr int64_t kChunkQ = 1024;  // most cluster points per warp chunk
 
 // gamma_k (real: the exponent rate, or its imaginary part for OSC) for k = 1..d.
-__global__ void __launch_bounds__(kScanThreads) closed_scan_kernel(int d, double a, const double *__restrict__ params,
+__global__ void __launch_bounds__(kScanThreads) closed_scan_kernel(int d, double inva,
+                                                                   const double *__restrict__ params,
                                                                    double *__restrict__ gamma) {
   __shared__ double sA[kScanThreads], sB[kScanThreads];
   const int per = (d + blockDim.x - 1) / blockDim.x;
   const int lo = threadIdx.x * per, hi = min(d - 1, lo + per);  // maps for levels lo+1..hi (k < d)
   // Composite of beta_k = beta_{k-1}/a + c_k/a over this thread's levels.
   double A = 1.0, B = 0.0;
-  const double inva = 1.0 / a;
   for (int k = lo; k < hi; ++k) {  // 0-based level k <-> paper's level k+1
     A *= inva;
     B = (B + params[k]) * inva;
@@ -75,9 +75,15 @@ __global__ void __launch_bounds__(kScanThreads) closed_scan_kernel(int d, double
 // Chunks: levels k < d-1 have a points, cut into cpl chunks of q points; the last
 // level has n_last points in cpl_last chunks.  q (a multiple of 32, at most 1024)
 // is chosen so that about 32 warps per SM get a chunk when the levels are small.
+// The reciprocals 1/a and 1/n_last of the two cluster radices are formed once on
+// the host (correctly rounded, the same double the device's division gives) and
+// also as float pairs: an FP64 division per chunk would cost GB300's FP64 pipe
+// about as much as the chunk's own sum.
 struct Chunks {
   int cpl, cpl_last, total;
   int64_t q;
+  double inv_a, inv_nl;
+  float2 inv_a_df, inv_nl_df;
 };
 static int64_t chunk_q(int d, int64_t a, int64_t n_last) {
   const double points = (double)(d - 1) * (double)a + (double)n_last;
@@ -86,8 +92,16 @@ static int64_t chunk_q(int d, int64_t a, int64_t n_last) {
   q = (q + 31) / 32 * 32;
   return std::max<int64_t>(32, std::min<int64_t>(kChunkQ, q));
 }
+static float2 split_df(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
 static Chunks make_chunks(int d, int64_t a, int64_t n_last) {
   Chunks c;
+  c.inv_a = 1.0 / (double)a;
+  c.inv_nl = 1.0 / (double)n_last;
+  c.inv_a_df = split_df(c.inv_a);
+  c.inv_nl_df = split_df(c.inv_nl);
   c.q = chunk_q(d, a, n_last);
   c.cpl = (int)((a + c.q - 1) / c.q);
   c.cpl_last = (int)((n_last + c.q - 1) / c.q);
@@ -128,11 +142,12 @@ __global__ void __launch_bounds__(kChunkThreads) closed_chunk_kernel(int d, int6
     }
     const int64_t r = (k + 1 < d) ? a : n_last;
     const int64_t q0 = (int64_t)j * ch.q, q1 = min(r, q0 + ch.q);
-    const double g = gamma[k], invr = 1.0 / (double)r;
+    const double g = gamma[k], invr = (k + 1 < d) ? ch.inv_a : ch.inv_nl;
     double2 s = make_double2(0.0, 0.0), t = make_double2(0.0, 0.0);
     df32 sr{0.f, 0.f}, si{0.f, 0.f};
     if (DFE && fabs(g) <= 64.0) {
-      const df32 gd = df_from_double(g), ird = df_from_double(invr);
+      const float2 irf = (k + 1 < d) ? ch.inv_a_df : ch.inv_nl_df;
+      const df32 gd = df_from_double(g), ird{irf.x, irf.y};
       const bool small = r <= (int64_t)(1 << 24);  // q exact in one float
       DfAcc as, at;
       for (int64_t q = q0 + lane; q < q1; q += kWarp) {
@@ -211,7 +226,7 @@ __global__ void closed_reduce_small_kernel(int d, int64_t a, int64_t n_last, Chu
                                            double2 *__restrict__ S, double2 *__restrict__ T) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < d; k += gridDim.x * blockDim.x) {
     const int n = k < d - 1 ? ch.cpl : ch.cpl_last, base = chunk_base(k, d, ch.cpl);
-    const double invr = 1.0 / (double)((k + 1 < d) ? a : n_last);
+    const double invr = (k + 1 < d) ? ch.inv_a : ch.inv_nl;
     double2 s = make_double2(0.0, 0.0), t = make_double2(0.0, 0.0);
     for (int j = 0; j < n; ++j) {
       s = c_add(s, partS[base + j]);
@@ -239,7 +254,7 @@ __global__ void __launch_bounds__(kReduceThreads) closed_reduce_kernel(int d, in
   __shared__ double2 s_red[kReduceThreads / kWarp];
   for (int k = blockIdx.x; k < d; k += gridDim.x) {
     const int n = k < d - 1 ? ch.cpl : ch.cpl_last, base = chunk_base(k, d, ch.cpl);
-    const double invr = 1.0 / (double)((k + 1 < d) ? a : n_last);
+    const double invr = (k + 1 < d) ? ch.inv_a : ch.inv_nl;
     double2 s = make_double2(0.0, 0.0), t = make_double2(0.0, 0.0);
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       s = c_add(s, partS[base + j]);
@@ -368,7 +383,7 @@ static mdi_status run_levels_sums(int d, int64_t a, int64_t n_last, const double
   double2 *partS = (double2 *)(base + L.partS), *partT = (double2 *)(base + L.partT);
   double2 *S = (double2 *)(base + L.S), *T = (double2 *)(base + L.T);
   const Chunks ch = make_chunks(d, a, n_last);
-  closed_scan_kernel<<<1, scan_threads(d), 0, stream>>>(d, (double)a, params, gamma);
+  closed_scan_kernel<<<1, scan_threads(d), 0, stream>>>(d, ch.inv_a, params, gamma);
   mdi_status st = check_launch();
   if (st != MDI_OK) return st;
   closed_chunk_kernel<FAM, PREC, WITH_T><<<chunk_grid(ch), kChunkThreads, 0, stream>>>(d, a, n_last, ch, gamma, partS,
@@ -440,7 +455,7 @@ __global__ void __launch_bounds__(kChunkThreads) midpoint_chunk_kernel(int d, in
     }
     const int64_t r = (k + 1 < d) ? N : n_last;
     const int64_t q0 = (int64_t)j * ch.q, q1 = min(r, q0 + ch.q);
-    const double invr = 1.0 / (double)r;
+    const double invr = (k + 1 < d) ? ch.inv_a : ch.inv_nl;
     const AxisParams ap = load_axis(params, d, k);
     double2 s = make_double2(0.0, 0.0);
     for (int64_t q = q0 + lane; q < q1; q += kWarp) s = c_add(s, as2(phi<FAM, false>(((double)q + 0.5) * invr, ap)));

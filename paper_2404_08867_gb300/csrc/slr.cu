@@ -10,6 +10,7 @@
 // one partial per CTA, and a second one-CTA kernel adds the partials in index
 // order, so the result is bitwise reproducible.
 #include <algorithm>
+#include <type_traits>
 #include <mutex>
 
 #include "mdi_common.cuh"
@@ -134,9 +135,12 @@ __global__ void __launch_bounds__(kSlrThreads) slr_kernel(const __grid_constant_
 // whose value would leave the float range (argument of exp beyond 64 in size, or
 // a peak product outside 2^(+-100)) is evaluated in FP64 into a separate double
 // accumulator.  Each thread's Dot2 sum and double sum are added in double, then
-// the fixed block tree as in slr_kernel.
+// the fixed block tree as in slr_kernel.  IDX32 steps the numerators in 32-bit
+// integers, half the integer work of the 64-bit steps; it is used for n <= 2^24
+// (one-limb coordinates), where it was measured faster (with two-limb
+// coordinates it measured slower, so larger n keeps 64-bit steps).
 constexpr int kSlrDfMaxLog2N = 48;
-template <int FAM, int MAXD>
+template <int FAM, int MAXD, bool IDX32>
 __global__ void __launch_bounds__(kSlrThreads) slr_df_kernel(const __grid_constant__ SlrArgs args,
                                                              const double *__restrict__ params,
                                                              double *__restrict__ partials) {
@@ -161,7 +165,8 @@ __global__ void __launch_bounds__(kSlrThreads) slr_df_kernel(const __grid_consta
   const uint64_t n = args.n;
   const bool one_limb = n <= (1ull << 24);
   const df32 inv_n = df_from_double(args.inv_n), inv_n24 = df_from_double(args.inv_n * 16777216.0);
-  auto coord = [&](uint64_t ri) -> df32 {
+  using Idx = typename std::conditional<IDX32, uint32_t, uint64_t>::type;
+  auto coord = [&](Idx ri) -> df32 {
     if (one_limb) return df_mul_f(inv_n, (float)(uint32_t)ri);
     return df_add_sloppy(df_mul_f(inv_n24, (float)(uint32_t)(ri >> 24)), df_mul_f(inv_n, (float)(uint32_t)(ri & 0xFFFFFFu)));
   };
@@ -169,10 +174,11 @@ __global__ void __launch_bounds__(kSlrThreads) slr_df_kernel(const __grid_consta
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint64_t j0, j1;
   thread_run(n, tid, nthreads, j0, j1);
-  uint64_t r[MAXD];
+  const Idx nn = (Idx)n;
+  Idx r[MAXD];
 #pragma unroll(kUnroll)
   for (int i = 0; i < MAXD; ++i)
-    if (i < d) r[i] = (j0 < j1) ? mulmod_u63(j0, args.z[i], n) : 0;
+    if (i < d) r[i] = (j0 < j1) ? (Idx)mulmod_u63(j0, args.z[i], n) : 0;
 
   DfAcc acc;
   double acc64 = 0.0;
@@ -234,8 +240,8 @@ __global__ void __launch_bounds__(kSlrThreads) slr_df_kernel(const __grid_consta
 #pragma unroll(kUnroll)
     for (int i = 0; i < MAXD; ++i) {
       if (i < d) {
-        uint64_t v = r[i] + args.z[i];
-        r[i] = (v >= n) ? v - n : v;
+        const Idx v = r[i] + (Idx)args.z[i];
+        r[i] = (v >= nn) ? v - nn : v;
       }
     }
   }
@@ -302,12 +308,17 @@ static void launch_slr_d(int grid, const SlrArgs &args, const double *params, do
   else launch_slr<FAM, F32, kSlrMaxD>(grid, args, params, partials, s);
 }
 
+template <int FAM, bool IDX32>
+static void launch_slr_df_i(int grid, const SlrArgs &args, const double *params, double *partials, cudaStream_t s) {
+  if (args.d <= 8) slr_df_kernel<FAM, 8, IDX32><<<grid, kSlrThreads, 0, s>>>(args, params, partials);
+  else if (args.d <= 16) slr_df_kernel<FAM, 16, IDX32><<<grid, kSlrThreads, 0, s>>>(args, params, partials);
+  else if (args.d <= 32) slr_df_kernel<FAM, 32, IDX32><<<grid, kSlrThreads, 0, s>>>(args, params, partials);
+  else slr_df_kernel<FAM, kSlrMaxD, IDX32><<<grid, kSlrThreads, 0, s>>>(args, params, partials);
+}
 template <int FAM>
 static void launch_slr_df_d(int grid, const SlrArgs &args, const double *params, double *partials, cudaStream_t s) {
-  if (args.d <= 8) slr_df_kernel<FAM, 8><<<grid, kSlrThreads, 0, s>>>(args, params, partials);
-  else if (args.d <= 16) slr_df_kernel<FAM, 16><<<grid, kSlrThreads, 0, s>>>(args, params, partials);
-  else if (args.d <= 32) slr_df_kernel<FAM, 32><<<grid, kSlrThreads, 0, s>>>(args, params, partials);
-  else slr_df_kernel<FAM, kSlrMaxD><<<grid, kSlrThreads, 0, s>>>(args, params, partials);
+  if (args.n <= (1ull << 24)) launch_slr_df_i<FAM, true>(grid, args, params, partials, s);
+  else launch_slr_df_i<FAM, false>(grid, args, params, partials, s);
 }
 
 // The point sums of one plain-rule launch into `partials` (grid entries).
