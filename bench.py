@@ -761,15 +761,13 @@ def main():
     device_out = plan.out.clone()
 
     # End to end: pinned host inputs -> device, the launch, results -> pinned host.
-    h_descs = plan.descs.cpu().pin_memory()
-    h_order = plan.order.cpu().pin_memory()
-    h_pool = plan.pool.cpu().pin_memory()
+    # The step's inputs (descriptors, order, parameters) in the plan's packed
+    # layout, pinned: one host-to-device copy per step, one copy of the results back.
+    h_in = plan.host_inputs(pinned=True)
     h_out = torch.empty(len(b), dtype=torch.float64).pin_memory()
 
     def e2e_step():
-        plan.descs.copy_(h_descs, non_blocking=True)
-        plan.order.copy_(h_order, non_blocking=True)
-        plan.pool.copy_(h_pool, non_blocking=True)
+        plan.inputs.copy_(h_in, non_blocking=True)
         plan.run()
         h_out.copy_(plan.out, non_blocking=True)
 
@@ -819,7 +817,7 @@ def main():
                 "gpu_launches": args.steps, "launch": {"cuda_graph": True, **{k: v for k, v in tuning.items()
                                                                               if k != "candidates"}},
                 "e2e": {"value": e2e_value, "unit": "integrals/s",
-                        "h2d_bytes_per_step": int(h_descs.numel() + 4 * h_order.numel() + 8 * h_pool.numel()),
+                        "h2d_bytes_per_step": int(h_in.numel()),
                         "d2h_bytes_per_step": int(8 * h_out.numel())},
                 "roofline": roof, "clocks": clocks, "wall_s_timed_region": wall}
         if not args.no_extras:

@@ -1,8 +1,10 @@
 """Autotuned, CUDA-graph-captured batched MDI-LR launches.
 
 ``BatchedMDILR`` owns the device copies of a batch (descriptors, processing
-order from the library's longest-first planner, parameter pool), a prepared
-workspace, and the launch shape.  ``tune()`` times the candidate shapes -- CTA
+order from the library's longest-first planner, parameter pool -- three views of
+one packed device buffer, so that a new batch of the same shape arrives in one
+host-to-device copy of ``host_inputs()``), a prepared workspace, and the launch
+shape.  ``tune()`` times the candidate shapes -- CTA
 size and whether each integral's basis table is staged in shared memory or read
 through L1 -- on the batch itself with CUDA events and keeps the fastest (cached
 per batch signature for the process).  ``capture()`` records the one-kernel
@@ -32,15 +34,42 @@ class BatchedMDILR:
         descs = make_batch_descs(families, d, a, n_last, offsets)
         self.descs_host = descs
         order = mdi_batch_plan(descs, nodes=nodes)
-        self.descs = torch.from_numpy(descs.view(np.uint8).copy()).to(device)
-        self.order = torch.from_numpy(order).to(device)
         pool_t = pool if isinstance(pool, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(pool))
-        self.pool = pool_t.to(device=device, dtype=torch.float64).contiguous()
+        pool_t = pool_t.to(dtype=torch.float64).contiguous().cpu()
+        # Packed inputs: descriptors | order | pool, each 256-byte aligned.
+        def up(x):
+            return (x + 255) // 256 * 256
+        nb_d, nb_o, nb_p = descs.nbytes, 4 * len(order), 8 * pool_t.numel()
+        self._off = (0, up(nb_d), up(nb_d) + up(nb_o))
+        self._nbytes = (nb_d, nb_o, nb_p)
+        host = torch.zeros(self._off[2] + up(nb_p), dtype=torch.uint8)
+        host[0:nb_d] = torch.from_numpy(descs.view(np.uint8).copy())
+        host[self._off[1]:self._off[1] + nb_o] = torch.from_numpy(np.ascontiguousarray(order, dtype=np.int32)).view(
+            torch.uint8)
+        host[self._off[2]:self._off[2] + nb_p] = pool_t.view(torch.uint8)
+        self._host_template = host
+        self.inputs = host.to(device)
+        self.descs, self.order, self.pool = self._views(self.inputs)
         self.out = torch.empty(self.count, dtype=torch.float64, device=device)
         self.workspace = mdi_lr_batched_prepare(device=device, nodes=nodes, precision=precision)
         self.opts = {"nodes": nodes, "precision": precision}
         self.graph: Optional[torch.cuda.CUDAGraph] = None
         self.tuning: Dict = {}
+
+    def _views(self, buf: torch.Tensor):
+        (od, oo, op), (nd, no, npool) = self._off, self._nbytes
+        return (buf[od:od + nd], buf[oo:oo + no].view(torch.int32), buf[op:op + npool].view(torch.float64))
+
+    def host_inputs(self, pinned: bool = True) -> torch.Tensor:
+        """The packed input layout on the host (pinned by default): fill its views
+        (``host_views``) with a new batch of the same shape and copy it into
+        ``inputs`` in one transfer."""
+        h = self._host_template.clone()
+        return h.pin_memory() if pinned else h
+
+    def host_views(self, host: torch.Tensor):
+        """(descriptor bytes, order, parameter pool) views of a ``host_inputs()`` buffer."""
+        return self._views(host)
 
     def signature(self) -> Tuple:
         d = self.descs_host["d"].astype(np.int64)

@@ -68,6 +68,26 @@ def test_graph_replays_after_input_update():
     _check_sample(b2, out, k=24, seed=1)
 
 
+def test_packed_host_inputs_in_one_copy():
+    """A new batch of the same shape written into the plan's pinned packed host
+    layout and copied in one transfer gives the same results as a plan built on it."""
+    b = inputs.batch(count=256, seed=6)
+    plan = _plan(b, "df64")
+    plan.capture()
+    plan.run()
+    b2 = inputs.batch(count=256, seed=6)
+    b2.pool = b2.pool * 1.03
+    h = plan.host_inputs(pinned=True)
+    hd, ho, hp = plan.host_views(h)
+    hp.copy_(torch.from_numpy(b2.pool))
+    plan.inputs.copy_(h, non_blocking=True)
+    out = plan.run().cpu()
+    fresh = _plan(b2, "df64")
+    fresh.opts.update(plan.opts)
+    assert torch.equal(out, fresh.launch().cpu())
+    _check_sample(b2, out.numpy(), k=16, seed=2)
+
+
 def test_bench_batch_in_the_bench_launch_configuration():
     """The bench's own workload (4096 integrals, seed 0, DF64) through the bench's
     path -- autotuned shape, CUDA-graph capture, replay -- with 96 sampled outputs
