@@ -3,7 +3,7 @@ profiling one kernel at a time (``python -m paper_2404_08867_gb300.cases NAME
 [REPEATS]``).  Inputs are the seeded synthetic ones of ``inputs``; nothing here
 computes: every launch goes through the C ABI.
 
-  batch-df64      4096-integral batch, double-float node state (block 64, table via L1)
+  batch-df64      4096-integral batch, double-float node state (block 32, table via L1)
   batch-fp64      the same batch in FP64 (block 64, table via L1)
   levels-d1000    one integral, node state parallel over levels, d = 1000, N = 16:
                   forward and adjoint
@@ -41,7 +41,7 @@ def _batch(precision: str, block: int):
 
 def build_case(name: str):
     if name == "batch-df64":
-        return _batch("df64", 64)
+        return _batch("df64", 32)
     if name == "batch-fp64":
         return _batch("fp64", 64)
     if name == "levels-d1000":

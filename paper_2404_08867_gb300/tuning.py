@@ -81,21 +81,34 @@ class BatchedMDILR:
         return mdi_lr_integrate_batched(self.descs, self.pool, self.count, order=self.order, out=self.out,
                                         workspace=self.workspace, **self.opts, **shape)
 
-    def _time(self, reps: int = 5, **shape) -> float:
+    def _time(self, reps: int = 7, **shape) -> float:
+        """Median device time of one launch with `shape`, replayed from a CUDA graph
+        (as run() replays it), so that host-side marshalling is not counted."""
         for _ in range(2):
             self.launch(**shape)
+        torch.cuda.synchronize()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.launch(**shape)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.launch(**shape)
+        g.replay()
         torch.cuda.synchronize()
         ts = []
         for _ in range(reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            self.launch(**shape)
+            g.replay()
             e1.record()
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1))
         return statistics.median(ts)
 
-    def tune(self, reps: int = 5) -> Dict:
+    def tune(self, reps: int = 7) -> Dict:
         """Times every candidate shape on this batch and keeps the fastest."""
         key = self.signature()
         if key not in _cache:
