@@ -66,6 +66,22 @@ def test_ghosts_beyond_lattice_at_large_n():
     assert abs(got.item() - expect) <= 1e-12 * expect
 
 
+def test_wide_ghost_kernel_closed_form():
+    # d = 33 (the kernel's widest digit bucket), a = 2, n = 1001: M = 2^32 lines of
+    # one position, so the completed grid is r = 0 .. 2^32 - 1 and 2^32 - 1001
+    # ghosts carry 32-digit lines; f = exp(c x_d) has the closed form over r/n.
+    d, a, n = 33, 2, 1001
+    M = a ** (d - 1)
+    N = M * (-(-n // M))
+    cd = 2e-7  # x_d = r/n reaches N/n = 4.3e6: c N/n = 0.86 keeps the terms in [1, 2.4]
+    c = np.zeros(d)
+    c[-1] = cd
+    got, ns = mdi.lattice_rule_integrate_improved("exp", dev(np.r_[c, np.zeros(d)]), d, n, a)
+    assert ns == N - n
+    expect = math.expm1(cd * N / n) / (N * math.expm1(cd / n))
+    assert abs(got.item() - expect) <= 1e-12 * expect
+
+
 def test_matches_plain_rule_without_ghosts():
     d, a, nl = 5, 6, 11
     n = nl * a ** (d - 1)
