@@ -66,7 +66,11 @@ typedef enum { MDI_FAM_EXP = 0, MDI_FAM_OSC = 1, MDI_FAM_GAUSS = 2, MDI_FAM_PEAK
  *                    evaluations in all; exact, exponential in d.
  *   MDI_STATE_CLOSED G_k(x) = K_k exp(beta_k x); exact, for EXP and OSC only.
  *   MDI_STATE_NODES  values at P Chebyshev points, read back by barycentric
- *                    interpolation; O(d a P^2), for every family.
+ *                    interpolation; O(d a P^2), for every family.  A single
+ *                    integral with d >= 8 runs level-parallel (every level's
+ *                    P x P operator at once, then grouped products) in FP64 and
+ *                    both single-precision-evaluation modes; DF64 and d < 8 run
+ *                    the levels in order in one CTA.
  *   MDI_STATE_AUTO   CLOSED for EXP/OSC, NODES otherwise. */
 typedef enum { MDI_STATE_AUTO = 0, MDI_STATE_EXACT = 1, MDI_STATE_CLOSED = 2, MDI_STATE_NODES = 3 } mdi_state;
 

@@ -78,7 +78,9 @@ static int default_checkpoint(int d) {
 // K0: L[t][q*P + p] = l_t((q + xi_p)/a) for one a.  One warp per point u: lane t
 // forms bw_t / (u - xi_t), a shuffle sum gives the denominator, so each lane does
 // two FP64 divisions (the FP64 unit is the scarce one on this chip); the nodes and
-// weights are computed once per CTA.
+// weights are computed once per CTA.  DF writes each value as a float pair into
+// the same 8-byte slot (the compensated double-float build reads it so).
+template <bool DF>
 __global__ void levels_table_kernel(int P, int a, double *__restrict__ L) {
   __shared__ double s_xi[kNodesPMax], s_bw[kNodesPMax];
   for (int t = threadIdx.x; t < P; t += blockDim.x) {
@@ -98,7 +100,15 @@ __global__ void levels_table_kernel(int P, int a, double *__restrict__ L) {
   const double r = (on && !hit) ? s_bw[lane] / (u - xi) : 0.0;
   double den = r;
   for (int off = kWarp / 2; off > 0; off >>= 1) den += __shfl_xor_sync(0xffffffffu, den, off);
-  if (on) L[(size_t)lane * npts + pt] = hit ? (lane == __ffs(hit) - 1 ? 1.0 : 0.0) : r / den;
+  if (on) {
+    const double v = hit ? (lane == __ffs(hit) - 1 ? 1.0 : 0.0) : r / den;
+    if constexpr (DF) {
+      const float h = (float)v;
+      reinterpret_cast<float2 *>(L)[(size_t)lane * npts + pt] = make_float2(h, (float)(v - (double)h));
+    } else {
+      L[(size_t)lane * npts + pt] = v;
+    }
+  }
 }
 
 // Barycentric basis value l_t(u) with the nodes and weights in shared memory.
@@ -112,14 +122,20 @@ __device__ __forceinline__ double basis_at(const double *xi, const double *bw, i
 }
 
 // K1: M_k for k = 1..d-1 (block k-1) and w (block d-1).  M is stored [k][t][p].
-template <int FAM, bool F32>
+// PREC: FP64; FP32_EVAL_FP64 (phi in float); FP32_EVAL_DF32 (phi in float, the
+// cluster sum of each entry as a Dot2 accumulation of the float-pair table values
+// times the float phi values, rounded to double once per entry).
+template <int FAM, int PREC>
 __global__ void __launch_bounds__(kLvThreads) levels_build_kernel(int d, int a, int n_last, int P,
                                                                   const double *__restrict__ prm,
                                                                   const double *__restrict__ L,
                                                                   double2 *__restrict__ M, double2 *__restrict__ w) {
   using V = typename FamTraits<FAM>::V;
+  constexpr bool F32 = PREC != MDI_PREC_FP64;
+  constexpr bool DF = PREC == MDI_PREC_FP32_EVAL_DF32;
   __shared__ double s_xi[kNodesPMax], s_bw[kNodesPMax];
-  __shared__ double2 s_f[kLvMaxPts];
+  __shared__ double2 s_f[DF ? 1 : kLvMaxPts];
+  __shared__ float2 s_ff[DF ? kLvMaxPts : 1];
   __shared__ double2 s_part[kLvThreads];
   for (int t = threadIdx.x; t < P; t += blockDim.x) {
     s_xi[t] = cheb_node(t, P);
@@ -134,21 +150,36 @@ __global__ void __launch_bounds__(kLvThreads) levels_build_kernel(int d, int a, 
       // level k = lev + 1 < d
       for (int i = threadIdx.x; i < npts; i += blockDim.x) {
         const int q = i / P, p = i % P;
-        s_f[i] = as2(phi<FAM, F32>(((double)q + s_xi[p]) * inv_a, ap));
+        const double2 f = as2(phi<FAM, F32>(((double)q + s_xi[p]) * inv_a, ap));
+        if constexpr (DF) s_ff[i] = make_float2((float)f.x, (float)f.y);  // float values: exact
+        else s_f[i] = f;
       }
       __syncthreads();
       double2 *Mk = M + (size_t)lev * P * P;
       for (int o = threadIdx.x; o < P * P; o += blockDim.x) {
         const int t = o / P, p = o % P;
-        const double *Lt = L + (size_t)t * npts + p;
-        double2 acc = make_double2(0.0, 0.0);
-        for (int q = 0; q < a; ++q) {
-          const double l = Lt[q * P];
-          const double2 f = s_f[q * P + p];
-          acc.x = fma(l, f.x, acc.x);
-          if constexpr (FAM == MDI_FAM_OSC) acc.y = fma(l, f.y, acc.y);
+        if constexpr (DF) {
+          const float2 *Lt = reinterpret_cast<const float2 *>(L) + (size_t)t * npts + p;
+          DfAcc ar, ai;
+          for (int q = 0; q < a; ++q) {
+            const float2 l = Lt[q * P];
+            const float2 f = s_ff[q * P + p];
+            dacc_prod(ar, df32{l.x, l.y}, df32{f.x, 0.f});
+            if constexpr (FAM == MDI_FAM_OSC) dacc_prod(ai, df32{l.x, l.y}, df32{f.y, 0.f});
+          }
+          const double im = FAM == MDI_FAM_OSC ? df_to_double(dacc_value(ai)) : 0.0;
+          Mk[o] = c_scale(make_double2(df_to_double(dacc_value(ar)), im), inv_a);
+        } else {
+          const double *Lt = L + (size_t)t * npts + p;
+          double2 acc = make_double2(0.0, 0.0);
+          for (int q = 0; q < a; ++q) {
+            const double l = Lt[q * P];
+            const double2 f = s_f[q * P + p];
+            acc.x = fma(l, f.x, acc.x);
+            if constexpr (FAM == MDI_FAM_OSC) acc.y = fma(l, f.y, acc.y);
+          }
+          Mk[o] = c_scale(acc, inv_a);
         }
-        Mk[o] = c_scale(acc, inv_a);
       }
       __syncthreads();
     } else {
@@ -543,7 +574,7 @@ size_t levels_workspace_bytes(int d, int64_t a, const NodesConfig &cfg, int chec
   return levels_layout(d, a, cfg.P, C).total;
 }
 
-template <int FAM, bool F32>
+template <int FAM, int PREC>
 static mdi_status run_levels(int d, int a, int n_last, const double *params, const NodesConfig &cfg, int C,
                              double *value, double *grad, void *ws, cudaStream_t stream) {
   const LevelsLayout Lo = levels_layout(d, a, cfg.P, C);
@@ -552,11 +583,11 @@ static mdi_status run_levels(int d, int a, int n_last, const double *params, con
   double2 *M = (double2 *)(base + Lo.M), *w = (double2 *)(base + Lo.w);
   double2 *gck = (double2 *)(base + Lo.gck), *lck = (double2 *)(base + Lo.lck), *misc = (double2 *)(base + Lo.misc);
   const int P = cfg.P;
-  levels_table_kernel<<<(a * P + 7) / 8, 8 * kWarp, 0, stream>>>(P, a, L);
+  levels_table_kernel<PREC == MDI_PREC_FP32_EVAL_DF32><<<(a * P + 7) / 8, 8 * kWarp, 0, stream>>>(P, a, L);
   mdi_status st = check_launch();
   if (st != MDI_OK) return st;
   const int grid = std::min(d, sm_count() * 8);
-  levels_build_kernel<FAM, F32><<<grid, kLvThreads, 0, stream>>>(d, a, n_last, P, params, L, M, w);
+  levels_build_kernel<FAM, PREC><<<grid, kLvThreads, 0, stream>>>(d, a, n_last, P, params, L, M, w);
   if ((st = check_launch()) != MDI_OK) return st;
   static bool attrs = false;
   if (!attrs) {
@@ -594,31 +625,38 @@ static mdi_status run_levels(int d, int a, int n_last, const double *params, con
   return st;
 }
 
+template <int FAM>
+static mdi_status run_levels_p(int precision, int d, int a, int n_last, const double *params, const NodesConfig &cfg,
+                               int C, double *value, double *grad, void *ws, cudaStream_t stream) {
+  switch (precision) {
+    case MDI_PREC_FP32_EVAL_FP64:
+      return run_levels<FAM, MDI_PREC_FP32_EVAL_FP64>(d, a, n_last, params, cfg, C, value, grad, ws, stream);
+    case MDI_PREC_FP32_EVAL_DF32:
+      return run_levels<FAM, MDI_PREC_FP32_EVAL_DF32>(d, a, n_last, params, cfg, C, value, grad, ws, stream);
+    default: return run_levels<FAM, MDI_PREC_FP64>(d, a, n_last, params, cfg, C, value, grad, ws, stream);
+  }
+}
+
 mdi_status levels_launch(int family, int d, int64_t a, int64_t n_last, const double *params, const NodesConfig &cfg,
                          int checkpoint, double *value, double *grad, void *workspace, size_t ws_bytes,
                          cudaStream_t stream) {
   if (d < 1 || d > (1 << 16) || a < 1 || a > kNodesAMax || n_last < 1 || n_last > 4096) return MDI_EUNSUPPORTED;
   if (cfg.P < 2 || cfg.P > kNodesPMax || (cfg.P & 1)) return MDI_EINVAL;
   if (grad && cfg.precision != MDI_PREC_FP64) return MDI_EUNSUPPORTED;
-  if (cfg.precision == MDI_PREC_FP32_EVAL_DF32 || cfg.precision == MDI_PREC_DF64) return MDI_EUNSUPPORTED;
+  if (cfg.precision == MDI_PREC_DF64) return MDI_EUNSUPPORTED;
   const int C = checkpoint > 0 ? checkpoint : default_checkpoint(d);
   if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < levels_layout(d, a, cfg.P, C).total)
     return MDI_EWORKSPACE;
-  const bool f32 = cfg.precision == MDI_PREC_FP32_EVAL_FP64;
   const int ai = (int)a, nl = (int)n_last;
   switch (family) {
-    case MDI_FAM_EXP:
-      return f32 ? run_levels<MDI_FAM_EXP, true>(d, ai, nl, params, cfg, C, value, grad, workspace, stream)
-                 : run_levels<MDI_FAM_EXP, false>(d, ai, nl, params, cfg, C, value, grad, workspace, stream);
-    case MDI_FAM_OSC:
-      return f32 ? run_levels<MDI_FAM_OSC, true>(d, ai, nl, params, cfg, C, value, grad, workspace, stream)
-                 : run_levels<MDI_FAM_OSC, false>(d, ai, nl, params, cfg, C, value, grad, workspace, stream);
-    case MDI_FAM_GAUSS:
-      return f32 ? run_levels<MDI_FAM_GAUSS, true>(d, ai, nl, params, cfg, C, value, grad, workspace, stream)
-                 : run_levels<MDI_FAM_GAUSS, false>(d, ai, nl, params, cfg, C, value, grad, workspace, stream);
-    default:
-      return f32 ? run_levels<MDI_FAM_PEAK, true>(d, ai, nl, params, cfg, C, value, grad, workspace, stream)
-                 : run_levels<MDI_FAM_PEAK, false>(d, ai, nl, params, cfg, C, value, grad, workspace, stream);
+    case MDI_FAM_EXP: return run_levels_p<MDI_FAM_EXP>(cfg.precision, d, ai, nl, params, cfg, C, value, grad,
+                                                         workspace, stream);
+    case MDI_FAM_OSC: return run_levels_p<MDI_FAM_OSC>(cfg.precision, d, ai, nl, params, cfg, C, value, grad,
+                                                         workspace, stream);
+    case MDI_FAM_GAUSS: return run_levels_p<MDI_FAM_GAUSS>(cfg.precision, d, ai, nl, params, cfg, C, value, grad,
+                                                             workspace, stream);
+    default: return run_levels_p<MDI_FAM_PEAK>(cfg.precision, d, ai, nl, params, cfg, C, value, grad, workspace,
+                                               stream);
   }
 }
 

@@ -248,6 +248,21 @@ def test_nodes_precision_modes(prec, tol, fam):
     close(got, o.mdi_nodes(fam, 50, 32, 32, 16, params[:50], params[50:]), fam, tol=tol)
 
 
+@pytest.mark.parametrize("fam", ["gauss", "peak", "osc", "exp"])
+@pytest.mark.parametrize("d,a", [(50, 32), (8, 16), (200, 20)])
+def test_nodes_compensated_accumulation(fam, d, a):
+    # Both single-precision-evaluation modes evaluate phi to the same floats; the
+    # compensated one (level-parallel path: Dot2 cluster sums on float-pair basis
+    # values) must give the FP64-accumulated result to double-float accuracy.
+    params = inputs.random_product(fam, d, seed=d + a, c_range=(0.2, 1.2))
+    if fam == "osc":
+        params[d] = 0.3
+    p = dev(params)
+    ref = mdi.mdi_lr_integrate(fam, p, d, a, a, state="nodes", precision="fp32_eval_fp64").item()
+    got = mdi.mdi_lr_integrate(fam, p, d, a, a, state="nodes", precision="fp32_eval_df32").item()
+    close(got, ref, fam, tol=1e-12)
+
+
 # ----------------------------------------------------------------------------
 # Batched node state: the bench's launch configuration
 # ----------------------------------------------------------------------------
