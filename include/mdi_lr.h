@@ -68,9 +68,9 @@ typedef enum { MDI_FAM_EXP = 0, MDI_FAM_OSC = 1, MDI_FAM_GAUSS = 2, MDI_FAM_PEAK
  *   MDI_STATE_NODES  values at P Chebyshev points, read back by barycentric
  *                    interpolation; O(d a P^2), for every family.  A single
  *                    integral with d >= 8 runs level-parallel (every level's
- *                    P x P operator at once, then grouped products) in FP64 and
- *                    both single-precision-evaluation modes; DF64 and d < 8 run
- *                    the levels in order in one CTA.
+ *                    P x P operator at once, then grouped products in FP64) in
+ *                    every precision mode; d < 8 runs the levels in order in
+ *                    one CTA.
  *   MDI_STATE_AUTO   CLOSED for EXP/OSC, NODES otherwise. */
 typedef enum { MDI_STATE_AUTO = 0, MDI_STATE_EXACT = 1, MDI_STATE_CLOSED = 2, MDI_STATE_NODES = 3 } mdi_state;
 
@@ -82,8 +82,9 @@ typedef enum { MDI_STATE_AUTO = 0, MDI_STATE_EXACT = 1, MDI_STATE_CLOSED = 2, MD
  *                             floats; level states, cross-level products, the final
  *                             sum and coordinates in double.
  *   MDI_PREC_DF64            FP64-class results without the FP64 pipe, for the
- *                             node state (batched kernel and short single
- *                             integrals): coordinates, phi (own double-float exp
+ *                             node state (batched kernel; single integrals, where
+ *                             the level-parallel path keeps the products between
+ *                             levels in FP64): coordinates, phi (own double-float exp
  *                             and reciprocal), interpolation and cluster sums in
  *                             double-float pairs of floats (about 48 significant
  *                             bits); FP64 only between levels and on the last

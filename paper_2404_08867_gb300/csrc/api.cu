@@ -68,7 +68,7 @@ static double nodes_cost(const mdi_batch_desc &d, int P) {
 // One node-state integral runs parallel over levels (mdi_levels.cu) when it has
 // enough levels to fill several SMs; short ones take one CTA of the batched kernel.
 static bool use_levels(int d, const NodesConfig &cfg) {
-  return d >= 8 && cfg.precision != MDI_PREC_DF64;
+  return d >= 8;
 }
 
 static bool desc_ok(const mdi_batch_desc &d) {

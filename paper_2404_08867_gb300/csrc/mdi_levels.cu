@@ -31,6 +31,7 @@
 #include <algorithm>
 
 #include "mdi_common.cuh"
+#include "mdi_exp2_table.inc"
 #include "mdi_internal.h"
 #include "mdi_nodes.cuh"
 
@@ -124,19 +125,26 @@ __device__ __forceinline__ double basis_at(const double *xi, const double *bw, i
 // K1: M_k for k = 1..d-1 (block k-1) and w (block d-1).  M is stored [k][t][p].
 // PREC: FP64; FP32_EVAL_FP64 (phi in float); FP32_EVAL_DF32 (phi in float, the
 // cluster sum of each entry as a Dot2 accumulation of the float-pair table values
-// times the float phi values, rounded to double once per entry).
+// times the float phi values, rounded to double once per entry); DF64 (phi in
+// double-float at the double coordinates -- FP64 for OSC -- and the same Dot2
+// sums).  The products between levels and the last axis stay FP64.
 template <int FAM, int PREC>
 __global__ void __launch_bounds__(kLvThreads) levels_build_kernel(int d, int a, int n_last, int P,
                                                                   const double *__restrict__ prm,
                                                                   const double *__restrict__ L,
                                                                   double2 *__restrict__ M, double2 *__restrict__ w) {
   using V = typename FamTraits<FAM>::V;
-  constexpr bool F32 = PREC != MDI_PREC_FP64;
+  constexpr bool F32 = PREC == MDI_PREC_FP32_EVAL_FP64 || PREC == MDI_PREC_FP32_EVAL_DF32;
   constexpr bool DF = PREC == MDI_PREC_FP32_EVAL_DF32;
+  constexpr bool D64 = PREC == MDI_PREC_DF64;
   __shared__ double s_xi[kNodesPMax], s_bw[kNodesPMax];
-  __shared__ double2 s_f[DF ? 1 : kLvMaxPts];
+  __shared__ double2 s_f[DF || D64 ? 1 : kLvMaxPts];
   __shared__ float2 s_ff[DF ? kLvMaxPts : 1];
+  __shared__ float4 s_fd[D64 ? kLvMaxPts : 1];  // (re.hi, re.lo, im.hi, im.lo)
+  __shared__ float2 s_exp2[D64 ? kExpTable : 1];
   __shared__ double2 s_part[kLvThreads];
+  if constexpr (D64)
+    for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s_exp2[j] = kExp2TableGen[j];
   for (int t = threadIdx.x; t < P; t += blockDim.x) {
     s_xi[t] = cheb_node(t, P);
     s_bw[t] = cheb_weight(t, P);
@@ -148,24 +156,49 @@ __global__ void __launch_bounds__(kLvThreads) levels_build_kernel(int d, int a, 
     const AxisParams ap = load_axis(prm, d, lev);
     if (lev < d - 1) {
       // level k = lev + 1 < d
+      df32 cd{0.f, 0.f}, wd{0.f, 0.f}, icd{0.f, 0.f};
+      if constexpr (D64 && FAM != MDI_FAM_OSC) {
+        cd = df_from_double(prm[lev]);
+        wd = df_from_double(prm[d + lev]);
+        icd = df_rcp(df_sqr(cd));
+      }
       for (int i = threadIdx.x; i < npts; i += blockDim.x) {
         const int q = i / P, p = i % P;
-        const double2 f = as2(phi<FAM, F32>(((double)q + s_xi[p]) * inv_a, ap));
-        if constexpr (DF) s_ff[i] = make_float2((float)f.x, (float)f.y);  // float values: exact
-        else s_f[i] = f;
+        const double u = ((double)q + s_xi[p]) * inv_a;
+        if constexpr (D64) {
+          if constexpr (FAM == MDI_FAM_OSC) {
+            const double2 f = as2(phi<FAM, false>(u, ap));
+            const df32 re = df_from_double(f.x), im = df_from_double(f.y);
+            s_fd[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+          } else {
+            const df32 f = phi_df<FAM>(df_from_double(u), make_float4(cd.hi, cd.lo, wd.hi, wd.lo),
+                                       make_float2(icd.hi, icd.lo), s_exp2);
+            s_fd[i] = make_float4(f.hi, f.lo, 0.f, 0.f);
+          }
+        } else {
+          const double2 f = as2(phi<FAM, F32>(u, ap));
+          if constexpr (DF) s_ff[i] = make_float2((float)f.x, (float)f.y);  // float values: exact
+          else s_f[i] = f;
+        }
       }
       __syncthreads();
       double2 *Mk = M + (size_t)lev * P * P;
       for (int o = threadIdx.x; o < P * P; o += blockDim.x) {
         const int t = o / P, p = o % P;
-        if constexpr (DF) {
+        if constexpr (DF || D64) {
           const float2 *Lt = reinterpret_cast<const float2 *>(L) + (size_t)t * npts + p;
           DfAcc ar, ai;
           for (int q = 0; q < a; ++q) {
             const float2 l = Lt[q * P];
-            const float2 f = s_ff[q * P + p];
-            dacc_prod(ar, df32{l.x, l.y}, df32{f.x, 0.f});
-            if constexpr (FAM == MDI_FAM_OSC) dacc_prod(ai, df32{l.x, l.y}, df32{f.y, 0.f});
+            if constexpr (D64) {
+              const float4 f = s_fd[q * P + p];
+              dacc_prod(ar, df32{l.x, l.y}, df32{f.x, f.y});
+              if constexpr (FAM == MDI_FAM_OSC) dacc_prod(ai, df32{l.x, l.y}, df32{f.z, f.w});
+            } else {
+              const float2 f = s_ff[q * P + p];
+              dacc_prod(ar, df32{l.x, l.y}, df32{f.x, 0.f});
+              if constexpr (FAM == MDI_FAM_OSC) dacc_prod(ai, df32{l.x, l.y}, df32{f.y, 0.f});
+            }
           }
           const double im = FAM == MDI_FAM_OSC ? df_to_double(dacc_value(ai)) : 0.0;
           Mk[o] = c_scale(make_double2(df_to_double(dacc_value(ar)), im), inv_a);
@@ -583,7 +616,8 @@ static mdi_status run_levels(int d, int a, int n_last, const double *params, con
   double2 *M = (double2 *)(base + Lo.M), *w = (double2 *)(base + Lo.w);
   double2 *gck = (double2 *)(base + Lo.gck), *lck = (double2 *)(base + Lo.lck), *misc = (double2 *)(base + Lo.misc);
   const int P = cfg.P;
-  levels_table_kernel<PREC == MDI_PREC_FP32_EVAL_DF32><<<(a * P + 7) / 8, 8 * kWarp, 0, stream>>>(P, a, L);
+  constexpr bool kDfTable = PREC == MDI_PREC_FP32_EVAL_DF32 || PREC == MDI_PREC_DF64;
+  levels_table_kernel<kDfTable><<<(a * P + 7) / 8, 8 * kWarp, 0, stream>>>(P, a, L);
   mdi_status st = check_launch();
   if (st != MDI_OK) return st;
   const int grid = std::min(d, sm_count() * 8);
@@ -633,6 +667,8 @@ static mdi_status run_levels_p(int precision, int d, int a, int n_last, const do
       return run_levels<FAM, MDI_PREC_FP32_EVAL_FP64>(d, a, n_last, params, cfg, C, value, grad, ws, stream);
     case MDI_PREC_FP32_EVAL_DF32:
       return run_levels<FAM, MDI_PREC_FP32_EVAL_DF32>(d, a, n_last, params, cfg, C, value, grad, ws, stream);
+    case MDI_PREC_DF64:
+      return run_levels<FAM, MDI_PREC_DF64>(d, a, n_last, params, cfg, C, value, grad, ws, stream);
     default: return run_levels<FAM, MDI_PREC_FP64>(d, a, n_last, params, cfg, C, value, grad, ws, stream);
   }
 }
@@ -643,7 +679,6 @@ mdi_status levels_launch(int family, int d, int64_t a, int64_t n_last, const dou
   if (d < 1 || d > (1 << 16) || a < 1 || a > kNodesAMax || n_last < 1 || n_last > 4096) return MDI_EUNSUPPORTED;
   if (cfg.P < 2 || cfg.P > kNodesPMax || (cfg.P & 1)) return MDI_EINVAL;
   if (grad && cfg.precision != MDI_PREC_FP64) return MDI_EUNSUPPORTED;
-  if (cfg.precision == MDI_PREC_DF64) return MDI_EUNSUPPORTED;
   const int C = checkpoint > 0 ? checkpoint : default_checkpoint(d);
   if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < levels_layout(d, a, cfg.P, C).total)
     return MDI_EWORKSPACE;

@@ -255,20 +255,6 @@ __device__ __forceinline__ void load_level_chunk(LevelConst *lc, const double *_
   for (int j = threadIdx.x; j < n; j += blockDim.x) make_level_const<DF>(prm, d, base + j, lc[j]);
 }
 
-// phi_j(u) in double-float arithmetic (EXP, GAUSS, PEAK).
-template <int FAM> __device__ __forceinline__ df32 phi_df(df32 u, float4 cw, float2 ic, const float2 *tab) {
-  const df32 c{cw.x, cw.y}, w{cw.z, cw.w};
-  if constexpr (FAM == MDI_FAM_EXP) {
-    return df_exp(df_mul(c, u), tab);
-  } else if constexpr (FAM == MDI_FAM_GAUSS) {
-    const df32 t = df_mul(c, df_add(u, df_neg(w)));
-    return df_exp(df_neg(df_sqr(t)), tab);
-  } else {
-    const df32 t = df_add(u, df_neg(w));
-    return df_rcp(df_add(df_sqr(t), df32{ic.x, ic.y}));
-  }
-}
-
 // The argument of phi at the cluster points u = q/a + x0 of one node is affine in
 // q: t = s1 q + s0.  Per level and node:
 //   GAUSS  t = c (u - w)  ->  s1 = c/a, s0 = c (x0 - w);   phi = exp(-t^2)

@@ -52,4 +52,20 @@ template <> __device__ __forceinline__ PhiGrad<MDI_FAM_PEAK> phi_grad64<MDI_FAM_
   return {f, 2.0 * p.ic2 / p.c * f2, 2.0 * t * f2};
 }
 
+// phi_j(u) in double-float arithmetic for the real families: cw = (c.hi, c.lo,
+// w.hi, w.lo), ic = 1/c^2 as a float pair (PEAK), tab = the 2^(j/256) table of the
+// double-float exp.
+template <int FAM> __device__ __forceinline__ df32 phi_df(df32 u, float4 cw, float2 ic, const float2 *tab) {
+  const df32 c{cw.x, cw.y}, w{cw.z, cw.w};
+  if constexpr (FAM == MDI_FAM_EXP) {
+    return df_exp(df_mul(c, u), tab);
+  } else if constexpr (FAM == MDI_FAM_GAUSS) {
+    const df32 t = df_mul(c, df_add(u, df_neg(w)));
+    return df_exp(df_neg(df_sqr(t)), tab);
+  } else {
+    const df32 t = df_add(u, df_neg(w));
+    return df_rcp(df_add(df_sqr(t), df32{ic.x, ic.y}));
+  }
+}
+
 }  // namespace mdi

@@ -318,7 +318,8 @@ def test_batched_mixed_families_and_edges():
 # ----------------------------------------------------------------------------
 @pytest.mark.parametrize("fam", ["gauss", "peak", "exp", "osc"])
 @pytest.mark.parametrize("d,a,nd,P", [(4, 16, 16, 16), (1, 9, 9, 16), (2, 1, 5, 16), (12, 8, 8, 8), (6, 32, 13, 32),
-                                      (5, 64, 64, 16), (30, 20, 20, 16), (20, 32, 32, 16)])
+                                      (5, 64, 64, 16), (30, 20, 20, 16), (20, 32, 32, 16), (50, 32, 32, 16),
+                                      (200, 16, 16, 16), (40, 24, 9, 12)])
 def test_df64_nodes_matches_fp64_oracle(fam, d, a, nd, P):
     params = inputs.random_product(fam, d, seed=3 * d + a)
     got = mdi.mdi_lr_integrate(fam, dev(params), d, a, nd, state="nodes", nodes=P, precision="df64").item()
