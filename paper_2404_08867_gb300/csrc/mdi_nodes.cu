@@ -453,6 +453,22 @@ __device__ void last_level(NodesShared &sh, const void *__restrict__ Ftab, int P
 // the cluster points q = qs, qs + Q, ... and add their sums with shuffles, so a
 // level ends with one barrier; the state is double-buffered by level parity.
 // ---------------------------------------------------------------------------
+// v 2^S for the power-of-two state scales, by adding S to the exponent field (exact;
+// integer operations only -- the FP64 pipe is the scarce one); a result that
+// would leave the normal range, and zero, subnormal or non-finite v, go through
+// ldexp.
+__device__ __forceinline__ double scale_pow2(double v, int S) {
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7FF), ne = e + S;
+  if (e == 0 || e == 0x7FF || ne <= 0 || ne >= 0x7FF) return ldexp(v, S);
+  return __longlong_as_double((b & ~(0x7FFll << 52)) | ((long long)ne << 52));
+}
+// Unbiased exponent of a normal, finite double (0 otherwise), from its bits.
+__device__ __forceinline__ int exponent_of(double v) {
+  const int e = (int)((__double_as_longlong(v) >> 52) & 0x7FF);
+  return (e == 0 || e == 0x7FF) ? 0 : e - 1023;
+}
+
 template <int FAM, int PREC>
 __device__ void sweep_one(NodesShared &sh, const NodesConsts *__restrict__ kc, const void *__restrict__ Ltab,
                           const void *__restrict__ Ftab, int P, int d, int a, int n_last,
@@ -480,6 +496,12 @@ __device__ void sweep_one(NodesShared &sh, const NodesConsts *__restrict__ kc, c
   __syncthreads();
   const double inv_a = 1.0 / (double)a;  // FP64 modes only (folded away in DF64)
   const double xi_p = sh.xi[p];
+  // Single-precision evaluation with double-float contractions interpolates from
+  // a float-pair copy of the state: it is kept as G 2^-S (a power of two per
+  // level, from the first stored value's exponent) so that the copy stays inside
+  // the float range whatever d; the result gets 2^S at the end.
+  constexpr bool RESCALE = DF && !DFSTATE;
+  int S = 0;
 
   for (int k = 1; k < d; ++k) {
     const int j = k - 1;  // axis of this level
@@ -489,6 +511,14 @@ __device__ void sweep_one(NodesShared &sh, const NodesConsts *__restrict__ kc, c
     }
     const LevelConst &L = sh.lc[j % kLvChunk];
     const int rb = (k - 1) & 1, wb = k & 1;
+    double scale = 1.0;
+    if constexpr (RESCALE) {
+      if (k > 1) {
+        const int sk = max(-100, min(100, exponent_of(sh.G[rb][0].x)));
+        S += sk;
+        scale = __longlong_as_double((long long)(1023 - sk) << 52);  // 2^-sk
+      }
+    }
     double2 acc = make_double2(0.0, 0.0);
     DfAcc dre, dim;
     if (act) {
@@ -559,7 +589,7 @@ __device__ void sweep_one(NodesShared &sh, const NodesConsts *__restrict__ kc, c
             const df32 gr = df_mul(sr, ia), gi = df_mul(si, ia);
             sh.Gdf[wb][p] = make_float4(gr.hi, gr.lo, gi.hi, gi.lo);
           } else {
-            const double2 g = make_double2(df_to_double(sr) * inv_a, df_to_double(si) * inv_a);
+            const double2 g = make_double2(df_to_double(sr) * (inv_a * scale), df_to_double(si) * (inv_a * scale));
             sh.G[wb][p] = g;
             sh.Gdf[wb][p] = split2(g);
           }
@@ -574,6 +604,8 @@ __device__ void sweep_one(NodesShared &sh, const NodesConsts *__restrict__ kc, c
 
   // Last level: Q = (1/n_last) sum_s phi_d(s/n_last) G_{d-1}(s/n_last).
   last_level<FAM, PREC>(sh, Ftab, P, d, a, n_last, prm, out_slot, (d - 1) & 1);
+  if constexpr (RESCALE)
+    if (tid == 0 && S != 0) *out_slot = scale_pow2(*out_slot, S);  // the thread that wrote it
 }
 
 // ---------------------------------------------------------------------------
@@ -631,6 +663,11 @@ __device__ void sweep_paired(NodesShared &sh, const NodesConsts *__restrict__ kc
   __syncthreads();
   const df32 ia{sh.iadf.x, sh.iadf.y};
   const df32 ia2{0.5f * ia.hi, 0.5f * ia.lo};  // 1/(2a), exact halving
+  // The stored state is G 2^-S: each level rescales its output by 2^-s, s the
+  // exponent of the first stored value it reads, so that the float pairs hold one
+  // level's growth whatever d (the product over levels leaves the float range,
+  // e.g. 3.7e40 for d = 130).  Exact: powers of two; the result gets 2^S at the end.
+  int S = 0;
 
   for (int k = 1; k < d; ++k) {
     const int j = k - 1;
@@ -658,12 +695,23 @@ __device__ void sweep_paired(NodesShared &sh, const NodesConsts *__restrict__ kc
         dacc_prod(acc_b, phi_df_affine<FAM>(s1b, s0b, (float)(a - 1 - q), L.ic, sh.exp2tab), gb);
       }
     }
+    // The read buffer rb is not written this level: its first value's exponent is
+    // read here, after the cluster loop, so nothing extra stays live through it.
+    int sk = 0;
+    if (k > 1) {
+      const int bits = __float_as_int(sh.Gdf[rb][0].x) & 0x7FFFFFFF;
+      if (bits != 0 && bits < 0x7F800000) sk = max(-100, min(100, (bits >> 23) - 127));
+    }
+    S += sk;
+    const float scale = __int_as_float((127 - sk) << 23);  // 2^-sk
     if (warp_act) {
       const DfAcc sa = lanes_sum_acc(acc_a, Q), sbv = lanes_sum_acc(acc_b, Q);
       if (act && qs == 0) {
-        // E = (G_a + G_b)/2, O = (G_a - G_b)/2 with G = (1/a) * sum: one scale by 1/(2a).
-        const df32 E = df_mul(pair_combine(sa, sbv, 1.0f), ia2);
-        const df32 O = df_mul(pair_combine(sa, sbv, -1.0f), ia2);
+        // E = (G_a + G_b)/2, O = (G_a - G_b)/2 with G = (1/a) * sum: one scale by
+        // 2^-sk/(2a).
+        const df32 ia2s{ia2.hi * scale, ia2.lo * scale};
+        const df32 E = df_mul(pair_combine(sa, sbv, 1.0f), ia2s);
+        const df32 O = df_mul(pair_combine(sa, sbv, -1.0f), ia2s);
         sh.Gdf[wb][pp] = make_float4(E.hi, E.lo, O.hi, O.lo);
       }
     }
@@ -680,6 +728,7 @@ __device__ void sweep_paired(NodesShared &sh, const NodesConsts *__restrict__ kc
   }
   __syncthreads();
   last_level<FAM, MDI_PREC_DF64>(sh, Ftab, P, d, a, n_last, prm, out_slot, gbuf);
+  if (tid == 0 && S != 0) *out_slot = scale_pow2(*out_slot, S);  // the thread that wrote it
 }
 
 // The same pairing in FP64 (real families): the state (E_t, O_t) in sh.G as

@@ -194,3 +194,16 @@ def test_improved_rule_and_df64_modes_validate_before_launching(lib):
     o.state = _ffi.STATE["closed"]
     o.precision = 3
     assert lib.mdi_lr_integrate(0, 2, 1 << 31, 4, fake, ctypes.byref(o), fake, fake, 1 << 30, _null()) == U
+
+
+def test_empty_batch_is_refused(lib):
+    """An empty batch (count 0) or a negative count is refused before any launch,
+    as are the planner and the workspace query on it."""
+    fake = ctypes.c_void_p(0x1000)
+    o = _ffi.MdiOpts()
+    for count in (0, -3):
+        assert lib.mdi_lr_integrate_batched(fake, fake, count, fake, ctypes.byref(o), fake, fake, 1 << 30,
+                                            _null()) == _ffi.MDI_EINVAL
+        assert lib.mdi_batch_plan(fake, count, ctypes.byref(o), fake) == _ffi.MDI_EINVAL
+    b = ctypes.c_size_t()
+    assert lib.mdi_lr_batched_workspace_size(0, ctypes.byref(o), ctypes.byref(b)) == _ffi.MDI_EINVAL

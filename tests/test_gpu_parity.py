@@ -295,7 +295,10 @@ def test_batched_full_size_sampled():
         close(out1[i], o.mdi_nodes(it.family, it.d, it.a, it.n_last, 16, it.c, it.w), it.family)
 
 
-def test_batched_mixed_families_and_edges():
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_batched_mixed_families_and_edges(prec):
+    # d = 1, a = 1, a = 64, n_last = 4096 and n_last != a (the untabulated last
+    # axis), d = 130 (three chunks of level constants), every family.
     fams = ["exp", "osc", "gauss", "peak", "gauss", "exp", "peak", "osc"]
     ds = [1, 2, 3, 64, 5, 130, 7, 1]
     as_ = [1, 64, 5, 2, 33, 16, 1, 3]
@@ -306,10 +309,35 @@ def test_batched_mixed_families_and_edges():
         if f == "osc":
             pool[offs[i] + ds[i]] = 0.17 * (i + 1)
     descs = mdi.make_batch_descs(fams, ds, as_, nls, offs)
-    out = mdi.mdi_lr_integrate_batched(torch.from_numpy(descs.view(np.uint8)).cuda(), dev(pool), len(fams)).cpu()
+    out = mdi.mdi_lr_integrate_batched(torch.from_numpy(descs.view(np.uint8)).cuda(), dev(pool), len(fams),
+                                       precision=prec).cpu()
     for i, f in enumerate(fams):
         p = pool[offs[i]:offs[i] + 2 * ds[i]]
         close(out[i].item(), o.mdi_nodes(f, ds[i], as_[i], nls[i], 16, p[:ds[i]], p[ds[i]:]), f)
+
+
+@pytest.mark.parametrize("prec,tol", [("df64", 1e-12), ("fp32_eval_df32", 1e-4), ("fp64", 1e-12)])
+def test_batched_values_beyond_the_float_range(prec, tol):
+    # d = 300: the exponential integral grows to ~1e90 and the Gaussian and peak
+    # ones shrink below 1e-38, outside what a float pair holds; the double-float
+    # modes keep their state scaled by powers of two and must still match.
+    fams = ["exp", "gauss", "peak", "exp"]
+    ds = [300, 300, 260, 9]
+    as_ = [16, 12, 8, 5]
+    offs = np.concatenate([[0], np.cumsum([2 * d for d in ds[:-1]])])
+    ranges = [(0.6, 1.6), (1.5, 2.5), (0.3, 0.6), (0.6, 1.6)]
+    pool = np.concatenate([inputs.random_product(f, d, seed=40 + i, c_range=ranges[i])
+                           for i, (f, d) in enumerate(zip(fams, ds))])
+    descs = mdi.make_batch_descs(fams, ds, as_, as_, offs)
+    out = mdi.mdi_lr_integrate_batched(torch.from_numpy(descs.view(np.uint8)).cuda(), dev(pool), len(fams),
+                                       precision=prec).cpu()
+    refs = []
+    for i, f in enumerate(fams):
+        p = pool[offs[i]:offs[i] + 2 * ds[i]]
+        refs.append(o.mdi_nodes(f, ds[i], as_[i], as_[i], 16, p[:ds[i]], p[ds[i]:]))
+    assert refs[0] > 1e60 and refs[1] < 1e-38 and refs[2] < 1e-38
+    for i, f in enumerate(fams):
+        close(out[i].item(), refs[i], f, tol=tol)
 
 
 # ----------------------------------------------------------------------------
