@@ -89,7 +89,11 @@ typedef enum { MDI_STATE_AUTO = 0, MDI_STATE_EXACT = 1, MDI_STATE_CLOSED = 2, MD
  *                             double-float pairs of floats (about 48 significant
  *                             bits); FP64 only between levels and on the last
  *                             axis.  OSC keeps phi in FP64.  GB300 runs FP32 64x
- *                             faster than FP64.  Closed state (forward): the
+ *                             faster than FP64.  The node state's values may leave
+ *                             the float range (the state is kept scaled by powers
+ *                             of two), but each factor phi_j must not: EXP needs
+ *                             |c_j| <= 80, GAUSS c_j^2 (x - w_j)^2 <= 80 and PEAK
+ *                             c_j <= 2^60 on [0, 1]; beyond that use MDI_PREC_FP64.  Closed state (forward): the
  *                             cluster sums of the exponential family in
  *                             double-float (own exp, Dot2 sums) on levels with
  *                             |gamma_k| <= 64, other levels and everything else
