@@ -171,13 +171,17 @@ mdi_status lattice_rule_integrate_noalloc(int32_t family, int32_t d, int64_t n, 
  *   shifts   DEVICE, R*d doubles, Delta_r = shifts[r*d .. r*d + d), each in [0, 1)
  *   out      DEVICE, R doubles
  *   R        1..65535
- * FP64; other arguments and the index arithmetic as lattice_rule_integrate.  Two
+ *   precision MDI_PREC_FP64, or MDI_PREC_DF64 (n <= 2^48; the shifted coordinate
+ *            {r/n + Delta} as a float pair, the rest as the plain rule's DF64 mode;
+ *            OSC in FP64); others MDI_EUNSUPPORTED
+ * Other arguments and the index arithmetic as lattice_rule_integrate.  Two
  * launches on `stream`.  MDI_EINVAL for bad sizes; MDI_EWORKSPACE for a missing,
  * misaligned or short workspace (lattice_rule_shifted_workspace_size).
  * ------------------------------------------------------------------------- */
 mdi_status lattice_rule_integrate_shifted(int32_t family, int32_t d, int64_t n, const int64_t *z,
-                                          const double *params, const double *shifts, int32_t R, double *out,
-                                          void *workspace, size_t ws_bytes, mdi_stream_t stream);
+                                          const double *params, const double *shifts, int32_t R,
+                                          int32_t precision, double *out, void *workspace, size_t ws_bytes,
+                                          mdi_stream_t stream);
 mdi_status lattice_rule_shifted_workspace_size(int32_t d, int64_t n, int32_t R, size_t *bytes);
 
 /* ---------------------------------------------------------------------------

@@ -113,7 +113,7 @@ def lattice_rule_shifted_workspace_size(d: int, n: int, R: int) -> int:
 
 def lattice_rule_integrate_shifted(family, params: torch.Tensor, n: int, z: Sequence[int], shifts: torch.Tensor,
                                    out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
-                                   stream=None) -> torch.Tensor:
+                                   stream=None, precision="fp64") -> torch.Tensor:
     """R replicates of the randomly shifted rule, (1/n) sum_j f({j z/n + Delta_r}):
     ``shifts`` is an (R, d) float64 CUDA tensor of shifts in [0, 1).  Returns R values."""
     _dev_f64(params, "params")
@@ -128,7 +128,7 @@ def lattice_rule_integrate_shifted(family, params: torch.Tensor, n: int, z: Sequ
     ws = _workspace(lattice_rule_shifted_workspace_size(d, n, R), params.device, workspace)
     st = _ffi.load().lattice_rule_integrate_shifted(_fam(family), d, int(n), zz.ctypes.data_as(ctypes.c_void_p),
                                                     ctypes.c_void_p(params.data_ptr()),
-                                                    ctypes.c_void_p(shifts.data_ptr()), R,
+                                                    ctypes.c_void_p(shifts.data_ptr()), R, _prec(precision),
                                                     ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
                                                     ws.numel(), _stream(stream))
     _ffi.check(st, "lattice_rule_integrate_shifted")

@@ -119,11 +119,13 @@ mdi_status lattice_rule_shifted_workspace_size(int32_t d, int64_t n, int32_t R, 
 }
 
 mdi_status lattice_rule_integrate_shifted(int32_t family, int32_t d, int64_t n, const int64_t *z,
-                                          const double *params, const double *shifts, int32_t R, double *out,
-                                          void *workspace, size_t ws_bytes, mdi_stream_t stream) {
+                                          const double *params, const double *shifts, int32_t R,
+                                          int32_t precision, double *out, void *workspace, size_t ws_bytes,
+                                          mdi_stream_t stream) {
   NvtxRange nvtx_scope("lattice_rule_integrate_shifted");
   if (!family_ok(family)) return MDI_EINVAL;
-  return slr_shifted_launch(family, d, n, z, params, shifts, R, out, workspace, ws_bytes, (cudaStream_t)stream);
+  return slr_shifted_launch(family, d, n, z, params, shifts, R, precision, out, workspace, ws_bytes,
+                            (cudaStream_t)stream);
 }
 
 mdi_status lattice_rule_improved_workspace_size(int32_t d, int64_t n, int64_t a, size_t *bytes) {

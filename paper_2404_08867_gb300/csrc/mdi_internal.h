@@ -34,8 +34,8 @@ size_t slr_improved_workspace_bytes(int d, int64_t n, int64_t a);  // 0 when out
 mdi_status slr_improved_launch(int family, int d, int64_t n, int64_t a, const double *params, double *out,
                                int64_t *n_ghost, void *workspace, size_t ws_bytes, cudaStream_t stream);
 mdi_status slr_shifted_launch(int family, int d, int64_t n, const int64_t *z, const double *params,
-                              const double *shifts, int R, double *out, void *workspace, size_t ws_bytes,
-                              cudaStream_t stream);
+                              const double *shifts, int R, int precision, double *out, void *workspace,
+                              size_t ws_bytes, cudaStream_t stream);
 
 // mdi_ridge.cu: paper-table mode for (c0 + sum x_i)^(-p), histogram state
 size_t ridge_workspace_bytes(int d, int64_t N, int64_t n_last);  // 0 when out of range

@@ -140,10 +140,16 @@ __global__ void __launch_bounds__(kSlrThreads) slr_kernel(const __grid_constant_
 // (one-limb coordinates), where it was measured faster (with two-limb
 // coordinates it measured slower, so larger n keeps 64-bit steps).
 constexpr int kSlrDfMaxLog2N = 48;
-template <int FAM, int MAXD, bool IDX32>
+// SHIFT: the randomly shifted rule, x = {j z / n + Delta_r} for replicate
+// r = blockIdx.y (as slr_kernel): the shift as a float pair is added to the
+// coordinate and 1 subtracted when the sum reaches 1 (exact: Sterbenz).
+template <int FAM, int MAXD, bool IDX32, bool SHIFT = false>
 __global__ void __launch_bounds__(kSlrThreads) slr_df_kernel(const __grid_constant__ SlrArgs args,
                                                              const double *__restrict__ params,
-                                                             double *__restrict__ partials) {
+                                                             double *__restrict__ partials,
+                                                             const double *__restrict__ shifts = nullptr) {
+  __shared__ float2 s_dx[SHIFT ? MAXD : 1];
+  __shared__ double s_dxd[SHIFT ? MAXD : 1];
   __shared__ float4 s_cw[MAXD];  // (c.hi, c.lo, w.hi, w.lo)
   __shared__ float2 s_ic[MAXD];  // 1/c^2 (PEAK)
   __shared__ double s_c[MAXD], s_w[MAXD];
@@ -159,16 +165,40 @@ __global__ void __launch_bounds__(kSlrThreads) slr_df_kernel(const __grid_consta
     s_ic[i] = make_float2(ic.hi, ic.lo);
     s_c[i] = c;
     s_w[i] = w;
+    if constexpr (SHIFT) {
+      const double dx = shifts[(size_t)blockIdx.y * d + i];
+      const df32 dd = df_from_double(dx);
+      s_dx[i] = make_float2(dd.hi, dd.lo);
+      s_dxd[i] = dx;
+    }
   }
+  if constexpr (SHIFT) partials += (size_t)blockIdx.y * gridDim.x;
   for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s_exp2[j] = kExp2TableGen[j];
   __syncthreads();
   const uint64_t n = args.n;
   const bool one_limb = n <= (1ull << 24);
   const df32 inv_n = df_from_double(args.inv_n), inv_n24 = df_from_double(args.inv_n * 16777216.0);
   using Idx = typename std::conditional<IDX32, uint32_t, uint64_t>::type;
-  auto coord = [&](Idx ri) -> df32 {
+  auto coord0 = [&](Idx ri) -> df32 {
     if (one_limb) return df_mul_f(inv_n, (float)(uint32_t)ri);
     return df_add_sloppy(df_mul_f(inv_n24, (float)(uint32_t)(ri >> 24)), df_mul_f(inv_n, (float)(uint32_t)(ri & 0xFFFFFFu)));
+  };
+  auto coord = [&](Idx ri, int i) -> df32 {
+    df32 x = coord0(ri);
+    if constexpr (SHIFT) {
+      x = df_add_sloppy(x, df32{s_dx[i].x, s_dx[i].y});
+      if (x.hi > 1.0f || (x.hi == 1.0f && x.lo >= 0.0f)) x = df_add_sloppy(x, df32{-1.0f, 0.0f});
+    }
+    return x;
+  };
+  // The same coordinate in double for the FP64 fallback.
+  auto coord64 = [&](Idx ri, int i) -> double {
+    double x = (double)ri * args.inv_n;
+    if constexpr (SHIFT) {
+      x += s_dxd[i];
+      if (x >= 1.0) x -= 1.0;
+    }
+    return x;
   };
   const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -189,7 +219,7 @@ __global__ void __launch_bounds__(kSlrThreads) slr_df_kernel(const __grid_consta
       for (int i = 0; i < MAXD; ++i) {
         if (i < d) {
           const float4 cw = s_cw[i];
-          const df32 t = df_add_sloppy(coord(r[i]), df32{-cw.z, -cw.w});
+          const df32 t = df_add_sloppy(coord(r[i], i), df32{-cw.z, -cw.w});
           p = df_mul(p, df_add_sloppy(df_sqr(t), df32{s_ic[i].x, s_ic[i].y}));
         }
       }
@@ -199,7 +229,7 @@ __global__ void __launch_bounds__(kSlrThreads) slr_df_kernel(const __grid_consta
       } else {
         double q = 1.0;
         for (int i = 0; i < d; ++i) {
-          const double t = (double)r[i] * args.inv_n - s_w[i];
+          const double t = coord64(r[i], i) - s_w[i];
           q *= 1.0 / (1.0 / (s_c[i] * s_c[i]) + t * t);
         }
         acc64 += q;
@@ -210,7 +240,7 @@ __global__ void __launch_bounds__(kSlrThreads) slr_df_kernel(const __grid_consta
       for (int i = 0; i < MAXD; ++i) {
         if (i < d) {
           const float4 cw = s_cw[i];
-          const df32 x = coord(r[i]);
+          const df32 x = coord(r[i], i);
           if constexpr (FAM == MDI_FAM_GAUSS) {
             const df32 t = df_mul(df32{cw.x, cw.y}, df_add_sloppy(x, df32{-cw.z, -cw.w}));
             dacc_prod(sa, t, t);
@@ -226,7 +256,7 @@ __global__ void __launch_bounds__(kSlrThreads) slr_df_kernel(const __grid_consta
       } else {
         double sum = 0.0;
         for (int i = 0; i < d; ++i) {
-          const double x = (double)r[i] * args.inv_n;
+          const double x = coord64(r[i], i);
           if constexpr (FAM == MDI_FAM_GAUSS) {
             const double t = s_c[i] * (x - s_w[i]);
             sum = fma(t, t, sum);
@@ -404,11 +434,29 @@ size_t slr_shifted_workspace_bytes(int d, int64_t n, int R) {
   return align_up(sizeof(double) * (size_t)slr_shifted_grid((uint64_t)n, R) * (size_t)R);
 }
 
+template <int FAM, bool IDX32>
+static void launch_slr_df_shift_i(int grid, int R, const SlrArgs &args, const double *params, double *partials,
+                                  const double *shifts, cudaStream_t s) {
+  const dim3 g(grid, R);
+  if (args.d <= 8) slr_df_kernel<FAM, 8, IDX32, true><<<g, kSlrThreads, 0, s>>>(args, params, partials, shifts);
+  else if (args.d <= 16) slr_df_kernel<FAM, 16, IDX32, true><<<g, kSlrThreads, 0, s>>>(args, params, partials, shifts);
+  else if (args.d <= 32) slr_df_kernel<FAM, 32, IDX32, true><<<g, kSlrThreads, 0, s>>>(args, params, partials, shifts);
+  else slr_df_kernel<FAM, kSlrMaxD, IDX32, true><<<g, kSlrThreads, 0, s>>>(args, params, partials, shifts);
+}
+template <int FAM>
+static void launch_slr_df_shift(int grid, int R, const SlrArgs &args, const double *params, double *partials,
+                                const double *shifts, cudaStream_t s) {
+  if (args.n <= (1ull << 24)) launch_slr_df_shift_i<FAM, true>(grid, R, args, params, partials, shifts, s);
+  else launch_slr_df_shift_i<FAM, false>(grid, R, args, params, partials, shifts, s);
+}
+
 mdi_status slr_shifted_launch(int family, int d, int64_t n, const int64_t *z, const double *params,
-                              const double *shifts, int R, double *out, void *workspace, size_t ws_bytes,
-                              cudaStream_t stream) {
+                              const double *shifts, int R, int precision, double *out, void *workspace,
+                              size_t ws_bytes, cudaStream_t stream) {
   if (d < 1 || d > kSlrMaxD || n < 1 || !z || !params || !shifts || !out || R < 1 || R > 65535) return MDI_EINVAL;
   if (family < MDI_FAM_EXP || family > MDI_FAM_PEAK) return MDI_EINVAL;
+  if (precision != MDI_PREC_FP64 && !(precision == MDI_PREC_DF64 && (uint64_t)n <= (1ull << kSlrDfMaxLog2N)))
+    return MDI_EUNSUPPORTED;
   for (int i = 0; i < d; ++i)
     if (z[i] < 0 || z[i] >= n) return MDI_EINVAL;
   if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < slr_shifted_workspace_bytes(d, n, R))
@@ -420,11 +468,21 @@ mdi_status slr_shifted_launch(int family, int d, int64_t n, const int64_t *z, co
   for (int i = 0; i < d; ++i) args.z[i] = (uint64_t)z[i];
   const int grid = slr_shifted_grid((uint64_t)n, R);
   double *partials = (double *)workspace;
+  const bool df = precision == MDI_PREC_DF64;  // OSC evaluates in FP64
   switch (family) {
-    case MDI_FAM_EXP: launch_slr_shifted<MDI_FAM_EXP>(grid, R, args, params, partials, shifts, stream); break;
+    case MDI_FAM_EXP:
+      df ? launch_slr_df_shift<MDI_FAM_EXP>(grid, R, args, params, partials, shifts, stream)
+         : launch_slr_shifted<MDI_FAM_EXP>(grid, R, args, params, partials, shifts, stream);
+      break;
     case MDI_FAM_OSC: launch_slr_shifted<MDI_FAM_OSC>(grid, R, args, params, partials, shifts, stream); break;
-    case MDI_FAM_GAUSS: launch_slr_shifted<MDI_FAM_GAUSS>(grid, R, args, params, partials, shifts, stream); break;
-    default: launch_slr_shifted<MDI_FAM_PEAK>(grid, R, args, params, partials, shifts, stream); break;
+    case MDI_FAM_GAUSS:
+      df ? launch_slr_df_shift<MDI_FAM_GAUSS>(grid, R, args, params, partials, shifts, stream)
+         : launch_slr_shifted<MDI_FAM_GAUSS>(grid, R, args, params, partials, shifts, stream);
+      break;
+    default:
+      df ? launch_slr_df_shift<MDI_FAM_PEAK>(grid, R, args, params, partials, shifts, stream)
+         : launch_slr_shifted<MDI_FAM_PEAK>(grid, R, args, params, partials, shifts, stream);
+      break;
   }
   mdi_status st = check_launch();
   if (st != MDI_OK) return st;

@@ -143,9 +143,12 @@ def test_new_entry_points_validate_before_launching(lib):
     # shifted rule: R range, z range
     z = (ctypes.c_int64 * 2)(1, 5)
     zp = ctypes.cast(z, ctypes.c_void_p)
-    assert lib.lattice_rule_integrate_shifted(0, 2, 11, zp, fake, fake, 0, fake, fake, 1 << 20, _null()) == E
-    assert lib.lattice_rule_integrate_shifted(0, 2, 11, zp, fake, fake, 70000, fake, fake, 1 << 20, _null()) == E
-    assert lib.lattice_rule_integrate_shifted(0, 2, 5, zp, fake, fake, 2, fake, fake, 1 << 20, _null()) == E  # z >= n
+    assert lib.lattice_rule_integrate_shifted(0, 2, 11, zp, fake, fake, 0, 0, fake, fake, 1 << 20, _null()) == E
+    assert lib.lattice_rule_integrate_shifted(0, 2, 11, zp, fake, fake, 70000, 0, fake, fake, 1 << 20, _null()) == E
+    assert lib.lattice_rule_integrate_shifted(0, 2, 5, zp, fake, fake, 2, 0, fake, fake, 1 << 20, _null()) == E  # z >= n
+    # precision: FP64 or DF64 only, DF64 up to 2^48 points
+    assert lib.lattice_rule_integrate_shifted(0, 2, 11, zp, fake, fake, 2, 1, fake, fake, 1 << 20,
+                                              _null()) == _ffi.MDI_EUNSUPPORTED
     # Korobov search: alpha, d, count, workspace
     assert lib.lattice_korobov_search(3, 4, 101, 1, 10, fake, fake, fake, 1 << 20, _null()) == E
     assert lib.lattice_korobov_search(2, 257, 101, 1, 10, fake, fake, fake, 1 << 20, _null()) == E

@@ -41,6 +41,35 @@ def test_shifted_replicates_match_oracle(fam, d, n, a, R):
         assert abs(got[r] - ref) <= TOL * scale, (r, got[r], ref)
 
 
+@pytest.mark.parametrize("fam", ["exp", "osc", "gauss", "peak"])
+@pytest.mark.parametrize("d,n,a,R", [(1, 1, 1, 2), (3, 1009, 76, 5), (9, 65536, 12345, 3), (40, 20011, 5, 2),
+                                     (3, (1 << 25) + 3, 76543, 2)])
+def test_shifted_df64_matches_oracle(fam, d, n, a, R):
+    # Double-float replicates (the shifted coordinate as a float pair, wrapped by an
+    # exact subtraction of 1); n > 2^24 takes the two-limb coordinate; OSC in FP64.
+    params = inputs.random_product(fam, d, seed=d + R + 1, c_range=(0.2, 0.8) if d >= 40 else (0.5, 2.0))
+    if fam == "osc":
+        params[d] = 0.61
+    z = o.korobov_z(d, a, n)
+    shifts = np.random.default_rng(n + d + 1).uniform(0.0, 1.0, (R, d))
+    got = mdi.lattice_rule_integrate_shifted(fam, dev(params), n, z.astype(np.int64), dev(shifts),
+                                             precision="df64").cpu().numpy()
+    for r in range(R):
+        ref = o.slr_shifted(fam, d, n, z, params[:d], params[d:], shifts[r])
+        scale = max(abs(ref), 1.0) if fam == "osc" else abs(ref)
+        assert abs(got[r] - ref) <= TOL * scale, (r, got[r], ref)
+
+
+@pytest.mark.parametrize("fam", ["exp", "gauss", "peak"])
+def test_zero_shift_df64_is_the_df64_lattice_rule(fam):
+    d, n = 4, 65536
+    params = inputs.random_product(fam, d, seed=3)
+    z = o.korobov_z(d, 12345, n).astype(np.int64)
+    one = mdi.lattice_rule_integrate_shifted(fam, dev(params), n, z, dev(np.zeros((1, d))), precision="df64").item()
+    plain = mdi.lattice_rule_integrate(fam, dev(params), n, z, precision="df64").item()
+    assert abs(one - plain) <= 1e-15 * abs(plain)
+
+
 @pytest.mark.parametrize("fam", ["exp", "osc", "gauss"])
 def test_zero_shift_is_the_lattice_rule_bitwise(fam):
     d, n = 4, 65536
