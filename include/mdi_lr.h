@@ -80,7 +80,12 @@ typedef enum { MDI_STATE_AUTO = 0, MDI_STATE_EXACT = 1, MDI_STATE_CLOSED = 2, MD
  *   MDI_PREC_FP32_EVAL_DF32   phi_j in float; level contractions (interpolation and
  *                             the sum over the cluster) in double-float pairs of
  *                             floats; level states, cross-level products, the final
- *                             sum and coordinates in double.
+ *                             sum and coordinates in double (the batched node
+ *                             state's real families keep their state as float
+ *                             pairs, scaled by a power of two per level).
+ *   In both single-precision-evaluation modes the batched node state's real
+ *   families take phi_j at the float coordinate (q + xi_p)/a, so both modes give
+ *   phi_j the same floats.
  *   MDI_PREC_DF64            FP64-class results without the FP64 pipe, for the
  *                             node state (batched kernel; single integrals, where
  *                             the level-parallel path keeps the products between

@@ -29,15 +29,17 @@
 //   FP64             everything in double;
 //   FP32_EVAL_FP64   phi in float, interpolation and sums in double;
 //   FP32_EVAL_DF32   phi in float, interpolation and the cluster sum in
-//                    double-float, the state in double between levels;
+//                    double-float (the state in double between levels for OSC,
+//                    as float pairs for the real families);
 //   DF64             coordinates, phi, interpolation, sums and the state in
 //                    double-float (no FP64 instruction per cluster point or per
-//                    level); OSC keeps phi in double.  The real families use
-//                    paired cluster points (sweep_paired): by the symmetry of
-//                    the nodes, one pass over a table of sums and differences of
-//                    basis values interpolates the point u of node p and the
-//                    point 1 - u of node P-1-p, lanes are pair-major, and the
-//                    state is kept as sums and differences of mirrored nodes.
+//                    level); OSC keeps phi in double.
+// In every mode the real families use paired cluster points (sweep_paired,
+// sweep_paired_fp64): by the symmetry of the nodes, one pass over a table of sums
+// and differences of basis values interpolates the point u of node p and the
+// point 1 - u of node P-1-p, lanes are pair-major, and the state is kept as sums
+// and differences of mirrored nodes.  The single-precision-evaluation modes take
+// phi at the float coordinate (q + xi_p)/a there, so both give phi the same floats.
 #include <algorithm>
 
 #include "mdi_common.cuh"
@@ -645,7 +647,36 @@ __device__ __forceinline__ void paired_dot(const float4 *__restrict__ Lt, int st
   }
 }
 
-template <int FAM, int H>
+// phi_j at a float coordinate, evaluated in float (the single-precision-evaluation
+// modes of the paired sweeps): the formulas of phi32 with float parameters.
+struct AxisF {
+  float c, w, ic2;
+};
+template <int FAM>
+__device__ __forceinline__ float phi_f(float u, const AxisF &p) {
+  if constexpr (FAM == MDI_FAM_EXP) {
+    return expf(p.c * u);
+  } else if constexpr (FAM == MDI_FAM_GAUSS) {
+    const float t = p.c * (u - p.w);
+    return expf(-t * t);
+  } else {
+    const float t = u - p.w;
+    return 1.0f / fmaf(t, t, p.ic2);
+  }
+}
+// acc += f g for a float f and a double-float g: the exact product of f and g.hi,
+// and f g.lo folded into the low sum.
+__device__ __forceinline__ void dacc_prod_f(DfAcc &a, float f, df32 g) {
+  const float p = __fmul_rn(f, g.hi);
+  const float e = __fmaf_rn(f, g.hi, -p);
+  const df32 t = two_sum(a.s, p);
+  a.s = t.hi;
+  a.c = __fadd_rn(a.c, __fmaf_rn(f, g.lo, __fadd_rn(e, t.lo)));
+}
+
+// PREC: MDI_PREC_DF64 (phi in double-float) or MDI_PREC_FP32_EVAL_DF32 (phi in
+// float at the float coordinate (q + xi_p)/a, the rest as in DF64).
+template <int FAM, int H, int PREC = MDI_PREC_DF64>
 __device__ void sweep_paired(NodesShared &sh, const NodesConsts *__restrict__ kc, const float4 *__restrict__ Lpm,
                              const void *__restrict__ Ftab, int P, int d, int a, int n_last,
                              const double *__restrict__ prm, double *__restrict__ out_slot) {
@@ -656,10 +687,11 @@ __device__ void sweep_paired(NodesShared &sh, const NodesConsts *__restrict__ kc
   const bool act = tid < h * Q;
   const bool warp_act = (tid & ~(kWarp - 1)) < h * Q;
   const int npts_h = a * h;
+  constexpr bool F32 = (PREC == MDI_PREC_FP32_EVAL_DF32);
   if (tid < h) sh.Gdf[0][tid] = make_float4(1.f, 0.f, 0.f, 0.f);  // G_0 = 1: E = 1, O = 0
   if (tid < P) sh.xadf[tid] = kc->xa[a][tid];
   if (tid == 0) sh.iadf = kc->ia[a];
-  load_level_chunk<true>(sh.lc, prm, d, 0);
+  load_level_chunk<!F32>(sh.lc, prm, d, 0);
   __syncthreads();
   const df32 ia{sh.iadf.x, sh.iadf.y};
   const df32 ia2{0.5f * ia.hi, 0.5f * ia.lo};  // 1/(2a), exact halving
@@ -672,13 +704,29 @@ __device__ void sweep_paired(NodesShared &sh, const NodesConsts *__restrict__ kc
   for (int k = 1; k < d; ++k) {
     const int j = k - 1;
     if (j > 0 && j % kLvChunk == 0) {
-      load_level_chunk<true>(sh.lc, prm, d, j);
+      load_level_chunk<!F32>(sh.lc, prm, d, j);
       __syncthreads();
     }
     const LevelConst &L = sh.lc[j % kLvChunk];
     const int rb = (k - 1) & 1, wb = k & 1;
     DfAcc acc_a, acc_b;
-    if (act) {
+    if constexpr (F32) {
+      if (act) {
+        const AxisF af{(float)L.c, (float)L.w, (float)L.ic2};
+        const float iaf = ia.hi, xaf = sh.xadf[pp].x, xbf = sh.xadf[pb].x;
+        for (int q = qs; q < a; q += Q) {
+          df32 ga{1.f, 0.f}, gb{1.f, 0.f};
+          if (k > 1) {
+            DfAcc sp, sm;
+            paired_dot<H>(Lpm + pp * a + q, npts_h, sh.Gdf[rb], h, sp, sm);
+            ga = pair_combine(sp, sm, 1.0f);
+            gb = pair_combine(sp, sm, -1.0f);
+          }
+          dacc_prod_f(acc_a, phi_f<FAM>(fmaf((float)q, iaf, xaf), af), ga);
+          dacc_prod_f(acc_b, phi_f<FAM>(fmaf((float)(a - 1 - q), iaf, xbf), af), gb);
+        }
+      }
+    } else if (act) {
       const df32 xa{sh.xadf[pp].x, sh.xadf[pp].y}, xb{sh.xadf[pb].x, sh.xadf[pb].y};
       df32 s1a, s0a, s1b, s0b;
       phi_affine_coeffs<FAM>(L.cw, ia, xa, s1a, s0a);
@@ -725,20 +773,22 @@ __device__ void sweep_paired(NodesShared &sh, const NodesConsts *__restrict__ kc
     const df32 E{eo.x, eo.y}, O{eo.z, eo.w};
     const df32 v = tid < h ? df_add(E, O) : df_add(E, df_neg(O));
     sh.Gdf[gbuf][tid] = make_float4(v.hi, v.lo, 0.f, 0.f);
+    if constexpr (F32) sh.G[gbuf][tid] = make_double2(df_to_double(v), 0.0);  // its last level reads doubles
   }
   __syncthreads();
-  last_level<FAM, MDI_PREC_DF64>(sh, Ftab, P, d, a, n_last, prm, out_slot, gbuf);
+  last_level<FAM, PREC>(sh, Ftab, P, d, a, n_last, prm, out_slot, gbuf);
   if (tid == 0 && S != 0) *out_slot = scale_pow2(*out_slot, S);  // the thread that wrote it
 }
 
 // The same pairing in FP64 (real families): the state (E_t, O_t) in sh.G as
 // doubles, the paired table as (Lp, Lm) doubles, phi in FP64.  P/2 fused
 // multiply-adds per cluster point instead of P, on the FP64 pipe that bounds
-// this mode.
-template <int FAM, int H>
-__device__ void sweep_paired_fp64(NodesShared &sh, const double2 *__restrict__ Lpm, const void *__restrict__ Ftab,
-                                  int P, int d, int a, int n_last, const double *__restrict__ prm,
-                                  double *__restrict__ out_slot) {
+// this mode.  F32 (MDI_PREC_FP32_EVAL_FP64): phi in float at the float coordinate
+// (q + xi_p)/a, as the paired double-float sweep evaluates it.
+template <int FAM, int H, bool F32 = false>
+__device__ void sweep_paired_fp64(NodesShared &sh, const NodesConsts *__restrict__ kc,
+                                  const double2 *__restrict__ Lpm, const void *__restrict__ Ftab, int P, int d, int a,
+                                  int n_last, const double *__restrict__ prm, double *__restrict__ out_slot) {
   const int h = H > 0 ? H : P / 2;
   const int tid = threadIdx.x, B = blockDim.x;
   const int Q = node_lanes(B, h);
@@ -747,10 +797,12 @@ __device__ void sweep_paired_fp64(NodesShared &sh, const double2 *__restrict__ L
   const bool warp_act = (tid & ~(kWarp - 1)) < h * Q;
   const int npts_h = a * h;
   if (tid < h) sh.G[0][tid] = make_double2(1.0, 0.0);  // G_0 = 1: E = 1, O = 0
+  if (F32 && tid < P) sh.xadf[tid] = kc->xa[a][tid];
   load_level_chunk(sh.lc, prm, d, 0);
   __syncthreads();
   const double inv_a = 1.0 / (double)a, half_inv_a = 0.5 * inv_a;
   const double xa = sh.xi[pp], xb = sh.xi[pb];
+  const float iaf = F32 ? kc->ia[a].x : 0.f, xaf = F32 ? sh.xadf[pp].x : 0.f, xbf = F32 ? sh.xadf[pb].x : 0.f;
 
   for (int k = 1; k < d; ++k) {
     const int j = k - 1;
@@ -786,8 +838,14 @@ __device__ void sweep_paired_fp64(NodesShared &sh, const double2 *__restrict__ L
           ga = sp + sm;
           gb = sp - sm;
         }
-        acc_a = fma(phi<FAM, false>(((double)q + xa) * inv_a, ap), ga, acc_a);
-        acc_b = fma(phi<FAM, false>(((double)(a - 1 - q) + xb) * inv_a, ap), gb, acc_b);
+        if constexpr (F32) {
+          const AxisF af{(float)L.c, (float)L.w, (float)L.ic2};
+          acc_a = fma((double)phi_f<FAM>(fmaf((float)q, iaf, xaf), af), ga, acc_a);
+          acc_b = fma((double)phi_f<FAM>(fmaf((float)(a - 1 - q), iaf, xbf), af), gb, acc_b);
+        } else {
+          acc_a = fma(phi<FAM, false>(((double)q + xa) * inv_a, ap), ga, acc_a);
+          acc_b = fma(phi<FAM, false>(((double)(a - 1 - q) + xb) * inv_a, ap), gb, acc_b);
+        }
       }
     }
     if (warp_act) {
@@ -803,7 +861,27 @@ __device__ void sweep_paired_fp64(NodesShared &sh, const double2 *__restrict__ L
     sh.G[gbuf][tid] = make_double2(tid < h ? eo.x + eo.y : eo.x - eo.y, 0.0);
   }
   __syncthreads();
-  last_level<FAM, MDI_PREC_FP64>(sh, Ftab, P, d, a, n_last, prm, out_slot, gbuf);
+  last_level<FAM, F32 ? MDI_PREC_FP32_EVAL_FP64 : MDI_PREC_FP64>(sh, Ftab, P, d, a, n_last, prm, out_slot, gbuf);
+}
+
+// One integral of a real family on the paired sweep of a single-precision-
+// evaluation mode; H > 0 fixes the number of node pairs at compile time.
+template <int PREC, int H, int FAM>
+__device__ __forceinline__ void paired_one(NodesShared &sh, const NodesConsts *__restrict__ kc, const void *C,
+                                           const void *Ftab, int P, int d, int a, int n_last,
+                                           const double *__restrict__ prm, double *out_slot) {
+  if constexpr (PREC == MDI_PREC_FP32_EVAL_DF32)
+    sweep_paired<FAM, H, PREC>(sh, kc, (const float4 *)C, Ftab, P, d, a, n_last, prm, out_slot);
+  else
+    sweep_paired_fp64<FAM, H, true>(sh, kc, (const double2 *)C, Ftab, P, d, a, n_last, prm, out_slot);
+}
+template <int PREC, int H>
+__device__ __forceinline__ void run_paired(NodesShared &sh, const NodesConsts *__restrict__ kc, const void *C,
+                                           const void *Ftab, int P, int family, int d, int a, int n_last,
+                                           const double *__restrict__ prm, double *out_slot) {
+  if (family == MDI_FAM_EXP) paired_one<PREC, H, MDI_FAM_EXP>(sh, kc, C, Ftab, P, d, a, n_last, prm, out_slot);
+  else if (family == MDI_FAM_GAUSS) paired_one<PREC, H, MDI_FAM_GAUSS>(sh, kc, C, Ftab, P, d, a, n_last, prm, out_slot);
+  else paired_one<PREC, H, MDI_FAM_PEAK>(sh, kc, C, Ftab, P, d, a, n_last, prm, out_slot);
 }
 
 template <int PREC>
@@ -844,10 +922,9 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
       if (threadIdx.x == 0) out[inst] = __longlong_as_double(0x7ff8000000000000ll);  // NaN marks a bad descriptor
       continue;
     }
-    // Basis tables of a: the cluster part (the paired one for real families in
-    // DF64), staged in shared memory when asked and it fits, and the last-axis part.
-    const bool use_paired = (PREC == MDI_PREC_DF64 || PREC == MDI_PREC_FP64) && paired != nullptr &&
-                            ds.family != MDI_FAM_OSC;
+    // Basis tables of a: the cluster part (the paired one for real families),
+    // staged in shared memory when asked and it fits, and the last-axis part.
+    const bool use_paired = paired != nullptr && ds.family != MDI_FAM_OSC;
     const size_t tbytes = (size_t)a * P * P * 8;  // plain cluster part; a multiple of 16 for even P
     const unsigned char *gtab = (const unsigned char *)tables + table_offset(a, P) * 8;
     const void *Ftab = gtab + tbytes;
@@ -868,7 +945,24 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
     const double *prm = pool + ds.param_offset;
     if (use_paired) {
       // P = 16 (the default node count) runs with the pair loop fully unrolled.
-      if constexpr (PREC == MDI_PREC_DF64) {
+      if constexpr (PREC == MDI_PREC_FP64) {
+        // FP64 and DF64 spelled out: this form keeps their instantiations as
+        // they were tuned (the FP64 one free of spills).
+        const double2 *Lpm = (const double2 *)C;
+        if (P == 16) {
+          if (ds.family == MDI_FAM_EXP)
+            sweep_paired_fp64<MDI_FAM_EXP, 8>(sh, nullptr, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+          else if (ds.family == MDI_FAM_GAUSS)
+            sweep_paired_fp64<MDI_FAM_GAUSS, 8>(sh, nullptr, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+          else sweep_paired_fp64<MDI_FAM_PEAK, 8>(sh, nullptr, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+        } else {
+          if (ds.family == MDI_FAM_EXP)
+            sweep_paired_fp64<MDI_FAM_EXP, 0>(sh, nullptr, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+          else if (ds.family == MDI_FAM_GAUSS)
+            sweep_paired_fp64<MDI_FAM_GAUSS, 0>(sh, nullptr, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+          else sweep_paired_fp64<MDI_FAM_PEAK, 0>(sh, nullptr, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+        }
+      } else if constexpr (PREC == MDI_PREC_DF64) {
         const float4 *Lpm = (const float4 *)C;
         if (P == 16) {
           if (ds.family == MDI_FAM_EXP) sweep_paired<MDI_FAM_EXP, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
@@ -881,19 +975,10 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
             sweep_paired<MDI_FAM_GAUSS, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
           else sweep_paired<MDI_FAM_PEAK, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
         }
-      } else if constexpr (PREC == MDI_PREC_FP64) {
-        const double2 *Lpm = (const double2 *)C;
-        if (P == 16) {
-          if (ds.family == MDI_FAM_EXP) sweep_paired_fp64<MDI_FAM_EXP, 8>(sh, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-          else if (ds.family == MDI_FAM_GAUSS)
-            sweep_paired_fp64<MDI_FAM_GAUSS, 8>(sh, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-          else sweep_paired_fp64<MDI_FAM_PEAK, 8>(sh, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-        } else {
-          if (ds.family == MDI_FAM_EXP) sweep_paired_fp64<MDI_FAM_EXP, 0>(sh, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-          else if (ds.family == MDI_FAM_GAUSS)
-            sweep_paired_fp64<MDI_FAM_GAUSS, 0>(sh, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-          else sweep_paired_fp64<MDI_FAM_PEAK, 0>(sh, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-        }
+      } else if (P == 16) {
+        run_paired<PREC, 8>(sh, kc, C, Ftab, P, ds.family, ds.d, a, ds.n_last, prm, out + inst);
+      } else {
+        run_paired<PREC, 0>(sh, kc, C, Ftab, P, ds.family, ds.d, a, ds.n_last, prm, out + inst);
       }
       continue;
     }
@@ -958,16 +1043,16 @@ static bool df_tables(const NodesConfig &c) {
 
 static size_t counter_bytes() { return align_up(4 * sizeof(unsigned)); }
 
-// Tag stamped by the preparation: node count and table format.
-static bool paired_tables(const NodesConfig &c) {
-  return c.precision == MDI_PREC_DF64 || c.precision == MDI_PREC_FP64;
-}
+// Every precision pairs the real families' cluster points (float-pair entries in
+// the double-float modes, doubles otherwise).
+static bool paired_tables(const NodesConfig &) { return true; }
 
+// Tag stamped by the preparation: node count and table format.
 static unsigned nodes_tag(const NodesConfig &c) {
   return 0x4D440000u | ((unsigned)c.P << 4) | (df_tables(c) ? 1u : 0u) | (paired_tables(c) ? 2u : 0u);
 }
 
-// Workspace: queue counters | basis tables | paired tables (DF64) | NodesConsts.
+// Workspace: queue counters | basis tables | paired tables | NodesConsts.
 static size_t consts_offset(const NodesConfig &cfg) {
   return counter_bytes() + align_up(table_bytes(cfg.P)) + (paired_tables(cfg) ? align_up(paired_bytes(cfg.P)) : 0);
 }
@@ -994,7 +1079,7 @@ mdi_status nodes_prepare(const NodesConfig &cfg, void *workspace, size_t ws_byte
   if (st != MDI_OK) return st;
   if (paired_tables(cfg)) {
     float4 *paired = (float4 *)((char *)tables + align_up(table_bytes(cfg.P)));
-    if (cfg.precision == MDI_PREC_DF64) nodes_paired_table_kernel<true><<<table_grid, 256, 0, stream>>>(cfg.P, paired);
+    if (df_tables(cfg)) nodes_paired_table_kernel<true><<<table_grid, 256, 0, stream>>>(cfg.P, paired);
     else nodes_paired_table_kernel<false><<<table_grid, 256, 0, stream>>>(cfg.P, paired);
     if ((st = check_launch()) != MDI_OK) return st;
   }

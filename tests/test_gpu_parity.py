@@ -295,8 +295,30 @@ def test_batched_full_size_sampled():
         close(out1[i], o.mdi_nodes(it.family, it.d, it.a, it.n_last, 16, it.c, it.w), it.family)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "df64"])
-def test_batched_mixed_families_and_edges(prec):
+@pytest.mark.parametrize("prec", ["fp32_eval_fp64", "fp32_eval_df32"])
+def test_batched_single_precision_evaluation_modes(prec):
+    # The paired sweeps evaluate phi in float at the float coordinate (q + xi_p)/a:
+    # each factor carries a few 1e-7 relative, d <= 20 factors per product.
+    b = inputs.batch(count=193, seed=5)
+    _, d_descs, d_order, pool = _batch_to_device(b)
+    out = mdi.mdi_lr_integrate_batched(d_descs, pool, len(b), order=d_order, precision=prec).cpu().numpy()
+    for i in range(len(b)):
+        it = b.integral(i)
+        close(out[i], o.mdi_nodes(it.family, it.d, it.a, it.n_last, 16, it.c, it.w), it.family, tol=2e-5)
+
+
+def test_batched_single_precision_evaluation_modes_agree():
+    # Both modes give phi the same floats; the double-float contractions must
+    # reproduce the FP64 ones to double-float accuracy on the whole batch.
+    b = inputs.batch(count=1024, seed=9)
+    _, d_descs, d_order, pool = _batch_to_device(b)
+    ref = mdi.mdi_lr_integrate_batched(d_descs, pool, len(b), order=d_order, precision="fp32_eval_fp64").cpu().numpy()
+    got = mdi.mdi_lr_integrate_batched(d_descs, pool, len(b), order=d_order, precision="fp32_eval_df32").cpu().numpy()
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL), ("df64", TOL), ("fp32_eval_fp64", 1e-4), ("fp32_eval_df32", 1e-4)])
+def test_batched_mixed_families_and_edges(prec, tol):
     # d = 1, a = 1, a = 64, n_last = 4096 and n_last != a (the untabulated last
     # axis), d = 130 (three chunks of level constants), every family.
     fams = ["exp", "osc", "gauss", "peak", "gauss", "exp", "peak", "osc"]
@@ -313,10 +335,11 @@ def test_batched_mixed_families_and_edges(prec):
                                        precision=prec).cpu()
     for i, f in enumerate(fams):
         p = pool[offs[i]:offs[i] + 2 * ds[i]]
-        close(out[i].item(), o.mdi_nodes(f, ds[i], as_[i], nls[i], 16, p[:ds[i]], p[ds[i]:]), f)
+        close(out[i].item(), o.mdi_nodes(f, ds[i], as_[i], nls[i], 16, p[:ds[i]], p[ds[i]:]), f, tol=tol)
 
 
-@pytest.mark.parametrize("prec,tol", [("df64", 1e-12), ("fp32_eval_df32", 1e-4), ("fp64", 1e-12)])
+@pytest.mark.parametrize("prec,tol", [("df64", 1e-12), ("fp32_eval_df32", 1e-4), ("fp32_eval_fp64", 1e-4),
+                                      ("fp64", 1e-12)])
 def test_batched_values_beyond_the_float_range(prec, tol):
     # d = 300: the exponential integral grows to ~1e90 and the Gaussian and peak
     # ones shrink below 1e-38, outside what a float pair holds; the double-float
