@@ -24,8 +24,11 @@
 // beta) (CBC component s) for r <= n/2 is formed once, as a float pair, and every
 // term becomes one table lookup and a double-float multiply on the FP32 pipe,
 // accumulated with Dot2-style compensated sums; the running CBC products are
-// float pairs too.  Korobov searches with larger n (or d > 16) use the direct FP64
-// kernel; CBC is limited to n <= 2^24 (its work grows as d n^2 / 4).
+// float pairs too.  In these kernels thread t of B takes k = 1 + t, 1 + t + B, ...
+// (residues stepped by B z_j mod n in 32 bits), so that a warp's loads of the
+// first factor (z_1 = 1) and of p(k) fall on neighbouring entries.  Korobov
+// searches with larger n (or d > 16) use the direct FP64 kernel; CBC is limited
+// to n <= 2^24 (its work grows as d n^2 / 4).
 #include <algorithm>
 #include <cmath>
 
@@ -251,31 +254,44 @@ __global__ void __launch_bounds__(kSearchThreads) korobov_table_criterion_kernel
       __syncthreads();
       continue;
     }
-    uint64_t k0, k1;
-    thread_run(h, threadIdx.x, blockDim.x, k0, k1);
-    k0 += 1;
-    k1 += 1;
-    uint64_t r[MAXD];
+    // Thread t takes k = 1 + t, 1 + t + B, ... (B threads): the lanes of a warp read
+    // neighbouring entries for the first factor (z_1 = 1).  n <= 2^24 here, so
+    // residues, steps and folds fit 32 bits (r + step < 2^25).
+    const uint32_t n32 = (uint32_t)n, B = blockDim.x, h32 = (uint32_t)h;
+    uint32_t r[MAXD], step[MAXD];
 #pragma unroll(kUnroll)
     for (int j = 0; j < MAXD; ++j)
-      if (j < d) r[j] = (k0 < k1) ? (k0 * s_z[j]) % n : 0;  // k < 2^23, z < 2^24
-    DfAcc acc;
-    for (uint64_t k = k0; k < k1; ++k) {
-      const float2 f0 = T[fold(r[0], n)];
+      if (j < d) {
+        r[j] = (uint32_t)(((uint64_t)(1 + threadIdx.x) * s_z[j]) % n);
+        step[j] = (uint32_t)(((uint64_t)B * s_z[j]) % n);
+      }
+    // The term of one k: the product of its d factors; steps the residues to k + B.
+    auto term = [&]() -> df32 {
+      const float2 f0 = T[r[0] <= n32 - r[0] ? r[0] : n32 - r[0]];
       df32 prod{f0.x, f0.y};
-      r[0] += s_z[0];
-      if (r[0] >= n) r[0] -= n;
+      r[0] += step[0];
+      if (r[0] >= n32) r[0] -= n32;
 #pragma unroll(kUnroll)
       for (int j = 1; j < MAXD; ++j) {
         if (j < d) {
-          const float2 f = T[fold(r[j], n)];
+          const float2 f = T[r[j] <= n32 - r[j] ? r[j] : n32 - r[j]];
           prod = df_mul(prod, df32{f.x, f.y});
-          r[j] += s_z[j];
-          if (r[j] >= n) r[j] -= n;
+          r[j] += step[j];
+          if (r[j] >= n32) r[j] -= n32;
         }
       }
-      dacc_add(acc, prod);
+      return prod;
+    };
+    DfAcc acc;
+    uint32_t k = 1 + threadIdx.x;
+    // Two terms per pass (twice the lookups in flight), added in the order of k.
+    for (; k + B <= h32; k += 2 * B) {
+      const df32 pa = term();
+      const df32 pb = term();
+      dacc_add(acc, pa);
+      dacc_add(acc, pb);
     }
+    if (k <= h32) dacc_add(acc, term());
     const df32 tot = block_sum_df32(dacc_value(acc), s_red);
     if (threadIdx.x == 0) {
       double p0 = 1.0, pm = 1.0;
@@ -321,17 +337,30 @@ __global__ void __launch_bounds__(kSearchThreads) cbc_df_candidates_kernel(int s
       if (threadIdx.x == 0) vals[t] = INFINITY;
       continue;
     }
-    uint64_t k0, k1;
-    thread_run(h, threadIdx.x, blockDim.x, k0, k1);
-    k0 += 1;
-    k1 += 1;
-    uint64_t r = (k0 < k1) ? (k0 * z) % n : 0;
+    // Thread t takes k = 1 + t, 1 + t + B, ... (B threads): the lanes of a warp read
+    // neighbouring p[k].  n <= 2^24 here, so the residue, its step and fold fit
+    // 32 bits (r + step < 2^25).
+    const uint32_t n32 = (uint32_t)n, B = blockDim.x, h32 = (uint32_t)h;
+    const uint32_t step = (uint32_t)(((uint64_t)B * z) % n);
+    uint32_t r = (uint32_t)(((uint64_t)(1 + threadIdx.x) * z) % n);
+    auto factor = [&]() -> float2 {
+      const float2 f = T[r <= n32 - r ? r : n32 - r];
+      r += step;
+      if (r >= n32) r -= n32;
+      return f;
+    };
     DfAcc acc;
-    for (uint64_t k = k0; k < k1; ++k) {
-      const float2 pk = p[k], f = T[fold(r, n)];
+    uint32_t k = 1 + threadIdx.x;
+    // Two terms per pass (twice the lookups in flight), accumulated in the order of k.
+    for (; k + B <= h32; k += 2 * B) {
+      const float2 f0 = factor(), f1 = factor();
+      const float2 p0 = p[k], p1 = p[k + B];
+      dacc_prod(acc, df32{p0.x, p0.y}, df32{f0.x, f0.y});
+      dacc_prod(acc, df32{p1.x, p1.y}, df32{f1.x, f1.y});
+    }
+    if (k <= h32) {
+      const float2 pk = p[k], f = factor();
       dacc_prod(acc, df32{pk.x, pk.y}, df32{f.x, f.y});
-      r += z;
-      if (r >= n) r -= n;
     }
     const df32 tot = block_sum_df32(dacc_value(acc), s_red);
     if (threadIdx.x == 0) {

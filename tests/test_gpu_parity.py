@@ -248,6 +248,23 @@ def test_nodes_precision_modes(prec, tol, fam):
     close(got, o.mdi_nodes(fam, 50, 32, 32, 16, params[:50], params[50:]), fam, tol=tol)
 
 
+@pytest.mark.parametrize("fam", ["gauss", "peak", "exp"])
+@pytest.mark.parametrize("d,a,nd,P", [(4, 16, 16, 16), (2, 1, 5, 16), (6, 32, 13, 32), (5, 64, 64, 16),
+                                      (7, 3, 100, 4), (6, 24, 24, 12)])
+def test_nodes_single_precision_evaluation_paired(fam, d, a, nd, P):
+    # d < 8: one integral on the batched kernel's paired sweeps (P = 16 unrolled,
+    # other P generic; nd != a takes the untabulated last axis).  Both modes give
+    # phi the same floats, so they agree to double-float accuracy.
+    params = inputs.random_product(fam, d, seed=3 * d + a)
+    p = dev(params)
+    ref = o.mdi_nodes(fam, d, a, nd, P, params[:d], params[d:])
+    f64 = mdi.mdi_lr_integrate(fam, p, d, a, nd, state="nodes", nodes=P, precision="fp32_eval_fp64").item()
+    dfs = mdi.mdi_lr_integrate(fam, p, d, a, nd, state="nodes", nodes=P, precision="fp32_eval_df32").item()
+    close(f64, ref, fam, tol=2e-5)
+    close(dfs, ref, fam, tol=2e-5)
+    close(dfs, f64, fam, tol=1e-12)
+
+
 @pytest.mark.parametrize("fam", ["gauss", "peak", "osc", "exp"])
 @pytest.mark.parametrize("d,a", [(50, 32), (8, 16), (200, 20)])
 def test_nodes_compensated_accumulation(fam, d, a):
