@@ -515,12 +515,16 @@ def extra_improved_rule(torch, mdi):
     nstar = mdi.lattice_rule_integrate_improved("exp", p, d, n, a, out=out, workspace=ws)[1]
     v, ms = event_ms(torch, lambda: mdi.lattice_rule_integrate_improved("exp", p, d, n, a, out=out, workspace=ws)[0],
                      reps=3)
+    vd, ms_d = event_ms(torch, lambda: mdi.lattice_rule_integrate_improved("exp", p, d, n, a, precision="df64",
+                                                                             out=out, workspace=ws)[0], reps=3)
     z = mdi.korobov_vector(d, a, n).astype(np.int64)
     vp, ms_p = event_ms(torch, lambda: mdi.lattice_rule_integrate("exp", p, n, z), reps=3)
+    vpd, ms_pd = event_ms(torch, lambda: mdi.lattice_rule_integrate("exp", p, n, z, precision="df64"), reps=3)
     return {"workload": f"d={d}, z=(1,{a},..,{a}^{d - 1}), n=1+{a}^{d}={n}, f=exp(sum x_j/j)",
             "n_ghost": nstar, "improved_ms": ms, "improved_points_per_s": (n + nstar) / (ms * 1e-3),
             "improved_rel_err": abs(v.item() - exact) / exact,
-            "plain_ms": ms_p, "plain_rel_err": abs(vp.item() - exact) / exact}
+            "improved_df64_ms": ms_d, "improved_df64_vs_fp64": abs(vd.item() - v.item()) / abs(v.item()),
+            "plain_ms": ms_p, "plain_rel_err": abs(vp.item() - exact) / exact, "plain_df64_ms": ms_pd}
 
 
 def extra_batch_size_sweep(torch, mdi, inputs, counts=(4096, 16384, 65536)):

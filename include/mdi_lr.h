@@ -201,16 +201,19 @@ mdi_status lattice_rule_shifted_workspace_size(int32_t d, int64_t n, int32_t R, 
  *   d        1..64;  a >= 1 with a^(d-1) * ceil(n / a^(d-1)) < 2^62
  *   n        1 <= n < 2^62; gcd(a, n) = 1 unless a^(d-1) divides n
  *   params   DEVICE, the family's parameters as lattice_rule_integrate
+ *   precision  mdi_precision of the n lattice points, as lattice_rule_integrate
+ *            (MDI_PREC_DF64: n <= 2^48); the n* ghosts are evaluated in FP64
  *   out      DEVICE, 1 double
  *   n_ghost  HOST, optional (may be NULL): receives n*
- * FP64.  Three launches on `stream` (lattice points, ghosts, ordered sum).
+ * Three launches on `stream` (lattice points, ghosts, ordered sum).
  * MDI_EINVAL for bad sizes or a common factor of a and n with ghosts present;
+ * MDI_EUNSUPPORTED for a precision the lattice points cannot take;
  * MDI_EWORKSPACE for a missing, misaligned or short workspace
  * (lattice_rule_improved_workspace_size).
  * ------------------------------------------------------------------------- */
 mdi_status lattice_rule_integrate_improved(int32_t family, int32_t d, int64_t n, int64_t a, const double *params,
-                                           double *out, int64_t *n_ghost, void *workspace, size_t ws_bytes,
-                                           mdi_stream_t stream);
+                                           int32_t precision, double *out, int64_t *n_ghost, void *workspace,
+                                           size_t ws_bytes, mdi_stream_t stream);
 mdi_status lattice_rule_improved_workspace_size(int32_t d, int64_t n, int64_t a, size_t *bytes);
 
 /* ---------------------------------------------------------------------------

@@ -152,13 +152,14 @@ def lattice_rule_improved_workspace_size(d: int, n: int, a: int) -> int:
     return b.value
 
 
-def lattice_rule_integrate_improved(family, params: torch.Tensor, d: int, n: int, a: int,
+def lattice_rule_integrate_improved(family, params: torch.Tensor, d: int, n: int, a: int, precision="fp64",
                                     out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
                                     stream=None):
     """Improved lattice rule (Definition 3.3) on the Korobov lattice z = (1, a, ..)
     for general n: the n lattice points plus the n* points completing the
-    transformed tensor grid, weight 1/(n + n*).  Returns (1-element float64 CUDA
-    tensor, n*)."""
+    transformed tensor grid, weight 1/(n + n*).  ``precision`` applies to the
+    lattice points ("fp64", "fp32_eval_fp64" or "df64"; the ghosts are FP64).
+    Returns (1-element float64 CUDA tensor, n*)."""
     _dev_f64(params, "params")
     if params.numel() < 2 * d:
         raise ValueError("params must hold 2*d doubles")
@@ -167,7 +168,7 @@ def lattice_rule_integrate_improved(family, params: torch.Tensor, d: int, n: int
     ws = _workspace(lattice_rule_improved_workspace_size(d, n, a), params.device, workspace)
     ng = ctypes.c_int64()
     st = _ffi.load().lattice_rule_integrate_improved(_fam(family), d, int(n), int(a),
-                                                     ctypes.c_void_p(params.data_ptr()),
+                                                     ctypes.c_void_p(params.data_ptr()), _prec(precision),
                                                      ctypes.c_void_p(out.data_ptr()), ctypes.byref(ng),
                                                      ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
     _ffi.check(st, "lattice_rule_integrate_improved")

@@ -38,7 +38,7 @@ SIGNATURES = {
     "lattice_rule_integrate_noalloc": (_I32, [_I32, _I32, _I64, _P, _P, _I32, _P, _P]),
     "lattice_rule_integrate_shifted": (_I32, [_I32, _I32, _I64, _P, _P, _P, _I32, _I32, _P, _P, _SZ, _P]),
     "lattice_rule_shifted_workspace_size": (_I32, [_I32, _I64, _I32, _c.POINTER(_SZ)]),
-    "lattice_rule_integrate_improved": (_I32, [_I32, _I32, _I64, _I64, _P, _P, _c.POINTER(_I64), _P, _SZ, _P]),
+    "lattice_rule_integrate_improved": (_I32, [_I32, _I32, _I64, _I64, _P, _I32, _P, _c.POINTER(_I64), _P, _SZ, _P]),
     "lattice_rule_improved_workspace_size": (_I32, [_I32, _I64, _I64, _c.POINTER(_SZ)]),
     "mdi_lr_integrate": (_I32, [_I32, _I32, _I64, _I64, _P, _c.POINTER(MdiOpts), _P, _P, _SZ, _P]),
     "mdi_lr_workspace_size": (_I32, [_I32, _I32, _I64, _I64, _c.POINTER(MdiOpts), _c.POINTER(_SZ)]),

@@ -19,6 +19,7 @@ computes: every launch goes through the C ABI.
                   n = 2^24, Korobov a = 12345
   improved-d7     improved lattice rule, d = 7, z = (1, 16, .., 16^6), n = 1 + 16^7
                   (16^6 - 1 ghosts), f = exp(sum x_j / j)
+  improved-d7-df64  the same with the lattice points in double-float
 """
 from __future__ import annotations
 
@@ -74,13 +75,15 @@ def build_case(name: str):
         p = torch.as_tensor(inputs.small_exp(7).params).cuda()
         z = mdi.korobov_vector(7, 12345, 1 << 24)
         return lambda: mdi.lattice_rule_integrate("exp", p, 1 << 24, z, precision="df64")
-    if name == "improved-d7":
+    if name in ("improved-d7", "improved-d7-df64"):
         d, a = 7, 16
+        prec = "df64" if name.endswith("df64") else "fp64"
         p = torch.as_tensor(np.r_[1.0 / np.arange(1, d + 1), np.zeros(d)]).cuda()
         ws = torch.empty(mdi.lattice_rule_improved_workspace_size(d, 1 + a ** d, a), dtype=torch.uint8,
                          device="cuda")
         out = torch.empty(1, dtype=torch.float64, device="cuda")
-        return lambda: mdi.lattice_rule_integrate_improved("exp", p, d, 1 + a ** d, a, out=out, workspace=ws)
+        return lambda: mdi.lattice_rule_integrate_improved("exp", p, d, 1 + a ** d, a, precision=prec, out=out,
+                                                           workspace=ws)
     raise SystemExit(f"unknown case {name!r}; see the module docstring")
 
 

@@ -135,11 +135,12 @@ mdi_status lattice_rule_improved_workspace_size(int32_t d, int64_t n, int64_t a,
 }
 
 mdi_status lattice_rule_integrate_improved(int32_t family, int32_t d, int64_t n, int64_t a, const double *params,
-                                           double *out, int64_t *n_ghost, void *workspace, size_t ws_bytes,
-                                           mdi_stream_t stream) {
+                                           int32_t precision, double *out, int64_t *n_ghost, void *workspace,
+                                           size_t ws_bytes, mdi_stream_t stream) {
   NvtxRange nvtx_scope("lattice_rule_integrate_improved");
   if (!family_ok(family)) return MDI_EINVAL;
-  return slr_improved_launch(family, d, n, a, params, out, n_ghost, workspace, ws_bytes, (cudaStream_t)stream);
+  return slr_improved_launch(family, d, n, a, params, precision, out, n_ghost, workspace, ws_bytes,
+                             (cudaStream_t)stream);
 }
 
 mdi_status lattice_rule_integrate_noalloc(int32_t family, int32_t d, int64_t n, const int64_t *z, const double *params,

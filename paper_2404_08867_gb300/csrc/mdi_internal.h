@@ -31,8 +31,8 @@ mdi_status closed_launch(int family, int d, int64_t a, int64_t n_last, const dou
 // slr.cu: randomly shifted lattice rule, R replicates
 size_t slr_shifted_workspace_bytes(int d, int64_t n, int R);  // 0 when out of range
 size_t slr_improved_workspace_bytes(int d, int64_t n, int64_t a);  // 0 when out of range
-mdi_status slr_improved_launch(int family, int d, int64_t n, int64_t a, const double *params, double *out,
-                               int64_t *n_ghost, void *workspace, size_t ws_bytes, cudaStream_t stream);
+mdi_status slr_improved_launch(int family, int d, int64_t n, int64_t a, const double *params, int precision,
+                               double *out, int64_t *n_ghost, void *workspace, size_t ws_bytes, cudaStream_t stream);
 mdi_status slr_shifted_launch(int family, int d, int64_t n, const int64_t *z, const double *params,
                               const double *shifts, int R, int precision, double *out, void *workspace,
                               size_t ws_bytes, cudaStream_t stream);

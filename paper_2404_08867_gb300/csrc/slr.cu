@@ -750,12 +750,13 @@ static void launch_ghost_d(int grid, const GhostArgs &g, const double *params, d
   else launch_ghost<FAM, kGhostMaxD>(grid, g, params, partials, s);
 }
 
-mdi_status slr_improved_launch(int family, int d, int64_t n, int64_t a, const double *params, double *out,
-                               int64_t *n_ghost, void *workspace, size_t ws_bytes, cudaStream_t stream) {
+mdi_status slr_improved_launch(int family, int d, int64_t n, int64_t a, const double *params, int precision,
+                               double *out, int64_t *n_ghost, void *workspace, size_t ws_bytes, cudaStream_t stream) {
   if (!params || !out) return MDI_EINVAL;
   if (family < MDI_FAM_EXP || family > MDI_FAM_PEAK) return MDI_EINVAL;
   ImprovedPlan pl{};
   if (!improved_plan(d, n, a, pl)) return MDI_EINVAL;
+  if (slr_precision_ok(precision, n) != MDI_OK) return MDI_EUNSUPPORTED;
   if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < slr_improved_workspace_bytes(d, n, a))
     return MDI_EWORKSPACE;
   SlrArgs args{};
@@ -768,12 +769,8 @@ mdi_status slr_improved_launch(int family, int d, int64_t n, int64_t a, const do
     zi = (uint64_t)(((unsigned __int128)zi * (uint64_t)a) % (uint64_t)n);
   }
   double *partials = (double *)workspace;
-  switch (family) {
-    case MDI_FAM_EXP: launch_slr_d<MDI_FAM_EXP, false>(pl.grid_lattice, args, params, partials, stream); break;
-    case MDI_FAM_OSC: launch_slr_d<MDI_FAM_OSC, false>(pl.grid_lattice, args, params, partials, stream); break;
-    case MDI_FAM_GAUSS: launch_slr_d<MDI_FAM_GAUSS, false>(pl.grid_lattice, args, params, partials, stream); break;
-    default: launch_slr_d<MDI_FAM_PEAK, false>(pl.grid_lattice, args, params, partials, stream); break;
-  }
+  // The lattice points in the requested arithmetic; the ghosts below in FP64.
+  launch_slr_points(family, precision, pl.grid_lattice, args, params, partials, stream);
   mdi_status st = check_launch();
   if (st != MDI_OK) return st;
   if (pl.grid_ghost > 0) {

@@ -172,19 +172,24 @@ def test_improved_rule_and_df64_modes_validate_before_launching(lib):
     b = ctypes.c_size_t()
     ng = ctypes.c_int64(-1)
     # improved rule: family, d range, n < 1, a^(d-1) beyond 2^62, gcd(a, n) > 1 with ghosts
-    assert lib.lattice_rule_integrate_improved(7, 3, 100, 7, fake, fake, ctypes.byref(ng), fake, 1 << 20, _null()) == E
-    assert lib.lattice_rule_integrate_improved(0, 0, 100, 7, fake, fake, None, fake, 1 << 20, _null()) == E
-    assert lib.lattice_rule_integrate_improved(0, 65, 100, 2, fake, fake, None, fake, 1 << 20, _null()) == E
-    assert lib.lattice_rule_integrate_improved(0, 3, 0, 7, fake, fake, None, fake, 1 << 20, _null()) == E
-    assert lib.lattice_rule_integrate_improved(0, 41, 1000, 3, fake, fake, None, fake, 1 << 20, _null()) == E
-    assert lib.lattice_rule_integrate_improved(0, 3, 150, 10, fake, fake, None, fake, 1 << 20, _null()) == E
-    assert lib.lattice_rule_integrate_improved(0, 3, 100, 7, _null(), fake, None, fake, 1 << 20, _null()) == E
+    assert lib.lattice_rule_integrate_improved(7, 3, 100, 7, fake, 0, fake, ctypes.byref(ng), fake, 1 << 20, _null()) == E
+    assert lib.lattice_rule_integrate_improved(0, 0, 100, 7, fake, 0, fake, None, fake, 1 << 20, _null()) == E
+    assert lib.lattice_rule_integrate_improved(0, 65, 100, 2, fake, 0, fake, None, fake, 1 << 20, _null()) == E
+    assert lib.lattice_rule_integrate_improved(0, 3, 0, 7, fake, 0, fake, None, fake, 1 << 20, _null()) == E
+    assert lib.lattice_rule_integrate_improved(0, 41, 1000, 3, fake, 0, fake, None, fake, 1 << 20, _null()) == E
+    assert lib.lattice_rule_integrate_improved(0, 3, 150, 10, fake, 0, fake, None, fake, 1 << 20, _null()) == E
+    assert lib.lattice_rule_integrate_improved(0, 3, 100, 7, _null(), 0, fake, None, fake, 1 << 20, _null()) == E
     assert ng.value == -1  # nothing written on refusal
     # workspace: missing, misaligned, short
-    assert lib.lattice_rule_integrate_improved(0, 3, 100, 7, fake, fake, None, _null(), 1 << 20, _null()) == W
-    assert lib.lattice_rule_integrate_improved(0, 3, 100, 7, fake, fake, None, ctypes.c_void_p(0x1008), 1 << 20,
+    assert lib.lattice_rule_integrate_improved(0, 3, 100, 7, fake, 0, fake, None, _null(), 1 << 20, _null()) == W
+    assert lib.lattice_rule_integrate_improved(0, 3, 100, 7, fake, 0, fake, None, ctypes.c_void_p(0x1008), 1 << 20,
                                                _null()) == W
-    assert lib.lattice_rule_integrate_improved(0, 3, 100, 7, fake, fake, None, fake, 8, _null()) == W
+    assert lib.lattice_rule_integrate_improved(0, 3, 100, 7, fake, 0, fake, None, fake, 8, _null()) == W
+    # precision of the lattice points: the compensated single-precision mode has no
+    # lattice kernel; double-float coordinates hold n <= 2^48
+    assert lib.lattice_rule_integrate_improved(0, 3, 100, 7, fake, 2, fake, None, fake, 1 << 20, _null()) == U
+    assert lib.lattice_rule_integrate_improved(0, 2, (1 << 49) + 2, 3, fake, 3, fake, None, fake, 1 << 20,
+                                               _null()) == U
     assert lib.lattice_rule_improved_workspace_size(3, 150, 10, ctypes.byref(b)) == E
     assert lib.lattice_rule_improved_workspace_size(3, 100, 10, ctypes.byref(b)) == _ffi.MDI_OK  # 10^2 | 100: no ghosts
     # double-float plain rule beyond 2^48 points

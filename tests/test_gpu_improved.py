@@ -37,20 +37,27 @@ def params(fam, d, seed):
     return c, w
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL), ("df64", TOL), ("fp32_eval_fp64", 2e-5)])
 @pytest.mark.parametrize("fam", ["exp", "osc", "gauss", "peak"])
 @pytest.mark.parametrize("d,n,a", [(2, 81, 7), (3, 161, 4), (1, 1000, 7), (4, 2003, 6), (3, 4 * 49, 7),
                                    (6, 100003, 7), (9, 65537, 3), (2, 97, 96), (12, 30011, 2), (40, 20011, 1)])
-def test_parity(fam, d, n, a):
+def test_parity(fam, d, n, a, precision, tol):
+    # precision applies to the n lattice points (double-float: the FP64 class of
+    # the oracle; float evaluation: a few 1e-7 per factor); the ghosts are FP64.
     c, w = params(fam, d, seed=d * 7919 + n)
     ref, ns_ref = o.improved_rule(fam, d, n, a, c, w)
-    got, ns = mdi.lattice_rule_integrate_improved(fam, dev(np.r_[c, w]), d, n, a)
+    got, ns = mdi.lattice_rule_integrate_improved(fam, dev(np.r_[c, w]), d, n, a, precision=precision)
     assert ns == ns_ref
-    err = abs(got.item() - ref) / abs(ref)
-    assert err <= TOL, (fam, d, n, a, got.item(), ref, err)
+    # |f| <= 1 for OSC: a float evaluation's error is absolute there
+    scale = 1.0 if (fam == "osc" and precision == "fp32_eval_fp64") else abs(ref)
+    err = abs(got.item() - ref) / scale
+    assert err <= tol, (fam, d, n, a, got.item(), ref, err)
 
 
-def test_ghosts_beyond_lattice_at_large_n():
-    # n = 1 + 16^6 on z = (1, 16, .., 16^6): n* = 16^6 - 1 ghosts (one per line);
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_ghosts_beyond_lattice_at_large_n(precision):
+    # n = 1 + 16^7 on z = (1, 16, .., 16^6): n* = 16^6 - 1 ghosts (one per line);
+    # in double-float the 2.7e8 lattice coordinates take two 24-bit limbs;
     # f = exp(c x_d) has the closed form (e^{cN/n} - 1) / (N (e^{c/n} - 1)) over the
     # completed last coordinates r/n, r < N.
     d, a = 7, 16
@@ -60,7 +67,7 @@ def test_ghosts_beyond_lattice_at_large_n():
     cd = 0.9
     c = np.zeros(d)
     c[-1] = cd
-    got, ns = mdi.lattice_rule_integrate_improved("exp", dev(np.r_[c, np.zeros(d)]), d, n, a)
+    got, ns = mdi.lattice_rule_integrate_improved("exp", dev(np.r_[c, np.zeros(d)]), d, n, a, precision=precision)
     assert ns == N - n == M - 1
     expect = math.expm1(cd * N / n) / (N * math.expm1(cd / n))
     assert abs(got.item() - expect) <= 1e-12 * expect
@@ -100,6 +107,6 @@ def test_rejected(d, n, a):
     p = dev(np.ones(2 * d))
     out = torch.empty(1, dtype=torch.float64, device="cuda")
     ws = torch.empty(1 << 16, dtype=torch.uint8, device="cuda")
-    st = _ffi.load().lattice_rule_integrate_improved(1, d, n, a, p.data_ptr(), out.data_ptr(), None,
+    st = _ffi.load().lattice_rule_integrate_improved(1, d, n, a, p.data_ptr(), 0, out.data_ptr(), None,
                                                      ws.data_ptr(), ws.numel(), None)
     assert st == _ffi.MDI_EINVAL
