@@ -351,14 +351,16 @@ __global__ void __launch_bounds__(kSearchThreads) cbc_df_candidates_kernel(int s
     };
     DfAcc acc;
     uint32_t k = 1 + threadIdx.x;
-    // Two terms per pass (twice the lookups in flight), accumulated in the order of k.
-    for (; k + B <= h32; k += 2 * B) {
-      const float2 f0 = factor(), f1 = factor();
-      const float2 p0 = p[k], p1 = p[k + B];
+    // Four terms per pass (four lookups in flight), accumulated in the order of k.
+    for (; k + 3 * B <= h32; k += 4 * B) {
+      const float2 f0 = factor(), f1 = factor(), f2 = factor(), f3 = factor();
+      const float2 p0 = p[k], p1 = p[k + B], p2 = p[k + 2 * B], p3 = p[k + 3 * B];
       dacc_prod(acc, df32{p0.x, p0.y}, df32{f0.x, f0.y});
       dacc_prod(acc, df32{p1.x, p1.y}, df32{f1.x, f1.y});
+      dacc_prod(acc, df32{p2.x, p2.y}, df32{f2.x, f2.y});
+      dacc_prod(acc, df32{p3.x, p3.y}, df32{f3.x, f3.y});
     }
-    if (k <= h32) {
+    for (; k <= h32; k += B) {
       const float2 pk = p[k], f = factor();
       dacc_prod(acc, df32{pk.x, pk.y}, df32{f.x, f.y});
     }
