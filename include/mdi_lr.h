@@ -201,8 +201,9 @@ mdi_status lattice_rule_shifted_workspace_size(int32_t d, int64_t n, int32_t R, 
  *   d        1..64;  a >= 1 with a^(d-1) * ceil(n / a^(d-1)) < 2^62
  *   n        1 <= n < 2^62; gcd(a, n) = 1 unless a^(d-1) divides n
  *   params   DEVICE, the family's parameters as lattice_rule_integrate
- *   precision  mdi_precision of the n lattice points, as lattice_rule_integrate
- *            (MDI_PREC_DF64: n <= 2^48); the n* ghosts are evaluated in FP64
+ *   precision  mdi_precision, as lattice_rule_integrate (MDI_PREC_DF64: n <= 2^48);
+ *            the n* ghosts take DF64 too when n + n* <= 2^48 and a <= 2^24 (real
+ *            families), FP64 otherwise
  *   out      DEVICE, 1 double
  *   n_ghost  HOST, optional (may be NULL): receives n*
  * Three launches on `stream` (lattice points, ghosts, ordered sum).

@@ -157,8 +157,9 @@ def lattice_rule_integrate_improved(family, params: torch.Tensor, d: int, n: int
                                     stream=None):
     """Improved lattice rule (Definition 3.3) on the Korobov lattice z = (1, a, ..)
     for general n: the n lattice points plus the n* points completing the
-    transformed tensor grid, weight 1/(n + n*).  ``precision`` applies to the
-    lattice points ("fp64", "fp32_eval_fp64" or "df64"; the ghosts are FP64).
+    transformed tensor grid, weight 1/(n + n*).  ``precision``: "fp64",
+    "fp32_eval_fp64" (the lattice points; ghosts in FP64) or "df64" (both, where
+    the ghosts' coordinates fit float pairs; see the C header).
     Returns (1-element float64 CUDA tensor, n*)."""
     _dev_f64(params, "params")
     if params.numel() < 2 * d:

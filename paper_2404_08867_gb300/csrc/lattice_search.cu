@@ -202,20 +202,6 @@ __device__ __forceinline__ float2 split_f2(double v) {
 }
 __device__ __forceinline__ uint64_t fold(uint64_t r, uint64_t n) { return r <= n - r ? r : n - r; }
 
-// Block sum of a double-float value in a fixed order; valid in thread 0.
-__device__ __forceinline__ df32 block_sum_df32(df32 v, float2 *scratch) {
-  const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x / kWarp;
-#pragma unroll
-  for (int off = kWarp / 2; off > 0; off >>= 1) v = df_add(v, df_shfl_down(v, off));
-  if (lane == 0) scratch[warp] = make_float2(v.hi, v.lo);
-  __syncthreads();
-  df32 t{0.f, 0.f};
-  if (threadIdx.x == 0)
-    for (int w = 0; w < (int)(blockDim.x + kWarp - 1) / kWarp; ++w) t = df_add(t, df32{scratch[w].x, scratch[w].y});
-  __syncthreads();
-  return t;
-}
-
 template <int ALPHA>
 __global__ void korobov_table_kernel(uint64_t n, float2 *__restrict__ T) {
   constexpr double C = p_alpha_coef<ALPHA>();
@@ -230,7 +216,7 @@ __global__ void __launch_bounds__(kSearchThreads) korobov_table_criterion_kernel
                                                                                  const float2 *__restrict__ T,
                                                                                  double *__restrict__ values) {
   __shared__ uint64_t s_z[MAXD];
-  __shared__ float2 s_red[kSearchThreads / kWarp];
+  __shared__ double s_red[kSearchThreads / kWarp];
   __shared__ int s_ok;
   constexpr int kUnroll = MAXD <= 16 ? MAXD : 1;
   constexpr double C = p_alpha_coef<ALPHA>();
@@ -283,6 +269,8 @@ __global__ void __launch_bounds__(kSearchThreads) korobov_table_criterion_kernel
       return prod;
     };
     DfAcc acc;
+    double acc64 = 0.0;
+    int cnt = 0;
     uint32_t k = 1 + threadIdx.x;
     // Two terms per pass (twice the lookups in flight), added in the order of k.
     for (; k + B <= h32; k += 2 * B) {
@@ -290,9 +278,10 @@ __global__ void __launch_bounds__(kSearchThreads) korobov_table_criterion_kernel
       const df32 pb = term();
       dacc_add(acc, pa);
       dacc_add(acc, pb);
+      df_flush(acc, acc64, cnt);
     }
     if (k <= h32) dacc_add(acc, term());
-    const df32 tot = block_sum_df32(dacc_value(acc), s_red);
+    const double tot = block_sum((double)acc.s + ((double)acc.c + acc64), s_red);
     if (threadIdx.x == 0) {
       double p0 = 1.0, pm = 1.0;
       const double f0 = fma(C, bernoulli_even<ALPHA>(0.0), 1.0);
@@ -300,7 +289,7 @@ __global__ void __launch_bounds__(kSearchThreads) korobov_table_criterion_kernel
         p0 *= f0;
         pm *= fma(C, bernoulli_even<ALPHA>((s_z[j] & 1ull) ? 0.5 : 0.0), 1.0);
       }
-      const double S = p0 + 2.0 * ((double)tot.hi + (double)tot.lo) + ((n % 2 == 0 && n > 1) ? pm : 0.0);
+      const double S = p0 + 2.0 * tot + ((n % 2 == 0 && n > 1) ? pm : 0.0);
       values[t] = -1.0 + S / (double)n;
     }
     __syncthreads();
@@ -329,7 +318,7 @@ __global__ void __launch_bounds__(kSearchThreads) cbc_df_candidates_kernel(int s
                                                                            const double *__restrict__ pref,
                                                                            uint64_t z_first, uint64_t count,
                                                                            double *__restrict__ vals) {
-  __shared__ float2 s_red[kSearchThreads / kWarp];
+  __shared__ double s_red[kSearchThreads / kWarp];
   const uint64_t h = (n - 1) / 2;
   for (uint64_t t = blockIdx.x; t < count; t += gridDim.x) {
     const uint64_t z = z_first + t;
@@ -350,6 +339,8 @@ __global__ void __launch_bounds__(kSearchThreads) cbc_df_candidates_kernel(int s
       return f;
     };
     DfAcc acc;
+    double acc64 = 0.0;
+    int cnt = 0;
     uint32_t k = 1 + threadIdx.x;
     // Four terms per pass (four lookups in flight), accumulated in the order of k.
     for (; k + 3 * B <= h32; k += 4 * B) {
@@ -359,17 +350,18 @@ __global__ void __launch_bounds__(kSearchThreads) cbc_df_candidates_kernel(int s
       dacc_prod(acc, df32{p1.x, p1.y}, df32{f1.x, f1.y});
       dacc_prod(acc, df32{p2.x, p2.y}, df32{f2.x, f2.y});
       dacc_prod(acc, df32{p3.x, p3.y}, df32{f3.x, f3.y});
+      df_flush(acc, acc64, cnt);
     }
     for (; k <= h32; k += B) {
       const float2 pk = p[k], f = factor();
       dacc_prod(acc, df32{pk.x, pk.y}, df32{f.x, f.y});
     }
-    const df32 tot = block_sum_df32(dacc_value(acc), s_red);
+    const double tot = block_sum((double)acc.s + ((double)acc.c + acc64), s_red);
     if (threadIdx.x == 0) {
       const double inv_n = 1.0 / (double)n, g = gamma[s];
       const float2 p0 = p[0];
       double S = ((double)p0.x + (double)p0.y) * cbc_factor(g, beta, 0, inv_n) +
-                 2.0 * ((double)tot.hi + (double)tot.lo);
+                 2.0 * tot;
       if (n % 2 == 0 && n > 1) {
         const float2 pm = p[n / 2];
         S += ((double)pm.x + (double)pm.y) * cbc_factor(g, beta, (z & 1ull) ? n / 2 : 0, inv_n);

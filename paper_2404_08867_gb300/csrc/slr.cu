@@ -212,6 +212,7 @@ __global__ void __launch_bounds__(kSlrThreads) slr_df_kernel(const __grid_consta
 
   DfAcc acc;
   double acc64 = 0.0;
+  int cnt = 0;
   for (uint64_t j = j0; j < j1; ++j) {
     if constexpr (FAM == MDI_FAM_PEAK) {
       df32 p{1.f, 0.f};
@@ -274,6 +275,7 @@ __global__ void __launch_bounds__(kSlrThreads) slr_df_kernel(const __grid_consta
         r[i] = (v >= nn) ? v - nn : v;
       }
     }
+    df_flush(acc, acc64, cnt);
   }
   const double b = block_sum((double)acc.s + ((double)acc.c + acc64), s_red);
   if (threadIdx.x == 0) partials[blockIdx.x] = b;
@@ -602,6 +604,84 @@ struct GhostArgs {
   int ninv_digit[kGhostMaxD];  // base-a digits of n^{-1} mod M, least significant first
 };
 
+// Base-a digits of the line Q(r) = -r n^{-1} mod M of grid index r, least
+// significant first.
+template <int KDIG, int UNROLL>
+__device__ __forceinline__ void ghost_digits(const GhostArgs &g, uint64_t r, int (&q)[KDIG]) {
+  const uint64_t m = mulmod_u63(r % g.M, g.ninv, g.M);
+  uint64_t Q = m ? g.M - m : 0;
+#pragma unroll(UNROLL)
+  for (int k = 0; k < KDIG; ++k) {
+    if (k + 1 < g.d) {
+      q[k] = (int)(Q % (uint64_t)g.a);
+      Q /= (uint64_t)g.a;
+    }
+  }
+}
+
+// Q(r + 1) = Q(r) - n^{-1} mod M, digit by digit (the borrow out of the top digit
+// is the reduction mod M).
+template <int KDIG, int UNROLL>
+__device__ __forceinline__ void ghost_step(const GhostArgs &g, int (&q)[KDIG]) {
+  int borrow = 0;
+#pragma unroll(UNROLL)
+  for (int k = 0; k < KDIG; ++k) {
+    if (k + 1 < g.d) {
+      const int v = q[k] - g.ninv_digit[k] - borrow;
+      borrow = v < 0;
+      q[k] = borrow ? v + g.a : v;
+    }
+  }
+}
+
+// f at the grid point of index r with line digits q, in FP64: x_d = r/n, then
+// x_{d-1} = (q_0 + x_d)/a, x_{d-2} = (q_1 + x_{d-1})/a, ...
+template <int FAM, int KDIG, int UNROLL>
+__device__ __forceinline__ double ghost_value64(const GhostArgs &g, uint64_t r, const int (&q)[KDIG],
+                                                const double *s_c, const double *s_w, const double *s_ic2,
+                                                double u2pi) {
+  const int d = g.d;
+  double x = (double)r * g.inv_n;
+  if constexpr (FAM == MDI_FAM_PEAK) {
+    const double u0 = x - s_w[d - 1];
+    double p = 1.0, den = fma(u0, u0, s_ic2[d - 1]);
+#pragma unroll(UNROLL)
+    for (int k = 1; k <= KDIG; ++k) {
+      if (k < d) {
+        x = ((double)q[k - 1] + x) * g.inv_a;
+        const int i = d - 1 - k;
+        const double u = x - s_w[i];
+        den *= fma(u, u, s_ic2[i]);
+        if ((k & 7) == 7) {
+          p /= den;
+          den = 1.0;
+        }
+      }
+    }
+    return p / den;
+  } else {
+    auto term = [&](int i, double xi, double sum) {
+      if constexpr (FAM == MDI_FAM_GAUSS) {
+        const double u = s_c[i] * (xi - s_w[i]);
+        return fma(u, u, sum);
+      } else {
+        return fma(s_c[i], xi, sum);
+      }
+    };
+    double sum = term(d - 1, x, 0.0);
+#pragma unroll(UNROLL)
+    for (int k = 1; k <= KDIG; ++k) {
+      if (k < d) {
+        x = ((double)q[k - 1] + x) * g.inv_a;
+        sum = term(d - 1 - k, x, sum);
+      }
+    }
+    if constexpr (FAM == MDI_FAM_EXP) return exp(sum);
+    else if constexpr (FAM == MDI_FAM_GAUSS) return exp(-sum);
+    else return cos(u2pi + sum);
+  }
+}
+
 template <int FAM, int MAXD>
 __global__ void __launch_bounds__(kSlrThreads) ghost_kernel(const __grid_constant__ GhostArgs g,
                                                             const double *__restrict__ params,
@@ -625,74 +705,101 @@ __global__ void __launch_bounds__(kSlrThreads) ghost_kernel(const __grid_constan
   constexpr int kDig = MAXD > 1 ? MAXD - 1 : 1;
   constexpr int kUnroll = MAXD <= 32 ? kDig : 1;
   int q[kDig];
-  if (t0 < t1) {
-    const uint64_t r0 = g.n + t0;
-    const uint64_t m = mulmod_u63(r0 % g.M, g.ninv, g.M);
-    uint64_t Q = m ? g.M - m : 0;
-#pragma unroll(kUnroll)
-    for (int k = 0; k < kDig; ++k) {
-      if (k + 1 < d) {
-        q[k] = (int)(Q % (uint64_t)g.a);
-        Q /= (uint64_t)g.a;
-      }
-    }
-  }
+  if (t0 < t1) ghost_digits<kDig, kUnroll>(g, g.n + t0, q);
   double acc = 0.0;
   for (uint64_t t = t0; t < t1; ++t) {
-    double x = (double)(g.n + t) * g.inv_n;  // x_d, then x_{d-1}, x_{d-2}, ...
-    double f;
+    acc += ghost_value64<FAM, kDig, kUnroll>(g, g.n + t, q, s_c, s_w, s_ic2, u2pi);
+    ghost_step<kDig, kUnroll>(g, q);
+  }
+  const double b = block_sum(acc, s_red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = b;
+}
+
+// The ghosts in double-float (the lattice points' DF64 mode, real families): the
+// chain x_d = r/n (r in two 24-bit limbs, r < 2^48), x_{i} = (q + x_{i+1})/a (q < 2^24)
+// as float pairs, then the integrand as slr_df_kernel forms it; a ghost whose
+// exponent leaves [-64, 64] or whose peak product leaves 2^+-100 is evaluated in
+// FP64 from the same digits.
+template <int FAM, int MAXD>
+__global__ void __launch_bounds__(kSlrThreads) ghost_df_kernel(const __grid_constant__ GhostArgs g,
+                                                               const double *__restrict__ params,
+                                                               double *__restrict__ partials) {
+  __shared__ float4 s_cw[MAXD];  // (c.hi, c.lo, w.hi, w.lo)
+  __shared__ float2 s_ic[MAXD];  // 1/c^2 (PEAK)
+  __shared__ double s_c[MAXD], s_w[MAXD], s_ic2[MAXD];
+  __shared__ float2 s_exp2[kExpTable];
+  __shared__ double s_red[kSlrThreads / kWarp];
+  const int d = g.d;
+  for (int i = threadIdx.x; i < d; i += blockDim.x) {
+    const double c = params[i], w = params[d + i];
+    const df32 cd = df_from_double(c), wd = df_from_double(w);
+    s_cw[i] = make_float4(cd.hi, cd.lo, wd.hi, wd.lo);
+    const df32 ic = df_rcp(df_sqr(cd));
+    s_ic[i] = make_float2(ic.hi, ic.lo);
+    s_c[i] = c;
+    s_w[i] = w;
+    s_ic2[i] = 1.0 / (c * c);
+  }
+  for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s_exp2[j] = kExp2TableGen[j];
+  __syncthreads();
+  const df32 inv_n = df_from_double(g.inv_n), inv_n24 = df_from_double(g.inv_n * 16777216.0);
+  const df32 inv_a = df_from_double(g.inv_a);
+  const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t t0, t1;
+  thread_run(g.count, tid, nthreads, t0, t1);
+  constexpr int kDig = MAXD > 1 ? MAXD - 1 : 1;
+  constexpr int kUnroll = MAXD <= 32 ? kDig : 1;
+  int q[kDig];
+  if (t0 < t1) ghost_digits<kDig, kUnroll>(g, g.n + t0, q);
+  DfAcc acc;
+  double acc64 = 0.0;
+  int cnt = 0;
+  for (uint64_t t = t0; t < t1; ++t) {
+    const uint64_t r = g.n + t;
+    df32 x = df_add_sloppy(df_mul_f(inv_n24, (float)(uint32_t)(r >> 24)),
+                           df_mul_f(inv_n, (float)(uint32_t)(r & 0xFFFFFFu)));
+    bool ok;
     if constexpr (FAM == MDI_FAM_PEAK) {
-      const double u0 = x - s_w[d - 1];
-      double p = 1.0, den = fma(u0, u0, s_ic2[d - 1]);
+      df32 p{1.f, 0.f};
 #pragma unroll(kUnroll)
-      for (int k = 1; k <= kDig; ++k) {
+      for (int k = 0; k <= kDig; ++k) {
         if (k < d) {
-          x = ((double)q[k - 1] + x) * g.inv_a;
+          if (k > 0) x = df_mul(df_add_sloppy(x, df32{(float)q[k - 1], 0.f}), inv_a);
           const int i = d - 1 - k;
-          const double u = x - s_w[i];
-          den *= fma(u, u, s_ic2[i]);
-          if ((k & 7) == 7) {
-            p /= den;
-            den = 1.0;
+          const float4 cw = s_cw[i];
+          const df32 u = df_add_sloppy(x, df32{-cw.z, -cw.w});
+          p = df_mul(p, df_add_sloppy(df_sqr(u), df32{s_ic[i].x, s_ic[i].y}));
+        }
+      }
+      const float mag = fabsf(p.hi);
+      ok = mag > 0x1p-100f && mag < 0x1p100f;
+      if (ok) dacc_add(acc, df_rcp(p));
+    } else {
+      DfAcc sa;
+#pragma unroll(kUnroll)
+      for (int k = 0; k <= kDig; ++k) {
+        if (k < d) {
+          if (k > 0) x = df_mul(df_add_sloppy(x, df32{(float)q[k - 1], 0.f}), inv_a);
+          const float4 cw = s_cw[d - 1 - k];
+          if constexpr (FAM == MDI_FAM_GAUSS) {
+            const df32 u = df_mul(df32{cw.x, cw.y}, df_add_sloppy(x, df32{-cw.z, -cw.w}));
+            dacc_prod(sa, u, u);
+          } else {
+            dacc_prod(sa, df32{cw.x, cw.y}, x);
           }
         }
       }
-      f = p / den;
-    } else {
-      auto term = [&](int i, double xi, double sum) {
-        if constexpr (FAM == MDI_FAM_GAUSS) {
-          const double u = s_c[i] * (xi - s_w[i]);
-          return fma(u, u, sum);
-        } else {
-          return fma(s_c[i], xi, sum);
-        }
-      };
-      double sum = term(d - 1, x, 0.0);
-#pragma unroll(kUnroll)
-      for (int k = 1; k <= kDig; ++k) {
-        if (k < d) {
-          x = ((double)q[k - 1] + x) * g.inv_a;
-          sum = term(d - 1 - k, x, sum);
-        }
-      }
-      if constexpr (FAM == MDI_FAM_EXP) f = exp(sum);
-      else if constexpr (FAM == MDI_FAM_GAUSS) f = exp(-sum);
-      else f = cos(u2pi + sum);
+      df32 arg = dacc_value(sa);
+      if constexpr (FAM == MDI_FAM_GAUSS) arg = df_neg(arg);
+      ok = fabsf(arg.hi) <= 64.0f;
+      if (ok) dacc_add(acc, df_exp(arg, s_exp2));
     }
-    acc += f;
-    // Q(r + 1) = Q(r) - n^{-1} mod M, digit by digit (the borrow out of the top
-    // digit is the reduction mod M).
-    int borrow = 0;
-#pragma unroll(kUnroll)
-    for (int k = 0; k < kDig; ++k) {
-      if (k + 1 < d) {
-        const int v = q[k] - g.ninv_digit[k] - borrow;
-        borrow = v < 0;
-        q[k] = borrow ? v + g.a : v;
-      }
-    }
+    if (!ok) acc64 += ghost_value64<FAM, kDig, kUnroll>(g, r, q, s_c, s_w, s_ic2, 0.0);
+    ghost_step<kDig, kUnroll>(g, q);
+    df_flush(acc, acc64, cnt);
   }
-  const double b = block_sum(acc, s_red);
+  const double b = block_sum((double)acc.s + ((double)acc.c + acc64), s_red);
   if (threadIdx.x == 0) partials[blockIdx.x] = b;
 }
 
@@ -749,6 +856,12 @@ static void launch_ghost_d(int grid, const GhostArgs &g, const double *params, d
   else if (g.d <= 32) launch_ghost<FAM, 32>(grid, g, params, partials, s);
   else launch_ghost<FAM, kGhostMaxD>(grid, g, params, partials, s);
 }
+template <int FAM>
+static void launch_ghost_df_d(int grid, const GhostArgs &g, const double *params, double *partials, cudaStream_t s) {
+  if (g.d <= 8) ghost_df_kernel<FAM, 8><<<grid, kSlrThreads, 0, s>>>(g, params, partials);
+  else if (g.d <= 32) ghost_df_kernel<FAM, 32><<<grid, kSlrThreads, 0, s>>>(g, params, partials);
+  else ghost_df_kernel<FAM, kGhostMaxD><<<grid, kSlrThreads, 0, s>>>(g, params, partials);
+}
 
 mdi_status slr_improved_launch(int family, int d, int64_t n, int64_t a, const double *params, int precision,
                                double *out, int64_t *n_ghost, void *workspace, size_t ws_bytes, cudaStream_t stream) {
@@ -769,7 +882,7 @@ mdi_status slr_improved_launch(int family, int d, int64_t n, int64_t a, const do
     zi = (uint64_t)(((unsigned __int128)zi * (uint64_t)a) % (uint64_t)n);
   }
   double *partials = (double *)workspace;
-  // The lattice points in the requested arithmetic; the ghosts below in FP64.
+  // The lattice points in the requested arithmetic; the ghosts below in DF64 or FP64.
   launch_slr_points(family, precision, pl.grid_lattice, args, params, partials, stream);
   mdi_status st = check_launch();
   if (st != MDI_OK) return st;
@@ -789,11 +902,24 @@ mdi_status slr_improved_launch(int family, int d, int64_t n, int64_t a, const do
       v /= (uint64_t)a;
     }
     double *gp = partials + pl.grid_lattice;
+    // DF64 ghosts where their coordinates fit float pairs exactly enough: grid
+    // indices below 2^48 (two 24-bit limbs) and line digits below 2^24.
+    const bool df = precision == MDI_PREC_DF64 && family != MDI_FAM_OSC && pl.N <= (1ull << 48) &&
+                    (uint64_t)a <= (1ull << 24);
     switch (family) {
-      case MDI_FAM_EXP: launch_ghost_d<MDI_FAM_EXP>(pl.grid_ghost, g, params, gp, stream); break;
+      case MDI_FAM_EXP:
+        df ? launch_ghost_df_d<MDI_FAM_EXP>(pl.grid_ghost, g, params, gp, stream)
+           : launch_ghost_d<MDI_FAM_EXP>(pl.grid_ghost, g, params, gp, stream);
+        break;
       case MDI_FAM_OSC: launch_ghost_d<MDI_FAM_OSC>(pl.grid_ghost, g, params, gp, stream); break;
-      case MDI_FAM_GAUSS: launch_ghost_d<MDI_FAM_GAUSS>(pl.grid_ghost, g, params, gp, stream); break;
-      default: launch_ghost_d<MDI_FAM_PEAK>(pl.grid_ghost, g, params, gp, stream); break;
+      case MDI_FAM_GAUSS:
+        df ? launch_ghost_df_d<MDI_FAM_GAUSS>(pl.grid_ghost, g, params, gp, stream)
+           : launch_ghost_d<MDI_FAM_GAUSS>(pl.grid_ghost, g, params, gp, stream);
+        break;
+      default:
+        df ? launch_ghost_df_d<MDI_FAM_PEAK>(pl.grid_ghost, g, params, gp, stream)
+           : launch_ghost_d<MDI_FAM_PEAK>(pl.grid_ghost, g, params, gp, stream);
+        break;
     }
     if ((st = check_launch()) != MDI_OK) return st;
   }

@@ -73,7 +73,8 @@ def test_ghosts_beyond_lattice_at_large_n(precision):
     assert abs(got.item() - expect) <= 1e-12 * expect
 
 
-def test_wide_ghost_kernel_closed_form():
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_wide_ghost_kernel_closed_form(precision):
     # d = 33 (the kernel's widest digit bucket), a = 2, n = 1001: M = 2^32 lines of
     # one position, so the completed grid is r = 0 .. 2^32 - 1 and 2^32 - 1001
     # ghosts carry 32-digit lines; f = exp(c x_d) has the closed form over r/n.
@@ -83,7 +84,7 @@ def test_wide_ghost_kernel_closed_form():
     cd = 2e-7  # x_d = r/n reaches N/n = 4.3e6: c N/n = 0.86 keeps the terms in [1, 2.4]
     c = np.zeros(d)
     c[-1] = cd
-    got, ns = mdi.lattice_rule_integrate_improved("exp", dev(np.r_[c, np.zeros(d)]), d, n, a)
+    got, ns = mdi.lattice_rule_integrate_improved("exp", dev(np.r_[c, np.zeros(d)]), d, n, a, precision=precision)
     assert ns == N - n
     expect = math.expm1(cd * N / n) / (N * math.expm1(cd / n))
     assert abs(got.item() - expect) <= 1e-12 * expect
