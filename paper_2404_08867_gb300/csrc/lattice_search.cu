@@ -270,15 +270,17 @@ __global__ void __launch_bounds__(kSearchThreads) korobov_table_criterion_kernel
     };
     DfAcc acc;
     double acc64 = 0.0;
-    int cnt = 0;
     uint32_t k = 1 + threadIdx.x;
-    // Two terms per pass (twice the lookups in flight), added in the order of k.
-    for (; k + B <= h32; k += 2 * B) {
-      const df32 pa = term();
-      const df32 pb = term();
-      dacc_add(acc, pa);
-      dacc_add(acc, pb);
-      df_flush(acc, acc64, cnt);
+    // Two terms per pass (twice the lookups in flight), added in the order of k;
+    // chunks of kDfFlush passes, each chunk's float-pair sum then moved into acc64.
+    while (k + B <= h32) {
+      for (int c = 0; c < kDfFlush && k + B <= h32; ++c, k += 2 * B) {
+        const df32 pa = term();
+        const df32 pb = term();
+        dacc_add(acc, pa);
+        dacc_add(acc, pb);
+      }
+      df_flush(acc, acc64);
     }
     if (k <= h32) dacc_add(acc, term());
     const double tot = block_sum((double)acc.s + ((double)acc.c + acc64), s_red);
@@ -340,17 +342,19 @@ __global__ void __launch_bounds__(kSearchThreads) cbc_df_candidates_kernel(int s
     };
     DfAcc acc;
     double acc64 = 0.0;
-    int cnt = 0;
     uint32_t k = 1 + threadIdx.x;
-    // Four terms per pass (four lookups in flight), accumulated in the order of k.
-    for (; k + 3 * B <= h32; k += 4 * B) {
-      const float2 f0 = factor(), f1 = factor(), f2 = factor(), f3 = factor();
-      const float2 p0 = p[k], p1 = p[k + B], p2 = p[k + 2 * B], p3 = p[k + 3 * B];
-      dacc_prod(acc, df32{p0.x, p0.y}, df32{f0.x, f0.y});
-      dacc_prod(acc, df32{p1.x, p1.y}, df32{f1.x, f1.y});
-      dacc_prod(acc, df32{p2.x, p2.y}, df32{f2.x, f2.y});
-      dacc_prod(acc, df32{p3.x, p3.y}, df32{f3.x, f3.y});
-      df_flush(acc, acc64, cnt);
+    // Four terms per pass (four lookups in flight), accumulated in the order of k;
+    // chunks of kDfFlush passes, each chunk's float-pair sum then moved into acc64.
+    while (k + 3 * B <= h32) {
+      for (int c = 0; c < kDfFlush && k + 3 * B <= h32; ++c, k += 4 * B) {
+        const float2 f0 = factor(), f1 = factor(), f2 = factor(), f3 = factor();
+        const float2 p0 = p[k], p1 = p[k + B], p2 = p[k + 2 * B], p3 = p[k + 3 * B];
+        dacc_prod(acc, df32{p0.x, p0.y}, df32{f0.x, f0.y});
+        dacc_prod(acc, df32{p1.x, p1.y}, df32{f1.x, f1.y});
+        dacc_prod(acc, df32{p2.x, p2.y}, df32{f2.x, f2.y});
+        dacc_prod(acc, df32{p3.x, p3.y}, df32{f3.x, f3.y});
+      }
+      df_flush(acc, acc64);
     }
     for (; k <= h32; k += B) {
       const float2 pk = p[k], f = factor();

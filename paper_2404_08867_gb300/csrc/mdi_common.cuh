@@ -205,18 +205,15 @@ __device__ __forceinline__ void dacc_add(DfAcc &a, df32 x) {
   a.c = __fadd_rn(a.c, __fadd_rn(x.lo, t.lo));
 }
 __device__ __forceinline__ df32 dacc_value(const DfAcc &a) { return two_sum(a.s, a.c); }
-// Long per-thread sums: after kDfFlush calls (one per term, or per pass of a few
-// terms) the float-pair accumulator moves into a double.  The pair's compensated
-// sum loses up to about one unit of 2^-48 of the running total per term, so runs
-// of thousands of terms (2^32 ghosts, lattices of up to 2^48 points, 2^22 Korobov
-// terms per thread) are cut short.
+// Long per-thread sums run in chunks of kDfFlush steps (a term, or a pass of a
+// few terms), each chunk's float-pair accumulator then moving into a double.  The
+// pair's compensated sum loses up to about one unit of 2^-48 of the running total
+// per term, so runs of thousands of terms (2^32 ghosts, lattices of up to 2^48
+// points, 2^22 Korobov terms per thread) are cut short.
 constexpr int kDfFlush = 128;
-__device__ __forceinline__ void df_flush(DfAcc &acc, double &acc64, int &cnt) {
-  if (++cnt == kDfFlush) {
-    acc64 += (double)acc.s + (double)acc.c;
-    acc = DfAcc{};
-    cnt = 0;
-  }
+__device__ __forceinline__ void df_flush(DfAcc &acc, double &acc64) {
+  acc64 += (double)acc.s + (double)acc.c;
+  acc = DfAcc{};
 }
 // x * f for a double-float x and a float f (Joldes et al. 2017, Algorithm 9 without
 // the final renormalisation of the error term).

@@ -212,8 +212,8 @@ __global__ void __launch_bounds__(kSlrThreads) slr_df_kernel(const __grid_consta
 
   DfAcc acc;
   double acc64 = 0.0;
-  int cnt = 0;
-  for (uint64_t j = j0; j < j1; ++j) {
+  // One point: its value into acc (or acc64), its residues stepped by z.
+  auto point = [&]() {
     if constexpr (FAM == MDI_FAM_PEAK) {
       df32 p{1.f, 0.f};
 #pragma unroll(kUnroll)
@@ -275,7 +275,17 @@ __global__ void __launch_bounds__(kSlrThreads) slr_df_kernel(const __grid_consta
         r[i] = (v >= nn) ? v - nn : v;
       }
     }
-    df_flush(acc, acc64, cnt);
+  };
+  if constexpr (IDX32 && !SHIFT) {
+    // n <= 2^24 over at least 2 x 256 threads per SM: at most 216 points per thread.
+    for (uint64_t j = j0; j < j1; ++j) point();
+  } else {
+    // Chunks of kDfFlush points, each chunk's float-pair sum then moved into acc64.
+    for (uint64_t jc = j0; jc < j1; jc += kDfFlush) {
+      const uint64_t je = jc + kDfFlush < j1 ? jc + kDfFlush : j1;
+      for (uint64_t j = jc; j < je; ++j) point();
+      df_flush(acc, acc64);
+    }
   }
   const double b = block_sum((double)acc.s + ((double)acc.c + acc64), s_red);
   if (threadIdx.x == 0) partials[blockIdx.x] = b;
@@ -754,50 +764,53 @@ __global__ void __launch_bounds__(kSlrThreads) ghost_df_kernel(const __grid_cons
   if (t0 < t1) ghost_digits<kDig, kUnroll>(g, g.n + t0, q);
   DfAcc acc;
   double acc64 = 0.0;
-  int cnt = 0;
-  for (uint64_t t = t0; t < t1; ++t) {
-    const uint64_t r = g.n + t;
-    df32 x = df_add_sloppy(df_mul_f(inv_n24, (float)(uint32_t)(r >> 24)),
-                           df_mul_f(inv_n, (float)(uint32_t)(r & 0xFFFFFFu)));
-    bool ok;
-    if constexpr (FAM == MDI_FAM_PEAK) {
-      df32 p{1.f, 0.f};
+  // Chunks of kDfFlush ghosts, each chunk's float-pair sum then moved into acc64.
+  for (uint64_t tc = t0; tc < t1; tc += kDfFlush) {
+    const uint64_t te = tc + kDfFlush < t1 ? tc + kDfFlush : t1;
+    for (uint64_t t = tc; t < te; ++t) {
+      const uint64_t r = g.n + t;
+      df32 x = df_add_sloppy(df_mul_f(inv_n24, (float)(uint32_t)(r >> 24)),
+                             df_mul_f(inv_n, (float)(uint32_t)(r & 0xFFFFFFu)));
+      bool ok;
+      if constexpr (FAM == MDI_FAM_PEAK) {
+        df32 p{1.f, 0.f};
 #pragma unroll(kUnroll)
-      for (int k = 0; k <= kDig; ++k) {
-        if (k < d) {
-          if (k > 0) x = df_mul(df_add_sloppy(x, df32{(float)q[k - 1], 0.f}), inv_a);
-          const int i = d - 1 - k;
-          const float4 cw = s_cw[i];
-          const df32 u = df_add_sloppy(x, df32{-cw.z, -cw.w});
-          p = df_mul(p, df_add_sloppy(df_sqr(u), df32{s_ic[i].x, s_ic[i].y}));
-        }
-      }
-      const float mag = fabsf(p.hi);
-      ok = mag > 0x1p-100f && mag < 0x1p100f;
-      if (ok) dacc_add(acc, df_rcp(p));
-    } else {
-      DfAcc sa;
-#pragma unroll(kUnroll)
-      for (int k = 0; k <= kDig; ++k) {
-        if (k < d) {
-          if (k > 0) x = df_mul(df_add_sloppy(x, df32{(float)q[k - 1], 0.f}), inv_a);
-          const float4 cw = s_cw[d - 1 - k];
-          if constexpr (FAM == MDI_FAM_GAUSS) {
-            const df32 u = df_mul(df32{cw.x, cw.y}, df_add_sloppy(x, df32{-cw.z, -cw.w}));
-            dacc_prod(sa, u, u);
-          } else {
-            dacc_prod(sa, df32{cw.x, cw.y}, x);
+        for (int k = 0; k <= kDig; ++k) {
+          if (k < d) {
+            if (k > 0) x = df_mul(df_add_sloppy(x, df32{(float)q[k - 1], 0.f}), inv_a);
+            const int i = d - 1 - k;
+            const float4 cw = s_cw[i];
+            const df32 u = df_add_sloppy(x, df32{-cw.z, -cw.w});
+            p = df_mul(p, df_add_sloppy(df_sqr(u), df32{s_ic[i].x, s_ic[i].y}));
           }
         }
+        const float mag = fabsf(p.hi);
+        ok = mag > 0x1p-100f && mag < 0x1p100f;
+        if (ok) dacc_add(acc, df_rcp(p));
+      } else {
+        DfAcc sa;
+#pragma unroll(kUnroll)
+        for (int k = 0; k <= kDig; ++k) {
+          if (k < d) {
+            if (k > 0) x = df_mul(df_add_sloppy(x, df32{(float)q[k - 1], 0.f}), inv_a);
+            const float4 cw = s_cw[d - 1 - k];
+            if constexpr (FAM == MDI_FAM_GAUSS) {
+              const df32 u = df_mul(df32{cw.x, cw.y}, df_add_sloppy(x, df32{-cw.z, -cw.w}));
+              dacc_prod(sa, u, u);
+            } else {
+              dacc_prod(sa, df32{cw.x, cw.y}, x);
+            }
+          }
+        }
+        df32 arg = dacc_value(sa);
+        if constexpr (FAM == MDI_FAM_GAUSS) arg = df_neg(arg);
+        ok = fabsf(arg.hi) <= 64.0f;
+        if (ok) dacc_add(acc, df_exp(arg, s_exp2));
       }
-      df32 arg = dacc_value(sa);
-      if constexpr (FAM == MDI_FAM_GAUSS) arg = df_neg(arg);
-      ok = fabsf(arg.hi) <= 64.0f;
-      if (ok) dacc_add(acc, df_exp(arg, s_exp2));
+      if (!ok) acc64 += ghost_value64<FAM, kDig, kUnroll>(g, r, q, s_c, s_w, s_ic2, 0.0);
+      ghost_step<kDig, kUnroll>(g, q);
     }
-    if (!ok) acc64 += ghost_value64<FAM, kDig, kUnroll>(g, r, q, s_c, s_w, s_ic2, 0.0);
-    ghost_step<kDig, kUnroll>(g, q);
-    df_flush(acc, acc64, cnt);
+    df_flush(acc, acc64);
   }
   const double b = block_sum((double)acc.s + ((double)acc.c + acc64), s_red);
   if (threadIdx.x == 0) partials[blockIdx.x] = b;
