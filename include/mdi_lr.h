@@ -116,8 +116,9 @@ typedef struct {
   int32_t state;       /* mdi_state */
   int32_t precision;   /* mdi_precision */
   int32_t nodes;       /* P for MDI_STATE_NODES, 2..32; 0 selects 16 */
-  int32_t block;       /* threads per CTA for the node-state kernels (64..512,
-                          multiple of 32 and of P); 0 selects the library default */
+  int32_t block;       /* threads per CTA for the node-state kernels (32..512, a
+                          multiple of 32 and at least P); 0 selects the library
+                          default */
   int32_t ctas_per_sm; /* resident CTAs per SM for persistent grids; 0 = default */
   int32_t checkpoint;  /* level-checkpoint interval of the adjoint; 0 = ceil(sqrt(d)) */
   int32_t table_in_l1; /* node-state kernels: 0 = stage each integral's basis table in
@@ -276,8 +277,9 @@ typedef struct {
 
 /* One-time set-up of a workspace for mdi_lr_integrate_batched: builds the
  * barycentric basis tables l_t((q + xi_p)/a) for a = 1..64 and the P of opts (they
- * depend on nothing else) -- for MDI_PREC_DF64 also the paired table
- * l_t +- l_{P-1-t} that the real families' sweep uses -- and the constants every
+ * depend on nothing else) and the paired table l_t +- l_{P-1-t} that the real
+ * families' sweeps use (float pairs in the double-float modes, doubles
+ * otherwise) -- and the constants every
  * integral shares (the Chebyshev nodes and weights, xi_p/a and 1/a as float
  * pairs, the 2^(j/256) table of the double-float exp), zeroes the work-queue
  * counters and stamps a tag naming opts->nodes and the table format of
