@@ -5,6 +5,7 @@ computes: every launch goes through the C ABI.
 
   batch-df64      4096-integral batch, double-float node state (block 32, table via L1)
   batch-fp64      the same batch in FP64 (block 64, table via L1)
+  batch-f32df     the same batch, phi in float, double-float sums (block 32, table via L1)
   levels-d1000    one integral, node state parallel over levels, d = 1000, N = 16:
                   forward and adjoint
   korobov         P_2 Korobov search, n = 65536, d = 4, every a in 1..n/2
@@ -45,6 +46,8 @@ def build_case(name: str):
         return _batch("df64", 32)
     if name == "batch-fp64":
         return _batch("fp64", 64)
+    if name == "batch-f32df":
+        return _batch("fp32_eval_df32", 32)
     if name == "levels-d1000":
         w = inputs.scale_exp(1000, 16)
         p = torch.as_tensor(w.params).cuda()
