@@ -53,6 +53,11 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 128 FFMA lanes per SM per c
 # Float operations (an FMA counts 2) of the double-float primitives, by construction.
 DF_FLOPS = {"u": 28, "dot_term": 15, "dot_value": 6, "acc": 15, "combine": 22,
             "phi": {"gauss": 122, "peak": 83, "exp": 93, "osc": 0}}
+# The single-precision-evaluation mode with double-float sums: the coordinate is
+# one float FMA, phi the float formula with exp or the reciprocal counted as one
+# operation (gauss: subtract, multiply, square, exp; peak: subtract, FMA,
+# reciprocal; exp: multiply, exp), the accumulation a float-by-pair Dot2 step.
+F32_FLOPS = {"u": 2, "acc": 13, "phi": {"gauss": 4, "peak": 4, "exp": 2, "osc": 0}}
 
 
 def exact_integral(family, d, c, w=None):
@@ -143,14 +148,15 @@ def fp64_flops(b, P=P_NODES, paired=True):
     return float((interp * per_point + first * 8 + nl * (2 * P + 8)).sum())
 
 
-def df_flops(b, P=P_NODES, paired=True):
+def df_flops(b, P=P_NODES, paired=True, float_phi=False):
     """Float operations of the double-float formulation (FMA = 2), by construction:
     per cluster point of level k >= 2: coordinate, phi, the interpolation and the
     accumulation; level 1 without interpolation; last axis with a P-term Dot2 per
     point.  Paired (DF64, real families): one pass of P Dot2 terms (P/2 for the
     sums of the table values, P/2 for their differences) interpolates two mirrored
     points, plus per point one Dot2 value, a double-float add and a halving;
-    otherwise P Dot2 terms and one value per point."""
+    otherwise P Dot2 terms and one value per point.  float_phi: the cluster points'
+    coordinate, phi and accumulation as F32_FLOPS counts them."""
     total = 0.0
     interp_one = P * DF_FLOPS["dot_term"] + DF_FLOPS["dot_value"]
     interp_paired = P * DF_FLOPS["dot_term"] / 2 + DF_FLOPS["dot_value"] + DF_FLOPS["combine"]
@@ -158,8 +164,9 @@ def df_flops(b, P=P_NODES, paired=True):
         d, a, nl = int(b.d[i]), int(b.a[i]), int(b.n_last[i])
         phi = DF_FLOPS["phi"][fam]
         pt = DF_FLOPS["u"] + phi + DF_FLOPS["acc"]
+        pc = (F32_FLOPS["u"] + F32_FLOPS["phi"][fam] + F32_FLOPS["acc"]) if (float_phi and fam != "osc") else pt
         interp = interp_paired if (paired and fam != "osc") else interp_one
-        total += max(d - 2, 0) * a * P * (pt + interp) + (a * P * pt if d >= 2 else 0) + nl * (pt + interp_one)
+        total += max(d - 2, 0) * a * P * (pc + interp) + (a * P * pc if d >= 2 else 0) + nl * (pt + interp_one)
     return total
 
 
@@ -796,7 +803,7 @@ def main():
     if rank == 0:
         kernel_ms = statistics.mean(step_ms)
         if args.precision in ("df64", "fp32_eval_df32"):
-            flops = df_flops(b, paired=args.precision == "df64")
+            flops = df_flops(b, paired=True, float_phi=args.precision == "fp32_eval_df32")
             achieved = flops / (kernel_ms / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": profiled_traffic(args.precision),

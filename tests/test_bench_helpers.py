@@ -71,3 +71,23 @@ def test_oracle_only_in_cpu_baseline_and_reference_legs():
     for f in os.listdir(pkg):
         if f.endswith(".py"):
             assert not _oracle_importers(os.path.join(pkg, f)), f
+
+
+def test_flop_counts_of_the_batched_formulations():
+    # By construction: one cluster point of an unpaired level costs the coordinate,
+    # phi, the accumulation and a P-term Dot2; pairing halves the Dot2 terms; the
+    # float-phi mode replaces the coordinate, phi and accumulation counts.
+    from types import SimpleNamespace
+    P = bench.P_NODES
+    one = SimpleNamespace(families=["gauss"], d=np.array([3]), a=np.array([5]), n_last=np.array([5]))
+    F = bench.DF_FLOPS
+    pt = F["u"] + F["phi"]["gauss"] + F["acc"]
+    full = P * F["dot_term"] + F["dot_value"]
+    half = P * F["dot_term"] / 2 + F["dot_value"] + F["combine"]
+    last = 5 * (pt + full)
+    assert bench.df_flops(one, paired=False) == 5 * P * (pt + full) + 5 * P * pt + last
+    assert bench.df_flops(one) == 5 * P * (pt + half) + 5 * P * pt + last
+    pf = bench.F32_FLOPS["u"] + bench.F32_FLOPS["phi"]["gauss"] + bench.F32_FLOPS["acc"]
+    assert bench.df_flops(one, float_phi=True) == 5 * P * (pf + half) + 5 * P * pf + last
+    osc = SimpleNamespace(families=["osc"], d=np.array([3]), a=np.array([5]), n_last=np.array([5]))
+    assert bench.df_flops(osc, float_phi=True) == bench.df_flops(osc, paired=False)  # OSC: unpaired, FP64 phi
