@@ -134,8 +134,9 @@ __global__ void __launch_bounds__(kSlrThreads) slr_kernel(const __grid_constant_
 // coordinates are Dot2 accumulations, exp and 1/x the double-float ones; a point
 // whose value would leave the float range (argument of exp beyond 64 in size, or
 // a peak product outside 2^(+-100)) is evaluated in FP64 into a separate double
-// accumulator.  Each thread's Dot2 sum and double sum are added in double, then
-// the fixed block tree as in slr_kernel.  IDX32 steps the numerators in 32-bit
+// accumulator.  Each thread's Dot2 sum moves into the double sum every kDfFlush
+// points (except the unshifted n <= 2^24 case, at most a few hundred points per
+// thread), then the fixed block tree as in slr_kernel.  IDX32 steps the numerators in 32-bit
 // integers, half the integer work of the 64-bit steps; it is used for n <= 2^24
 // (one-limb coordinates), where it was measured faster (with two-limb
 // coordinates it measured slower, so larger n keeps 64-bit steps).
