@@ -67,9 +67,7 @@ static double nodes_cost(const mdi_batch_desc &d, int P) {
 
 // One node-state integral runs parallel over levels (mdi_levels.cu) when it has
 // enough levels to fill several SMs; short ones take one CTA of the batched kernel.
-static bool use_levels(int d, const NodesConfig &cfg) {
-  return d >= 8;
-}
+static bool use_levels(int d) { return d >= 8; }
 
 static bool desc_ok(const mdi_batch_desc &d) {
   return family_ok(d.family) && d.d >= 1 && d.d <= MDI_BATCH_MAX_D && d.a >= 1 && d.a <= 64 && d.n_last >= 1 &&
@@ -167,7 +165,7 @@ mdi_status mdi_lr_workspace_size(int32_t family, int32_t d, int64_t a, int64_t n
       return MDI_OK;
     default: {
       const NodesConfig cfg = nodes_config(opts);
-      *bytes = use_levels(d, cfg) ? levels_workspace_bytes(d, a, cfg, opts ? opts->checkpoint : 0)
+      *bytes = use_levels(d) ? levels_workspace_bytes(d, a, cfg, opts ? opts->checkpoint : 0)
                                   : nodes_single_workspace_bytes(cfg);
       return MDI_OK;
     }
@@ -186,7 +184,7 @@ mdi_status mdi_lr_integrate(int32_t family, int32_t d, int64_t a, int64_t n_last
     case MDI_STATE_CLOSED: return closed_launch(family, d, a, n_last, params, precision, out, workspace, ws_bytes, s);
     default: {
       const NodesConfig cfg = nodes_config(opts);
-      if (use_levels(d, cfg))
+      if (use_levels(d))
         return levels_launch(family, d, a, n_last, params, cfg, opts ? opts->checkpoint : 0, out, nullptr, workspace,
                              ws_bytes, s);
       return nodes_single_launch(family, d, a, n_last, params, cfg, out, workspace, ws_bytes, s);
