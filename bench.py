@@ -5,22 +5,25 @@ uneven size -- d ~ U{6..20}, N ~ U{8..32} points per transformed axis (a = n_las
 = N), product-peak and Gaussian integrands alternating, c_j ~ U(0.5, 2),
 w_j ~ U(0, 1), node state with P = 16.  Every level of every integral runs in one
 persistent kernel launch, autotuned (CTA size, table placement) and replayed from
-a CUDA graph.  The default arithmetic is the double-float mode (FP64-class, held to
-1e-12 of the FP64 oracle by the tests); --precision fp64 times the FP64 path.
+a CUDA graph.  The headline arithmetic is FP64 (the paper's); the double-float
+and single-precision-evaluation modes are timed on the same batch as secondary
+entries, each with its largest error against the FP64 oracle over the whole batch.
 
 Printed (rank 0, one JSON line): integrals/s over the timed steps (device time,
 inputs resident in HBM, L2 flushed between steps), the same metric end to end
 (pinned host inputs copied in and results copied out inside the timed region),
-the roofline of the batched kernel, the CPU oracle on a bounded sample, SM clocks
-sampled during the timed region, and (unless --no-extras) the other workloads:
-the FP64 mode of the same batch, the d = 4 comparison of MDI-LR with the plain
-lattice kernel including time to 1e-6 (with a Korobov parameter from the GPU's
-P_2 search, and 16 random shifts), the precision modes on the oscillatory d = 50
-integral, the adjoint on the d = 100 Gaussian, the cost-vs-d sweep, the paper's
-printed MDI-LR errors recomputed in the paper-table mode (and Test 7's ridge
-integrand), and the Korobov search and CBC construction at n = 65536.
+the roofline of the batched kernel against FMA peaks measured in the same run,
+the CPU oracle on all host cores (and on one), SM clocks sampled during the timed
+region, and (unless --no-extras) the other workloads: the d = 4 comparison of
+MDI-LR with the plain lattice kernel including time to 1e-6 (with a Korobov
+parameter from the GPU's P_2 search, and 16 random shifts), the precision modes on
+the oscillatory d = 50 integral, the adjoint on the d = 100 Gaussian, the
+cost-vs-d sweep, the paper's printed MDI-LR errors recomputed in the paper-table
+mode (and Test 7's ridge integrand), and the Korobov search and CBC construction
+at n = 65536.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --case NAME [--repeats R]     (one workload, for profilers)
 Under torchrun every rank sweeps its own batch (weak scaling, no collective on
 the data path); the barrier and the max over ranks bracket the timed region.
 """
@@ -46,9 +49,16 @@ BASELINE_METRIC = "time to 1e-6 rel err, MDI-LR vs plain lattice kernel; integra
 COUNT = 4096
 P_NODES = 16
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
-# Peaks derived from unit counts and the maximum SM clock (2.07 GHz, 152 SMs):
+# Peaks from unit counts and the maximum SM clock (2.07 GHz, 152 SMs), context
+# beside the peaks the run measures with the library's FMA probe:
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12    # 2 DFMA lanes per SM per clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 128 FFMA lanes per SM per clock
+# Algorithmic flops of one node-state integral (the survey's measurement table):
+# d N (P C_phi + P^2) -- per level and cluster point, P evaluations of phi at
+# C_phi flops each and the P^2 terms of interpolating the state.  C_phi counts an
+# exp or a division as 20 flops plus the affine argument, its square and the
+# scaling (Gaussian: exp(-(c (u - w))^2); peak: 1/(c^-2 + (u - w)^2)).
+C_PHI = {"gauss": 25, "peak": 25, "exp": 25, "osc": 50}
 
 # Float operations (an FMA counts 2) of the double-float primitives, by construction.
 DF_FLOPS = {"u": 28, "dot_term": 15, "dot_value": 6, "acc": 15, "combine": 22,
@@ -107,8 +117,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--count", type=int, default=COUNT)
-    ap.add_argument("--precision", default="df64", choices=["df64", "fp64", "fp32_eval_fp64", "fp32_eval_df32"])
-    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="budget of the CPU oracle sample")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "fp32_eval_fp64", "fp32_eval_df32"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="budget of the CPU oracle sample (all cores)")
+    ap.add_argument("--case", default=None, help="run one named workload --repeats times and exit (profiling)")
+    ap.add_argument("--repeats", type=int, default=5)
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-tune", action="store_true", help="fixed launch shape (--block, --table-in-l1), no autotuning")
     ap.add_argument("--block", type=int, default=128, help="CTA size with --no-tune")
@@ -170,6 +182,14 @@ def df_flops(b, P=P_NODES, paired=True, float_phi=False):
     return total
 
 
+def alg_flops(b, P=P_NODES):
+    """Algorithmic flops of a batch: sum over integrals of d N (P C_phi + P^2)
+    (a = n_last = N), whatever arithmetic the kernel uses to get there."""
+    d, a = b.d.astype(np.float64), b.a.astype(np.float64)
+    cphi = np.array([C_PHI[f] for f in b.families], dtype=np.float64)
+    return float((d * a * (P * cphi + P * P)).sum())
+
+
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -216,9 +236,74 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def cpu_oracle_sample(b, budget_s, P=P_NODES, limit=None):
-    """Times the FP64 CPU oracle (node state) on consecutive integrals of the batch
-    until `budget_s` seconds (or `limit` integrals) are done."""
+def host_cores():
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+_CPU_BATCH = {}
+
+
+def cpu_oracle_chunk(task):
+    """Worker of the CPU oracle legs: the FP64 oracle's node-state value (P = 16) of
+    integrals lo..hi-1 of the seeded batch (count, seed), which every worker draws
+    itself from the seeded generator."""
+    from oracle import oracle as o
+    from paper_2404_08867_gb300 import inputs
+    count, seed, lo, hi = task
+    if (count, seed) not in _CPU_BATCH:
+        _CPU_BATCH[(count, seed)] = inputs.batch(count=count, seed=seed)
+    b = _CPU_BATCH[(count, seed)]
+    out = []
+    for i in range(lo, hi):
+        it = b.integral(i)
+        out.append(o.mdi_nodes(it.family, it.d, it.a, it.n_last, P_NODES, it.c, it.w))
+    return lo, out
+
+
+def cpu_oracle_pool(cores):
+    """A pool of `cores` oracle workers, started by spawn (not fork: the parent may
+    already hold a CUDA context)."""
+    import multiprocessing as mp
+    from oracle import oracle as o
+    o.build()
+    return mp.get_context("spawn").Pool(processes=cores)
+
+
+def cpu_oracle_batch_pass(pool, count, seed, cores):
+    """One pass of the oracle over the whole batch on the pool; returns the values."""
+    step = max(1, count // (cores * 8))
+    tasks = [(count, seed, lo, min(count, lo + step)) for lo in range(0, count, step)]
+    vals = np.empty(count)
+    for lo, out in pool.imap_unordered(cpu_oracle_chunk, tasks):
+        vals[lo:lo + len(out)] = out
+    return vals
+
+
+def cpu_baseline_all_cores(count, seed, budget_s):
+    """CPU baseline on every host core: whole passes of the FP64 oracle over the
+    batch until `budget_s` seconds, after one untimed pass (pool start-up).
+    Returns (oracle values of the batch, integrals/s, cores, passes, seconds)."""
+    cores = host_cores()
+    with cpu_oracle_pool(cores) as pool:
+        vals = cpu_oracle_batch_pass(pool, count, seed, cores)
+        t0 = time.perf_counter()
+        passes = 0
+        while True:
+            cpu_oracle_batch_pass(pool, count, seed, cores)
+            passes += 1
+            el = time.perf_counter() - t0
+            if el >= budget_s:
+                break
+    return vals, passes * count / el, cores, passes, el
+
+
+def cpu_baseline_one_core(b, budget_s, P=P_NODES):
+    """The FP64 oracle (node state) on one core, on consecutive integrals of the
+    batch until `budget_s` seconds."""
     from oracle import oracle as o
     o.build()
     t0 = time.perf_counter()
@@ -228,7 +313,7 @@ def cpu_oracle_sample(b, budget_s, P=P_NODES, limit=None):
         o.mdi_nodes(it.family, it.d, it.a, it.n_last, P, it.c, it.w)
         done += 1
         el = time.perf_counter() - t0
-        if (limit is None and el >= budget_s) or (limit is not None and done >= limit):
+        if el >= budget_s:
             return done / el, done, el
 
 
@@ -247,30 +332,29 @@ def cpu_baseline_korobov_search(d, n, budget_s):
             "sample": f"{k} candidates of the n = {n}, d = {d} search in {el:.1f} s"}
 
 
-def run_reference(args, rank, world):
-    """Reference arm: the CPU oracle, as it stands, on one host core."""
+def cpu_reference_arm(args, rank, world):
+    """Reference arm: the CPU oracle, as it stands, on every host core; one step is
+    one pass over the same 4096-integral batch (seed 0) as our arm's step."""
     if rank != 0:
         return
-    from paper_2404_08867_gb300 import inputs
-    b = inputs.batch(count=args.count, seed=0)
-    per_step = 48
-    for _ in range(args.warmup):
-        cpu_oracle_sample(b, 0, limit=per_step)
-    times = []
-    done = 0
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        _, n, _ = cpu_oracle_sample(b, 0, limit=per_step)
-        times.append(time.perf_counter() - t0)
-        done += n
-    value = done / sum(times)
+    cores = host_cores()
+    with cpu_oracle_pool(cores) as pool:
+        for _ in range(max(1, args.warmup)):
+            cpu_oracle_batch_pass(pool, args.count, 0, cores)
+        times = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            cpu_oracle_batch_pass(pool, args.count, 0, cores)
+            times.append(time.perf_counter() - t0)
+    value = args.count * args.steps / sum(times)
     line = {"metric": METRIC, "value": value, "unit": "integrals/s", "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.count, args.precision),  # the same workload as our arm
+            "config": workload_config(args.count, "fp64"),  # the same workload as our arm
             "reference_arithmetic": "f64 (the oracle computes every integral in double)",
-            "cpu_baseline": {"value": value, "unit": "integrals/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{per_step} integrals of the batch per step (node state, P=16)"},
+            "cpu_baseline": {"value": value, "unit": "integrals/s", "cores": cores, "kind": "oracle",
+                             "sample": f"the whole {args.count}-integral batch per step on {cores} host cores "
+                                       f"(node state, P=16)"},
             "e2e": {"value": value, "unit": "integrals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -534,20 +618,20 @@ def extra_improved_rule(torch, mdi):
             "plain_ms": ms_p, "plain_rel_err": abs(vp.item() - exact) / exact, "plain_df64_ms": ms_pd}
 
 
-def extra_batch_size_sweep(torch, mdi, inputs, counts=(4096, 16384, 65536)):
-    """The batched DF64 launch on larger batches of the same distribution (seed 0):
+def extra_batch_size_sweep(torch, mdi, inputs, precision, counts=(4096, 16384, 65536)):
+    """The batched launch on larger batches of the same distribution (seed 0):
     integrals/s as the persistent launch's tail (its largest integrals finishing
     alone) weighs less.  Context beside the configured 4096-integral step."""
     from paper_2404_08867_gb300.tuning import BatchedMDILR
     rows = []
     for count in counts:
         b = inputs.batch(count=count, seed=0)
-        plan = BatchedMDILR(b.families, b.d, b.a, b.n_last, b.offsets, b.pool, precision="df64", nodes=P_NODES)
+        plan = BatchedMDILR(b.families, b.d, b.a, b.n_last, b.offsets, b.pool, precision=precision, nodes=P_NODES)
         plan.tune()
         _, ms = event_ms(torch, lambda: plan.launch(), reps=5)
         rows.append({"count": count, "ms": ms, "integrals_per_s": count / (ms * 1e-3),
                      "block": plan.opts.get("block")})
-    return {"workload": "batches of the configured distribution, DF64, tuned shape", "rows": rows}
+    return {"workload": f"batches of the configured distribution, {precision}, tuned shape", "rows": rows}
 
 
 def extra_paper_context(torch, mdi):
@@ -650,33 +734,45 @@ def extra_lattice_search(torch, mdi):
     return res
 
 
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "oracle_workloads.json")
+
+
+def golden_oracle():
+    """The oracle's FP64 values of the fixed extra workloads, stored by
+    tests/golden/make_oracle_workloads.py (which calls only the oracle)."""
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
 def extra_precision(torch, mdi, inputs):
     """d = 50, N = 32, f = cos(2 pi u + sum a_j x_j): every precision mode, closed and
-    node state, its difference from the FP64 mode of the same state (which the
-    parity tests hold to 1e-12 of the FP64 oracle) and its error against the exact
-    integral."""
+    node state, its error against the FP64 oracle's value of the same state and
+    against the exact integral (|f| <= 1: absolute errors)."""
     w = inputs.oscillatory(50, 32, seed=0)
     p = torch.as_tensor(w.params).cuda()
     exact = exact_integral("osc", 50, w.c, w.w)
-    res = {"workload": "d=50, N=32, cos(2 pi u + sum a_j x_j)", "exact": exact}
+    ref = golden_oracle()["precision"]
+    res = {"workload": "d=50, N=32, cos(2 pi u + sum a_j x_j)", "exact": exact, "oracle": ref}
     for state in ("closed", "nodes"):
-        ref = mdi.mdi_lr_integrate("osc", p, 50, 32, state=state, precision="fp64").item()
         for prec in ("fp64", "fp32_eval_fp64", "fp32_eval_df32", "df64"):
             v, ms = event_ms(torch, lambda: mdi.mdi_lr_integrate("osc", p, 50, 32, state=state, precision=prec))
-            res[f"{state}/{prec}"] = {"abs_diff_vs_fp64_mode": abs(v.item() - ref),
+            res[f"{state}/{prec}"] = {"abs_err_vs_oracle": abs(v.item() - ref[state]),
                                       "abs_err_vs_exact": abs(v.item() - exact), "ms": ms}
     return res
 
 
 def extra_differentiation(torch, mdi, inputs):
     """d = 100, N = 16 Gaussian: value and 200-parameter gradient by the adjoint
-    sweep (checkpoints every 10 levels) against central differences of the GPU's
+    sweep (checkpoints every 10 levels) against the FP64 oracle's derivative of the
+    same rule (component by component), against central differences of the GPU's
     FP64 forward sweep (h = 1e-6, 400 forward calls) and the exact gradient."""
     w = inputs.gaussian(100, 16, seed=0)
     p = torch.as_tensor(w.params).cuda()
     (val, g), ms = event_ms(torch, lambda: mdi.mdi_lr_grad("gauss", p, 100, 16, 16, state="nodes", checkpoint=10))
     _, fwd_ms = event_ms(torch, lambda: mdi.mdi_lr_integrate("gauss", p, 100, 16, state="nodes"))
     g = g.cpu().numpy()
+    ref = golden_oracle()["differentiation"]
+    gref = np.array(ref["grad"])
     h, base = 1e-6, w.params.copy()
     fd = np.empty(2 * 100)
     for i in range(2 * 100):
@@ -688,6 +784,8 @@ def extra_differentiation(torch, mdi, inputs):
         fd[i] = (fu - fdn) / (2 * h)
     exact = exact_gauss_grad(100, w.c, w.w)
     return {"workload": "d=100, N=16 Gaussian, 200 parameters, checkpoint 10", "adjoint_ms": ms, "forward_ms": fwd_ms,
+            "grad_max_componentwise_rel_err_vs_oracle": float(np.max(np.abs(g - gref) / np.abs(gref))),
+            "value_rel_err_vs_oracle": abs(val.item() - ref["value"]) / abs(ref["value"]),
             "grad_err_vs_central_fd_normwise": float(np.max(np.abs(g - fd)) / np.max(np.abs(fd))),
             "grad_diff_vs_exact_normwise": float(np.max(np.abs(g - exact)) / np.max(np.abs(exact))),
             "value_rel_err_vs_exact": abs(val.item() - exact_integral("gauss", 100, w.c, w.w)) /
@@ -696,10 +794,12 @@ def extra_differentiation(torch, mdi, inputs):
 
 def extra_scale(torch, mdi, inputs):
     """d in {100, 250, 500, 1000}, N = 16, f = exp(sum x_j/j^2): forward and adjoint
-    in the closed and node states; fitted exponent of time ~ d^beta."""
+    in the closed and node states; fitted exponent of time ~ d^beta; each forward
+    value's error against the FP64 oracle's."""
     res = {"workload": "N=16, f=exp(sum x_j/j^2)"}
+    ref = golden_oracle()["scale"]
     for state in ("closed", "nodes"):
-        ds, fw, ad = [], [], []
+        ds, fw, ad, err = [], [], [], []
         for d in (100, 250, 500, 1000):
             w = inputs.scale_exp(d, 16)
             p = torch.as_tensor(w.params).cuda()
@@ -708,12 +808,174 @@ def extra_scale(torch, mdi, inputs):
             ds.append(d)
             fw.append(f_ms)
             ad.append(a_ms)
+            err.append(abs(v.item() / ref[str(d)][state] - 1.0))
             if d == 1000:
                 exact = exact_integral("exp", d, w.c, w.w)
                 res[f"{state}/d1000_rel_err_vs_exact"] = abs(v.item() - exact) / exact
         beta = lambda t: float(np.polyfit(np.log(ds), np.log(t), 1)[0])
-        res[state] = {"d": ds, "forward_ms": fw, "adjoint_ms": ad, "forward_beta": beta(fw), "adjoint_beta": beta(ad)}
+        res[state] = {"d": ds, "forward_ms": fw, "adjoint_ms": ad, "forward_beta": beta(fw), "adjoint_beta": beta(ad),
+                      "forward_rel_err_vs_oracle": err}
     return res
+
+
+def measure_peaks(torch, mdi, reps=3):
+    """FMA throughput of this GPU at its current clock, from the library's probe
+    kernel (16 independent FMA chains per thread, several CTAs per SM): the best
+    of `reps` launches, timed with CUDA events.  TFLOP/s, an FMA counting 2."""
+    out = {}
+    for kind, iters in (("fp64", 2048), ("fp32", 65536)):
+        threads = mdi.mdi_peak_probe_threads(kind)
+        sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+        mdi.mdi_peak_probe(kind, 64, sink)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            mdi.mdi_peak_probe(kind, iters, sink)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        out[kind] = {"tflops": threads * 32.0 * iters / (best * 1e-3) / 1e12, "ms": best, "threads": threads,
+                     "fma_per_thread": 16 * iters}
+    return out
+
+
+def time_plan(torch, plan, flush, stream, steps):
+    """CUDA-event times (ms) of `steps` graph replays of a batched plan, L2 flushed
+    before each."""
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return ts
+
+
+def roofline_entry(b, precision, kernel_ms, peaks, traffic=None):
+    """Roofline of one batched launch: the algorithmic flops of the survey's count
+    (d N (P C_phi + P^2) per integral) over the launch's time, against the measured
+    FMA peak of the pipe the mode runs on (FP64 for the FP64 mode, FP32 for the
+    double-float and single-precision-evaluation modes); impl_flops is what the
+    kernel's own formulation executes (the paired interpolation, and double-float
+    primitives counted in float operations)."""
+    flops = alg_flops(b)
+    achieved = flops / (kernel_ms / 1e3) / 1e12
+    fp64 = precision in ("fp64", "fp32_eval_fp64")
+    peak = peaks["fp64" if fp64 else "fp32"]["tflops"]
+    impl = fp64_flops(b) if fp64 else df_flops(b, paired=True, float_phi=precision == "fp32_eval_df32")
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "traffic_unit": "DRAM bytes per launch (ncu)", "kernel": "nodes_batched_kernel",
+            "pipe": "FP64" if fp64 else "FP32 (double-float arithmetic)",
+            "peak_source": "measured in this run: mdi_peak_probe (" + ("DFMA" if fp64 else "FFMA") + "), of measured",
+            "peak_from_unit_counts": FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS,
+            "flops_per_launch": flops, "flops_formula": "sum_i d_i N_i (P C_phi + P^2), P = 16",
+            "c_phi": {f: C_PHI[f] for f in sorted(set(b.families))}, "kernel_ms": kernel_ms,
+            "impl_flops_per_launch": impl, "impl_tflops": impl / (kernel_ms / 1e3) / 1e12}
+
+
+def max_rel_err(got, ref):
+    return float(np.max(np.abs(np.asarray(got) - ref) / np.abs(ref)))
+
+
+# ---------------------------------------------------------------------------
+# Named workloads for profilers (``python bench.py --case NAME --repeats R``): each
+# runs R times through the public API on the seeded synthetic inputs.
+# ---------------------------------------------------------------------------
+def _case_batch(precision, block):
+    from paper_2404_08867_gb300 import inputs
+    from paper_2404_08867_gb300.tuning import BatchedMDILR
+    b = inputs.batch(count=COUNT, seed=0)
+    plan = BatchedMDILR(b.families, b.d, b.a, b.n_last, b.offsets, b.pool, precision=precision, nodes=P_NODES)
+    plan.opts.update(block=block, table_in_l1=1)
+    return plan.launch
+
+
+def build_case(name):
+    """The launch function of a named workload:
+      batch-fp64      4096-integral batch, FP64 node state (block 64, table via L1)
+      batch-df64      the same batch, double-float node state (block 32, table via L1)
+      batch-f32df     the same batch, phi in float, double-float sums (block 32)
+      levels-d1000    one integral, node state parallel over levels, d = 1000, N = 16:
+                      forward and adjoint
+      korobov         P_2 Korobov search, n = 65536, d = 4, every a in 1..n/2
+      cbc             CBC, n = 65536, d = 4, gamma_j = 1/j^2, unanchored
+      midpoint-d1000  paper-table mode, d = 1000, N = 20, n_last = 21 (Gaussian)
+      closed-d4       closed state forward, f = exp(sum x_j / j), d = 4, a = N = 65536,
+                      double-float cluster sums (time to 1e-6 of the small workload)
+      closed-d4-fp64  the same in FP64
+      closed-d1000    closed state forward, exp(sum x_j / j^2), d = 1000, N = 16, FP64
+      slr-d4          plain lattice rule, f = exp(sum x_j / j), d = 4, n = 65536,
+                      Korobov a = 11119 (the small workload's error-scanned parameter)
+      slr-df-d7       plain lattice rule in double-float, f = exp(sum x_j / j), d = 7,
+                      n = 2^24, Korobov a = 12345
+      improved-d7     improved lattice rule, d = 7, z = (1, 16, .., 16^6), n = 1 + 16^7
+                      (16^6 - 1 ghosts), f = exp(sum x_j / j)
+      improved-d7-df64  the same with the lattice points in double-float"""
+    import torch
+    import paper_2404_08867_gb300 as mdi
+    from paper_2404_08867_gb300 import inputs
+    if name == "batch-fp64":
+        return _case_batch("fp64", 64)
+    if name == "batch-df64":
+        return _case_batch("df64", 32)
+    if name == "batch-f32df":
+        return _case_batch("fp32_eval_df32", 32)
+    if name == "levels-d1000":
+        w = inputs.scale_exp(1000, 16)
+        p = torch.as_tensor(w.params).cuda()
+        return lambda: (mdi.mdi_lr_integrate("exp", p, 1000, 16, state="nodes"),
+                        mdi.mdi_lr_grad("exp", p, 1000, 16, 16, state="nodes"))
+    if name == "korobov":
+        vals = torch.empty(32768, dtype=torch.float64, device="cuda")
+        return lambda: mdi.lattice_korobov_search(65536, 4, a_first=1, count=32768, values=vals)
+    if name == "cbc":
+        g = torch.as_tensor(1.0 / np.arange(1, 5) ** 2).cuda()
+        ws = torch.empty(mdi.lattice_cbc_workspace_size(65536), dtype=torch.uint8, device="cuda")
+        return lambda: mdi.lattice_cbc(65536, g, 0.0, workspace=ws)
+    if name == "midpoint-d1000":
+        w = inputs.gaussian(1000, 20, seed=0)
+        p = torch.as_tensor(w.params).cuda()
+        return lambda: mdi.mdi_midpoint_integrate("gauss", p, 1000, 20, 21)
+    if name in ("closed-d4", "closed-d4-fp64"):
+        p = torch.as_tensor(inputs.small_exp(4).params).cuda()
+        prec = "fp64" if name.endswith("fp64") else "df64"
+        return lambda: mdi.mdi_lr_integrate("exp", p, 4, 65536, 65536, state="closed", precision=prec)
+    if name == "closed-d1000":
+        p = torch.as_tensor(inputs.scale_exp(1000, 16).params).cuda()
+        return lambda: mdi.mdi_lr_integrate("exp", p, 1000, 16, 16, state="closed")
+    if name == "slr-d4":
+        p = torch.as_tensor(inputs.small_exp(4).params).cuda()
+        z = mdi.korobov_vector(4, 11119, 65536)
+        return lambda: mdi.lattice_rule_integrate("exp", p, 65536, z)
+    if name == "slr-df-d7":
+        p = torch.as_tensor(inputs.small_exp(7).params).cuda()
+        z = mdi.korobov_vector(7, 12345, 1 << 24)
+        return lambda: mdi.lattice_rule_integrate("exp", p, 1 << 24, z, precision="df64")
+    if name in ("improved-d7", "improved-d7-df64"):
+        d, a = 7, 16
+        prec = "df64" if name.endswith("df64") else "fp64"
+        p = torch.as_tensor(np.r_[1.0 / np.arange(1, d + 1), np.zeros(d)]).cuda()
+        ws = torch.empty(mdi.lattice_rule_improved_workspace_size(d, 1 + a ** d, a), dtype=torch.uint8,
+                         device="cuda")
+        out = torch.empty(1, dtype=torch.float64, device="cuda")
+        return lambda: mdi.lattice_rule_integrate_improved("exp", p, d, 1 + a ** d, a, precision=prec, out=out,
+                                                           workspace=ws)
+    raise SystemExit(f"unknown case {name!r}; see build_case")
+
+
+def run_case(name, repeats):
+    import torch
+    run = build_case(name)
+    for _ in range(repeats):
+        run()
+    torch.cuda.synchronize()
+    print(f"{name}: {repeats} runs ok")
 
 
 def main():
@@ -723,7 +985,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.impl == "reference":
-        return run_reference(args, rank, world)
+        return cpu_reference_arm(args, rank, world)
+    if args.case:
+        return run_case(args.case, args.repeats)
 
     import torch
     import torch.distributed as dist
@@ -755,6 +1019,8 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.4)
+    # FMA peaks at this clock, inside the sampled window, before the timed steps.
+    peaks = measure_peaks(torch, mdi)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier()
@@ -802,25 +1068,7 @@ def main():
 
     if rank == 0:
         kernel_ms = statistics.mean(step_ms)
-        if args.precision in ("df64", "fp32_eval_df32"):
-            flops = df_flops(b, paired=True, float_phi=args.precision == "fp32_eval_df32")
-            achieved = flops / (kernel_ms / 1e3) / 1e12
-            roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP32_PEAK_TFLOPS, "traffic": profiled_traffic(args.precision),
-                    "traffic_unit": "bytes per launch (ncu)", "kernel": "nodes_batched_kernel",
-                    "pipe": "FP32 (double-float arithmetic)",
-                    "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2 x 2.07 GHz",
-                    "flops_per_launch": flops, "kernel_ms": kernel_ms,
-                    "fp64_equivalent_tflops": fp64_flops(b) / (kernel_ms / 1e3) / 1e12,
-                    "fp64_peak_tflops": FP64_PEAK_TFLOPS}
-        else:
-            flops = fp64_flops(b)
-            achieved = flops / (kernel_ms / 1e3) / 1e12
-            roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": profiled_traffic(args.precision),
-                    "traffic_unit": "bytes per launch (ncu)", "kernel": "nodes_batched_kernel",
-                    "pipe": "FP64", "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
-                    "flops_per_launch": flops, "kernel_ms": kernel_ms}
+        roof = roofline_entry(b, args.precision, kernel_ms, peaks, profiled_traffic(args.precision))
         dtype = {"df64": "f32x2 (double-float, FP64-class)", "fp64": "f64", "fp32_eval_fp64": "f32 eval + f64",
                  "fp32_eval_df32": "f32 eval + f32x2"}[args.precision]
         line = {"metric": METRIC, "value": value, "unit": "integrals/s", "n_gpus": world, "steps": args.steps,
@@ -832,27 +1080,24 @@ def main():
                 "e2e": {"value": e2e_value, "unit": "integrals/s",
                         "h2d_bytes_per_step": int(h_in.numel()),
                         "d2h_bytes_per_step": int(8 * h_out.numel())},
-                "roofline": roof, "clocks": clocks, "wall_s_timed_region": wall}
+                "roofline": roof, "measured_peaks": peaks, "clocks": clocks, "wall_s_timed_region": wall}
+        # The other arithmetic modes on the same batch (secondary entries).
+        modes_out = {}
         if not args.no_extras:
-            if args.precision != "fp64":
-                fp = BatchedMDILR(b.families, b.d, b.a, b.n_last, b.offsets, b.pool, precision="fp64", nodes=P_NODES)
-                ft = fp.tune()
-                fp.capture()
-                fms_list = []
-                for _ in range(10):
-                    flush.zero_()
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    fp.run()
-                    e1.record(stream)
-                    torch.cuda.synchronize()
-                    fms_list.append(e0.elapsed_time(e1))
-                fms = statistics.median(fms_list)
-                fl = fp64_flops(b) / (fms / 1e3) / 1e12
-                line["fp64_mode"] = {"ms_per_step": fms, "integrals_per_s": len(b) / (fms / 1e3),
-                                     "fp64_tflops": fl, "frac_of_fp64_peak": fl / FP64_PEAK_TFLOPS,
-                                     "block": ft["block"], "table_in_l1": ft["table_in_l1"],
-                                     "max_abs_diff_vs_headline": float((fp.out - device_out).abs().max())}
+            modes = {}
+            for prec in ("fp64", "df64", "fp32_eval_df32", "fp32_eval_fp64"):
+                if prec == args.precision:
+                    continue
+                mp_ = BatchedMDILR(b.families, b.d, b.a, b.n_last, b.offsets, b.pool, precision=prec, nodes=P_NODES)
+                mt = mp_.tune()
+                mp_.capture()
+                ms = statistics.median(time_plan(torch, mp_, flush, stream, 10))
+                modes_out[prec] = mp_.out.cpu().numpy()
+                modes[prec] = {"ms_per_step": ms, "integrals_per_s": len(b) / (ms / 1e3), "block": mt["block"],
+                               "table_in_l1": mt["table_in_l1"],
+                               "roofline": {k: v for k, v in roofline_entry(b, prec, ms, peaks).items()
+                                            if k in ("achieved", "peak", "frac", "pipe", "impl_tflops")}}
+            line["modes"] = modes
             line["small_workload"] = extra_small_workload(torch, mdi, inputs)
             line["precision_workload"] = extra_precision(torch, mdi, inputs)
             line["differentiation_workload"] = extra_differentiation(torch, mdi, inputs)
@@ -863,10 +1108,20 @@ def main():
             line["batch_vs_plain_kernel"] = extra_batch_vs_plain(torch, mdi, inputs)
             line["improved_rule"] = extra_improved_rule(torch, mdi)
             line["time_to_1e-6_vs_d"] = extra_time_to_1e6_vs_d(torch, mdi, inputs)
-            line["batch_size_sweep"] = extra_batch_size_sweep(torch, mdi, inputs)
-        rate, n_done, secs = cpu_oracle_sample(b, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": rate, "unit": "integrals/s", "cores": 1, "kind": "oracle",
-                                "sample": f"first {n_done} integrals of the batch, {secs:.1f} s single-threaded"}
+            line["batch_size_sweep"] = extra_batch_size_sweep(torch, mdi, inputs, args.precision)
+        # CPU baseline: the FP64 oracle on every host core (whole passes over this
+        # batch), and on one core; the all-core pass also gives the oracle's value of
+        # every integral, against which each mode's largest error is stated.
+        ref, rate, cores, passes, secs = cpu_baseline_all_cores(len(b), rank, args.cpu_seconds)
+        rate1, n1, secs1 = cpu_baseline_one_core(b, min(3.0, args.cpu_seconds))
+        line["cpu_baseline"] = {"value": rate, "unit": "integrals/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{passes} passes over the {len(b)}-integral batch on {cores} host cores "
+                                          f"in {secs:.1f} s",
+                                "one_core": {"value": rate1, "unit": "integrals/s", "cores": 1,
+                                             "sample": f"first {n1} integrals of the batch, {secs1:.1f} s"}}
+        line["max_rel_err_vs_oracle"] = max_rel_err(device_out.cpu().numpy(), ref)
+        for prec, out in modes_out.items():
+            line["modes"][prec]["max_rel_err_vs_oracle"] = max_rel_err(out, ref)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

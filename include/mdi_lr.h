@@ -148,6 +148,13 @@ mdi_status lattice_rule_integrate(int32_t family, int32_t d, int64_t n, const in
                                   void *workspace, size_t ws_bytes, mdi_stream_t stream);
 mdi_status lattice_rule_workspace_size(int32_t d, int64_t n, size_t *bytes);
 
+/* Example 2's Korobov generating vector, z_i = a^(i-1) mod n for i = 1..d, in exact
+ * integer arithmetic (128-bit products), written to z (HOST, d int64): the z that
+ * lattice_rule_integrate and lattice_rule_integrate_shifted take for a Korobov
+ * lattice.  Host only, nothing is enqueued.  MDI_EINVAL unless 1 <= d, 1 <= n < 2^63,
+ * 0 <= a and z != NULL. */
+mdi_status lattice_korobov_vector(int32_t d, int64_t a, int64_t n, int64_t *z);
+
 /* lattice_rule_integrate without a workspace, for callers that cannot allocate
  * device memory when they call (for instance code inside an application that
  * reserves all GPU memory at start-up and forbids later allocation, or a plug-in
@@ -162,7 +169,10 @@ mdi_status lattice_rule_workspace_size(int32_t d, int64_t n, size_t *bytes);
  *     (with that device current); make that first call before any stream capture.
  *   - All calls share the array.  Each call overwrites every slot it reads, so no
  *     clearing is needed, but calls that overlap on the GPU (other streams, other
- *     host threads) race on it and must be serialised by the caller. */
+ *     host threads) race on it and must be serialised by the caller.
+ *   - The looked-up address is kept for the life of the process: after a
+ *     cudaDeviceReset on a device, this entry point must not be called on it
+ *     again. */
 mdi_status lattice_rule_integrate_noalloc(int32_t family, int32_t d, int64_t n, const int64_t *z,
                                           const double *params, int32_t precision, double *out,
                                           mdi_stream_t stream);
@@ -189,6 +199,14 @@ mdi_status lattice_rule_integrate_shifted(int32_t family, int32_t d, int64_t n, 
                                           int32_t precision, double *out, void *workspace, size_t ws_bytes,
                                           mdi_stream_t stream);
 mdi_status lattice_rule_shifted_workspace_size(int32_t d, int64_t n, int32_t R, size_t *bytes);
+
+/* The estimate of Section 2.1 from R replicates of the randomly shifted rule:
+ *     mean_se[0] = (1/R) sum_r values[r],
+ *     mean_se[1] = sqrt(sum_r (values[r] - mean)^2 / (R (R - 1)))   (0 for R = 1),
+ * the integral's estimate and its standard error.  values and mean_se are DEVICE
+ * pointers (R and 2 doubles); one single-CTA launch on `stream` with fixed-order
+ * sums.  MDI_EINVAL unless 1 <= R <= 65535 and both pointers are non-NULL. */
+mdi_status lattice_shifted_estimate(const double *values, int32_t R, double *mean_se, mdi_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Improved lattice rule (Definition 3.3, Section 2.2.2) for the Korobov vector
@@ -219,17 +237,27 @@ mdi_status lattice_rule_integrate_improved(int32_t family, int32_t d, int64_t n,
 mdi_status lattice_rule_improved_workspace_size(int32_t d, int64_t n, int64_t a, size_t *bytes);
 
 /* ---------------------------------------------------------------------------
- * MDI-LR, Algorithm 2 (Section 4) with m = 1 on the Korobov lattice.
+ * MDI-LR, Algorithm 2 (Section 4) with m = 1 on the Korobov lattice.  The
+ * algorithm's inputs are f, Omega = [0,1]^d, d, the Korobov parameter a and n;
+ * its generating vector is Example 2's z = (1, a, ..., a^(d-1)) mod n.
  *   d        dimension, >= 1 (EXACT: n <= 2^40; CLOSED: d <= 2^20; NODES: d <= 2^20)
  *   a        Korobov parameter = points per transformed axis 1..d-1, a >= 1
  *            (NODES: a <= 64, EXACT: a <= 4096)
  *   n_last   points on the last transformed axis (n_d of eq. (3.5)), >= 1;
  *            n = n_last * a^(d-1); Lemma 3.2's equal-N case is n_last = a
+ *   z        HOST, d int64 entries, or NULL.  NULL means Example 2's Korobov vector
+ *            for (a, n), which MDI-LR never forms (for large d, n exceeds every
+ *            integer type; the sweep works on the digits of the transformed grid).
+ *            A non-NULL z is checked against that vector: n must be below 2^63
+ *            (MDI_EOVERFLOW otherwise: such a z cannot be written in int64), and
+ *            z_i must equal a^(i-1) mod n for every i (MDI_EUNSUPPORTED otherwise:
+ *            another vector needs the ghost points of Definition 3.3, see
+ *            lattice_rule_integrate_improved, or the plain rule).
  *   params   DEVICE, 2*d doubles
  *   opts     HOST, may be NULL (all defaults)
  *   out      DEVICE, 1 double
  * ------------------------------------------------------------------------- */
-mdi_status mdi_lr_integrate(int32_t family, int32_t d, int64_t a, int64_t n_last,
+mdi_status mdi_lr_integrate(int32_t family, int32_t d, int64_t a, int64_t n_last, const int64_t *z,
                             const double *params, const mdi_opts *opts, double *out,
                             void *workspace, size_t ws_bytes, mdi_stream_t stream);
 mdi_status mdi_lr_workspace_size(int32_t family, int32_t d, int64_t a, int64_t n_last,
@@ -243,6 +271,7 @@ mdi_status mdi_lr_workspace_size(int32_t family, int32_t d, int64_t a, int64_t n
  *            the rest of the second half is 0.  Q is the rule's own value, so this
  *            is the exact derivative of the computed number, not of the integral.
  *   value    DEVICE, 1 double, or NULL: receives Q as well.
+ *   z        HOST or NULL, checked as for mdi_lr_integrate.
  *   opts     state CLOSED (EXP, OSC) or NODES (any family; AUTO picks as in
  *            mdi_lr_integrate); precision must be MDI_PREC_FP64.
  * CLOSED: the levels run in reverse as an affine recurrence, dQ/dc_k =
@@ -253,9 +282,9 @@ mdi_status mdi_lr_workspace_size(int32_t family, int32_t d, int64_t a, int64_t n
  * and each level's contribution is then formed in parallel after recomputing its
  * states from the nearest checkpoints.
  * ------------------------------------------------------------------------- */
-mdi_status mdi_lr_grad(int32_t family, int32_t d, int64_t a, int64_t n_last, const double *params,
-                       const mdi_opts *opts, double *value, double *grad, void *workspace, size_t ws_bytes,
-                       mdi_stream_t stream);
+mdi_status mdi_lr_grad(int32_t family, int32_t d, int64_t a, int64_t n_last, const int64_t *z,
+                       const double *params, const mdi_opts *opts, double *value, double *grad, void *workspace,
+                       size_t ws_bytes, mdi_stream_t stream);
 mdi_status mdi_lr_grad_workspace_size(int32_t family, int32_t d, int64_t a, int64_t n_last,
                                       const mdi_opts *opts, size_t *bytes);
 
@@ -293,23 +322,48 @@ mdi_status mdi_lr_batched_prepare(const mdi_opts *opts, void *workspace, size_t 
  *              them up (from mdi_batch_plan), or NULL for 0..count-1
  *   count      number of integrals, >= 1
  *   param_pool DEVICE doubles
+ *   pool_len   number of doubles in param_pool: descriptor i reads
+ *              param_pool[param_offset, param_offset + 2 d), which must lie inside it
  *   out        DEVICE, count doubles; out[i] belongs to descs[i]
  *   workspace  prepared by mdi_lr_batched_prepare with the same nodes/precision
  * One kernel launch: a persistent grid of CTAs takes integrals from an atomic
- * counter in the workspace; the last CTA to finish re-arms the counter.  A
- * descriptor outside the limits above, an order entry outside 0..count-1 (that
- * entry only) or an unprepared workspace yields NaN in the affected outputs. */
+ * counter in the workspace; the last CTA to finish re-arms the counter.  The
+ * descriptors live in device memory, so the host cannot check them: the kernel
+ * does.  A descriptor outside the limits above, or whose parameters leave the
+ * pool, yields NaN in its output and sets a flag in the workspace's device status
+ * word; an order entry outside 0..count-1 is skipped (that entry only) and flagged;
+ * an unprepared workspace yields NaN everywhere and is flagged.  Read and clear the
+ * flags with mdi_get_device_status. */
 mdi_status mdi_lr_integrate_batched(const mdi_batch_desc *descs, const int32_t *order, int32_t count,
-                                    const double *param_pool, const mdi_opts *opts, double *out,
+                                    const double *param_pool, int64_t pool_len, const mdi_opts *opts, double *out,
                                     void *workspace, size_t ws_bytes, mdi_stream_t stream);
 mdi_status mdi_lr_batched_workspace_size(int32_t count, const mdi_opts *opts, size_t *bytes);
 
 /* Host-side scheduler: writes into order (HOST, count int32) a processing order
  * for mdi_lr_integrate_batched -- longest estimated work first, ties grouped by a
  * so that consecutive pick-ups share their interpolation table.  descs is a HOST
- * copy of the descriptor table.  Returns MDI_EINVAL on an invalid descriptor. */
-mdi_status mdi_batch_plan(const mdi_batch_desc *descs, int32_t count, const mdi_opts *opts,
+ * copy of the descriptor table; pool_len the number of doubles of the parameter
+ * pool the batch will read.  Returns MDI_EINVAL on an invalid descriptor or one
+ * whose 2*d parameters leave the pool. */
+mdi_status mdi_batch_plan(const mdi_batch_desc *descs, int32_t count, int64_t pool_len, const mdi_opts *opts,
                           int32_t *order);
+
+/* Flags of the device status word of a batched workspace (bitwise OR). */
+#define MDI_DEV_BAD_DESC 1u    /* a descriptor outside the limits (its output is NaN) */
+#define MDI_DEV_BAD_ORDER 2u   /* an order entry outside 0..count-1 (skipped) */
+#define MDI_DEV_UNPREPARED 4u  /* the workspace was not prepared for these opts (NaN) */
+#define MDI_DEV_POOL_RANGE 8u  /* a descriptor's parameters leave the pool (NaN) */
+
+/* Reads the device status word of a workspace prepared by mdi_lr_batched_prepare:
+ * enqueues a 4-byte device-to-host copy on `stream` and waits for the stream (this
+ * call, unlike the compute calls, synchronises, so it cannot be captured in a CUDA
+ * graph).  With clear != 0 the word is zeroed afterwards, in stream order.
+ *   flags   HOST, may be NULL: receives the MDI_DEV_* bits seen since the
+ *           preparation or the last clear
+ * Returns MDI_OK when no flag is set, MDI_EINVAL when one is (or for a NULL,
+ * misaligned or short workspace), MDI_ECUDA if the copy fails. */
+mdi_status mdi_get_device_status(const void *workspace, size_t ws_bytes, int32_t clear, uint32_t *flags,
+                                 mdi_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Paper-table mode for the ridge integrand f(x) = (c0 + sum_i x_i)^(-power) of
@@ -403,12 +457,29 @@ mdi_status mdi_midpoint_workspace_size(int32_t d, int64_t N, int64_t n_last, siz
 mdi_status mdi_debug_lattice_indices(int32_t d, int64_t n, const int64_t *z, int64_t j0,
                                      int64_t count, int64_t *r_out, mdi_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Measurement aid (the paper has no counterpart): a dependency-free fused
+ * multiply-add loop that keeps one arithmetic pipe busy, so that a benchmark can
+ * measure the pipe's throughput on the running GPU and clock.
+ *   kind   0: FP64 (DFMA), 1: FP32 (FFMA)
+ *   iters  loop trips per thread, 1..2^20; each trip issues 16 independent FMAs
+ *   sink   DEVICE, one double; written only if the chains' sum hits a value it
+ *          never reaches, a condition the compiler cannot decide, so every FMA
+ *          must run
+ * One launch of mdi_peak_probe_threads(kind) threads on `stream`, each doing
+ * 16 * iters FMAs, i.e. 32 * iters flops per thread.  MDI_EINVAL for a bad kind,
+ * iters or sink.
+ * ------------------------------------------------------------------------- */
+mdi_status mdi_peak_probe(int32_t kind, int32_t iters, double *sink, mdi_stream_t stream);
+/* Threads one mdi_peak_probe launch runs on the current device (0 for a bad kind). */
+int64_t mdi_peak_probe_threads(int32_t kind);
+
 const char *mdi_status_string(mdi_status status);
 /* Text of the last CUDA error seen by this library on the calling host thread. */
 const char *mdi_last_cuda_error(void);
 /* ABI version of this header (bumped on any incompatible change). */
 int32_t mdi_abi_version(void);
-#define MDI_ABI_VERSION 1
+#define MDI_ABI_VERSION 2
 
 #ifdef __cplusplus
 }

@@ -28,7 +28,7 @@ __all__ = [
     "mdi_midpoint_integrate", "mdi_midpoint_workspace_size", "mdi_midpoint_ridge", "lattice_korobov_search", "lattice_cbc",
     "lattice_cbc_workspace_size", "lattice_korobov_search_workspace_size", "lattice_rule_integrate_shifted", "lattice_rule_shifted_workspace_size",
     "lattice_rule_integrate_improved", "lattice_rule_improved_workspace_size", "korobov_vector",
-    "shifted_estimate",
+    "shifted_estimate", "mdi_get_device_status", "mdi_peak_probe", "mdi_peak_probe_threads",
 ]
 
 
@@ -137,12 +137,12 @@ def lattice_rule_integrate_shifted(family, params: torch.Tensor, n: int, z: Sequ
 
 def korobov_vector(d: int, a: int, n: int) -> np.ndarray:
     """The Korobov generating vector of Example 2, z_j = a^(j-1) mod n (j = 1..d),
-    in exact integer arithmetic: the z argument of the lattice-rule calls."""
-    z, v = [], 1 % int(n)
-    for _ in range(int(d)):
-        z.append(v)
-        v = v * int(a) % int(n)
-    return np.asarray(z, dtype=np.int64)
+    from the library's exact integer routine: the z argument of the lattice-rule
+    calls (int64 numpy array)."""
+    z = np.zeros(int(d), dtype=np.int64)
+    _ffi.check(_ffi.load().lattice_korobov_vector(int(d), int(a), int(n), z.ctypes.data_as(ctypes.c_void_p)),
+               "lattice_korobov_vector")
+    return z
 
 
 def lattice_rule_improved_workspace_size(d: int, n: int, a: int) -> int:
@@ -176,13 +176,17 @@ def lattice_rule_integrate_improved(family, params: torch.Tensor, d: int, n: int
     return out, ng.value
 
 
-def shifted_estimate(values: torch.Tensor):
-    """(mean, standard error) of R shifted-rule replicates: the estimate of the
-    integral and of its error (sample standard deviation / sqrt(R))."""
-    R = values.numel()
-    mean = values.mean()
-    se = values.std(correction=1) / (R ** 0.5) if R > 1 else torch.zeros_like(mean)
-    return mean, se
+def shifted_estimate(values: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None):
+    """(mean, standard error) of R shifted-rule replicates (a float64 CUDA tensor),
+    computed on the device by the library: the estimate of the integral and of its
+    error.  Returns two 0-dim views of one 2-element float64 CUDA tensor."""
+    _dev_f64(values, "values")
+    if out is None:
+        out = torch.empty(2, dtype=torch.float64, device=values.device)
+    _ffi.check(_ffi.load().lattice_shifted_estimate(ctypes.c_void_p(values.data_ptr()), int(values.numel()),
+                                                    ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+               "lattice_shifted_estimate")
+    return out[0], out[1]
 
 
 def lattice_rule_integrate_noalloc(family, params: torch.Tensor, n: int, z: Sequence[int], precision="fp64",
@@ -218,12 +222,22 @@ def mdi_lr_workspace_size(family, d: int, a: int, n_last: int, **opts) -> int:
     return b.value
 
 
+def _host_z(z):
+    """(keep-alive array, pointer) of an optional host generating vector."""
+    if z is None:
+        return None, ctypes.c_void_p(0)
+    zz = np.ascontiguousarray(np.asarray(z, dtype=np.int64))
+    return zz, zz.ctypes.data_as(ctypes.c_void_p)
+
+
 def mdi_lr_integrate(family, params: torch.Tensor, d: int, a: int, n_last: Optional[int] = None,
                      out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None, stream=None,
-                     **opts) -> torch.Tensor:
+                     z: Optional[Sequence[int]] = None, **opts) -> torch.Tensor:
     """MDI-LR value on the Korobov lattice with a points per transformed axis and
-    n_last (default a) on the last one; opts: state, precision, nodes, block,
-    ctas_per_sm.  Returns a 1-element float64 CUDA tensor."""
+    n_last (default a) on the last one; ``z`` (optional) is Algorithm 2's
+    generating vector, which must be Example 2's Korobov vector for (a, n); opts:
+    state, precision, nodes, block, ctas_per_sm.  Returns a 1-element float64 CUDA
+    tensor."""
     _dev_f64(params, "params")
     n_last = a if n_last is None else n_last
     if params.numel() < 2 * d:
@@ -231,8 +245,9 @@ def mdi_lr_integrate(family, params: torch.Tensor, d: int, a: int, n_last: Optio
     if out is None:
         out = torch.empty(1, dtype=torch.float64, device=params.device)
     o = _opts(**opts)
+    zz, zp = _host_z(z)
     ws = _workspace(mdi_lr_workspace_size(family, d, a, n_last, **opts), params.device, workspace)
-    st = _ffi.load().mdi_lr_integrate(_fam(family), d, a, n_last, ctypes.c_void_p(params.data_ptr()),
+    st = _ffi.load().mdi_lr_integrate(_fam(family), d, a, n_last, zp, ctypes.c_void_p(params.data_ptr()),
                                       ctypes.byref(o), ctypes.c_void_p(out.data_ptr()),
                                       ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
     _ffi.check(st, "mdi_lr_integrate")
@@ -249,7 +264,7 @@ def mdi_lr_grad_workspace_size(family, d: int, a: int, n_last: int, **opts) -> i
 
 def mdi_lr_grad(family, params: torch.Tensor, d: int, a: int, n_last: Optional[int] = None,
                 value: Optional[torch.Tensor] = None, grad: Optional[torch.Tensor] = None,
-                workspace: Optional[torch.Tensor] = None, stream=None, **opts):
+                workspace: Optional[torch.Tensor] = None, stream=None, z: Optional[Sequence[int]] = None, **opts):
     """(value, grad): the MDI-LR value and its derivative with respect to the 2*d
     parameters, from the adjoint sweep on the GPU (FP64).  opts: state
     ("auto", "closed", "nodes"), nodes, checkpoint."""
@@ -260,8 +275,9 @@ def mdi_lr_grad(family, params: torch.Tensor, d: int, a: int, n_last: Optional[i
     if grad is None:
         grad = torch.empty(2 * d, dtype=torch.float64, device=params.device)
     o = _opts(**opts)
+    zz, zp = _host_z(z)
     ws = _workspace(mdi_lr_grad_workspace_size(family, d, a, n_last, **opts), params.device, workspace)
-    st = _ffi.load().mdi_lr_grad(_fam(family), d, a, n_last, ctypes.c_void_p(params.data_ptr()), ctypes.byref(o),
+    st = _ffi.load().mdi_lr_grad(_fam(family), d, a, n_last, zp, ctypes.c_void_p(params.data_ptr()), ctypes.byref(o),
                                  ctypes.c_void_p(value.data_ptr()), ctypes.c_void_p(grad.data_ptr()),
                                  ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
     _ffi.check(st, "mdi_lr_grad")
@@ -307,13 +323,14 @@ def make_batch_descs(families, ds, as_, n_lasts, param_offsets) -> np.ndarray:
     return descs
 
 
-def mdi_batch_plan(descs: np.ndarray, **opts) -> np.ndarray:
-    """Longest-first processing order computed by the library's host scheduler."""
+def mdi_batch_plan(descs: np.ndarray, pool_len: int, **opts) -> np.ndarray:
+    """Longest-first processing order computed by the library's host scheduler;
+    ``pool_len``: doubles in the parameter pool the batch reads."""
     descs = np.ascontiguousarray(descs, dtype=BATCH_DESC_DTYPE)
     order = np.zeros(descs.size, dtype=np.int32)
     o = _opts(**opts)
-    _ffi.check(_ffi.load().mdi_batch_plan(descs.ctypes.data_as(ctypes.c_void_p), descs.size, ctypes.byref(o),
-                                          order.ctypes.data_as(ctypes.c_void_p)), "mdi_batch_plan")
+    _ffi.check(_ffi.load().mdi_batch_plan(descs.ctypes.data_as(ctypes.c_void_p), descs.size, int(pool_len),
+                                          ctypes.byref(o), order.ctypes.data_as(ctypes.c_void_p)), "mdi_batch_plan")
     return order
 
 
@@ -356,10 +373,37 @@ def mdi_lr_integrate_batched(descs: torch.Tensor, param_pool: torch.Tensor, coun
     o = _opts(**opts)
     st = _ffi.load().mdi_lr_integrate_batched(
         ctypes.c_void_p(descs.data_ptr()), ctypes.c_void_p(order.data_ptr() if order is not None else 0), count,
-        ctypes.c_void_p(param_pool.data_ptr()), ctypes.byref(o), ctypes.c_void_p(out.data_ptr()),
-        ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream(stream))
+        ctypes.c_void_p(param_pool.data_ptr()), int(param_pool.numel()), ctypes.byref(o),
+        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream(stream))
     _ffi.check(st, "mdi_lr_integrate_batched")
     return out
+
+
+def mdi_get_device_status(workspace: torch.Tensor, clear: bool = False, stream=None) -> int:
+    """The MDI_DEV_* flags of a batched workspace's device status word (0: no
+    integral rejected since the preparation or the last clear).  Waits for the
+    stream; ``clear`` zeroes the word afterwards."""
+    flags = ctypes.c_uint32(0)
+    st = _ffi.load().mdi_get_device_status(ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), int(bool(clear)),
+                                           ctypes.byref(flags), _stream(stream))
+    if st not in (_ffi.MDI_OK, _ffi.MDI_EINVAL) or (st == _ffi.MDI_EINVAL and flags.value == 0):
+        _ffi.check(st, "mdi_get_device_status")
+    return flags.value
+
+
+def mdi_peak_probe_threads(kind: str) -> int:
+    """Threads of one mdi_peak_probe launch ("fp64" or "fp32")."""
+    return int(_ffi.load().mdi_peak_probe_threads({"fp64": 0, "fp32": 1}[kind]))
+
+
+def mdi_peak_probe(kind: str, iters: int, sink: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """One launch of the library's FMA throughput probe ("fp64": DFMA, "fp32": FFMA):
+    mdi_peak_probe_threads(kind) threads, 16 * iters FMAs each."""
+    if sink is None:
+        sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    _ffi.check(_ffi.load().mdi_peak_probe({"fp64": 0, "fp32": 1}[kind], int(iters), ctypes.c_void_p(sink.data_ptr()),
+                                          _stream(stream)), "mdi_peak_probe")
+    return sink
 
 
 def mdi_debug_lattice_indices(n: int, z: Sequence[int], j0: int, count: int, device="cuda",

@@ -11,6 +11,9 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libmdilr.so")
 
 MDI_OK, MDI_EINVAL, MDI_EUNSUPPORTED, MDI_EOVERFLOW, MDI_ECUDA, MDI_EWORKSPACE = range(6)
+ABI_VERSION = 2
+# Flags of the batched workspace's device status word (MDI_DEV_*).
+DEV_FLAGS = {"bad_desc": 1, "bad_order": 2, "unprepared": 4, "pool_range": 8}
 FAMILY = {"exp": 0, "osc": 1, "gauss": 2, "peak": 3}
 STATE = {"auto": 0, "exact": 1, "closed": 2, "nodes": 3}
 PRECISION = {"fp64": 0, "fp32_eval_fp64": 1, "fp32_eval_df32": 2, "df64": 3}
@@ -40,14 +43,19 @@ SIGNATURES = {
     "lattice_rule_shifted_workspace_size": (_I32, [_I32, _I64, _I32, _c.POINTER(_SZ)]),
     "lattice_rule_integrate_improved": (_I32, [_I32, _I32, _I64, _I64, _P, _I32, _P, _c.POINTER(_I64), _P, _SZ, _P]),
     "lattice_rule_improved_workspace_size": (_I32, [_I32, _I64, _I64, _c.POINTER(_SZ)]),
-    "mdi_lr_integrate": (_I32, [_I32, _I32, _I64, _I64, _P, _c.POINTER(MdiOpts), _P, _P, _SZ, _P]),
+    "mdi_lr_integrate": (_I32, [_I32, _I32, _I64, _I64, _P, _P, _c.POINTER(MdiOpts), _P, _P, _SZ, _P]),
     "mdi_lr_workspace_size": (_I32, [_I32, _I32, _I64, _I64, _c.POINTER(MdiOpts), _c.POINTER(_SZ)]),
-    "mdi_lr_grad": (_I32, [_I32, _I32, _I64, _I64, _P, _c.POINTER(MdiOpts), _P, _P, _P, _SZ, _P]),
+    "mdi_lr_grad": (_I32, [_I32, _I32, _I64, _I64, _P, _P, _c.POINTER(MdiOpts), _P, _P, _P, _SZ, _P]),
     "mdi_lr_grad_workspace_size": (_I32, [_I32, _I32, _I64, _I64, _c.POINTER(MdiOpts), _c.POINTER(_SZ)]),
-    "mdi_lr_integrate_batched": (_I32, [_P, _P, _I32, _P, _c.POINTER(MdiOpts), _P, _P, _SZ, _P]),
+    "mdi_lr_integrate_batched": (_I32, [_P, _P, _I32, _P, _I64, _c.POINTER(MdiOpts), _P, _P, _SZ, _P]),
     "mdi_lr_batched_workspace_size": (_I32, [_I32, _c.POINTER(MdiOpts), _c.POINTER(_SZ)]),
     "mdi_lr_batched_prepare": (_I32, [_c.POINTER(MdiOpts), _P, _SZ, _P]),
-    "mdi_batch_plan": (_I32, [_P, _I32, _c.POINTER(MdiOpts), _P]),
+    "mdi_batch_plan": (_I32, [_P, _I32, _I64, _c.POINTER(MdiOpts), _P]),
+    "mdi_get_device_status": (_I32, [_P, _SZ, _I32, _c.POINTER(_c.c_uint32), _P]),
+    "lattice_korobov_vector": (_I32, [_I32, _I64, _I64, _P]),
+    "lattice_shifted_estimate": (_I32, [_P, _I32, _P, _P]),
+    "mdi_peak_probe": (_I32, [_I32, _I32, _P, _P]),
+    "mdi_peak_probe_threads": (_I64, [_I32]),
     "mdi_debug_lattice_indices": (_I32, [_I32, _I64, _P, _I64, _I64, _P, _P]),
     "mdi_midpoint_integrate": (_I32, [_I32, _I32, _I64, _I64, _P, _P, _P, _SZ, _P]),
     "lattice_korobov_search": (_I32, [_I32, _I32, _I64, _I64, _I64, _P, _P, _P, _SZ, _P]),
@@ -80,7 +88,7 @@ def load():
                 fn = getattr(lib, name)
                 fn.restype = res
                 fn.argtypes = args
-            if lib.mdi_abi_version() != 1:
+            if lib.mdi_abi_version() != ABI_VERSION:
                 raise RuntimeError("libmdilr.so ABI version mismatch; rebuild it")
             _lib = lib
     return _lib

@@ -74,6 +74,36 @@ static bool desc_ok(const mdi_batch_desc &d) {
          d.n_last <= 4096 && d.param_offset >= 0 && d.reserved == 0;
 }
 
+// The 2*d parameters of a descriptor lie inside a pool of pool_len doubles.
+static bool desc_in_pool(const mdi_batch_desc &d, int64_t pool_len) {
+  return d.param_offset <= pool_len && 2 * (int64_t)d.d <= pool_len - d.param_offset;
+}
+
+// x * y mod m for 0 <= x, y < m < 2^63, exact through a 128-bit product.
+static int64_t mulmod(int64_t x, int64_t y, int64_t m) {
+  return (int64_t)((unsigned __int128)(uint64_t)x * (uint64_t)y % (unsigned __int128)(uint64_t)m);
+}
+
+// A generating vector handed to an MDI-LR call (Algorithm 2's z) must be Example
+// 2's Korobov vector for (a, n = n_last a^(d-1)): the sweep's digits describe that
+// lattice only.  NULL selects it.
+static mdi_status check_korobov_z(int d, int64_t a, int64_t n_last, const int64_t *z) {
+  if (!z) return MDI_OK;
+  unsigned __int128 n = (unsigned __int128)n_last;
+  const unsigned __int128 limit = ((unsigned __int128)1 << 63) - 1;
+  for (int i = 1; i < d; ++i) {
+    n *= (unsigned __int128)a;
+    if (n > limit) return MDI_EOVERFLOW;
+  }
+  const int64_t nn = (int64_t)n;
+  int64_t v = 1 % nn;
+  for (int i = 0; i < d; ++i) {
+    if (z[i] != v) return MDI_EUNSUPPORTED;
+    v = mulmod(v, a % nn, nn);
+  }
+  return MDI_OK;
+}
+
 }  // namespace mdi
 
 using namespace mdi;
@@ -141,6 +171,33 @@ mdi_status lattice_rule_integrate_improved(int32_t family, int32_t d, int64_t n,
                              (cudaStream_t)stream);
 }
 
+mdi_status lattice_korobov_vector(int32_t d, int64_t a, int64_t n, int64_t *z) {
+  if (d < 1 || n < 1 || a < 0 || !z) return MDI_EINVAL;
+  int64_t v = 1 % n;
+  const int64_t am = a % n;
+  for (int32_t i = 0; i < d; ++i) {
+    z[i] = v;
+    v = mulmod(v, am, n);
+  }
+  return MDI_OK;
+}
+
+mdi_status lattice_shifted_estimate(const double *values, int32_t R, double *mean_se, mdi_stream_t stream) {
+  NvtxRange nvtx_scope("lattice_shifted_estimate");
+  if (!values || !mean_se || R < 1 || R > 65535) return MDI_EINVAL;
+  return shifted_estimate_launch(values, R, mean_se, (cudaStream_t)stream);
+}
+
+mdi_status mdi_peak_probe(int32_t kind, int32_t iters, double *sink, mdi_stream_t stream) {
+  if ((kind != 0 && kind != 1) || iters < 1 || iters > (1 << 20) || !sink) return MDI_EINVAL;
+  return peak_probe_launch(kind, iters, sink, (cudaStream_t)stream);
+}
+
+int64_t mdi_peak_probe_threads(int32_t kind) {
+  if (kind != 0 && kind != 1) return 0;
+  return peak_probe_threads(kind);
+}
+
 mdi_status lattice_rule_integrate_noalloc(int32_t family, int32_t d, int64_t n, const int64_t *z, const double *params,
                                           int32_t precision, double *out, mdi_stream_t stream) {
   NvtxRange nvtx_scope("lattice_rule_integrate_noalloc");
@@ -172,11 +229,12 @@ mdi_status mdi_lr_workspace_size(int32_t family, int32_t d, int64_t a, int64_t n
   }
 }
 
-mdi_status mdi_lr_integrate(int32_t family, int32_t d, int64_t a, int64_t n_last, const double *params,
-                            const mdi_opts *opts, double *out, void *workspace, size_t ws_bytes,
-                            mdi_stream_t stream) {
+mdi_status mdi_lr_integrate(int32_t family, int32_t d, int64_t a, int64_t n_last, const int64_t *z,
+                            const double *params, const mdi_opts *opts, double *out, void *workspace,
+                            size_t ws_bytes, mdi_stream_t stream) {
   NvtxRange nvtx_scope("mdi_lr_integrate");
   if (!family_ok(family) || d < 1 || a < 1 || n_last < 1 || !params || !out || !opts_ok(opts)) return MDI_EINVAL;
+  if (mdi_status zs = check_korobov_z(d, a, n_last, z); zs != MDI_OK) return zs;
   const int precision = opts ? opts->precision : MDI_PREC_FP64;
   cudaStream_t s = (cudaStream_t)stream;
   switch (resolve_state(family, opts)) {
@@ -208,11 +266,12 @@ mdi_status mdi_lr_grad_workspace_size(int32_t family, int32_t d, int64_t a, int6
   }
 }
 
-mdi_status mdi_lr_grad(int32_t family, int32_t d, int64_t a, int64_t n_last, const double *params,
+mdi_status mdi_lr_grad(int32_t family, int32_t d, int64_t a, int64_t n_last, const int64_t *z, const double *params,
                        const mdi_opts *opts, double *value, double *grad, void *workspace, size_t ws_bytes,
                        mdi_stream_t stream) {
   NvtxRange nvtx_scope("mdi_lr_grad");
   if (!family_ok(family) || d < 1 || a < 1 || n_last < 1 || !params || !grad || !opts_ok(opts)) return MDI_EINVAL;
+  if (mdi_status zs = check_korobov_z(d, a, n_last, z); zs != MDI_OK) return zs;
   const int precision = opts ? opts->precision : MDI_PREC_FP64;
   if (precision != MDI_PREC_FP64) return MDI_EUNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
@@ -238,21 +297,32 @@ mdi_status mdi_lr_batched_prepare(const mdi_opts *opts, void *workspace, size_t 
 }
 
 mdi_status mdi_lr_integrate_batched(const mdi_batch_desc *descs, const int32_t *order, int32_t count,
-                                    const double *param_pool, const mdi_opts *opts, double *out, void *workspace,
-                                    size_t ws_bytes, mdi_stream_t stream) {
+                                    const double *param_pool, int64_t pool_len, const mdi_opts *opts, double *out,
+                                    void *workspace, size_t ws_bytes, mdi_stream_t stream) {
   NvtxRange nvtx_scope("mdi_lr_integrate_batched");
-  if (!opts_ok(opts)) return MDI_EINVAL;
+  if (!opts_ok(opts) || pool_len < 0) return MDI_EINVAL;
   if (opts && opts->state != MDI_STATE_AUTO && opts->state != MDI_STATE_NODES) return MDI_EUNSUPPORTED;
-  return nodes_batched_launch(descs, order, count, param_pool, nodes_config(opts), out, workspace, ws_bytes,
-                              (cudaStream_t)stream);
+  return nodes_batched_launch(descs, order, count, param_pool, pool_len, nodes_config(opts), out, workspace,
+                              ws_bytes, (cudaStream_t)stream);
 }
 
-mdi_status mdi_batch_plan(const mdi_batch_desc *descs, int32_t count, const mdi_opts *opts, int32_t *order) {
-  if (!descs || !order || count < 1 || !opts_ok(opts)) return MDI_EINVAL;
+mdi_status mdi_get_device_status(const void *workspace, size_t ws_bytes, int32_t clear, uint32_t *flags,
+                                 mdi_stream_t stream) {
+  if (!workspace || ((uintptr_t)workspace % kAlign) != 0 || ws_bytes < nodes_status_word_bytes()) return MDI_EINVAL;
+  uint32_t word = 0;
+  mdi_status st = nodes_read_status(workspace, clear != 0, &word, (cudaStream_t)stream);
+  if (st != MDI_OK) return st;
+  if (flags) *flags = word;
+  return word ? MDI_EINVAL : MDI_OK;
+}
+
+mdi_status mdi_batch_plan(const mdi_batch_desc *descs, int32_t count, int64_t pool_len, const mdi_opts *opts,
+                          int32_t *order) {
+  if (!descs || !order || count < 1 || pool_len < 0 || !opts_ok(opts)) return MDI_EINVAL;
   const int P = nodes_config(opts).P;
   std::vector<double> cost((size_t)count);
   for (int32_t i = 0; i < count; ++i) {
-    if (!desc_ok(descs[i])) return MDI_EINVAL;
+    if (!desc_ok(descs[i]) || !desc_in_pool(descs[i], pool_len)) return MDI_EINVAL;
     cost[(size_t)i] = nodes_cost(descs[i], P);
   }
   std::vector<int32_t> idx((size_t)count);

@@ -18,6 +18,13 @@ mdi_status slr_launch_noalloc(int family, int d, int64_t n, const int64_t *z, co
 mdi_status lattice_indices_launch(int d, int64_t n, const int64_t *z, int64_t j0, int64_t count, int64_t *r_out,
                                   cudaStream_t stream);
 
+// slr.cu: mean and standard error of shifted-rule replicates (Section 2.1)
+mdi_status shifted_estimate_launch(const double *values, int R, double *mean_se, cudaStream_t stream);
+
+// probe.cu: FMA throughput probe (measurement aid)
+mdi_status peak_probe_launch(int kind, int iters, double *sink, cudaStream_t stream);
+int64_t peak_probe_threads(int kind);
+
 // mdi_exact.cu
 size_t exact_workspace_bytes(int family, int d, int64_t a, int64_t n_last);
 mdi_status exact_launch(int family, int d, int64_t a, int64_t n_last, const double *params, int precision,
@@ -71,8 +78,12 @@ NodesConfig nodes_config(const mdi_opts *opts);
 size_t nodes_batched_workspace_bytes(int count, const NodesConfig &cfg);
 mdi_status nodes_prepare(const NodesConfig &cfg, void *workspace, size_t ws_bytes, cudaStream_t stream);
 mdi_status nodes_batched_launch(const mdi_batch_desc *descs, const int32_t *order, int count,
-                                const double *param_pool, const NodesConfig &cfg, double *out, void *workspace,
-                                size_t ws_bytes, cudaStream_t stream);
+                                const double *param_pool, int64_t pool_len, const NodesConfig &cfg, double *out,
+                                void *workspace, size_t ws_bytes, cudaStream_t stream);
+// Device status word of a batched workspace (MDI_DEV_* flags): bytes needed to
+// hold it, and a stream-ordered read (waits for the stream), optionally cleared.
+size_t nodes_status_word_bytes();
+mdi_status nodes_read_status(const void *workspace, bool clear, uint32_t *word, cudaStream_t stream);
 // Single integral through the batched machinery (descriptor built on the device).
 size_t nodes_single_workspace_bytes(const NodesConfig &cfg);
 mdi_status nodes_single_launch(int family, int d, int64_t a, int64_t n_last, const double *params,

@@ -889,6 +889,7 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
                                                                        const int32_t *__restrict__ order, int count,
                                                                        mdi_batch_desc single,
                                                                        const double *__restrict__ pool,
+                                                                       long long pool_len,
                                                                        const void *__restrict__ tables,
                                                                        const float4 *__restrict__ paired,
                                                                        const NodesConsts *__restrict__ kc, int P,
@@ -905,7 +906,8 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
   if (PREC == MDI_PREC_DF64)
     for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) sh.exp2tab[j] = kc->exp2tab[j];
   int staged_a = -1;
-  // counter[0]: next work item; counter[1]: CTAs finished; counter[2]: preparation tag.
+  // counter[0]: next work item; counter[1]: CTAs finished; counter[2]: preparation
+  // tag; counter[3]: the device status word (MDI_DEV_* flags, OR-ed in).
   const bool prepared = counter[2] == expect_tag;
   while (true) {
     if (threadIdx.x == 0) sh.inst = (int)atomicAdd(&counter[0], 1u);
@@ -914,12 +916,22 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
     __syncthreads();
     if (slot >= count) break;
     const int inst = order ? order[slot] : slot;
-    if (inst < 0 || inst >= count) continue;  // an order entry outside the batch is skipped
+    if (inst < 0 || inst >= count) {  // an order entry outside the batch is skipped
+      if (threadIdx.x == 0) atomicOr(&counter[3], MDI_DEV_BAD_ORDER);
+      continue;
+    }
     const mdi_batch_desc ds = descs ? descs[inst] : single;
     const int a = ds.a;
-    if (!prepared || ds.family < MDI_FAM_EXP || ds.family > MDI_FAM_PEAK || ds.d < 1 || ds.d > MDI_BATCH_MAX_D ||
-        a < 1 || a > kNodesAMax || ds.n_last < 1 || ds.n_last > 4096 || ds.param_offset < 0) {
-      if (threadIdx.x == 0) out[inst] = __longlong_as_double(0x7ff8000000000000ll);  // NaN marks a bad descriptor
+    const bool desc_ok = ds.family >= MDI_FAM_EXP && ds.family <= MDI_FAM_PEAK && ds.d >= 1 &&
+                         ds.d <= MDI_BATCH_MAX_D && a >= 1 && a <= kNodesAMax && ds.n_last >= 1 &&
+                         ds.n_last <= 4096 && ds.param_offset >= 0;
+    // The integral's 2d parameters must lie inside the pool (no read past its end).
+    const bool in_pool = desc_ok && ds.param_offset <= pool_len && 2ll * ds.d <= pool_len - ds.param_offset;
+    if (!prepared || !in_pool) {
+      if (threadIdx.x == 0) {
+        out[inst] = __longlong_as_double(0x7ff8000000000000ll);  // NaN marks a rejected integral
+        atomicOr(&counter[3], !prepared ? MDI_DEV_UNPREPARED : !desc_ok ? MDI_DEV_BAD_DESC : MDI_DEV_POOL_RANGE);
+      }
       continue;
     }
     // Basis tables of a: the cluster part (the paired one for real families),
@@ -1007,11 +1019,12 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
   }
 }
 
-// Zeroes the queue counters and stamps the preparation tag.
+// Zeroes the queue counters and the status word and stamps the preparation tag.
 __global__ void nodes_arm_kernel(unsigned *counter, unsigned tag) {
   counter[0] = 0u;
   counter[1] = 0u;
   counter[2] = tag;
+  counter[3] = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -1091,8 +1104,8 @@ mdi_status nodes_prepare(const NodesConfig &cfg, void *workspace, size_t ws_byte
 
 template <int PREC>
 static mdi_status launch_nodes(const mdi_batch_desc *descs, const int32_t *order, int count,
-                               const mdi_batch_desc &single, const double *pool, const NodesConfig &cfg, double *out,
-                               void *ws, cudaStream_t stream) {
+                               const mdi_batch_desc &single, const double *pool, int64_t pool_len,
+                               const NodesConfig &cfg, double *out, void *ws, cudaStream_t stream) {
   unsigned *counter = (unsigned *)ws;
   void *tables = (char *)ws + counter_bytes();
   const size_t smem = nodes_smem_bytes(cfg.block, cfg.P, cfg.stage != 0);
@@ -1121,32 +1134,48 @@ static mdi_status launch_nodes(const mdi_batch_desc *descs, const int32_t *order
   const int grid = std::max(1, std::min(count, sm_count() * per_sm));
   const float4 *paired = paired_tables(cfg) ? (const float4 *)((char *)tables + align_up(table_bytes(cfg.P))) : nullptr;
   const NodesConsts *kc = (const NodesConsts *)((char *)ws + consts_offset(cfg));
-  nodes_batched_kernel<PREC><<<grid, cfg.block, smem, stream>>>(descs, order, count, single, pool, tables, paired, kc,
-                                                                 cfg.P, cfg.stage, out, counter, nodes_tag(cfg));
+  nodes_batched_kernel<PREC><<<grid, cfg.block, smem, stream>>>(descs, order, count, single, pool,
+                                                                 (long long)pool_len, tables, paired, kc, cfg.P,
+                                                                 cfg.stage, out, counter, nodes_tag(cfg));
   return check_launch();
 }
 
 static mdi_status dispatch_nodes(const mdi_batch_desc *descs, const int32_t *order, int count,
-                                 const mdi_batch_desc &single, const double *pool, const NodesConfig &cfg,
-                                 double *out, void *ws, cudaStream_t stream) {
+                                 const mdi_batch_desc &single, const double *pool, int64_t pool_len,
+                                 const NodesConfig &cfg, double *out, void *ws, cudaStream_t stream) {
   switch (cfg.precision) {
-    case MDI_PREC_FP64: return launch_nodes<MDI_PREC_FP64>(descs, order, count, single, pool, cfg, out, ws, stream);
+    case MDI_PREC_FP64:
+      return launch_nodes<MDI_PREC_FP64>(descs, order, count, single, pool, pool_len, cfg, out, ws, stream);
     case MDI_PREC_FP32_EVAL_FP64:
-      return launch_nodes<MDI_PREC_FP32_EVAL_FP64>(descs, order, count, single, pool, cfg, out, ws, stream);
+      return launch_nodes<MDI_PREC_FP32_EVAL_FP64>(descs, order, count, single, pool, pool_len, cfg, out, ws, stream);
     case MDI_PREC_FP32_EVAL_DF32:
-      return launch_nodes<MDI_PREC_FP32_EVAL_DF32>(descs, order, count, single, pool, cfg, out, ws, stream);
-    default: return launch_nodes<MDI_PREC_DF64>(descs, order, count, single, pool, cfg, out, ws, stream);
+      return launch_nodes<MDI_PREC_FP32_EVAL_DF32>(descs, order, count, single, pool, pool_len, cfg, out, ws, stream);
+    default: return launch_nodes<MDI_PREC_DF64>(descs, order, count, single, pool, pool_len, cfg, out, ws, stream);
   }
 }
 
 mdi_status nodes_batched_launch(const mdi_batch_desc *descs, const int32_t *order, int count,
-                                const double *param_pool, const NodesConfig &cfg, double *out, void *workspace,
-                                size_t ws_bytes, cudaStream_t stream) {
+                                const double *param_pool, int64_t pool_len, const NodesConfig &cfg, double *out,
+                                void *workspace, size_t ws_bytes, cudaStream_t stream) {
   if (!descs || !param_pool || !out || count < 1) return MDI_EINVAL;
   if (!config_ok(cfg)) return MDI_EINVAL;
   if (!ws_ok(workspace, ws_bytes, cfg)) return MDI_EWORKSPACE;
   mdi_batch_desc none{};
-  return dispatch_nodes(descs, order, count, none, param_pool, cfg, out, workspace, stream);
+  return dispatch_nodes(descs, order, count, none, param_pool, pool_len, cfg, out, workspace, stream);
+}
+
+size_t nodes_status_word_bytes() { return 4 * sizeof(unsigned); }
+
+mdi_status nodes_read_status(const void *workspace, bool clear, uint32_t *word, cudaStream_t stream) {
+  unsigned *status = (unsigned *)workspace + 3;  // counter[3]
+  cudaError_t e = cudaMemcpyAsync(word, status, sizeof(unsigned), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e == cudaSuccess && clear) e = cudaMemsetAsync(status, 0, sizeof(unsigned), stream);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return MDI_ECUDA;
+  }
+  return MDI_OK;
 }
 
 mdi_status nodes_single_launch(int family, int d, int64_t a, int64_t n_last, const double *params,
@@ -1156,7 +1185,7 @@ mdi_status nodes_single_launch(int family, int d, int64_t a, int64_t n_last, con
   mdi_status st = nodes_prepare(cfg, workspace, ws_bytes, stream);
   if (st != MDI_OK) return st;
   mdi_batch_desc one{family, d, (int32_t)a, (int32_t)n_last, 0, 0};
-  return dispatch_nodes(nullptr, nullptr, 1, one, params, cfg, out, workspace, stream);
+  return dispatch_nodes(nullptr, nullptr, 1, one, params, 2 * (int64_t)d, cfg, out, workspace, stream);
 }
 
 }  // namespace mdi

@@ -503,6 +503,46 @@ mdi_status slr_shifted_launch(int family, int d, int64_t n, const int64_t *z, co
   return check_launch();
 }
 
+// Section 2.1's estimate from R shifted replicates: their mean and its standard
+// error, sqrt(sum_r (v_r - mean)^2 / (R (R - 1))).  One CTA; each thread sums a
+// strided subset in index order and a fixed shared-memory tree adds the threads'
+// sums, so the result does not depend on timing.  Two passes (mean, then the
+// squared deviations from it) avoid the cancellation of a one-pass variance.
+constexpr int kEstThreads = 256;
+__device__ double block_tree_sum(double v, double *sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = kEstThreads / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+__global__ void __launch_bounds__(kEstThreads) shifted_estimate_kernel(const double *__restrict__ values, int R,
+                                                                       double *__restrict__ mean_se) {
+  __shared__ double sh[kEstThreads];
+  double acc = 0.0;
+  for (int r = threadIdx.x; r < R; r += kEstThreads) acc += values[r];
+  const double mean = block_tree_sum(acc, sh) / (double)R;
+  double dev = 0.0;
+  for (int r = threadIdx.x; r < R; r += kEstThreads) {
+    const double e = values[r] - mean;
+    dev = fma(e, e, dev);
+  }
+  const double ss = block_tree_sum(dev, sh);
+  if (threadIdx.x == 0) {
+    mean_se[0] = mean;
+    mean_se[1] = R > 1 ? sqrt(ss / ((double)R * (double)(R - 1))) : 0.0;
+  }
+}
+
+mdi_status shifted_estimate_launch(const double *values, int R, double *mean_se, cudaStream_t stream) {
+  shifted_estimate_kernel<<<1, kEstThreads, 0, stream>>>(values, R, mean_se);
+  return check_launch();
+}
+
 mdi_status lattice_indices_launch(int d, int64_t n, const int64_t *z, int64_t j0, int64_t count, int64_t *r_out,
                                   cudaStream_t stream) {
   if (d < 1 || d > kSlrMaxD || n < 1 || !z || !r_out || j0 < 0 || count < 1) return MDI_EINVAL;

@@ -33,9 +33,9 @@ class BatchedMDILR:
         self.precision, self.nodes = precision, nodes
         descs = make_batch_descs(families, d, a, n_last, offsets)
         self.descs_host = descs
-        order = mdi_batch_plan(descs, nodes=nodes)
         pool_t = pool if isinstance(pool, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(pool))
         pool_t = pool_t.to(dtype=torch.float64).contiguous().cpu()
+        order = mdi_batch_plan(descs, pool_t.numel(), nodes=nodes)
         # Packed inputs: descriptors | order | pool, each 256-byte aligned.
         def up(x):
             return (x + 255) // 256 * 256

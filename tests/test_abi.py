@@ -25,7 +25,8 @@ def lib():
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+char\s*\*|mdi_status|int32_t)\s*(\w+)\s*\(", text, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:const\s+char\s*\*|mdi_status|int32_t|int64_t)\s*(\w+)\s*\(", text,
+                                 flags=re.M)))
 
 
 def test_header_declares_expected_entry_points():
@@ -43,7 +44,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.mdi_abi_version() == 1
+    assert lib.mdi_abi_version() == _ffi.ABI_VERSION == 2
     for code in range(6):
         s = lib.mdi_status_string(code).decode()
         assert s.startswith("MDI_")
@@ -79,13 +80,13 @@ def test_lattice_rule_rejects_bad_arguments(lib):
 def test_mdi_rejects_bad_arguments(lib):
     fake = ctypes.c_void_p(0x1000)
     o = _ffi.MdiOpts()
-    assert lib.mdi_lr_integrate(0, 0, 16, 16, fake, ctypes.byref(o), fake, fake, 1 << 20, _null()) == _ffi.MDI_EINVAL
-    assert lib.mdi_lr_integrate(0, 4, 0, 16, fake, ctypes.byref(o), fake, fake, 1 << 20, _null()) == _ffi.MDI_EINVAL
+    assert lib.mdi_lr_integrate(0, 0, 16, 16, _null(), fake, ctypes.byref(o), fake, fake, 1 << 20, _null()) == _ffi.MDI_EINVAL
+    assert lib.mdi_lr_integrate(0, 4, 0, 16, _null(), fake, ctypes.byref(o), fake, fake, 1 << 20, _null()) == _ffi.MDI_EINVAL
     o.reserved = 1
-    assert lib.mdi_lr_integrate(0, 4, 16, 16, fake, ctypes.byref(o), fake, fake, 1 << 20, _null()) == _ffi.MDI_EINVAL
+    assert lib.mdi_lr_integrate(0, 4, 16, 16, _null(), fake, ctypes.byref(o), fake, fake, 1 << 20, _null()) == _ffi.MDI_EINVAL
     o = _ffi.MdiOpts()
     o.state = _ffi.STATE["closed"]
-    assert lib.mdi_lr_integrate(2, 4, 16, 16, fake, ctypes.byref(o), fake, fake, 1 << 20,
+    assert lib.mdi_lr_integrate(2, 4, 16, 16, _null(), fake, ctypes.byref(o), fake, fake, 1 << 20,
                                 _null()) == _ffi.MDI_EUNSUPPORTED
     o.state = _ffi.STATE["exact"]
     b = ctypes.c_size_t()
@@ -93,9 +94,9 @@ def test_mdi_rejects_bad_arguments(lib):
     assert lib.mdi_lr_workspace_size(2, 4, 16, 16, ctypes.byref(o), ctypes.byref(b)) == _ffi.MDI_OK
     o.state = _ffi.STATE["nodes"]
     o.nodes = 15  # odd P is refused
-    assert lib.mdi_lr_integrate(2, 4, 16, 16, fake, ctypes.byref(o), fake, fake, 1 << 30, _null()) == _ffi.MDI_EINVAL
+    assert lib.mdi_lr_integrate(2, 4, 16, 16, _null(), fake, ctypes.byref(o), fake, fake, 1 << 30, _null()) == _ffi.MDI_EINVAL
     o.nodes = 16
-    assert lib.mdi_lr_integrate(2, 4, 65, 16, fake, ctypes.byref(o), fake, fake, 1 << 30,
+    assert lib.mdi_lr_integrate(2, 4, 65, 16, _null(), fake, ctypes.byref(o), fake, fake, 1 << 30,
                                 _null()) == _ffi.MDI_EUNSUPPORTED
 
 
@@ -104,7 +105,7 @@ def test_batch_plan_is_longest_first_permutation(lib):
     n = 500
     a = rng.integers(8, 33, n)
     descs = mdi.make_batch_descs(["gauss"] * n, rng.integers(6, 21, n), a, a, np.arange(n) * 40)
-    order = mdi.mdi_batch_plan(descs)
+    order = mdi.mdi_batch_plan(descs, 40 * n)
     assert sorted(order.tolist()) == list(range(n))
     # one family, n_last = a: the work is dominated by the (d - 1) * a cluster points;
     # the last axis adds less than 3 such units for a <= 32
@@ -114,7 +115,7 @@ def test_batch_plan_is_longest_first_permutation(lib):
     bad = descs.copy()
     bad["a"][3] = 65
     with pytest.raises(mdi.MdiError):
-        mdi.mdi_batch_plan(bad)
+        mdi.mdi_batch_plan(bad, 40 * n)
 
 
 def test_workspace_queries(lib):
@@ -201,7 +202,7 @@ def test_improved_rule_and_df64_modes_validate_before_launching(lib):
     o = _ffi.MdiOpts()
     o.state = _ffi.STATE["closed"]
     o.precision = 3
-    assert lib.mdi_lr_integrate(0, 2, 1 << 31, 4, fake, ctypes.byref(o), fake, fake, 1 << 30, _null()) == U
+    assert lib.mdi_lr_integrate(0, 2, 1 << 31, 4, _null(), fake, ctypes.byref(o), fake, fake, 1 << 30, _null()) == U
 
 
 def test_empty_batch_is_refused(lib):
@@ -210,8 +211,80 @@ def test_empty_batch_is_refused(lib):
     fake = ctypes.c_void_p(0x1000)
     o = _ffi.MdiOpts()
     for count in (0, -3):
-        assert lib.mdi_lr_integrate_batched(fake, fake, count, fake, ctypes.byref(o), fake, fake, 1 << 30,
+        assert lib.mdi_lr_integrate_batched(fake, fake, count, fake, 1 << 20, ctypes.byref(o), fake, fake, 1 << 30,
                                             _null()) == _ffi.MDI_EINVAL
-        assert lib.mdi_batch_plan(fake, count, ctypes.byref(o), fake) == _ffi.MDI_EINVAL
+        assert lib.mdi_batch_plan(fake, count, 1 << 20, ctypes.byref(o), fake) == _ffi.MDI_EINVAL
     b = ctypes.c_size_t()
     assert lib.mdi_lr_batched_workspace_size(0, ctypes.byref(o), ctypes.byref(b)) == _ffi.MDI_EINVAL
+
+
+def test_generating_vector_argument_is_checked_on_the_host(lib):
+    """Algorithm 2's z: NULL or Example 2's Korobov vector for (a, n = n_last a^(d-1));
+    another vector is refused (MDI_EUNSUPPORTED), and so is any z when n does not
+    fit an int64 (MDI_EOVERFLOW) -- before anything is launched."""
+    fake = ctypes.c_void_p(0x1000)
+    o = _ffi.MdiOpts()
+    d, a, nl = 4, 16, 16
+    good = mdi.korobov_vector(d, a, nl * a ** (d - 1))
+    assert list(good) == [1, 16, 256, 4096]
+    for bad in ([1, 16, 256, 4097], [1, 17, 289, 4913], [0, 16, 256, 4096]):
+        z = np.asarray(bad, dtype=np.int64)
+        zp = z.ctypes.data_as(ctypes.c_void_p)
+        assert lib.mdi_lr_integrate(0, d, a, nl, zp, fake, ctypes.byref(o), fake, fake, 1 << 20,
+                                    _null()) == _ffi.MDI_EUNSUPPORTED
+        assert lib.mdi_lr_grad(0, d, a, nl, zp, fake, ctypes.byref(o), fake, fake, fake, 1 << 20,
+                               _null()) == _ffi.MDI_EUNSUPPORTED
+    big = np.ones(20, dtype=np.int64)  # n = 16^20 does not fit an int64
+    assert lib.mdi_lr_integrate(0, 20, 16, 16, big.ctypes.data_as(ctypes.c_void_p), fake, ctypes.byref(o), fake,
+                                fake, 1 << 20, _null()) == _ffi.MDI_EOVERFLOW
+    # n_last = 1: z_d = a^(d-1) mod n = 0
+    z1 = mdi.korobov_vector(3, 5, 25)
+    assert list(z1) == [1, 5, 0]
+
+
+def test_korobov_vector_entry_point(lib):
+    z = np.zeros(5, dtype=np.int64)
+    assert lib.lattice_korobov_vector(5, 3, 7, z.ctypes.data_as(ctypes.c_void_p)) == _ffi.MDI_OK
+    assert list(z) == [1, 3, 2, 6, 4]
+    n = (1 << 63) - 25
+    assert lib.lattice_korobov_vector(3, n - 1, n, z.ctypes.data_as(ctypes.c_void_p)) == _ffi.MDI_OK
+    assert list(z[:3]) == [1, n - 1, 1]  # (-1)^2 = 1 mod n, exact through 128-bit products
+    assert lib.lattice_korobov_vector(0, 3, 7, z.ctypes.data_as(ctypes.c_void_p)) == _ffi.MDI_EINVAL
+    assert lib.lattice_korobov_vector(3, 3, 0, z.ctypes.data_as(ctypes.c_void_p)) == _ffi.MDI_EINVAL
+    assert lib.lattice_korobov_vector(3, -1, 7, z.ctypes.data_as(ctypes.c_void_p)) == _ffi.MDI_EINVAL
+    assert lib.lattice_korobov_vector(3, 3, 7, _null()) == _ffi.MDI_EINVAL
+
+
+def test_batch_plan_checks_the_parameter_pool(lib):
+    """Every descriptor's 2*d parameters must lie inside the pool: an offset one past
+    the last admissible one is refused by the planner (the kernel flags it on the
+    device, where the host cannot look)."""
+    descs = mdi.make_batch_descs(["gauss", "peak"], [3, 4], [8, 9], [8, 9], [0, 6])
+    assert sorted(mdi.mdi_batch_plan(descs, 14).tolist()) == [0, 1]
+    with pytest.raises(mdi.MdiError):
+        mdi.mdi_batch_plan(descs, 13)
+    bad = descs.copy()
+    bad["param_offset"][1] = 7
+    with pytest.raises(mdi.MdiError):
+        mdi.mdi_batch_plan(bad, 14)
+    o = _ffi.MdiOpts()
+    fake = ctypes.c_void_p(0x1000)
+    assert lib.mdi_batch_plan(descs.ctypes.data_as(ctypes.c_void_p), 2, -1, ctypes.byref(o), fake) == _ffi.MDI_EINVAL
+    assert lib.mdi_lr_integrate_batched(fake, fake, 2, fake, -1, ctypes.byref(o), fake, fake, 1 << 30,
+                                        _null()) == _ffi.MDI_EINVAL
+
+
+def test_status_estimate_and_probe_validate_arguments(lib):
+    fake = ctypes.c_void_p(0x1000)
+    flags = ctypes.c_uint32(0)
+    assert lib.mdi_get_device_status(_null(), 1 << 20, 0, ctypes.byref(flags), _null()) == _ffi.MDI_EINVAL
+    assert lib.mdi_get_device_status(ctypes.c_void_p(0x1008), 1 << 20, 0, ctypes.byref(flags), _null()) == _ffi.MDI_EINVAL
+    assert lib.mdi_get_device_status(fake, 8, 0, ctypes.byref(flags), _null()) == _ffi.MDI_EINVAL
+    assert lib.lattice_shifted_estimate(fake, 0, fake, _null()) == _ffi.MDI_EINVAL
+    assert lib.lattice_shifted_estimate(fake, 65536, fake, _null()) == _ffi.MDI_EINVAL
+    assert lib.lattice_shifted_estimate(_null(), 4, fake, _null()) == _ffi.MDI_EINVAL
+    assert lib.mdi_peak_probe(2, 10, fake, _null()) == _ffi.MDI_EINVAL
+    assert lib.mdi_peak_probe(0, 0, fake, _null()) == _ffi.MDI_EINVAL
+    assert lib.mdi_peak_probe(1, 10, _null(), _null()) == _ffi.MDI_EINVAL
+    assert lib.mdi_peak_probe_threads(5) == 0
+    assert _ffi.DEV_FLAGS == {"bad_desc": 1, "bad_order": 2, "unprepared": 4, "pool_range": 8}

@@ -91,3 +91,13 @@ def test_flop_counts_of_the_batched_formulations():
     assert bench.df_flops(one, float_phi=True) == 5 * P * (pf + half) + 5 * P * pf + last
     osc = SimpleNamespace(families=["osc"], d=np.array([3]), a=np.array([5]), n_last=np.array([5]))
     assert bench.df_flops(osc, float_phi=True) == bench.df_flops(osc, paired=False)  # OSC: unpaired, FP64 phi
+
+
+def test_algorithmic_flop_count():
+    """The survey's count for the batch: d N (P C_phi + P^2) per integral (a = N)."""
+    from types import SimpleNamespace
+    P = bench.P_NODES
+    b = SimpleNamespace(families=["gauss", "peak"], d=np.array([3, 7]), a=np.array([5, 20]), n_last=np.array([5, 20]))
+    expect = 3 * 5 * (P * bench.C_PHI["gauss"] + P * P) + 7 * 20 * (P * bench.C_PHI["peak"] + P * P)
+    assert bench.alg_flops(b) == expect
+    assert bench.C_PHI["gauss"] == bench.C_PHI["peak"] == 25

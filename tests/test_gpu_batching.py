@@ -113,35 +113,59 @@ def _descs_dev(descs):
 
 @pytest.mark.parametrize("precision", ["df64", "fp64"])
 def test_injected_faults_are_reported_not_run(precision):
-    """Host-side fault injection: descriptors outside the limits give NaN in their own
+    """Host-side fault injection: descriptors outside the limits, and one whose
+    parameters run one double past the end of the pool, give NaN in their own
     output only; a zeroed (unprepared) workspace and one prepared for another node
-    count (whose tag differs) give NaN everywhere; order entries outside the batch are
-    skipped.  Every
-    one of these is rejected before the kernel touches memory for that entry."""
+    count (whose tag differs) give NaN everywhere; order entries outside the batch
+    are skipped.  Each is rejected before the kernel touches memory for that entry,
+    and each sets its flag in the workspace's device status word, which
+    mdi_get_device_status reads (and clears)."""
     import paper_2404_08867_gb300 as mdi
+    F = mdi._ffi.DEV_FLAGS
     b = inputs.batch(count=16, seed=2)
     descs = mdi.make_batch_descs(b.families, b.d, b.a, b.n_last, b.offsets)
     pool = torch.as_tensor(b.pool).cuda()
-    good = mdi.mdi_lr_integrate_batched(_descs_dev(descs), pool, 16, precision=precision).cpu().numpy()
+    ws = mdi.mdi_lr_batched_prepare(nodes=16, precision=precision)
+
+    def run(dd, **kw):
+        kw.setdefault("workspace", ws)
+        return mdi.mdi_lr_integrate_batched(_descs_dev(dd), pool, 16, precision=precision, **kw)
+
+    good = run(descs).cpu().numpy()
+    assert mdi.mdi_get_device_status(ws) == 0
     bad = descs.copy()
     bad["a"][3], bad["d"][5], bad["family"][7], bad["n_last"][9], bad["param_offset"][11] = 65, 0, 9, 5000, -8
-    out = mdi.mdi_lr_integrate_batched(_descs_dev(bad), pool, 16, precision=precision).cpu().numpy()
+    out = run(bad).cpu().numpy()
     hit = [3, 5, 7, 9, 11]
     assert np.all(np.isnan(out[hit]))
     keep = [i for i in range(16) if i not in hit]
     np.testing.assert_array_equal(out[keep], good[keep])
+    assert mdi.mdi_get_device_status(ws, clear=True) == F["bad_desc"]
+    assert mdi.mdi_get_device_status(ws) == 0  # cleared
+    # The last integral's 2d parameters moved one double past the pool's end.
+    past = descs.copy()
+    past["param_offset"][15] = pool.numel() - 2 * int(descs["d"][15]) + 1
+    out = run(past).cpu().numpy()
+    assert np.isnan(out[15]) and np.array_equal(out[:15], good[:15])
+    assert mdi.mdi_get_device_status(ws, clear=True) == F["pool_range"]
+    # At the pool's end exactly: accepted (the parameters are those of another
+    # integral, so only the status is checked).
+    edge = descs.copy()
+    edge["param_offset"][15] = pool.numel() - 2 * int(descs["d"][15])
+    assert np.all(np.isfinite(run(edge).cpu().numpy()))
+    assert mdi.mdi_get_device_status(ws) == 0
     nbytes = mdi.mdi_lr_batched_workspace_size(16, nodes=16, precision=precision)
     zeroed = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
-    out = mdi.mdi_lr_integrate_batched(_descs_dev(descs), pool, 16, workspace=zeroed, precision=precision)
-    assert torch.isnan(out).all()
+    assert torch.isnan(run(descs, workspace=zeroed)).all()
+    assert mdi.mdi_get_device_status(zeroed) == F["unprepared"]
     # prepared for P = 18: large enough, but its tag names another node count
     other = mdi.mdi_lr_batched_prepare(nodes=18, precision=precision)
     assert other.numel() >= nbytes
-    out = mdi.mdi_lr_integrate_batched(_descs_dev(descs), pool, 16, workspace=other, precision=precision)
-    assert torch.isnan(out).all()
+    assert torch.isnan(run(descs, workspace=other)).all()
+    assert mdi.mdi_get_device_status(other) == F["unprepared"]
     order = torch.as_tensor(np.array([-1] + list(range(15)), dtype=np.int32)).cuda()
     filled = torch.full((16,), 7.0, dtype=torch.float64, device="cuda")
-    out = mdi.mdi_lr_integrate_batched(_descs_dev(descs), pool, 16, order=order, out=filled,
-                                       precision=precision).cpu().numpy()
+    out = run(descs, order=order, out=filled).cpu().numpy()
     assert out[15] == 7.0
     np.testing.assert_array_equal(out[:15], good[:15])
+    assert mdi.mdi_get_device_status(ws, clear=True) == F["bad_order"]

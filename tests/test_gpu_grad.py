@@ -1,7 +1,10 @@
 """Adjoint sweep on the GPU (mdi_lr_grad and the autograd Function) against the
 oracle's forward-mode derivative of the same rule, central differences and the
-closed-form gradient.  Gradients are compared in the max norm: every component
-within 1e-12 of the largest one (normwise relative error 1e-12)."""
+closed-form gradient.  Gradients are compared component by component: every
+|g_i - ref_i| <= 1e-12 |ref_i| + 1e-15 max_k |ref_k| (the absolute floor, three
+orders below the relative bound of the largest component, only matters for
+components at rounding level, e.g. dQ/dw_j of a factor centred at w_j = 1/2),
+and in the max norm as well."""
 import numpy as np
 import pytest
 import torch
@@ -25,10 +28,15 @@ def dev(x):
     return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64)).cuda()
 
 
-def assert_grad_close(got, ref, tol=TOL):
+def assert_grad_close(got, ref, tol=TOL, floor=1e-15):
+    got, ref = np.asarray(got), np.asarray(ref)
     scale = max(np.max(np.abs(ref)), 1e-300)
-    err = np.max(np.abs(got - ref)) / scale
-    assert err <= tol, f"normwise relative error {err:.3e}"
+    err = np.abs(got - ref)
+    bound = tol * np.abs(ref) + floor * scale
+    bad = np.flatnonzero(err > bound)
+    assert bad.size == 0, (f"{bad.size} components outside |g - ref| <= {tol:g}|ref| + {floor:g} max|ref|; first "
+                           f"{bad[:5].tolist()}: got {got[bad[:5]].tolist()} ref {ref[bad[:5]].tolist()}")
+    assert np.max(err) / scale <= tol, f"normwise relative error {np.max(err) / scale:.3e}"
 
 
 @pytest.mark.parametrize("fam", ["gauss", "peak", "exp", "osc"])
@@ -95,7 +103,7 @@ def test_checkpoint_interval_does_not_change_the_gradient(C):
     w = inputs.gaussian(100, 16, seed=1)
     _, g0 = mdi.mdi_lr_grad("gauss", dev(w.params), 100, 16, 16, state="nodes", checkpoint=10)
     _, g1 = mdi.mdi_lr_grad("gauss", dev(w.params), 100, 16, 16, state="nodes", checkpoint=C)
-    assert_grad_close(g1.cpu().numpy(), g0.cpu().numpy(), tol=1e-14)
+    assert_grad_close(g1.cpu().numpy(), g0.cpu().numpy(), tol=1e-14, floor=1e-16)
 
 
 def test_scale_workload_gradient():

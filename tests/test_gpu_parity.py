@@ -285,7 +285,7 @@ def test_nodes_compensated_accumulation(fam, d, a):
 # ----------------------------------------------------------------------------
 def _batch_to_device(b):
     descs = mdi.make_batch_descs(b.families, b.d, b.a, b.n_last, b.offsets)
-    order = mdi.mdi_batch_plan(descs)
+    order = mdi.mdi_batch_plan(descs, b.pool.size)
     d_descs = torch.from_numpy(descs.view(np.uint8)).cuda()
     return descs, d_descs, torch.from_numpy(order).cuda(), dev(b.pool)
 
@@ -299,17 +299,37 @@ def test_batched_small_matches_oracle_elementwise():
         close(out[i], o.mdi_nodes(it.family, it.d, it.a, it.n_last, 16, it.c, it.w), it.family)
 
 
-def test_batched_full_size_sampled():
-    """4096 integrals (d ~ U{6..20}, N ~ U{8..32}) in one launch; 96 sampled
-    outputs checked against the oracle, the rest against their own re-run."""
+_ORACLE_BATCH = {}
+
+
+def oracle_batch(count, seed):
+    """The oracle's FP64 node-state value (P = 16) of every integral of a batch,
+    computed once per module."""
+    key = (count, seed)
+    if key not in _ORACLE_BATCH:
+        b = inputs.batch(count=count, seed=seed)
+        _ORACLE_BATCH[key] = np.array([o.mdi_nodes(it.family, it.d, it.a, it.n_last, 16, it.c, it.w)
+                                       for it in (b.integral(i) for i in range(len(b)))])
+    return _ORACLE_BATCH[key]
+
+
+def assert_batch_close(got, ref, tol):
+    rel = np.abs(got - ref) / np.abs(ref)
+    bad = np.flatnonzero(~(rel <= tol))
+    assert bad.size == 0, f"{bad.size} integrals beyond {tol:g}; worst {np.nanmax(rel):.3e} at {bad[:5].tolist()}"
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_batched_full_size_every_output(prec):
+    """The bench's 4096-integral batch (seed 0; d ~ U{6..20}, N ~ U{8..32}) in one
+    launch: every output against the oracle within 1e-12 relative, in FP64 and in
+    the double-float mode; the scheduling order changes no value."""
     b = inputs.batch(count=4096, seed=0)
     _, d_descs, d_order, pool = _batch_to_device(b)
-    out1 = mdi.mdi_lr_integrate_batched(d_descs, pool, len(b), order=d_order).cpu().numpy()
-    out2 = mdi.mdi_lr_integrate_batched(d_descs, pool, len(b)).cpu().numpy()
-    np.testing.assert_array_equal(out1, out2)  # scheduling order does not change any value
-    for i in np.random.default_rng(0).choice(len(b), 96, replace=False):
-        it = b.integral(int(i))
-        close(out1[i], o.mdi_nodes(it.family, it.d, it.a, it.n_last, 16, it.c, it.w), it.family)
+    out1 = mdi.mdi_lr_integrate_batched(d_descs, pool, len(b), order=d_order, precision=prec).cpu().numpy()
+    out2 = mdi.mdi_lr_integrate_batched(d_descs, pool, len(b), precision=prec).cpu().numpy()
+    np.testing.assert_array_equal(out1, out2)
+    assert_batch_close(out1, oracle_batch(4096, 0), TOL)
 
 
 @pytest.mark.parametrize("prec", ["fp32_eval_fp64", "fp32_eval_df32"])
@@ -394,18 +414,6 @@ def test_df64_nodes_matches_fp64_oracle(fam, d, a, nd, P):
     close(got, o.mdi_nodes(fam, d, a, nd, P, params[:d], params[d:]), fam)
 
 
-def test_df64_batched_full_size_sampled():
-    b = inputs.batch(count=4096, seed=0)
-    _, d_descs, d_order, pool = _batch_to_device(b)
-    out = mdi.mdi_lr_integrate_batched(d_descs, pool, len(b), order=d_order, precision="df64").cpu().numpy()
-    worst = 0.0
-    for i in np.random.default_rng(1).choice(len(b), 128, replace=False):
-        it = b.integral(int(i))
-        ref = o.mdi_nodes(it.family, it.d, it.a, it.n_last, 16, it.c, it.w)
-        worst = max(worst, abs(out[i] - ref) / abs(ref))
-    assert worst <= TOL, worst
-
-
 def test_df64_wide_parameter_range():
     """Larger c (steeper Gaussians and peaks) than the batch draws: the double-float
     exp and reciprocal keep 1e-12 over the state's wider dynamic range."""
@@ -413,3 +421,24 @@ def test_df64_wide_parameter_range():
         params = inputs.random_product(fam, 15, seed=seed, c_range=(0.5, 4.0))
         got = mdi.mdi_lr_integrate(fam, dev(params), 15, 24, 24, state="nodes", precision="df64").item()
         close(got, o.mdi_nodes(fam, 15, 24, 24, 16, params[:15], params[15:]), fam)
+
+
+@pytest.mark.parametrize("fam,state", [("exp", "closed"), ("osc", "closed"), ("gauss", "nodes"), ("peak", "nodes"),
+                                       ("exp", "exact")])
+def test_generating_vector_argument(fam, state):
+    """Algorithm 2's z, given explicitly as Example 2's Korobov vector (from the
+    library's exact routine), gives the value of the call without it, bit for bit;
+    so does the adjoint."""
+    d, a, nl = 5, 12, 7
+    params = inputs.random_product(fam, d, seed=8)
+    z = mdi.korobov_vector(d, a, nl * a ** (d - 1))
+    np.testing.assert_array_equal(z.astype(np.uint64), o.korobov_z(d, a, nl * a ** (d - 1)))
+    v0 = mdi.mdi_lr_integrate(fam, dev(params), d, a, nl, state=state).item()
+    v1 = mdi.mdi_lr_integrate(fam, dev(params), d, a, nl, state=state, z=z).item()
+    assert v0 == v1
+    if state != "exact":
+        _, g0 = mdi.mdi_lr_grad(fam, dev(params), d, a, nl, state=state)
+        _, g1 = mdi.mdi_lr_grad(fam, dev(params), d, a, nl, state=state, z=z)
+        assert torch.equal(g0, g1)
+    with pytest.raises(mdi.MdiError):
+        mdi.mdi_lr_integrate(fam, dev(params), d, a, nl, state=state, z=z + np.eye(1, d, 2, dtype=np.int64)[0])

@@ -107,3 +107,17 @@ def test_shift_average_estimates_the_integral_and_its_error():
     exact = o.closed_form("gauss", d, params[:d], params[d:])
     assert abs(mean.item() - exact) <= 4.0 * se.item() + 1e-15
     assert se.item() < 1e-3 * abs(exact)
+
+
+@pytest.mark.parametrize("R", [1, 2, 17, 64, 1000, 65535])
+def test_shifted_estimate_kernel_matches_its_definition(R):
+    """The device estimate of Section 2.1 (mean of the replicates and its standard
+    error, sqrt(sum (v - mean)^2 / (R (R - 1)))) against the same formulas in numpy
+    on the same values, including a large common offset (the two-pass variance
+    keeps the spread that a one-pass formula would cancel)."""
+    vals = 3.0e6 + np.random.default_rng(R).normal(0.0, 1e-3, R)
+    mean, se = mdi.shifted_estimate(dev(vals))
+    ref_mean = float(np.mean(vals))
+    ref_se = float(np.std(vals, ddof=1) / math.sqrt(R)) if R > 1 else 0.0
+    assert abs(mean.item() - ref_mean) <= 1e-14 * abs(ref_mean)
+    assert abs(se.item() - ref_se) <= 1e-9 * max(ref_se, 1e-300) if R > 1 else se.item() == 0.0

@@ -1,5 +1,5 @@
 """The ncu summaries under profiles/ name commands that run committed files only:
-every workload they profile is a case of paper_2404_08867_gb300.cases, every ncu
+every workload they profile is a case of bench.py --case, every ncu
 command leaves the clocks alone (--clock-control none), and a full capture names
 one kernel and a bounded launch count.  Checked as text; nothing runs."""
 import pathlib
@@ -7,7 +7,8 @@ import re
 
 ROOT = pathlib.Path(__file__).resolve().parent.parent
 PROFILES = sorted((ROOT / "profiles").glob("*.md"))
-CASES_SRC = (ROOT / "paper_2404_08867_gb300" / "cases.py").read_text()
+BENCH_SRC = (ROOT / "bench.py").read_text()
+CASES_SRC = BENCH_SRC[BENCH_SRC.index("def build_case("):BENCH_SRC.index("def run_case(")]
 
 
 def _case_names():
@@ -24,7 +25,9 @@ def test_there_are_profiles():
 def test_profiled_workloads_are_committed_cases():
     known = _case_names()
     for p in PROFILES:
-        for name in re.findall(r"paper_2404_08867_gb300\.cases ([a-z0-9-]+)", p.read_text()):
+        text = p.read_text()
+        assert "paper_2404_08867_gb300.cases" not in text, p.name
+        for name in re.findall(r"bench\.py --case ([a-z0-9-]+)", text):
             assert name in known, (p.name, name)
 
 
