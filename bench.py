@@ -536,7 +536,7 @@ def extra_time_to_1e6_vs_d(torch, mdi, inputs, dims=(4, 6, 8, 10, 12, 16, 20, 24
 # is repeated.
 TRAFFIC_SOURCES = ["paper_2404_08867_gb300/csrc/mdi_nodes.cu", "paper_2404_08867_gb300/csrc/mdi_nodes.cuh",
                    "paper_2404_08867_gb300/csrc/mdi_common.cuh"]
-PROFILED_TRAFFIC = {"df64": ("67f2f94470e4c282", 1718528)}
+PROFILED_TRAFFIC = {"fp64": ("3bba43dfae0a8429", 1672960)}
 
 
 def kernel_sources_key() -> str:

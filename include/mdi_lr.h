@@ -474,6 +474,13 @@ mdi_status mdi_peak_probe(int32_t kind, int32_t iters, double *sink, mdi_stream_
 /* Threads one mdi_peak_probe launch runs on the current device (0 for a bad kind). */
 int64_t mdi_peak_probe_threads(int32_t kind);
 
+/* Test hook (the paper has no counterpart): y[i] = the FP64 batched node-state
+ * sweep's own exp(x[i]) (which = 0: Tang's table-driven method) or 1/x[i]
+ * (which = 1: float seed and one cubic Newton-Raphson step; x[i] > 0), so tests can
+ * hold them to CUDA's exp and IEEE division.  x, y: DEVICE, n doubles.  One
+ * launch on `stream`; MDI_EINVAL for a bad `which`, pointer or n < 1. */
+mdi_status mdi_debug_fp64_phi(int32_t which, const double *x, double *y, int64_t n, mdi_stream_t stream);
+
 const char *mdi_status_string(mdi_status status);
 /* Text of the last CUDA error seen by this library on the calling host thread. */
 const char *mdi_last_cuda_error(void);

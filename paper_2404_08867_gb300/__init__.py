@@ -406,6 +406,17 @@ def mdi_peak_probe(kind: str, iters: int, sink: Optional[torch.Tensor] = None, s
     return sink
 
 
+def mdi_debug_fp64_phi(which: str, x: torch.Tensor, stream=None) -> torch.Tensor:
+    """The FP64 batched sweep's own exp ("exp") or reciprocal ("rcp") of every
+    element of a float64 CUDA tensor (test hook)."""
+    _dev_f64(x, "x")
+    y = torch.empty_like(x)
+    _ffi.check(_ffi.load().mdi_debug_fp64_phi({"exp": 0, "rcp": 1}[which], ctypes.c_void_p(x.data_ptr()),
+                                              ctypes.c_void_p(y.data_ptr()), int(x.numel()), _stream(stream)),
+               "mdi_debug_fp64_phi")
+    return y
+
+
 def mdi_debug_lattice_indices(n: int, z: Sequence[int], j0: int, count: int, device="cuda",
                               stream=None) -> torch.Tensor:
     """(count, d) int64 CUDA tensor of (j0 + t) z_i mod n from the kernel's generator."""

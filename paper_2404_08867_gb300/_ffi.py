@@ -57,6 +57,7 @@ SIGNATURES = {
     "mdi_peak_probe": (_I32, [_I32, _I32, _P, _P]),
     "mdi_peak_probe_threads": (_I64, [_I32]),
     "mdi_debug_lattice_indices": (_I32, [_I32, _I64, _P, _I64, _I64, _P, _P]),
+    "mdi_debug_fp64_phi": (_I32, [_I32, _P, _P, _I64, _P]),
     "mdi_midpoint_integrate": (_I32, [_I32, _I32, _I64, _I64, _P, _P, _P, _SZ, _P]),
     "lattice_korobov_search": (_I32, [_I32, _I32, _I64, _I64, _I64, _P, _P, _P, _SZ, _P]),
     "lattice_korobov_search_workspace_size": (_I32, [_I64, _c.POINTER(_SZ)]),

@@ -57,10 +57,49 @@ def exp2_table_source() -> str:
             "static __device__ const float2 kExp2TableGen[256] = {\n" + "\n".join(rows) + "\n};\n")
 
 
+def exp64_constants_source() -> str:
+    """Constants of the FP64 table-driven exp (Tang's method) from their
+    definitions, evaluated with 60-digit decimal arithmetic and rounded once to
+    double: 2^(j/256) for j = 0..255; 256/ln2 (only used to pick the table index);
+    ln2/256 split as L1 + L2 with L1 holding 33 significant bits, so that n L1 is
+    exact for |n| < 2^20."""
+    import decimal
+    from fractions import Fraction
+    ctx = decimal.Context(prec=60)
+    ln2 = ctx.ln(decimal.Decimal(2))
+    L = Fraction(ln2) / 256
+    e = 0
+    while Fraction(2) ** e <= L:
+        e += 1
+    while Fraction(2) ** e > L:
+        e -= 1
+    scale = Fraction(2) ** (32 - e)
+    L1 = Fraction(round(L * scale)) / scale
+    L2 = float(L - L1)
+    inv = float(Fraction(256) / Fraction(ln2))
+    rows = []
+    for j in range(256):
+        v = ctx.power(decimal.Decimal(2), ctx.divide(decimal.Decimal(j), decimal.Decimal(256)))
+        rows.append(f"    {float(v).hex()},")
+    return ("// Generated by build.py: constants of the FP64 table-driven exp.\n"
+            f"static constexpr double kExp64Inv = {inv.hex()};  // 256 / ln2\n"
+            f"static constexpr double kExp64L1 = {float(L1).hex()};  // ln2/256, 33 significant bits\n"
+            f"static constexpr double kExp64L2 = {L2.hex()};  // ln2/256 - L1\n"
+            "static __device__ const double kExp2TableD[256] = {\n" + "\n".join(rows) + "\n};\n")
+
+
 def _write_generated():
     os.makedirs(GEN, exist_ok=True)
+    _write_if_changed(os.path.join(GEN, "mdi_exp64_consts.inc"), exp64_constants_source())
     path = os.path.join(GEN, "mdi_exp2_table.inc")
     src = exp2_table_source()
+    if not os.path.exists(path) or open(path).read() != src:
+        with open(path + ".tmp", "w") as f:
+            f.write(src)
+        os.replace(path + ".tmp", path)
+
+
+def _write_if_changed(path: str, src: str):
     if not os.path.exists(path) or open(path).read() != src:
         with open(path + ".tmp", "w") as f:
             f.write(src)

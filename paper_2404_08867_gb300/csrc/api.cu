@@ -387,6 +387,11 @@ mdi_status mdi_midpoint_ridge(int32_t d, int64_t N, int64_t n_last, double c0, d
   return ridge_launch(d, N, n_last, c0, power, out, workspace, ws_bytes, (cudaStream_t)stream);
 }
 
+mdi_status mdi_debug_fp64_phi(int32_t which, const double *x, double *y, int64_t n, mdi_stream_t stream) {
+  if ((which != 0 && which != 1) || !x || !y || n < 1) return MDI_EINVAL;
+  return fp64_phi_debug_launch(which, x, y, n, (cudaStream_t)stream);
+}
+
 mdi_status mdi_debug_lattice_indices(int32_t d, int64_t n, const int64_t *z, int64_t j0, int64_t count,
                                      int64_t *r_out, mdi_stream_t stream) {
   return lattice_indices_launch(d, n, z, j0, count, r_out, (cudaStream_t)stream);

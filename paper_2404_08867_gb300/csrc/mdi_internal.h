@@ -83,6 +83,7 @@ mdi_status nodes_batched_launch(const mdi_batch_desc *descs, const int32_t *orde
 // Device status word of a batched workspace (MDI_DEV_* flags): bytes needed to
 // hold it, and a stream-ordered read (waits for the stream), optionally cleared.
 size_t nodes_status_word_bytes();
+mdi_status fp64_phi_debug_launch(int which, const double *x, double *y, int64_t n, cudaStream_t stream);
 mdi_status nodes_read_status(const void *workspace, bool clear, uint32_t *word, cudaStream_t stream);
 // Single integral through the batched machinery (descriptor built on the device).
 size_t nodes_single_workspace_bytes(const NodesConfig &cfg);

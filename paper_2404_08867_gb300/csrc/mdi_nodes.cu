@@ -43,6 +43,7 @@
 #include <algorithm>
 
 #include "mdi_common.cuh"
+#include "mdi_exp64_consts.inc"
 #include "mdi_internal.h"
 #include "mdi_nodes.cuh"
 
@@ -68,7 +69,11 @@ struct NodesShared {
   float2 xadf[kNodesPMax];    // xi_p / a as float pairs (DF64), per integral
   double2 red[kNodesMaxBlock / kWarp];
   float4 redf[kNodesMaxBlock / kWarp];
-  float2 exp2tab[kExpTable];  // 2^(j/256) as float pairs (double-float exp)
+  union {
+    float2 exp2tab[kExpTable];  // 2^(j/256) as float pairs (double-float exp, DF64)
+    double exp2d[kExpTable];    // 2^(j/256) as doubles (FP64 exp)
+  };
+  double qd[kNodesAMax];      // q as a double, q < 64 (FP64)
   LevelConst lc[kLvChunk];    // constants of axes base .. base+63
   float2 iadf;                // 1/a as a float pair (DF64)
   int inst;
@@ -82,13 +87,17 @@ struct NodesShared {
 // and xi_p/a.
 struct NodesConsts {
   float2 exp2tab[kExpTable];
+  double exp2d[kExpTable];
   double xi[kNodesPMax], bw[kNodesPMax];
   float2 ia[kNodesAMax + 1];
   float2 xa[kNodesAMax + 1][kNodesPMax];
 };
 
 __global__ void nodes_consts_kernel(int P, NodesConsts *__restrict__ kc) {
-  for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) kc->exp2tab[j] = exp2_table_entry(j);
+  for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) {
+    kc->exp2tab[j] = exp2_table_entry(j);
+    kc->exp2d[j] = kExp2TableD[j];
+  }
   for (int t = threadIdx.x; t < P; t += blockDim.x) {
     kc->xi[t] = cheb_node(t, P);
     kc->bw[t] = cheb_weight(t, P);
@@ -780,6 +789,96 @@ __device__ void sweep_paired(NodesShared &sh, const NodesConsts *__restrict__ kc
   if (tid == 0 && S != 0) *out_slot = scale_pow2(*out_slot, S);  // the thread that wrote it
 }
 
+// exp(x) in FP64 by a table-driven reduction (P. T. P. Tang, "Table-driven
+// implementation of the exponential function in IEEE floating-point arithmetic",
+// ACM TOMS 15, 1989): x = (256 k + j) ln2/256 + r with |r| <= ln2/512, n = 256 k + j
+// picked by the round-to-integer of adding 1.5 2^52 (n lands in the low word);
+// ln2/256 = L1 + L2 with n L1 exact, so r = (x - n L1) - n L2 has one rounding;
+// exp(r) - 1 = r + r^2 (1/2 + r (1/6 + r (1/24 + r/120))) (the next Taylor term
+// is below 2^-66 relative); the result is 2^(j/256) (1 + (exp(r) - 1)) with the
+// table entry read from `T` and 2^k put into its exponent field by an integer add.
+// Ten FP64 operations.  Off the hot path (decided on the integer high word, so no
+// FP64 compare): |x| >= 745.15 gives 0 or +inf (exp(-745.14) already rounds to
+// 0) and NaN stays NaN, selected at the end rather than returned early; results
+// outside the normal range apply 2^k as two normal factors.  No call into the
+// math library and no early return: either made ptxas give the sweep kernel
+// half its registers, with spills.
+__device__ __forceinline__ double exp_tang64(double x, const double *__restrict__ T) {
+  const int hx = __double2hiint(x), ax = hx & 0x7FFFFFFF;
+  const bool big = ax >= 0x40874933;  // |x| >= 745.15, inf or NaN: result selected below
+  const double xs = big ? 0.0 : x;
+  const double shifted = fma(xs, kExp64Inv, 0x1.8p52);
+  const int n = __double2loint(shifted);
+  const double nd = shifted - 0x1.8p52;
+  const double r = fma(-nd, kExp64L2, fma(-nd, kExp64L1, xs));
+  const double p = fma(r, fma(r, fma(r, 1.0 / 120.0, 1.0 / 24.0), 1.0 / 6.0), 0.5);
+  const double em1 = fma(r * r, p, r);
+  const int k = n >> 8;  // floor(n / 256), -1076 <= k <= 1075
+  const double tj = T[n & (kExpTable - 1)];
+  double res;
+  if (k >= -1021 && k <= 1023) {  // 2^k tj normal
+    const double t = __longlong_as_double(__double_as_longlong(tj) + ((long long)k << 52));
+    res = fma(t, em1, t);
+  } else {
+    const int h = k / 2;  // both 2^h and 2^(k-h) are normal: underflow or overflow
+    res = fma(tj, em1, tj) * __longlong_as_double((long long)(h + 1023) << 52) *  // happens in the last product
+          __longlong_as_double((long long)(k - h + 1023) << 52);
+  }
+  if (big) {
+    const bool nan = ax > 0x7FF00000 || (ax == 0x7FF00000 && __double2loint(x) != 0);
+    res = nan ? x : (hx < 0 ? 0.0 : __longlong_as_double(0x7FF0000000000000ll));
+  }
+  return res;
+}
+
+// 1/D for D > 0 in FP64: a float seed from D's leading 20 fraction bits (integer
+// operations build the float and bring the seed back), the hardware's
+// approximate float reciprocal, and one cubic Newton-Raphson step
+// y = y0 (1 + e + e^2), e = 1 - D y0: the seed's relative error (below 2^-19)
+// cubes to below 2^-57.  Three FP64 operations.  D outside [2^-120, 2^120] is first
+// brought to [1, 2) by an exact power of two (its exponent field), and the result
+// scaled back the same way (as two normal factors); D = 0, subnormal, infinite
+// or NaN follow IEEE division's results (+inf, a huge value or +inf, 0, NaN).  No
+// call into the math library (see exp_tang64).
+__device__ __forceinline__ double rcp_nr64_core(double D, int e) {
+  const int hi = __double2hiint(D);
+  const float f = __int_as_float(((e + 127) << 23) | ((hi & 0xFFFFF) << 3));
+  float yf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(f));
+  const int yb = __float_as_int(yf);
+  const double y0 = __hiloint2double(((((yb >> 23) & 0xFF) - 127 + 1023) << 20) | ((yb & 0x7FFFFF) >> 3),
+                                     (yb & 7) << 29);
+  const double er = fma(-D, y0, 1.0);
+  return fma(y0, fma(er, er, er), y0);
+}
+__device__ __forceinline__ double rcp_nr64(double D) {
+  const int hi = __double2hiint(D);
+  int e = ((hi >> 20) & 0x7FF) - 1023;
+  if (e >= -120 && e <= 120) return rcp_nr64_core(D, e);
+  if (e == 1024) return D != D ? D : 0.0;  // inf -> 0, NaN -> NaN
+  double post = 1.0;
+  if (e == -1023) {  // zero or subnormal
+    if (D == 0.0) return __longlong_as_double(0x7FF0000000000000ll);
+    D *= 0x1p600;     // exact, now normal
+    post = 0x1p600;
+    e = ((__double2hiint(D) >> 20) & 0x7FF) - 1023;
+  }
+  // D = m 2^e with m in [1, 2): 1/D = (1/m) 2^-e
+  const double m = __longlong_as_double((__double_as_longlong(D) & 0x800FFFFFFFFFFFFFll) | (1023ll << 52));
+  const int h = -e / 2;
+  return rcp_nr64_core(m, 0) * __longlong_as_double((long long)(h + 1023) << 52) *
+         __longlong_as_double((long long)(-e - h + 1023) << 52) * post;
+}
+
+// phi_j in FP64 at the affine argument t of the point (see phi_affine_coeffs):
+// Gaussian exp(-t^2), peak 1/(t^2 + 1/c^2), exponential exp(t).
+template <int FAM>
+__device__ __forceinline__ double phi_t64(double t, double ic2, const double *__restrict__ T) {
+  if constexpr (FAM == MDI_FAM_GAUSS) return exp_tang64(-(t * t), T);
+  else if constexpr (FAM == MDI_FAM_PEAK) return rcp_nr64(fma(t, t, ic2));
+  else return exp_tang64(t, T);
+}
+
 // The same pairing in FP64 (real families): the state (E_t, O_t) in sh.G as
 // doubles, the paired table as (Lp, Lm) doubles, phi in FP64.  P/2 fused
 // multiply-adds per cluster point instead of P, on the FP64 pipe that bounds
@@ -811,8 +910,30 @@ __device__ void sweep_paired_fp64(NodesShared &sh, const NodesConsts *__restrict
       __syncthreads();
     }
     const LevelConst &L = sh.lc[j % kLvChunk];
-    const AxisParams ap{L.c, L.w, L.ic2};
     const int rb = (k - 1) & 1, wb = k & 1;
+    // phi's argument at the cluster points u_a = q/a + xi_pp/a of node pp and
+    // u_b = 1 - u_a of node P-1-pp, as t = s1 q + s0:
+    //   GAUSS  t = c (u - w)      (sign of t_b immaterial: phi depends on t^2)
+    //   PEAK   t = u - w          (likewise)
+    //   EXP    t = c u
+    double s1a = 0.0, s0a = 0.0, s1b = 0.0, s0b = 0.0;
+    if constexpr (!F32) {
+      const double x0 = xa * inv_a;  // xi_pp / a
+      if constexpr (FAM == MDI_FAM_GAUSS) {
+        s1a = s1b = L.c * inv_a;
+        s0a = L.c * (x0 - L.w);
+        s0b = L.c * (x0 - (1.0 - L.w));
+      } else if constexpr (FAM == MDI_FAM_PEAK) {
+        s1a = s1b = inv_a;
+        s0a = x0 - L.w;
+        s0b = x0 - (1.0 - L.w);
+      } else {
+        s1a = L.c * inv_a;
+        s1b = -s1a;
+        s0a = L.c * x0;
+        s0b = L.c - s0a;
+      }
+    }
     double acc_a = 0.0, acc_b = 0.0;
     if (act) {
       for (int q = qs; q < a; q += Q) {
@@ -843,8 +964,10 @@ __device__ void sweep_paired_fp64(NodesShared &sh, const NodesConsts *__restrict
           acc_a = fma((double)phi_f<FAM>(fmaf((float)q, iaf, xaf), af), ga, acc_a);
           acc_b = fma((double)phi_f<FAM>(fmaf((float)(a - 1 - q), iaf, xbf), af), gb, acc_b);
         } else {
-          acc_a = fma(phi<FAM, false>(((double)q + xa) * inv_a, ap), ga, acc_a);
-          acc_b = fma(phi<FAM, false>(((double)(a - 1 - q) + xb) * inv_a, ap), gb, acc_b);
+          // The arguments of both mirrored points are affine in q (u_b = 1 - u_a).
+          const double qd = sh.qd[q];
+          acc_a = fma(phi_t64<FAM>(fma(s1a, qd, s0a), L.ic2, sh.exp2d), ga, acc_a);
+          acc_b = fma(phi_t64<FAM>(fma(s1b, qd, s0b), L.ic2, sh.exp2d), gb, acc_b);
         }
       }
     }
@@ -905,6 +1028,10 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
   }
   if (PREC == MDI_PREC_DF64)
     for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) sh.exp2tab[j] = kc->exp2tab[j];
+  if (PREC == MDI_PREC_FP64) {
+    for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) sh.exp2d[j] = kc->exp2d[j];
+    for (int q = threadIdx.x; q < kNodesAMax; q += blockDim.x) sh.qd[q] = (double)q;
+  }
   int staged_a = -1;
   // counter[0]: next work item; counter[1]: CTAs finished; counter[2]: preparation
   // tag; counter[3]: the device status word (MDI_DEV_* flags, OR-ed in).
@@ -1025,6 +1152,16 @@ __global__ void nodes_arm_kernel(unsigned *counter, unsigned tag) {
   counter[1] = 0u;
   counter[2] = tag;
   counter[3] = 0u;
+}
+
+// Element-wise view of the FP64 exp and reciprocal of the paired sweep (tests
+// compare them with CUDA's exp and IEEE division).
+__global__ void fp64_phi_debug_kernel(int which, const double *__restrict__ x, double *__restrict__ y, int64_t n) {
+  __shared__ double T[kExpTable];
+  for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) T[j] = kExp2TableD[j];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = which == 0 ? exp_tang64(x[i], T) : rcp_nr64(x[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1165,6 +1302,12 @@ mdi_status nodes_batched_launch(const mdi_batch_desc *descs, const int32_t *orde
 }
 
 size_t nodes_status_word_bytes() { return 4 * sizeof(unsigned); }
+
+mdi_status fp64_phi_debug_launch(int which, const double *x, double *y, int64_t n, cudaStream_t stream) {
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8));
+  fp64_phi_debug_kernel<<<grid, 256, 0, stream>>>(which, x, y, n);
+  return check_launch();
+}
 
 mdi_status nodes_read_status(const void *workspace, bool clear, uint32_t *word, cudaStream_t stream) {
   unsigned *status = (unsigned *)workspace + 3;  // counter[3]
