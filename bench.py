@@ -818,6 +818,38 @@ def extra_scale(torch, mdi, inputs):
     return res
 
 
+def extra_step_size(torch, mdi, inputs):
+    """Algorithm 1's step size m = 1, 2, 3 with the node state (P = 16 unless stated):
+    the state is read once per m levels, at the price of a^m cluster tuples per
+    operator instead of a.  d = 100, N = 16: time and value for the Gaussian of the
+    differentiation workload and for exp(sum x_j/j^2), each against the oracle's
+    step-m value, the exponential one also against its closed state (the exact
+    rule, so that difference is the node state's own error); and on an
+    enumerable case (d = 6, a = 8, P = 8) each m's error against the exact sweep."""
+    ref = golden_oracle()["step"]
+    res = {"workload": "node state, step m = 1, 2, 3"}
+    g = inputs.gaussian(100, 16, seed=0)
+    e = inputs.scale_exp(100, 16)
+    for name, fam, w in (("gauss_d100", "gauss", g), ("exp_d100", "exp", e)):
+        p = torch.as_tensor(w.params).cuda()
+        rows = {}
+        for m in (1, 2, 3):
+            v, ms = event_ms(torch, lambda: mdi.mdi_lr_integrate(fam, p, 100, 16, state="nodes", step=m), reps=3)
+            row = {"ms": ms, "value": v.item(), "rel_err_vs_oracle": abs(v.item() / ref[fam][str(m)] - 1.0)}
+            if fam == "exp":
+                row["rel_err_vs_exact_rule"] = abs(v.item() / ref["exp_closed"] - 1.0)
+            rows[f"m{m}"] = row
+        res[name] = rows
+    small = {}
+    for fam in ("gauss", "peak"):
+        p = torch.as_tensor(inputs.random_product(fam, 6, seed=19)).cuda()
+        ex = mdi.mdi_lr_integrate(fam, p, 6, 8, state="exact").item()
+        small[fam] = {f"m{m}": abs(mdi.mdi_lr_integrate(fam, p, 6, 8, state="nodes", nodes=8, step=m).item() / ex - 1.0)
+                      for m in (1, 2, 3)}
+    res["d6_a8_P8_rel_err_vs_exact_sweep"] = small
+    return res
+
+
 def measure_peaks(torch, mdi, reps=3):
     """FMA throughput of this GPU at its current clock, from the library's probe
     kernel (16 independent FMA chains per thread, several CTAs per SM): the best
@@ -1102,6 +1134,7 @@ def main():
             line["precision_workload"] = extra_precision(torch, mdi, inputs)
             line["differentiation_workload"] = extra_differentiation(torch, mdi, inputs)
             line["scale_workload"] = extra_scale(torch, mdi, inputs)
+            line["step_size_workload"] = extra_step_size(torch, mdi, inputs)
             line["paper_table_workload"] = extra_paper_tables(torch, mdi)
             line["lattice_search_workload"] = extra_lattice_search(torch, mdi)
             line["paper_context"] = extra_paper_context(torch, mdi)

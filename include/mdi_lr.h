@@ -124,7 +124,13 @@ typedef struct {
   int32_t table_in_l1; /* node-state kernels: 0 = stage each integral's basis table in
                           shared memory (when it fits 64 KiB), 1 = read it through L1
                           (less shared memory, more resident CTAs) */
-  int32_t reserved;    /* must be 0 */
+  int32_t step;        /* m of Algorithm 1: transformed axes contracted per iteration,
+                          0 or 1 (the paper's choice, m = 1), 2 or 3.  With the exact
+                          and closed states every m gives the same sum; with the node
+                          state, m > 1 reads the state once per m levels (Algorithm 1,
+                          eq. 2.14c: the factors of the m axes multiplied over the
+                          a^m digit tuples), for single integrals in FP64 with
+                          a^m <= 4096 and no gradient; other uses MDI_EUNSUPPORTED */
 } mdi_opts;
 
 /* ---------------------------------------------------------------------------

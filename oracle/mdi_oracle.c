@@ -457,6 +457,61 @@ int or_mdi_nodes_states(int fam, int d, uint64_t a, uint64_t nd, int P, const do
   return 0;
 }
 
+/* Node state with step size m (Algorithm 1 with m = 1, 2, 3; eq. 2.14c): every
+ * iteration contracts m transformed axes at once instead of one.  The symbolic
+ * function after the iteration, g_{k-m}, is kept at the P nodes like the m = 1
+ * state; its value at node xi_p is the weighted sum over the a^m digit tuples
+ * (q_i, ..., q_{i+m-1}) of the contracted axes of the product of their factors,
+ * the coordinates generated outermost first by the affine recurrence of
+ * Theorem 3.1 / Lemma 3.2 (x_{i+m} = xi_p, x_j = (q_j + x_{j+1}) / a), times the
+ * previous iteration's function read at the innermost coordinate x_i.  Each tuple
+ * weighs 1/a^m (w_{i_1} ... w_{i_m} with w = 1/a).  The d-1 cluster axes are taken
+ * in order, the first m first (the paper deletes the first m components); when
+ * m does not divide d-1 the last iteration takes the remaining axes.  The last
+ * axis (n_d points s/n_d) is summed as in the m = 1 sweep.  m = 1 is
+ * or_mdi_nodes. */
+double or_mdi_nodes_step(int fam, int d, uint64_t a, uint64_t nd, int P, int m, const double *c,
+                         const double *w) {
+  if (!is_product(fam) || P < 2 || m < 1 || m > 3) return NAN;
+  double *xi = (double *)malloc(sizeof(double) * (size_t)P);
+  double *bw = (double *)malloc(sizeof(double) * (size_t)P);
+  cplx *G = (cplx *)malloc(sizeof(cplx) * (size_t)P);
+  cplx *H = (cplx *)malloc(sizeof(cplx) * (size_t)P);
+  cheb_nodes(P, xi, bw);
+  for (int p = 0; p < P; ++p) G[p] = 1.0;
+  for (int i = 1; i < d; i += m) {           /* contract axes i .. i+mi-1 (1-based) */
+    int mi = (d - i < m) ? d - i : m;
+    uint64_t tuples = 1;  /* a^mi: every tuple weighs 1/a^mi */
+    for (int j = 0; j < mi; ++j) tuples *= a;
+    for (int p = 0; p < P; ++p) {
+      cplx acc = 0.0;
+      for (uint64_t t = 0; t < tuples; ++t) {
+        /* digit of axis i+j is (t / a^j) mod a */
+        double x = xi[p];
+        cplx prod = 1.0;
+        for (int j = mi - 1; j >= 0; --j) {
+          uint64_t aj = 1;
+          for (int l = 0; l < j; ++l) aj *= a;
+          uint64_t q = (t / aj) % a;
+          x = ((double)q + x) / (double)a;  /* x_{i+j} */
+          prod *= phi(fam, i + j - 1, x, c, w);
+        }
+        acc += prod * bary(P, xi, bw, G, x);
+      }
+      H[p] = acc / (double)tuples;
+    }
+    memcpy(G, H, sizeof(cplx) * (size_t)P);
+  }
+  cplx acc = 0.0;
+  for (uint64_t s = 0; s < nd; ++s) {
+    double u = (double)s / (double)nd;
+    acc += phi(fam, d - 1, u, c, w) * (d > 1 ? bary(P, xi, bw, G, u) : 1.0);
+  }
+  acc /= (double)nd;
+  free(xi); free(bw); free(G); free(H);
+  return creal(front(fam, w) * acc);
+}
+
 /* Forward-mode derivative of the node-state sweep with respect to c_t and w_t for
  * the parameters t listed in which[0..nwhich) (indices into the 2d-long gradient:
  * t < d is c_t, t >= d is w_{t-d}; for OR_OSC index d is u).  The tangent Gdot is

@@ -69,6 +69,7 @@ def _load():
                 "or_mdi_closed": (D, [I, I, U, U, P, P]),
                 "or_mdi_closed_grad": (I, [I, I, U, U, P, P, P]),
                 "or_mdi_nodes": (D, [I, I, U, U, I, P, P]),
+                "or_mdi_nodes_step": (D, [I, I, U, U, I, I, P, P]),
                 "or_mdi_nodes_states": (I, [I, I, U, U, I, P, P, P]),
                 "or_mdi_nodes_grad": (I, [I, I, U, U, I, P, P, P, I, P]),
                 "or_bary_matrix": (I, [I, U, P]),
@@ -183,6 +184,13 @@ def mdi_closed_grad(family, d, a, nd, c, w=None) -> np.ndarray:
 def mdi_nodes(family, d, a, nd, P, c, w=None) -> float:
     c, w = _f64(c, d), _f64(w, d)
     return _load().or_mdi_nodes(_fam(family), d, a, nd, P, _p(c), _p(w))
+
+
+def mdi_nodes_step(family, d, a, nd, P, m, c, w=None) -> float:
+    """Node-state sweep with step size m of Algorithm 1: m transformed axes
+    contracted per iteration (m = 1 is mdi_nodes)."""
+    c, w = _f64(c, d), _f64(w, d)
+    return _load().or_mdi_nodes_step(_fam(family), d, a, nd, P, m, _p(c), _p(w))
 
 
 def mdi_nodes_states(family, d, a, nd, P, c, w=None) -> np.ndarray:

@@ -59,10 +59,12 @@ def _dev_f64(t: torch.Tensor, name: str) -> torch.Tensor:
     return t
 
 
-def _opts(state="auto", precision="fp64", nodes=0, block=0, ctas_per_sm=0, checkpoint=0, table_in_l1=0) -> MdiOpts:
+def _opts(state="auto", precision="fp64", nodes=0, block=0, ctas_per_sm=0, checkpoint=0, table_in_l1=0,
+          step=0) -> MdiOpts:
     o = MdiOpts()
     o.state, o.precision, o.nodes, o.block = _state(state), _prec(precision), int(nodes), int(block)
     o.ctas_per_sm, o.checkpoint, o.table_in_l1 = int(ctas_per_sm), int(checkpoint), int(bool(table_in_l1))
+    o.step = int(step)
     return o
 
 
@@ -236,8 +238,8 @@ def mdi_lr_integrate(family, params: torch.Tensor, d: int, a: int, n_last: Optio
     """MDI-LR value on the Korobov lattice with a points per transformed axis and
     n_last (default a) on the last one; ``z`` (optional) is Algorithm 2's
     generating vector, which must be Example 2's Korobov vector for (a, n); opts:
-    state, precision, nodes, block, ctas_per_sm.  Returns a 1-element float64 CUDA
-    tensor."""
+    state, precision, nodes, block, ctas_per_sm, checkpoint, step (Algorithm 1's m).
+    Returns a 1-element float64 CUDA tensor."""
     _dev_f64(params, "params")
     n_last = a if n_last is None else n_last
     if params.numel() < 2 * d:

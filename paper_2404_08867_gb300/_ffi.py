@@ -28,7 +28,7 @@ _SZ = _c.c_size_t
 
 class MdiOpts(ctypes.Structure):
     _fields_ = [("state", _I32), ("precision", _I32), ("nodes", _I32), ("block", _I32),
-                ("ctas_per_sm", _I32), ("checkpoint", _I32), ("table_in_l1", _I32), ("reserved", _I32)]
+                ("ctas_per_sm", _I32), ("checkpoint", _I32), ("table_in_l1", _I32), ("step", _I32)]
 
 
 BATCH_DESC_DTYPE = np.dtype([("family", np.int32), ("d", np.int32), ("a", np.int32), ("n_last", np.int32),

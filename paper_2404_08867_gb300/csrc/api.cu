@@ -50,8 +50,10 @@ static bool opts_ok(const mdi_opts *o) {
   if (o->precision < MDI_PREC_FP64 || o->precision > MDI_PREC_DF64) return false;
   if (o->nodes < 0 || o->block < 0 || o->ctas_per_sm < 0 || o->checkpoint < 0) return false;
   if (o->table_in_l1 != 0 && o->table_in_l1 != 1) return false;
-  return o->reserved == 0;
+  return o->step >= 0 && o->step <= 3;
 }
+
+
 
 static int resolve_state(int family, const mdi_opts *o) {
   int s = o ? o->state : MDI_STATE_AUTO;
@@ -222,6 +224,10 @@ mdi_status mdi_lr_workspace_size(int32_t family, int32_t d, int64_t a, int64_t n
       return MDI_OK;
     default: {
       const NodesConfig cfg = nodes_config(opts);
+      if (cfg.step > 1) {
+        *bytes = levels_step_workspace_bytes(d, a, cfg, opts->checkpoint);
+        return *bytes ? MDI_OK : MDI_EUNSUPPORTED;
+      }
       *bytes = use_levels(d) ? levels_workspace_bytes(d, a, cfg, opts ? opts->checkpoint : 0)
                                   : nodes_single_workspace_bytes(cfg);
       return MDI_OK;
@@ -242,7 +248,7 @@ mdi_status mdi_lr_integrate(int32_t family, int32_t d, int64_t a, int64_t n_last
     case MDI_STATE_CLOSED: return closed_launch(family, d, a, n_last, params, precision, out, workspace, ws_bytes, s);
     default: {
       const NodesConfig cfg = nodes_config(opts);
-      if (use_levels(d))
+      if (use_levels(d) || cfg.step > 1)
         return levels_launch(family, d, a, n_last, params, cfg, opts ? opts->checkpoint : 0, out, nullptr, workspace,
                              ws_bytes, s);
       return nodes_single_launch(family, d, a, n_last, params, cfg, out, workspace, ws_bytes, s);
@@ -261,6 +267,7 @@ mdi_status mdi_lr_grad_workspace_size(int32_t family, int32_t d, int64_t a, int6
       if (*bytes == 0) return MDI_EINVAL;
       return MDI_OK;
     default:
+      if (opts && opts->step > 1) return MDI_EUNSUPPORTED;
       *bytes = levels_workspace_bytes(d, a, nodes_config(opts), opts ? opts->checkpoint : 0);
       return MDI_OK;
   }
@@ -275,6 +282,7 @@ mdi_status mdi_lr_grad(int32_t family, int32_t d, int64_t a, int64_t n_last, con
   const int precision = opts ? opts->precision : MDI_PREC_FP64;
   if (precision != MDI_PREC_FP64) return MDI_EUNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
+  if (resolve_state(family, opts) == MDI_STATE_NODES && opts && opts->step > 1) return MDI_EUNSUPPORTED;
   switch (resolve_state(family, opts)) {
     case MDI_STATE_EXACT: return MDI_EUNSUPPORTED;
     case MDI_STATE_CLOSED: return closed_grad_launch(family, d, a, n_last, params, value, grad, workspace, ws_bytes, s);
@@ -302,6 +310,7 @@ mdi_status mdi_lr_integrate_batched(const mdi_batch_desc *descs, const int32_t *
   NvtxRange nvtx_scope("mdi_lr_integrate_batched");
   if (!opts_ok(opts) || pool_len < 0) return MDI_EINVAL;
   if (opts && opts->state != MDI_STATE_AUTO && opts->state != MDI_STATE_NODES) return MDI_EUNSUPPORTED;
+  if (opts && opts->step > 1) return MDI_EUNSUPPORTED;
   return nodes_batched_launch(descs, order, count, param_pool, pool_len, nodes_config(opts), out, workspace,
                               ws_bytes, (cudaStream_t)stream);
 }

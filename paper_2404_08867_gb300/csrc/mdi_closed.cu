@@ -13,17 +13,23 @@
 // GB300 mapping.  beta is an affine recurrence (beta_k = beta_{k-1}/a + c_k/a;
 // for OSC the same real recurrence gives the imaginary part), so instead of
 // walking the d levels one after the other on one SM:
-//   1. one CTA solves it with a block-wide scan of affine maps (gamma_k, all k);
+//   1. the recurrence is solved as a scan of affine maps (gamma_k, all k): for
+//      d <= 32 by one warp of every CTA of step 2 (shuffles), otherwise by one CTA
+//      in a launch of its own;
 //   2. the cluster sums of all levels run at once across the GPU: every level's
 //      r_k points are cut into chunks of up to 1024, one warp per chunk;
-//   3. the chunk sums of each level are added in chunk order (S_k);
-//   4. one CTA multiplies the S_k in level order.
-// Launch count does not depend on d or on a.
+//   3. the chunk sums of each level are added in chunk order (S_k), and
+//   4. the S_k multiplied in level order by a fixed tree: when the chunk sums
+//      number at most 2048, both by one CTA in one launch, otherwise a launch each.
+// So d <= 32 takes two launches whatever a (the small workload's time to 1e-6),
+// and the launch count never depends on d or on a beyond that.  Each launch
+// waits on no other CTA, so the workspace needs no initial contents.
 #include <algorithm>
 #include <cmath>
 
 #include "mdi_common.cuh"
 #include "mdi_exp2_table.inc"
+#include "mdi_fp64.cuh"
 #include "mdi_internal.h"
 #include "mdi_nodes.cuh"
 
@@ -32,6 +38,33 @@ namespace mdi {
 constexpr int kScanThreads = 1024;
 constexpr int kChunkThreads = 256;
 constexpr int64_t kChunkQ = 1024;  // most cluster points per warp chunk
+constexpr int kWarpScanMaxD = 32;  // gamma by one warp of each chunk CTA up to this d
+constexpr int kFinishMaxChunks = 2048;  // per-level sums and product in one CTA up to this many chunks
+constexpr int kAnchor = 16;             // FP64 cluster terms: a fresh exp every 16 points of a lane
+
+// gamma_k, k < d <= 32, by one warp: lane k holds the map beta -> (beta + c_k)/a
+// of level k (k < d - 1); an inclusive Hillis-Steele scan over shuffles composes
+// the maps of levels 0..k (earlier map first), which applied to beta_0 = 0 gives
+// beta_k, and gamma_k = beta_{k-1} + c_k.  Valid in lanes k < d.
+__device__ __forceinline__ double warp_gamma(int d, double inva, const double *__restrict__ params) {
+  const int lane = threadIdx.x & (kWarp - 1);
+  const double ck = lane < d ? params[lane] : 0.0;
+  double A = 1.0, B = 0.0;
+  if (lane < d - 1) {
+    A = inva;
+    B = ck * inva;
+  }
+#pragma unroll
+  for (int off = 1; off < kWarp; off <<= 1) {
+    const double pA = __shfl_up_sync(0xffffffffu, A, off), pB = __shfl_up_sync(0xffffffffu, B, off);
+    if (lane >= off) {
+      B = fma(A, pB, B);
+      A *= pA;
+    }
+  }
+  const double bprev = __shfl_up_sync(0xffffffffu, B, 1);
+  return (lane == 0 ? 0.0 : bprev) + ck;
+}
 
 // gamma_k (real: the exponent rate, or its imaginary part for OSC) for k = 1..d.
 __global__ void __launch_bounds__(kScanThreads) closed_scan_kernel(int d, double inva,
@@ -74,7 +107,10 @@ __global__ void __launch_bounds__(kScanThreads) closed_scan_kernel(int d, double
 
 // Chunks: levels k < d-1 have a points, cut into cpl chunks of q points; the last
 // level has n_last points in cpl_last chunks.  q (a multiple of 32, at most 1024)
-// is chosen so that about 32 warps per SM get a chunk when the levels are small.
+// is chosen so that about 8 warps per SM (two per sub-partition) get a chunk: a
+// warp instruction occupies GB300's FP64 unit about as long as a dependent FP64
+// result takes, so two warps per sub-partition keep it busy, and larger chunks
+// spread each warp's set-up over more points.
 // The reciprocals 1/a and 1/n_last of the two cluster radices are formed once on
 // the host (correctly rounded, the same double the device's division gives) and
 // also as float pairs: an FP64 division per chunk would cost GB300's FP64 pipe
@@ -87,7 +123,7 @@ struct Chunks {
 };
 static int64_t chunk_q(int d, int64_t a, int64_t n_last) {
   const double points = (double)(d - 1) * (double)a + (double)n_last;
-  const double target = (double)sm_count() * 32.0;
+  const double target = (double)sm_count() * 8.0;
   int64_t q = (int64_t)std::ceil(points / target);
   q = (q + 31) / 32 * 32;
   return std::max<int64_t>(32, std::min<int64_t>(kChunkQ, q));
@@ -117,17 +153,47 @@ __device__ __forceinline__ int chunk_base(int k, int d, int cpl) { return k < d 
 // |gamma| <= 64, whose terms e^(gamma x) lie in [e^-64, e^64] and whose chunk sums
 // (at most 1024 terms) stay inside the float range with normal low parts; other
 // levels are summed in FP64.
+// gamma: the levels' rates in global memory, or NULL for d <= kWarpScanMaxD, where
+// the CTA's first warp computes them (params, 1/a) into shared memory.  FP64 terms
+// of the exponential family use the table-driven exp of mdi_fp64.cuh.
 template <int FAM, int PREC, bool WITH_T>
 __global__ void __launch_bounds__(kChunkThreads) closed_chunk_kernel(int d, int64_t a, int64_t n_last, Chunks ch,
-                                                                     const double *__restrict__ gamma,
+                                                                     const double *__restrict__ gamma_g,
+                                                                     const double *__restrict__ params,
                                                                      double2 *__restrict__ partS,
                                                                      double2 *__restrict__ partT) {
   constexpr bool DFE = (PREC == MDI_PREC_DF64) && (FAM != MDI_FAM_OSC);
+  constexpr bool TANG = (PREC == MDI_PREC_FP64 || PREC == MDI_PREC_DF64) && (FAM != MDI_FAM_OSC);
   __shared__ float2 s_exp2[DFE ? kExpTable : 1];
-  if constexpr (DFE) {
+  __shared__ double s_exp2d[TANG ? kExpTable : 1];
+  constexpr bool STEP = (PREC == MDI_PREC_FP64 || PREC == MDI_PREC_DF64);  // FP64 terms stepped by R
+  __shared__ double s_gamma[kWarpScanMaxD];
+  __shared__ double2 s_step[STEP ? kWarpScanMaxD : 1];
+  if constexpr (DFE)
     for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s_exp2[j] = kExp2TableGen[j];
-    __syncthreads();
+  if constexpr (TANG)
+    for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s_exp2d[j] = kExp2TableD[j];
+  __syncthreads();  // the exp table is read below
+  if (!gamma_g && threadIdx.x < kWarp) {
+    // gamma_k for every level, and (FP64 terms) each level's step R_k = e^{32 gamma_k / r_k}
+    const int k = threadIdx.x;
+    const double g = warp_gamma(d, ch.inv_a, params);
+    if (k < d) {
+      s_gamma[k] = g;
+      if constexpr (STEP) {
+        const double arg = 32.0 * (g * ((k + 1 < d) ? ch.inv_a : ch.inv_nl));
+        if constexpr (FAM == MDI_FAM_OSC) {
+          double rs, rc;
+          sincos(arg, &rs, &rc);
+          s_step[k] = make_double2(rc, rs);
+        } else {
+          s_step[k] = make_double2(exp_tang64(arg, s_exp2d), 0.0);
+        }
+      }
+    }
   }
+  __syncthreads();
+  const double *gamma = gamma_g ? gamma_g : s_gamma;
   const int lane = threadIdx.x & (kWarp - 1);
   const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
   const int nwarps = gridDim.x * blockDim.x / kWarp;
@@ -175,7 +241,44 @@ __global__ void __launch_bounds__(kChunkThreads) closed_chunk_kernel(int d, int6
       }
       continue;
     }
-    for (int64_t q = q0 + lane; q < q1; q += kWarp) {
+    if constexpr (PREC == MDI_PREC_FP64 || PREC == MDI_PREC_DF64) {
+      // FP64 terms: along the cluster they form a geometric progression,
+      // e^{g (q + 32)/r} = e^{g q/r} R with R = e^{32 g/r} (complex for OSC), so each
+      // lane steps its points by one multiply and takes a fresh exp (sincos) every
+      // kAnchor points: a term's error stays below about 2 kAnchor ulps.
+      const double gr = g * invr;
+      if constexpr (FAM == MDI_FAM_OSC) {
+        double rs, rc;
+        if (gamma_g) {
+          sincos(32.0 * gr, &rs, &rc);
+        } else {
+          rc = s_step[k].x;
+          rs = s_step[k].y;
+        }
+        double2 E = make_double2(1.0, 0.0);
+        int i = 0;
+        for (int64_t q = q0 + lane; q < q1; q += kWarp, ++i) {
+          if ((i & (kAnchor - 1)) == 0) {
+            double es, ec;
+            sincos(gr * (double)q, &es, &ec);
+            E = make_double2(ec, es);
+          }
+          s = c_add(s, E);
+          if constexpr (WITH_T) t = c_add(t, c_scale(E, (double)q * invr));
+          E = make_double2(fma(E.x, rc, -E.y * rs), fma(E.x, rs, E.y * rc));
+        }
+      } else {
+        const double R = gamma_g ? exp_tang64(32.0 * gr, s_exp2d) : s_step[k].x;
+        double E = 1.0;
+        int i = 0;
+        for (int64_t q = q0 + lane; q < q1; q += kWarp, ++i) {
+          if ((i & (kAnchor - 1)) == 0) E = exp_tang64(gr * (double)q, s_exp2d);
+          s.x += E;
+          if constexpr (WITH_T) t.x = fma(E, (double)q * invr, t.x);
+          E *= R;
+        }
+      }
+    } else for (int64_t q = q0 + lane; q < q1; q += kWarp) {
       const double x = (double)q * invr;
       const double arg = g * x;
       double2 e;
@@ -189,8 +292,10 @@ __global__ void __launch_bounds__(kChunkThreads) closed_chunk_kernel(int d, int6
           sincosf((float)arg, &fs, &fc);
           e = make_double2((double)fc, (double)fs);
         }
+      } else if constexpr (TANG) {
+        e = make_double2(exp_tang64(arg, s_exp2d), 0.0);
       } else {
-        e = make_double2(PREC == MDI_PREC_FP64 || PREC == MDI_PREC_DF64 ? exp(arg) : (double)expf((float)arg), 0.0);
+        e = make_double2((double)expf((float)arg), 0.0);
       }
       if constexpr (PREC == MDI_PREC_FP32_EVAL_DF32) {
         sr = df_add(sr, df32{(float)e.x, 0.f});
@@ -280,6 +385,48 @@ static void launch_reduce(int d, int64_t a, int64_t n_last, const Chunks &ch, co
         d, a, n_last, ch, partS, partT, S, T);
 }
 
+// Steps 3 and 4 in one CTA when the chunk sums number at most kFinishMaxChunks:
+// the CTA first copies every chunk sum into shared memory (all loads in flight at
+// once: a level's sums read one after the other would each wait for L2), then
+// forms S_k -- one thread per level adding its chunks in order when levels have
+// few chunks, else warp w takes levels w, w + 8, ... with its lanes adding a
+// strided subset and an xor butterfly adding the lanes (fixed orders either way)
+// -- and multiplies the S_k by the fixed tree of product_body.
+template <int FAM>
+__device__ void product_body(int d, const double *__restrict__ params, const double2 *__restrict__ S,
+                             double *__restrict__ out, typename FamTraits<FAM>::V *sW);
+constexpr int kFinishThreads = 256;
+template <int FAM>
+__global__ void __launch_bounds__(kFinishThreads) closed_finish_kernel(int d, Chunks ch,
+                                                                       const double *__restrict__ params,
+                                                                       const double2 *__restrict__ partS,
+                                                                       double2 *__restrict__ S,
+                                                                       double *__restrict__ out) {
+  extern __shared__ double2 s_part[];  // ch.total chunk sums
+  __shared__ typename FamTraits<FAM>::V sW[kFinishThreads / kWarp];
+  for (int c = threadIdx.x; c < ch.total; c += kFinishThreads) s_part[c] = partS[c];
+  __syncthreads();
+  const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x / kWarp, nw = kFinishThreads / kWarp;
+  if (ch.cpl <= 8 && ch.cpl_last <= 8) {
+    for (int k = threadIdx.x; k < d; k += kFinishThreads) {
+      const int n = k < d - 1 ? ch.cpl : ch.cpl_last, base = chunk_base(k, d, ch.cpl);
+      double2 v = make_double2(0.0, 0.0);
+      for (int j = 0; j < n; ++j) v = c_add(v, s_part[base + j]);
+      S[k] = c_scale(v, (k + 1 < d) ? ch.inv_a : ch.inv_nl);
+    }
+  } else {
+    for (int k = warp; k < d; k += nw) {
+      const int n = k < d - 1 ? ch.cpl : ch.cpl_last, base = chunk_base(k, d, ch.cpl);
+      double2 v = make_double2(0.0, 0.0);
+      for (int j = lane; j < n; j += kWarp) v = c_add(v, s_part[base + j]);
+      v = warp_sum(v);
+      if (lane == 0) S[k] = c_scale(v, (k + 1 < d) ? ch.inv_a : ch.inv_nl);
+    }
+  }
+  __syncthreads();  // the S_k written above are visible to the whole CTA
+  product_body<FAM>(d, params, S, out, sW);
+}
+
 // out = Re(front * prod_k S_k) by a fixed tree: each thread multiplies a run of
 // consecutive factors, the 32 runs of a warp are combined by an xor butterfly
 // (IEEE multiplication commutes exactly, so every lane holds the same value), and
@@ -292,7 +439,9 @@ __device__ void product_body(int d, const double *__restrict__ params, const dou
   const int per = (d + blockDim.x - 1) / blockDim.x;
   const int lo = min(d, (int)threadIdx.x * per), hi = min(d, lo + per);
   V p = VOps<V>::one();
-  for (int k = lo; k < hi; ++k) p = VOps<V>::mul(p, from2<V>(S[k]));
+  // __ldcg: S may have been written earlier in the same launch (closed_finish_kernel),
+  // so it must not come through the non-coherent read-only path.
+  for (int k = lo; k < hi; ++k) p = VOps<V>::mul(p, from2<V>(__ldcg(S + k)));
   for (int off = 1; off < kWarp; off <<= 1) {
     if constexpr (FAM == MDI_FAM_OSC) {
       const double2 o = make_double2(__shfl_xor_sync(0xffffffffu, p.x, off), __shfl_xor_sync(0xffffffffu, p.y, off));
@@ -376,20 +525,29 @@ static int chunk_grid(const Chunks &ch) {
   return std::max(1, std::min((ch.total + warps_per_cta - 1) / warps_per_cta, sm_count() * 8));
 }
 
+// Steps 1-3 (and 4 when `out` is given), see the top of this file.
 template <int FAM, int PREC, bool WITH_T>
 static mdi_status run_levels_sums(int d, int64_t a, int64_t n_last, const double *params, char *base,
-                                  const ClosedLayout &L, cudaStream_t stream) {
+                                  const ClosedLayout &L, double *out, cudaStream_t stream) {
   double *gamma = (double *)(base + L.gamma);
   double2 *partS = (double2 *)(base + L.partS), *partT = (double2 *)(base + L.partT);
   double2 *S = (double2 *)(base + L.S), *T = (double2 *)(base + L.T);
   const Chunks ch = make_chunks(d, a, n_last);
-  closed_scan_kernel<<<1, scan_threads(d), 0, stream>>>(d, ch.inv_a, params, gamma);
-  mdi_status st = check_launch();
-  if (st != MDI_OK) return st;
-  closed_chunk_kernel<FAM, PREC, WITH_T><<<chunk_grid(ch), kChunkThreads, 0, stream>>>(d, a, n_last, ch, gamma, partS,
-                                                                                     partT);
+  mdi_status st;
+  if (d > kWarpScanMaxD) {
+    closed_scan_kernel<<<1, scan_threads(d), 0, stream>>>(d, ch.inv_a, params, gamma);
+    if ((st = check_launch()) != MDI_OK) return st;
+  }
+  closed_chunk_kernel<FAM, PREC, WITH_T><<<chunk_grid(ch), kChunkThreads, 0, stream>>>(
+      d, a, n_last, ch, d > kWarpScanMaxD ? gamma : nullptr, params, partS, partT);
   if ((st = check_launch()) != MDI_OK) return st;
+  if (out && ch.total <= kFinishMaxChunks) {
+    closed_finish_kernel<FAM><<<1, kFinishThreads, sizeof(double2) * ch.total, stream>>>(d, ch, params, partS, S, out);
+    return check_launch();
+  }
   launch_reduce<WITH_T>(d, a, n_last, ch, partS, partT, S, T, stream);
+  if ((st = check_launch()) != MDI_OK || !out) return st;
+  closed_product_kernel<FAM><<<1, kProdThreads, 0, stream>>>(d, params, S, out);
   return check_launch();
 }
 
@@ -397,10 +555,7 @@ template <int FAM, int PREC>
 static mdi_status run_closed(int d, int64_t a, int64_t n_last, const double *params, double *out, void *ws,
                              cudaStream_t stream) {
   const ClosedLayout L = closed_layout(d, a, n_last, false);
-  mdi_status st = run_levels_sums<FAM, PREC, false>(d, a, n_last, params, (char *)ws, L, stream);
-  if (st != MDI_OK) return st;
-  closed_product_kernel<FAM><<<1, kProdThreads, 0, stream>>>(d, params, (const double2 *)((char *)ws + L.S), out);
-  return check_launch();
+  return run_levels_sums<FAM, PREC, false>(d, a, n_last, params, (char *)ws, L, out, stream);
 }
 
 template <int FAM>
@@ -476,6 +631,10 @@ static mdi_status run_midpoint(int d, int64_t N, int64_t n_last, const double *p
   midpoint_chunk_kernel<FAM><<<chunk_grid(ch), kChunkThreads, 0, stream>>>(d, N, n_last, ch, params, partS);
   mdi_status st = check_launch();
   if (st != MDI_OK) return st;
+  if (ch.total <= kFinishMaxChunks) {
+    closed_finish_kernel<FAM><<<1, kFinishThreads, sizeof(double2) * ch.total, stream>>>(d, ch, params, partS, S, out);
+    return check_launch();
+  }
   launch_reduce<false>(d, N, n_last, ch, partS, partS, S, S, stream);
   if ((st = check_launch()) != MDI_OK) return st;
   closed_product_kernel<FAM><<<1, kProdThreads, 0, stream>>>(d, params, S, out);
@@ -610,7 +769,7 @@ static mdi_status run_closed_grad(int d, int64_t a, int64_t n_last, const double
                                   double *grad, void *ws, cudaStream_t stream) {
   const ClosedLayout L = closed_layout(d, a, n_last, true);
   char *base = (char *)ws;
-  mdi_status st = run_levels_sums<FAM, MDI_PREC_FP64, true>(d, a, n_last, params, base, L, stream);
+  mdi_status st = run_levels_sums<FAM, MDI_PREC_FP64, true>(d, a, n_last, params, base, L, nullptr, stream);
   if (st != MDI_OK) return st;
   closed_grad_final_kernel<FAM><<<1, kScanThreads, 0, stream>>>(d, (double)a, params, (const double2 *)(base + L.S),
                                                                 (const double2 *)(base + L.T), (double2 *)(base + L.nu),

@@ -73,6 +73,7 @@ struct NodesConfig {
   int ctas_per_sm;  // persistent CTAs per SM
   int precision;    // mdi_precision
   int stage;        // 1: stage each integral's basis table in shared memory; 0: read it through L1
+  int step;         // m of Algorithm 1 (1, 2, 3)
 };
 NodesConfig nodes_config(const mdi_opts *opts);
 size_t nodes_batched_workspace_bytes(int count, const NodesConfig &cfg);
@@ -93,6 +94,8 @@ mdi_status nodes_single_launch(int family, int d, int64_t a, int64_t n_last, con
 
 // mdi_levels.cu: one integral, node state, parallel over levels (forward and adjoint)
 size_t levels_workspace_bytes(int d, int64_t a, const NodesConfig &cfg, int checkpoint);
+// Step size m = cfg.step > 1 (forward, FP64): 0 when a^m exceeds the table limit.
+size_t levels_step_workspace_bytes(int d, int64_t a, const NodesConfig &cfg, int checkpoint);
 mdi_status levels_launch(int family, int d, int64_t a, int64_t n_last, const double *params, const NodesConfig &cfg,
                          int checkpoint, double *value, double *grad, void *workspace, size_t ws_bytes,
                          cudaStream_t stream);

@@ -39,6 +39,7 @@ namespace mdi {
 
 constexpr int kLvThreads = 256;
 constexpr int kLvMaxPts = kNodesAMax * kNodesPMax;  // a*P <= 2048
+constexpr int64_t kStepMaxRadix = 4096;              // a^m for the step-m operators
 
 // Groups: g = 0..ng-1 covers levels gC+1 .. min((g+1)C, d-1); boundary b_g = gC
 // for g < ng and b_ng = d-1.  gck[g] = G at b_g, lck[g] = lambda at b_g.
@@ -240,6 +241,112 @@ __global__ void __launch_bounds__(kLvThreads) levels_build_kernel(int d, int a, 
     }
   }
   (void)sizeof(V);
+}
+
+// Step size m of Algorithm 1 (m = 2, 3; forward value, FP64).  Operator j covers
+// the cluster axes l0 = j m .. l0 + mj - 1 (0-based; mj = m, or the remainder for
+// the last operator) and reads the previous state once, at the group's innermost
+// coordinate:
+//     M_j[p][t] = (1/a^mj) sum_{Q < a^mj} prod_{i < mj} phi_{l0+i}(x_i) l_t(x_0),
+//     x_i = ((Q mod a^(mj-i)) + xi_p) / a^(mj-i),
+// which is the affine recurrence x_i = (q_i + x_{i+1}) / a from x_mj = xi_p unrolled:
+// the digit q_i of axis l0 + i weighs a^(mj-1-i) in Q (the innermost axis' digit
+// is the most significant).  One CTA per operator
+// (block ns computes the last level's row w); the points (Q, p) go in tiles whose
+// products of phi are staged in shared memory, and l_t(x_0) is read from the basis
+// table of radix a^mj (levels_table_kernel with a^mj in place of a, so x_0 is the
+// same double in both).
+constexpr int kStepTile = 1024;          // points (Q, p) per tile
+constexpr int kStepMaxEntries = 4;       // P*P <= kStepMaxEntries * kLvThreads
+template <int FAM>
+__global__ void __launch_bounds__(kLvThreads) levels_step_build_kernel(int d, int a, int n_last, int P, int m,
+                                                                       int ns, const double *__restrict__ prm,
+                                                                       const double *__restrict__ Lm,
+                                                                       const double *__restrict__ Lr,
+                                                                       double2 *__restrict__ M,
+                                                                       double2 *__restrict__ w) {
+  using V = typename FamTraits<FAM>::V;
+  __shared__ double s_xi[kNodesPMax], s_bw[kNodesPMax];
+  __shared__ V s_f[kStepTile];
+  __shared__ double2 s_part[kLvThreads];
+  __shared__ AxisParams s_ap[3];
+  for (int t = threadIdx.x; t < P; t += blockDim.x) {
+    s_xi[t] = cheb_node(t, P);
+    s_bw[t] = cheb_weight(t, P);
+  }
+  __syncthreads();
+  const int tileQ = kStepTile / P;
+  for (int j = blockIdx.x; j <= ns; j += gridDim.x) {
+    if (j < ns) {
+      const int l0 = j * m, mj = min(m, d - 1 - l0);
+      int R = 1;
+      for (int i = 0; i < mj; ++i) R *= a;
+      const double *L = (mj == m) ? Lm : Lr;
+      const int npts = R * P;
+      if (threadIdx.x < mj) s_ap[threadIdx.x] = load_axis(prm, d, l0 + threadIdx.x);
+      V acc[kStepMaxEntries];
+#pragma unroll
+      for (int e = 0; e < kStepMaxEntries; ++e) acc[e] = VOps<V>::zero();
+      __syncthreads();
+      for (int Q0 = 0; Q0 < R; Q0 += tileQ) {
+        const int nq = min(tileQ, R - Q0);
+        for (int i = threadIdx.x; i < nq * P; i += blockDim.x) {
+          const int Q = Q0 + i / P, p = i % P;
+          V prod = VOps<V>::one();
+          int Ri = R;
+          for (int ii = 0; ii < mj; ++ii) {  // x_ii = ((Q mod a^(mj-ii)) + xi_p) / a^(mj-ii)
+            const double x = ((double)(Q % Ri) + s_xi[p]) / (double)Ri;
+            prod = VOps<V>::mul(prod, phi<FAM, false>(x, s_ap[ii]));
+            Ri /= a;
+          }
+          s_f[i] = prod;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < kStepMaxEntries; ++e) {
+          const int o = threadIdx.x + e * kLvThreads;
+          if (o < P * P) {
+            const int t = o / P, p = o % P;
+            const double *Lt = L + (size_t)t * npts + (size_t)Q0 * P + p;
+            V a_e = acc[e];
+            for (int q = 0; q < nq; ++q) a_e = VOps<V>::fma_s(Lt[(size_t)q * P], s_f[q * P + p], a_e);
+            acc[e] = a_e;
+          }
+        }
+        __syncthreads();
+      }
+      double2 *Mj = M + (size_t)j * P * P;
+      const double invR = 1.0 / (double)R;
+#pragma unroll
+      for (int e = 0; e < kStepMaxEntries; ++e) {
+        const int o = threadIdx.x + e * kLvThreads;
+        if (o < P * P) Mj[o] = c_scale(as2(acc[e]), invR);  // stored [t][p]
+      }
+    } else {
+      // last level: w[t] = (1/n_last) sum_s phi_d(s/n_last) l_t(s/n_last)
+      const AxisParams ap = load_axis(prm, d, d - 1);
+      const int rows = blockDim.x / P;
+      const int t = threadIdx.x % P, r = threadIdx.x / P;
+      double2 acc = make_double2(0.0, 0.0);
+      if (r < rows) {
+        for (int s = r; s < n_last; s += rows) {
+          const double u = (double)s / (double)n_last;
+          const double2 f = as2(phi<FAM, false>(u, ap));
+          const double l = (d == 1) ? (t == 0 ? 1.0 : 0.0) : basis_at(s_xi, s_bw, P, t, u);
+          acc.x = fma(l, f.x, acc.x);
+          if constexpr (FAM == MDI_FAM_OSC) acc.y = fma(l, f.y, acc.y);
+        }
+      }
+      s_part[threadIdx.x] = acc;
+      __syncthreads();
+      if (threadIdx.x < P) {
+        double2 sum = make_double2(0.0, 0.0);
+        for (int rr = 0; rr < rows; ++rr) sum = c_add(sum, s_part[rr * P + threadIdx.x]);
+        w[threadIdx.x] = c_scale(sum, 1.0 / (double)n_last);
+      }
+    }
+    __syncthreads();
+  }
 }
 
 // cp.async helpers for staging operators into shared memory (hardware
@@ -659,6 +766,109 @@ static mdi_status run_levels(int d, int a, int n_last, const double *params, con
   return st;
 }
 
+// Step size m > 1: workspace | table of radix a^m | table of radix a^rem | M (ns
+// operators) | R | w | gck | lck | misc, with ns = ceil((d-1)/m) operators in
+// groups of C.
+struct StepLayout {
+  size_t Lm, Lr, M, R, w, gck, lck, misc, total;
+  int ns, ng, C, Rm, Rr;
+};
+static StepLayout step_layout(int d, int64_t a, int P, int m, int checkpoint) {
+  StepLayout L{};
+  L.ns = (d - 1 + m - 1) / m;
+  L.C = checkpoint > 0 ? checkpoint : default_checkpoint(std::max(L.ns, 1));
+  L.ng = L.C > 1 ? (L.ns + L.C - 1) / L.C : L.ns;
+  const int rem = (d - 1) % m;
+  L.Rm = 1;
+  for (int i = 0; i < m; ++i) L.Rm *= (int)a;
+  L.Rr = 1;
+  for (int i = 0; i < rem; ++i) L.Rr *= (int)a;
+  size_t off = 0;
+  L.Lm = off;
+  off += align_up(sizeof(double) * (size_t)L.Rm * P * P);
+  L.Lr = off;
+  if (rem) off += align_up(sizeof(double) * (size_t)L.Rr * P * P);
+  L.M = off;
+  off += align_up(sizeof(double2) * (size_t)std::max(L.ns, 1) * P * P);
+  L.R = off;
+  if (L.C > 1) off += align_up(sizeof(double2) * (size_t)std::max(L.ng, 1) * P * P);
+  L.w = off;
+  off += align_up(sizeof(double2) * P);
+  L.gck = off;
+  off += align_up(sizeof(double2) * (size_t)(L.ng + 1) * P);
+  L.lck = off;
+  off += align_up(sizeof(double2) * (size_t)(L.ng + 1) * P);
+  L.misc = off;
+  off += align_up(4 * sizeof(double2));
+  L.total = off;
+  return L;
+}
+
+static bool step_sizes_ok(int64_t a, int m) {
+  int64_t R = 1;
+  for (int i = 0; i < m; ++i) {
+    R *= a;
+    if (R > kStepMaxRadix) return false;
+  }
+  return true;
+}
+
+size_t levels_step_workspace_bytes(int d, int64_t a, const NodesConfig &cfg, int checkpoint) {
+  if (cfg.step < 2 || !step_sizes_ok(a, cfg.step)) return 0;
+  return step_layout(d, a, cfg.P, cfg.step, checkpoint).total;
+}
+
+template <int FAM>
+static mdi_status run_levels_step(int d, int a, int n_last, const double *params, const NodesConfig &cfg,
+                                  int checkpoint, double *value, void *ws, cudaStream_t stream) {
+  const int P = cfg.P, m = cfg.step;
+  const StepLayout Lo = step_layout(d, a, P, m, checkpoint);
+  char *base = (char *)ws;
+  double *Lm = (double *)(base + Lo.Lm), *Lr = (double *)(base + Lo.Lr);
+  double2 *M = (double2 *)(base + Lo.M), *w = (double2 *)(base + Lo.w);
+  double2 *gck = (double2 *)(base + Lo.gck), *lck = (double2 *)(base + Lo.lck), *misc = (double2 *)(base + Lo.misc);
+  levels_table_kernel<false><<<(Lo.Rm * P + 7) / 8, 8 * kWarp, 0, stream>>>(P, Lo.Rm, Lm);
+  mdi_status st = check_launch();
+  if (st != MDI_OK) return st;
+  if ((d - 1) % m) {
+    levels_table_kernel<false><<<(Lo.Rr * P + 7) / 8, 8 * kWarp, 0, stream>>>(P, Lo.Rr, Lr);
+    if ((st = check_launch()) != MDI_OK) return st;
+  }
+  levels_step_build_kernel<FAM><<<std::min(Lo.ns + 1, sm_count() * 8), kLvThreads, 0, stream>>>(
+      d, a, n_last, P, m, Lo.ns, params, Lm, Lr, M, w);
+  if ((st = check_launch()) != MDI_OK) return st;
+  static bool attrs = false;
+  if (!attrs) {
+    cudaError_t e = cudaFuncSetAttribute(levels_chain_kernel<FAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kChainSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(levels_group_kernel<FAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(4 * sizeof(double2) * kNodesPMax * kNodesPMax));
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      return MDI_ECUDA;
+    }
+    attrs = true;
+  }
+  // The operators play the levels' part in the group products and the chain: the
+  // group kernel reads its "d - 1" as the operator count.
+  const double2 *ops = M;
+  if (Lo.C > 1 && Lo.ng > 0) {
+    double2 *Rg = (double2 *)(base + Lo.R);
+    const size_t group_smem = 4 * sizeof(double2) * (size_t)P * P;
+    levels_group_kernel<FAM><<<Lo.ng, std::max(32, (P * P + 31) / 32 * 32), group_smem, stream>>>(Lo.ns + 1, P, Lo.C,
+                                                                                                 M, Rg);
+    if ((st = check_launch()) != MDI_OK) return st;
+    ops = Rg;
+  }
+  const int LC = chain_levels_per_chunk(P);
+  const size_t chain_smem = 2 * (size_t)LC * P * P * sizeof(double2);
+  const int chain_threads = std::max(32, (P * chain_group(P) + 31) / 32 * 32);
+  levels_chain_kernel<FAM><<<1, chain_threads, chain_smem, stream>>>(d, Lo.ng, P, LC, params, ops, w, gck, lck, misc,
+                                                                     value, nullptr, 0);
+  return check_launch();
+}
+
 template <int FAM>
 static mdi_status run_levels_p(int precision, int d, int a, int n_last, const double *params, const NodesConfig &cfg,
                                int C, double *value, double *grad, void *ws, cudaStream_t stream) {
@@ -679,6 +889,19 @@ mdi_status levels_launch(int family, int d, int64_t a, int64_t n_last, const dou
   if (d < 1 || d > (1 << 16) || a < 1 || a > kNodesAMax || n_last < 1 || n_last > 4096) return MDI_EUNSUPPORTED;
   if (cfg.P < 2 || cfg.P > kNodesPMax || (cfg.P & 1)) return MDI_EINVAL;
   if (grad && cfg.precision != MDI_PREC_FP64) return MDI_EUNSUPPORTED;
+  if (cfg.step > 1) {  // Algorithm 1 with m = 2, 3: forward value in FP64
+    if (grad || cfg.precision != MDI_PREC_FP64 || !step_sizes_ok(a, cfg.step)) return MDI_EUNSUPPORTED;
+    if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < levels_step_workspace_bytes(d, a, cfg, checkpoint))
+      return MDI_EWORKSPACE;
+    const int ai = (int)a, nl = (int)n_last;
+    switch (family) {
+      case MDI_FAM_EXP: return run_levels_step<MDI_FAM_EXP>(d, ai, nl, params, cfg, checkpoint, value, workspace, stream);
+      case MDI_FAM_OSC: return run_levels_step<MDI_FAM_OSC>(d, ai, nl, params, cfg, checkpoint, value, workspace, stream);
+      case MDI_FAM_GAUSS:
+        return run_levels_step<MDI_FAM_GAUSS>(d, ai, nl, params, cfg, checkpoint, value, workspace, stream);
+      default: return run_levels_step<MDI_FAM_PEAK>(d, ai, nl, params, cfg, checkpoint, value, workspace, stream);
+    }
+  }
   const int C = checkpoint > 0 ? checkpoint : default_checkpoint(d);
   if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < levels_layout(d, a, cfg.P, C).total)
     return MDI_EWORKSPACE;

@@ -13,6 +13,9 @@ Contents (the node state with P = 16 everywhere):
                    derivatives (c_1..c_100, w_1..w_100)
   scale            N = 16, exp(sum x_j / j^2), d in {100, 250, 500, 1000}: closed
                    and node-state values
+  step             Algorithm 1's step size m = 1, 2, 3 with the node state at d = 100,
+                   N = 16: the Gaussian of the differentiation workload, and
+                   exp(sum x_j / j^2) beside its closed state (the exact rule)
 """
 import json
 import os
@@ -41,7 +44,11 @@ def compute():
         s = inputs.scale_exp(d, 16)
         scale[str(d)] = {"closed": o.mdi_closed("exp", d, 16, 16, s.c, s.w),
                          "nodes": o.mdi_nodes("exp", d, 16, 16, 16, s.c, s.w)}
-    return {"precision": precision, "differentiation": differentiation, "scale": scale}
+    s100 = inputs.scale_exp(100, 16)
+    step = {"gauss": {str(m): o.mdi_nodes_step("gauss", 100, 16, 16, 16, m, g.c, g.w) for m in (1, 2, 3)},
+            "exp": {str(m): o.mdi_nodes_step("exp", 100, 16, 16, 16, m, s100.c, s100.w) for m in (1, 2, 3)},
+            "exp_closed": o.mdi_closed("exp", 100, 16, 16, s100.c, s100.w)}
+    return {"precision": precision, "differentiation": differentiation, "scale": scale, "step": step}
 
 
 if __name__ == "__main__":

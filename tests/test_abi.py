@@ -82,7 +82,9 @@ def test_mdi_rejects_bad_arguments(lib):
     o = _ffi.MdiOpts()
     assert lib.mdi_lr_integrate(0, 0, 16, 16, _null(), fake, ctypes.byref(o), fake, fake, 1 << 20, _null()) == _ffi.MDI_EINVAL
     assert lib.mdi_lr_integrate(0, 4, 0, 16, _null(), fake, ctypes.byref(o), fake, fake, 1 << 20, _null()) == _ffi.MDI_EINVAL
-    o.reserved = 1
+    o.step = 4  # Algorithm 1's m is 1, 2 or 3
+    assert lib.mdi_lr_integrate(0, 4, 16, 16, _null(), fake, ctypes.byref(o), fake, fake, 1 << 20, _null()) == _ffi.MDI_EINVAL
+    o.step = -1
     assert lib.mdi_lr_integrate(0, 4, 16, 16, _null(), fake, ctypes.byref(o), fake, fake, 1 << 20, _null()) == _ffi.MDI_EINVAL
     o = _ffi.MdiOpts()
     o.state = _ffi.STATE["closed"]
@@ -288,3 +290,24 @@ def test_status_estimate_and_probe_validate_arguments(lib):
     assert lib.mdi_peak_probe(1, 10, _null(), _null()) == _ffi.MDI_EINVAL
     assert lib.mdi_peak_probe_threads(5) == 0
     assert _ffi.DEV_FLAGS == {"bad_desc": 1, "bad_order": 2, "unprepared": 4, "pool_range": 8}
+
+
+def test_step_size_limits(lib):
+    """Algorithm 1's m > 1 with the node state: FP64 forward only, a^m <= 4096; the
+    gradient and the batched call refuse it."""
+    fake = ctypes.c_void_p(0x1000)
+    b = ctypes.c_size_t()
+    o = _ffi.MdiOpts()
+    o.state, o.step = _ffi.STATE["nodes"], 2
+    assert lib.mdi_lr_workspace_size(2, 10, 64, 64, ctypes.byref(o), ctypes.byref(b)) == _ffi.MDI_OK  # 64^2
+    o.step = 3
+    assert lib.mdi_lr_workspace_size(2, 10, 17, 17, ctypes.byref(o), ctypes.byref(b)) == _ffi.MDI_EUNSUPPORTED
+    assert lib.mdi_lr_workspace_size(2, 10, 16, 16, ctypes.byref(o), ctypes.byref(b)) == _ffi.MDI_OK
+    assert lib.mdi_lr_grad(2, 10, 16, 16, _null(), fake, ctypes.byref(o), fake, fake, fake, 1 << 30,
+                           _null()) == _ffi.MDI_EUNSUPPORTED
+    assert lib.mdi_lr_grad_workspace_size(2, 10, 16, 16, ctypes.byref(o), ctypes.byref(b)) == _ffi.MDI_EUNSUPPORTED
+    assert lib.mdi_lr_integrate_batched(fake, fake, 4, fake, 1 << 20, ctypes.byref(o), fake, fake, 1 << 30,
+                                        _null()) == _ffi.MDI_EUNSUPPORTED
+    o.precision = _ffi.PRECISION["df64"]
+    assert lib.mdi_lr_integrate(2, 10, 16, 16, _null(), fake, ctypes.byref(o), fake, fake, 1 << 30,
+                                _null()) == _ffi.MDI_EUNSUPPORTED

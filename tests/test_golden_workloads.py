@@ -33,3 +33,7 @@ def test_stored_values_are_the_oracles():
     for d in map(str, m.SCALE_DS):
         for k in ("closed", "nodes"):
             assert abs(stored["scale"][d][k] / fresh["scale"][d][k] - 1) <= 1e-14
+    for fam in ("gauss", "exp"):
+        for k in ("1", "2", "3"):
+            assert abs(stored["step"][fam][k] / fresh["step"][fam][k] - 1) <= 1e-14
+    assert abs(stored["step"]["exp_closed"] / fresh["step"]["exp_closed"] - 1) <= 1e-14

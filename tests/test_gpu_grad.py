@@ -1,10 +1,14 @@
 """Adjoint sweep on the GPU (mdi_lr_grad and the autograd Function) against the
 oracle's forward-mode derivative of the same rule, central differences and the
 closed-form gradient.  Gradients are compared component by component: every
-|g_i - ref_i| <= 1e-12 |ref_i| + 1e-15 max_k |ref_k| (the absolute floor, three
-orders below the relative bound of the largest component, only matters for
-components at rounding level, e.g. dQ/dw_j of a factor centred at w_j = 1/2),
-and in the max norm as well."""
+|g_i - ref_i| <= 1e-12 |ref_i| + 1e-15 M (the absolute floor, three orders below
+the relative bound of the largest component, only matters for components at
+rounding level, e.g. dQ/dw_j of a factor centred at w_j = 1/2), and in the max
+norm as well.  M = max_k |ref_k| for the real families.  For the oscillatory
+family M = 2 pi, the bound of |df/du| (|df/dc_j| <= 1): its cluster sums add
+unit-modulus terms that can cancel to far below them, so a component is only
+determined to rounding relative to those terms -- the same reason its forward
+values are held to an absolute tolerance."""
 import numpy as np
 import pytest
 import torch
@@ -28,9 +32,9 @@ def dev(x):
     return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64)).cuda()
 
 
-def assert_grad_close(got, ref, tol=TOL, floor=1e-15):
+def assert_grad_close(got, ref, tol=TOL, floor=1e-15, fam=None):
     got, ref = np.asarray(got), np.asarray(ref)
-    scale = max(np.max(np.abs(ref)), 1e-300)
+    scale = max(np.max(np.abs(ref)), 2 * np.pi if fam == "osc" else 0.0, 1e-300)
     err = np.abs(got - ref)
     bound = tol * np.abs(ref) + floor * scale
     bad = np.flatnonzero(err > bound)
@@ -48,7 +52,7 @@ def test_nodes_grad_matches_oracle(fam, d, a, nd, P, C):
         params[d] = 0.41
     val, g = mdi.mdi_lr_grad(fam, dev(params), d, a, nd, state="nodes", nodes=P, checkpoint=C)
     ref = o.mdi_nodes_grad(fam, d, a, nd, P, params[:d], params[d:])
-    assert_grad_close(g.cpu().numpy(), ref)
+    assert_grad_close(g.cpu().numpy(), ref, fam=fam)
     fwd = o.mdi_nodes(fam, d, a, nd, P, params[:d], params[d:])
     assert abs(val.item() - fwd) <= TOL * max(abs(fwd), 1.0 if fam == "osc" else 0.0)
 
@@ -60,7 +64,7 @@ def test_closed_grad_matches_oracle(fam, d, a, nd):
     if fam == "osc":
         params[d] = 0.29
     val, g = mdi.mdi_lr_grad(fam, dev(params), d, a, nd, state="closed")
-    assert_grad_close(g.cpu().numpy(), o.mdi_closed_grad(fam, d, a, nd, params[:d], params[d:]))
+    assert_grad_close(g.cpu().numpy(), o.mdi_closed_grad(fam, d, a, nd, params[:d], params[d:]), fam=fam)
     fwd = o.mdi_closed(fam, d, a, nd, params[:d], params[d:])
     assert abs(val.item() - fwd) <= TOL * (1.0 if fam == "osc" else abs(fwd))
 
@@ -74,7 +78,7 @@ def test_grads_equal_lattice_gradient_small():
     for fam, state in (("gauss", "nodes"), ("peak", "nodes"), ("exp", "closed"), ("osc", "closed")):
         params = inputs.random_product(fam, d, seed=17)
         _, g = mdi.mdi_lr_grad(fam, dev(params), d, a, a, state=state)
-        assert_grad_close(g.cpu().numpy(), o.slr_grad(fam, d, n, z, params[:d], params[d:]), tol=2e-12)
+        assert_grad_close(g.cpu().numpy(), o.slr_grad(fam, d, n, z, params[:d], params[d:]), tol=2e-12, fam=fam)
 
 
 def test_differentiation_workload():

@@ -243,6 +243,48 @@ def test_nodes_state_equals_closed_state_large_d():
     assert o.mdi_nodes("exp", d, a, a, 16, c) == pytest.approx(o.mdi_closed("exp", d, a, a, c), rel=1e-13)
 
 
+# Step size m of Algorithm 1 (eq. 2.14c): m axes per iteration, the state read
+# once per m levels.
+@pytest.mark.parametrize("fam", ["gauss", "peak", "exp", "osc"])
+@pytest.mark.parametrize("d,a,nd", [(4, 16, 16), (5, 8, 8), (6, 4, 5), (7, 3, 4), (3, 12, 7), (2, 9, 9), (1, 5, 5)])
+def test_nodes_step_matches_exact_sweep(fam, d, a, nd):
+    rng = np.random.default_rng(13 * d + a)
+    c, w = rng.uniform(0.5, 2.0, d), rng.uniform(0, 1, d)
+    ex = o.mdi_exact(fam, d, a, nd, c, w)
+    for m in (2, 3):
+        assert o.mdi_nodes_step(fam, d, a, nd, 16, m, c, w) == pytest.approx(ex, rel=2e-14, abs=1e-15)
+
+
+@pytest.mark.parametrize("fam", ["gauss", "peak", "exp", "osc"])
+def test_nodes_step_one_is_the_m1_sweep(fam):
+    for d, a, nd in ((6, 8, 8), (4, 6, 9), (9, 5, 3)):
+        rng = np.random.default_rng(d + a)
+        c, w = rng.uniform(0.5, 2.0, d), rng.uniform(0, 1, d)
+        assert o.mdi_nodes_step(fam, d, a, nd, 16, 1, c, w) == o.mdi_nodes(fam, d, a, nd, 16, c, w)
+
+
+def test_nodes_step_equals_closed_state_large_d():
+    """Beyond enumerable sizes: the exponential family's node state with m = 2 and 3
+    against the closed state (exact for every m), at d = 61 (m = 3 leaves no
+    remainder) and d = 62 (remainders 1 and 2)."""
+    for d in (61, 62):
+        c = 1.0 / np.arange(1, d + 1)
+        ref = o.mdi_closed("exp", d, 8, 8, c)
+        for m in (2, 3):
+            assert o.mdi_nodes_step("exp", d, 8, 8, 16, m, c) == pytest.approx(ref, rel=1e-13)
+
+
+def test_nodes_step_converges_in_P():
+    """d = 20 Gaussian (no exact sweep at this size): with m = 2 the values for
+    P = 12, 16, 24 agree to rounding, and P = 6 is visibly off."""
+    d, a = 20, 6
+    rng = np.random.default_rng(21)
+    c, w = rng.uniform(0.5, 2.0, d), rng.uniform(0, 1, d)
+    v = {P: o.mdi_nodes_step("gauss", d, a, a, P, 2, c, w) for P in (6, 12, 16, 24)}
+    assert abs(v[16] - v[24]) <= 1e-14 * abs(v[24]) and abs(v[12] - v[24]) <= 1e-12 * abs(v[24])
+    assert abs(v[6] - v[24]) > 1e-10 * abs(v[24])
+
+
 # ----------------------------------------------------------------------------
 # Closed forms against independent quadrature, gradients against differences
 # ----------------------------------------------------------------------------
