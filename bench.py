@@ -919,18 +919,19 @@ def max_rel_err(got, ref):
 # Named workloads for profilers (``python bench.py --case NAME --repeats R``): each
 # runs R times through the public API on the seeded synthetic inputs.
 # ---------------------------------------------------------------------------
-def _case_batch(precision, block):
+def _case_batch(precision, block, hybrid=False):
     from paper_2404_08867_gb300 import inputs
     from paper_2404_08867_gb300.tuning import BatchedMDILR
     b = inputs.batch(count=COUNT, seed=0)
     plan = BatchedMDILR(b.families, b.d, b.a, b.n_last, b.offsets, b.pool, precision=precision, nodes=P_NODES)
-    plan.opts.update(block=block, table_in_l1=1)
+    plan.opts.update(block=block, table_in_l1=1, split=plan.hybrid_split if hybrid else plan.count)
     return plan.launch
 
 
 def build_case(name):
     """The launch function of a named workload:
       batch-fp64      4096-integral batch, FP64 node state (block 64, table via L1)
+      batch-fp64-hybrid  the same with the planner's hybrid schedule
       batch-df64      the same batch, double-float node state (block 32, table via L1)
       batch-f32df     the same batch, phi in float, double-float sums (block 32)
       levels-d1000    one integral, node state parallel over levels, d = 1000, N = 16:
@@ -954,6 +955,8 @@ def build_case(name):
     from paper_2404_08867_gb300 import inputs
     if name == "batch-fp64":
         return _case_batch("fp64", 64)
+    if name == "batch-fp64-hybrid":
+        return _case_batch("fp64", 64, hybrid=True)
     if name == "batch-df64":
         return _case_batch("df64", 32)
     if name == "batch-f32df":

@@ -327,6 +327,13 @@ mdi_status mdi_lr_batched_prepare(const mdi_opts *opts, void *workspace, size_t 
  *   order      DEVICE, count int32 instance indices in the order CTAs should pick
  *              them up (from mdi_batch_plan), or NULL for 0..count-1
  *   count      number of integrals, >= 1
+ *   split      hybrid schedule (from mdi_batch_plan): order slots below split are
+ *              swept by whole CTAs, later ones by single warps, each with a state
+ *              of its own (so the largest integrals, which come first, finish
+ *              sooner, and the rest run at the lane efficiency of one warp).  It is
+ *              honoured for MDI_PREC_FP64 with 64-thread CTAs (opts->block = 64) and
+ *              the tables read through L1 (opts->table_in_l1 = 1), and treated as
+ *              count otherwise; split >= count means whole CTAs throughout
  *   param_pool DEVICE doubles
  *   pool_len   number of doubles in param_pool: descriptor i reads
  *              param_pool[param_offset, param_offset + 2 d), which must lie inside it
@@ -341,18 +348,23 @@ mdi_status mdi_lr_batched_prepare(const mdi_opts *opts, void *workspace, size_t 
  * an unprepared workspace yields NaN everywhere and is flagged.  Read and clear the
  * flags with mdi_get_device_status. */
 mdi_status mdi_lr_integrate_batched(const mdi_batch_desc *descs, const int32_t *order, int32_t count,
-                                    const double *param_pool, int64_t pool_len, const mdi_opts *opts, double *out,
-                                    void *workspace, size_t ws_bytes, mdi_stream_t stream);
+                                    int32_t split, const double *param_pool, int64_t pool_len, const mdi_opts *opts,
+                                    double *out, void *workspace, size_t ws_bytes, mdi_stream_t stream);
 mdi_status mdi_lr_batched_workspace_size(int32_t count, const mdi_opts *opts, size_t *bytes);
 
 /* Host-side scheduler: writes into order (HOST, count int32) a processing order
  * for mdi_lr_integrate_batched -- longest estimated work first, ties grouped by a
- * so that consecutive pick-ups share their interpolation table.  descs is a HOST
- * copy of the descriptor table; pool_len the number of doubles of the parameter
- * pool the batch will read.  Returns MDI_EINVAL on an invalid descriptor or one
- * whose 2*d parameters leave the pool. */
+ * so that consecutive pick-ups share their interpolation table -- and into *split
+ * (HOST, may be NULL) the hybrid schedule's split for these opts: for FP64 batches
+ * of real families with opts->block = 64 and tables through L1 it simulates the
+ * persistent launch (the resident CTAs of this GPU taking the order, a modelled
+ * time per integral for one- and two-warp teams) for 41 splits and keeps the
+ * shortest, otherwise count.  descs is a HOST copy of the descriptor table;
+ * pool_len the number of doubles of the parameter pool the batch will read.
+ * Returns MDI_EINVAL on an invalid descriptor or one whose 2*d parameters leave
+ * the pool. */
 mdi_status mdi_batch_plan(const mdi_batch_desc *descs, int32_t count, int64_t pool_len, const mdi_opts *opts,
-                          int32_t *order);
+                          int32_t *order, int32_t *split);
 
 /* Flags of the device status word of a batched workspace (bitwise OR). */
 #define MDI_DEV_BAD_DESC 1u    /* a descriptor outside the limits (its output is NaN) */

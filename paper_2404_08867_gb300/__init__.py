@@ -325,15 +325,19 @@ def make_batch_descs(families, ds, as_, n_lasts, param_offsets) -> np.ndarray:
     return descs
 
 
-def mdi_batch_plan(descs: np.ndarray, pool_len: int, **opts) -> np.ndarray:
-    """Longest-first processing order computed by the library's host scheduler;
-    ``pool_len``: doubles in the parameter pool the batch reads."""
+def mdi_batch_plan(descs: np.ndarray, pool_len: int, **opts):
+    """(order, split): the library's host scheduler -- longest-first processing
+    order and the hybrid schedule's split for these opts (count when whole CTAs
+    are kept throughout); ``pool_len``: doubles in the parameter pool the batch
+    reads."""
     descs = np.ascontiguousarray(descs, dtype=BATCH_DESC_DTYPE)
     order = np.zeros(descs.size, dtype=np.int32)
+    split = ctypes.c_int32(0)
     o = _opts(**opts)
     _ffi.check(_ffi.load().mdi_batch_plan(descs.ctypes.data_as(ctypes.c_void_p), descs.size, int(pool_len),
-                                          ctypes.byref(o), order.ctypes.data_as(ctypes.c_void_p)), "mdi_batch_plan")
-    return order
+                                          ctypes.byref(o), order.ctypes.data_as(ctypes.c_void_p),
+                                          ctypes.byref(split)), "mdi_batch_plan")
+    return order, int(split.value)
 
 
 def mdi_lr_batched_workspace_size(count: int, **opts) -> int:
@@ -357,12 +361,14 @@ def mdi_lr_batched_prepare(workspace: Optional[torch.Tensor] = None, device="cud
 
 def mdi_lr_integrate_batched(descs: torch.Tensor, param_pool: torch.Tensor, count: int,
                              order: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
-                             workspace: Optional[torch.Tensor] = None, stream=None, **opts) -> torch.Tensor:
+                             workspace: Optional[torch.Tensor] = None, stream=None, split: Optional[int] = None,
+                             **opts) -> torch.Tensor:
     """``descs``: uint8 CUDA tensor holding ``count`` mdi_batch_desc records
     (``torch.from_numpy(make_batch_descs(...).view(np.uint8)).cuda()``); ``order``:
-    optional int32 CUDA tensor from mdi_batch_plan; ``workspace``: from
-    mdi_lr_batched_prepare with the same opts (prepared here when omitted).
-    Returns ``count`` float64 values."""
+    optional int32 CUDA tensor from mdi_batch_plan; ``split``: the hybrid
+    schedule's split from mdi_batch_plan (default: whole CTAs throughout);
+    ``workspace``: from mdi_lr_batched_prepare with the same opts (prepared here
+    when omitted).  Returns ``count`` float64 values."""
     if not (descs.is_cuda and descs.dtype == torch.uint8 and descs.numel() >= 32 * count):
         raise TypeError("descs must be a uint8 CUDA tensor of count*32 bytes")
     _dev_f64(param_pool, "param_pool")
@@ -375,7 +381,8 @@ def mdi_lr_integrate_batched(descs: torch.Tensor, param_pool: torch.Tensor, coun
     o = _opts(**opts)
     st = _ffi.load().mdi_lr_integrate_batched(
         ctypes.c_void_p(descs.data_ptr()), ctypes.c_void_p(order.data_ptr() if order is not None else 0), count,
-        ctypes.c_void_p(param_pool.data_ptr()), int(param_pool.numel()), ctypes.byref(o),
+        int(count if split is None else split), ctypes.c_void_p(param_pool.data_ptr()), int(param_pool.numel()),
+        ctypes.byref(o),
         ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream(stream))
     _ffi.check(st, "mdi_lr_integrate_batched")
     return out

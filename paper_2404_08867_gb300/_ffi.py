@@ -47,10 +47,10 @@ SIGNATURES = {
     "mdi_lr_workspace_size": (_I32, [_I32, _I32, _I64, _I64, _c.POINTER(MdiOpts), _c.POINTER(_SZ)]),
     "mdi_lr_grad": (_I32, [_I32, _I32, _I64, _I64, _P, _P, _c.POINTER(MdiOpts), _P, _P, _P, _SZ, _P]),
     "mdi_lr_grad_workspace_size": (_I32, [_I32, _I32, _I64, _I64, _c.POINTER(MdiOpts), _c.POINTER(_SZ)]),
-    "mdi_lr_integrate_batched": (_I32, [_P, _P, _I32, _P, _I64, _c.POINTER(MdiOpts), _P, _P, _SZ, _P]),
+    "mdi_lr_integrate_batched": (_I32, [_P, _P, _I32, _I32, _P, _I64, _c.POINTER(MdiOpts), _P, _P, _SZ, _P]),
     "mdi_lr_batched_workspace_size": (_I32, [_I32, _c.POINTER(MdiOpts), _c.POINTER(_SZ)]),
     "mdi_lr_batched_prepare": (_I32, [_c.POINTER(MdiOpts), _P, _SZ, _P]),
-    "mdi_batch_plan": (_I32, [_P, _I32, _I64, _c.POINTER(MdiOpts), _P]),
+    "mdi_batch_plan": (_I32, [_P, _I32, _I64, _c.POINTER(MdiOpts), _P, _P]),
     "mdi_get_device_status": (_I32, [_P, _SZ, _I32, _c.POINTER(_c.c_uint32), _P]),
     "lattice_korobov_vector": (_I32, [_I32, _I64, _I64, _P]),
     "lattice_shifted_estimate": (_I32, [_P, _I32, _P, _P]),

@@ -5,6 +5,8 @@
 #include <atomic>
 #include <cstring>
 #include <numeric>
+#include <queue>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -304,14 +306,14 @@ mdi_status mdi_lr_batched_prepare(const mdi_opts *opts, void *workspace, size_t 
   return nodes_prepare(nodes_config(opts), workspace, ws_bytes, (cudaStream_t)stream);
 }
 
-mdi_status mdi_lr_integrate_batched(const mdi_batch_desc *descs, const int32_t *order, int32_t count,
+mdi_status mdi_lr_integrate_batched(const mdi_batch_desc *descs, const int32_t *order, int32_t count, int32_t split,
                                     const double *param_pool, int64_t pool_len, const mdi_opts *opts, double *out,
                                     void *workspace, size_t ws_bytes, mdi_stream_t stream) {
   NvtxRange nvtx_scope("mdi_lr_integrate_batched");
-  if (!opts_ok(opts) || pool_len < 0) return MDI_EINVAL;
+  if (!opts_ok(opts) || pool_len < 0 || split < 0) return MDI_EINVAL;
   if (opts && opts->state != MDI_STATE_AUTO && opts->state != MDI_STATE_NODES) return MDI_EUNSUPPORTED;
   if (opts && opts->step > 1) return MDI_EUNSUPPORTED;
-  return nodes_batched_launch(descs, order, count, param_pool, pool_len, nodes_config(opts), out, workspace,
+  return nodes_batched_launch(descs, order, count, split, param_pool, pool_len, nodes_config(opts), out, workspace,
                               ws_bytes, (cudaStream_t)stream);
 }
 
@@ -325,14 +327,64 @@ mdi_status mdi_get_device_status(const void *workspace, size_t ws_bytes, int32_t
   return word ? MDI_EINVAL : MDI_OK;
 }
 
+// Time of one node-state integral on a team of `warps` warps (1 or 2) of the FP64
+// paired sweep, in units of one FP64 warp instruction: each of the d-1 cluster
+// levels takes ceil(a / lanes_per_pair) passes (8 node pairs share the team's
+// lanes), a pass costs each warp the interpolation of one point pair (P/2 fused
+// multiply-adds for each of the pair's two sums, their sum and difference, two
+// accumulations) and two evaluations of phi; the first level has no
+// interpolation; each level adds its constants and sums; the last axis is small.
+static double team_time(const mdi_batch_desc &d, int P, int warps) {
+  const double phi = d.family == MDI_FAM_PEAK ? 5.0 : 12.0;  // FP64 operations of one phi
+  const double pair = (double)P + 4.0 + 2.0 * phi, first = 2.0 + 2.0 * phi, level = 10.0;
+  const int lanes_per_pair = 4 * warps;
+  const double passes = std::ceil((double)d.a / lanes_per_pair);
+  const double last = std::ceil((double)d.n_last / (kWarp * warps)) * ((double)P + phi);
+  if (d.d < 2) return last;
+  return (double)(d.d - 2) * (passes * pair + level) + passes * first + level + last;
+}
+
+// Makespan of the hybrid schedule in the order `idx`: `ctas` two-warp CTAs take
+// the first `split` integrals as whole teams (longest first, each to the CTA that
+// frees first), then every warp takes the rest on its own.
+static double hybrid_makespan(const std::vector<double> &t2, const std::vector<double> &t1,
+                              const std::vector<int32_t> &idx, int split, int ctas) {
+  std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
+  for (int c = 0; c < ctas; ++c) free_at.push(0.0);
+  for (int i = 0; i < split; ++i) {
+    const double t0 = free_at.top();
+    free_at.pop();
+    free_at.push(t0 + t2[(size_t)idx[(size_t)i]]);
+  }
+  std::priority_queue<double, std::vector<double>, std::greater<double>> warps;
+  double end = 0.0;
+  while (!free_at.empty()) {
+    warps.push(free_at.top());
+    warps.push(free_at.top());
+    end = std::max(end, free_at.top());
+    free_at.pop();
+  }
+  for (size_t i = (size_t)split; i < idx.size(); ++i) {
+    const double t0 = warps.top();
+    warps.pop();
+    const double t = t0 + t1[(size_t)idx[i]];
+    end = std::max(end, t);
+    warps.push(t);
+  }
+  return end;
+}
+
 mdi_status mdi_batch_plan(const mdi_batch_desc *descs, int32_t count, int64_t pool_len, const mdi_opts *opts,
-                          int32_t *order) {
+                          int32_t *order, int32_t *split) {
   if (!descs || !order || count < 1 || pool_len < 0 || !opts_ok(opts)) return MDI_EINVAL;
-  const int P = nodes_config(opts).P;
+  const NodesConfig cfg = nodes_config(opts);
+  const int P = cfg.P;
   std::vector<double> cost((size_t)count);
+  bool all_real = true;
   for (int32_t i = 0; i < count; ++i) {
     if (!desc_ok(descs[i]) || !desc_in_pool(descs[i], pool_len)) return MDI_EINVAL;
     cost[(size_t)i] = nodes_cost(descs[i], P);
+    all_real = all_real && descs[i].family != MDI_FAM_OSC;
   }
   std::vector<int32_t> idx((size_t)count);
   std::iota(idx.begin(), idx.end(), 0);
@@ -342,6 +394,26 @@ mdi_status mdi_batch_plan(const mdi_batch_desc *descs, int32_t count, int64_t po
     return descs[x].a < descs[y].a;
   });
   std::memcpy(order, idx.data(), sizeof(int32_t) * (size_t)count);
+  if (split) {
+    *split = count;  // whole CTAs throughout unless the hybrid schedule applies and pays
+    if (all_real && cfg.precision == MDI_PREC_FP64 && cfg.block == 2 * kWarp && !cfg.stage) {
+      std::vector<double> t1((size_t)count), t2((size_t)count);
+      for (int32_t i = 0; i < count; ++i) {
+        t1[(size_t)i] = team_time(descs[i], P, 1);
+        t2[(size_t)i] = team_time(descs[i], P, 2);
+      }
+      const int ctas = std::max(1, nodes_workers(cfg));
+      double best = hybrid_makespan(t2, t1, idx, count, ctas);
+      for (int k = 0; k < 40; ++k) {
+        const int sp = (int)((int64_t)count * k / 40);
+        const double m = hybrid_makespan(t2, t1, idx, sp, ctas);
+        if (m < best) {
+          best = m;
+          *split = sp;
+        }
+      }
+    }
+  }
   return MDI_OK;
 }
 

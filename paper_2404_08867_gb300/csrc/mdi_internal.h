@@ -78,9 +78,11 @@ struct NodesConfig {
 NodesConfig nodes_config(const mdi_opts *opts);
 size_t nodes_batched_workspace_bytes(int count, const NodesConfig &cfg);
 mdi_status nodes_prepare(const NodesConfig &cfg, void *workspace, size_t ws_bytes, cudaStream_t stream);
-mdi_status nodes_batched_launch(const mdi_batch_desc *descs, const int32_t *order, int count,
+mdi_status nodes_batched_launch(const mdi_batch_desc *descs, const int32_t *order, int count, int split,
                                 const double *param_pool, int64_t pool_len, const NodesConfig &cfg, double *out,
                                 void *workspace, size_t ws_bytes, cudaStream_t stream);
+// Persistent CTAs one batched launch with this configuration keeps resident.
+int nodes_workers(const NodesConfig &cfg);
 // Device status word of a batched workspace (MDI_DEV_* flags): bytes needed to
 // hold it, and a stream-ordered read (waits for the stream), optionally cleared.
 size_t nodes_status_word_bytes();

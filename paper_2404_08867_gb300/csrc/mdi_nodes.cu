@@ -54,6 +54,32 @@ constexpr int kNodesSmemTable = 64 * 1024;  // table bytes staged in shared memo
 
 constexpr int kLvChunk = 64;  // levels whose constants are held in shared memory at once
 
+// The threads sweeping one integral: the whole CTA, or one warp of it (the second
+// phase of the hybrid schedule, where each warp of a two-warp CTA takes integrals
+// of its own).  tid and size stand for threadIdx.x and blockDim.x inside a sweep;
+// sync() is the team's barrier.
+struct Team {
+  int tid, size;
+  __device__ __forceinline__ void sync() const {
+    if (size == kWarp) __syncwarp();
+    else __syncthreads();
+  }
+  static __device__ __forceinline__ Team block() { return Team{(int)threadIdx.x, (int)blockDim.x}; }
+};
+
+// Sum over the team, valid in its thread 0.
+template <typename V> __device__ __forceinline__ V team_sum(V v, V *scratch, const Team &tm) {
+  v = warp_sum(v);
+  if (tm.size <= kWarp) return v;
+  const int lane = tm.tid & (kWarp - 1), warp = tm.tid / kWarp, nwarps = (tm.size + kWarp - 1) / kWarp;
+  if (lane == 0) scratch[warp] = v;
+  tm.sync();
+  V r = VOps<V>::zero();
+  if (warp == 0) r = warp_sum(lane < nwarps ? scratch[lane] : VOps<V>::zero());
+  tm.sync();
+  return r;
+}
+
 // Per-axis constants of a level: c, w, 1/c^2 in double and as float pairs.
 struct LevelConst {
   double c, w, ic2;
@@ -261,9 +287,10 @@ __device__ __forceinline__ void make_level_const(const double *__restrict__ prm,
 
 // Fills sh.lc with the constants of axes base .. base+kLvChunk-1 (all threads).
 template <bool DF = false>
-__device__ __forceinline__ void load_level_chunk(LevelConst *lc, const double *__restrict__ prm, int d, int base) {
+__device__ __forceinline__ void load_level_chunk(LevelConst *lc, const double *__restrict__ prm, int d, int base,
+                                                 const Team &tm = Team::block()) {
   const int n = min(kLvChunk, d - base);
-  for (int j = threadIdx.x; j < n; j += blockDim.x) make_level_const<DF>(prm, d, base + j, lc[j]);
+  for (int j = tm.tid; j < n; j += tm.size) make_level_const<DF>(prm, d, base + j, lc[j]);
 }
 
 // The argument of phi at the cluster points u = q/a + x0 of one node is affine in
@@ -364,17 +391,18 @@ __device__ __forceinline__ df32 pair_combine(const DfAcc &x, const DfAcc &y, flo
 // and the level constants of the chunk holding axis d-2 in sh.lc.
 template <int FAM, int PREC>
 __device__ void last_level(NodesShared &sh, const void *__restrict__ Ftab, int P, int d, int a, int n_last,
-                           const double *__restrict__ prm, double *__restrict__ out_slot, int sb) {
+                           const double *__restrict__ prm, double *__restrict__ out_slot, int sb,
+                           const Team &tm = Team::block()) {
   using V = typename FamTraits<FAM>::V;
   constexpr bool F32 = (PREC == MDI_PREC_FP32_EVAL_FP64 || PREC == MDI_PREC_FP32_EVAL_DF32);
   constexpr bool DF = (PREC == MDI_PREC_FP32_EVAL_DF32 || PREC == MDI_PREC_DF64);
   constexpr bool CPLX = (FAM == MDI_FAM_OSC);
   constexpr bool DF64 = (PREC == MDI_PREC_DF64) && !CPLX;
   constexpr bool DFSTATE = (PREC == MDI_PREC_DF64);
-  const int tid = threadIdx.x, B = blockDim.x;
+  const int tid = tm.tid, B = tm.size;
   if (d > 1 && (d - 1) % kLvChunk == 0) {
-    load_level_chunk<DFSTATE>(sh.lc, prm, d, d - 1);
-    __syncthreads();
+    load_level_chunk<DFSTATE>(sh.lc, prm, d, d - 1, tm);
+    tm.sync();
   }
   const LevelConst &LL = sh.lc[(d - 1) % kLvChunk];
   const bool tabulated = (n_last == a) && d > 1;
@@ -403,7 +431,7 @@ __device__ void last_level(NodesShared &sh, const void *__restrict__ Ftab, int P
   }
   if constexpr (DFSTATE) {  // double view of the state for the general last level
     if (tid < P) sh.G[sb][tid] = join2(sh.Gdf[sb][tid]);
-    __syncthreads();
+    tm.sync();
   }
   const AxisParams ap{LL.c, LL.w, LL.ic2};
   const double inv_n = 1.0 / (double)n_last;
@@ -442,7 +470,7 @@ __device__ void last_level(NodesShared &sh, const void *__restrict__ Ftab, int P
     }
     acc = VOps<V>::add(acc, VOps<V>::mul(phi<FAM, F32 && !DFSTATE>(u, ap), g));
   }
-  const V tot = block_sum(acc, (V *)sh.red);
+  const V tot = team_sum(acc, (V *)sh.red, tm);
   if (tid == 0) {
     if constexpr (CPLX) {
       double sn, cs;
@@ -452,7 +480,7 @@ __device__ void last_level(NodesShared &sh, const void *__restrict__ Ftab, int P
       *out_slot = tot * inv_n;
     }
   }
-  __syncthreads();
+  tm.sync();
 }
 
 
@@ -806,9 +834,10 @@ __device__ __forceinline__ double phi_t64(double t, double ic2, const double *__
 template <int FAM, int H, bool F32 = false>
 __device__ void sweep_paired_fp64(NodesShared &sh, const NodesConsts *__restrict__ kc,
                                   const double2 *__restrict__ Lpm, const void *__restrict__ Ftab, int P, int d, int a,
-                                  int n_last, const double *__restrict__ prm, double *__restrict__ out_slot) {
+                                  int n_last, const double *__restrict__ prm, double *__restrict__ out_slot,
+                                  const Team &tm = Team::block()) {
   const int h = H > 0 ? H : P / 2;
-  const int tid = threadIdx.x, B = blockDim.x;
+  const int tid = tm.tid, B = tm.size;
   const int Q = node_lanes(B, h);
   const int pp = min(tid / Q, h - 1), pb = P - 1 - pp, qs = tid % Q;
   const bool act = tid < h * Q;
@@ -816,8 +845,8 @@ __device__ void sweep_paired_fp64(NodesShared &sh, const NodesConsts *__restrict
   const int npts_h = a * h;
   if (tid < h) sh.G[0][tid] = make_double2(1.0, 0.0);  // G_0 = 1: E = 1, O = 0
   if (F32 && tid < P) sh.xadf[tid] = kc->xa[a][tid];
-  load_level_chunk(sh.lc, prm, d, 0);
-  __syncthreads();
+  load_level_chunk(sh.lc, prm, d, 0, tm);
+  tm.sync();
   const double inv_a = 1.0 / (double)a, half_inv_a = 0.5 * inv_a;
   const double xa = sh.xi[pp], xb = sh.xi[pb];
   const float iaf = F32 ? kc->ia[a].x : 0.f, xaf = F32 ? sh.xadf[pp].x : 0.f, xbf = F32 ? sh.xadf[pb].x : 0.f;
@@ -825,8 +854,8 @@ __device__ void sweep_paired_fp64(NodesShared &sh, const NodesConsts *__restrict
   for (int k = 1; k < d; ++k) {
     const int j = k - 1;
     if (j > 0 && j % kLvChunk == 0) {
-      load_level_chunk(sh.lc, prm, d, j);
-      __syncthreads();
+      load_level_chunk(sh.lc, prm, d, j, tm);
+      tm.sync();
     }
     const LevelConst &L = sh.lc[j % kLvChunk];
     const int rb = (k - 1) & 1, wb = k & 1;
@@ -894,7 +923,7 @@ __device__ void sweep_paired_fp64(NodesShared &sh, const NodesConsts *__restrict
       const double2 s2 = lanes_sum(make_double2(acc_a, acc_b), Q);
       if (act && qs == 0) sh.G[wb][pp] = make_double2((s2.x + s2.y) * half_inv_a, (s2.x - s2.y) * half_inv_a);
     }
-    __syncthreads();
+    tm.sync();
   }
   const int eb = (d - 1) & 1, gbuf = eb ^ 1;
   if (tid < P) {
@@ -902,8 +931,8 @@ __device__ void sweep_paired_fp64(NodesShared &sh, const NodesConsts *__restrict
     const double2 eo = sh.G[eb][t];
     sh.G[gbuf][tid] = make_double2(tid < h ? eo.x + eo.y : eo.x - eo.y, 0.0);
   }
-  __syncthreads();
-  last_level<FAM, F32 ? MDI_PREC_FP32_EVAL_FP64 : MDI_PREC_FP64>(sh, Ftab, P, d, a, n_last, prm, out_slot, gbuf);
+  tm.sync();
+  last_level<FAM, F32 ? MDI_PREC_FP32_EVAL_FP64 : MDI_PREC_FP64>(sh, Ftab, P, d, a, n_last, prm, out_slot, gbuf, tm);
 }
 
 // One integral of a real family on the paired sweep of a single-precision-
@@ -926,6 +955,113 @@ __device__ __forceinline__ void run_paired(NodesShared &sh, const NodesConsts *_
   else paired_one<PREC, H, MDI_FAM_PEAK>(sh, kc, C, Ftab, P, d, a, n_last, prm, out_slot);
 }
 
+// One work item of the batched kernel: order slot `slot`, swept by team `tm` with
+// state `sh`.  `whole` says the team is the whole CTA (which may stage the basis
+// table in shared memory and runs every family); a one-warp team of the hybrid
+// schedule runs the FP64 paired sweep of the real families only.
+template <int PREC>
+__device__ __forceinline__ void nodes_item(int slot, const Team &tm, bool whole, NodesShared &sh,
+                                           unsigned char *tab_smem, int &staged_a,
+                                           const mdi_batch_desc *__restrict__ descs,
+                                           const int32_t *__restrict__ order, int count,
+                                           const mdi_batch_desc &single, const double *__restrict__ pool,
+                                           long long pool_len, const void *__restrict__ tables,
+                                           const float4 *__restrict__ paired, const NodesConsts *__restrict__ kc,
+                                           int P, int stage, double *__restrict__ out, unsigned *__restrict__ counter,
+                                           bool prepared) {
+  const int inst = order ? order[slot] : slot;
+  if (inst < 0 || inst >= count) {  // an order entry outside the batch is skipped
+    if (tm.tid == 0) atomicOr(&counter[3], MDI_DEV_BAD_ORDER);
+    return;
+  }
+  const mdi_batch_desc ds = descs ? descs[inst] : single;
+  const int a = ds.a;
+  const bool desc_ok = ds.family >= MDI_FAM_EXP && ds.family <= MDI_FAM_PEAK && ds.d >= 1 &&
+                       ds.d <= MDI_BATCH_MAX_D && a >= 1 && a <= kNodesAMax && ds.n_last >= 1 &&
+                       ds.n_last <= 4096 && ds.param_offset >= 0 && (whole || ds.family != MDI_FAM_OSC);
+  // The integral's 2d parameters must lie inside the pool (no read past its end).
+  const bool in_pool = desc_ok && ds.param_offset <= pool_len && 2ll * ds.d <= pool_len - ds.param_offset;
+  if (!prepared || !in_pool) {
+    if (tm.tid == 0) {
+      out[inst] = __longlong_as_double(0x7ff8000000000000ll);  // NaN marks a rejected integral
+      atomicOr(&counter[3], !prepared ? MDI_DEV_UNPREPARED : !desc_ok ? MDI_DEV_BAD_DESC : MDI_DEV_POOL_RANGE);
+    }
+    return;
+  }
+  // Basis tables of a: the cluster part (the paired one for real families),
+  // staged in shared memory when asked and it fits, and the last-axis part.
+  const bool use_paired = paired != nullptr && ds.family != MDI_FAM_OSC;
+  const size_t tbytes = (size_t)a * P * P * 8;  // plain cluster part; a multiple of 16 for even P
+  const unsigned char *gtab = (const unsigned char *)tables + table_offset(a, P) * 8;
+  const void *Ftab = gtab + tbytes;
+  const unsigned char *csrc = use_paired ? (const unsigned char *)(paired + paired_offset(a, P)) : gtab;
+  const size_t cbytes = use_paired ? (size_t)a * P * P * 4 : tbytes;
+  const void *C = csrc;
+  if (whole && stage && cbytes <= (size_t)kNodesSmemTable && ds.d > 1) {
+    const int key = 2 * a + (use_paired ? 1 : 0);
+    if (staged_a != key) {
+      const double2 *src = (const double2 *)csrc;
+      double2 *dst = (double2 *)tab_smem;
+      for (size_t i = threadIdx.x; i < cbytes / 16; i += blockDim.x) dst[i] = src[i];
+      staged_a = key;
+      __syncthreads();
+    }
+    C = tab_smem;
+  }
+  const double *prm = pool + ds.param_offset;
+  double *out_slot = out + inst;
+  if (use_paired) {
+    // P = 16 (the default node count) runs with the pair loop fully unrolled.
+    if constexpr (PREC == MDI_PREC_FP64) {
+      // FP64 and DF64 spelled out: this form keeps their instantiations as
+      // they were tuned (the FP64 one free of spills).
+      const double2 *Lpm = (const double2 *)C;
+      if (P == 16) {
+        if (ds.family == MDI_FAM_EXP)
+          sweep_paired_fp64<MDI_FAM_EXP, 8>(sh, nullptr, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot, tm);
+        else if (ds.family == MDI_FAM_GAUSS)
+          sweep_paired_fp64<MDI_FAM_GAUSS, 8>(sh, nullptr, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot, tm);
+        else sweep_paired_fp64<MDI_FAM_PEAK, 8>(sh, nullptr, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot, tm);
+      } else {
+        if (ds.family == MDI_FAM_EXP)
+          sweep_paired_fp64<MDI_FAM_EXP, 0>(sh, nullptr, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot, tm);
+        else if (ds.family == MDI_FAM_GAUSS)
+          sweep_paired_fp64<MDI_FAM_GAUSS, 0>(sh, nullptr, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot, tm);
+        else sweep_paired_fp64<MDI_FAM_PEAK, 0>(sh, nullptr, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot, tm);
+      }
+    } else if constexpr (PREC == MDI_PREC_DF64) {
+      const float4 *Lpm = (const float4 *)C;
+      if (P == 16) {
+        if (ds.family == MDI_FAM_EXP) sweep_paired<MDI_FAM_EXP, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot);
+        else if (ds.family == MDI_FAM_GAUSS)
+          sweep_paired<MDI_FAM_GAUSS, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot);
+        else sweep_paired<MDI_FAM_PEAK, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot);
+      } else {
+        if (ds.family == MDI_FAM_EXP) sweep_paired<MDI_FAM_EXP, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot);
+        else if (ds.family == MDI_FAM_GAUSS)
+          sweep_paired<MDI_FAM_GAUSS, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot);
+        else sweep_paired<MDI_FAM_PEAK, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot);
+      }
+    } else if (P == 16) {
+      run_paired<PREC, 8>(sh, kc, C, Ftab, P, ds.family, ds.d, a, ds.n_last, prm, out_slot);
+    } else {
+      run_paired<PREC, 0>(sh, kc, C, Ftab, P, ds.family, ds.d, a, ds.n_last, prm, out_slot);
+    }
+    return;
+  }
+  switch (ds.family) {
+    case MDI_FAM_EXP: sweep_one<MDI_FAM_EXP, PREC>(sh, kc, C, Ftab, P, ds.d, a, ds.n_last, prm, out_slot); break;
+    case MDI_FAM_OSC: sweep_one<MDI_FAM_OSC, PREC>(sh, kc, C, Ftab, P, ds.d, a, ds.n_last, prm, out_slot); break;
+    case MDI_FAM_GAUSS: sweep_one<MDI_FAM_GAUSS, PREC>(sh, kc, C, Ftab, P, ds.d, a, ds.n_last, prm, out_slot); break;
+    default: sweep_one<MDI_FAM_PEAK, PREC>(sh, kc, C, Ftab, P, ds.d, a, ds.n_last, prm, out_slot); break;
+  }
+}
+
+// Persistent batched kernel.  Order slots below `split` are swept by the whole
+// CTA; from the first slot at or past it (hybrid schedule, FP64 with two-warp
+// CTAs and the tables read through L1 only) each warp takes slots of its own,
+// with its own copy of the state (the second NodesShared).  split >= count: every
+// slot by the whole CTA.
 template <int PREC>
 __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi_batch_desc *__restrict__ descs,
                                                                        const int32_t *__restrict__ order, int count,
@@ -935,125 +1071,60 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
                                                                        const void *__restrict__ tables,
                                                                        const float4 *__restrict__ paired,
                                                                        const NodesConsts *__restrict__ kc, int P,
-                                                                       int stage, double *__restrict__ out,
+                                                                       int stage, int split, double *__restrict__ out,
                                                                        unsigned *__restrict__ counter,
                                                                        unsigned expect_tag) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
+  const bool hybrid = split < count;
   NodesShared &sh = *reinterpret_cast<NodesShared *>(dyn_smem);
-  unsigned char *tab_smem = dyn_smem + align16(sizeof(NodesShared));
-  for (int t = threadIdx.x; t < P; t += blockDim.x) {
-    sh.xi[t] = kc->xi[t];
-    sh.bw[t] = kc->bw[t];
-  }
-  if (PREC == MDI_PREC_DF64)
-    for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) sh.exp2tab[j] = kc->exp2tab[j];
-  if (PREC == MDI_PREC_FP64) {
-    for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) sh.exp2d[j] = kc->exp2d[j];
-    for (int q = threadIdx.x; q < kNodesAMax; q += blockDim.x) sh.qd[q] = (double)q;
+  NodesShared &sh2 = *reinterpret_cast<NodesShared *>(dyn_smem + (hybrid ? align16(sizeof(NodesShared)) : 0));
+  unsigned char *tab_smem = dyn_smem + align16(sizeof(NodesShared)) * (hybrid ? 2 : 1);
+  for (int c = 0; c < (hybrid ? 2 : 1); ++c) {
+    NodesShared &s = c ? sh2 : sh;
+    for (int t = threadIdx.x; t < P; t += blockDim.x) {
+      s.xi[t] = kc->xi[t];
+      s.bw[t] = kc->bw[t];
+    }
+    if (PREC == MDI_PREC_DF64)
+      for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s.exp2tab[j] = kc->exp2tab[j];
+    if (PREC == MDI_PREC_FP64) {
+      for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s.exp2d[j] = kc->exp2d[j];
+      for (int q = threadIdx.x; q < kNodesAMax; q += blockDim.x) s.qd[q] = (double)q;
+    }
   }
   int staged_a = -1;
   // counter[0]: next work item; counter[1]: CTAs finished; counter[2]: preparation
   // tag; counter[3]: the device status word (MDI_DEV_* flags, OR-ed in).
   const bool prepared = counter[2] == expect_tag;
+  int slot;
   while (true) {
     if (threadIdx.x == 0) sh.inst = (int)atomicAdd(&counter[0], 1u);
     __syncthreads();
-    const int slot = sh.inst;
+    slot = sh.inst;
     __syncthreads();
-    if (slot >= count) break;
-    const int inst = order ? order[slot] : slot;
-    if (inst < 0 || inst >= count) {  // an order entry outside the batch is skipped
-      if (threadIdx.x == 0) atomicOr(&counter[3], MDI_DEV_BAD_ORDER);
-      continue;
-    }
-    const mdi_batch_desc ds = descs ? descs[inst] : single;
-    const int a = ds.a;
-    const bool desc_ok = ds.family >= MDI_FAM_EXP && ds.family <= MDI_FAM_PEAK && ds.d >= 1 &&
-                         ds.d <= MDI_BATCH_MAX_D && a >= 1 && a <= kNodesAMax && ds.n_last >= 1 &&
-                         ds.n_last <= 4096 && ds.param_offset >= 0;
-    // The integral's 2d parameters must lie inside the pool (no read past its end).
-    const bool in_pool = desc_ok && ds.param_offset <= pool_len && 2ll * ds.d <= pool_len - ds.param_offset;
-    if (!prepared || !in_pool) {
-      if (threadIdx.x == 0) {
-        out[inst] = __longlong_as_double(0x7ff8000000000000ll);  // NaN marks a rejected integral
-        atomicOr(&counter[3], !prepared ? MDI_DEV_UNPREPARED : !desc_ok ? MDI_DEV_BAD_DESC : MDI_DEV_POOL_RANGE);
-      }
-      continue;
-    }
-    // Basis tables of a: the cluster part (the paired one for real families),
-    // staged in shared memory when asked and it fits, and the last-axis part.
-    const bool use_paired = paired != nullptr && ds.family != MDI_FAM_OSC;
-    const size_t tbytes = (size_t)a * P * P * 8;  // plain cluster part; a multiple of 16 for even P
-    const unsigned char *gtab = (const unsigned char *)tables + table_offset(a, P) * 8;
-    const void *Ftab = gtab + tbytes;
-    const unsigned char *csrc = use_paired ? (const unsigned char *)(paired + paired_offset(a, P)) : gtab;
-    const size_t cbytes = use_paired ? (size_t)a * P * P * 4 : tbytes;
-    const void *C = csrc;
-    if (stage && cbytes <= (size_t)kNodesSmemTable && ds.d > 1) {
-      const int key = 2 * a + (use_paired ? 1 : 0);
-      if (staged_a != key) {
-        const double2 *src = (const double2 *)csrc;
-        double2 *dst = (double2 *)tab_smem;
-        for (size_t i = threadIdx.x; i < cbytes / 16; i += blockDim.x) dst[i] = src[i];
-        staged_a = key;
-        __syncthreads();
-      }
-      C = tab_smem;
-    }
-    const double *prm = pool + ds.param_offset;
-    if (use_paired) {
-      // P = 16 (the default node count) runs with the pair loop fully unrolled.
-      if constexpr (PREC == MDI_PREC_FP64) {
-        // FP64 and DF64 spelled out: this form keeps their instantiations as
-        // they were tuned (the FP64 one free of spills).
-        const double2 *Lpm = (const double2 *)C;
-        if (P == 16) {
-          if (ds.family == MDI_FAM_EXP)
-            sweep_paired_fp64<MDI_FAM_EXP, 8>(sh, nullptr, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-          else if (ds.family == MDI_FAM_GAUSS)
-            sweep_paired_fp64<MDI_FAM_GAUSS, 8>(sh, nullptr, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-          else sweep_paired_fp64<MDI_FAM_PEAK, 8>(sh, nullptr, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-        } else {
-          if (ds.family == MDI_FAM_EXP)
-            sweep_paired_fp64<MDI_FAM_EXP, 0>(sh, nullptr, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-          else if (ds.family == MDI_FAM_GAUSS)
-            sweep_paired_fp64<MDI_FAM_GAUSS, 0>(sh, nullptr, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-          else sweep_paired_fp64<MDI_FAM_PEAK, 0>(sh, nullptr, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
+    if (slot >= count || slot >= split) break;
+    nodes_item<PREC>(slot, Team::block(), true, sh, tab_smem, staged_a, descs, order, count, single, pool, pool_len,
+                     tables, paired, kc, P, stage, out, counter, prepared);
+  }
+  if (slot < count) {  // hybrid: slot is the first one past the split; warp 0 takes it
+    if constexpr (PREC == MDI_PREC_FP64) {
+      const int warp = threadIdx.x / kWarp, lane = threadIdx.x & (kWarp - 1);
+      NodesShared &shw = warp == 0 ? sh : sh2;
+      const Team tm{lane, kWarp};
+      int mine = warp == 0 ? slot : -1;
+      while (true) {
+        if (mine < 0) {
+          unsigned v = 0;
+          if (lane == 0) v = atomicAdd(&counter[0], 1u);
+          mine = (int)__shfl_sync(0xffffffffu, v, 0);
         }
-      } else if constexpr (PREC == MDI_PREC_DF64) {
-        const float4 *Lpm = (const float4 *)C;
-        if (P == 16) {
-          if (ds.family == MDI_FAM_EXP) sweep_paired<MDI_FAM_EXP, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-          else if (ds.family == MDI_FAM_GAUSS)
-            sweep_paired<MDI_FAM_GAUSS, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-          else sweep_paired<MDI_FAM_PEAK, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-        } else {
-          if (ds.family == MDI_FAM_EXP) sweep_paired<MDI_FAM_EXP, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-          else if (ds.family == MDI_FAM_GAUSS)
-            sweep_paired<MDI_FAM_GAUSS, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-          else sweep_paired<MDI_FAM_PEAK, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-        }
-      } else if (P == 16) {
-        run_paired<PREC, 8>(sh, kc, C, Ftab, P, ds.family, ds.d, a, ds.n_last, prm, out + inst);
-      } else {
-        run_paired<PREC, 0>(sh, kc, C, Ftab, P, ds.family, ds.d, a, ds.n_last, prm, out + inst);
+        if (mine >= count) break;
+        nodes_item<PREC>(mine, tm, false, shw, tab_smem, staged_a, descs, order, count, single, pool, pool_len,
+                         tables, paired, kc, P, 0, out, counter, prepared);
+        mine = -1;
       }
-      continue;
     }
-    switch (ds.family) {
-      case MDI_FAM_EXP:
-        sweep_one<MDI_FAM_EXP, PREC>(sh, kc, C, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-        break;
-      case MDI_FAM_OSC:
-        sweep_one<MDI_FAM_OSC, PREC>(sh, kc, C, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-        break;
-      case MDI_FAM_GAUSS:
-        sweep_one<MDI_FAM_GAUSS, PREC>(sh, kc, C, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-        break;
-      default:
-        sweep_one<MDI_FAM_PEAK, PREC>(sh, kc, C, Ftab, P, ds.d, a, ds.n_last, prm, out + inst);
-        break;
-    }
+    __syncthreads();
   }
   // The last CTA to finish re-arms the queue for the next call on this workspace.
   if (threadIdx.x == 0) {
@@ -1159,13 +1230,53 @@ mdi_status nodes_prepare(const NodesConfig &cfg, void *workspace, size_t ws_byte
   return check_launch();
 }
 
+// The hybrid schedule needs two-warp CTAs reading their tables through L1, and the
+// FP64 paired sweep (the only one written for a one-warp team).
+static bool hybrid_ok(const NodesConfig &cfg) {
+  return cfg.precision == MDI_PREC_FP64 && cfg.block == 2 * kWarp && !cfg.stage;
+}
+
 template <int PREC>
-static mdi_status launch_nodes(const mdi_batch_desc *descs, const int32_t *order, int count,
+static int resident_ctas(const NodesConfig &cfg, size_t smem, bool hybrid) {
+  // Resident CTAs per SM for this (block, P, staging, schedule), queried once per process.
+  static int occ_cache[4][kNodesMaxBlock / 32 + 1][kNodesPMax / 2 + 1][2][2];
+  int &occ = occ_cache[PREC][cfg.block / 32][cfg.P / 2][cfg.stage ? 1 : 0][hybrid ? 1 : 0];
+  if (occ == 0) {
+    int o = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, nodes_batched_kernel<PREC>, cfg.block, smem);
+    occ = std::max(1, o);
+  }
+  return occ;
+}
+
+static size_t launch_smem(const NodesConfig &cfg, bool hybrid) {
+  return nodes_smem_bytes(cfg.block, cfg.P, cfg.stage != 0) + (hybrid ? align16(sizeof(NodesShared)) : 0);
+}
+
+int nodes_workers(const NodesConfig &cfg) {
+  const bool hybrid = hybrid_ok(cfg);
+  const size_t smem = launch_smem(cfg, hybrid);
+  int per_sm = cfg.ctas_per_sm;
+  if (per_sm == 0) {
+    switch (cfg.precision) {
+      case MDI_PREC_FP64: per_sm = resident_ctas<MDI_PREC_FP64>(cfg, smem, hybrid); break;
+      case MDI_PREC_FP32_EVAL_FP64: per_sm = resident_ctas<MDI_PREC_FP32_EVAL_FP64>(cfg, smem, hybrid); break;
+      case MDI_PREC_FP32_EVAL_DF32: per_sm = resident_ctas<MDI_PREC_FP32_EVAL_DF32>(cfg, smem, hybrid); break;
+      default: per_sm = resident_ctas<MDI_PREC_DF64>(cfg, smem, hybrid); break;
+    }
+  }
+  return sm_count() * per_sm;
+}
+
+template <int PREC>
+static mdi_status launch_nodes(const mdi_batch_desc *descs, const int32_t *order, int count, int split,
                                const mdi_batch_desc &single, const double *pool, int64_t pool_len,
                                const NodesConfig &cfg, double *out, void *ws, cudaStream_t stream) {
   unsigned *counter = (unsigned *)ws;
   void *tables = (char *)ws + counter_bytes();
-  const size_t smem = nodes_smem_bytes(cfg.block, cfg.P, cfg.stage != 0);
+  const bool hybrid = split < count && hybrid_ok(cfg);
+  const int split_eff = hybrid ? std::max(split, 0) : count;
+  const size_t smem = launch_smem(cfg, hybrid);
   static thread_local bool attr_set[4] = {false, false, false, false};
   if (!attr_set[PREC]) {
     cudaError_t e = cudaFuncSetAttribute(nodes_batched_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1176,49 +1287,41 @@ static mdi_status launch_nodes(const mdi_batch_desc *descs, const int32_t *order
     }
     attr_set[PREC] = true;
   }
-  int per_sm = cfg.ctas_per_sm;
-  if (per_sm == 0) {
-    // Resident CTAs per SM for this (block, P, staging), queried once per process.
-    static int occ_cache[4][kNodesMaxBlock / 32 + 1][kNodesPMax / 2 + 1][2];
-    int &occ = occ_cache[PREC][cfg.block / 32][cfg.P / 2][cfg.stage ? 1 : 0];
-    if (occ == 0) {
-      int o = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, nodes_batched_kernel<PREC>, cfg.block, smem);
-      occ = std::max(1, o);
-    }
-    per_sm = occ;
-  }
+  const int per_sm = cfg.ctas_per_sm ? cfg.ctas_per_sm : resident_ctas<PREC>(cfg, smem, hybrid);
   const int grid = std::max(1, std::min(count, sm_count() * per_sm));
   const float4 *paired = paired_tables(cfg) ? (const float4 *)((char *)tables + align_up(table_bytes(cfg.P))) : nullptr;
   const NodesConsts *kc = (const NodesConsts *)((char *)ws + consts_offset(cfg));
   nodes_batched_kernel<PREC><<<grid, cfg.block, smem, stream>>>(descs, order, count, single, pool,
                                                                  (long long)pool_len, tables, paired, kc, cfg.P,
-                                                                 cfg.stage, out, counter, nodes_tag(cfg));
+                                                                 cfg.stage, split_eff, out, counter, nodes_tag(cfg));
   return check_launch();
 }
 
-static mdi_status dispatch_nodes(const mdi_batch_desc *descs, const int32_t *order, int count,
+static mdi_status dispatch_nodes(const mdi_batch_desc *descs, const int32_t *order, int count, int split,
                                  const mdi_batch_desc &single, const double *pool, int64_t pool_len,
                                  const NodesConfig &cfg, double *out, void *ws, cudaStream_t stream) {
   switch (cfg.precision) {
     case MDI_PREC_FP64:
-      return launch_nodes<MDI_PREC_FP64>(descs, order, count, single, pool, pool_len, cfg, out, ws, stream);
+      return launch_nodes<MDI_PREC_FP64>(descs, order, count, split, single, pool, pool_len, cfg, out, ws, stream);
     case MDI_PREC_FP32_EVAL_FP64:
-      return launch_nodes<MDI_PREC_FP32_EVAL_FP64>(descs, order, count, single, pool, pool_len, cfg, out, ws, stream);
+      return launch_nodes<MDI_PREC_FP32_EVAL_FP64>(descs, order, count, split, single, pool, pool_len, cfg, out, ws,
+                                                   stream);
     case MDI_PREC_FP32_EVAL_DF32:
-      return launch_nodes<MDI_PREC_FP32_EVAL_DF32>(descs, order, count, single, pool, pool_len, cfg, out, ws, stream);
-    default: return launch_nodes<MDI_PREC_DF64>(descs, order, count, single, pool, pool_len, cfg, out, ws, stream);
+      return launch_nodes<MDI_PREC_FP32_EVAL_DF32>(descs, order, count, split, single, pool, pool_len, cfg, out, ws,
+                                                   stream);
+    default:
+      return launch_nodes<MDI_PREC_DF64>(descs, order, count, split, single, pool, pool_len, cfg, out, ws, stream);
   }
 }
 
-mdi_status nodes_batched_launch(const mdi_batch_desc *descs, const int32_t *order, int count,
+mdi_status nodes_batched_launch(const mdi_batch_desc *descs, const int32_t *order, int count, int split,
                                 const double *param_pool, int64_t pool_len, const NodesConfig &cfg, double *out,
                                 void *workspace, size_t ws_bytes, cudaStream_t stream) {
   if (!descs || !param_pool || !out || count < 1) return MDI_EINVAL;
   if (!config_ok(cfg)) return MDI_EINVAL;
   if (!ws_ok(workspace, ws_bytes, cfg)) return MDI_EWORKSPACE;
   mdi_batch_desc none{};
-  return dispatch_nodes(descs, order, count, none, param_pool, pool_len, cfg, out, workspace, stream);
+  return dispatch_nodes(descs, order, count, split, none, param_pool, pool_len, cfg, out, workspace, stream);
 }
 
 size_t nodes_status_word_bytes() { return 4 * sizeof(unsigned); }
@@ -1248,7 +1351,7 @@ mdi_status nodes_single_launch(int family, int d, int64_t a, int64_t n_last, con
   mdi_status st = nodes_prepare(cfg, workspace, ws_bytes, stream);
   if (st != MDI_OK) return st;
   mdi_batch_desc one{family, d, (int32_t)a, (int32_t)n_last, 0, 0};
-  return dispatch_nodes(nullptr, nullptr, 1, one, params, 2 * (int64_t)d, cfg, out, workspace, stream);
+  return dispatch_nodes(nullptr, nullptr, 1, 1, one, params, 2 * (int64_t)d, cfg, out, workspace, stream);
 }
 
 }  // namespace mdi

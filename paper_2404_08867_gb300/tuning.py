@@ -4,10 +4,11 @@
 order from the library's longest-first planner, parameter pool -- three views of
 one packed device buffer, so that a new batch of the same shape arrives in one
 host-to-device copy of ``host_inputs()``), a prepared workspace, and the launch
-shape.  ``tune()`` times the candidate shapes -- CTA
-size and whether each integral's basis table is staged in shared memory or read
-through L1 -- on the batch itself with CUDA events and keeps the fastest (cached
-per batch signature for the process).  ``capture()`` records the one-kernel
+shape.  ``tune()`` times the candidate shapes -- CTA size, whether each
+integral's basis table is staged in shared memory or read through L1, and (FP64)
+the planner's hybrid schedule on two-warp CTAs, whose largest integrals run on
+whole CTAs and the rest one per warp -- on the batch itself with CUDA events and
+keeps the fastest (cached per batch signature for the process).  ``capture()`` records the one-kernel
 launch into a CUDA graph; ``run()`` replays it.  Nothing here computes: every
 launch goes through the C ABI.
 """
@@ -35,7 +36,10 @@ class BatchedMDILR:
         self.descs_host = descs
         pool_t = pool if isinstance(pool, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(pool))
         pool_t = pool_t.to(dtype=torch.float64).contiguous().cpu()
-        order = mdi_batch_plan(descs, pool_t.numel(), nodes=nodes)
+        # The order does not depend on the launch shape; the hybrid split is the
+        # planner's for two-warp CTAs reading their tables through L1.
+        order, self.hybrid_split = mdi_batch_plan(descs, pool_t.numel(), nodes=nodes, precision=precision, block=64,
+                                                  table_in_l1=1)
         # Packed inputs: descriptors | order | pool, each 256-byte aligned.
         def up(x):
             return (x + 255) // 256 * 256
@@ -78,8 +82,10 @@ class BatchedMDILR:
                 int(d.max()), torch.cuda.get_device_name())
 
     def launch(self, **shape) -> torch.Tensor:
+        opts = dict(self.opts, **shape)
+        split = opts.pop("split", self.count)
         return mdi_lr_integrate_batched(self.descs, self.pool, self.count, order=self.order, out=self.out,
-                                        workspace=self.workspace, **self.opts, **shape)
+                                        workspace=self.workspace, split=split, **opts)
 
     def _time(self, reps: int = 7, flush: Optional[torch.Tensor] = None, **shape) -> float:
         """Median device time of one launch with `shape`, replayed from a CUDA graph
@@ -124,12 +130,18 @@ class BatchedMDILR:
                 if block % self.nodes:
                     continue
                 for l1 in CANDIDATE_TABLE_IN_L1:
-                    results[(block, l1)] = self._time(reps, flush=flush, block=block, table_in_l1=l1)
-            (block, l1), best = min(results.items(), key=lambda kv: kv[1])
-            _cache[key] = {"block": block, "table_in_l1": l1, "ms": best,
-                           "candidates": {f"block={b},table_in_l1={t}": ms for (b, t), ms in results.items()}}
+                    results[(block, l1, self.count)] = self._time(reps, flush=flush, block=block, table_in_l1=l1,
+                                                                  split=self.count)
+            if self.hybrid_split < self.count:
+                results[(64, 1, self.hybrid_split)] = self._time(reps, flush=flush, block=64, table_in_l1=1,
+                                                                 split=self.hybrid_split)
+            (block, l1, split), best = min(results.items(), key=lambda kv: kv[1])
+            _cache[key] = {"block": block, "table_in_l1": l1, "split": split, "ms": best,
+                           "candidates": {f"block={b},table_in_l1={t},split={sp}": ms
+                                          for (b, t, sp), ms in results.items()}}
         self.tuning = _cache[key]
-        self.opts.update(block=self.tuning["block"], table_in_l1=self.tuning["table_in_l1"])
+        self.opts.update(block=self.tuning["block"], table_in_l1=self.tuning["table_in_l1"],
+                         split=self.tuning["split"])
         self.graph = None
         return self.tuning
 

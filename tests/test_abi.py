@@ -107,7 +107,8 @@ def test_batch_plan_is_longest_first_permutation(lib):
     n = 500
     a = rng.integers(8, 33, n)
     descs = mdi.make_batch_descs(["gauss"] * n, rng.integers(6, 21, n), a, a, np.arange(n) * 40)
-    order = mdi.mdi_batch_plan(descs, 40 * n)
+    order, split = mdi.mdi_batch_plan(descs, 40 * n)
+    assert split == n  # default 256-thread CTAs: whole CTAs throughout
     assert sorted(order.tolist()) == list(range(n))
     # one family, n_last = a: the work is dominated by the (d - 1) * a cluster points;
     # the last axis adds less than 3 such units for a <= 32
@@ -213,9 +214,9 @@ def test_empty_batch_is_refused(lib):
     fake = ctypes.c_void_p(0x1000)
     o = _ffi.MdiOpts()
     for count in (0, -3):
-        assert lib.mdi_lr_integrate_batched(fake, fake, count, fake, 1 << 20, ctypes.byref(o), fake, fake, 1 << 30,
-                                            _null()) == _ffi.MDI_EINVAL
-        assert lib.mdi_batch_plan(fake, count, 1 << 20, ctypes.byref(o), fake) == _ffi.MDI_EINVAL
+        assert lib.mdi_lr_integrate_batched(fake, fake, count, count, fake, 1 << 20, ctypes.byref(o), fake, fake,
+                                            1 << 30, _null()) == _ffi.MDI_EINVAL
+        assert lib.mdi_batch_plan(fake, count, 1 << 20, ctypes.byref(o), fake, _null()) == _ffi.MDI_EINVAL
     b = ctypes.c_size_t()
     assert lib.mdi_lr_batched_workspace_size(0, ctypes.byref(o), ctypes.byref(b)) == _ffi.MDI_EINVAL
 
@@ -262,7 +263,7 @@ def test_batch_plan_checks_the_parameter_pool(lib):
     the last admissible one is refused by the planner (the kernel flags it on the
     device, where the host cannot look)."""
     descs = mdi.make_batch_descs(["gauss", "peak"], [3, 4], [8, 9], [8, 9], [0, 6])
-    assert sorted(mdi.mdi_batch_plan(descs, 14).tolist()) == [0, 1]
+    assert sorted(mdi.mdi_batch_plan(descs, 14)[0].tolist()) == [0, 1]
     with pytest.raises(mdi.MdiError):
         mdi.mdi_batch_plan(descs, 13)
     bad = descs.copy()
@@ -271,8 +272,11 @@ def test_batch_plan_checks_the_parameter_pool(lib):
         mdi.mdi_batch_plan(bad, 14)
     o = _ffi.MdiOpts()
     fake = ctypes.c_void_p(0x1000)
-    assert lib.mdi_batch_plan(descs.ctypes.data_as(ctypes.c_void_p), 2, -1, ctypes.byref(o), fake) == _ffi.MDI_EINVAL
-    assert lib.mdi_lr_integrate_batched(fake, fake, 2, fake, -1, ctypes.byref(o), fake, fake, 1 << 30,
+    assert lib.mdi_batch_plan(descs.ctypes.data_as(ctypes.c_void_p), 2, -1, ctypes.byref(o), fake,
+                              _null()) == _ffi.MDI_EINVAL
+    assert lib.mdi_lr_integrate_batched(fake, fake, 2, 2, fake, -1, ctypes.byref(o), fake, fake, 1 << 30,
+                                        _null()) == _ffi.MDI_EINVAL
+    assert lib.mdi_lr_integrate_batched(fake, fake, 2, -1, fake, 16, ctypes.byref(o), fake, fake, 1 << 30,
                                         _null()) == _ffi.MDI_EINVAL
 
 
@@ -306,7 +310,7 @@ def test_step_size_limits(lib):
     assert lib.mdi_lr_grad(2, 10, 16, 16, _null(), fake, ctypes.byref(o), fake, fake, fake, 1 << 30,
                            _null()) == _ffi.MDI_EUNSUPPORTED
     assert lib.mdi_lr_grad_workspace_size(2, 10, 16, 16, ctypes.byref(o), ctypes.byref(b)) == _ffi.MDI_EUNSUPPORTED
-    assert lib.mdi_lr_integrate_batched(fake, fake, 4, fake, 1 << 20, ctypes.byref(o), fake, fake, 1 << 30,
+    assert lib.mdi_lr_integrate_batched(fake, fake, 4, 4, fake, 1 << 20, ctypes.byref(o), fake, fake, 1 << 30,
                                         _null()) == _ffi.MDI_EUNSUPPORTED
     o.precision = _ffi.PRECISION["df64"]
     assert lib.mdi_lr_integrate(2, 10, 16, 16, _null(), fake, ctypes.byref(o), fake, fake, 1 << 30,

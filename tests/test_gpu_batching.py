@@ -169,3 +169,62 @@ def test_injected_faults_are_reported_not_run(precision):
     assert out[15] == 7.0
     np.testing.assert_array_equal(out[:15], good[:15])
     assert mdi.mdi_get_device_status(ws, clear=True) == F["bad_order"]
+
+
+def _oracle_values(b):
+    return np.array([o.mdi_nodes(it.family, it.d, it.a, it.n_last, 16, it.c, it.w)
+                     for it in (b.integral(i) for i in range(len(b)))])
+
+
+def test_hybrid_schedule_every_split():
+    """The hybrid schedule (FP64, two-warp CTAs, tables through L1): the order's
+    first `split` integrals on whole CTAs, the rest one per warp with a state of its
+    own.  Every split -- none, the planner's, a third, all -- gives every output
+    within 1e-12 of the oracle; the one-warp and two-warp sweeps add their cluster
+    sums in different orders, so values agree to rounding, not bit for bit."""
+    import paper_2404_08867_gb300 as mdi
+    b = inputs.batch(count=1500, seed=11)
+    plan = _plan(b, "fp64")
+    ref = _oracle_values(b)
+    assert 0 <= plan.hybrid_split <= len(b)
+    for split in sorted({0, plan.hybrid_split, len(b) // 3, len(b)}):
+        out = plan.launch(block=64, table_in_l1=1, split=split).cpu().numpy()
+        rel = np.abs(out - ref) / np.abs(ref)
+        assert rel.max() <= TOL, (split, rel.max())
+    assert mdi.mdi_get_device_status(plan.workspace) == 0
+
+
+def test_hybrid_graph_replay_and_bench_batch():
+    """The bench's batch (4096, seed 0) with the planner's split, captured and
+    replayed: equal to a direct launch, every output within 1e-12 of the oracle."""
+    b = inputs.batch(count=4096, seed=0)
+    plan = _plan(b, "fp64")
+    plan.opts.update(block=64, table_in_l1=1, split=plan.hybrid_split)
+    direct = plan.launch().clone()
+    plan.capture()
+    replay = plan.run().clone()
+    torch.cuda.synchronize()
+    assert torch.equal(direct, replay)
+    ref = _oracle_values(b)
+    assert (np.abs(replay.cpu().numpy() - ref) / np.abs(ref)).max() <= TOL
+
+
+def test_hybrid_rejects_what_a_warp_cannot_run():
+    """A one-warp team runs the FP64 paired sweep only: an oscillatory integral past
+    the split (which the planner never produces) is rejected with NaN and a flag,
+    and the others are unaffected."""
+    import paper_2404_08867_gb300 as mdi
+    F = mdi._ffi.DEV_FLAGS
+    b = inputs.batch(count=64, seed=12)
+    fams = list(b.families)
+    fams[-1] = "osc"
+    descs = mdi.make_batch_descs(fams, b.d, b.a, b.n_last, b.offsets)
+    pool = torch.as_tensor(b.pool).cuda()
+    ws = mdi.mdi_lr_batched_prepare(nodes=16, precision="fp64", block=64, table_in_l1=1)
+    out = mdi.mdi_lr_integrate_batched(_descs_dev(descs), pool, 64, split=0, workspace=ws, precision="fp64",
+                                       block=64, table_in_l1=1).cpu().numpy()
+    assert np.isnan(out[-1]) and np.all(np.isfinite(out[:-1]))
+    assert mdi.mdi_get_device_status(ws, clear=True) == F["bad_desc"]
+    whole = mdi.mdi_lr_integrate_batched(_descs_dev(descs), pool, 64, workspace=ws, precision="fp64", block=64,
+                                         table_in_l1=1).cpu().numpy()
+    assert np.all(np.isfinite(whole)) and mdi.mdi_get_device_status(ws) == 0

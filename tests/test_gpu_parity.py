@@ -285,7 +285,7 @@ def test_nodes_compensated_accumulation(fam, d, a):
 # ----------------------------------------------------------------------------
 def _batch_to_device(b):
     descs = mdi.make_batch_descs(b.families, b.d, b.a, b.n_last, b.offsets)
-    order = mdi.mdi_batch_plan(descs, b.pool.size)
+    order, _ = mdi.mdi_batch_plan(descs, b.pool.size)
     d_descs = torch.from_numpy(descs.view(np.uint8)).cuda()
     return descs, d_descs, torch.from_numpy(order).cuda(), dev(b.pool)
 
