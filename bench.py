@@ -535,8 +535,8 @@ def extra_time_to_1e6_vs_d(torch, mdi, inputs, dims=(4, 6, 8, 10, 12, 16, 20, 24
 # removed): after any change to their code the bench reports null until the capture
 # is repeated.
 TRAFFIC_SOURCES = ["paper_2404_08867_gb300/csrc/mdi_nodes.cu", "paper_2404_08867_gb300/csrc/mdi_nodes.cuh",
-                   "paper_2404_08867_gb300/csrc/mdi_common.cuh"]
-PROFILED_TRAFFIC = {"fp64": ("3bba43dfae0a8429", 1672960)}
+                   "paper_2404_08867_gb300/csrc/mdi_common.cuh", "paper_2404_08867_gb300/csrc/mdi_fp64.cuh"]
+PROFILED_TRAFFIC = {"fp64": ("4b6313f061116acc", 1722368)}
 
 
 def kernel_sources_key() -> str:

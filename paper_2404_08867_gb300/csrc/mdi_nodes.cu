@@ -80,10 +80,11 @@ template <typename V> __device__ __forceinline__ V team_sum(V v, V *scratch, con
   return r;
 }
 
-// Per-axis constants of a level: c, w, 1/c^2 in double and as float pairs.
+// Per-axis constants of a level: c, w, 1/c^2 in double and as float pairs; c w and
+// c (1 - w) for the FP64 sweep's affine arguments.
 struct LevelConst {
-  double c, w, ic2;
-  float4 cw;   // (c.hi, c.lo, w.hi, w.lo)
+  double c, w, ic2, cw, c1w;
+  float4 cwf;  // (c.hi, c.lo, w.hi, w.lo)
   float2 ic;   // 1/c^2 as a float pair
 };
 
@@ -281,7 +282,9 @@ __device__ __forceinline__ void make_level_const(const double *__restrict__ prm,
   }
   L.c = c;
   L.w = w;
-  L.cw = make_float4(cd.hi, cd.lo, wd.hi, wd.lo);
+  L.cw = c * w;
+  L.c1w = c * (1.0 - w);
+  L.cwf = make_float4(cd.hi, cd.lo, wd.hi, wd.lo);
   L.ic = make_float2(id.hi, id.lo);
 }
 
@@ -410,7 +413,7 @@ __device__ void last_level(NodesShared &sh, const void *__restrict__ Ftab, int P
     if (tabulated) {
       const df32 ia{sh.iadf.x, sh.iadf.y};
       df32 s1, s0;  // the last axis' points are s/a: no node offset
-      phi_affine_coeffs<FAM>(LL.cw, ia, df32{0.f, 0.f}, s1, s0);
+      phi_affine_coeffs<FAM>(LL.cwf, ia, df32{0.f, 0.f}, s1, s0);
       DfAcc acc;
       for (int s = tid; s < n_last; s += B) {
         const float2 *F = (const float2 *)Ftab + s;
@@ -564,7 +567,7 @@ __device__ void sweep_one(NodesShared &sh, const NodesConsts *__restrict__ kc, c
       const df32 ia{sh.iadf.x, sh.iadf.y}, xa{sh.xadf[p].x, sh.xadf[p].y};
       const AxisParams ap{L.c, L.w, L.ic2};
       df32 s1{0.f, 0.f}, s0{0.f, 0.f};
-      if constexpr (DF64) phi_affine_coeffs<FAM>(L.cw, ia, xa, s1, s0);
+      if constexpr (DF64) phi_affine_coeffs<FAM>(L.cwf, ia, xa, s1, s0);
       for (int q = qs; q < a; q += Q) {
         const int i = p * a + q;
         V f;
@@ -766,8 +769,8 @@ __device__ void sweep_paired(NodesShared &sh, const NodesConsts *__restrict__ kc
     } else if (act) {
       const df32 xa{sh.xadf[pp].x, sh.xadf[pp].y}, xb{sh.xadf[pb].x, sh.xadf[pb].y};
       df32 s1a, s0a, s1b, s0b;
-      phi_affine_coeffs<FAM>(L.cw, ia, xa, s1a, s0a);
-      phi_affine_coeffs<FAM>(L.cw, ia, xb, s1b, s0b);
+      phi_affine_coeffs<FAM>(L.cwf, ia, xa, s1a, s0a);
+      phi_affine_coeffs<FAM>(L.cwf, ia, xb, s1b, s0b);
       for (int q = qs; q < a; q += Q) {
         df32 ga{1.f, 0.f}, gb{1.f, 0.f};
         if (k > 1) {
@@ -849,6 +852,7 @@ __device__ void sweep_paired_fp64(NodesShared &sh, const NodesConsts *__restrict
   tm.sync();
   const double inv_a = 1.0 / (double)a, half_inv_a = 0.5 * inv_a;
   const double xa = sh.xi[pp], xb = sh.xi[pb];
+  const double x0 = xa * inv_a;  // xi_pp / a
   const float iaf = F32 ? kc->ia[a].x : 0.f, xaf = F32 ? sh.xadf[pp].x : 0.f, xbf = F32 ? sh.xadf[pb].x : 0.f;
 
   for (int k = 1; k < d; ++k) {
@@ -866,11 +870,10 @@ __device__ void sweep_paired_fp64(NodesShared &sh, const NodesConsts *__restrict
     //   EXP    t = c u
     double s1a = 0.0, s0a = 0.0, s1b = 0.0, s0b = 0.0;
     if constexpr (!F32) {
-      const double x0 = xa * inv_a;  // xi_pp / a
-      if constexpr (FAM == MDI_FAM_GAUSS) {
+      if constexpr (FAM == MDI_FAM_GAUSS) {  // c (x0 - w), c (x0 - (1 - w))
         s1a = s1b = L.c * inv_a;
-        s0a = L.c * (x0 - L.w);
-        s0b = L.c * (x0 - (1.0 - L.w));
+        s0a = fma(L.c, x0, -L.cw);
+        s0b = fma(L.c, x0, -L.c1w);
       } else if constexpr (FAM == MDI_FAM_PEAK) {
         s1a = s1b = inv_a;
         s0a = x0 - L.w;
