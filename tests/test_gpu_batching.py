@@ -228,3 +228,24 @@ def test_hybrid_rejects_what_a_warp_cannot_run():
     whole = mdi.mdi_lr_integrate_batched(_descs_dev(descs), pool, 64, workspace=ws, precision="fp64", block=64,
                                          table_in_l1=1).cpu().numpy()
     assert np.all(np.isfinite(whole)) and mdi.mdi_get_device_status(ws) == 0
+
+
+@pytest.mark.parametrize("P", [8, 12, 32])
+def test_hybrid_schedule_other_node_counts(P):
+    """The one-warp teams of the hybrid schedule with node counts other than the
+    unrolled P = 16 (8, 12 and 32 nodes: 4, 6 and 16 node pairs over 32 lanes)."""
+    import paper_2404_08867_gb300 as mdi
+    b = inputs.batch(count=300, seed=13)
+    descs = mdi.make_batch_descs(b.families, b.d, b.a, b.n_last, b.offsets)
+    order, split = mdi.mdi_batch_plan(descs, b.pool.size, nodes=P, precision="fp64", block=64, table_in_l1=1)
+    pool = torch.as_tensor(b.pool).cuda()
+    ws = mdi.mdi_lr_batched_prepare(nodes=P, precision="fp64", block=64, table_in_l1=1)
+    for sp in sorted({0, split, 150}):
+        out = mdi.mdi_lr_integrate_batched(_descs_dev(descs), pool, len(b), order=torch.from_numpy(order).cuda(),
+                                           split=sp, workspace=ws, nodes=P, precision="fp64", block=64,
+                                           table_in_l1=1).cpu().numpy()
+        for i in range(0, len(b), 7):
+            it = b.integral(i)
+            ref = o.mdi_nodes(it.family, it.d, it.a, it.n_last, P, it.c, it.w)
+            assert abs(out[i] - ref) <= TOL * abs(ref), (P, sp, i, out[i], ref)
+    assert mdi.mdi_get_device_status(ws) == 0
