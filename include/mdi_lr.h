@@ -331,9 +331,10 @@ mdi_status mdi_lr_batched_prepare(const mdi_opts *opts, void *workspace, size_t 
  *              swept by whole CTAs, later ones by single warps, each with a state
  *              of its own (so the largest integrals, which come first, finish
  *              sooner, and the rest run at the lane efficiency of one warp).  It is
- *              honoured for MDI_PREC_FP64 with 64-thread CTAs (opts->block = 64) and
- *              the tables read through L1 (opts->table_in_l1 = 1), and treated as
- *              count otherwise; split >= count means whole CTAs throughout
+ *              honoured with 64-thread CTAs (opts->block = 64) and the tables read
+ *              through L1 (opts->table_in_l1 = 1), and treated as count otherwise;
+ *              split >= count means whole CTAs throughout.  An oscillatory integral
+ *              past the split is rejected (NaN, MDI_DEV_BAD_DESC)
  *   param_pool DEVICE doubles
  *   pool_len   number of doubles in param_pool: descriptor i reads
  *              param_pool[param_offset, param_offset + 2 d), which must lie inside it
@@ -355,8 +356,8 @@ mdi_status mdi_lr_batched_workspace_size(int32_t count, const mdi_opts *opts, si
 /* Host-side scheduler: writes into order (HOST, count int32) a processing order
  * for mdi_lr_integrate_batched -- longest estimated work first, ties grouped by a
  * so that consecutive pick-ups share their interpolation table -- and into *split
- * (HOST, may be NULL) the hybrid schedule's split for these opts: for FP64 batches
- * of real families with opts->block = 64 and tables through L1 it simulates the
+ * (HOST, may be NULL) the hybrid schedule's split for these opts: for batches of
+ * real families with opts->block = 64 and tables through L1 it simulates the
  * persistent launch (the resident CTAs of this GPU taking the order, a modelled
  * time per integral for one- and two-warp teams) for 41 splits and keeps the
  * shortest, otherwise count.  descs is a HOST copy of the descriptor table;

@@ -327,8 +327,10 @@ mdi_status mdi_get_device_status(const void *workspace, size_t ws_bytes, int32_t
   return word ? MDI_EINVAL : MDI_OK;
 }
 
-// Time of one node-state integral on a team of `warps` warps (1 or 2) of the FP64
-// paired sweep, in units of one FP64 warp instruction: each of the d-1 cluster
+// Time of one node-state integral on a team of `warps` warps (1 or 2) of the paired
+// sweep, in units of one FP64 warp instruction of the FP64 sweep (the other
+// precisions' sweeps have the same passes and are scheduled with the same model):
+// each of the d-1 cluster
 // levels takes ceil(a / lanes_per_pair) passes (8 node pairs share the team's
 // lanes), a pass costs each warp the interpolation of one point pair (P/2 fused
 // multiply-adds for each of the pair's two sums, their sum and difference, two
@@ -396,7 +398,7 @@ mdi_status mdi_batch_plan(const mdi_batch_desc *descs, int32_t count, int64_t po
   std::memcpy(order, idx.data(), sizeof(int32_t) * (size_t)count);
   if (split) {
     *split = count;  // whole CTAs throughout unless the hybrid schedule applies and pays
-    if (all_real && cfg.precision == MDI_PREC_FP64 && cfg.block == 2 * kWarp && !cfg.stage) {
+    if (all_real && cfg.block == 2 * kWarp && !cfg.stage) {
       std::vector<double> t1((size_t)count), t2((size_t)count);
       for (int32_t i = 0; i < count; ++i) {
         t1[(size_t)i] = team_time(descs[i], P, 1);

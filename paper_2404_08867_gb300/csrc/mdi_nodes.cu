@@ -18,7 +18,7 @@
 // against the basis table L_a[t][p*a + q] = l_t(u_qp), contiguous in q), multiplies
 // by phi_k and accumulates; the Q lanes add their sums with shuffles and one lane
 // writes G_k[p] into the other half of a double-buffered state, so a level costs
-// one barrier.  The constants of 64 levels at a time are prepared by all threads
+// one barrier.  The constants of 32 levels at a time are prepared by all threads
 // together.  The basis tables depend only on (a, P) and are built once per workspace
 // (mdi_lr_batched_prepare) for a = 1..64, together with the basis at the last
 // axis' points s/a (used when n_last = a).  A CTA may stage its table in shared
@@ -52,7 +52,7 @@ namespace mdi {
 constexpr int kNodesMaxBlock = 512;
 constexpr int kNodesSmemTable = 64 * 1024;  // table bytes staged in shared memory
 
-constexpr int kLvChunk = 64;  // levels whose constants are held in shared memory at once
+constexpr int kLvChunk = 32;  // levels whose constants are held in shared memory at once
 
 // The threads sweeping one integral: the whole CTA, or one warp of it (the second
 // phase of the hybrid schedule, where each warp of a two-warp CTA takes integrals
@@ -83,9 +83,9 @@ template <typename V> __device__ __forceinline__ V team_sum(V v, V *scratch, con
 // Per-axis constants of a level: c, w, 1/c^2 in double and as float pairs; c w and
 // c (1 - w) for the FP64 sweep's affine arguments.
 struct LevelConst {
-  double c, w, ic2, cw, c1w;
   float4 cwf;  // (c.hi, c.lo, w.hi, w.lo)
   float2 ic;   // 1/c^2 as a float pair
+  double c, w, ic2, cw, c1w;
 };
 
 // Fixed part of the dynamic shared memory; the staged table (if any) follows it.
@@ -101,7 +101,7 @@ struct NodesShared {
     double exp2d[kExpTable];    // 2^(j/256) as doubles (FP64 exp)
   };
   double qd[kNodesAMax];      // q as a double, q < 64 (FP64)
-  LevelConst lc[kLvChunk];    // constants of axes base .. base+63
+  LevelConst lc[kLvChunk];    // constants of axes base .. base+kLvChunk-1
   float2 iadf;                // 1/a as a float pair (DF64)
   int inst;
   int pad;
@@ -358,6 +358,17 @@ __device__ __forceinline__ float4 block_sum_df(df32 re, df32 im, float4 *scratch
   return r;
 }
 
+// Sum of double-float pairs (re, im) over a team; result valid in its thread 0.
+__device__ __forceinline__ float4 team_sum_df(df32 re, df32 im, float4 *scratch, const Team &tm) {
+  if (tm.size > kWarp) return block_sum_df(re, im, scratch);
+#pragma unroll
+  for (int off = kWarp / 2; off > 0; off >>= 1) {
+    re = df_add(re, df_shfl_down(re, off));
+    im = df_add(im, df_shfl_down(im, off));
+  }
+  return make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
 // Sums over aligned groups of Q lanes (Q a power of two <= 32), valid in every lane.
 __device__ __forceinline__ double2 lanes_sum(double2 v, int Q) {
   for (int off = 1; off < Q; off <<= 1) {
@@ -426,9 +437,9 @@ __device__ void last_level(NodesShared &sh, const void *__restrict__ Ftab, int P
         }
         dacc_prod(acc, phi_df_affine<FAM>(s1, s0, (float)s, LL.ic, sh.exp2tab), dacc_value(ag));
       }
-      const float4 tot = block_sum_df(dacc_value(acc), df32{0.f, 0.f}, sh.redf);
+      const float4 tot = team_sum_df(dacc_value(acc), df32{0.f, 0.f}, sh.redf, tm);
       if (tid == 0) *out_slot = ((double)tot.x + (double)tot.y) / (double)n_last;
-      __syncthreads();
+      tm.sync();
       return;
     }
   }
@@ -719,9 +730,10 @@ __device__ __forceinline__ void dacc_prod_f(DfAcc &a, float f, df32 g) {
 template <int FAM, int H, int PREC = MDI_PREC_DF64>
 __device__ void sweep_paired(NodesShared &sh, const NodesConsts *__restrict__ kc, const float4 *__restrict__ Lpm,
                              const void *__restrict__ Ftab, int P, int d, int a, int n_last,
-                             const double *__restrict__ prm, double *__restrict__ out_slot) {
+                             const double *__restrict__ prm, double *__restrict__ out_slot,
+                             const Team &tm = Team::block()) {
   const int h = H > 0 ? H : P / 2;
-  const int tid = threadIdx.x, B = blockDim.x;
+  const int tid = tm.tid, B = tm.size;
   const int Q = node_lanes(B, h);
   const int pp = min(tid / Q, h - 1), pb = P - 1 - pp, qs = tid % Q;
   const bool act = tid < h * Q;
@@ -731,8 +743,8 @@ __device__ void sweep_paired(NodesShared &sh, const NodesConsts *__restrict__ kc
   if (tid < h) sh.Gdf[0][tid] = make_float4(1.f, 0.f, 0.f, 0.f);  // G_0 = 1: E = 1, O = 0
   if (tid < P) sh.xadf[tid] = kc->xa[a][tid];
   if (tid == 0) sh.iadf = kc->ia[a];
-  load_level_chunk<!F32>(sh.lc, prm, d, 0);
-  __syncthreads();
+  load_level_chunk<!F32>(sh.lc, prm, d, 0, tm);
+  tm.sync();
   const df32 ia{sh.iadf.x, sh.iadf.y};
   const df32 ia2{0.5f * ia.hi, 0.5f * ia.lo};  // 1/(2a), exact halving
   // The stored state is G 2^-S: each level rescales its output by 2^-s, s the
@@ -744,8 +756,8 @@ __device__ void sweep_paired(NodesShared &sh, const NodesConsts *__restrict__ kc
   for (int k = 1; k < d; ++k) {
     const int j = k - 1;
     if (j > 0 && j % kLvChunk == 0) {
-      load_level_chunk<!F32>(sh.lc, prm, d, j);
-      __syncthreads();
+      load_level_chunk<!F32>(sh.lc, prm, d, j, tm);
+      tm.sync();
     }
     const LevelConst &L = sh.lc[j % kLvChunk];
     const int rb = (k - 1) & 1, wb = k & 1;
@@ -803,7 +815,7 @@ __device__ void sweep_paired(NodesShared &sh, const NodesConsts *__restrict__ kc
         sh.Gdf[wb][pp] = make_float4(E.hi, E.lo, O.hi, O.lo);
       }
     }
-    __syncthreads();
+    tm.sync();
   }
   // G_{d-1} from (E, O) into the other buffer, then the common last level.
   const int eb = (d - 1) & 1, gbuf = eb ^ 1;
@@ -815,8 +827,8 @@ __device__ void sweep_paired(NodesShared &sh, const NodesConsts *__restrict__ kc
     sh.Gdf[gbuf][tid] = make_float4(v.hi, v.lo, 0.f, 0.f);
     if constexpr (F32) sh.G[gbuf][tid] = make_double2(df_to_double(v), 0.0);  // its last level reads doubles
   }
-  __syncthreads();
-  last_level<FAM, PREC>(sh, Ftab, P, d, a, n_last, prm, out_slot, gbuf);
+  tm.sync();
+  last_level<FAM, PREC>(sh, Ftab, P, d, a, n_last, prm, out_slot, gbuf, tm);
   if (tid == 0 && S != 0) *out_slot = scale_pow2(*out_slot, S);  // the thread that wrote it
 }
 
@@ -943,25 +955,26 @@ __device__ void sweep_paired_fp64(NodesShared &sh, const NodesConsts *__restrict
 template <int PREC, int H, int FAM>
 __device__ __forceinline__ void paired_one(NodesShared &sh, const NodesConsts *__restrict__ kc, const void *C,
                                            const void *Ftab, int P, int d, int a, int n_last,
-                                           const double *__restrict__ prm, double *out_slot) {
+                                           const double *__restrict__ prm, double *out_slot, const Team &tm) {
   if constexpr (PREC == MDI_PREC_FP32_EVAL_DF32)
-    sweep_paired<FAM, H, PREC>(sh, kc, (const float4 *)C, Ftab, P, d, a, n_last, prm, out_slot);
+    sweep_paired<FAM, H, PREC>(sh, kc, (const float4 *)C, Ftab, P, d, a, n_last, prm, out_slot, tm);
   else
-    sweep_paired_fp64<FAM, H, true>(sh, kc, (const double2 *)C, Ftab, P, d, a, n_last, prm, out_slot);
+    sweep_paired_fp64<FAM, H, true>(sh, kc, (const double2 *)C, Ftab, P, d, a, n_last, prm, out_slot, tm);
 }
 template <int PREC, int H>
 __device__ __forceinline__ void run_paired(NodesShared &sh, const NodesConsts *__restrict__ kc, const void *C,
                                            const void *Ftab, int P, int family, int d, int a, int n_last,
-                                           const double *__restrict__ prm, double *out_slot) {
-  if (family == MDI_FAM_EXP) paired_one<PREC, H, MDI_FAM_EXP>(sh, kc, C, Ftab, P, d, a, n_last, prm, out_slot);
-  else if (family == MDI_FAM_GAUSS) paired_one<PREC, H, MDI_FAM_GAUSS>(sh, kc, C, Ftab, P, d, a, n_last, prm, out_slot);
-  else paired_one<PREC, H, MDI_FAM_PEAK>(sh, kc, C, Ftab, P, d, a, n_last, prm, out_slot);
+                                           const double *__restrict__ prm, double *out_slot, const Team &tm) {
+  if (family == MDI_FAM_EXP) paired_one<PREC, H, MDI_FAM_EXP>(sh, kc, C, Ftab, P, d, a, n_last, prm, out_slot, tm);
+  else if (family == MDI_FAM_GAUSS)
+    paired_one<PREC, H, MDI_FAM_GAUSS>(sh, kc, C, Ftab, P, d, a, n_last, prm, out_slot, tm);
+  else paired_one<PREC, H, MDI_FAM_PEAK>(sh, kc, C, Ftab, P, d, a, n_last, prm, out_slot, tm);
 }
 
 // One work item of the batched kernel: order slot `slot`, swept by team `tm` with
 // state `sh`.  `whole` says the team is the whole CTA (which may stage the basis
 // table in shared memory and runs every family); a one-warp team of the hybrid
-// schedule runs the FP64 paired sweep of the real families only.
+// schedule runs the paired sweeps of the real families only.
 template <int PREC>
 __device__ __forceinline__ void nodes_item(int slot, const Team &tm, bool whole, NodesShared &sh,
                                            unsigned char *tab_smem, int &staged_a,
@@ -1035,20 +1048,22 @@ __device__ __forceinline__ void nodes_item(int slot, const Team &tm, bool whole,
     } else if constexpr (PREC == MDI_PREC_DF64) {
       const float4 *Lpm = (const float4 *)C;
       if (P == 16) {
-        if (ds.family == MDI_FAM_EXP) sweep_paired<MDI_FAM_EXP, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot);
+        if (ds.family == MDI_FAM_EXP)
+          sweep_paired<MDI_FAM_EXP, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot, tm);
         else if (ds.family == MDI_FAM_GAUSS)
-          sweep_paired<MDI_FAM_GAUSS, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot);
-        else sweep_paired<MDI_FAM_PEAK, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot);
+          sweep_paired<MDI_FAM_GAUSS, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot, tm);
+        else sweep_paired<MDI_FAM_PEAK, 8>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot, tm);
       } else {
-        if (ds.family == MDI_FAM_EXP) sweep_paired<MDI_FAM_EXP, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot);
+        if (ds.family == MDI_FAM_EXP)
+          sweep_paired<MDI_FAM_EXP, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot, tm);
         else if (ds.family == MDI_FAM_GAUSS)
-          sweep_paired<MDI_FAM_GAUSS, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot);
-        else sweep_paired<MDI_FAM_PEAK, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot);
+          sweep_paired<MDI_FAM_GAUSS, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot, tm);
+        else sweep_paired<MDI_FAM_PEAK, 0>(sh, kc, Lpm, Ftab, P, ds.d, a, ds.n_last, prm, out_slot, tm);
       }
     } else if (P == 16) {
-      run_paired<PREC, 8>(sh, kc, C, Ftab, P, ds.family, ds.d, a, ds.n_last, prm, out_slot);
+      run_paired<PREC, 8>(sh, kc, C, Ftab, P, ds.family, ds.d, a, ds.n_last, prm, out_slot, tm);
     } else {
-      run_paired<PREC, 0>(sh, kc, C, Ftab, P, ds.family, ds.d, a, ds.n_last, prm, out_slot);
+      run_paired<PREC, 0>(sh, kc, C, Ftab, P, ds.family, ds.d, a, ds.n_last, prm, out_slot, tm);
     }
     return;
   }
@@ -1061,10 +1076,10 @@ __device__ __forceinline__ void nodes_item(int slot, const Team &tm, bool whole,
 }
 
 // Persistent batched kernel.  Order slots below `split` are swept by the whole
-// CTA; from the first slot at or past it (hybrid schedule, FP64 with two-warp
-// CTAs and the tables read through L1 only) each warp takes slots of its own,
-// with its own copy of the state (the second NodesShared).  split >= count: every
-// slot by the whole CTA.
+// CTA; from the first slot at or past it (hybrid schedule: two-warp CTAs with the
+// tables read through L1) each warp takes slots of its own, with its own copy of
+// the state (the second NodesShared).  split >= count: every slot by the whole
+// CTA.
 template <int PREC>
 __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi_batch_desc *__restrict__ descs,
                                                                        const int32_t *__restrict__ order, int count,
@@ -1110,7 +1125,7 @@ __global__ void __launch_bounds__(kNodesMaxBlock) nodes_batched_kernel(const mdi
                      tables, paired, kc, P, stage, out, counter, prepared);
   }
   if (slot < count) {  // hybrid: slot is the first one past the split; warp 0 takes it
-    if constexpr (PREC == MDI_PREC_FP64) {
+    {
       const int warp = threadIdx.x / kWarp, lane = threadIdx.x & (kWarp - 1);
       NodesShared &shw = warp == 0 ? sh : sh2;
       const Team tm{lane, kWarp};
@@ -1233,11 +1248,9 @@ mdi_status nodes_prepare(const NodesConfig &cfg, void *workspace, size_t ws_byte
   return check_launch();
 }
 
-// The hybrid schedule needs two-warp CTAs reading their tables through L1, and the
-// FP64 paired sweep (the only one written for a one-warp team).
-static bool hybrid_ok(const NodesConfig &cfg) {
-  return cfg.precision == MDI_PREC_FP64 && cfg.block == 2 * kWarp && !cfg.stage;
-}
+// The hybrid schedule needs two-warp CTAs reading their tables through L1 (its
+// one-warp teams run the paired sweeps of every precision).
+static bool hybrid_ok(const NodesConfig &cfg) { return cfg.block == 2 * kWarp && !cfg.stage; }
 
 template <int PREC>
 static int resident_ctas(const NodesConfig &cfg, size_t smem, bool hybrid) {

@@ -5,10 +5,11 @@ order from the library's longest-first planner, parameter pool -- three views of
 one packed device buffer, so that a new batch of the same shape arrives in one
 host-to-device copy of ``host_inputs()``), a prepared workspace, and the launch
 shape.  ``tune()`` times the candidate shapes -- CTA size, whether each
-integral's basis table is staged in shared memory or read through L1, and (FP64)
-the planner's hybrid schedule on two-warp CTAs, whose largest integrals run on
-whole CTAs and the rest one per warp -- on the batch itself with CUDA events and
-keeps the fastest (cached per batch signature for the process).  ``capture()`` records the one-kernel
+integral's basis table is staged in shared memory or read through L1, and the
+planner's hybrid schedule on two-warp CTAs (its split and a few multiples of it),
+whose largest integrals run on whole CTAs and the rest one per warp -- on the
+batch itself with CUDA events and keeps the fastest (cached per batch signature
+for the process).  ``capture()`` records the one-kernel
 launch into a CUDA graph; ``run()`` replays it.  Nothing here computes: every
 launch goes through the C ABI.
 """
@@ -133,8 +134,11 @@ class BatchedMDILR:
                     results[(block, l1, self.count)] = self._time(reps, flush=flush, block=block, table_in_l1=l1,
                                                                   split=self.count)
             if self.hybrid_split < self.count:
-                results[(64, 1, self.hybrid_split)] = self._time(reps, flush=flush, block=64, table_in_l1=1,
-                                                                 split=self.hybrid_split)
+                # the planner's split (from a cost model of the FP64 sweep) and a few
+                # multiples of it, timed like the fixed shapes
+                splits = {min(self.count, int(self.hybrid_split * f)) for f in (0.25, 0.5, 1.0, 2.0, 4.0)}
+                for sp in sorted(splits):
+                    results[(64, 1, sp)] = self._time(reps, flush=flush, block=64, table_in_l1=1, split=sp)
             (block, l1, split), best = min(results.items(), key=lambda kv: kv[1])
             _cache[key] = {"block": block, "table_in_l1": l1, "split": split, "ms": best,
                            "candidates": {f"block={b},table_in_l1={t},split={sp}": ms

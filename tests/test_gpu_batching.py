@@ -176,21 +176,24 @@ def _oracle_values(b):
                      for it in (b.integral(i) for i in range(len(b)))])
 
 
-def test_hybrid_schedule_every_split():
-    """The hybrid schedule (FP64, two-warp CTAs, tables through L1): the order's
-    first `split` integrals on whole CTAs, the rest one per warp with a state of its
-    own.  Every split -- none, the planner's, a third, all -- gives every output
-    within 1e-12 of the oracle; the one-warp and two-warp sweeps add their cluster
-    sums in different orders, so values agree to rounding, not bit for bit."""
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL), ("df64", TOL), ("fp32_eval_df32", 2e-5),
+                                           ("fp32_eval_fp64", 2e-5)])
+def test_hybrid_schedule_every_split(precision, tol):
+    """The hybrid schedule (two-warp CTAs, tables through L1): the order's first
+    `split` integrals on whole CTAs, the rest one per warp with a state of its own,
+    in every precision's paired sweep.  Every split -- none, the planner's, a third,
+    all -- gives every output within the mode's tolerance of the oracle; the
+    one-warp and two-warp sweeps add their cluster sums in different orders, so
+    values agree to rounding, not bit for bit."""
     import paper_2404_08867_gb300 as mdi
     b = inputs.batch(count=1500, seed=11)
-    plan = _plan(b, "fp64")
+    plan = _plan(b, precision)
     ref = _oracle_values(b)
     assert 0 <= plan.hybrid_split <= len(b)
     for split in sorted({0, plan.hybrid_split, len(b) // 3, len(b)}):
         out = plan.launch(block=64, table_in_l1=1, split=split).cpu().numpy()
         rel = np.abs(out - ref) / np.abs(ref)
-        assert rel.max() <= TOL, (split, rel.max())
+        assert rel.max() <= tol, (split, rel.max())
     assert mdi.mdi_get_device_status(plan.workspace) == 0
 
 
