@@ -101,3 +101,18 @@ def test_algorithmic_flop_count():
     expect = 3 * 5 * (P * bench.C_PHI["gauss"] + P * P) + 7 * 20 * (P * bench.C_PHI["peak"] + P * P)
     assert bench.alg_flops(b) == expect
     assert bench.C_PHI["gauss"] == bench.C_PHI["peak"] == 25
+
+
+def test_reference_arm_prints_one_line():
+    """bench.py --impl reference: the CPU oracle on the host cores (spawned pool),
+    one pass over the batch per step, one JSON line with the contract's keys."""
+    import json
+    import subprocess
+    import sys
+    res = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                          "--warmup", "1", "--count", "48"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert res.returncode == 0, res.stderr
+    line = json.loads(res.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "integrals/s" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["steps"] == 2 and line["dtype"] == "f64"
