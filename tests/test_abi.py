@@ -315,3 +315,19 @@ def test_step_size_limits(lib):
     o.precision = _ffi.PRECISION["df64"]
     assert lib.mdi_lr_integrate(2, 10, 16, 16, _null(), fake, ctypes.byref(o), fake, fake, 1 << 30,
                                 _null()) == _ffi.MDI_EUNSUPPORTED
+
+
+def test_batch_plan_split_rules(lib):
+    """The planner's hybrid split: count unless the batch is all real families, with
+    64-thread CTAs reading their tables through L1; otherwise within [0, count]."""
+    rng = np.random.default_rng(3)
+    n = 300
+    a = rng.integers(8, 33, n)
+    fams = ["gauss", "peak"] * (n // 2)
+    descs = mdi.make_batch_descs(fams, rng.integers(6, 21, n), a, a, np.arange(n) * 40)
+    _, split = mdi.mdi_batch_plan(descs, 40 * n, block=64, table_in_l1=1)
+    assert 0 <= split <= n
+    assert mdi.mdi_batch_plan(descs, 40 * n, block=64, table_in_l1=0)[1] == n
+    assert mdi.mdi_batch_plan(descs, 40 * n, block=128, table_in_l1=1)[1] == n
+    osc = mdi.make_batch_descs(["osc"] + fams[1:], rng.integers(6, 21, n), a, a, np.arange(n) * 40)
+    assert mdi.mdi_batch_plan(osc, 40 * n, block=64, table_in_l1=1)[1] == n

@@ -252,3 +252,28 @@ def test_hybrid_schedule_other_node_counts(P):
             ref = o.mdi_nodes(it.family, it.d, it.a, it.n_last, P, it.c, it.w)
             assert abs(out[i] - ref) <= TOL * abs(ref), (P, sp, i, out[i], ref)
     assert mdi.mdi_get_device_status(ws) == 0
+
+
+@pytest.mark.parametrize("precision,big_tol", [("fp64", 1e-11), ("df64", 5e-10)])
+def test_batched_maximum_dimension(precision, big_tol):
+    """The batched kernel's largest dimension, d = 65536 (65535 cluster levels in one
+    CTA), next to small integrals, on whole CTAs and on the hybrid schedule's warps.
+    Rounding accumulates over the levels, at most about d u relative with u the
+    arithmetic's unit roundoff, so this case is held to 1e-11 in FP64 (d 2^-53 =
+    7.3e-12) and 5e-10 in double-float (d 2^-47 = 4.7e-10); the small ones to the
+    usual 1e-12."""
+    import paper_2404_08867_gb300 as mdi
+    dmax = 65536
+    big = inputs.random_product("gauss", dmax, seed=3, c_range=(0.05, 0.3))
+    small = inputs.random_product("peak", 7, seed=4)
+    pool = np.concatenate([big, small, small])
+    descs = mdi.make_batch_descs(["gauss", "peak", "peak"], [dmax, 7, 7], [2, 9, 9], [3, 9, 9],
+                                 [0, 2 * dmax, 2 * dmax + 14])
+    ref_big = o.mdi_nodes("gauss", dmax, 2, 3, 16, big[:dmax], big[dmax:])
+    ref_small = o.mdi_nodes("peak", 7, 9, 9, 16, small[:7], small[7:])
+    for split in (3, 1, 0):
+        out = mdi.mdi_lr_integrate_batched(_descs_dev(descs), torch.as_tensor(pool).cuda(), 3, split=split,
+                                           precision=precision, block=64, table_in_l1=1).cpu().numpy()
+        assert abs(out[0] - ref_big) <= big_tol * abs(ref_big), (split, out[0], ref_big)
+        for v in out[1:]:
+            assert abs(v - ref_small) <= TOL * abs(ref_small), (split, v, ref_small)
