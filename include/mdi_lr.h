@@ -357,10 +357,12 @@ mdi_status mdi_lr_batched_workspace_size(int32_t count, const mdi_opts *opts, si
  * for mdi_lr_integrate_batched -- longest estimated work first, ties grouped by a
  * so that consecutive pick-ups share their interpolation table -- and into *split
  * (HOST, may be NULL) the hybrid schedule's split for these opts: for batches of
- * real families with opts->block = 64 and tables through L1 it simulates the
- * persistent launch (the resident CTAs of this GPU taking the order, a modelled
- * time per integral for one- and two-warp teams) for 41 splits and keeps the
- * shortest, otherwise count.  descs is a HOST copy of the descriptor table;
+ * real families with opts->block = 64 and tables through L1 the work is a
+ * modelled time per integral for one- and two-warp teams (passes per level, the
+ * precision's phi), the order is by the one-warp time, and the planner simulates
+ * the persistent launch (the resident CTAs of this GPU taking the order) for 41
+ * splits and keeps the shortest; otherwise the work is an operation count and
+ * the split is count.  descs is a HOST copy of the descriptor table;
  * pool_len the number of doubles of the parameter pool the batch will read.
  * Returns MDI_EINVAL on an invalid descriptor or one whose 2*d parameters leave
  * the pool. */

@@ -336,11 +336,17 @@ mdi_status mdi_get_device_status(const void *workspace, size_t ws_bytes, int32_t
 // multiply-adds for each of the pair's two sums, their sum and difference, two
 // accumulations) and two evaluations of phi; the first level has no
 // interpolation; each level adds its constants and sums; the last axis is small.
-static double team_time(const mdi_batch_desc &d, int P, int warps) {
+// The FP64 sweep steps a Gaussian's factors by a recurrence when a lane has at
+// least three points (two multiplies per factor after five exps per level; the
+// model takes its argument guard as met).
+static double team_time(const mdi_batch_desc &d, int P, int warps, bool fp64) {
   const double phi = d.family == MDI_FAM_PEAK ? 5.0 : 12.0;  // FP64 operations of one phi
-  const double pair = (double)P + 4.0 + 2.0 * phi, first = 2.0 + 2.0 * phi, level = 10.0;
   const int lanes_per_pair = 4 * warps;
   const double passes = std::ceil((double)d.a / lanes_per_pair);
+  const bool rec = fp64 && d.family == MDI_FAM_GAUSS && passes >= 3.0;
+  const double pphi = rec ? 2.0 : phi;
+  const double pair = (double)P + 4.0 + 2.0 * pphi, first = 2.0 + 2.0 * pphi;
+  const double level = 10.0 + (rec ? 5.0 * phi + 8.0 : 0.0);
   const double last = std::ceil((double)d.n_last / (kWarp * warps)) * ((double)P + phi);
   if (d.d < 2) return last;
   return (double)(d.d - 2) * (passes * pair + level) + passes * first + level + last;
@@ -388,6 +394,21 @@ mdi_status mdi_batch_plan(const mdi_batch_desc *descs, int32_t count, int64_t po
     cost[(size_t)i] = nodes_cost(descs[i], P);
     all_real = all_real && descs[i].family != MDI_FAM_OSC;
   }
+  // The hybrid schedule's launches order by the modelled time of a one-warp team
+  // (which knows the passes per level and the FP64 sweep's Gaussian recurrence);
+  // the rest by the estimated operations.
+  const bool hybrid = all_real && cfg.block == 2 * kWarp && !cfg.stage;
+  const bool fp64 = cfg.precision == MDI_PREC_FP64;
+  std::vector<double> t1, t2;
+  if (hybrid) {
+    t1.resize((size_t)count);
+    t2.resize((size_t)count);
+    for (int32_t i = 0; i < count; ++i) {
+      t1[(size_t)i] = team_time(descs[i], P, 1, fp64);
+      t2[(size_t)i] = team_time(descs[i], P, 2, fp64);
+      cost[(size_t)i] = t1[(size_t)i];
+    }
+  }
   std::vector<int32_t> idx((size_t)count);
   std::iota(idx.begin(), idx.end(), 0);
   // Longest processing time first; equal costs grouped by a, then by index.
@@ -398,12 +419,7 @@ mdi_status mdi_batch_plan(const mdi_batch_desc *descs, int32_t count, int64_t po
   std::memcpy(order, idx.data(), sizeof(int32_t) * (size_t)count);
   if (split) {
     *split = count;  // whole CTAs throughout unless the hybrid schedule applies and pays
-    if (all_real && cfg.block == 2 * kWarp && !cfg.stage) {
-      std::vector<double> t1((size_t)count), t2((size_t)count);
-      for (int32_t i = 0; i < count; ++i) {
-        t1[(size_t)i] = team_time(descs[i], P, 1);
-        t2[(size_t)i] = team_time(descs[i], P, 2);
-      }
+    if (hybrid) {
       const int ctas = std::max(1, nodes_workers(cfg));
       double best = hybrid_makespan(t2, t1, idx, count, ctas);
       for (int k = 0; k < 40; ++k) {

@@ -897,6 +897,33 @@ __device__ void sweep_paired_fp64(NodesShared &sh, const NodesConsts *__restrict
         s0b = L.c - s0a;
       }
     }
+    // Gaussian factors along a lane's points q = qs, qs + Q, ...: t steps by
+    // dq = s1 Q, so phi(q + Q) = phi(q) rho(q) and rho(q + Q) = rho(q) kappa with
+    // rho(q) = exp(-(2 t dq + dq^2)) and kappa = exp(-2 dq^2) -- two multiplies per
+    // point after five exps per lane and level, against an exp per point.  Taken
+    // when every lane of the warp has at least three points and the arguments stay
+    // moderate (|t| < 20, |2 t dq + dq^2| < 500: no factor leaves the normal range),
+    // the same choice for the whole warp.  The k-th factor's relative error is the
+    // rounding of the arguments carried along, about (t0^2 + k |2 t0 dq| + k^2 dq^2)
+    // ulps -- the size of the direct exp's own argument rounding, t_k^2 ulps -- plus
+    // about 2k ulps of products.
+    bool rec = false;
+    double fa = 0.0, fb = 0.0, rho_a = 0.0, rho_b = 0.0, kap = 0.0;
+    if constexpr (FAM == MDI_FAM_GAUSS && !F32) {
+      const double dq = s1a * (double)Q;
+      const double tmax = fmax(fabs(s0a), fabs(s0b)) + fabs(s1a) * (double)a;
+      const bool ok = !act || (tmax < 20.0 && fabs(dq) * (2.0 * tmax + fabs(dq)) < 500.0);
+      rec = (a + Q - 1) / Q >= 3 && __all_sync(0xffffffffu, ok);
+      if (rec && act) {
+        const double qd0 = sh.qd[qs];
+        const double ta = fma(s1a, qd0, s0a), tb = fma(s1b, qd0, s0b);
+        fa = exp_tang64(-(ta * ta), sh.exp2d);
+        fb = exp_tang64(-(tb * tb), sh.exp2d);
+        rho_a = exp_tang64(-fma(2.0 * ta, dq, dq * dq), sh.exp2d);
+        rho_b = exp_tang64(-fma(2.0 * tb, dq, dq * dq), sh.exp2d);
+        kap = exp_tang64(-2.0 * dq * dq, sh.exp2d);
+      }
+    }
     double acc_a = 0.0, acc_b = 0.0;
     if (act) {
       for (int q = qs; q < a; q += Q) {
@@ -926,6 +953,13 @@ __device__ void sweep_paired_fp64(NodesShared &sh, const NodesConsts *__restrict
           const AxisF af{(float)L.c, (float)L.w, (float)L.ic2};
           acc_a = fma((double)phi_f<FAM>(fmaf((float)q, iaf, xaf), af), ga, acc_a);
           acc_b = fma((double)phi_f<FAM>(fmaf((float)(a - 1 - q), iaf, xbf), af), gb, acc_b);
+        } else if (FAM == MDI_FAM_GAUSS && rec) {
+          acc_a = fma(fa, ga, acc_a);
+          acc_b = fma(fb, gb, acc_b);
+          fa *= rho_a;
+          rho_a *= kap;
+          fb *= rho_b;
+          rho_b *= kap;
         } else {
           // The arguments of both mirrored points are affine in q (u_b = 1 - u_a).
           const double qd = sh.qd[q];

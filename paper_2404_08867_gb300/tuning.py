@@ -37,8 +37,9 @@ class BatchedMDILR:
         self.descs_host = descs
         pool_t = pool if isinstance(pool, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(pool))
         pool_t = pool_t.to(dtype=torch.float64).contiguous().cpu()
-        # The order does not depend on the launch shape; the hybrid split is the
-        # planner's for two-warp CTAs reading their tables through L1.
+        # One order for every candidate shape: the planner's for two-warp CTAs
+        # reading their tables through L1 (longest modelled team time first), with
+        # the hybrid schedule's split.
         order, self.hybrid_split = mdi_batch_plan(descs, pool_t.numel(), nodes=nodes, precision=precision, block=64,
                                                   table_in_l1=1)
         # Packed inputs: descriptors | order | pool, each 256-byte aligned.

@@ -331,3 +331,22 @@ def test_batch_plan_split_rules(lib):
     assert mdi.mdi_batch_plan(descs, 40 * n, block=128, table_in_l1=1)[1] == n
     osc = mdi.make_batch_descs(["osc"] + fams[1:], rng.integers(6, 21, n), a, a, np.arange(n) * 40)
     assert mdi.mdi_batch_plan(osc, 40 * n, block=64, table_in_l1=1)[1] == n
+
+
+def test_batch_plan_hybrid_order_is_longest_modelled_first(lib):
+    """With the hybrid schedule's opts (64-thread CTAs, tables through L1) the order
+    is a permutation that puts the longest integrals first: for one family with
+    n_last = a, the work of a one-warp team grows with the levels and the passes
+    per level, ceil(a / 4) (8 node pairs x 4 lanes)."""
+    rng = np.random.default_rng(2)
+    n = 600
+    a = rng.integers(8, 33, n)
+    d = rng.integers(6, 21, n)
+    descs = mdi.make_batch_descs(["peak"] * n, d, a, a, np.arange(n) * 40)
+    order, split = mdi.mdi_batch_plan(descs, 40 * n, block=64, table_in_l1=1, precision="fp64")
+    assert sorted(order.tolist()) == list(range(n))
+    assert 0 <= split <= n
+    work = (descs["d"][order] - 1) * np.ceil(descs["a"][order] / 4)
+    head, tail = work[: n // 20], work[-(n // 20):]
+    assert head.min() > tail.max()
+    assert work[0] == work.max()

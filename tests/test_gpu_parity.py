@@ -442,3 +442,41 @@ def test_generating_vector_argument(fam, state):
         assert torch.equal(g0, g1)
     with pytest.raises(mdi.MdiError):
         mdi.mdi_lr_integrate(fam, dev(params), d, a, nl, state=state, z=z + np.eye(1, d, 2, dtype=np.int64)[0])
+
+
+@pytest.mark.parametrize("split", [0, 1000])
+def test_batched_fp64_gaussian_recurrence_and_its_guard(split):
+    """The FP64 sweep steps the Gaussian's factors along a lane's cluster points by a
+    multiplicative recurrence when the arguments stay moderate, and evaluates each
+    factor directly otherwise, on one-warp teams (split 0) and whole CTAs, at
+    a = 9 ... 64.
+    * Moderate Gaussians (c up to 8; the recurrence): within 1e-12 of the oracle.
+    * Steep ones (c in 8 ... 40, most beyond the guard): N = a points per axis leave
+      them far from resolved, and their node states span a hundred orders of
+      magnitude, so the interpolation cancels and amplifies rounding-level
+      differences in the factors, whoever computes them (the sweep without the
+      recurrence gives the same errors).  They are held to 1e-12 or 200 times the
+      oracle's own change when every c_j moves by one ulp, whichever is larger
+      (the worst case here, at d = 7, a = 9, is 2.5e-11, 48 times that change,
+      and the oracle itself is 7.8e-13 from the 60-digit value of its sum)."""
+    rng = np.random.default_rng(77)
+    count = 240
+    ds = rng.integers(3, 12, count)
+    as_ = rng.choice([9, 12, 17, 24, 32, 48, 64], count)
+    ranges = [(0.2, 2.0), (2.0, 8.0), (8.0, 40.0)]
+    pool = np.concatenate([inputs.random_product("gauss", int(d), seed=i, c_range=ranges[i % 3])
+                           for i, d in enumerate(ds)])
+    offs = np.concatenate([[0], np.cumsum(2 * ds[:-1])])
+    descs = mdi.make_batch_descs(["gauss"] * count, ds, as_, as_, offs)
+    out = mdi.mdi_lr_integrate_batched(torch.from_numpy(descs.view(np.uint8)).cuda(), dev(pool), count,
+                                       split=min(split, count), precision="fp64", block=64,
+                                       table_in_l1=1).cpu().numpy()
+    for i in range(count):
+        d, a = int(ds[i]), int(as_[i])
+        p = pool[offs[i]:offs[i] + 2 * d]
+        ref = o.mdi_nodes("gauss", d, a, a, 16, p[:d], p[d:])
+        tol = TOL
+        if i % 3 == 2:
+            bumped = o.mdi_nodes("gauss", d, a, a, 16, np.nextafter(p[:d], np.inf), p[d:])
+            tol = max(TOL, 200.0 * abs(bumped - ref) / abs(ref))
+        assert abs(out[i] - ref) <= tol * abs(ref), (i, d, a, out[i], ref, tol)
