@@ -470,9 +470,8 @@ int or_mdi_nodes_states(int fam, int d, uint64_t a, uint64_t nd, int P, const do
  * m does not divide d-1 the last iteration takes the remaining axes.  The last
  * axis (n_d points s/n_d) is summed as in the m = 1 sweep.  m = 1 is
  * or_mdi_nodes. */
-double or_mdi_nodes_step(int fam, int d, uint64_t a, uint64_t nd, int P, int m, const double *c,
-                         const double *w) {
-  if (!is_product(fam) || P < 2 || m < 1 || m > 3) return NAN;
+static cplx mdi_nodes_step_core(int fam, int d, uint64_t a, uint64_t nd, int P, int m, const double *c,
+                                const double *w) {
   double *xi = (double *)malloc(sizeof(double) * (size_t)P);
   double *bw = (double *)malloc(sizeof(double) * (size_t)P);
   cplx *G = (cplx *)malloc(sizeof(cplx) * (size_t)P);
@@ -509,7 +508,83 @@ double or_mdi_nodes_step(int fam, int d, uint64_t a, uint64_t nd, int P, int m, 
   }
   acc /= (double)nd;
   free(xi); free(bw); free(G); free(H);
-  return creal(front(fam, w) * acc);
+  return acc;
+}
+
+double or_mdi_nodes_step(int fam, int d, uint64_t a, uint64_t nd, int P, int m, const double *c,
+                         const double *w) {
+  if (!is_product(fam) || P < 2 || m < 1 || m > 3) return NAN;
+  return creal(front(fam, w) * mdi_nodes_step_core(fam, d, a, nd, P, m, c, w));
+}
+
+/* Forward-mode derivative of the step-m node-state sweep (or_mdi_nodes_step) with
+ * respect to the parameters t listed in which[0..nwhich) (indices as in
+ * or_mdi_nodes_grad).  The tangent Gd is carried through each iteration by the
+ * same weighted tuple sum as G; in the iteration that contracts the parameter's
+ * axis, the tuple's factor of that axis is replaced by its derivative (the
+ * product rule over the tuple's factors) and multiplied by G read at the same
+ * innermost coordinate.  A parameter of the last axis enters the last sum. */
+int or_mdi_nodes_step_grad(int fam, int d, uint64_t a, uint64_t nd, int P, int m, const double *c,
+                           const double *w, const int *which, int nwhich, double *grad_out) {
+  if (!is_product(fam) || P < 2 || m < 1 || m > 3) return -1;
+  double *xi = (double *)malloc(sizeof(double) * (size_t)P);
+  double *bw = (double *)malloc(sizeof(double) * (size_t)P);
+  cplx *G = (cplx *)malloc(sizeof(cplx) * (size_t)P), *H = (cplx *)malloc(sizeof(cplx) * (size_t)P);
+  cplx *Gd = (cplx *)malloc(sizeof(cplx) * (size_t)P), *Hd = (cplx *)malloc(sizeof(cplx) * (size_t)P);
+  cheb_nodes(P, xi, bw);
+  for (int iw = 0; iw < nwhich; ++iw) {
+    int t = which[iw];
+    if (fam == OR_OSC && t == d) {  /* Q = Re(exp(2 pi i u) q): dQ/du = Re(2 pi i exp(2 pi i u) q) */
+      cplx q = mdi_nodes_step_core(fam, d, a, nd, P, m, c, w);
+      grad_out[iw] = creal(2.0 * M_PI * I * front(fam, w) * q);
+      continue;
+    }
+    int lev = (t < d) ? t : t - d;  /* 0-based axis of the parameter */
+    int kind = (t < d) ? 0 : 1;     /* 0: c, 1: w */
+    if (kind == 1 && (fam == OR_EXP || fam == OR_OSC)) { grad_out[iw] = 0.0; continue; }
+    for (int p = 0; p < P; ++p) { G[p] = 1.0; Gd[p] = 0.0; }
+    for (int i = 1; i < d; i += m) {  /* axes i .. i+mi-1 (1-based), as or_mdi_nodes_step */
+      int mi = (d - i < m) ? d - i : m;
+      uint64_t tuples = 1;
+      for (int j = 0; j < mi; ++j) tuples *= a;
+      int here = lev >= i - 1 && lev < i - 1 + mi;  /* the parameter's axis is contracted now */
+      for (int p = 0; p < P; ++p) {
+        cplx acc = 0.0, accd = 0.0;
+        for (uint64_t tu = 0; tu < tuples; ++tu) {
+          double x = xi[p];
+          cplx prod = 1.0, dprod = 1.0;
+          for (int j = mi - 1; j >= 0; --j) {
+            uint64_t aj = 1;
+            for (int l = 0; l < j; ++l) aj *= a;
+            uint64_t q = (tu / aj) % a;
+            x = ((double)q + x) / (double)a;  /* x_{i+j} */
+            cplx f = phi(fam, i + j - 1, x, c, w);
+            prod *= f;
+            dprod *= (i + j - 1 == lev) ? dphi(fam, i + j - 1, kind, x, c, w) : f;
+          }
+          cplx g = bary(P, xi, bw, G, x), gd = bary(P, xi, bw, Gd, x);
+          acc += prod * g;
+          accd += prod * gd;
+          if (here) accd += dprod * g;
+        }
+        H[p] = acc / (double)tuples;
+        Hd[p] = accd / (double)tuples;
+      }
+      memcpy(G, H, sizeof(cplx) * (size_t)P);
+      memcpy(Gd, Hd, sizeof(cplx) * (size_t)P);
+    }
+    cplx accd = 0.0;
+    for (uint64_t s = 0; s < nd; ++s) {
+      double u = (double)s / (double)nd;
+      cplx g = d > 1 ? bary(P, xi, bw, G, u) : 1.0;
+      cplx gd = d > 1 ? bary(P, xi, bw, Gd, u) : 0.0;
+      accd += phi(fam, d - 1, u, c, w) * gd;
+      if (d - 1 == lev) accd += dphi(fam, d - 1, kind, u, c, w) * g;
+    }
+    grad_out[iw] = creal(front(fam, w) * accd / (double)nd);
+  }
+  free(xi); free(bw); free(G); free(H); free(Gd); free(Hd);
+  return 0;
 }
 
 /* Forward-mode derivative of the node-state sweep with respect to c_t and w_t for

@@ -72,6 +72,7 @@ def _load():
                 "or_mdi_nodes_step": (D, [I, I, U, U, I, I, P, P]),
                 "or_mdi_nodes_states": (I, [I, I, U, U, I, P, P, P]),
                 "or_mdi_nodes_grad": (I, [I, I, U, U, I, P, P, P, I, P]),
+                "or_mdi_nodes_step_grad": (I, [I, I, U, U, I, I, P, P, P, I, P]),
                 "or_bary_matrix": (I, [I, U, P]),
                 "or_midpoint_grid": (D, [I, I, P, P, P]),
                 "or_midpoint_product": (D, [I, I, P, P, P]),
@@ -207,6 +208,17 @@ def mdi_nodes_grad(family, d, a, nd, P, c, w=None, which=None) -> np.ndarray:
     g = np.zeros(which.size)
     assert _load().or_mdi_nodes_grad(_fam(family), d, a, nd, P, _p(c), _p(w), _p(which),
                                      int(which.size), _p(g)) == 0
+    return g
+
+
+def mdi_nodes_step_grad(family, d, a, nd, P, m, c, w=None, which=None) -> np.ndarray:
+    """Derivative of the step-m node-state sweep (forward mode), entries as
+    mdi_nodes_grad."""
+    c, w = _f64(c, d), _f64(w, d)
+    which = np.arange(2 * d, dtype=np.int32) if which is None else np.ascontiguousarray(which, dtype=np.int32)
+    g = np.zeros(which.size)
+    assert _load().or_mdi_nodes_step_grad(_fam(family), d, a, nd, P, m, _p(c), _p(w), _p(which),
+                                          int(which.size), _p(g)) == 0
     return g
 
 

@@ -367,6 +367,47 @@ def test_sweep_gradients_equal_lattice_gradient(fam, d, a, nd):
         np.testing.assert_allclose(o.mdi_closed_grad(fam, d, a, nd, c, w), ref, rtol=1e-11, atol=1e-13 * scale)
 
 
+@pytest.mark.parametrize("fam", ["gauss", "peak", "exp", "osc"])
+@pytest.mark.parametrize("d,a,nd", [(3, 5, 5), (4, 8, 6), (5, 4, 7), (2, 16, 16)])
+def test_step_sweep_gradient_equals_lattice_gradient(fam, d, a, nd):
+    """The derivative of the step-m node sweep (m = 2, 3) equals the derivative of
+    the lattice sum it reproduces, and m = 1 is the m = 1 sweep's derivative."""
+    rng = np.random.default_rng(5 * d + a)
+    c, w = rng.uniform(0.5, 2.0, d), rng.uniform(0, 1, d)
+    if fam == "osc":
+        w[0] = 0.3
+    n = nd * a ** (d - 1)
+    ref = o.slr_grad(fam, d, n, o.korobov_z(d, a, n), c, w)
+    scale = np.max(np.abs(ref))
+    for m in (2, 3):
+        np.testing.assert_allclose(o.mdi_nodes_step_grad(fam, d, a, nd, 16, m, c, w), ref, rtol=1e-11,
+                                   atol=1e-13 * scale)
+    np.testing.assert_array_equal(o.mdi_nodes_step_grad(fam, d, a, nd, 16, 1, c, w),
+                                  o.mdi_nodes_grad(fam, d, a, nd, 16, c, w))
+
+
+@pytest.mark.parametrize("fam,m", [("gauss", 2), ("peak", 3), ("osc", 2)])
+def test_step_sweep_gradient_matches_central_difference(fam, m):
+    """Beyond enumerable sizes (d = 14): every parameter's derivative against a
+    central difference of the step-m sweep itself, h = 1e-6."""
+    d, a = 14, 6
+    rng = np.random.default_rng(17 + m)
+    c, w = rng.uniform(0.3, 1.5, d), rng.uniform(0, 1, d)
+    if fam == "osc":
+        w[0] = 0.3
+    g = o.mdi_nodes_step_grad(fam, d, a, a, 16, m, c, w)
+    h = 1e-6
+    scale = np.max(np.abs(g))
+    for t in range(2 * d):
+        cp, wp, cm, wm = c.copy(), w.copy(), c.copy(), w.copy()
+        if t < d:
+            cp[t] += h; cm[t] -= h
+        else:
+            wp[t - d] += h; wm[t - d] -= h
+        fd = (o.mdi_nodes_step(fam, d, a, a, 16, m, cp, wp) - o.mdi_nodes_step(fam, d, a, a, 16, m, cm, wm)) / (2 * h)
+        assert g[t] == pytest.approx(fd, rel=1e-6, abs=1e-9 * scale), (t, g[t], fd)
+
+
 def test_nodes_grad_large_d_matches_central_difference():
     d, a = 40, 16
     rng = np.random.default_rng(9)
