@@ -130,7 +130,8 @@ typedef struct {
                           state, m > 1 reads the state once per m levels (Algorithm 1,
                           eq. 2.14c: the factors of the m axes multiplied over the
                           a^m digit tuples), for single integrals in FP64 with
-                          a^m <= 4096 and no gradient; other uses MDI_EUNSUPPORTED */
+                          a^m <= 4096, value (mdi_lr_integrate) and gradient
+                          (mdi_lr_grad); other uses MDI_EUNSUPPORTED */
 } mdi_opts;
 
 /* ---------------------------------------------------------------------------
@@ -286,7 +287,9 @@ mdi_status mdi_lr_workspace_size(int32_t family, int32_t d, int64_t a, int64_t n
  * built in parallel, one CTA runs the forward and the reverse (adjoint) chains
  * keeping level states only every opts->checkpoint levels (0: ceil(sqrt(d))),
  * and each level's contribution is then formed in parallel after recomputing its
- * states from the nearest checkpoints.
+ * states from the nearest checkpoints.  With opts->step = m > 1 the same runs over
+ * the step-m operators (one per m axes), and each operator's m axes take their
+ * derivatives by the product rule over the a^m digit tuples.
  * ------------------------------------------------------------------------- */
 mdi_status mdi_lr_grad(int32_t family, int32_t d, int64_t a, int64_t n_last, const int64_t *z,
                        const double *params, const mdi_opts *opts, double *value, double *grad, void *workspace,

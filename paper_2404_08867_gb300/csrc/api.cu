@@ -269,7 +269,10 @@ mdi_status mdi_lr_grad_workspace_size(int32_t family, int32_t d, int64_t a, int6
       if (*bytes == 0) return MDI_EINVAL;
       return MDI_OK;
     default:
-      if (opts && opts->step > 1) return MDI_EUNSUPPORTED;
+      if (opts && opts->step > 1) {
+        *bytes = levels_step_workspace_bytes(d, a, nodes_config(opts), opts->checkpoint);
+        return *bytes ? MDI_OK : MDI_EUNSUPPORTED;
+      }
       *bytes = levels_workspace_bytes(d, a, nodes_config(opts), opts ? opts->checkpoint : 0);
       return MDI_OK;
   }
@@ -284,7 +287,6 @@ mdi_status mdi_lr_grad(int32_t family, int32_t d, int64_t a, int64_t n_last, con
   const int precision = opts ? opts->precision : MDI_PREC_FP64;
   if (precision != MDI_PREC_FP64) return MDI_EUNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
-  if (resolve_state(family, opts) == MDI_STATE_NODES && opts && opts->step > 1) return MDI_EUNSUPPORTED;
   switch (resolve_state(family, opts)) {
     case MDI_STATE_EXACT: return MDI_EUNSUPPORTED;
     case MDI_STATE_CLOSED: return closed_grad_launch(family, d, a, n_last, params, value, grad, workspace, ws_bytes, s);

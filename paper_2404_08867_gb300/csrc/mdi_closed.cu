@@ -26,6 +26,7 @@
 // waits on no other CTA, so the workspace needs no initial contents.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "mdi_common.cuh"
 #include "mdi_exp2_table.inc"
@@ -46,16 +47,16 @@ constexpr int kAnchor = 16;             // FP64 cluster terms: a fresh exp every
 // of level k (k < d - 1); an inclusive Hillis-Steele scan over shuffles composes
 // the maps of levels 0..k (earlier map first), which applied to beta_0 = 0 gives
 // beta_k, and gamma_k = beta_{k-1} + c_k.  Valid in lanes k < d.
-__device__ __forceinline__ double warp_gamma(int d, double inva, const double *__restrict__ params) {
+// ck: c_k of lane k (0 in lanes k >= d), loaded by the caller.
+__device__ __forceinline__ double warp_gamma(int d, double inva, double ck) {
   const int lane = threadIdx.x & (kWarp - 1);
-  const double ck = lane < d ? params[lane] : 0.0;
   double A = 1.0, B = 0.0;
   if (lane < d - 1) {
     A = inva;
     B = ck * inva;
   }
-#pragma unroll
-  for (int off = 1; off < kWarp; off <<= 1) {
+  // Lanes k >= d hold identity maps, so rounds with off >= d change no lane below d.
+  for (int off = 1; off < d; off <<= 1) {
     const double pA = __shfl_up_sync(0xffffffffu, A, off), pB = __shfl_up_sync(0xffffffffu, B, off);
     if (lane >= off) {
       B = fma(A, pB, B);
@@ -169,6 +170,8 @@ __global__ void __launch_bounds__(kChunkThreads) closed_chunk_kernel(int d, int6
   constexpr bool STEP = (PREC == MDI_PREC_FP64 || PREC == MDI_PREC_DF64);  // FP64 terms stepped by R
   __shared__ double s_gamma[kWarpScanMaxD];
   __shared__ double2 s_step[STEP ? kWarpScanMaxD : 1];
+  // The first warp's c_k load is issued before the table copy, so the two overlap.
+  const double ck = (!gamma_g && threadIdx.x < d && threadIdx.x < kWarp) ? params[threadIdx.x] : 0.0;
   if constexpr (DFE)
     for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s_exp2[j] = kExp2TableGen[j];
   if constexpr (TANG)
@@ -177,7 +180,7 @@ __global__ void __launch_bounds__(kChunkThreads) closed_chunk_kernel(int d, int6
   if (!gamma_g && threadIdx.x < kWarp) {
     // gamma_k for every level, and (FP64 terms) each level's step R_k = e^{32 gamma_k / r_k}
     const int k = threadIdx.x;
-    const double g = warp_gamma(d, ch.inv_a, params);
+    const double g = warp_gamma(d, ch.inv_a, ck);
     if (k < d) {
       s_gamma[k] = g;
       if constexpr (STEP) {
@@ -312,10 +315,15 @@ __global__ void __launch_bounds__(kChunkThreads) closed_chunk_kernel(int d, int6
         si = df_add(si, df_shfl_down(si, off));
       }
       s = make_double2(df_to_double(sr), df_to_double(si));
-    } else {
+    } else if constexpr (FAM == MDI_FAM_OSC) {
       s = warp_sum(s);
+    } else {  // real terms: the imaginary parts are zero
+      s.x = warp_sum(s.x);
     }
-    if constexpr (WITH_T) t = warp_sum(t);
+    if constexpr (WITH_T) {
+      if constexpr (FAM == MDI_FAM_OSC) t = warp_sum(t);
+      else t.x = warp_sum(t.x);
+    }
     if (lane == 0) {
       partS[c] = s;
       if constexpr (WITH_T) partT[c] = t;
@@ -385,6 +393,42 @@ static void launch_reduce(int d, int64_t a, int64_t n_last, const Chunks &ch, co
         d, a, n_last, ch, partS, partT, S, T);
 }
 
+// S_k = (1/r_k) (sum of level k's chunk sums, in shared memory) for every level,
+// by one CTA in a fixed order: one thread per level adding its chunks in order
+// when levels have few chunks, else warp w takes levels w, w + nw, ... with its
+// lanes adding a strided subset and an xor butterfly adding the lanes.  Real
+// families (REAL) add real parts only: their imaginary parts are zero.
+template <bool REAL>
+__device__ __forceinline__ void level_sums(int d, const Chunks &ch, const double2 *part, double2 *__restrict__ S) {
+  using V = typename std::conditional<REAL, double, double2>::type;
+  const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x / kWarp, nw = blockDim.x / kWarp;
+  auto load = [&](int c) -> V {
+    if constexpr (REAL) return part[c].x;
+    else return part[c];
+  };
+  auto store = [&](int k, V v) {
+    const double r = (k + 1 < d) ? ch.inv_a : ch.inv_nl;
+    if constexpr (REAL) S[k] = make_double2(v * r, 0.0);
+    else S[k] = c_scale(v, r);
+  };
+  if (ch.cpl <= 8 && ch.cpl_last <= 8) {
+    for (int k = threadIdx.x; k < d; k += blockDim.x) {
+      const int n = k < d - 1 ? ch.cpl : ch.cpl_last, base = chunk_base(k, d, ch.cpl);
+      V v = VOps<V>::zero();
+      for (int j = 0; j < n; ++j) v = VOps<V>::add(v, load(base + j));
+      store(k, v);
+    }
+  } else {
+    for (int k = warp; k < d; k += nw) {
+      const int n = k < d - 1 ? ch.cpl : ch.cpl_last, base = chunk_base(k, d, ch.cpl);
+      V v = VOps<V>::zero();
+      for (int j = lane; j < n; j += kWarp) v = VOps<V>::add(v, load(base + j));
+      v = warp_sum(v);
+      if (lane == 0) store(k, v);
+    }
+  }
+}
+
 // Steps 3 and 4 in one CTA when the chunk sums number at most kFinishMaxChunks:
 // the CTA first copies every chunk sum into shared memory (all loads in flight at
 // once: a level's sums read one after the other would each wait for L2), then
@@ -406,23 +450,7 @@ __global__ void __launch_bounds__(kFinishThreads) closed_finish_kernel(int d, Ch
   __shared__ typename FamTraits<FAM>::V sW[kFinishThreads / kWarp];
   for (int c = threadIdx.x; c < ch.total; c += kFinishThreads) s_part[c] = partS[c];
   __syncthreads();
-  const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x / kWarp, nw = kFinishThreads / kWarp;
-  if (ch.cpl <= 8 && ch.cpl_last <= 8) {
-    for (int k = threadIdx.x; k < d; k += kFinishThreads) {
-      const int n = k < d - 1 ? ch.cpl : ch.cpl_last, base = chunk_base(k, d, ch.cpl);
-      double2 v = make_double2(0.0, 0.0);
-      for (int j = 0; j < n; ++j) v = c_add(v, s_part[base + j]);
-      S[k] = c_scale(v, (k + 1 < d) ? ch.inv_a : ch.inv_nl);
-    }
-  } else {
-    for (int k = warp; k < d; k += nw) {
-      const int n = k < d - 1 ? ch.cpl : ch.cpl_last, base = chunk_base(k, d, ch.cpl);
-      double2 v = make_double2(0.0, 0.0);
-      for (int j = lane; j < n; j += kWarp) v = c_add(v, s_part[base + j]);
-      v = warp_sum(v);
-      if (lane == 0) S[k] = c_scale(v, (k + 1 < d) ? ch.inv_a : ch.inv_nl);
-    }
-  }
+  level_sums<FAM != MDI_FAM_OSC>(d, ch, s_part, S);
   __syncthreads();  // the S_k written above are visible to the whole CTA
   product_body<FAM>(d, params, S, out, sW);
 }
@@ -453,8 +481,10 @@ __device__ void product_body(int d, const double *__restrict__ params, const dou
   if ((threadIdx.x & (kWarp - 1)) == 0) sW[threadIdx.x / kWarp] = p;
   __syncthreads();
   if (threadIdx.x == 0) {
+    // Warps past the last factor hold exactly 1, so leaving them out changes no bit.
+    const int nw = min((int)(blockDim.x / kWarp), (d + per * kWarp - 1) / (per * kWarp));
     V K = sW[0];
-    for (int w = 1; w < (int)(blockDim.x / kWarp); ++w) K = VOps<V>::mul(K, sW[w]);
+    for (int w = 1; w < nw; ++w) K = VOps<V>::mul(K, sW[w]);
     if constexpr (FAM == MDI_FAM_OSC) {
       double sn, cs;
       sincos(kTwoPi * params[d], &sn, &cs);

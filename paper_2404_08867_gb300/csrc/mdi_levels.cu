@@ -706,6 +706,160 @@ __global__ void __launch_bounds__(kLvThreads) levels_grad_kernel(int d, int a, i
   }
 }
 
+// K4 for the step size m > 1: block b < ns takes operator k = b + 1, which
+// contracts the axes l0 = b m .. l0 + mj - 1 over the a^mj digit tuples (Q, p);
+// block ns takes the last axis.  With G_{k-1} and lambda_k recomputed from the
+// checkpoints as above, each axis ii of the operator gets
+//     dQ/dtheta_ii = (1/a^mj) sum_{Q,p} lambda_k[p] (prod_{jj != ii} phi_jj) dphi_ii/dtheta G~_{k-1}(x_0),
+// the product rule over the tuple's factors (x_jj = ((Q mod a^(mj-jj)) + xi_p) /
+// a^(mj-jj), as the operator's build), G~ read at x_0 from the radix-a^mj table.
+constexpr int kStepMaxM = 3;
+template <int FAM>
+__global__ void __launch_bounds__(kLvThreads) levels_step_grad_kernel(int d, int a, int n_last, int P, int m, int ns,
+                                                                      int C, const double *__restrict__ prm,
+                                                                      const double *__restrict__ Lm,
+                                                                      const double *__restrict__ Lr,
+                                                                      const double2 *__restrict__ M,
+                                                                      const double2 *__restrict__ gck,
+                                                                      const double2 *__restrict__ lck,
+                                                                      double *__restrict__ grad) {
+  using V = typename FamTraits<FAM>::V;
+  __shared__ double s_xi[kNodesPMax], s_bw[kNodesPMax];
+  __shared__ V s_g[2][kNodesPMax], s_l[2][kNodesPMax];
+  __shared__ V s_red[kLvThreads / kWarp];
+  __shared__ AxisParams s_ap[kStepMaxM];
+  for (int t = threadIdx.x; t < P; t += blockDim.x) {
+    s_xi[t] = cheb_node(t, P);
+    s_bw[t] = cheb_weight(t, P);
+  }
+  const int ng = C > 1 ? (ns + C - 1) / C : ns;
+  double2 front = make_double2(1.0, 0.0);
+  if (FAM == MDI_FAM_OSC) {
+    double sn, cs;
+    sincos(kTwoPi * prm[d], &sn, &cs);
+    front = make_double2(cs, sn);
+  }
+  const int tid = threadIdx.x;
+  for (int b = blockIdx.x; b <= ns; b += gridDim.x) {
+    // G after b operators, from the checkpoint at or below it (ping-pong buffers).
+    const int j0 = b / C;
+    int cg = 0;
+    if (tid < P) s_g[0][tid] = from2<V>(gck[(size_t)j0 * P + tid]);
+    __syncthreads();
+    for (int op = j0 * C + 1; op <= b; ++op) {
+      matvec8<V, false>(M + (size_t)(op - 1) * P * P, s_g[cg], s_g[cg ^ 1], P);
+      cg ^= 1;
+      __syncthreads();
+    }
+    const V *g_b = s_g[cg];
+    if (b < ns) {
+      const int k = b + 1, l0 = b * m, mj = min(m, d - 1 - l0);
+      int R = 1;
+      for (int i = 0; i < mj; ++i) R *= a;
+      const double *L = (mj == m) ? Lm : Lr;
+      const int npts = R * P;
+      // lambda_k from the checkpoint at or above it.
+      int top = ((k + C - 1) / C) * C;
+      const double2 *src;
+      if (top > ns) {
+        top = ns;
+        src = lck + (size_t)ng * P;
+      } else {
+        src = lck + (size_t)(top / C) * P;
+      }
+      int cl = 0;
+      if (tid < P) s_l[0][tid] = from2<V>(src[tid]);
+      if (tid < mj) s_ap[tid] = load_axis(prm, d, l0 + tid);
+      __syncthreads();
+      for (int op = top; op >= k + 1; --op) {
+        matvec8<V, true>(M + (size_t)(op - 1) * P * P, s_l[cl], s_l[cl ^ 1], P);
+        cl ^= 1;
+        __syncthreads();
+      }
+      const V *l_k = s_l[cl];
+      V acc_c[kStepMaxM], acc_w[kStepMaxM];
+#pragma unroll
+      for (int ii = 0; ii < kStepMaxM; ++ii) acc_c[ii] = acc_w[ii] = VOps<V>::zero();
+      for (int i = tid; i < npts; i += blockDim.x) {
+        const int Q = i / P, p = i % P;
+        PhiGrad<FAM> pg[kStepMaxM];
+        int Ri = R;
+#pragma unroll
+        for (int ii = 0; ii < kStepMaxM; ++ii) {
+          if (ii < mj) {
+            const double x = ((double)(Q % Ri) + s_xi[p]) / (double)Ri;
+            pg[ii] = phi_grad64<FAM>(x, s_ap[ii]);
+            Ri /= a;
+          }
+        }
+        V g = VOps<V>::one();
+        if (b > 0) {
+          g = VOps<V>::zero();
+          for (int t = 0; t < P; ++t) g = VOps<V>::fma_s(L[(size_t)t * npts + i], g_b[t], g);
+        }
+        const V lg = VOps<V>::mul(l_k[p], g);
+#pragma unroll
+        for (int ii = 0; ii < kStepMaxM; ++ii) {
+          if (ii < mj) {
+            V others = lg;
+#pragma unroll
+            for (int jj = 0; jj < kStepMaxM; ++jj)
+              if (jj < mj && jj != ii) others = VOps<V>::mul(others, pg[jj].f);
+            acc_c[ii] = VOps<V>::add(acc_c[ii], VOps<V>::mul(others, pg[ii].dc));
+            acc_w[ii] = VOps<V>::add(acc_w[ii], VOps<V>::mul(others, pg[ii].dw));
+          }
+        }
+      }
+      const double invR = 1.0 / (double)R;
+#pragma unroll
+      for (int ii = 0; ii < kStepMaxM; ++ii) {
+        if (ii < mj) {  // mj is the same in every thread of the block
+          const V tc = block_sum(acc_c[ii], s_red);
+          const V tw = block_sum(acc_w[ii], s_red);
+          if (tid == 0) {
+            grad[l0 + ii] = as2(tc).x * invR;
+            if (FAM != MDI_FAM_OSC) grad[d + l0 + ii] = as2(tw).x * invR;
+          }
+        }
+      }
+    } else {
+      // last axis: dQ/dtheta_d = Re(front (1/n_last) sum_s dphi_d(s/n_last) G~(s/n_last))
+      const AxisParams ap = load_axis(prm, d, d - 1);
+      V acc_c = VOps<V>::zero(), acc_w = VOps<V>::zero();
+      for (int s = tid; s < n_last; s += blockDim.x) {
+        const double u = (double)s / (double)n_last;
+        const PhiGrad<FAM> pg = phi_grad64<FAM>(u, ap);
+        V g = VOps<V>::one();
+        if (d > 1) {
+          V num = VOps<V>::zero();
+          double den = 0.0;
+          int hit = -1;
+          for (int t = 0; t < P; ++t) {
+            if (u == s_xi[t]) {
+              hit = t;
+              continue;
+            }
+            const double wt = s_bw[t] / (u - s_xi[t]);
+            den += wt;
+            num = VOps<V>::fma_s(wt, g_b[t], num);
+          }
+          g = hit >= 0 ? g_b[hit] : VOps<V>::scale(num, 1.0 / den);
+        }
+        const V fg = from2<V>(c_mul(front, as2(g)));
+        acc_c = VOps<V>::add(acc_c, VOps<V>::mul(fg, pg.dc));
+        acc_w = VOps<V>::add(acc_w, VOps<V>::mul(fg, pg.dw));
+      }
+      const V tc = block_sum(acc_c, s_red);
+      const V tw = block_sum(acc_w, s_red);
+      if (tid == 0) {
+        grad[d - 1] = as2(tc).x / (double)n_last;
+        if (FAM != MDI_FAM_OSC) grad[2 * d - 1] = as2(tw).x / (double)n_last;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -820,7 +974,7 @@ size_t levels_step_workspace_bytes(int d, int64_t a, const NodesConfig &cfg, int
 
 template <int FAM>
 static mdi_status run_levels_step(int d, int a, int n_last, const double *params, const NodesConfig &cfg,
-                                  int checkpoint, double *value, void *ws, cudaStream_t stream) {
+                                  int checkpoint, double *value, double *grad, void *ws, cudaStream_t stream) {
   const int P = cfg.P, m = cfg.step;
   const StepLayout Lo = step_layout(d, a, P, m, checkpoint);
   char *base = (char *)ws;
@@ -865,7 +1019,10 @@ static mdi_status run_levels_step(int d, int a, int n_last, const double *params
   const size_t chain_smem = 2 * (size_t)LC * P * P * sizeof(double2);
   const int chain_threads = std::max(32, (P * chain_group(P) + 31) / 32 * 32);
   levels_chain_kernel<FAM><<<1, chain_threads, chain_smem, stream>>>(d, Lo.ng, P, LC, params, ops, w, gck, lck, misc,
-                                                                     value, nullptr, 0);
+                                                                     value, grad, grad ? 1 : 0);
+  if ((st = check_launch()) != MDI_OK || !grad) return st;
+  levels_step_grad_kernel<FAM><<<std::min(Lo.ns + 1, sm_count() * 8), kLvThreads, 0, stream>>>(
+      d, a, n_last, P, m, Lo.ns, Lo.C, params, Lm, Lr, M, gck, lck, grad);
   return check_launch();
 }
 
@@ -889,17 +1046,20 @@ mdi_status levels_launch(int family, int d, int64_t a, int64_t n_last, const dou
   if (d < 1 || d > (1 << 16) || a < 1 || a > kNodesAMax || n_last < 1 || n_last > 4096) return MDI_EUNSUPPORTED;
   if (cfg.P < 2 || cfg.P > kNodesPMax || (cfg.P & 1)) return MDI_EINVAL;
   if (grad && cfg.precision != MDI_PREC_FP64) return MDI_EUNSUPPORTED;
-  if (cfg.step > 1) {  // Algorithm 1 with m = 2, 3: forward value in FP64
-    if (grad || cfg.precision != MDI_PREC_FP64 || !step_sizes_ok(a, cfg.step)) return MDI_EUNSUPPORTED;
+  if (cfg.step > 1) {  // Algorithm 1 with m = 2, 3 in FP64: value and adjoint
+    if (cfg.precision != MDI_PREC_FP64 || !step_sizes_ok(a, cfg.step)) return MDI_EUNSUPPORTED;
     if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < levels_step_workspace_bytes(d, a, cfg, checkpoint))
       return MDI_EWORKSPACE;
     const int ai = (int)a, nl = (int)n_last;
     switch (family) {
-      case MDI_FAM_EXP: return run_levels_step<MDI_FAM_EXP>(d, ai, nl, params, cfg, checkpoint, value, workspace, stream);
-      case MDI_FAM_OSC: return run_levels_step<MDI_FAM_OSC>(d, ai, nl, params, cfg, checkpoint, value, workspace, stream);
+      case MDI_FAM_EXP:
+        return run_levels_step<MDI_FAM_EXP>(d, ai, nl, params, cfg, checkpoint, value, grad, workspace, stream);
+      case MDI_FAM_OSC:
+        return run_levels_step<MDI_FAM_OSC>(d, ai, nl, params, cfg, checkpoint, value, grad, workspace, stream);
       case MDI_FAM_GAUSS:
-        return run_levels_step<MDI_FAM_GAUSS>(d, ai, nl, params, cfg, checkpoint, value, workspace, stream);
-      default: return run_levels_step<MDI_FAM_PEAK>(d, ai, nl, params, cfg, checkpoint, value, workspace, stream);
+        return run_levels_step<MDI_FAM_GAUSS>(d, ai, nl, params, cfg, checkpoint, value, grad, workspace, stream);
+      default:
+        return run_levels_step<MDI_FAM_PEAK>(d, ai, nl, params, cfg, checkpoint, value, grad, workspace, stream);
     }
   }
   const int C = checkpoint > 0 ? checkpoint : default_checkpoint(d);

@@ -297,8 +297,9 @@ def test_status_estimate_and_probe_validate_arguments(lib):
 
 
 def test_step_size_limits(lib):
-    """Algorithm 1's m > 1 with the node state: FP64 forward only, a^m <= 4096; the
-    gradient and the batched call refuse it."""
+    """Algorithm 1's m > 1 with the node state: FP64 value and gradient, a^m <= 4096;
+    the batched call refuses it.  (No call here reaches a launch: each is refused on
+    the host.)"""
     fake = ctypes.c_void_p(0x1000)
     b = ctypes.c_size_t()
     o = _ffi.MdiOpts()
@@ -307,9 +308,15 @@ def test_step_size_limits(lib):
     o.step = 3
     assert lib.mdi_lr_workspace_size(2, 10, 17, 17, ctypes.byref(o), ctypes.byref(b)) == _ffi.MDI_EUNSUPPORTED
     assert lib.mdi_lr_workspace_size(2, 10, 16, 16, ctypes.byref(o), ctypes.byref(b)) == _ffi.MDI_OK
+    assert lib.mdi_lr_grad_workspace_size(2, 10, 16, 16, ctypes.byref(o), ctypes.byref(b)) == _ffi.MDI_OK
+    assert b.value > 0
+    assert lib.mdi_lr_grad_workspace_size(2, 10, 17, 17, ctypes.byref(o), ctypes.byref(b)) == _ffi.MDI_EUNSUPPORTED
+    assert lib.mdi_lr_grad(2, 10, 17, 17, _null(), fake, ctypes.byref(o), fake, fake, fake, 1 << 30,
+                           _null()) == _ffi.MDI_EUNSUPPORTED  # 17^3 > 4096
+    o.precision = _ffi.PRECISION["df64"]
     assert lib.mdi_lr_grad(2, 10, 16, 16, _null(), fake, ctypes.byref(o), fake, fake, fake, 1 << 30,
-                           _null()) == _ffi.MDI_EUNSUPPORTED
-    assert lib.mdi_lr_grad_workspace_size(2, 10, 16, 16, ctypes.byref(o), ctypes.byref(b)) == _ffi.MDI_EUNSUPPORTED
+                           _null()) == _ffi.MDI_EUNSUPPORTED  # gradients are FP64
+    o.precision = _ffi.PRECISION["fp64"]
     assert lib.mdi_lr_integrate_batched(fake, fake, 4, 4, fake, 1 << 20, ctypes.byref(o), fake, fake, 1 << 30,
                                         _null()) == _ffi.MDI_EUNSUPPORTED
     o.precision = _ffi.PRECISION["df64"]

@@ -67,3 +67,44 @@ def test_step_closed_and_exact_states_ignore_m():
         v1 = mdi.mdi_lr_integrate("exp", dev(p), 5, 8, state=state).item()
         v2 = mdi.mdi_lr_integrate("exp", dev(p), 5, 8, state=state, step=2).item()
         assert v1 == v2
+
+
+def assert_grad_close(got, ref, fam, tol=TOL, floor=1e-15):
+    """Per component: |g_i - ref_i| <= tol |ref_i| + floor M, M = max|ref| (2 pi for
+    the oscillatory family, the bound of |df/du|), as the m = 1 adjoint's tests."""
+    got, ref = np.asarray(got), np.asarray(ref)
+    scale = max(np.max(np.abs(ref)), 2 * np.pi if fam == "osc" else 0.0, 1e-300)
+    bad = np.flatnonzero(np.abs(got - ref) > tol * np.abs(ref) + floor * scale)
+    assert bad.size == 0, (bad[:5].tolist(), got[bad[:5]].tolist(), ref[bad[:5]].tolist())
+
+
+@pytest.mark.parametrize("fam", ["gauss", "peak", "exp", "osc"])
+@pytest.mark.parametrize("m", [2, 3])
+@pytest.mark.parametrize("d,a,nd,P,C", [(1, 7, 7, 16, 0), (2, 9, 5, 16, 0), (4, 16, 16, 16, 1), (7, 5, 9, 8, 0),
+                                        (12, 6, 6, 12, 2), (20, 8, 16, 16, 0), (31, 3, 4, 32, 5)])
+def test_step_grad_matches_oracle(fam, m, d, a, nd, P, C):
+    """The adjoint over the step-m operators against the oracle's forward-mode
+    derivative of the step-m sweep, every component."""
+    params = inputs.random_product(fam, d, seed=11 * d + a + m)
+    if fam == "osc":
+        params[d] = 0.37
+    val, g = mdi.mdi_lr_grad(fam, dev(params), d, a, nd, state="nodes", nodes=P, step=m, checkpoint=C)
+    ref = o.mdi_nodes_step_grad(fam, d, a, nd, P, m, params[:d], params[d:])
+    assert_grad_close(g.cpu().numpy(), ref, fam)
+    close(val.item(), o.mdi_nodes_step(fam, d, a, nd, P, m, params[:d], params[d:]), fam)
+
+
+@pytest.mark.parametrize("m,C", [(2, 0), (3, 7)])
+def test_step_grad_differentiation_config(m, C):
+    """d = 100, N = 16 Gaussian, 200 parameters: sampled components (first, last
+    and interior axes, c and w) against the oracle, which takes one forward-mode
+    pass per parameter, and every component against the m = 1 adjoint (both are
+    derivatives of rules exact to rounding at P = 16)."""
+    w = inputs.gaussian(100, 16, seed=0)
+    _, g = mdi.mdi_lr_grad("gauss", dev(w.params), 100, 16, state="nodes", step=m, checkpoint=C)
+    g = g.cpu().numpy()
+    which = np.array([0, 1, 2, 3, 50, 97, 98, 99, 100, 101, 102, 150, 198, 199])
+    ref = o.mdi_nodes_step_grad("gauss", 100, 16, 16, 16, m, w.c, w.w, which)
+    assert_grad_close(g[which], ref, "gauss")
+    _, g1 = mdi.mdi_lr_grad("gauss", dev(w.params), 100, 16, state="nodes")
+    assert_grad_close(g, g1.cpu().numpy(), "gauss", tol=1e-11, floor=1e-14)
