@@ -536,7 +536,7 @@ def extra_time_to_1e6_vs_d(torch, mdi, inputs, dims=(4, 6, 8, 10, 12, 16, 20, 24
 # is repeated.
 TRAFFIC_SOURCES = ["paper_2404_08867_gb300/csrc/mdi_nodes.cu", "paper_2404_08867_gb300/csrc/mdi_nodes.cuh",
                    "paper_2404_08867_gb300/csrc/mdi_common.cuh", "paper_2404_08867_gb300/csrc/mdi_fp64.cuh"]
-PROFILED_TRAFFIC = {"fp64": ("9d69ed439868dd00", 1733888)}
+PROFILED_TRAFFIC = {"fp64": ("9d69ed439868dd00", 1703936)}
 
 
 def kernel_sources_key() -> str:
@@ -630,7 +630,8 @@ def extra_batch_size_sweep(torch, mdi, inputs, precision, counts=(4096, 16384, 6
         plan.tune()
         _, ms = event_ms(torch, lambda: plan.launch(), reps=5)
         rows.append({"count": count, "ms": ms, "integrals_per_s": count / (ms * 1e-3),
-                     "block": plan.opts.get("block")})
+                     "block": plan.opts.get("block"), "split": plan.opts.get("split"),
+                     "ctas_per_sm": plan.opts.get("ctas_per_sm")})
     return {"workload": f"batches of the configured distribution, {precision}, tuned shape", "rows": rows}
 
 
@@ -824,8 +825,9 @@ def extra_step_size(torch, mdi, inputs):
     operator instead of a.  d = 100, N = 16: time and value for the Gaussian of the
     differentiation workload and for exp(sum x_j/j^2), each against the oracle's
     step-m value, the exponential one also against its closed state (the exact
-    rule, so that difference is the node state's own error); and on an
-    enumerable case (d = 6, a = 8, P = 8) each m's error against the exact sweep."""
+    rule, so that difference is the node state's own error), and the adjoint's
+    time and its gradient against m = 1's; and on an enumerable case (d = 6,
+    a = 8, P = 8) each m's error against the exact sweep."""
     ref = golden_oracle()["step"]
     res = {"workload": "node state, step m = 1, 2, 3"}
     g = inputs.gaussian(100, 16, seed=0)
@@ -833,11 +835,19 @@ def extra_step_size(torch, mdi, inputs):
     for name, fam, w in (("gauss_d100", "gauss", g), ("exp_d100", "exp", e)):
         p = torch.as_tensor(w.params).cuda()
         rows = {}
+        g1 = None
         for m in (1, 2, 3):
             v, ms = event_ms(torch, lambda: mdi.mdi_lr_integrate(fam, p, 100, 16, state="nodes", step=m), reps=3)
             row = {"ms": ms, "value": v.item(), "rel_err_vs_oracle": abs(v.item() / ref[fam][str(m)] - 1.0)}
             if fam == "exp":
                 row["rel_err_vs_exact_rule"] = abs(v.item() / ref["exp_closed"] - 1.0)
+            # the adjoint over the step-m operators: time, and its gradient against m = 1's
+            (_, gm), gms = event_ms(torch, lambda: mdi.mdi_lr_grad(fam, p, 100, 16, state="nodes", step=m), reps=3)
+            gm = gm.cpu().numpy()
+            g1 = gm if m == 1 else g1
+            row["adjoint_ms"] = gms
+            if m > 1:
+                row["grad_max_rel_diff_vs_m1"] = float(np.max(np.abs(gm - g1)) / np.max(np.abs(g1)))
             rows[f"m{m}"] = row
         res[name] = rows
     small = {}
@@ -919,12 +929,14 @@ def max_rel_err(got, ref):
 # Named workloads for profilers (``python bench.py --case NAME --repeats R``): each
 # runs R times through the public API on the seeded synthetic inputs.
 # ---------------------------------------------------------------------------
-def _case_batch(precision, block, hybrid=False):
+def _case_batch(precision, block, hybrid=False, ctas_per_sm=0, split=None):
     from paper_2404_08867_gb300 import inputs
     from paper_2404_08867_gb300.tuning import BatchedMDILR
     b = inputs.batch(count=COUNT, seed=0)
     plan = BatchedMDILR(b.families, b.d, b.a, b.n_last, b.offsets, b.pool, precision=precision, nodes=P_NODES)
-    plan.opts.update(block=block, table_in_l1=1, split=plan.hybrid_split if hybrid else plan.count)
+    if split is None:
+        split = plan.hybrid_split if hybrid else plan.count
+    plan.opts.update(block=block, table_in_l1=1, split=split, ctas_per_sm=ctas_per_sm)
     return plan.launch
 
 
@@ -932,6 +944,8 @@ def build_case(name):
     """The launch function of a named workload:
       batch-fp64      4096-integral batch, FP64 node state (block 64, table via L1)
       batch-fp64-hybrid  the same with the planner's hybrid schedule
+      batch-fp64-w10  the same on 5 two-warp CTAs per SM (10 warps), one warp per
+                      integral (the tuner's choice for this batch)
       batch-df64      the same batch, double-float node state (block 32, table via L1)
       batch-f32df     the same batch, phi in float, double-float sums (block 32)
       levels-d1000    one integral, node state parallel over levels, d = 1000, N = 16:
@@ -957,6 +971,8 @@ def build_case(name):
         return _case_batch("fp64", 64)
     if name == "batch-fp64-hybrid":
         return _case_batch("fp64", 64, hybrid=True)
+    if name == "batch-fp64-w10":
+        return _case_batch("fp64", 64, ctas_per_sm=5, split=0)
     if name == "batch-df64":
         return _case_batch("df64", 32)
     if name == "batch-f32df":
@@ -1129,7 +1145,8 @@ def main():
                 ms = statistics.median(time_plan(torch, mp_, flush, stream, 10))
                 modes_out[prec] = mp_.out.cpu().numpy()
                 modes[prec] = {"ms_per_step": ms, "integrals_per_s": len(b) / (ms / 1e3), "block": mt["block"],
-                               "table_in_l1": mt["table_in_l1"],
+                               "table_in_l1": mt["table_in_l1"], "split": mt["split"],
+                               "ctas_per_sm": mt["ctas_per_sm"],
                                "roofline": {k: v for k, v in roofline_entry(b, prec, ms, peaks).items()
                                             if k in ("achieved", "peak", "frac", "pipe", "impl_tflops")}}
             line["modes"] = modes

@@ -5,11 +5,14 @@ order from the library's longest-first planner, parameter pool -- three views of
 one packed device buffer, so that a new batch of the same shape arrives in one
 host-to-device copy of ``host_inputs()``), a prepared workspace, and the launch
 shape.  ``tune()`` times the candidate shapes -- CTA size, whether each
-integral's basis table is staged in shared memory or read through L1, and the
+integral's basis table is staged in shared memory or read through L1, the
 planner's hybrid schedule on two-warp CTAs (its split and a few multiples of it),
-whose largest integrals run on whole CTAs and the rest one per warp -- on the
-batch itself with CUDA events and keeps the fastest (cached per batch signature
-for the process).  ``capture()`` records the one-kernel
+whose largest integrals run on whole CTAs and the rest one per warp, and fewer
+resident CTAs per SM than the occupancy allows (8 to 12 warps per SM: when the
+FP64 pipe is saturated by fewer warps, fewer workers each take more integrals of
+the longest-first order, which evens out the end of the launch) -- on the batch
+itself with CUDA events and keeps the fastest (cached per batch signature for
+the process).  ``capture()`` records the one-kernel
 launch into a CUDA graph; ``run()`` replays it.  Nothing here computes: every
 launch goes through the C ABI.
 """
@@ -25,6 +28,7 @@ from . import make_batch_descs, mdi_batch_plan, mdi_lr_batched_prepare, mdi_lr_i
 
 CANDIDATE_BLOCKS = (32, 64, 128, 256)
 CANDIDATE_TABLE_IN_L1 = (1, 0)
+CANDIDATE_WARPS_PER_SM = (8, 10, 12)  # resident warps per SM tried below the occupancy (tables through L1)
 _cache: Dict[Tuple, Dict] = {}
 
 
@@ -42,6 +46,7 @@ class BatchedMDILR:
         # the hybrid schedule's split.
         order, self.hybrid_split = mdi_batch_plan(descs, pool_t.numel(), nodes=nodes, precision=precision, block=64,
                                                   table_in_l1=1)
+        self.pool_len = pool_t.numel()
         # Packed inputs: descriptors | order | pool, each 256-byte aligned.
         def up(x):
             return (x + 255) // 256 * 256
@@ -132,21 +137,34 @@ class BatchedMDILR:
                 if block % self.nodes:
                     continue
                 for l1 in CANDIDATE_TABLE_IN_L1:
-                    results[(block, l1, self.count)] = self._time(reps, flush=flush, block=block, table_in_l1=l1,
-                                                                  split=self.count)
+                    results[(block, l1, self.count, 0)] = self._time(reps, flush=flush, block=block, table_in_l1=l1,
+                                                                     split=self.count)
             if self.hybrid_split < self.count:
                 # the planner's split (from a cost model of the FP64 sweep) and a few
                 # multiples of it, timed like the fixed shapes
                 splits = {min(self.count, int(self.hybrid_split * f)) for f in (0.25, 0.5, 1.0, 2.0, 4.0)}
                 for sp in sorted(splits):
-                    results[(64, 1, sp)] = self._time(reps, flush=flush, block=64, table_in_l1=1, split=sp)
-            (block, l1, split), best = min(results.items(), key=lambda kv: kv[1])
-            _cache[key] = {"block": block, "table_in_l1": l1, "split": split, "ms": best,
-                           "candidates": {f"block={b},table_in_l1={t},split={sp}": ms
-                                          for (b, t, sp), ms in results.items()}}
+                    results[(64, 1, sp, 0)] = self._time(reps, flush=flush, block=64, table_in_l1=1, split=sp)
+            # Fewer resident CTAs per SM: one- and two-warp CTAs holding 8..12 warps per
+            # SM, the two-warp ones with the planner's split for that worker count.
+            for block in (32, 64):
+                if block % self.nodes:
+                    continue
+                for w in CANDIDATE_WARPS_PER_SM:
+                    cps = w // (block // 32)
+                    sp = self.count
+                    if block == 64:
+                        _, sp = mdi_batch_plan(self.descs_host, self.pool_len, nodes=self.nodes,
+                                               precision=self.precision, block=64, table_in_l1=1, ctas_per_sm=cps)
+                    results[(block, 1, sp, cps)] = self._time(reps, flush=flush, block=block, table_in_l1=1,
+                                                              split=sp, ctas_per_sm=cps)
+            (block, l1, split, cps), best = min(results.items(), key=lambda kv: kv[1])
+            _cache[key] = {"block": block, "table_in_l1": l1, "split": split, "ctas_per_sm": cps, "ms": best,
+                           "candidates": {f"block={b},table_in_l1={t},split={sp},ctas_per_sm={c}": ms
+                                          for (b, t, sp, c), ms in results.items()}}
         self.tuning = _cache[key]
         self.opts.update(block=self.tuning["block"], table_in_l1=self.tuning["table_in_l1"],
-                         split=self.tuning["split"])
+                         split=self.tuning["split"], ctas_per_sm=self.tuning["ctas_per_sm"])
         self.graph = None
         return self.tuning
 

@@ -58,6 +58,30 @@ def test_every_launch_shape_gives_the_same_values(block, table_in_l1, precision,
     _check_sample(b, out, k=32, seed=block, tol=tol)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_fewer_resident_ctas_give_the_same_values(precision):
+    """The tuner's fewer-workers shapes (ctas_per_sm below the occupancy, one- and
+    two-warp CTAs, the hybrid split for that worker count): the worker count only
+    changes which CTA takes an integral, so each shape equals the default launch of
+    the same CTA size and split bit for bit, and every output is within 1e-12 of
+    the oracle."""
+    import paper_2404_08867_gb300 as mdi
+    b = inputs.batch(count=512, seed=8)
+    plan = _plan(b, precision)
+    ref = np.array([o.mdi_nodes(it.family, it.d, it.a, it.n_last, 16, it.c, it.w)
+                    for it in (b.integral(i) for i in range(len(b)))])
+    for block, cps in ((32, 8), (32, 1), (64, 4), (64, 5)):
+        sp = len(b)
+        if block == 64:
+            _, sp = mdi.mdi_batch_plan(plan.descs_host, plan.pool_len, nodes=16, precision=precision, block=64,
+                                       table_in_l1=1, ctas_per_sm=cps)
+        got = plan.launch(block=block, table_in_l1=1, split=sp, ctas_per_sm=cps).clone()
+        dflt = plan.launch(block=block, table_in_l1=1, split=sp).clone()
+        assert torch.equal(got, dflt), (block, cps)
+        g = got.cpu().numpy()
+        assert np.all(np.abs(g - ref) <= TOL * np.abs(ref)), (block, cps, np.max(np.abs(g - ref) / np.abs(ref)))
+
+
 def test_graph_replays_after_input_update():
     """A captured graph reads the parameter pool at replay time: new parameters
     copied into the same device buffer give new results without re-capture."""
