@@ -339,7 +339,7 @@ mdi_status mdi_get_device_status(const void *workspace, size_t ws_bytes, int32_t
 // accumulations) and two evaluations of phi; the first level has no
 // interpolation; each level adds its constants and sums; the last axis is small.
 // The FP64 sweep steps a Gaussian's factors by a recurrence when a lane has at
-// least three points (two multiplies per factor after five exps per level; the
+// least three points (two multiplies per factor after three exps per level; the
 // model takes its argument guard as met).
 static double team_time(const mdi_batch_desc &d, int P, int warps, bool fp64) {
   const double phi = d.family == MDI_FAM_PEAK ? 5.0 : 12.0;  // FP64 operations of one phi
@@ -348,7 +348,7 @@ static double team_time(const mdi_batch_desc &d, int P, int warps, bool fp64) {
   const bool rec = fp64 && d.family == MDI_FAM_GAUSS && passes >= 3.0;
   const double pphi = rec ? 2.0 : phi;
   const double pair = (double)P + 4.0 + 2.0 * pphi, first = 2.0 + 2.0 * pphi;
-  const double level = 10.0 + (rec ? 5.0 * phi + 8.0 : 0.0);
+  const double level = 10.0 + (rec ? 3.0 * phi + 6.0 : 0.0);
   const double last = std::ceil((double)d.n_last / (kWarp * warps)) * ((double)P + phi);
   if (d.d < 2) return last;
   return (double)(d.d - 2) * (passes * pair + level) + passes * first + level + last;

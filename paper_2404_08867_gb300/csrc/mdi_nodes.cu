@@ -86,6 +86,10 @@ struct LevelConst {
   float4 cwf;  // (c.hi, c.lo, w.hi, w.lo)
   float2 ic;   // 1/c^2 as a float pair
   double c, w, ic2, cw, c1w;
+  // FP64 Gaussian sweep, for lanes that step their points by Q (dq = (c/a) Q):
+  double kap;  // exp(-2 dq^2), the recurrence's second ratio
+  double eb;   // exp(2 (t_a - t_b) dq): the mirrored point's first ratio is rho_a eb
+  int rec_ok;  // the arguments stay moderate on this level (the recurrence may run)
 };
 
 // Fixed part of the dynamic shared memory; the staged table (if any) follows it.
@@ -289,11 +293,28 @@ __device__ __forceinline__ void make_level_const(const double *__restrict__ prm,
 }
 
 // Fills sh.lc with the constants of axes base .. base+kLvChunk-1 (all threads).
+// With a table T (the FP64 Gaussian sweep), also each level's kap for lanes that
+// step their points by Q: dq = (c/a) Q, one exp per level and chunk rather than
+// per level and lane.
 template <bool DF = false>
 __device__ __forceinline__ void load_level_chunk(LevelConst *lc, const double *__restrict__ prm, int d, int base,
-                                                 const Team &tm = Team::block()) {
+                                                 const Team &tm = Team::block(), const double *T = nullptr,
+                                                 double inv_a = 0.0, double Qd = 0.0) {
   const int n = min(kLvChunk, d - base);
-  for (int j = tm.tid; j < n; j += tm.size) make_level_const<DF>(prm, d, base + j, lc[j]);
+  for (int j = tm.tid; j < n; j += tm.size) {
+    LevelConst &L = lc[j];
+    make_level_const<DF>(prm, d, base + j, L);
+    if (T) {
+      const double dq = (L.c * inv_a) * Qd;
+      // |t| <= B at every cluster point of the level (t = c (u - w) and
+      // c (u - 1 + w), u in [0, 1)); with |dq| (2B + |dq|) < 350 every factor, both
+      // first ratios and eb stay in the normal range.
+      const double B = fabs(L.c) * (fmax(fabs(L.w), fabs(1.0 - L.w)) + inv_a + 1.0);
+      L.rec_ok = B < 20.0 && fabs(dq) * (2.0 * B + fabs(dq)) < 350.0;
+      L.kap = exp_tang64(-2.0 * dq * dq, T);
+      L.eb = exp_tang64(2.0 * (L.c1w - L.cw) * dq, T);  // t_a - t_b = c (1 - w) - c w
+    }
+  }
 }
 
 // The argument of phi at the cluster points u = q/a + x0 of one node is affine in
@@ -860,9 +881,11 @@ __device__ void sweep_paired_fp64(NodesShared &sh, const NodesConsts *__restrict
   const int npts_h = a * h;
   if (tid < h) sh.G[0][tid] = make_double2(1.0, 0.0);  // G_0 = 1: E = 1, O = 0
   if (F32 && tid < P) sh.xadf[tid] = kc->xa[a][tid];
-  load_level_chunk(sh.lc, prm, d, 0, tm);
-  tm.sync();
   const double inv_a = 1.0 / (double)a, half_inv_a = 0.5 * inv_a;
+  constexpr bool REC = FAM == MDI_FAM_GAUSS && !F32;  // the recurrence's kap comes with the level constants
+  const double *ktab = REC ? sh.exp2d : nullptr;
+  load_level_chunk(sh.lc, prm, d, 0, tm, ktab, inv_a, (double)Q);
+  tm.sync();
   const double xa = sh.xi[pp], xb = sh.xi[pb];
   const double x0 = xa * inv_a;  // xi_pp / a
   const float iaf = F32 ? kc->ia[a].x : 0.f, xaf = F32 ? sh.xadf[pp].x : 0.f, xbf = F32 ? sh.xadf[pb].x : 0.f;
@@ -870,7 +893,7 @@ __device__ void sweep_paired_fp64(NodesShared &sh, const NodesConsts *__restrict
   for (int k = 1; k < d; ++k) {
     const int j = k - 1;
     if (j > 0 && j % kLvChunk == 0) {
-      load_level_chunk(sh.lc, prm, d, j, tm);
+      load_level_chunk(sh.lc, prm, d, j, tm, ktab, inv_a, (double)Q);
       tm.sync();
     }
     const LevelConst &L = sh.lc[j % kLvChunk];
@@ -900,28 +923,28 @@ __device__ void sweep_paired_fp64(NodesShared &sh, const NodesConsts *__restrict
     // Gaussian factors along a lane's points q = qs, qs + Q, ...: t steps by
     // dq = s1 Q, so phi(q + Q) = phi(q) rho(q) and rho(q + Q) = rho(q) kappa with
     // rho(q) = exp(-(2 t dq + dq^2)) and kappa = exp(-2 dq^2) -- two multiplies per
-    // point after five exps per lane and level, against an exp per point.  Taken
-    // when every lane of the warp has at least three points and the arguments stay
-    // moderate (|t| < 20, |2 t dq + dq^2| < 500: no factor leaves the normal range),
-    // the same choice for the whole warp.  The k-th factor's relative error is the
-    // rounding of the arguments carried along, about (t0^2 + k |2 t0 dq| + k^2 dq^2)
-    // ulps -- the size of the direct exp's own argument rounding, t_k^2 ulps -- plus
-    // about 2k ulps of products.
+    // point after three exps per lane and level, against an exp per point: the
+    // mirrored point's argument is t_b = t_a - (t_a - t_b) with a per-level
+    // difference, so rho_b = rho_a exp(2 (t_a - t_b) dq), and that factor and kappa
+    // come with the level's constants.  Taken when every lane has at least three
+    // points and the level's arguments stay moderate (|t| <= B < 20,
+    // |dq| (2B + |dq|) < 350: no factor or ratio leaves the normal range).  The k-th
+    // factor's relative error is the rounding of the arguments carried along,
+    // about (t0^2 + k |2 t0 dq| + k^2 dq^2) ulps -- the size of the direct exp's own
+    // argument rounding, t_k^2 ulps -- plus about 3k ulps of products.
     bool rec = false;
     double fa = 0.0, fb = 0.0, rho_a = 0.0, rho_b = 0.0, kap = 0.0;
     if constexpr (FAM == MDI_FAM_GAUSS && !F32) {
-      const double dq = s1a * (double)Q;
-      const double tmax = fmax(fabs(s0a), fabs(s0b)) + fabs(s1a) * (double)a;
-      const bool ok = !act || (tmax < 20.0 && fabs(dq) * (2.0 * tmax + fabs(dq)) < 500.0);
-      rec = (a + Q - 1) / Q >= 3 && __all_sync(0xffffffffu, ok);
+      rec = (a + Q - 1) / Q >= 3 && L.rec_ok;
       if (rec && act) {
+        const double dq = s1a * (double)Q;
         const double qd0 = sh.qd[qs];
         const double ta = fma(s1a, qd0, s0a), tb = fma(s1b, qd0, s0b);
         fa = exp_tang64(-(ta * ta), sh.exp2d);
         fb = exp_tang64(-(tb * tb), sh.exp2d);
         rho_a = exp_tang64(-fma(2.0 * ta, dq, dq * dq), sh.exp2d);
-        rho_b = exp_tang64(-fma(2.0 * tb, dq, dq * dq), sh.exp2d);
-        kap = exp_tang64(-2.0 * dq * dq, sh.exp2d);
+        rho_b = rho_a * L.eb;
+        kap = L.kap;
       }
     }
     double acc_a = 0.0, acc_b = 0.0;
