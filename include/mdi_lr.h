@@ -399,9 +399,12 @@ mdi_status mdi_get_device_status(const void *workspace, size_t ws_bytes, int32_t
  *     Q = sum_S H_{d-1}[S] (1/n_last) sum_{k<n_last} f at (S + (d-1)/2)/N + (k + 1/2)/n_last.
  *   out        DEVICE, one double
  *   workspace  DEVICE, >= mdi_midpoint_ridge_workspace_size bytes, 256-byte aligned
- * d + 2 launches on `stream`, FP64.  MDI_EINVAL unless d, N, n_last >= 1, c0 > 0
- * and power finite, and (d-1)(N-1) + 1 <= 2^26; MDI_EWORKSPACE for a bad
- * workspace.  f_6's integral is 1/(d+1)!, which leaves the double range near
+ * Three launches on `stream`, FP64: the d - 1 levels in one thread-block cluster
+ * (the histogram split over its CTAs' shared memory, a cluster barrier per level;
+ * d + 1 plain launches instead when the histogram does not fit), every (S, k)
+ * pair of the last axis, and the sum of the partials.  MDI_EINVAL unless d, N,
+ * n_last >= 1, c0 > 0 and power finite, (d-1)(N-1) + 1 <= 2^26 and
+ * ((d-1)(N-1) + 1) n_last <= 2^62; MDI_EWORKSPACE for a bad workspace.  f_6's integral is 1/(d+1)!, which leaves the double range near
  * d = 170.
  * ------------------------------------------------------------------------- */
 mdi_status mdi_midpoint_ridge(int32_t d, int64_t N, int64_t n_last, double c0, double power, double *out,

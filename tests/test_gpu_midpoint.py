@@ -57,10 +57,13 @@ def test_gpu_reproduces_printed_mdi_errors(row):
 
 @pytest.mark.parametrize("d,N,nl,c0,p", [(1, 7, 7, 1.0, None), (2, 5, 6, 1.0, None), (6, 10, 11, 1.0, None),
                                          (20, 8, 9, 1.0, None), (60, 16, 16, 1.0, None), (3, 300, 301, 0.5, 2.5),
-                                         (150, 4, 5, 1.0, None), (10, 33, 2, 2.0, 7.0)])
+                                         (150, 4, 5, 1.0, None), (10, 33, 2, 2.0, 7.0), (17, 16, 16, 1.0, None),
+                                         (200, 16, 16, 1.0, None), (5, 1, 3, 1.0, None), (2, 2, 2, 1.0, None)])
 def test_midpoint_ridge_matches_oracle(d, N, nl, c0, p):
     """Test 7's f_6 = (1 + sum x_i)^-(d+1) (and other c0, p): the GPU's histogram
-    sweep against the oracle's, element by element."""
+    sweep against the oracle's.  The sizes take the cluster path with 1 to 16 CTAs
+    (d = 17, N = 16: every CTA holds exactly N - 1 weights, so each halo is a whole
+    neighbour slice) and the one-launch-per-axis path (d = 1, N = 1)."""
     got = mdi.mdi_midpoint_ridge(d, N, nl, c0=c0, power=p).item()
     ref = o.midpoint_ridge(d, N, nl, c0, p)
     assert abs(got - ref) <= TOL * abs(ref), (got, ref)
