@@ -953,6 +953,8 @@ def build_case(name):
                       integral (the tuner's choice for this batch)
       batch-df64      the same batch, double-float node state (block 32, table via L1)
       batch-f32df     the same batch, phi in float, double-float sums (block 32)
+      levels-d100     one integral, node state parallel over levels, the differentiation
+                      workload (d = 100, N = 16 Gaussian, checkpoint 10): forward and adjoint
       levels-d1000    one integral, node state parallel over levels, d = 1000, N = 16:
                       forward and adjoint
       korobov         P_2 Korobov search, n = 65536, d = 4, every a in 1..n/2
@@ -982,6 +984,11 @@ def build_case(name):
         return _case_batch("df64", 32)
     if name == "batch-f32df":
         return _case_batch("fp32_eval_df32", 32)
+    if name == "levels-d100":
+        w = inputs.gaussian(100, 16, seed=0)
+        p = torch.as_tensor(w.params).cuda()
+        return lambda: (mdi.mdi_lr_integrate("gauss", p, 100, 16, state="nodes"),
+                        mdi.mdi_lr_grad("gauss", p, 100, 16, state="nodes", checkpoint=10))
     if name == "levels-d1000":
         w = inputs.scale_exp(1000, 16)
         p = torch.as_tensor(w.params).cuda()
