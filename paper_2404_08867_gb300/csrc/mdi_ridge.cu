@@ -21,6 +21,7 @@
 // The work is N^2 d^2 / 2 additions for the weights and about (d-1) N n_last
 // powers.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "mdi_common.cuh"
@@ -172,11 +173,11 @@ constexpr size_t kRidgeClusterSmem = 200 * 1024;
 // Largest cluster the GPU runs ridge_cluster_kernel in (16, else 8), once per
 // device; 0 if neither launches.
 static int ridge_cluster_size() {
-  static int cache[64];
+  static std::atomic<int> cache[64];  // 0: not asked yet, -1: no cluster runs
   int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) return 8;
-  if (cache[dev] != 0) return cache[dev] > 0 ? cache[dev] : 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;  // the per-level launches
+  const int known = cache[dev].load(std::memory_order_relaxed);
+  if (known != 0) return known > 0 ? known : 0;
   int best = -1;
   if (cudaFuncSetAttribute(ridge_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
       cudaFuncSetAttribute(ridge_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -201,7 +202,7 @@ static int ridge_cluster_size() {
     }
   }
   cudaGetLastError();  // a refused query leaves no error behind
-  cache[dev] = best;
+  cache[dev].store(best, std::memory_order_relaxed);
   return best > 0 ? best : 0;
 }
 
