@@ -801,7 +801,9 @@ static mdi_status run_closed_grad(int d, int64_t a, int64_t n_last, const double
   char *base = (char *)ws;
   mdi_status st = run_levels_sums<FAM, MDI_PREC_FP64, true>(d, a, n_last, params, base, L, nullptr, stream);
   if (st != MDI_OK) return st;
-  closed_grad_final_kernel<FAM><<<1, kScanThreads, 0, stream>>>(d, (double)a, params, (const double2 *)(base + L.S),
+  // One CTA of about d/8 threads: each takes a run of levels in order, and the
+  // scans between runs take log2 of the thread count rounds (FP64 work on one SM).
+  closed_grad_final_kernel<FAM><<<1, scan_threads(d), 0, stream>>>(d, (double)a, params, (const double2 *)(base + L.S),
                                                                 (const double2 *)(base + L.T), (double2 *)(base + L.nu),
                                                                 value, grad);
   return check_launch();

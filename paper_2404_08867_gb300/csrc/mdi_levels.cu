@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(kLvThreads) levels_step_build_kernel(int d, in
 
 // cp.async helpers for staging operators into shared memory (hardware
 // wait_group, double-buffered), so no product waits on an L2 round trip.
-constexpr int kChainMaxThreads = 1024;  // P x G thread grid, G = the power of two >= P
+constexpr int kChainMaxThreads = 8 * kNodesPMax;  // eight lanes per row of a P x P product
 constexpr int kChainSmem = 64 * 1024;  // two buffers of operators
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -441,21 +441,17 @@ template <> __device__ __forceinline__ double2 group_sum<double2>(double2 v, int
   return v;
 }
 
-// Lanes per row of the chain's thread grid: the power of two >= P.
-__host__ __device__ __forceinline__ int chain_group(int P) {
-  int g = 1;
-  while (g < P) g <<= 1;
-  return g;
-}
-
 static int chain_levels_per_chunk(int P) {
   return std::max(1, std::min(8, kChainSmem / 2 / (P * P * (int)sizeof(double2))));
 }
 
 // K3: the chain over the ng group operators (R_g, or M_k when C = 1), forward
 // with a checkpoint at every group boundary and the value, backward for the
-// adjoint.  One CTA: a P x G thread grid does each matrix-vector product (one
-// multiply per thread, summed over the G lanes of a row) while all threads stage
+// adjoint.  One CTA: eight lanes per row of each matrix-vector product, each
+// summing every eighth term, then three shuffle rounds (on GB300 a warp's FP64
+// instruction holds its sub-partition's FP64 unit for about 64 cycles, so fewer,
+// fuller warps finish a product sooner than one multiply per thread); the vector
+// is double-buffered in shared memory, one barrier per product; all threads stage
 // the next chunk of operators with cp.async.  Real families use real arithmetic
 // on the real parts.  misc[0] = Q before the front factor.
 template <int FAM>
@@ -472,19 +468,26 @@ __global__ void __launch_bounds__(kChainMaxThreads) levels_chain_kernel(int d, i
   extern __shared__ __align__(16) unsigned char chain_smem[];
   double2 *const buf0 = (double2 *)chain_smem;  // two chunks of LC operators
   const size_t bstride = (size_t)LC * P * P;
-  __shared__ V s_v[kNodesPMax], s_n[kNodesPMax];
-  const int G = chain_group(P);
-  const int row = threadIdx.x / G, col = threadIdx.x % G;
-  const bool cell = row < P && col < P;
+  __shared__ V s_v[2][kNodesPMax];  // the chain's vector, double-buffered
+  const int row = threadIdx.x >> 3, part = threadIdx.x & 7;
+  const bool rowok = row < P;
   const int p = threadIdx.x;
   const bool on = p < P;
-  auto mul = [](double2 m, V v) -> V {
-    if constexpr (FAM == MDI_FAM_OSC) return c_mul(m, v);
-    else return m.x * v;
+  // out[row] = sum_col Rk[row][col] v[col] (Rk row-major as staged), into s_v[nb]
+  auto product = [&](const double2 *Rk, int vb) -> V {
+    V acc = VOps<V>::zero();
+    if (rowok)
+      for (int col = part; col < P; col += 8) {
+        const double2 m = Rk[row * P + col];
+        if constexpr (FAM == MDI_FAM_OSC) acc = c_add(acc, c_mul(m, s_v[vb][col]));
+        else acc = fma(m.x, s_v[vb][col], acc);
+      }
+    return group_sum(acc, 8);
   };
-  if (on) s_v[p] = VOps<V>::one();
+  int vb = 0;
+  if (on) s_v[0][p] = VOps<V>::one();
   __syncthreads();
-  if (on) gck[p] = as2(s_v[p]);
+  if (on) gck[p] = as2(s_v[0][p]);
   const int nchunks = (ng + LC - 1) / LC;
   // Forward: chunk c holds operators 1 + c*LC .. min(ng, (c+1)*LC), staged as [p][t].
   // S_k[p] = sum_t R_k[p][t] S_{k-1}[t]: row = p, col = t.
@@ -501,15 +504,12 @@ __global__ void __launch_bounds__(kChainMaxThreads) levels_chain_kernel(int d, i
     __syncthreads();
     const double2 *B = buf0 + (c & 1) * bstride;
     for (int k = k0; k <= k1; ++k) {
-      const double2 *Rk = B + (size_t)(k - k0) * P * P;
-      V prod = cell ? mul(Rk[row * P + col], s_v[col]) : VOps<V>::zero();
-      prod = group_sum(prod, G);
-      if (cell && col == 0) {
-        s_n[row] = prod;
+      const V prod = product(B + (size_t)(k - k0) * P * P, vb);
+      if (rowok && part == 0) {
+        s_v[vb ^ 1][row] = prod;
         gck[(size_t)k * P + row] = as2(prod);
       }
-      __syncthreads();
-      if (on) s_v[p] = s_n[p];
+      vb ^= 1;
       __syncthreads();
     }
   }
@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(kChainMaxThreads) levels_chain_kernel(int d, i
   }
   if (threadIdx.x == 0) {
     double2 q = make_double2(0.0, 0.0);
-    for (int t = 0; t < P; ++t) q = c_add(q, c_mul(w[t], as2(s_v[t])));
+    for (int t = 0; t < P; ++t) q = c_add(q, c_mul(w[t], as2(s_v[vb][t])));
     misc[0] = q;
     const double2 fq = c_mul(front, q);
     if (value) *value = fq.x;
@@ -534,9 +534,10 @@ __global__ void __launch_bounds__(kChainMaxThreads) levels_chain_kernel(int d, i
   if (!adjoint) return;
   __syncthreads();
   // lambda at b_ng = d-1 is front * w (real for real families: front = 1, w real).
+  vb = 0;
   if (on) {
     const double2 l = c_mul(front, w[p]);
-    s_v[p] = from2<V>(l);
+    s_v[0][p] = from2<V>(l);
     lck[(size_t)ng * P + p] = l;
   }
   __syncthreads();
@@ -559,15 +560,12 @@ __global__ void __launch_bounds__(kChainMaxThreads) levels_chain_kernel(int d, i
     __syncthreads();
     const double2 *B = buf0 + (c & 1) * bstride;
     for (int k = top; k >= bot; --k) {
-      const double2 *Rk = B + (size_t)(k - bot) * P * P;
-      V prod = cell ? mul(Rk[row * P + col], s_v[col]) : VOps<V>::zero();
-      prod = group_sum(prod, G);
-      if (cell && col == 0) {
-        s_n[row] = prod;
+      const V prod = product(B + (size_t)(k - bot) * P * P, vb);
+      if (rowok && part == 0) {
+        s_v[vb ^ 1][row] = prod;
         lck[(size_t)(k - 1) * P + row] = as2(prod);
       }
-      __syncthreads();
-      if (on) s_v[p] = s_n[p];
+      vb ^= 1;
       __syncthreads();
     }
   }
@@ -908,7 +906,7 @@ static mdi_status run_levels(int d, int a, int n_last, const double *params, con
   }
   const int LC = chain_levels_per_chunk(P);
   const size_t chain_smem = 2 * (size_t)LC * P * P * sizeof(double2);
-  const int chain_threads = std::max(32, (P * chain_group(P) + 31) / 32 * 32);
+  const int chain_threads = std::max(32, (8 * P + 31) / 32 * 32);
   levels_chain_kernel<FAM><<<1, chain_threads, chain_smem, stream>>>(d, Lo.ng, P, LC, params, ops, w, gck, lck, misc,
                                                                      value, grad, grad ? 1 : 0);
   if ((st = check_launch()) != MDI_OK) return st;
@@ -1017,7 +1015,7 @@ static mdi_status run_levels_step(int d, int a, int n_last, const double *params
   }
   const int LC = chain_levels_per_chunk(P);
   const size_t chain_smem = 2 * (size_t)LC * P * P * sizeof(double2);
-  const int chain_threads = std::max(32, (P * chain_group(P) + 31) / 32 * 32);
+  const int chain_threads = std::max(32, (8 * P + 31) / 32 * 32);
   levels_chain_kernel<FAM><<<1, chain_threads, chain_smem, stream>>>(d, Lo.ng, P, LC, params, ops, w, gck, lck, misc,
                                                                      value, grad, grad ? 1 : 0);
   if ((st = check_launch()) != MDI_OK || !grad) return st;
