@@ -332,6 +332,20 @@ def test_batched_full_size_every_output(prec):
     assert_batch_close(out1, oracle_batch(4096, 0), TOL)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_batched_full_size_in_the_bench_launch_configuration(prec):
+    """The same batch through the bench's own path: the autotuned launch shape
+    (CTA size, table placement, hybrid split, resident CTAs per SM), captured in a
+    CUDA graph and replayed: every output against the oracle within 1e-12."""
+    from paper_2404_08867_gb300.tuning import BatchedMDILR
+    b = inputs.batch(count=4096, seed=0)
+    plan = BatchedMDILR(b.families, b.d, b.a, b.n_last, b.offsets, b.pool, precision=prec, nodes=16)
+    plan.tune(reps=2)
+    plan.capture()
+    out = plan.run().cpu().numpy()
+    assert_batch_close(out, oracle_batch(4096, 0), TOL)
+
+
 @pytest.mark.parametrize("prec", ["fp32_eval_fp64", "fp32_eval_df32"])
 def test_batched_single_precision_evaluation_modes(prec):
     # The paired sweeps evaluate phi in float at the float coordinate (q + xi_p)/a:
