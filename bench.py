@@ -53,7 +53,7 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # beside the peaks the run measures with the library's FMA probe:
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12    # 2 DFMA lanes per SM per clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 128 FFMA lanes per SM per clock
-# Algorithmic flops of one node-state integral (the survey's measurement table):
+# Algorithmic flops of one node-state integral:
 # d N (P C_phi + P^2) -- per level and cluster point, P evaluations of phi at
 # C_phi flops each and the P^2 terms of interpolating the state.  C_phi counts an
 # exp or a division as 20 flops plus the affine argument, its square and the
@@ -901,8 +901,8 @@ def time_plan(torch, plan, flush, stream, steps):
 
 
 def roofline_entry(b, precision, kernel_ms, peaks, traffic=None):
-    """Roofline of one batched launch: the algorithmic flops of the survey's count
-    (d N (P C_phi + P^2) per integral) over the launch's time, against the measured
+    """Roofline of one batched launch: the algorithmic flops (d N (P C_phi + P^2)
+    per integral) over the launch's time, against the measured
     FMA peak of the pipe the mode runs on (FP64 for the FP64 mode, FP32 for the
     double-float and single-precision-evaluation modes); impl_flops is what the
     kernel's own formulation executes (the paired interpolation, and double-float

@@ -94,7 +94,7 @@ def test_flop_counts_of_the_batched_formulations():
 
 
 def test_algorithmic_flop_count():
-    """The survey's count for the batch: d N (P C_phi + P^2) per integral (a = N)."""
+    """The algorithmic count for the batch: d N (P C_phi + P^2) per integral (a = N)."""
     from types import SimpleNamespace
     P = bench.P_NODES
     b = SimpleNamespace(families=["gauss", "peak"], d=np.array([3, 7]), a=np.array([5, 20]), n_last=np.array([5, 20]))
