@@ -15,6 +15,7 @@
 
 #include "mdi_common.cuh"
 #include "mdi_exp2_table.inc"
+#include "mdi_fp64.cuh"
 #include "mdi_internal.h"
 
 namespace mdi {
@@ -34,13 +35,25 @@ struct SlrArgs {
 // SHIFT: the randomly shifted rule of Section 2.1, x = {j z / n + Delta_r} with the
 // shift Delta_r = shifts[r*d .. r*d + d) of replicate r = blockIdx.y; each
 // replicate's CTAs write their partials at partials + r * gridDim.x.
+//
+// FP64 points of the unshifted rule (FAST) keep GB300's FP64 pipe, which bounds
+// them, to what the point needs: 1/n is folded into each coordinate's constant
+// (the exponential family's argument is sum_i (c_i/n) r_i, the Gaussian's t_i =
+// (c_i/n) r_i - c_i w_i), exp is the table-driven exp_tang64 (ten FP64
+// operations) and the peak's 1/prod is rcp_nr64 (three) instead of a division.
+// The coordinate numerators stay exact integers; only the rounding of the
+// argument's terms differs from forming x_i = r_i/n first (within a few units in
+// the last place of the argument).
 template <int FAM, bool FP32EVAL, int MAXD, bool SHIFT = false>
 __global__ void __launch_bounds__(kSlrThreads) slr_kernel(const __grid_constant__ SlrArgs args,
                                                           const double *__restrict__ params,
                                                           double *__restrict__ partials,
                                                           const double *__restrict__ shifts = nullptr) {
+  constexpr bool FAST = !FP32EVAL && !SHIFT && FAM != MDI_FAM_OSC;
   __shared__ double s_c[MAXD], s_w[MAXD], s_ic2[MAXD];
   __shared__ double s_dx[SHIFT ? MAXD : 1];
+  __shared__ double s_cn[FAST ? MAXD : 1], s_cw[FAST ? MAXD : 1];
+  __shared__ double s_exp2d[FAST && FAM != MDI_FAM_PEAK ? kExpTable : 1];
   __shared__ double s_red[kSlrThreads / kWarp];
   constexpr int kUnroll = MAXD <= 32 ? MAXD : 1;  // the wide bucket keeps r[] in local memory
   const int d = args.d;
@@ -49,7 +62,13 @@ __global__ void __launch_bounds__(kSlrThreads) slr_kernel(const __grid_constant_
     s_w[i] = params[d + i];
     s_ic2[i] = 1.0 / (params[i] * params[i]);
     if constexpr (SHIFT) s_dx[i] = shifts[(size_t)blockIdx.y * d + i];
+    if constexpr (FAST) {
+      s_cn[i] = params[i] * args.inv_n;
+      s_cw[i] = params[i] * params[d + i];
+    }
   }
+  if constexpr (FAST && FAM != MDI_FAM_PEAK)
+    for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s_exp2d[j] = kExp2TableD[j];
   if constexpr (SHIFT) partials += (size_t)blockIdx.y * gridDim.x;
   __syncthreads();
   // Coordinate i of the current point: r_i / n, shifted and wrapped into [0, 1).
@@ -77,7 +96,37 @@ __global__ void __launch_bounds__(kSlrThreads) slr_kernel(const __grid_constant_
   double acc = 0.0;
   for (uint64_t j = j0; j < j1; ++j) {
     double f;
-    if constexpr (FAM == MDI_FAM_PEAK) {
+    if constexpr (FAST) {
+      if constexpr (FAM == MDI_FAM_PEAK) {
+        double p = 1.0, den = 1.0;
+#pragma unroll(kUnroll)
+        for (int i = 0; i < MAXD; ++i) {
+          if (i < d) {
+            const double t = fma((double)r[i], args.inv_n, -s_w[i]);
+            den *= fma(t, t, s_ic2[i]);
+            if ((i & 7) == 7) {
+              p *= rcp_nr64(den);
+              den = 1.0;
+            }
+          }
+        }
+        f = p * rcp_nr64(den);
+      } else {
+        double sarg = 0.0;
+#pragma unroll(kUnroll)
+        for (int i = 0; i < MAXD; ++i) {
+          if (i < d) {
+            if constexpr (FAM == MDI_FAM_GAUSS) {
+              const double t = fma(s_cn[i], (double)r[i], -s_cw[i]);
+              sarg = fma(t, t, sarg);
+            } else {
+              sarg = fma(s_cn[i], (double)r[i], sarg);
+            }
+          }
+        }
+        f = exp_tang64(FAM == MDI_FAM_GAUSS ? -sarg : sarg, s_exp2d);
+      }
+    } else if constexpr (FAM == MDI_FAM_PEAK) {
       double p = 1.0, den = 1.0;
 #pragma unroll(kUnroll)
       for (int i = 0; i < MAXD; ++i) {
