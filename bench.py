@@ -538,6 +538,9 @@ def extra_time_to_1e6_vs_d(torch, mdi, inputs, dims=(4, 6, 8, 10, 12, 16, 20, 24
 TRAFFIC_SOURCES = ["paper_2404_08867_gb300/csrc/mdi_nodes.cu", "paper_2404_08867_gb300/csrc/mdi_nodes.cuh",
                    "paper_2404_08867_gb300/csrc/mdi_common.cuh", "paper_2404_08867_gb300/csrc/mdi_fp64.cuh"]
 PROFILED_TRAFFIC = {"fp64": ("17fe4096f9049691", 1703424)}
+# The same capture's FP64 pipe utilisation (sm__inst_executed_pipe_fp64, percent of
+# peak over the active cycles and over the elapsed time), under the same key.
+PROFILED_PIPE = {"fp64": ("17fe4096f9049691", 0.911, 0.875)}
 
 
 def kernel_sources_key() -> str:
@@ -558,6 +561,13 @@ def kernel_sources_key() -> str:
 def profiled_traffic(precision: str):
     entry = PROFILED_TRAFFIC.get(precision)
     return entry[1] if entry is not None and kernel_sources_key() == entry[0] else None
+
+
+def profiled_pipe(precision: str):
+    """(active, elapsed) FP64-pipe utilisation of the capture, or None once the
+    kernel sources have changed since it was taken."""
+    entry = PROFILED_PIPE.get(precision)
+    return entry[1:] if entry is not None and kernel_sources_key() == entry[0] else None
 
 
 def extra_batch_vs_plain(torch, mdi, inputs):
@@ -966,6 +976,8 @@ def build_case(name):
       closed-d1000    closed state forward, exp(sum x_j / j^2), d = 1000, N = 16, FP64
       slr-d4          plain lattice rule, f = exp(sum x_j / j), d = 4, n = 65536,
                       Korobov a = 11119 (the small workload's error-scanned parameter)
+      slr-d7          plain lattice rule in FP64, f = exp(sum x_j / j), d = 7, n = 2^24,
+                      Korobov a = 12345
       slr-df-d7       plain lattice rule in double-float, f = exp(sum x_j / j), d = 7,
                       n = 2^24, Korobov a = 12345
       improved-d7     improved lattice rule, d = 7, z = (1, 16, .., 16^6), n = 1 + 16^7
@@ -1016,6 +1028,10 @@ def build_case(name):
         p = torch.as_tensor(inputs.small_exp(4).params).cuda()
         z = mdi.korobov_vector(4, 11119, 65536)
         return lambda: mdi.lattice_rule_integrate("exp", p, 65536, z)
+    if name == "slr-d7":
+        p = torch.as_tensor(inputs.small_exp(7).params).cuda()
+        z = mdi.korobov_vector(7, 12345, 1 << 24)
+        return lambda: mdi.lattice_rule_integrate("exp", p, 1 << 24, z)
     if name == "slr-df-d7":
         p = torch.as_tensor(inputs.small_exp(7).params).cuda()
         z = mdi.korobov_vector(7, 12345, 1 << 24)
@@ -1132,6 +1148,10 @@ def main():
     if rank == 0:
         kernel_ms = statistics.mean(step_ms)
         roof = roofline_entry(b, args.precision, kernel_ms, peaks, profiled_traffic(args.precision))
+        pipe = profiled_pipe(args.precision)
+        if pipe is not None:
+            roof["pipe_busy_ncu"] = {"active": pipe[0], "elapsed": pipe[1],
+                                     "metric": "sm__inst_executed_pipe_fp64 (pct of peak), ncu capture in profiles/"}
         dtype = {"df64": "f32x2 (double-float, FP64-class)", "fp64": "f64", "fp32_eval_fp64": "f32 eval + f64",
                  "fp32_eval_df32": "f32 eval + f32x2"}[args.precision]
         line = {"metric": METRIC, "value": value, "unit": "integrals/s", "n_gpus": world, "steps": args.steps,
