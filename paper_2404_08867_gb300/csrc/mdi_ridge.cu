@@ -253,11 +253,12 @@ mdi_status ridge_launch(int d, int64_t N, int64_t n_last, double c0, double p, d
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
     const cudaError_t e = cudaLaunchKernelEx(&cfg, ridge_cluster_kernel, d, (int)N, (int)W, 1.0 / (double)N, buf[0]);
-    if (e != cudaSuccess) {
-      set_cuda_error(e);
-      return MDI_ECUDA;
+    if (e != cudaSuccess) {  // a cluster the GPU refuses now: the per-level launches below
+      cudaGetLastError();
+      cs = 0;
     }
-  } else {
+  }
+  if (cs == 0) {
     ridge_init_kernel<<<1, 1, 0, stream>>>(buf[0]);
     if ((st = check_launch()) != MDI_OK) return st;
     len = 1;
