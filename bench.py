@@ -795,7 +795,25 @@ def extra_differentiation(torch, mdi, inputs):
         fdn = mdi.mdi_lr_integrate("gauss", torch.as_tensor(dn).cuda(), 100, 16, state="nodes").item()
         fd[i] = (fu - fdn) / (2 * h)
     exact = exact_gauss_grad(100, w.c, w.w)
+    # The torch.autograd path a user takes: value and backward through the MDILR
+    # Function (its forward runs the adjoint call once), CUDA events around eager
+    # calls, so the host's Python and launch overhead is included.
+    pa = p.clone().requires_grad_(True)
+    for _ in range(3):
+        mdi.mdi_lr("gauss", pa, 100, 16, state="nodes", checkpoint=10).backward()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record()
+    for _ in range(reps):
+        pa.grad = None
+        mdi.mdi_lr("gauss", pa, 100, 16, state="nodes", checkpoint=10).backward()
+    e1.record()
+    torch.cuda.synchronize()
+    auto_ms = e0.elapsed_time(e1) / reps
+    auto_err = float(np.max(np.abs(pa.grad.cpu().numpy() - gref) / np.abs(gref)))
     return {"workload": "d=100, N=16 Gaussian, 200 parameters, checkpoint 10", "adjoint_ms": ms, "forward_ms": fwd_ms,
+            "autograd_forward_backward_ms_eager": auto_ms, "autograd_grad_max_componentwise_rel_err_vs_oracle": auto_err,
             "grad_max_componentwise_rel_err_vs_oracle": float(np.max(np.abs(g - gref) / np.abs(gref))),
             "value_rel_err_vs_oracle": abs(val.item() - ref["value"]) / abs(ref["value"]),
             "grad_err_vs_central_fd_normwise": float(np.max(np.abs(g - fd)) / np.max(np.abs(fd))),

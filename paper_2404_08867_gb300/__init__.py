@@ -287,22 +287,35 @@ def mdi_lr_grad(family, params: torch.Tensor, d: int, a: int, n_last: Optional[i
 
 
 class MDILR(torch.autograd.Function):
-    """Differentiable MDI-LR value: the forward pass runs the sweep, the backward
-    pass runs the adjoint sweep (levels in reverse, states recomputed from
-    checkpoints) and scales the parameter gradient by the incoming gradient."""
+    """Differentiable MDI-LR value.  When the parameters need a gradient and the
+    call is in FP64 (the adjoint's arithmetic), the forward pass runs the adjoint
+    call itself -- one sweep forward with checkpoints, the levels in reverse,
+    states recomputed from the checkpoints -- which returns the value and dQ/dtheta
+    together, and keeps only the 2d-long gradient; the backward pass scales it by
+    the incoming gradient.  Otherwise the forward pass runs the plain sweep and the
+    backward pass the adjoint call."""
 
     @staticmethod
     def forward(ctx, params, family, d, a, n_last, opts):
-        ctx.save_for_backward(params)
         ctx.meta = (family, d, a, n_last, dict(opts))
-        return mdi_lr_integrate(family, params.detach().contiguous(), d, a, n_last, **opts).reshape(())
+        p = params.detach().contiguous()
+        if ctx.needs_input_grad[0] and opts.get("precision", "fp64") == "fp64":
+            value, g = mdi_lr_grad(family, p, d, a, n_last, **opts)
+            ctx.save_for_backward(g)
+            ctx.fused = True
+            return value.reshape(())
+        ctx.save_for_backward(params)
+        ctx.fused = False
+        return mdi_lr_integrate(family, p, d, a, n_last, **opts).reshape(())
 
     @staticmethod
     def backward(ctx, grad_out):
-        (params,) = ctx.saved_tensors
+        (saved,) = ctx.saved_tensors
+        if ctx.fused:
+            return saved * grad_out, None, None, None, None, None
         family, d, a, n_last, opts = ctx.meta
         opts = {k: v for k, v in opts.items() if k != "precision"}
-        _, g = mdi_lr_grad(family, params.detach().contiguous(), d, a, n_last, **opts)
+        _, g = mdi_lr_grad(family, saved.detach().contiguous(), d, a, n_last, **opts)
         return g * grad_out, None, None, None, None, None
 
 

@@ -131,6 +131,26 @@ def test_autograd_function_backward_runs_the_adjoint():
     assert abs(q.item() - o.mdi_nodes("gauss", 30, 16, 16, 16, w.c, w.w)) <= TOL * abs(q.item())
 
 
+def test_autograd_fused_forward_and_the_two_call_path_agree():
+    """With a gradient needed (FP64) the forward pass runs the adjoint call once and
+    keeps its gradient; without one, or in another precision, the forward pass is
+    the plain sweep and the backward pass runs the adjoint call.  Both give the
+    same value (to the parity tolerance) and the adjoint's gradient."""
+    w = inputs.gaussian(12, 16, seed=5)
+    _, g_ref = mdi.mdi_lr_grad("gauss", dev(w.params), 12, 16, 16, state="nodes")
+    p = dev(w.params).requires_grad_(True)
+    q_fused = mdi.mdi_lr("gauss", p, 12, 16, state="nodes")
+    q_fused.backward()
+    torch.testing.assert_close(p.grad, g_ref, rtol=0, atol=0)
+    q_plain = mdi.mdi_lr("gauss", dev(w.params), 12, 16, state="nodes")  # no gradient needed
+    assert abs(q_fused.item() - q_plain.item()) <= TOL * abs(q_plain.item())
+    p2 = dev(w.params).requires_grad_(True)
+    q_df = mdi.mdi_lr("gauss", p2, 12, 16, state="nodes", precision="df64")  # backward: the FP64 adjoint
+    q_df.backward()
+    torch.testing.assert_close(p2.grad, g_ref, rtol=0, atol=0)
+    assert abs(q_df.item() - q_plain.item()) <= TOL * abs(q_plain.item())
+
+
 def test_autograd_matches_device_central_differences():
     w = inputs.oscillatory(20, 16, seed=3)
     p = dev(w.params).requires_grad_(True)
