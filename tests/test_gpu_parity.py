@@ -346,6 +346,33 @@ def test_batched_full_size_in_the_bench_launch_configuration(prec):
     assert_batch_close(out, oracle_batch(4096, 0), TOL)
 
 
+@pytest.mark.parametrize("prec,block,split,cps", [("fp64", 32, None, 10), ("fp64", 64, 0, 5), ("fp64", 64, 40, 0),
+                                                  ("df64", 32, None, 0), ("df64", 64, 40, 0)])
+def test_batched_centres_outside_the_unit_interval(prec, block, split, cps):
+    """Gaussian and peak factors centred outside [0, 1] (w in [-2, 3]): the FP64
+    sweep's Gaussian recurrence guard bounds |t| by |c| (max(|w|, |1 - w|) + 1/a + 1)
+    and falls back to the direct exp where that bound is large; every output
+    against the oracle within 1e-12, on one- and two-warp teams and the fewer-
+    workers shape.  (DF64: c <= 2.5 keeps c^2 (x - w)^2 within the mode's 80.)"""
+    rng = np.random.default_rng(31)
+    count = 160
+    fams = ["gauss" if i % 2 == 0 else "peak" for i in range(count)]
+    ds = rng.integers(3, 13, count)
+    as_ = rng.choice([8, 9, 16, 24, 32], count)
+    cmax = 2.5 if prec == "df64" else 3.0
+    pool = np.concatenate([np.r_[rng.uniform(0.5, cmax, d), rng.uniform(-2.0, 3.0, d)] for d in ds])
+    offs = np.concatenate([[0], np.cumsum(2 * ds[:-1])])
+    descs = mdi.make_batch_descs(fams, ds, as_, as_, offs)
+    d_descs = torch.from_numpy(descs.view(np.uint8)).cuda()
+    sp = count if split is None else split
+    out = mdi.mdi_lr_integrate_batched(d_descs, dev(pool), count, split=sp, precision=prec, block=block,
+                                       table_in_l1=1, ctas_per_sm=cps).cpu().numpy()
+    for i in range(count):
+        d, a = int(ds[i]), int(as_[i])
+        p = pool[offs[i]:offs[i] + 2 * d]
+        close(out[i], o.mdi_nodes(fams[i], d, a, a, 16, p[:d], p[d:]), fams[i])
+
+
 @pytest.mark.parametrize("prec", ["fp32_eval_fp64", "fp32_eval_df32"])
 def test_batched_single_precision_evaluation_modes(prec):
     # The paired sweeps evaluate phi in float at the float coordinate (q + xi_p)/a:
