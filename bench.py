@@ -537,10 +537,16 @@ def extra_time_to_1e6_vs_d(torch, mdi, inputs, dims=(4, 6, 8, 10, 12, 16, 20, 24
 # is repeated.
 TRAFFIC_SOURCES = ["paper_2404_08867_gb300/csrc/mdi_nodes.cu", "paper_2404_08867_gb300/csrc/mdi_nodes.cuh",
                    "paper_2404_08867_gb300/csrc/mdi_common.cuh", "paper_2404_08867_gb300/csrc/mdi_fp64.cuh"]
-PROFILED_TRAFFIC = {"fp64": ("17fe4096f9049691", 1703424)}
-# The same capture's FP64 pipe utilisation (sm__inst_executed_pipe_fp64, percent of
-# peak over the active cycles and over the elapsed time), under the same key.
-PROFILED_PIPE = {"fp64": ("17fe4096f9049691", 0.911, 0.875)}
+PROFILED_TRAFFIC = {"fp64": ("17fe4096f9049691", 1703424), "df64": ("17fe4096f9049691", 1754112)}
+# The same captures' pipe utilisation (fractions of peak over the SMs' active
+# cycles, or the elapsed time where stated), under the same key: the FP64 mode is
+# bound by the FP64 pipe, the double-float mode by instruction issue.
+PROFILED_PIPE = {
+    "fp64": ("17fe4096f9049691", {"fp64_pipe_active": 0.911, "fp64_pipe_elapsed": 0.875,
+                                  "metric": "sm__inst_executed_pipe_fp64"}),
+    "df64": ("17fe4096f9049691", {"issue_active": 0.638, "fma_pipe_active": 0.532,
+                                  "metric": "smsp__issue_active, sm__pipe_fma_cycles_active"}),
+}
 
 
 def kernel_sources_key() -> str:
@@ -564,10 +570,12 @@ def profiled_traffic(precision: str):
 
 
 def profiled_pipe(precision: str):
-    """(active, elapsed) FP64-pipe utilisation of the capture, or None once the
-    kernel sources have changed since it was taken."""
+    """The capture's pipe utilisation for this mode, or None once the kernel
+    sources have changed since it was taken."""
     entry = PROFILED_PIPE.get(precision)
-    return entry[1:] if entry is not None and kernel_sources_key() == entry[0] else None
+    if entry is None or kernel_sources_key() != entry[0]:
+        return None
+    return dict(entry[1], source="ncu capture summarised in profiles/")
 
 
 def extra_batch_vs_plain(torch, mdi, inputs):
@@ -980,6 +988,8 @@ def build_case(name):
       batch-fp64-w10  the same on 5 two-warp CTAs per SM (10 warps), one warp per
                       integral (the tuner's choice for this batch)
       batch-df64      the same batch, double-float node state (block 32, table via L1)
+      batch-df64-w12  the same on 6 two-warp CTAs per SM, the 102 largest integrals on
+                      whole CTAs (the tuner's choice for this batch)
       batch-f32df     the same batch, phi in float, double-float sums (block 32)
       levels-d100     one integral, node state parallel over levels, the differentiation
                       workload (d = 100, N = 16 Gaussian, checkpoint 10): forward and adjoint
@@ -1012,6 +1022,8 @@ def build_case(name):
         return _case_batch("fp64", 64, ctas_per_sm=5, split=0)
     if name == "batch-df64":
         return _case_batch("df64", 32)
+    if name == "batch-df64-w12":
+        return _case_batch("df64", 64, ctas_per_sm=6, split=102)
     if name == "batch-f32df":
         return _case_batch("fp32_eval_df32", 32)
     if name == "levels-d100":
@@ -1168,8 +1180,7 @@ def main():
         roof = roofline_entry(b, args.precision, kernel_ms, peaks, profiled_traffic(args.precision))
         pipe = profiled_pipe(args.precision)
         if pipe is not None:
-            roof["pipe_busy_ncu"] = {"active": pipe[0], "elapsed": pipe[1],
-                                     "metric": "sm__inst_executed_pipe_fp64 (pct of peak), ncu capture in profiles/"}
+            roof["pipe_busy_ncu"] = pipe
         dtype = {"df64": "f32x2 (double-float, FP64-class)", "fp64": "f64", "fp32_eval_fp64": "f32 eval + f64",
                  "fp32_eval_df32": "f32 eval + f32x2"}[args.precision]
         line = {"metric": METRIC, "value": value, "unit": "integrals/s", "n_gpus": world, "steps": args.steps,
@@ -1197,9 +1208,12 @@ def main():
                 modes[prec] = {"ms_per_step": ms, "integrals_per_s": len(b) / (ms / 1e3), "block": mt["block"],
                                "table_in_l1": mt["table_in_l1"], "split": mt["split"],
                                "ctas_per_sm": mt["ctas_per_sm"],
-                               "roofline": {k: v for k, v in roofline_entry(b, prec, ms, peaks).items()
+                               "roofline": {k: v for k, v in roofline_entry(b, prec, ms, peaks,
+                                                                           profiled_traffic(prec)).items()
                                             if k in ("achieved", "peak", "frac", "pipe", "impl_tflops",
-                                                     "flops_formula")}}
+                                                     "flops_formula", "traffic")}}
+                if profiled_pipe(prec) is not None:
+                    modes[prec]["roofline"]["pipe_busy_ncu"] = profiled_pipe(prec)
             line["modes"] = modes
             line["small_workload"] = extra_small_workload(torch, mdi, inputs)
             line["precision_workload"] = extra_precision(torch, mdi, inputs)
