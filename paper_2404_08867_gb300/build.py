@@ -88,9 +88,75 @@ def exp64_constants_source() -> str:
             "static __device__ const double kExp2TableD[256] = {\n" + "\n".join(rows) + "\n};\n")
 
 
+def _dec_pi(ctx):
+    """pi by Machin's formula, 16 atan(1/5) - 4 atan(1/239), in the context's precision."""
+    import decimal
+
+    def atan_inv(x):
+        x = decimal.Decimal(x)
+        term = ctx.divide(decimal.Decimal(1), x)
+        x2 = x * x
+        total, k, sign = term, 1, -1
+        while True:
+            term = ctx.divide(term, x2)
+            t = ctx.divide(term, decimal.Decimal(2 * k + 1))
+            if t == 0:
+                return total
+            total = ctx.add(total, t if sign > 0 else -t)
+            k, sign = k + 1, -sign
+
+    return ctx.subtract(ctx.multiply(16, atan_inv(5)), ctx.multiply(4, atan_inv(239)))
+
+
+def _dec_cos_sin(theta, ctx):
+    """cos and sin of theta (|theta| <= pi) by their Taylor series in the context's
+    precision (the terms fall below 10^-60 well before the 80th)."""
+    import decimal
+    c = s = decimal.Decimal(0)
+    term = decimal.Decimal(1)  # theta^k / k!
+    for k in range(0, 160):
+        if k % 4 == 0:
+            c = ctx.add(c, term)
+        elif k % 4 == 1:
+            s = ctx.add(s, term)
+        elif k % 4 == 2:
+            c = ctx.subtract(c, term)
+        else:
+            s = ctx.subtract(s, term)
+        term = ctx.divide(ctx.multiply(term, theta), decimal.Decimal(k + 1))
+    return c, s
+
+
+def cheb_table_source(pmax: int = 32) -> str:
+    """Chebyshev points of the first kind on [0, 1] and their barycentric weights,
+    xi_p = (1 + cos(theta_p)) / 2 and bw_p = (-1)^p sin(theta_p), theta_p =
+    pi (2p + 1) / (2P), for every P = 1..pmax, from these definitions in 60-digit
+    decimal arithmetic, each rounded once to double; the entries of P start at
+    P (P - 1) / 2.  No kernel evaluates them in FP64 at run time."""
+    import decimal
+    ctx = decimal.Context(prec=70)
+    pi = _dec_pi(ctx)
+    xs, ws = [], []
+    for P in range(1, pmax + 1):
+        for p in range(P):
+            theta = ctx.divide(ctx.multiply(pi, decimal.Decimal(2 * p + 1)), decimal.Decimal(2 * P))
+            c, s = _dec_cos_sin(theta, ctx)
+            xs.append(float(ctx.divide(ctx.add(decimal.Decimal(1), c), decimal.Decimal(2))))
+            ws.append(float(s if p % 2 == 0 else -s))
+    n = len(xs)
+    body_x = "\n".join(f"    {v.hex()}," for v in xs)
+    body_w = "\n".join(f"    {v.hex()}," for v in ws)
+    return ("// Generated by build.py: Chebyshev points of the first kind on [0, 1] and their\n"
+            f"// barycentric weights for P = 1..{pmax}; the entries of P start at P (P - 1) / 2.\n"
+            f"static constexpr int kChebTablePMax = {pmax};\n"
+            f"static __device__ const double kChebXiGen[{n}] = {{\n{body_x}\n}};\n"
+            f"static __device__ const double kChebBwGen[{n}] = {{\n{body_w}\n}};\n")
+
+
 def _write_generated():
     os.makedirs(GEN, exist_ok=True)
     _write_if_changed(os.path.join(GEN, "mdi_exp64_consts.inc"), exp64_constants_source())
+    _write_if_changed(os.path.join(GEN, "mdi_cheb_table.inc"), cheb_table_source())
     path = os.path.join(GEN, "mdi_exp2_table.inc")
     src = exp2_table_source()
     if not os.path.exists(path) or open(path).read() != src:

@@ -32,10 +32,65 @@
 
 #include "mdi_common.cuh"
 #include "mdi_exp2_table.inc"
+#include "mdi_fp64.cuh"
 #include "mdi_internal.h"
 #include "mdi_nodes.cuh"
 
 namespace mdi {
+
+// FP64 pieces of the level kernels, built on the sweep's own exp and reciprocal
+// (GB300's FP64 unit takes a warp instruction per ~64 cycles per sub-partition, and
+// the library exp and IEEE division take several times their instruction count).
+
+// 1/D for any D: the reciprocal of |D| with D's sign.
+__device__ __forceinline__ double rcp_signed64(double D) {
+  const double r = rcp_nr64(__hiloint2double(__double2hiint(D) & 0x7FFFFFFF, __double2loint(D)));
+  return __hiloint2double(__double2hiint(r) ^ (__double2hiint(D) & (int)0x80000000), __double2loint(r));
+}
+
+// c_j, w_j and 1/c_j^2 of axis j (the reciprocal as rcp_nr64).
+__device__ __forceinline__ AxisParams load_axis_lv(const double *params, int d, int j) {
+  AxisParams p;
+  p.c = params[j];
+  p.w = params[d + j];
+  p.ic2 = rcp_nr64(p.c * p.c);
+  return p;
+}
+
+// phi_j(u): the formulas of phi64 with the own exp (table T) and reciprocal; in
+// float when F32; OSC by sincos.
+template <int FAM, bool F32>
+__device__ __forceinline__ typename FamTraits<FAM>::V phi_lv(double u, const AxisParams &p, const double *T) {
+  if constexpr (F32 || FAM == MDI_FAM_OSC) {
+    return phi<FAM, F32>(u, p);
+  } else if constexpr (FAM == MDI_FAM_EXP) {
+    return exp_tang64(p.c * u, T);
+  } else if constexpr (FAM == MDI_FAM_GAUSS) {
+    const double t = p.c * (u - p.w);
+    return exp_tang64(-t * t, T);
+  } else {
+    const double t = u - p.w;
+    return rcp_nr64(fma(t, t, p.ic2));
+  }
+}
+
+// phi_j and its derivatives in c_j and w_j (the formulas of phi_grad64) with the
+// own exp and reciprocal; dcp = 2 / c_j^3, the PEAK factor of dc, per axis.
+template <int FAM>
+__device__ __forceinline__ PhiGrad<FAM> phi_grad_lv(double x, const AxisParams &p, double dcp, const double *T) {
+  if constexpr (FAM == MDI_FAM_OSC) {
+    return phi_grad64<FAM>(x, p);
+  } else if constexpr (FAM == MDI_FAM_EXP) {
+    const double e = exp_tang64(p.c * x, T);
+    return {e, x * e, 0.0};
+  } else if constexpr (FAM == MDI_FAM_GAUSS) {
+    const double t = x - p.w, e = exp_tang64(-(p.c * t) * (p.c * t), T);
+    return {e, -2.0 * p.c * t * t * e, 2.0 * p.c * p.c * t * e};
+  } else {
+    const double t = x - p.w, f = rcp_nr64(fma(t, t, p.ic2)), f2 = f * f;
+    return {f, dcp * f2, 2.0 * t * f2};
+  }
+}
 
 constexpr int kLvThreads = 256;
 constexpr int kLvMaxPts = kNodesAMax * kNodesPMax;  // a*P <= 2048
@@ -78,10 +133,10 @@ static int default_checkpoint(int d) {
 }
 
 // K0: L[t][q*P + p] = l_t((q + xi_p)/a) for one a.  One warp per point u: lane t
-// forms bw_t / (u - xi_t), a shuffle sum gives the denominator, so each lane does
-// two FP64 divisions (the FP64 unit is the scarce one on this chip); the nodes and
-// weights are computed once per CTA.  DF writes each value as a float pair into
-// the same 8-byte slot (the compensated double-float build reads it so).
+// forms bw_t / (u - xi_t), a shuffle sum gives the denominator, so each lane takes
+// two reciprocals (rcp_nr64: the FP64 unit is the scarce one on this chip).  DF
+// writes each value as a float pair into the same 8-byte slot (the compensated
+// double-float build reads it so).
 template <bool DF>
 __global__ void levels_table_kernel(int P, int a, double *__restrict__ L) {
   __shared__ double s_xi[kNodesPMax], s_bw[kNodesPMax];
@@ -99,11 +154,11 @@ __global__ void levels_table_kernel(int P, int a, double *__restrict__ L) {
   const bool on = lane < P;
   const double xi = on ? s_xi[lane] : 0.0;
   const unsigned hit = __ballot_sync(0xffffffffu, on && u == xi);
-  const double r = (on && !hit) ? s_bw[lane] / (u - xi) : 0.0;
+  const double r = (on && !hit) ? s_bw[lane] * rcp_signed64(u - xi) : 0.0;
   double den = r;
   for (int off = kWarp / 2; off > 0; off >>= 1) den += __shfl_xor_sync(0xffffffffu, den, off);
   if (on) {
-    const double v = hit ? (lane == __ffs(hit) - 1 ? 1.0 : 0.0) : r / den;
+    const double v = hit ? (lane == __ffs(hit) - 1 ? 1.0 : 0.0) : r * rcp_signed64(den);
     if constexpr (DF) {
       const float h = (float)v;
       reinterpret_cast<float2 *>(L)[(size_t)lane * npts + pt] = make_float2(h, (float)(v - (double)h));
@@ -143,9 +198,13 @@ __global__ void __launch_bounds__(kLvThreads) levels_build_kernel(int d, int a, 
   __shared__ float2 s_ff[DF ? kLvMaxPts : 1];
   __shared__ float4 s_fd[D64 ? kLvMaxPts : 1];  // (re.hi, re.lo, im.hi, im.lo)
   __shared__ float2 s_exp2[D64 ? kExpTable : 1];
+  constexpr bool kExp64 = !F32 && FAM != MDI_FAM_OSC;  // phi_lv's table
+  __shared__ double s_e64[kExp64 ? kExpTable : 1];
   __shared__ double2 s_part[kLvThreads];
   if constexpr (D64)
     for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s_exp2[j] = kExp2TableGen[j];
+  if constexpr (kExp64)
+    for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s_e64[j] = kExp2TableD[j];
   for (int t = threadIdx.x; t < P; t += blockDim.x) {
     s_xi[t] = cheb_node(t, P);
     s_bw[t] = cheb_weight(t, P);
@@ -153,8 +212,11 @@ __global__ void __launch_bounds__(kLvThreads) levels_build_kernel(int d, int a, 
   __syncthreads();
   const int npts = a * P;
   const double inv_a = 1.0 / (double)a;
-  for (int lev = blockIdx.x; lev < d; lev += gridDim.x) {
-    const AxisParams ap = load_axis(prm, d, lev);
+  // Block 0 takes the last level (w), whose points are the last axis' own, so that
+  // it starts in the first wave.
+  for (int b = blockIdx.x; b < d; b += gridDim.x) {
+    const int lev = b == 0 ? d - 1 : b - 1;
+    const AxisParams ap = load_axis_lv(prm, d, lev);
     if (lev < d - 1) {
       // level k = lev + 1 < d
       df32 cd{0.f, 0.f}, wd{0.f, 0.f}, icd{0.f, 0.f};
@@ -177,7 +239,7 @@ __global__ void __launch_bounds__(kLvThreads) levels_build_kernel(int d, int a, 
             s_fd[i] = make_float4(f.hi, f.lo, 0.f, 0.f);
           }
         } else {
-          const double2 f = as2(phi<FAM, F32>(u, ap));
+          const double2 f = as2(phi_lv<FAM, F32>(u, ap, s_e64));
           if constexpr (DF) s_ff[i] = make_float2((float)f.x, (float)f.y);  // float values: exact
           else s_f[i] = f;
         }
@@ -217,15 +279,29 @@ __global__ void __launch_bounds__(kLvThreads) levels_build_kernel(int d, int a, 
       }
       __syncthreads();
     } else {
-      // last level: w[t] = (1/n_last) sum_s phi_d(s/n_last) l_t(s/n_last)
-      const int rows = blockDim.x / P;
-      const int t = threadIdx.x % P, j = threadIdx.x / P;
+      // last level: w[t] = (1/n_last) sum_s phi_d(s/n_last) l_t(s/n_last), a group of
+      // GL lanes per point (lane t: l_t, by the warp-per-point scheme of K0).
+      const int GL = P <= kWarp / 2 ? kWarp / 2 : kWarp;
+      const int lane = threadIdx.x & (kWarp - 1), t = lane & (GL - 1);
+      const int per_warp = kWarp / GL, nwarps = blockDim.x / kWarp;
+      const unsigned gmask = GL == kWarp ? 0xffffffffu : (0xffffu << (lane & (kWarp / 2)));
+      const bool on = t < P;
+      const double xi = on ? s_xi[t] : 0.0, bw = on ? s_bw[t] : 0.0;
       double2 acc = make_double2(0.0, 0.0);
-      if (j < rows) {
-        for (int s = j; s < n_last; s += rows) {
-          const double u = (double)s / (double)n_last;
-          const double2 f = as2(phi<FAM, F32>(u, ap));
-          const double l = (d == 1) ? (t == 0 ? 1.0 : 0.0) : basis_at(s_xi, s_bw, P, t, u);
+      for (int base = (threadIdx.x / kWarp) * per_warp; base < n_last; base += nwarps * per_warp) {
+        const int s = base + lane / GL;  // whole warps run the loop and its shuffles
+        const bool pt = s < n_last;
+        const double u = (double)(pt ? s : 0) / (double)n_last;
+        double l = (t == 0) ? 1.0 : 0.0;  // d = 1: G_0 = 1 is constant
+        if (d > 1) {
+          const unsigned hit = __ballot_sync(0xffffffffu, on && u == xi) & gmask;
+          const double r = (on && !hit) ? bw * rcp_signed64(u - xi) : 0.0;
+          double den = r;
+          for (int off = 1; off < GL; off <<= 1) den += __shfl_xor_sync(0xffffffffu, den, off);
+          l = hit ? ((on && u == xi) ? 1.0 : 0.0) : r * rcp_signed64(den);
+        }
+        if (pt && on) {
+          const double2 f = as2(phi_lv<FAM, F32>(u, ap, s_e64));
           acc.x = fma(l, f.x, acc.x);
           if constexpr (FAM == MDI_FAM_OSC) acc.y = fma(l, f.y, acc.y);
         }
@@ -233,9 +309,9 @@ __global__ void __launch_bounds__(kLvThreads) levels_build_kernel(int d, int a, 
       s_part[threadIdx.x] = acc;
       __syncthreads();
       if (threadIdx.x < P) {
-        double2 s = make_double2(0.0, 0.0);
-        for (int r = 0; r < rows; ++r) s = c_add(s, s_part[r * P + threadIdx.x]);
-        w[threadIdx.x] = c_scale(s, 1.0 / (double)n_last);
+        double2 sum = make_double2(0.0, 0.0);
+        for (int r = 0; r < (int)blockDim.x / GL; ++r) sum = c_add(sum, s_part[r * GL + threadIdx.x]);
+        w[threadIdx.x] = c_scale(sum, 1.0 / (double)n_last);
       }
       __syncthreads();
     }
@@ -520,17 +596,24 @@ __global__ void __launch_bounds__(kChainMaxThreads) levels_chain_kernel(int d, i
     sincos(kTwoPi * prm[d], &sn, &cs);
     front = make_double2(cs, sn);
   }
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < kWarp) {  // the P terms on the lanes of warp 0, then a shuffle sum
+    const int t = threadIdx.x;
     double2 q = make_double2(0.0, 0.0);
-    for (int t = 0; t < P; ++t) q = c_add(q, c_mul(w[t], as2(s_v[vb][t])));
-    misc[0] = q;
-    const double2 fq = c_mul(front, q);
-    if (value) *value = fq.x;
-    if (adjoint && FAM == MDI_FAM_OSC) {
-      grad[d] = -kTwoPi * fq.y;  // dQ/du = Re(2 pi i front q)
-      for (int j = d + 1; j < 2 * d; ++j) grad[j] = 0.0;
+    if (t < P) {
+      if constexpr (FAM == MDI_FAM_OSC) q = c_mul(w[t], as2(s_v[vb][t]));
+      else q.x = w[t].x * as2(s_v[vb][t]).x;  // real w and G
+    }
+    if constexpr (FAM == MDI_FAM_OSC) q = warp_sum(q);
+    else q.x = warp_sum(q.x);
+    if (t == 0) {
+      misc[0] = q;
+      const double2 fq = c_mul(front, q);
+      if (value) *value = fq.x;
+      if (adjoint && FAM == MDI_FAM_OSC) grad[d] = -kTwoPi * fq.y;  // dQ/du = Re(2 pi i front q)
     }
   }
+  if (adjoint && FAM == MDI_FAM_OSC)
+    for (int j = d + 1 + (int)threadIdx.x; j < 2 * d; j += blockDim.x) grad[j] = 0.0;
   if (!adjoint) return;
   __syncthreads();
   // lambda at b_ng = d-1 is front * w (real for real families: front = 1, w real).
@@ -593,9 +676,38 @@ __device__ __forceinline__ void matvec8(const double2 *__restrict__ Op, const V 
   if (row < P && part == 0) out[row] = acc;
 }
 
-// K4: gradient of level k (block k-1, k = 1..d).  Real families run in real
-// arithmetic (the operators' imaginary parts are zero).
-template <int FAM>
+// Operator entries for the recompute products of K4: a lane holds E entries of a
+// row, E = 2 (eight lanes per row) for P <= 16 and E = 8 (four lanes per row) up to
+// P = 32, so that a G product and a lambda product run side by side in 128 threads
+// each.
+template <typename V> __device__ __forceinline__ V op_entry(const double2 *e);
+template <> __device__ __forceinline__ double op_entry<double>(const double2 *e) {
+  return reinterpret_cast<const double *>(e)[0];  // real families: the real part only
+}
+template <> __device__ __forceinline__ double2 op_entry<double2>(const double2 *e) { return *e; }
+
+// A lane's entries (row, part + j LR), j < E, of a level operator stored [t][p]:
+// not TRANSPOSE, out[p] = sum_t Op[p][t] in[t] (row p, column t at t*P + p);
+// TRANSPOSE, out[t] = sum_p in[p] Op[p][t] (row t, column p at t*P + p).
+template <typename V, bool TRANSPOSE, int E>
+__device__ __forceinline__ void op_fetch(const double2 *__restrict__ Op, int row, int part, int LR, int P, V (&e)[E]) {
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const int col = part + j * LR;
+    if (row < P && col < P) e[j] = op_entry<V>(Op + (TRANSPOSE ? row * P + col : col * P + row));
+  }
+}
+
+// K4: gradient of level k (block k-1, k = 1..d).  G_{k-1} is recomputed from the
+// checkpoint below by the first half of the CTA while the second half recomputes
+// lambda_k from the checkpoint above, one barrier per step of the longer chain; a
+// lane holds its entries of the next operator in registers while it multiplies by
+// the current one, so no step waits on an L2 round trip.  The phi derivatives at
+// the CTA's first points do not depend on the states: they are evaluated before the
+// chains, and their FP64 work fills the pipe while the products wait on one
+// another.  Real families run in real arithmetic (the operators' imaginary parts
+// are zero).
+template <int FAM, int E>
 __global__ void __launch_bounds__(kLvThreads) levels_grad_kernel(int d, int a, int n_last, int P, int C,
                                                                  const double *__restrict__ prm,
                                                                  const double *__restrict__ L,
@@ -604,13 +716,21 @@ __global__ void __launch_bounds__(kLvThreads) levels_grad_kernel(int d, int a, i
                                                                  const double2 *__restrict__ lck,
                                                                  double *__restrict__ grad) {
   using V = typename FamTraits<FAM>::V;
+  using O = VOps<V>;
+  constexpr bool kExp64 = FAM != MDI_FAM_OSC;
+  constexpr int kHalf = kLvThreads / 2;
+  constexpr int LR = E == 2 ? 8 : 4;  // lanes per row
   __shared__ double s_xi[kNodesPMax], s_bw[kNodesPMax];
+  __shared__ double s_e64[kExp64 ? kExpTable : 1];
   __shared__ V s_g[2][kNodesPMax], s_l[2][kNodesPMax];
-  __shared__ V s_red[kLvThreads / kWarp];
+  __shared__ double2 s_red[kLvThreads / kWarp];
   for (int t = threadIdx.x; t < P; t += blockDim.x) {
     s_xi[t] = cheb_node(t, P);
     s_bw[t] = cheb_weight(t, P);
   }
+  if constexpr (kExp64)
+    for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s_e64[j] = kExp2TableD[j];
+  __syncthreads();
   const int ng = (d - 1 + C - 1) / C;
   const int npts = a * P;
   const double inv_a = 1.0 / (double)a;
@@ -621,60 +741,92 @@ __global__ void __launch_bounds__(kLvThreads) levels_grad_kernel(int d, int a, i
     front = make_double2(cs, sn);
   }
   const int tid = threadIdx.x;
+  const int side = tid / kHalf, li = tid % kHalf;  // side 0: G, side 1: lambda
+  const int row = li / LR, part = li % LR;
   for (int k = blockIdx.x + 1; k <= d; k += gridDim.x) {
-    // G_{k-1} from the checkpoint at or below it (ping-pong buffers).
-    const int j0 = (k - 1) / C;
-    int cg = 0;
-    if (tid < P) s_g[0][tid] = from2<V>(gck[(size_t)j0 * P + tid]);
-    __syncthreads();
-    for (int m = j0 * C + 1; m <= k - 1; ++m) {
-      matvec8<V, false>(M + (size_t)(m - 1) * P * P, s_g[cg], s_g[cg ^ 1], P);
-      cg ^= 1;
-      __syncthreads();
+    const AxisParams ap = load_axis_lv(prm, d, k - 1);
+    const double dcp = 2.0 * ap.ic2 * rcp_signed64(ap.c);  // PEAK: d phi / dc = (2 / c^3) phi^2
+    // Level k < d reads the points (q + xi_p)/a, level d the points s/n_last.
+    const int npt = k < d ? npts : n_last;
+    PhiGrad<FAM> pg0{};
+    double u0 = 0.0;
+    if (tid < npt) {
+      u0 = k < d ? ((double)(tid / P) + s_xi[tid % P]) * inv_a : (double)tid / (double)n_last;
+      pg0 = phi_grad_lv<FAM>(u0, ap, dcp, s_e64);
     }
-    const V *g_k = s_g[cg];
-    V acc_c = VOps<V>::zero(), acc_w = VOps<V>::zero();
-    const AxisParams ap = load_axis(prm, d, k - 1);
+    // The chains: G over the operators j0 C + 1 .. k - 1, lambda over top .. k + 1.
+    const int j0 = (k - 1) / C, nG = (k - 1) - j0 * C;
+    int top = 0, nL = 0;
+    const double2 *lsrc = nullptr;
     if (k < d) {
-      // lambda_k from the checkpoint at or above it.
-      int top = ((k + C - 1) / C) * C;
-      const double2 *src;
+      top = ((k + C - 1) / C) * C;
       if (top > d - 1) {
         top = d - 1;
-        src = lck + (size_t)ng * P;
+        lsrc = lck + (size_t)ng * P;
       } else {
-        src = lck + (size_t)(top / C) * P;
+        lsrc = lck + (size_t)(top / C) * P;
       }
-      int cl = 0;
-      if (tid < P) s_l[0][tid] = from2<V>(src[tid]);
-      __syncthreads();
-      for (int m = top; m >= k + 1; --m) {
-        matvec8<V, true>(M + (size_t)(m - 1) * P * P, s_l[cl], s_l[cl ^ 1], P);
-        cl ^= 1;
-        __syncthreads();
-      }
-      const V *l_k = s_l[cl];
-      for (int i = tid; i < npts; i += blockDim.x) {
-        const int q = i / P, p = i % P;
-        const double u = ((double)q + s_xi[p]) * inv_a;
-        const PhiGrad<FAM> pg = phi_grad64<FAM>(u, ap);
-        V g = VOps<V>::one();
-        if (k > 1) {
-          g = VOps<V>::zero();
-          for (int t = 0; t < P; ++t) g = VOps<V>::fma_s(L[(size_t)t * npts + i], g_k[t], g);
+      nL = top - k;
+    }
+    const int mine = side ? nL : nG;
+    const size_t pp = (size_t)P * P;
+    auto op_at = [&](int st) { return side ? M + (size_t)(top - 1 - st) * pp : M + (size_t)(j0 * C + st) * pp; };
+    auto fetch = [&](int st, V(&e)[E]) {
+      if (side) op_fetch<V, true, E>(op_at(st), row, part, LR, P, e);
+      else op_fetch<V, false, E>(op_at(st), row, part, LR, P, e);
+    };
+    V cur[E], nxt[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) cur[j] = nxt[j] = O::zero();
+    if (mine > 0) fetch(0, cur);
+    if (tid < P) s_g[0][tid] = from2<V>(gck[(size_t)j0 * P + tid]);
+    if (k < d && side && li < P) s_l[0][li] = from2<V>(lsrc[li]);
+    __syncthreads();
+    const int nsteps = max(nG, nL);
+    for (int st = 0; st < nsteps; ++st) {
+      if (st < mine) {  // the same in every lane of a warp
+        if (st + 1 < mine) fetch(st + 1, nxt);
+        const V *in = side ? s_l[st & 1] : s_g[st & 1];
+        V acc = O::zero();
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          const int col = part + j * LR;
+          if (row < P && col < P) {
+            if constexpr (FAM == MDI_FAM_OSC) acc = c_add(acc, c_mul(cur[j], in[col]));
+            else acc = fma(cur[j], in[col], acc);
+          }
         }
-        const V lg = VOps<V>::mul(l_k[p], g);
-        acc_c = VOps<V>::add(acc_c, VOps<V>::mul(lg, pg.dc));
-        acc_w = VOps<V>::add(acc_w, VOps<V>::mul(lg, pg.dw));
+        acc = group_sum(acc, LR);
+        if (row < P && part == 0) (side ? s_l[(st & 1) ^ 1] : s_g[(st & 1) ^ 1])[row] = acc;
+#pragma unroll
+        for (int j = 0; j < E; ++j) cur[j] = nxt[j];
       }
+      __syncthreads();
+    }
+    const V *g_k = s_g[nG & 1];
+    const V *l_k = s_l[nL & 1];
+    V acc_c = O::zero(), acc_w = O::zero();
+    if (k < d) {
+      // dQ/dtheta_k = (1/a) sum_{q,p} lambda_k[p] dphi_k(u_qp)/dtheta G~_{k-1}(u_qp)
+      auto contract = [&](int i, const PhiGrad<FAM> &pg) {
+        V g = O::one();
+        if (k > 1) {
+          g = O::zero();
+          for (int t = 0; t < P; ++t) g = O::fma_s(L[(size_t)t * npts + i], g_k[t], g);
+        }
+        const V lg = O::mul(l_k[i % P], g);
+        acc_c = O::add(acc_c, O::mul(lg, pg.dc));
+        acc_w = O::add(acc_w, O::mul(lg, pg.dw));
+      };
+      if (tid < npts) contract(tid, pg0);
+      for (int i = tid + blockDim.x; i < npts; i += blockDim.x)
+        contract(i, phi_grad_lv<FAM>(((double)(i / P) + s_xi[i % P]) * inv_a, ap, dcp, s_e64));
     } else {
       // last level: dQ/dtheta_d = Re(front (1/n_last) sum_s dphi_d(s/n_last) G~_{d-1}(s/n_last))
-      for (int s = tid; s < n_last; s += blockDim.x) {
-        const double u = (double)s / (double)n_last;
-        const PhiGrad<FAM> pg = phi_grad64<FAM>(u, ap);
-        V g = VOps<V>::one();
+      auto contract = [&](double u, const PhiGrad<FAM> &pg) {
+        V g = O::one();
         if (d > 1) {
-          V num = VOps<V>::zero();
+          V num = O::zero();
           double den = 0.0;
           int hit = -1;
           for (int t = 0; t < P; ++t) {
@@ -682,23 +834,30 @@ __global__ void __launch_bounds__(kLvThreads) levels_grad_kernel(int d, int a, i
               hit = t;
               continue;
             }
-            const double wt = s_bw[t] / (u - s_xi[t]);
+            const double wt = s_bw[t] * rcp_signed64(u - s_xi[t]);
             den += wt;
-            num = VOps<V>::fma_s(wt, g_k[t], num);
+            num = O::fma_s(wt, g_k[t], num);
           }
-          g = hit >= 0 ? g_k[hit] : VOps<V>::scale(num, 1.0 / den);
+          g = hit >= 0 ? g_k[hit] : O::scale(num, rcp_signed64(den));
         }
         const V fg = from2<V>(c_mul(front, as2(g)));
-        acc_c = VOps<V>::add(acc_c, VOps<V>::mul(fg, pg.dc));
-        acc_w = VOps<V>::add(acc_w, VOps<V>::mul(fg, pg.dw));
+        acc_c = O::add(acc_c, O::mul(fg, pg.dc));
+        acc_w = O::add(acc_w, O::mul(fg, pg.dw));
+      };
+      if (tid < n_last) contract(u0, pg0);
+      for (int s = tid + blockDim.x; s < n_last; s += blockDim.x) {
+        const double u = (double)s / (double)n_last;
+        contract(u, phi_grad_lv<FAM>(u, ap, dcp, s_e64));
       }
     }
-    const V tc = block_sum(acc_c, s_red);
-    const V tw = block_sum(acc_w, s_red);
+    double2 both;
+    if constexpr (FAM == MDI_FAM_OSC) both = as2(acc_c);  // complex: its real part is the gradient
+    else both = make_double2(acc_c, acc_w);
+    const double2 tot = block_sum(both, s_red);
     if (tid == 0) {
       const double scale = (k < d) ? inv_a : 1.0 / (double)n_last;
-      grad[k - 1] = as2(tc).x * scale;
-      if (FAM != MDI_FAM_OSC) grad[d + k - 1] = as2(tw).x * scale;
+      grad[k - 1] = tot.x * scale;
+      if (FAM != MDI_FAM_OSC) grad[d + k - 1] = tot.y * scale;
     }
     __syncthreads();
   }
@@ -911,8 +1070,11 @@ static mdi_status run_levels(int d, int a, int n_last, const double *params, con
                                                                      value, grad, grad ? 1 : 0);
   if ((st = check_launch()) != MDI_OK) return st;
   if (grad) {
-    levels_grad_kernel<FAM><<<std::min(d, sm_count() * 8), kLvThreads, 0, stream>>>(d, a, n_last, P, C, params, L, M,
-                                                                                    gck, lck, grad);
+    const int grid = std::min(d, sm_count() * 8);
+    if (P <= 16)
+      levels_grad_kernel<FAM, 2><<<grid, kLvThreads, 0, stream>>>(d, a, n_last, P, C, params, L, M, gck, lck, grad);
+    else
+      levels_grad_kernel<FAM, 8><<<grid, kLvThreads, 0, stream>>>(d, a, n_last, P, C, params, L, M, gck, lck, grad);
     st = check_launch();
   }
   return st;

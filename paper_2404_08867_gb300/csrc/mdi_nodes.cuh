@@ -8,17 +8,22 @@
 // "Barycentric Lagrange interpolation", SIAM Review 46 (2004), Sec. 5).
 #pragma once
 
+#include "mdi_cheb_table.inc"
 #include "mdi_common.cuh"
 
 namespace mdi {
 
 constexpr int kNodesAMax = 64;  // largest a with a basis table
 constexpr int kNodesPMax = 32;
+static_assert(kChebTablePMax >= kNodesPMax, "the generated node table covers every P");
 
-__device__ __forceinline__ double cheb_node(int p, int P) { return 0.5 * (1.0 + cospi((2.0 * p + 1.0) / (2.0 * P))); }
-__device__ __forceinline__ double cheb_weight(int p, int P) {
-  return ((p & 1) ? -1.0 : 1.0) * sinpi((2.0 * p + 1.0) / (2.0 * P));
-}
+// xi_p and the weight of node p of P, 0 <= p < P <= kNodesPMax: read from the
+// table build.py writes from the definitions above (each value correctly
+// rounded), rather than by cospi/sinpi in FP64 at the start of every CTA --
+// about sixty FP64 instructions on the critical path of each, on a chip whose
+// FP64 unit takes a warp instruction per ~64 cycles per sub-partition.
+__device__ __forceinline__ double cheb_node(int p, int P) { return kChebXiGen[P * (P - 1) / 2 + p]; }
+__device__ __forceinline__ double cheb_weight(int p, int P) { return kChebBwGen[P * (P - 1) / 2 + p]; }
 
 __device__ __forceinline__ double2 as2(double v) { return make_double2(v, 0.0); }
 __device__ __forceinline__ double2 as2(double2 v) { return v; }
