@@ -99,19 +99,39 @@ constexpr int64_t kStepMaxRadix = 4096;              // a^m for the step-m opera
 // Groups: g = 0..ng-1 covers levels gC+1 .. min((g+1)C, d-1); boundary b_g = gC
 // for g < ng and b_ng = d-1.  gck[g] = G at b_g, lck[g] = lambda at b_g.
 struct LevelsLayout {
-  size_t table, M, R, w, gck, lck, misc, total;
+  size_t table, M, runs, R, w, gck, lck, misc, total;
   int C, ng;  // checkpoint interval (= group length) and number of groups
+  int r, nr;  // group products in two stages: runs of r levels, nr runs per group (nr = 1: one stage)
 };
+
+// Run length of the two-stage group products: about sqrt(C), which makes the
+// r - 1 + ceil(C/r) - 1 products in sequence fewest, lengthened while the runs take
+// more than 128 CTAs (one product per SM of GB300's 152) and the sequence does not
+// grow.  One stage below C = 8.
+static void group_runs(int C, int ng, int &r, int &nr) {
+  r = C;
+  nr = 1;
+  if (C < 8) return;
+  int s = 1;
+  while (s * s < C) ++s;
+  auto depth = [C](int x) { return x - 1 + (C + x - 1) / x - 1; };
+  while (s + 1 < C && (int64_t)ng * ((C + s - 1) / s) > 128 && depth(s + 1) <= depth(s)) ++s;
+  r = s;
+  nr = (C + s - 1) / s;
+}
 
 static LevelsLayout levels_layout(int d, int64_t a, int P, int C) {
   LevelsLayout L{};
   L.C = C;
   L.ng = (d - 1 + C - 1) / C;
+  group_runs(C, L.ng, L.r, L.nr);
   size_t off = 0;
   L.table = off;
   off += align_up(sizeof(double) * (size_t)a * P * P);
   L.M = off;
   off += align_up(sizeof(double2) * (size_t)std::max(d - 1, 1) * P * P);
+  L.runs = off;
+  if (C > 1 && L.nr > 1) off += align_up(sizeof(double2) * (size_t)std::max(L.ng, 1) * L.nr * P * P);
   L.R = off;
   if (C > 1) off += align_up(sizeof(double2) * (size_t)std::max(L.ng, 1) * P * P);
   L.w = off;
@@ -439,38 +459,59 @@ __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wa
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Operators ops_first .. ops_first+cnt-1 (1-based) -> dst, one 16-byte copy each.
-// Operators are stored [t][p]; `transpose` stages each one as [p][t].
+// Operators are stored [t][p]; `transpose` stages each one as [p][t], a thread
+// taking the same entries (t, p) of every operator so that it divides by P once
+// per entry rather than once per copy.
 __device__ __forceinline__ void stage_ops(double2 *dst, const double2 *ops, int first, int cnt, int P, bool transpose) {
-  const int n = cnt * P * P, pp = P * P;
+  const int pp = P * P;
   const double2 *src = ops + (size_t)(first - 1) * pp;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    int j = i;
-    if (transpose) {
-      const int lev = i / pp, e = i % pp;  // e = t*P + p
-      j = lev * pp + (e % P) * P + e / P;
+  if (!transpose) {
+    for (int i = threadIdx.x; i < cnt * pp; i += blockDim.x) cp_async16(dst + i, src + i);
+  } else {
+    for (int e = threadIdx.x; e < pp; e += blockDim.x) {
+      const int t = e / P, j = (e - t * P) * P + t;  // e = t*P + p -> p*P + t
+      for (int lev = 0; lev < cnt; ++lev) cp_async16(dst + lev * pp + j, src + lev * pp + e);
     }
-    cp_async16(dst + j, src + i);
   }
   cp_async_commit();
 }
 
 // K2: R_g = M_hi ... M_lo for the levels lo = gC+1 .. hi = min((g+1)C, d-1) of
-// group g = blockIdx.x.  Thread (p, t) forms entry (p, t) of each partial product
-// R' = M_k R, R'[p][t] = sum_s M_k[p][s] R[s][t], from the operator staged in
-// shared memory (the next one is in flight meanwhile) and R in shared memory,
-// [s][t] row-major.  R_g is written [t][p] like the operators.
+// each group g, in one or two stages of products of consecutive operators, one
+// CTA per product:
+//   stage 0, CTA b = g nr + j: the run of levels gC + 1 + j r .. min(gC + (j+1) r,
+//     (g+1)C, d-1) of group g (an empty run of a short last group writes nothing);
+//     with r = C, nr = 1 this is R_g itself;
+//   stage 1, CTA g: the product of group g's run products g nr + 1 .. g nr + nr_g
+//     (1-based; nr_g = ceil(len_g / r)).
+// Two stages take r - 1 + nr - 1 products in sequence instead of C - 1, on nr times
+// as many SMs (the FP64 unit of one SM takes about a microsecond per 16 x 16
+// product).  Thread (p, t) forms entry (p, t) of each partial product R' = M_k R,
+// R'[p][t] = sum_s M_k[p][s] R[s][t], from the operator staged in shared memory
+// (the next one is in flight meanwhile) and R in shared memory, [s][t] row-major.
+// Products are written [t][p] like the operators.
 constexpr int kGroupMaxThreads = kNodesPMax * kNodesPMax;
 
 template <int FAM>
-__global__ void __launch_bounds__(kGroupMaxThreads) levels_group_kernel(int d, int P, int C,
+__global__ void __launch_bounds__(kGroupMaxThreads) levels_group_kernel(int d, int P, int C, int r, int nr, int stage,
                                                                      const double2 *__restrict__ M,
                                                                      double2 *__restrict__ R) {
   extern __shared__ __align__(16) unsigned char group_smem[];
   const int pp = P * P;
   double2 *const sM = (double2 *)group_smem;  // two staged operators
   double2 *const sR = sM + 2 * pp;             // two partial products
-  const int g = blockIdx.x;
-  const int lo = g * C + 1, hi = min((g + 1) * C, d - 1);
+  int lo, hi;
+  if (stage == 0) {
+    const int g = blockIdx.x / nr, j = blockIdx.x - g * nr;
+    lo = g * C + 1 + j * r;
+    hi = min(lo + r - 1, min((g + 1) * C, d - 1));
+  } else {
+    const int g = blockIdx.x, len = min((g + 1) * C, d - 1) - g * C;
+    lo = g * nr + 1;
+    hi = g * nr + (len + r - 1) / r;
+  }
+  if (lo > hi) return;  // the whole CTA, before any barrier
+  const int g = blockIdx.x;  // the product written
   const int i = threadIdx.x, p = i / P, t = i % P;
   const bool on = i < pp;
   if (on) sR[p * P + t] = M[(size_t)(lo - 1) * pp + t * P + p];  // R = M_lo
@@ -676,40 +717,60 @@ __device__ __forceinline__ void matvec8(const double2 *__restrict__ Op, const V 
   if (row < P && part == 0) out[row] = acc;
 }
 
-// Operator entries for the recompute products of K4: a lane holds E entries of a
-// row, E = 2 (eight lanes per row) for P <= 16 and E = 8 (four lanes per row) up to
-// P = 32, so that a G product and a lambda product run side by side in 128 threads
-// each.
+// Operator entries for the recompute products of K4: four lanes per row, a lane
+// holding E = P/4 entries of it (E = 4 up to P = 16, 8 up to 32), so that a G
+// product and a lambda product run side by side, each on at most 128 threads.  On
+// GB300 a warp's FP64 instruction holds its sub-partition's FP64 unit for about 64
+// cycles: four lanes per row (E FMAs and two shuffle rounds on two warps for
+// P = 16) finish a product as soon as eight lanes per row (two FMAs and three
+// rounds on four warps) and leave the unit half the work.
+constexpr int kRecLanes = 4;
+constexpr int kGradMaxLevels = 8;  // levels per CTA in K4
+
 template <typename V> __device__ __forceinline__ V op_entry(const double2 *e);
 template <> __device__ __forceinline__ double op_entry<double>(const double2 *e) {
   return reinterpret_cast<const double *>(e)[0];  // real families: the real part only
 }
 template <> __device__ __forceinline__ double2 op_entry<double2>(const double2 *e) { return *e; }
 
-// A lane's entries (row, part + j LR), j < E, of a level operator stored [t][p]:
-// not TRANSPOSE, out[p] = sum_t Op[p][t] in[t] (row p, column t at t*P + p);
+// A lane's entries (row, part + j kRecLanes), j < E, of a level operator stored
+// [t][p]: not TRANSPOSE, out[p] = sum_t Op[p][t] in[t] (row p, column t at t*P + p);
 // TRANSPOSE, out[t] = sum_p in[p] Op[p][t] (row t, column p at t*P + p).
 template <typename V, bool TRANSPOSE, int E>
-__device__ __forceinline__ void op_fetch(const double2 *__restrict__ Op, int row, int part, int LR, int P, V (&e)[E]) {
+__device__ __forceinline__ void op_fetch(const double2 *__restrict__ Op, int row, int part, int P, V (&e)[E]) {
 #pragma unroll
   for (int j = 0; j < E; ++j) {
-    const int col = part + j * LR;
+    const int col = part + j * kRecLanes;
     if (row < P && col < P) e[j] = op_entry<V>(Op + (TRANSPOSE ? row * P + col : col * P + row));
   }
 }
 
-// K4: gradient of level k (block k-1, k = 1..d).  G_{k-1} is recomputed from the
-// checkpoint below by the first half of the CTA while the second half recomputes
-// lambda_k from the checkpoint above, one barrier per step of the longer chain; a
-// lane holds its entries of the next operator in registers while it multiplies by
-// the current one, so no step waits on an L2 round trip.  The phi derivatives at
-// the CTA's first points do not depend on the states: they are evaluated before the
-// chains, and their FP64 work fills the pipe while the products wait on one
-// another.  Real families run in real arithmetic (the operators' imaginary parts
-// are zero).
+// Per-level constants of K4: the axis, and 2 / c^3 (PEAK: d phi / dc = (2 / c^3) phi^2).
+struct GradAxis {
+  AxisParams ap;
+  double dcp;
+};
+
+// K4: gradients of a block of consecutive levels of one checkpoint group, or of
+// level d.  CTA b < ng nb takes block j = b mod nb of group g = b / nb, the levels
+// klo = gC + 1 + jB .. khi = min(klo + B - 1, (g+1)C, d-1) (none for the short
+// last group's spare blocks); the last CTA takes level d.  Every level of a group
+// recomputes from the same checkpoints: G from G_gC up through the operators
+// gC+1 .. khi-1 and lambda from lambda_top (top = min((g+1)C, d-1)) down through
+// top .. klo+1, the states of the block's own levels kept in shared memory -- so a
+// CTA of B levels takes one chain of each kind, not B, and no level state outside
+// the block and the checkpoints is ever stored.  The two chains run side by side
+// (one barrier per step of the longer), a lane holding its entries of the next
+// operator in registers while it multiplies by the current one.  The phi
+// derivatives at each thread's first point do not depend on the states and are
+// evaluated before the chains, so their FP64 work fills the pipe while the
+// products wait on one another.  Then, level by level,
+//     dQ/dtheta_k = (1/a) sum_{q,p} lambda_k[p] dphi_k(u_qp)/dtheta G~_{k-1}(u_qp),
+// warp sums per level into shared memory and one fixed-order sum at the end.  Real
+// families run in real arithmetic (the operators' imaginary parts are zero).
 template <int FAM, int E>
-__global__ void __launch_bounds__(kLvThreads) levels_grad_kernel(int d, int a, int n_last, int P, int C,
-                                                                 const double *__restrict__ prm,
+__global__ void __launch_bounds__(kLvThreads) levels_grad_kernel(int d, int a, int n_last, int P, int C, int B,
+                                                                 int nb, const double *__restrict__ prm,
                                                                  const double *__restrict__ L,
                                                                  const double2 *__restrict__ M,
                                                                  const double2 *__restrict__ gck,
@@ -718,96 +779,121 @@ __global__ void __launch_bounds__(kLvThreads) levels_grad_kernel(int d, int a, i
   using V = typename FamTraits<FAM>::V;
   using O = VOps<V>;
   constexpr bool kExp64 = FAM != MDI_FAM_OSC;
-  constexpr int kHalf = kLvThreads / 2;
-  constexpr int LR = E == 2 ? 8 : 4;  // lanes per row
+  constexpr int kSlots = 2 + kGradMaxLevels;  // two chain temporaries, then the block's levels
   __shared__ double s_xi[kNodesPMax], s_bw[kNodesPMax];
   __shared__ double s_e64[kExp64 ? kExpTable : 1];
-  __shared__ V s_g[2][kNodesPMax], s_l[2][kNodesPMax];
-  __shared__ double2 s_red[kLvThreads / kWarp];
-  for (int t = threadIdx.x; t < P; t += blockDim.x) {
+  __shared__ V s_g[kSlots][kNodesPMax], s_l[kSlots][kNodesPMax];
+  __shared__ GradAxis s_ax[kGradMaxLevels];
+  __shared__ double2 s_part[kGradMaxLevels][kLvThreads / kWarp];
+  const int tid = threadIdx.x, lane = tid & (kWarp - 1), warp = tid / kWarp;
+  const int ng = (d - 1 + C - 1) / C;
+  const int npts = a * P;
+  const double inv_a = 1.0 / (double)a;
+  // This CTA's levels klo..khi, the checkpoint group g0 of G, and lambda's top.
+  int g0, klo, khi, top = 0;
+  const double2 *lsrc = nullptr;
+  if ((int)blockIdx.x < ng * nb) {
+    const int g = blockIdx.x / nb, j = blockIdx.x - g * nb;
+    g0 = g;
+    klo = g * C + 1 + j * B;
+    top = min((g + 1) * C, d - 1);
+    khi = min(klo + B - 1, top);
+    if (klo > khi) return;  // the whole CTA, before any barrier
+    lsrc = lck + (size_t)((g + 1) * C > d - 1 ? ng : g + 1) * P;
+  } else {
+    g0 = (d - 1) / C;
+    klo = khi = d;
+  }
+  const int nlev = khi - klo + 1;
+  for (int t = tid; t < P; t += blockDim.x) {
     s_xi[t] = cheb_node(t, P);
     s_bw[t] = cheb_weight(t, P);
   }
   if constexpr (kExp64)
-    for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s_e64[j] = kExp2TableD[j];
-  __syncthreads();
-  const int ng = (d - 1 + C - 1) / C;
-  const int npts = a * P;
-  const double inv_a = 1.0 / (double)a;
+    for (int j = tid; j < kExpTable; j += blockDim.x) s_e64[j] = kExp2TableD[j];
+  if (tid < nlev) {
+    const AxisParams ap = load_axis_lv(prm, d, klo + tid - 1);
+    s_ax[tid] = GradAxis{ap, 2.0 * ap.ic2 * rcp_signed64(ap.c)};
+  }
   double2 front = make_double2(1.0, 0.0);
   if (FAM == MDI_FAM_OSC) {
     double sn, cs;
     sincos(kTwoPi * prm[d], &sn, &cs);
     front = make_double2(cs, sn);
   }
-  const int tid = threadIdx.x;
-  const int side = tid / kHalf, li = tid % kHalf;  // side 0: G, side 1: lambda
-  const int row = li / LR, part = li % LR;
-  for (int k = blockIdx.x + 1; k <= d; k += gridDim.x) {
-    const AxisParams ap = load_axis_lv(prm, d, k - 1);
-    const double dcp = 2.0 * ap.ic2 * rcp_signed64(ap.c);  // PEAK: d phi / dc = (2 / c^3) phi^2
-    // Level k < d reads the points (q + xi_p)/a, level d the points s/n_last.
-    const int npt = k < d ? npts : n_last;
-    PhiGrad<FAM> pg0{};
-    double u0 = 0.0;
-    if (tid < npt) {
-      u0 = k < d ? ((double)(tid / P) + s_xi[tid % P]) * inv_a : (double)tid / (double)n_last;
-      pg0 = phi_grad_lv<FAM>(u0, ap, dcp, s_e64);
-    }
-    // The chains: G over the operators j0 C + 1 .. k - 1, lambda over top .. k + 1.
-    const int j0 = (k - 1) / C, nG = (k - 1) - j0 * C;
-    int top = 0, nL = 0;
-    const double2 *lsrc = nullptr;
-    if (k < d) {
-      top = ((k + C - 1) / C) * C;
-      if (top > d - 1) {
-        top = d - 1;
-        lsrc = lck + (size_t)ng * P;
-      } else {
-        lsrc = lck + (size_t)(top / C) * P;
+  __syncthreads();
+  // Level klo < d reads the points (q + xi_p)/a, level d the points s/n_last.
+  const int npt = klo < d ? npts : n_last;
+  auto point = [&](int k, int i) {
+    return k < d ? ((double)(i / P) + s_xi[i % P]) * inv_a : (double)i / (double)n_last;
+  };
+  PhiGrad<FAM> pg0{};
+  if (tid < npt) pg0 = phi_grad_lv<FAM>(point(klo, tid), s_ax[0].ap, s_ax[0].dcp, s_e64);
+
+  // The chains.  G: vector i = G_{g0 C + i}, i = 0..nG, over the operators
+  // g0 C + 1 + st; lambda: vector i = lambda_{top - i}, i = 0..nL, over the
+  // transposed operators top - st.  The vectors of the block's levels (G_{k-1},
+  // lambda_k for klo <= k <= khi) go to slots 2 + (k - klo), the others alternate
+  // between slots 0 and 1.
+  const int nG = (khi - 1) - g0 * C, gfirst = (klo - 1) - g0 * C;
+  const int nL = klo < d ? top - klo : 0, lfirst = klo < d ? top - khi : 0;
+  auto gslot = [&](int i) { return i >= gfirst ? 2 + (i - gfirst) : (i & 1); };
+  auto lslot = [&](int i) { return i >= lfirst ? 2 + (top - i - klo) : (i & 1); };
+  // Side 0 (G) and side 1 (lambda) take the first whole warps: for P = 16 warps 0-1
+  // and 2-3, one per SM sub-partition, so that the two chains' FP64 instructions
+  // queue on different units; the other warps sit the chains out.
+  const int side_threads = (P * kRecLanes + kWarp - 1) / kWarp * kWarp;
+  const int side = tid / side_threads, li = tid % side_threads;
+  const int row = li / kRecLanes, part = li % kRecLanes;
+  const int mine = side == 0 ? nG : side == 1 ? nL : 0;
+  const size_t pp = (size_t)P * P;
+  // Operator of step st: G side g0 C + 1 + st, lambda side top - st (1-based).
+  const double2 *op0 = side == 1 && top > 0 ? M + (size_t)(top - 1) * pp : M + (size_t)g0 * C * pp;
+  const ptrdiff_t opstep = side == 1 ? -(ptrdiff_t)pp : (ptrdiff_t)pp;
+  V cur[E], nxt[E];
+#pragma unroll
+  for (int j = 0; j < E; ++j) cur[j] = nxt[j] = O::zero();
+  if (mine > 0) {
+    if (side) op_fetch<V, true, E>(op0, row, part, P, cur);
+    else op_fetch<V, false, E>(op0, row, part, P, cur);
+  }
+  if (tid < P) s_g[gslot(0)][tid] = from2<V>(gck[(size_t)g0 * P + tid]);
+  if (klo < d && side == 1 && li < P) s_l[lslot(0)][li] = from2<V>(lsrc[li]);
+  __syncthreads();
+  const int nsteps = max(nG, nL);
+  for (int st = 0; st < nsteps; ++st) {
+    if (st < mine) {  // the same in every lane of a warp
+      if (st + 1 < mine) {
+        const double2 *op = op0 + (st + 1) * opstep;
+        if (side) op_fetch<V, true, E>(op, row, part, P, nxt);
+        else op_fetch<V, false, E>(op, row, part, P, nxt);
       }
-      nL = top - k;
-    }
-    const int mine = side ? nL : nG;
-    const size_t pp = (size_t)P * P;
-    auto op_at = [&](int st) { return side ? M + (size_t)(top - 1 - st) * pp : M + (size_t)(j0 * C + st) * pp; };
-    auto fetch = [&](int st, V(&e)[E]) {
-      if (side) op_fetch<V, true, E>(op_at(st), row, part, LR, P, e);
-      else op_fetch<V, false, E>(op_at(st), row, part, LR, P, e);
-    };
-    V cur[E], nxt[E];
+      const V *in = side ? s_l[lslot(st)] : s_g[gslot(st)];
+      V acc = O::zero();
 #pragma unroll
-    for (int j = 0; j < E; ++j) cur[j] = nxt[j] = O::zero();
-    if (mine > 0) fetch(0, cur);
-    if (tid < P) s_g[0][tid] = from2<V>(gck[(size_t)j0 * P + tid]);
-    if (k < d && side && li < P) s_l[0][li] = from2<V>(lsrc[li]);
-    __syncthreads();
-    const int nsteps = max(nG, nL);
-    for (int st = 0; st < nsteps; ++st) {
-      if (st < mine) {  // the same in every lane of a warp
-        if (st + 1 < mine) fetch(st + 1, nxt);
-        const V *in = side ? s_l[st & 1] : s_g[st & 1];
-        V acc = O::zero();
-#pragma unroll
-        for (int j = 0; j < E; ++j) {
-          const int col = part + j * LR;
-          if (row < P && col < P) {
-            if constexpr (FAM == MDI_FAM_OSC) acc = c_add(acc, c_mul(cur[j], in[col]));
-            else acc = fma(cur[j], in[col], acc);
-          }
+      for (int j = 0; j < E; ++j) {
+        const int col = part + j * kRecLanes;
+        if (row < P && col < P) {
+          if constexpr (FAM == MDI_FAM_OSC) acc = c_add(acc, c_mul(cur[j], in[col]));
+          else acc = fma(cur[j], in[col], acc);
         }
-        acc = group_sum(acc, LR);
-        if (row < P && part == 0) (side ? s_l[(st & 1) ^ 1] : s_g[(st & 1) ^ 1])[row] = acc;
-#pragma unroll
-        for (int j = 0; j < E; ++j) cur[j] = nxt[j];
       }
-      __syncthreads();
+      acc = group_sum(acc, kRecLanes);
+      if (row < P && part == 0) (side ? s_l[lslot(st + 1)] : s_g[gslot(st + 1)])[row] = acc;
+#pragma unroll
+      for (int j = 0; j < E; ++j) cur[j] = nxt[j];
     }
-    const V *g_k = s_g[nG & 1];
-    const V *l_k = s_l[nL & 1];
+    __syncthreads();
+  }
+
+  // The contractions, level by level.
+  for (int lv = 0; lv < nlev; ++lv) {
+    const int k = klo + lv;
+    const GradAxis ax = s_ax[lv];
+    const V *g_k = s_g[2 + lv];  // G_{k-1}
+    const V *l_k = s_l[2 + lv];  // lambda_k (k < d)
     V acc_c = O::zero(), acc_w = O::zero();
     if (k < d) {
-      // dQ/dtheta_k = (1/a) sum_{q,p} lambda_k[p] dphi_k(u_qp)/dtheta G~_{k-1}(u_qp)
       auto contract = [&](int i, const PhiGrad<FAM> &pg) {
         V g = O::one();
         if (k > 1) {
@@ -818,11 +904,11 @@ __global__ void __launch_bounds__(kLvThreads) levels_grad_kernel(int d, int a, i
         acc_c = O::add(acc_c, O::mul(lg, pg.dc));
         acc_w = O::add(acc_w, O::mul(lg, pg.dw));
       };
-      if (tid < npts) contract(tid, pg0);
-      for (int i = tid + blockDim.x; i < npts; i += blockDim.x)
-        contract(i, phi_grad_lv<FAM>(((double)(i / P) + s_xi[i % P]) * inv_a, ap, dcp, s_e64));
+      const int i0 = lv == 0 ? tid + blockDim.x : tid;
+      if (lv == 0 && tid < npts) contract(tid, pg0);
+      for (int i = i0; i < npts; i += blockDim.x) contract(i, phi_grad_lv<FAM>(point(k, i), ax.ap, ax.dcp, s_e64));
     } else {
-      // last level: dQ/dtheta_d = Re(front (1/n_last) sum_s dphi_d(s/n_last) G~_{d-1}(s/n_last))
+      // level d: Re(front (1/n_last) sum_s dphi_d(s/n_last) G~_{d-1}(s/n_last))
       auto contract = [&](double u, const PhiGrad<FAM> &pg) {
         V g = O::one();
         if (d > 1) {
@@ -844,22 +930,26 @@ __global__ void __launch_bounds__(kLvThreads) levels_grad_kernel(int d, int a, i
         acc_c = O::add(acc_c, O::mul(fg, pg.dc));
         acc_w = O::add(acc_w, O::mul(fg, pg.dw));
       };
-      if (tid < n_last) contract(u0, pg0);
-      for (int s = tid + blockDim.x; s < n_last; s += blockDim.x) {
-        const double u = (double)s / (double)n_last;
-        contract(u, phi_grad_lv<FAM>(u, ap, dcp, s_e64));
+      if (tid < n_last) contract(point(d, tid), pg0);
+      for (int i = tid + blockDim.x; i < n_last; i += blockDim.x) {
+        const double u = point(d, i);
+        contract(u, phi_grad_lv<FAM>(u, ax.ap, ax.dcp, s_e64));
       }
     }
     double2 both;
     if constexpr (FAM == MDI_FAM_OSC) both = as2(acc_c);  // complex: its real part is the gradient
     else both = make_double2(acc_c, acc_w);
-    const double2 tot = block_sum(both, s_red);
-    if (tid == 0) {
-      const double scale = (k < d) ? inv_a : 1.0 / (double)n_last;
-      grad[k - 1] = tot.x * scale;
-      if (FAM != MDI_FAM_OSC) grad[d + k - 1] = tot.y * scale;
-    }
-    __syncthreads();
+    both = warp_sum(both);
+    if (lane == 0) s_part[lv][warp] = both;
+  }
+  __syncthreads();
+  if (tid < nlev) {
+    const int k = klo + tid, nw = blockDim.x / kWarp;
+    double2 tot = make_double2(0.0, 0.0);
+    for (int w = 0; w < nw; ++w) tot = c_add(tot, s_part[tid][w]);
+    const double scale = (k < d) ? inv_a : 1.0 / (double)n_last;
+    grad[k - 1] = tot.x * scale;
+    if (FAM != MDI_FAM_OSC) grad[d + k - 1] = tot.y * scale;
   }
 }
 
@@ -1059,7 +1149,15 @@ static mdi_status run_levels(int d, int a, int n_last, const double *params, con
   if (C > 1 && Lo.ng > 0) {
     double2 *R = (double2 *)(base + Lo.R);
     const size_t group_smem = 4 * sizeof(double2) * (size_t)P * P;
-    levels_group_kernel<FAM><<<Lo.ng, std::max(32, (P * P + 31) / 32 * 32), group_smem, stream>>>(d, P, C, M, R);
+    const int gthreads = std::max(32, (P * P + 31) / 32 * 32);
+    if (Lo.nr > 1) {
+      double2 *runs = (double2 *)(base + Lo.runs);
+      levels_group_kernel<FAM><<<Lo.ng * Lo.nr, gthreads, group_smem, stream>>>(d, P, C, Lo.r, Lo.nr, 0, M, runs);
+      if ((st = check_launch()) != MDI_OK) return st;
+      levels_group_kernel<FAM><<<Lo.ng, gthreads, group_smem, stream>>>(d, P, C, Lo.r, Lo.nr, 1, runs, R);
+    } else {
+      levels_group_kernel<FAM><<<Lo.ng, gthreads, group_smem, stream>>>(d, P, C, C, 1, 0, M, R);
+    }
     if ((st = check_launch()) != MDI_OK) return st;
     ops = R;
   }
@@ -1070,11 +1168,18 @@ static mdi_status run_levels(int d, int a, int n_last, const double *params, con
                                                                      value, grad, grad ? 1 : 0);
   if ((st = check_launch()) != MDI_OK) return st;
   if (grad) {
-    const int grid = std::min(d, sm_count() * 8);
+    // Blocks of B levels per CTA: one level each while the grid stays near 256 CTAs
+    // (the contractions spread over every SM), more levels for deep chains (one
+    // recompute serves them all).
+    const int B = std::max(1, std::min({kGradMaxLevels, C, (d + 255) / 256}));
+    const int nb = (C + B - 1) / B;
+    const int grid = Lo.ng * nb + 1;
     if (P <= 16)
-      levels_grad_kernel<FAM, 2><<<grid, kLvThreads, 0, stream>>>(d, a, n_last, P, C, params, L, M, gck, lck, grad);
+      levels_grad_kernel<FAM, 4><<<grid, kLvThreads, 0, stream>>>(d, a, n_last, P, C, B, nb, params, L, M, gck, lck,
+                                                                   grad);
     else
-      levels_grad_kernel<FAM, 8><<<grid, kLvThreads, 0, stream>>>(d, a, n_last, P, C, params, L, M, gck, lck, grad);
+      levels_grad_kernel<FAM, 8><<<grid, kLvThreads, 0, stream>>>(d, a, n_last, P, C, B, nb, params, L, M, gck, lck,
+                                                                   grad);
     st = check_launch();
   }
   return st;
@@ -1170,8 +1275,8 @@ static mdi_status run_levels_step(int d, int a, int n_last, const double *params
   if (Lo.C > 1 && Lo.ng > 0) {
     double2 *Rg = (double2 *)(base + Lo.R);
     const size_t group_smem = 4 * sizeof(double2) * (size_t)P * P;
-    levels_group_kernel<FAM><<<Lo.ng, std::max(32, (P * P + 31) / 32 * 32), group_smem, stream>>>(Lo.ns + 1, P, Lo.C,
-                                                                                                 M, Rg);
+    levels_group_kernel<FAM><<<Lo.ng, std::max(32, (P * P + 31) / 32 * 32), group_smem, stream>>>(
+        Lo.ns + 1, P, Lo.C, Lo.C, 1, 0, M, Rg);
     if ((st = check_launch()) != MDI_OK) return st;
     ops = Rg;
   }
