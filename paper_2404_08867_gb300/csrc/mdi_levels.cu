@@ -188,14 +188,46 @@ __global__ void levels_table_kernel(int P, int a, double *__restrict__ L) {
   }
 }
 
-// Barycentric basis value l_t(u) with the nodes and weights in shared memory.
-__device__ __forceinline__ double basis_at(const double *xi, const double *bw, int P, int t, double u) {
-  double den = 0.0;
-  for (int j = 0; j < P; ++j) {
-    if (u == xi[j]) return j == t ? 1.0 : 0.0;
-    den += bw[j] / (u - xi[j]);
+// The last level's row w[t] = (1/n_last) sum_s phi_d(s/n_last) l_t(s/n_last), by
+// one CTA: a group of GL lanes per point (lane t forms l_t, by the warp-per-point
+// scheme of K0), partial rows in `part` (blockDim entries), w written by threads
+// t < P.
+template <int FAM, bool F32>
+__device__ __forceinline__ void last_level_row(int d, int n_last, int P, const AxisParams &ap, const double *s_xi,
+                                               const double *s_bw, const double *s_e64, double2 *part,
+                                               double2 *__restrict__ w) {
+  const int GL = P <= kWarp / 2 ? kWarp / 2 : kWarp;
+  const int lane = threadIdx.x & (kWarp - 1), t = lane & (GL - 1);
+  const int per_warp = kWarp / GL, nwarps = blockDim.x / kWarp;
+  const unsigned gmask = GL == kWarp ? 0xffffffffu : (0xffffu << (lane & (kWarp / 2)));
+  const bool on = t < P;
+  const double xi = on ? s_xi[t] : 0.0, bw = on ? s_bw[t] : 0.0;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int base = (threadIdx.x / kWarp) * per_warp; base < n_last; base += nwarps * per_warp) {
+    const int s = base + lane / GL;  // whole warps run the loop and its shuffles
+    const bool pt = s < n_last;
+    const double u = (double)(pt ? s : 0) / (double)n_last;
+    double l = (t == 0) ? 1.0 : 0.0;  // d = 1: G_0 = 1 is constant
+    if (d > 1) {
+      const unsigned hit = __ballot_sync(0xffffffffu, on && u == xi) & gmask;
+      const double r = (on && !hit) ? bw * rcp_signed64(u - xi) : 0.0;
+      double den = r;
+      for (int off = 1; off < GL; off <<= 1) den += __shfl_xor_sync(0xffffffffu, den, off);
+      l = hit ? ((on && u == xi) ? 1.0 : 0.0) : r * rcp_signed64(den);
+    }
+    if (pt && on) {
+      const double2 f = as2(phi_lv<FAM, F32>(u, ap, s_e64));
+      acc.x = fma(l, f.x, acc.x);
+      if constexpr (FAM == MDI_FAM_OSC) acc.y = fma(l, f.y, acc.y);
+    }
   }
-  return (bw[t] / (u - xi[t])) / den;
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < P) {
+    double2 sum = make_double2(0.0, 0.0);
+    for (int r = 0; r < (int)blockDim.x / GL; ++r) sum = c_add(sum, part[r * GL + threadIdx.x]);
+    w[threadIdx.x] = c_scale(sum, 1.0 / (double)n_last);
+  }
 }
 
 // K1: M_k for k = 1..d-1 (block k-1) and w (block d-1).  M is stored [k][t][p].
@@ -299,40 +331,7 @@ __global__ void __launch_bounds__(kLvThreads) levels_build_kernel(int d, int a, 
       }
       __syncthreads();
     } else {
-      // last level: w[t] = (1/n_last) sum_s phi_d(s/n_last) l_t(s/n_last), a group of
-      // GL lanes per point (lane t: l_t, by the warp-per-point scheme of K0).
-      const int GL = P <= kWarp / 2 ? kWarp / 2 : kWarp;
-      const int lane = threadIdx.x & (kWarp - 1), t = lane & (GL - 1);
-      const int per_warp = kWarp / GL, nwarps = blockDim.x / kWarp;
-      const unsigned gmask = GL == kWarp ? 0xffffffffu : (0xffffu << (lane & (kWarp / 2)));
-      const bool on = t < P;
-      const double xi = on ? s_xi[t] : 0.0, bw = on ? s_bw[t] : 0.0;
-      double2 acc = make_double2(0.0, 0.0);
-      for (int base = (threadIdx.x / kWarp) * per_warp; base < n_last; base += nwarps * per_warp) {
-        const int s = base + lane / GL;  // whole warps run the loop and its shuffles
-        const bool pt = s < n_last;
-        const double u = (double)(pt ? s : 0) / (double)n_last;
-        double l = (t == 0) ? 1.0 : 0.0;  // d = 1: G_0 = 1 is constant
-        if (d > 1) {
-          const unsigned hit = __ballot_sync(0xffffffffu, on && u == xi) & gmask;
-          const double r = (on && !hit) ? bw * rcp_signed64(u - xi) : 0.0;
-          double den = r;
-          for (int off = 1; off < GL; off <<= 1) den += __shfl_xor_sync(0xffffffffu, den, off);
-          l = hit ? ((on && u == xi) ? 1.0 : 0.0) : r * rcp_signed64(den);
-        }
-        if (pt && on) {
-          const double2 f = as2(phi_lv<FAM, F32>(u, ap, s_e64));
-          acc.x = fma(l, f.x, acc.x);
-          if constexpr (FAM == MDI_FAM_OSC) acc.y = fma(l, f.y, acc.y);
-        }
-      }
-      s_part[threadIdx.x] = acc;
-      __syncthreads();
-      if (threadIdx.x < P) {
-        double2 sum = make_double2(0.0, 0.0);
-        for (int r = 0; r < (int)blockDim.x / GL; ++r) sum = c_add(sum, s_part[r * GL + threadIdx.x]);
-        w[threadIdx.x] = c_scale(sum, 1.0 / (double)n_last);
-      }
+      last_level_row<FAM, F32>(d, n_last, P, ap, s_xi, s_bw, s_e64, s_part, w);
       __syncthreads();
     }
   }
@@ -347,102 +346,109 @@ __global__ void __launch_bounds__(kLvThreads) levels_build_kernel(int d, int a, 
 //     x_i = ((Q mod a^(mj-i)) + xi_p) / a^(mj-i),
 // which is the affine recurrence x_i = (q_i + x_{i+1}) / a from x_mj = xi_p unrolled:
 // the digit q_i of axis l0 + i weighs a^(mj-1-i) in Q (the innermost axis' digit
-// is the most significant).  One CTA per operator
-// (block ns computes the last level's row w); the points (Q, p) go in tiles whose
-// products of phi are staged in shared memory, and l_t(x_0) is read from the basis
-// table of radix a^mj (levels_table_kernel with a^mj in place of a, so x_0 is the
-// same double in both).
+// is the most significant).  The a^mj tuples of each operator are cut into S
+// slices, one CTA each (the work of an operator is a^mj P (mj phi + P) FP64
+// operations: one SM per operator leaves most of the chip idle); CTA j S + s
+// writes the slice's partial sums, and levels_step_sum_kernel adds the S partials
+// of each entry in slice order.  The last CTA computes the last level's row w.
+// The points (Q, p) go in tiles whose products of phi are staged in shared
+// memory, and l_t(x_0) is read from the basis table of radix a^mj
+// (levels_table_kernel with a^mj in place of a, so x_0 is the same double in both).
 constexpr int kStepTile = 1024;          // points (Q, p) per tile
 constexpr int kStepMaxEntries = 4;       // P*P <= kStepMaxEntries * kLvThreads
 template <int FAM>
 __global__ void __launch_bounds__(kLvThreads) levels_step_build_kernel(int d, int a, int n_last, int P, int m,
-                                                                       int ns, const double *__restrict__ prm,
+                                                                       int ns, int S, const double *__restrict__ prm,
                                                                        const double *__restrict__ Lm,
                                                                        const double *__restrict__ Lr,
-                                                                       double2 *__restrict__ M,
+                                                                       double2 *__restrict__ Mpart,
                                                                        double2 *__restrict__ w) {
   using V = typename FamTraits<FAM>::V;
+  constexpr bool kExp64 = FAM != MDI_FAM_OSC;
   __shared__ double s_xi[kNodesPMax], s_bw[kNodesPMax];
+  __shared__ double s_e64[kExp64 ? kExpTable : 1];
   __shared__ V s_f[kStepTile];
   __shared__ double2 s_part[kLvThreads];
   __shared__ AxisParams s_ap[3];
+  __shared__ double s_inv[3];
   for (int t = threadIdx.x; t < P; t += blockDim.x) {
     s_xi[t] = cheb_node(t, P);
     s_bw[t] = cheb_weight(t, P);
   }
+  if constexpr (kExp64)
+    for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s_e64[j] = kExp2TableD[j];
   __syncthreads();
   const int tileQ = kStepTile / P;
-  for (int j = blockIdx.x; j <= ns; j += gridDim.x) {
-    if (j < ns) {
-      const int l0 = j * m, mj = min(m, d - 1 - l0);
-      int R = 1;
-      for (int i = 0; i < mj; ++i) R *= a;
-      const double *L = (mj == m) ? Lm : Lr;
-      const int npts = R * P;
-      if (threadIdx.x < mj) s_ap[threadIdx.x] = load_axis(prm, d, l0 + threadIdx.x);
-      V acc[kStepMaxEntries];
+  const int b = blockIdx.x;
+  if (b < ns * S) {
+    const int j = b / S, sl = b - j * S;
+    const int l0 = j * m, mj = min(m, d - 1 - l0);
+    int R = 1;
+    for (int i = 0; i < mj; ++i) R *= a;
+    const double *L = (mj == m) ? Lm : Lr;
+    const int npts = R * P;
+    const int Qb = (int)((int64_t)R * sl / S), Qe = (int)((int64_t)R * (sl + 1) / S);
+    if (threadIdx.x < mj) {
+      s_ap[threadIdx.x] = load_axis_lv(prm, d, l0 + threadIdx.x);
+      int Ri = 1;
+      for (int i = threadIdx.x; i < mj; ++i) Ri *= a;
+      s_inv[threadIdx.x] = 1.0 / (double)Ri;  // 1 / a^(mj-ii)
+    }
+    V acc[kStepMaxEntries];
 #pragma unroll
-      for (int e = 0; e < kStepMaxEntries; ++e) acc[e] = VOps<V>::zero();
-      __syncthreads();
-      for (int Q0 = 0; Q0 < R; Q0 += tileQ) {
-        const int nq = min(tileQ, R - Q0);
-        for (int i = threadIdx.x; i < nq * P; i += blockDim.x) {
-          const int Q = Q0 + i / P, p = i % P;
-          V prod = VOps<V>::one();
-          int Ri = R;
-          for (int ii = 0; ii < mj; ++ii) {  // x_ii = ((Q mod a^(mj-ii)) + xi_p) / a^(mj-ii)
-            const double x = ((double)(Q % Ri) + s_xi[p]) / (double)Ri;
-            prod = VOps<V>::mul(prod, phi<FAM, false>(x, s_ap[ii]));
-            Ri /= a;
-          }
-          s_f[i] = prod;
+    for (int e = 0; e < kStepMaxEntries; ++e) acc[e] = VOps<V>::zero();
+    __syncthreads();
+    for (int Q0 = Qb; Q0 < Qe; Q0 += tileQ) {
+      const int nq = min(tileQ, Qe - Q0);
+      for (int i = threadIdx.x; i < nq * P; i += blockDim.x) {
+        const int Q = Q0 + i / P, p = i % P;
+        V prod = VOps<V>::one();
+        int Ri = R;
+        for (int ii = 0; ii < mj; ++ii) {  // x_ii = ((Q mod a^(mj-ii)) + xi_p) / a^(mj-ii)
+          const double x = ((double)(Q % Ri) + s_xi[p]) * s_inv[ii];
+          prod = VOps<V>::mul(prod, phi_lv<FAM, false>(x, s_ap[ii], s_e64));
+          Ri /= a;
         }
-        __syncthreads();
-#pragma unroll
-        for (int e = 0; e < kStepMaxEntries; ++e) {
-          const int o = threadIdx.x + e * kLvThreads;
-          if (o < P * P) {
-            const int t = o / P, p = o % P;
-            const double *Lt = L + (size_t)t * npts + (size_t)Q0 * P + p;
-            V a_e = acc[e];
-            for (int q = 0; q < nq; ++q) a_e = VOps<V>::fma_s(Lt[(size_t)q * P], s_f[q * P + p], a_e);
-            acc[e] = a_e;
-          }
-        }
-        __syncthreads();
+        s_f[i] = prod;
       }
-      double2 *Mj = M + (size_t)j * P * P;
-      const double invR = 1.0 / (double)R;
+      __syncthreads();
 #pragma unroll
       for (int e = 0; e < kStepMaxEntries; ++e) {
         const int o = threadIdx.x + e * kLvThreads;
-        if (o < P * P) Mj[o] = c_scale(as2(acc[e]), invR);  // stored [t][p]
-      }
-    } else {
-      // last level: w[t] = (1/n_last) sum_s phi_d(s/n_last) l_t(s/n_last)
-      const AxisParams ap = load_axis(prm, d, d - 1);
-      const int rows = blockDim.x / P;
-      const int t = threadIdx.x % P, r = threadIdx.x / P;
-      double2 acc = make_double2(0.0, 0.0);
-      if (r < rows) {
-        for (int s = r; s < n_last; s += rows) {
-          const double u = (double)s / (double)n_last;
-          const double2 f = as2(phi<FAM, false>(u, ap));
-          const double l = (d == 1) ? (t == 0 ? 1.0 : 0.0) : basis_at(s_xi, s_bw, P, t, u);
-          acc.x = fma(l, f.x, acc.x);
-          if constexpr (FAM == MDI_FAM_OSC) acc.y = fma(l, f.y, acc.y);
+        if (o < P * P) {
+          const int t = o / P, p = o % P;
+          const double *Lt = L + (size_t)t * npts + (size_t)Q0 * P + p;
+          V a_e = acc[e];
+          for (int q = 0; q < nq; ++q) a_e = VOps<V>::fma_s(Lt[(size_t)q * P], s_f[q * P + p], a_e);
+          acc[e] = a_e;
         }
       }
-      s_part[threadIdx.x] = acc;
       __syncthreads();
-      if (threadIdx.x < P) {
-        double2 sum = make_double2(0.0, 0.0);
-        for (int rr = 0; rr < rows; ++rr) sum = c_add(sum, s_part[rr * P + threadIdx.x]);
-        w[threadIdx.x] = c_scale(sum, 1.0 / (double)n_last);
-      }
     }
-    __syncthreads();
+    double2 *Mp = Mpart + (size_t)b * P * P;
+#pragma unroll
+    for (int e = 0; e < kStepMaxEntries; ++e) {
+      const int o = threadIdx.x + e * kLvThreads;
+      if (o < P * P) Mp[o] = as2(acc[e]);  // stored [t][p]; scaled by 1/a^mj in the sum
+    }
+  } else {
+    last_level_row<FAM, false>(d, n_last, P, load_axis_lv(prm, d, d - 1), s_xi, s_bw, s_e64, s_part, w);
   }
+}
+
+// M_j = (1/a^mj) sum_s Mpart[j S + s], the slices in order (one thread per entry).
+__global__ void levels_step_sum_kernel(int d, int a, int m, int ns, int S, int pp,
+                                       const double2 *__restrict__ Mpart, double2 *__restrict__ M) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)ns * pp) return;
+  const int j = (int)(idx / pp), o = (int)(idx - (int64_t)j * pp);
+  const int mj = min(m, d - 1 - j * m);
+  int R = 1;
+  for (int i = 0; i < mj; ++i) R *= a;
+  const double2 *src = Mpart + (size_t)j * S * pp + o;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int s = 0; s < S; ++s) acc = c_add(acc, src[(size_t)s * pp]);
+  M[idx] = c_scale(acc, 1.0 / (double)R);
 }
 
 // cp.async helpers for staging operators into shared memory (hardware
@@ -953,32 +959,42 @@ __global__ void __launch_bounds__(kLvThreads) levels_grad_kernel(int d, int a, i
   }
 }
 
-// K4 for the step size m > 1: block b < ns takes operator k = b + 1, which
-// contracts the axes l0 = b m .. l0 + mj - 1 over the a^mj digit tuples (Q, p);
-// block ns takes the last axis.  With G_{k-1} and lambda_k recomputed from the
-// checkpoints as above, each axis ii of the operator gets
+// K4 for the step size m > 1: CTA j S + s takes slice s of operator k = j + 1,
+// which contracts the axes l0 = j m .. l0 + mj - 1 over the a^mj digit tuples
+// (Q, p) (the slices cut the tuples as in levels_step_build_kernel); the last CTA
+// takes the last axis.  With G_{k-1} and lambda_k recomputed from the checkpoints
+// as above (every slice of an operator recomputes the same two chains), each axis
+// ii of the operator gets
 //     dQ/dtheta_ii = (1/a^mj) sum_{Q,p} lambda_k[p] (prod_{jj != ii} phi_jj) dphi_ii/dtheta G~_{k-1}(x_0),
 // the product rule over the tuple's factors (x_jj = ((Q mod a^(mj-jj)) + xi_p) /
 // a^(mj-jj), as the operator's build), G~ read at x_0 from the radix-a^mj table.
+// A slice writes its partial sums (c and w for each of its axes) to Gpart, and
+// levels_step_grad_sum_kernel adds them in slice order.
 constexpr int kStepMaxM = 3;
 template <int FAM>
 __global__ void __launch_bounds__(kLvThreads) levels_step_grad_kernel(int d, int a, int n_last, int P, int m, int ns,
-                                                                      int C, const double *__restrict__ prm,
+                                                                      int S, int C, const double *__restrict__ prm,
                                                                       const double *__restrict__ Lm,
                                                                       const double *__restrict__ Lr,
                                                                       const double2 *__restrict__ M,
                                                                       const double2 *__restrict__ gck,
                                                                       const double2 *__restrict__ lck,
+                                                                      double2 *__restrict__ Gpart,
                                                                       double *__restrict__ grad) {
   using V = typename FamTraits<FAM>::V;
+  constexpr bool kExp64 = FAM != MDI_FAM_OSC;
   __shared__ double s_xi[kNodesPMax], s_bw[kNodesPMax];
+  __shared__ double s_e64[kExp64 ? kExpTable : 1];
   __shared__ V s_g[2][kNodesPMax], s_l[2][kNodesPMax];
   __shared__ V s_red[kLvThreads / kWarp];
-  __shared__ AxisParams s_ap[kStepMaxM];
+  __shared__ GradAxis s_ax[kStepMaxM];
+  __shared__ double s_inv[kStepMaxM];
   for (int t = threadIdx.x; t < P; t += blockDim.x) {
     s_xi[t] = cheb_node(t, P);
     s_bw[t] = cheb_weight(t, P);
   }
+  if constexpr (kExp64)
+    for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s_e64[j] = kExp2TableD[j];
   const int ng = C > 1 ? (ns + C - 1) / C : ns;
   double2 front = make_double2(1.0, 0.0);
   if (FAM == MDI_FAM_OSC) {
@@ -987,124 +1003,144 @@ __global__ void __launch_bounds__(kLvThreads) levels_step_grad_kernel(int d, int
     front = make_double2(cs, sn);
   }
   const int tid = threadIdx.x;
-  for (int b = blockIdx.x; b <= ns; b += gridDim.x) {
-    // G after b operators, from the checkpoint at or below it (ping-pong buffers).
-    const int j0 = b / C;
-    int cg = 0;
-    if (tid < P) s_g[0][tid] = from2<V>(gck[(size_t)j0 * P + tid]);
-    __syncthreads();
-    for (int op = j0 * C + 1; op <= b; ++op) {
-      matvec8<V, false>(M + (size_t)(op - 1) * P * P, s_g[cg], s_g[cg ^ 1], P);
-      cg ^= 1;
-      __syncthreads();
-    }
-    const V *g_b = s_g[cg];
-    if (b < ns) {
-      const int k = b + 1, l0 = b * m, mj = min(m, d - 1 - l0);
-      int R = 1;
-      for (int i = 0; i < mj; ++i) R *= a;
-      const double *L = (mj == m) ? Lm : Lr;
-      const int npts = R * P;
-      // lambda_k from the checkpoint at or above it.
-      int top = ((k + C - 1) / C) * C;
-      const double2 *src;
-      if (top > ns) {
-        top = ns;
-        src = lck + (size_t)ng * P;
-      } else {
-        src = lck + (size_t)(top / C) * P;
-      }
-      int cl = 0;
-      if (tid < P) s_l[0][tid] = from2<V>(src[tid]);
-      if (tid < mj) s_ap[tid] = load_axis(prm, d, l0 + tid);
-      __syncthreads();
-      for (int op = top; op >= k + 1; --op) {
-        matvec8<V, true>(M + (size_t)(op - 1) * P * P, s_l[cl], s_l[cl ^ 1], P);
-        cl ^= 1;
-        __syncthreads();
-      }
-      const V *l_k = s_l[cl];
-      V acc_c[kStepMaxM], acc_w[kStepMaxM];
-#pragma unroll
-      for (int ii = 0; ii < kStepMaxM; ++ii) acc_c[ii] = acc_w[ii] = VOps<V>::zero();
-      for (int i = tid; i < npts; i += blockDim.x) {
-        const int Q = i / P, p = i % P;
-        PhiGrad<FAM> pg[kStepMaxM];
-        int Ri = R;
-#pragma unroll
-        for (int ii = 0; ii < kStepMaxM; ++ii) {
-          if (ii < mj) {
-            const double x = ((double)(Q % Ri) + s_xi[p]) / (double)Ri;
-            pg[ii] = phi_grad64<FAM>(x, s_ap[ii]);
-            Ri /= a;
-          }
-        }
-        V g = VOps<V>::one();
-        if (b > 0) {
-          g = VOps<V>::zero();
-          for (int t = 0; t < P; ++t) g = VOps<V>::fma_s(L[(size_t)t * npts + i], g_b[t], g);
-        }
-        const V lg = VOps<V>::mul(l_k[p], g);
-#pragma unroll
-        for (int ii = 0; ii < kStepMaxM; ++ii) {
-          if (ii < mj) {
-            V others = lg;
-#pragma unroll
-            for (int jj = 0; jj < kStepMaxM; ++jj)
-              if (jj < mj && jj != ii) others = VOps<V>::mul(others, pg[jj].f);
-            acc_c[ii] = VOps<V>::add(acc_c[ii], VOps<V>::mul(others, pg[ii].dc));
-            acc_w[ii] = VOps<V>::add(acc_w[ii], VOps<V>::mul(others, pg[ii].dw));
-          }
-        }
-      }
-      const double invR = 1.0 / (double)R;
-#pragma unroll
-      for (int ii = 0; ii < kStepMaxM; ++ii) {
-        if (ii < mj) {  // mj is the same in every thread of the block
-          const V tc = block_sum(acc_c[ii], s_red);
-          const V tw = block_sum(acc_w[ii], s_red);
-          if (tid == 0) {
-            grad[l0 + ii] = as2(tc).x * invR;
-            if (FAM != MDI_FAM_OSC) grad[d + l0 + ii] = as2(tw).x * invR;
-          }
-        }
-      }
-    } else {
-      // last axis: dQ/dtheta_d = Re(front (1/n_last) sum_s dphi_d(s/n_last) G~(s/n_last))
-      const AxisParams ap = load_axis(prm, d, d - 1);
-      V acc_c = VOps<V>::zero(), acc_w = VOps<V>::zero();
-      for (int s = tid; s < n_last; s += blockDim.x) {
-        const double u = (double)s / (double)n_last;
-        const PhiGrad<FAM> pg = phi_grad64<FAM>(u, ap);
-        V g = VOps<V>::one();
-        if (d > 1) {
-          V num = VOps<V>::zero();
-          double den = 0.0;
-          int hit = -1;
-          for (int t = 0; t < P; ++t) {
-            if (u == s_xi[t]) {
-              hit = t;
-              continue;
-            }
-            const double wt = s_bw[t] / (u - s_xi[t]);
-            den += wt;
-            num = VOps<V>::fma_s(wt, g_b[t], num);
-          }
-          g = hit >= 0 ? g_b[hit] : VOps<V>::scale(num, 1.0 / den);
-        }
-        const V fg = from2<V>(c_mul(front, as2(g)));
-        acc_c = VOps<V>::add(acc_c, VOps<V>::mul(fg, pg.dc));
-        acc_w = VOps<V>::add(acc_w, VOps<V>::mul(fg, pg.dw));
-      }
-      const V tc = block_sum(acc_c, s_red);
-      const V tw = block_sum(acc_w, s_red);
-      if (tid == 0) {
-        grad[d - 1] = as2(tc).x / (double)n_last;
-        if (FAM != MDI_FAM_OSC) grad[2 * d - 1] = as2(tw).x / (double)n_last;
-      }
-    }
+  const int b = blockIdx.x < ns * S ? blockIdx.x / S : ns;  // operators applied before this unit
+  const int sl = blockIdx.x < ns * S ? blockIdx.x - b * S : 0;
+  // G after b operators, from the checkpoint at or below it (ping-pong buffers).
+  const int j0 = b / C;
+  int cg = 0;
+  if (tid < P) s_g[0][tid] = from2<V>(gck[(size_t)j0 * P + tid]);
+  __syncthreads();
+  for (int op = j0 * C + 1; op <= b; ++op) {
+    matvec8<V, false>(M + (size_t)(op - 1) * P * P, s_g[cg], s_g[cg ^ 1], P);
+    cg ^= 1;
     __syncthreads();
   }
+  const V *g_b = s_g[cg];
+  if (b < ns) {
+    const int k = b + 1, l0 = b * m, mj = min(m, d - 1 - l0);
+    int R = 1;
+    for (int i = 0; i < mj; ++i) R *= a;
+    const double *L = (mj == m) ? Lm : Lr;
+    const int npts = R * P;
+    const int ib = (int)((int64_t)R * sl / S) * P, ie = (int)((int64_t)R * (sl + 1) / S) * P;
+    // lambda_k from the checkpoint at or above it.
+    int top = ((k + C - 1) / C) * C;
+    const double2 *src;
+    if (top > ns) {
+      top = ns;
+      src = lck + (size_t)ng * P;
+    } else {
+      src = lck + (size_t)(top / C) * P;
+    }
+    int cl = 0;
+    if (tid < P) s_l[0][tid] = from2<V>(src[tid]);
+    if (tid < mj) {
+      const AxisParams ap = load_axis_lv(prm, d, l0 + tid);
+      s_ax[tid] = GradAxis{ap, 2.0 * ap.ic2 * rcp_signed64(ap.c)};
+      int Ri = 1;
+      for (int i = tid; i < mj; ++i) Ri *= a;
+      s_inv[tid] = 1.0 / (double)Ri;
+    }
+    __syncthreads();
+    for (int op = top; op >= k + 1; --op) {
+      matvec8<V, true>(M + (size_t)(op - 1) * P * P, s_l[cl], s_l[cl ^ 1], P);
+      cl ^= 1;
+      __syncthreads();
+    }
+    const V *l_k = s_l[cl];
+    V acc_c[kStepMaxM], acc_w[kStepMaxM];
+#pragma unroll
+    for (int ii = 0; ii < kStepMaxM; ++ii) acc_c[ii] = acc_w[ii] = VOps<V>::zero();
+    for (int i = ib + tid; i < ie; i += blockDim.x) {
+      const int Q = i / P, p = i % P;
+      PhiGrad<FAM> pg[kStepMaxM];
+      int Ri = R;
+#pragma unroll
+      for (int ii = 0; ii < kStepMaxM; ++ii) {
+        if (ii < mj) {
+          const double x = ((double)(Q % Ri) + s_xi[p]) * s_inv[ii];
+          pg[ii] = phi_grad_lv<FAM>(x, s_ax[ii].ap, s_ax[ii].dcp, s_e64);
+          Ri /= a;
+        }
+      }
+      V g = VOps<V>::one();
+      if (b > 0) {
+        g = VOps<V>::zero();
+        for (int t = 0; t < P; ++t) g = VOps<V>::fma_s(L[(size_t)t * npts + i], g_b[t], g);
+      }
+      const V lg = VOps<V>::mul(l_k[p], g);
+#pragma unroll
+      for (int ii = 0; ii < kStepMaxM; ++ii) {
+        if (ii < mj) {
+          V others = lg;
+#pragma unroll
+          for (int jj = 0; jj < kStepMaxM; ++jj)
+            if (jj < mj && jj != ii) others = VOps<V>::mul(others, pg[jj].f);
+          acc_c[ii] = VOps<V>::add(acc_c[ii], VOps<V>::mul(others, pg[ii].dc));
+          acc_w[ii] = VOps<V>::add(acc_w[ii], VOps<V>::mul(others, pg[ii].dw));
+        }
+      }
+    }
+#pragma unroll
+    for (int ii = 0; ii < kStepMaxM; ++ii) {
+      if (ii < mj) {  // mj is the same in every thread of the block
+        const V tc = block_sum(acc_c[ii], s_red);
+        const V tw = block_sum(acc_w[ii], s_red);
+        if (tid == 0) Gpart[((size_t)blockIdx.x * kStepMaxM + ii)] = make_double2(as2(tc).x, as2(tw).x);
+      }
+    }
+  } else {
+    // last axis: dQ/dtheta_d = Re(front (1/n_last) sum_s dphi_d(s/n_last) G~(s/n_last))
+    const AxisParams ap = load_axis_lv(prm, d, d - 1);
+    const double dcp = 2.0 * ap.ic2 * rcp_signed64(ap.c);
+    V acc_c = VOps<V>::zero(), acc_w = VOps<V>::zero();
+    for (int s = tid; s < n_last; s += blockDim.x) {
+      const double u = (double)s / (double)n_last;
+      const PhiGrad<FAM> pg = phi_grad_lv<FAM>(u, ap, dcp, s_e64);
+      V g = VOps<V>::one();
+      if (d > 1) {
+        V num = VOps<V>::zero();
+        double den = 0.0;
+        int hit = -1;
+        for (int t = 0; t < P; ++t) {
+          if (u == s_xi[t]) {
+            hit = t;
+            continue;
+          }
+          const double wt = s_bw[t] * rcp_signed64(u - s_xi[t]);
+          den += wt;
+          num = VOps<V>::fma_s(wt, g_b[t], num);
+        }
+        g = hit >= 0 ? g_b[hit] : VOps<V>::scale(num, rcp_signed64(den));
+      }
+      const V fg = from2<V>(c_mul(front, as2(g)));
+      acc_c = VOps<V>::add(acc_c, VOps<V>::mul(fg, pg.dc));
+      acc_w = VOps<V>::add(acc_w, VOps<V>::mul(fg, pg.dw));
+    }
+    const V tc = block_sum(acc_c, s_red);
+    const V tw = block_sum(acc_w, s_red);
+    if (tid == 0) {
+      grad[d - 1] = as2(tc).x / (double)n_last;
+      if (FAM != MDI_FAM_OSC) grad[2 * d - 1] = as2(tw).x / (double)n_last;
+    }
+  }
+}
+
+// The step-m gradients of the cluster axes: (1/a^mj) times the slices' partial
+// sums, in slice order (one thread per axis).
+template <int FAM>
+__global__ void levels_step_grad_sum_kernel(int d, int a, int m, int ns, int S, const double2 *__restrict__ Gpart,
+                                            double *__restrict__ grad) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;  // cluster axis 0 .. d-2
+  if (l >= d - 1) return;
+  const int j = l / m, ii = l - j * m, mj = min(m, d - 1 - j * m);
+  int R = 1;
+  for (int i = 0; i < mj; ++i) R *= a;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int s = 0; s < S; ++s) acc = c_add(acc, Gpart[((size_t)(j * S + s) * kStepMaxM + ii)]);
+  const double invR = 1.0 / (double)R;
+  grad[l] = acc.x * invR;
+  if (FAM != MDI_FAM_OSC) grad[d + l] = acc.y * invR;
 }
 
 // ---------------------------------------------------------------------------
@@ -1186,12 +1222,18 @@ static mdi_status run_levels(int d, int a, int n_last, const double *params, con
 }
 
 // Step size m > 1: workspace | table of radix a^m | table of radix a^rem | M (ns
-// operators) | R | w | gck | lck | misc, with ns = ceil((d-1)/m) operators in
-// groups of C.
+// operators) | their slices' partial sums | the gradient slices' partial sums | R
+// | w | gck | lck | misc, with ns = ceil((d-1)/m) operators in groups of C, each
+// cut into S slices of its tuples.
 struct StepLayout {
-  size_t Lm, Lr, M, R, w, gck, lck, misc, total;
-  int ns, ng, C, Rm, Rr;
+  size_t Lm, Lr, M, Mpart, Gpart, R, w, gck, lck, misc, total;
+  int ns, ng, C, Rm, Rr, S;
 };
+// Slices per step operator: about two CTAs per SM of a 152-SM GB300 over all
+// operators, a slice holding at least 16 tuples.
+static int step_slices(int ns, int Rm) {
+  return std::max(1, std::min((304 + ns - 1) / std::max(ns, 1), Rm / 16));
+}
 static StepLayout step_layout(int d, int64_t a, int P, int m, int checkpoint) {
   StepLayout L{};
   L.ns = (d - 1 + m - 1) / m;
@@ -1202,6 +1244,7 @@ static StepLayout step_layout(int d, int64_t a, int P, int m, int checkpoint) {
   for (int i = 0; i < m; ++i) L.Rm *= (int)a;
   L.Rr = 1;
   for (int i = 0; i < rem; ++i) L.Rr *= (int)a;
+  L.S = step_slices(L.ns, L.Rm);
   size_t off = 0;
   L.Lm = off;
   off += align_up(sizeof(double) * (size_t)L.Rm * P * P);
@@ -1209,6 +1252,10 @@ static StepLayout step_layout(int d, int64_t a, int P, int m, int checkpoint) {
   if (rem) off += align_up(sizeof(double) * (size_t)L.Rr * P * P);
   L.M = off;
   off += align_up(sizeof(double2) * (size_t)std::max(L.ns, 1) * P * P);
+  L.Mpart = off;
+  off += align_up(sizeof(double2) * (size_t)std::max(L.ns, 1) * L.S * P * P);
+  L.Gpart = off;
+  off += align_up(sizeof(double2) * (size_t)std::max(L.ns, 1) * L.S * kStepMaxM);
   L.R = off;
   if (L.C > 1) off += align_up(sizeof(double2) * (size_t)std::max(L.ng, 1) * P * P);
   L.w = off;
@@ -1253,9 +1300,16 @@ static mdi_status run_levels_step(int d, int a, int n_last, const double *params
     levels_table_kernel<false><<<(Lo.Rr * P + 7) / 8, 8 * kWarp, 0, stream>>>(P, Lo.Rr, Lr);
     if ((st = check_launch()) != MDI_OK) return st;
   }
-  levels_step_build_kernel<FAM><<<std::min(Lo.ns + 1, sm_count() * 8), kLvThreads, 0, stream>>>(
-      d, a, n_last, P, m, Lo.ns, params, Lm, Lr, M, w);
+  double2 *Mpart = (double2 *)(base + Lo.Mpart), *Gpart = (double2 *)(base + Lo.Gpart);
+  levels_step_build_kernel<FAM><<<Lo.ns * Lo.S + 1, kLvThreads, 0, stream>>>(d, a, n_last, P, m, Lo.ns, Lo.S, params,
+                                                                            Lm, Lr, Mpart, w);
   if ((st = check_launch()) != MDI_OK) return st;
+  if (Lo.ns > 0) {
+    const int64_t entries = (int64_t)Lo.ns * P * P;
+    levels_step_sum_kernel<<<(unsigned)((entries + 255) / 256), 256, 0, stream>>>(d, a, m, Lo.ns, Lo.S, P * P, Mpart,
+                                                                                M);
+    if ((st = check_launch()) != MDI_OK) return st;
+  }
   static bool attrs = false;
   if (!attrs) {
     cudaError_t e = cudaFuncSetAttribute(levels_chain_kernel<FAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1286,8 +1340,10 @@ static mdi_status run_levels_step(int d, int a, int n_last, const double *params
   levels_chain_kernel<FAM><<<1, chain_threads, chain_smem, stream>>>(d, Lo.ng, P, LC, params, ops, w, gck, lck, misc,
                                                                      value, grad, grad ? 1 : 0);
   if ((st = check_launch()) != MDI_OK || !grad) return st;
-  levels_step_grad_kernel<FAM><<<std::min(Lo.ns + 1, sm_count() * 8), kLvThreads, 0, stream>>>(
-      d, a, n_last, P, m, Lo.ns, Lo.C, params, Lm, Lr, M, gck, lck, grad);
+  levels_step_grad_kernel<FAM><<<Lo.ns * Lo.S + 1, kLvThreads, 0, stream>>>(d, a, n_last, P, m, Lo.ns, Lo.S, Lo.C,
+                                                                           params, Lm, Lr, M, gck, lck, Gpart, grad);
+  if ((st = check_launch()) != MDI_OK || d < 2) return st;
+  levels_step_grad_sum_kernel<FAM><<<(d - 1 + 255) / 256, 256, 0, stream>>>(d, a, m, Lo.ns, Lo.S, Gpart, grad);
   return check_launch();
 }
 
