@@ -57,6 +57,22 @@ def test_nodes_grad_matches_oracle(fam, d, a, nd, P, C):
     assert abs(val.item() - fwd) <= TOL * max(abs(fwd), 1.0 if fam == "osc" else 0.0)
 
 
+@pytest.mark.parametrize("fam", ["gauss", "peak"])
+@pytest.mark.parametrize("d,a,nd,P,C", [(300, 16, 16, 16, 0), (300, 24, 11, 16, 5), (300, 16, 16, 12, 0),
+                                        (520, 16, 16, 16, 40), (520, 9, 13, 16, 0)])
+def test_nodes_grad_deep_matches_oracle(fam, d, a, nd, P, C):
+    """Depths where the adjoint takes several levels per CTA (one recompute of each
+    chain for all of them) and the group products run in two stages (C >= 8), with
+    more cluster points per level than threads (a = 24) and P = 12: every component
+    against the oracle."""
+    params = inputs.random_product(fam, d, seed=3 * d + a)
+    val, g = mdi.mdi_lr_grad(fam, dev(params), d, a, nd, state="nodes", nodes=P, checkpoint=C)
+    ref = o.mdi_nodes_grad(fam, d, a, nd, P, params[:d], params[d:])
+    assert_grad_close(g.cpu().numpy(), ref, fam=fam)
+    fwd = o.mdi_nodes(fam, d, a, nd, P, params[:d], params[d:])
+    assert abs(val.item() - fwd) <= TOL * abs(fwd)
+
+
 @pytest.mark.parametrize("fam", ["exp", "osc"])
 @pytest.mark.parametrize("d,a,nd", [(1, 7, 7), (4, 16, 16), (50, 32, 32), (300, 16, 16), (1500, 2, 3), (64, 1, 9)])
 def test_closed_grad_matches_oracle(fam, d, a, nd):
