@@ -29,6 +29,7 @@
 //       theta_k = (c_k, w_k); level d uses the points s/n_last.  For OSC the
 //       phase derivative dQ/du = Re(2 pi i Q) comes from K3.
 #include <algorithm>
+#include <atomic>
 
 #include "mdi_common.cuh"
 #include "mdi_exp2_table.inc"
@@ -1146,6 +1147,29 @@ __global__ void levels_step_grad_sum_kernel(int d, int a, int m, int ns, int S, 
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
+// The chain and group kernels' dynamic shared-memory limits, set once per device
+// (an attribute belongs to the device whose context sets it; setting it twice from
+// racing threads is harmless).
+template <int FAM> static mdi_status levels_kernel_attrs() {
+  static std::atomic<int> done[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  cudaGetLastError();
+  const bool cached = dev >= 0 && dev < 64;
+  if (cached && done[dev].load(std::memory_order_acquire)) return MDI_OK;
+  cudaError_t e = cudaFuncSetAttribute(levels_chain_kernel<FAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kChainSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(levels_group_kernel<FAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(4 * sizeof(double2) * kNodesPMax * kNodesPMax));
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return MDI_ECUDA;
+  }
+  if (cached) done[dev].store(1, std::memory_order_release);
+  return MDI_OK;
+}
+
 size_t levels_workspace_bytes(int d, int64_t a, const NodesConfig &cfg, int checkpoint) {
   const int C = checkpoint > 0 ? checkpoint : default_checkpoint(d);
   return levels_layout(d, a, cfg.P, C).total;
@@ -1167,19 +1191,7 @@ static mdi_status run_levels(int d, int a, int n_last, const double *params, con
   const int grid = std::min(d, sm_count() * 8);
   levels_build_kernel<FAM, PREC><<<grid, kLvThreads, 0, stream>>>(d, a, n_last, P, params, L, M, w);
   if ((st = check_launch()) != MDI_OK) return st;
-  static bool attrs = false;
-  if (!attrs) {
-    cudaError_t e = cudaFuncSetAttribute(levels_chain_kernel<FAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kChainSmem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(levels_group_kernel<FAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(4 * sizeof(double2) * kNodesPMax * kNodesPMax));
-    if (e != cudaSuccess) {
-      set_cuda_error(e);
-      return MDI_ECUDA;
-    }
-    attrs = true;
-  }
+  if ((st = levels_kernel_attrs<FAM>()) != MDI_OK) return st;
   // Group products (skipped when every group is one level: the operators are M).
   const double2 *ops = M;
   if (C > 1 && Lo.ng > 0) {
@@ -1310,19 +1322,7 @@ static mdi_status run_levels_step(int d, int a, int n_last, const double *params
                                                                                 M);
     if ((st = check_launch()) != MDI_OK) return st;
   }
-  static bool attrs = false;
-  if (!attrs) {
-    cudaError_t e = cudaFuncSetAttribute(levels_chain_kernel<FAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kChainSmem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(levels_group_kernel<FAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(4 * sizeof(double2) * kNodesPMax * kNodesPMax));
-    if (e != cudaSuccess) {
-      set_cuda_error(e);
-      return MDI_ECUDA;
-    }
-    attrs = true;
-  }
+  if ((st = levels_kernel_attrs<FAM>()) != MDI_OK) return st;
   // The operators play the levels' part in the group products and the chain: the
   // group kernel reads its "d - 1" as the operator count.
   const double2 *ops = M;

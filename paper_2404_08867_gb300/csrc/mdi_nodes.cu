@@ -41,6 +41,7 @@
 // and differences of mirrored nodes.  The single-precision-evaluation modes take
 // phi at the float coordinate (q + xi_p)/a there, so both give phi the same floats.
 #include <algorithm>
+#include <atomic>
 
 #include "mdi_common.cuh"
 #include "mdi_fp64.cuh"
@@ -1311,15 +1312,18 @@ static bool hybrid_ok(const NodesConfig &cfg) { return cfg.block == 2 * kWarp &&
 
 template <int PREC>
 static int resident_ctas(const NodesConfig &cfg, size_t smem, bool hybrid) {
-  // Resident CTAs per SM for this (block, P, staging, schedule), queried once per process.
-  static int occ_cache[4][kNodesMaxBlock / 32 + 1][kNodesPMax / 2 + 1][2][2];
-  int &occ = occ_cache[PREC][cfg.block / 32][cfg.P / 2][cfg.stage ? 1 : 0][hybrid ? 1 : 0];
-  if (occ == 0) {
+  // Resident CTAs per SM for this (block, P, staging, schedule), queried once per
+  // process (the GPUs one process drives are taken to be of one kind).
+  static std::atomic<int> occ_cache[4][kNodesMaxBlock / 32 + 1][kNodesPMax / 2 + 1][2][2];
+  std::atomic<int> &occ = occ_cache[PREC][cfg.block / 32][cfg.P / 2][cfg.stage ? 1 : 0][hybrid ? 1 : 0];
+  int v = occ.load(std::memory_order_relaxed);
+  if (v == 0) {
     int o = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, nodes_batched_kernel<PREC>, cfg.block, smem);
-    occ = std::max(1, o);
+    v = std::max(1, o);
+    occ.store(v, std::memory_order_relaxed);
   }
-  return occ;
+  return v;
 }
 
 static size_t launch_smem(const NodesConfig &cfg, bool hybrid) {
@@ -1350,15 +1354,22 @@ static mdi_status launch_nodes(const mdi_batch_desc *descs, const int32_t *order
   const bool hybrid = split < count && hybrid_ok(cfg);
   const int split_eff = hybrid ? std::max(split, 0) : count;
   const size_t smem = launch_smem(cfg, hybrid);
-  static thread_local bool attr_set[4] = {false, false, false, false};
-  if (!attr_set[PREC]) {
+  // The dynamic shared-memory limit, set once per device and mode (an attribute
+  // belongs to the device whose context sets it; racing threads set it twice, which
+  // is harmless).
+  static std::atomic<unsigned> attr_set[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  cudaGetLastError();
+  const bool cached = dev >= 0 && dev < 64;
+  if (!cached || !(attr_set[dev].load(std::memory_order_acquire) & (1u << PREC))) {
     cudaError_t e = cudaFuncSetAttribute(nodes_batched_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)nodes_smem_bytes(kNodesMaxBlock, 2, true));
     if (e != cudaSuccess) {
       set_cuda_error(e);
       return MDI_ECUDA;
     }
-    attr_set[PREC] = true;
+    if (cached) attr_set[dev].fetch_or(1u << PREC, std::memory_order_release);
   }
   const int per_sm = cfg.ctas_per_sm ? cfg.ctas_per_sm : resident_ctas<PREC>(cfg, smem, hybrid);
   const int grid = std::max(1, std::min(count, sm_count() * per_sm));
