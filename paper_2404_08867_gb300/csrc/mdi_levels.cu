@@ -776,7 +776,7 @@ struct GradAxis {
 // warp sums per level into shared memory and one fixed-order sum at the end.  Real
 // families run in real arithmetic (the operators' imaginary parts are zero).
 template <int FAM, int E>
-__global__ void __launch_bounds__(kLvThreads) levels_grad_kernel(int d, int a, int n_last, int P, int C, int B,
+__global__ void __launch_bounds__(kLvThreads, 2) levels_grad_kernel(int d, int a, int n_last, int P, int C, int B,
                                                                  int nb, const double *__restrict__ prm,
                                                                  const double *__restrict__ L,
                                                                  const double2 *__restrict__ M,

@@ -45,7 +45,7 @@ struct SlrArgs {
 // argument's terms differs from forming x_i = r_i/n first (within a few units in
 // the last place of the argument).
 template <int FAM, bool FP32EVAL, int MAXD, bool SHIFT = false>
-__global__ void __launch_bounds__(kSlrThreads) slr_kernel(const __grid_constant__ SlrArgs args,
+__global__ void __launch_bounds__(kSlrThreads, MAXD <= 8 ? 2 : 1) slr_kernel(const __grid_constant__ SlrArgs args,
                                                           const double *__restrict__ params,
                                                           double *__restrict__ partials,
                                                           const double *__restrict__ shifts = nullptr) {
