@@ -724,14 +724,16 @@ __device__ __forceinline__ void matvec8(const double2 *__restrict__ Op, const V 
   if (row < P && part == 0) out[row] = acc;
 }
 
-// Operator entries for the recompute products of K4: four lanes per row, a lane
-// holding E = P/4 entries of it (E = 4 up to P = 16, 8 up to 32), so that a G
-// product and a lambda product run side by side, each on at most 128 threads.  On
-// GB300 a warp's FP64 instruction holds its sub-partition's FP64 unit for about 64
-// cycles: four lanes per row (E FMAs and two shuffle rounds on two warps for
-// P = 16) finish a product as soon as eight lanes per row (two FMAs and three
-// rounds on four warps) and leave the unit half the work.
-constexpr int kRecLanes = 4;
+// Operator entries for the recompute products of K4: a lane holds E entries of a
+// row, the row spread over rec_lanes(E) lanes -- E = 2 (eight lanes per row) or
+// E = 4 (four) up to P = 16, E = 8 (four) up to P = 32 -- so that a G product and a
+// lambda product run side by side, each on at most 128 threads.  On GB300 a warp's
+// FP64 instruction holds its sub-partition's FP64 unit for about 64 cycles: eight
+// lanes per row (two FMAs and three shuffle rounds) give the shortest chain of
+// dependent FP64 instructions per product, four lanes (four FMAs and two rounds on
+// half the warps) leave the unit more room for the contractions of a block of
+// levels running alongside.
+__host__ __device__ constexpr int rec_lanes(int E) { return E == 2 ? 8 : 4; }
 constexpr int kGradMaxLevels = 8;  // levels per CTA in K4
 
 template <typename V> __device__ __forceinline__ V op_entry(const double2 *e);
@@ -740,14 +742,14 @@ template <> __device__ __forceinline__ double op_entry<double>(const double2 *e)
 }
 template <> __device__ __forceinline__ double2 op_entry<double2>(const double2 *e) { return *e; }
 
-// A lane's entries (row, part + j kRecLanes), j < E, of a level operator stored
+// A lane's entries (row, part + j rec_lanes(E)), j < E, of a level operator stored
 // [t][p]: not TRANSPOSE, out[p] = sum_t Op[p][t] in[t] (row p, column t at t*P + p);
 // TRANSPOSE, out[t] = sum_p in[p] Op[p][t] (row t, column p at t*P + p).
 template <typename V, bool TRANSPOSE, int E>
 __device__ __forceinline__ void op_fetch(const double2 *__restrict__ Op, int row, int part, int P, V (&e)[E]) {
 #pragma unroll
   for (int j = 0; j < E; ++j) {
-    const int col = part + j * kRecLanes;
+    const int col = part + j * rec_lanes(E);
     if (row < P && col < P) e[j] = op_entry<V>(Op + (TRANSPOSE ? row * P + col : col * P + row));
   }
 }
@@ -849,9 +851,10 @@ __global__ void __launch_bounds__(kLvThreads, 2) levels_grad_kernel(int d, int a
   // Side 0 (G) and side 1 (lambda) take the first whole warps: for P = 16 warps 0-1
   // and 2-3, one per SM sub-partition, so that the two chains' FP64 instructions
   // queue on different units; the other warps sit the chains out.
-  const int side_threads = (P * kRecLanes + kWarp - 1) / kWarp * kWarp;
+  constexpr int LR = rec_lanes(E);
+  const int side_threads = (P * LR + kWarp - 1) / kWarp * kWarp;
   const int side = tid / side_threads, li = tid % side_threads;
-  const int row = li / kRecLanes, part = li % kRecLanes;
+  const int row = li / LR, part = li % LR;
   const int mine = side == 0 ? nG : side == 1 ? nL : 0;
   const size_t pp = (size_t)P * P;
   // Operator of step st: G side g0 C + 1 + st, lambda side top - st (1-based).
@@ -879,13 +882,13 @@ __global__ void __launch_bounds__(kLvThreads, 2) levels_grad_kernel(int d, int a
       V acc = O::zero();
 #pragma unroll
       for (int j = 0; j < E; ++j) {
-        const int col = part + j * kRecLanes;
+        const int col = part + j * LR;
         if (row < P && col < P) {
           if constexpr (FAM == MDI_FAM_OSC) acc = c_add(acc, c_mul(cur[j], in[col]));
           else acc = fma(cur[j], in[col], acc);
         }
       }
-      acc = group_sum(acc, kRecLanes);
+      acc = group_sum(acc, LR);
       if (row < P && part == 0) (side ? s_l[lslot(st + 1)] : s_g[gslot(st + 1)])[row] = acc;
 #pragma unroll
       for (int j = 0; j < E; ++j) cur[j] = nxt[j];
@@ -1222,7 +1225,10 @@ static mdi_status run_levels(int d, int a, int n_last, const double *params, con
     const int B = std::max(1, std::min({kGradMaxLevels, C, (d + 255) / 256}));
     const int nb = (C + B - 1) / B;
     const int grid = Lo.ng * nb + 1;
-    if (P <= 16)
+    if (P <= 16 && B == 1)
+      levels_grad_kernel<FAM, 2><<<grid, kLvThreads, 0, stream>>>(d, a, n_last, P, C, B, nb, params, L, M, gck, lck,
+                                                                   grad);
+    else if (P <= 16)
       levels_grad_kernel<FAM, 4><<<grid, kLvThreads, 0, stream>>>(d, a, n_last, P, C, B, nb, params, L, M, gck, lck,
                                                                    grad);
     else
