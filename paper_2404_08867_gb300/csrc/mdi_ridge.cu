@@ -12,9 +12,9 @@
 // GB300 mapping: the d - 1 box convolutions run in ONE launch of a thread-block
 // cluster (16 CTAs where the GPU allows it, else 8), each CTA holding a slice of
 // the histogram in shared memory: per level the CTA forms its weights from
-// power-of-two window sums (a few additions per weight instead of N - 1), stores
-// its last N - 1 weights into the next CTA's halo through distributed shared
-// memory, and a cluster barrier separates the levels.  (A histogram too long for
+// power-of-two window sums (a few additions per weight instead of N - 1); every
+// K levels it stores its last K (N - 1) weights into the next CTA's shared memory
+// and a cluster barrier follows, the CTAs recomputing the halo in between.  (A histogram too long for
 // the cluster's shared memory takes one launch per axis instead, with N-term sums
 // in the oracle's order, so its weights are bitwise the oracle's.)  Then one launch over every (S, k) pair of the last axis -- the whole
 // GPU -- with a block sum per CTA, and a one-CTA sum of the CTA partials in order.
@@ -71,12 +71,20 @@ __device__ __forceinline__ void cluster_store(unsigned addr, double v) {
 }
 
 // H_{d-1} by d - 1 box convolutions in one cluster of cs CTAs.  CTA c holds the
-// weights S in [c W, (c + 1) W) in two shared buffers (levels i - 1 and i), each
-// preceded by a halo of N - 1 entries (the previous CTA's last weights; zeros for
-// CTA 0, where S - k < 0).  Weights past the level's length are never written and
-// stay zero.  Every CTA passes the same d + 1 barriers, and the last remote store
+// weights S in [c W, (c + 1) W) in two level buffers, each preceded by a halo of
+// K (N - 1) entries.  Every K levels the CTAs exchange: each sends its last
+// K (N - 1) weights into the next CTA's receive buffer through distributed shared
+// memory, a cluster barrier follows, and each copies what it received into its
+// halo (CTA 0's halo stays zero: S < 0).  In between, a CTA recomputes the part of
+// the previous CTA's slice that its own next levels read -- the halo shrinks by
+// N - 1 per level -- so the cluster passes one barrier per K levels instead of one
+// per level; a recomputed weight is bitwise the owner's (the same operations on
+// the same inputs).  Weights past a level's length are never written and stay
+// zero.  Receive buffers alternate between exchanges, so a CTA that runs ahead
+// never overwrites one its neighbour has not copied yet (that takes passing the
+// next barrier).  Every CTA passes the same barriers, and the last remote store
 // comes before the last barrier, so no CTA leaves while another may still write
-// its shared memory.  W >= N - 1.
+// its shared memory.  W >= K (N - 1).
 //
 // A level's N-term window sums are built from power-of-two windows, as N's binary
 // digits: p_1 = H_{i-1}, p_2s[x] = p_s[x] + p_s[x - s], and each set bit s of N adds
@@ -85,31 +93,41 @@ __device__ __forceinline__ void cluster_store(unsigned addr, double v) {
 // then one multiply by 1/N.  The terms are the oracle's, all positive, summed in a
 // tree order: each weight is within about (log2 N + 2) units in the last place of
 // the oracle's sequential sum.  Two more buffers hold the p_s.
-__global__ void __launch_bounds__(kRidgeThreads) ridge_cluster_kernel(int d, int N, int W, double inv_n,
+__global__ void __launch_bounds__(kRidgeThreads) ridge_cluster_kernel(int d, int N, int W, int K, double inv_n,
                                                                       double *__restrict__ hout) {
-  extern __shared__ double s_h[];  // [4][N - 1 + W]: levels i - 1 and i, two p_s buffers
+  extern __shared__ double s_h[];  // [4][K (N - 1) + W]: levels i - 1 and i, two p_s buffers; [2][K (N - 1)] receive
   const int c = (int)cluster_rank(), cs = (int)gridDim.x;
-  const int H = N - 1, stride = H + W, S0 = c * W;
-  for (int i = threadIdx.x; i < 4 * stride; i += blockDim.x) s_h[i] = 0.0;
-  cluster_barrier();  // every buffer is zero before H_0 is written into one
-  if (c == 0 && threadIdx.x == 0) {
-    s_h[H] = 1.0;  // H_0 = [1]
-    // With W = N - 1 the next CTA's halo holds S = 0 as well.
-    if (W == H && cs > 1) cluster_store(cluster_map(s_h, 1), 1.0);
-  }
-  cluster_barrier();
-  double *tmp[2] = {s_h + 2 * stride + H, s_h + 3 * stride + H};
-  int cur = 0;
+  const int H = N - 1, KH = K * H, stride = KH + W, S0 = c * W;
+  double *const recv = s_h + 4 * stride;
+  for (int i = threadIdx.x; i < 4 * stride + 2 * KH; i += blockDim.x) s_h[i] = 0.0;
+  cluster_barrier();  // every buffer is zero before any remote store lands
+  if (c == 0 && threadIdx.x == 0) s_h[KH] = 1.0;  // H_0 = [1]
+  __syncthreads();
+  double *tmp[2] = {s_h + 2 * stride + KH, s_h + 3 * stride + KH};
+  int cur = 0, ex = 0;
   for (int i = 1; i < d; ++i) {
-    const int len = i * H + 1;  // weights of level i: S < len
-    const double *P = s_h + cur * stride + H;  // p_1 = H_{i-1} at local positions -H .. W-1
-    double *out = s_h + (cur ^ 1) * stride + H;
+    const int j = (i - 1) % K;
+    double *const Pb = s_h + cur * stride + KH;  // H_{i-1} at local positions -KH .. W-1
+    if (j == 0) {
+      double *const rb = recv + (ex & 1) * KH;
+      if (c + 1 < cs)
+        for (int t = threadIdx.x; t < KH; t += blockDim.x) cluster_store(cluster_map(rb + t, c + 1), Pb[W - KH + t]);
+      cluster_barrier();
+      if (c > 0)
+        for (int t = threadIdx.x; t < KH; t += blockDim.x) Pb[t - KH] = rb[t];
+      __syncthreads();
+      ++ex;
+    }
+    const int len = i * H + 1;          // weights of level i: S < len
+    const int lo = -(K - 1 - j) * H;    // what the levels up to the next exchange read
     const int hi = min(W, len - S0);
+    const double *P = Pb;
+    double *out = s_h + (cur ^ 1) * stride + KH;
     int m = 0, t = 0;
     for (int span = 1; span <= N; span <<= 1) {
       if (N & span) {  // window of offsets [m, m + span) joins the partial sum
         const bool last = m + span == N, first = m == 0;
-        for (int x = threadIdx.x; x < hi; x += blockDim.x) {
+        for (int x = lo + (int)threadIdx.x; x < hi; x += blockDim.x) {
           double v = first ? P[x - m] : out[x] + P[x - m];
           out[x] = last ? v * inv_n : v;
         }
@@ -117,19 +135,16 @@ __global__ void __launch_bounds__(kRidgeThreads) ridge_cluster_kernel(int d, int
       }
       if (2 * span <= N) {  // p_2s on the positions the remaining bits read
         double *Pn = tmp[t];
-        for (int x = threadIdx.x - (N - 2 * span); x < hi; x += blockDim.x) Pn[x] = P[x] + P[x - span];
+        for (int x = lo + (int)threadIdx.x - (N - 2 * span); x < hi; x += blockDim.x) Pn[x] = P[x] + P[x - span];
         P = Pn;
         t ^= 1;
       }
       __syncthreads();
     }
-    if (c + 1 < cs)
-      for (int j = threadIdx.x; j < H; j += blockDim.x) cluster_store(cluster_map(out - H + j, c + 1), out[W - H + j]);
-    cluster_barrier();
     cur ^= 1;
   }
   const int len = (d - 1) * H + 1;
-  const double *fin = s_h + cur * stride + H;
+  const double *fin = s_h + cur * stride + KH;
   for (int s = threadIdx.x; s < min(W, len - S0); s += blockDim.x) hout[S0 + s] = fin[s];
 }
 
@@ -167,8 +182,14 @@ static int ridge_grid(uint64_t len) {
                                                        (uint64_t)sm_count() * 8));
 }
 
-// The cluster path: at most kRidgeClusterSmem bytes of shared memory per CTA.
+// The cluster path: at most kRidgeClusterSmem bytes of shared memory per CTA, and
+// at most kRidgeMaxK levels between exchanges.
 constexpr size_t kRidgeClusterSmem = 200 * 1024;
+constexpr uint64_t kRidgeMaxK = 8;
+static size_t ridge_cluster_smem(uint64_t W, int64_t N, uint64_t K) {
+  const uint64_t KH = K * (uint64_t)(N - 1);
+  return sizeof(double) * (4 * (KH + W) + 2 * KH);
+}
 
 // Largest cluster the GPU runs ridge_cluster_kernel in (16, else 8), once per
 // device; 0 if neither launches.
@@ -234,16 +255,18 @@ mdi_status ridge_launch(int d, int64_t N, int64_t n_last, double c0, double p, d
   const int cmax = N > 1 ? ridge_cluster_size() : 0;
   int cs = 0;
   uint64_t W = 0;
+  uint64_t K = 1;  // levels per exchange
   if (cmax > 0 && N <= 4096) {
     cs = (int)std::min<uint64_t>((uint64_t)cmax, std::max<uint64_t>(1, L / (uint64_t)(N - 1)));
     W = (L + cs - 1) / cs;
-    if (W < (uint64_t)(N - 1) || 4 * sizeof(double) * (W + (uint64_t)N - 1) > kRidgeClusterSmem) cs = 0;
+    K = std::max<uint64_t>(1, std::min<uint64_t>(kRidgeMaxK, W / (uint64_t)(N - 1)));
+    if (W < (uint64_t)(N - 1) || ridge_cluster_smem(W, N, K) > kRidgeClusterSmem) cs = 0;
   }
   if (cs > 0) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs);
     cfg.blockDim = dim3(kRidgeThreads);
-    cfg.dynamicSmemBytes = 4 * sizeof(double) * (W + (uint64_t)N - 1);
+    cfg.dynamicSmemBytes = ridge_cluster_smem(W, N, K);
     cfg.stream = stream;
     cudaLaunchAttribute attr;
     attr.id = cudaLaunchAttributeClusterDimension;
@@ -252,7 +275,8 @@ mdi_status ridge_launch(int d, int64_t N, int64_t n_last, double c0, double p, d
     attr.val.clusterDim.z = 1;
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, ridge_cluster_kernel, d, (int)N, (int)W, 1.0 / (double)N, buf[0]);
+    const cudaError_t e =
+        cudaLaunchKernelEx(&cfg, ridge_cluster_kernel, d, (int)N, (int)W, (int)K, 1.0 / (double)N, buf[0]);
     if (e != cudaSuccess) {  // a cluster the GPU refuses now: the per-level launches below
       cudaGetLastError();
       cs = 0;
