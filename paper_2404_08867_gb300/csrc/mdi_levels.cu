@@ -1212,10 +1212,26 @@ static mdi_status run_levels(int d, int a, int n_last, const double *params, con
     if ((st = check_launch()) != MDI_OK) return st;
     ops = R;
   }
+  // The value alone needs no checkpoints: with many groups, the chain runs over
+  // products of about sqrt(ng) consecutive group products (one more product stage,
+  // written over the level operators, which are no longer read), so the sequence of
+  // dependent matrix-vector products is about 2 sqrt(ng) long instead of ng.
+  int nchain = Lo.ng;
+  if (!grad && C > 1 && Lo.ng >= 16) {
+    int s = 1;
+    while (s * s < Lo.ng) ++s;
+    const int nsg = (Lo.ng + s - 1) / s;
+    const size_t group_smem = 4 * sizeof(double2) * (size_t)P * P;
+    const int gthreads = std::max(32, (P * P + 31) / 32 * 32);
+    levels_group_kernel<FAM><<<nsg, gthreads, group_smem, stream>>>(Lo.ng + 1, P, s, s, 1, 0, ops, M);
+    if ((st = check_launch()) != MDI_OK) return st;
+    ops = M;
+    nchain = nsg;
+  }
   const int LC = chain_levels_per_chunk(P);
   const size_t chain_smem = 2 * (size_t)LC * P * P * sizeof(double2);
   const int chain_threads = std::max(32, (8 * P + 31) / 32 * 32);
-  levels_chain_kernel<FAM><<<1, chain_threads, chain_smem, stream>>>(d, Lo.ng, P, LC, params, ops, w, gck, lck, misc,
+  levels_chain_kernel<FAM><<<1, chain_threads, chain_smem, stream>>>(d, nchain, P, LC, params, ops, w, gck, lck, misc,
                                                                      value, grad, grad ? 1 : 0);
   if ((st = check_launch()) != MDI_OK) return st;
   if (grad) {

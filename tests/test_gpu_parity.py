@@ -212,6 +212,22 @@ def test_nodes_state_matches_oracle(fam, d, a, nd, P):
     close(got, o.mdi_nodes(fam, d, a, nd, P, params[:d], params[d:]), fam)
 
 
+@pytest.mark.parametrize("fam", ["gauss", "peak", "exp", "osc"])
+@pytest.mark.parametrize("d,a,nd,C", [(260, 16, 16, 0), (520, 12, 7, 0), (1000, 16, 16, 0), (300, 16, 16, 4),
+                                      (257, 5, 9, 16)])
+def test_nodes_state_deep_forward(fam, d, a, nd, C):
+    """The value alone at depths with 16 or more checkpoint groups, where the chain
+    runs over products of group products (one more product stage), against the
+    oracle; and the same value from the adjoint call, which keeps every group
+    boundary."""
+    params = inputs.random_product(fam, d, seed=5 * d + a)
+    got = mdi.mdi_lr_integrate(fam, dev(params), d, a, nd, state="nodes", checkpoint=C).item()
+    ref = o.mdi_nodes(fam, d, a, nd, 16, params[:d], params[d:])
+    close(got, ref, fam)
+    val, _ = mdi.mdi_lr_grad(fam, dev(params), d, a, nd, state="nodes", checkpoint=C)
+    close(val.item(), ref, fam)
+
+
 @pytest.mark.parametrize("block", [32, 64, 128, 512])
 def test_nodes_block_shapes(block):
     """Short integrals (d < 8) run on one CTA of the batched kernel: every block shape."""
