@@ -59,12 +59,14 @@ def test_nodes_grad_matches_oracle(fam, d, a, nd, P, C):
 
 @pytest.mark.parametrize("fam", ["gauss", "peak"])
 @pytest.mark.parametrize("d,a,nd,P,C", [(300, 16, 16, 16, 0), (300, 24, 11, 16, 5), (300, 16, 16, 12, 0),
-                                        (520, 16, 16, 16, 40), (520, 9, 13, 16, 0)])
+                                        (520, 16, 16, 16, 40), (520, 9, 13, 16, 0), (300, 8, 8, 32, 0),
+                                        (20, 6, 6, 32, 3), (12, 4, 5, 2, 2), (15, 9, 9, 4, 0)])
 def test_nodes_grad_deep_matches_oracle(fam, d, a, nd, P, C):
     """Depths where the adjoint takes several levels per CTA (one recompute of each
     chain for all of them) and the group products run in two stages (C >= 8), with
-    more cluster points per level than threads (a = 24) and P = 12: every component
-    against the oracle."""
+    more cluster points per level than threads (a = 24), P = 12 and P = 32 (four
+    lanes and eight entries per operator row), and shallow cases with P = 2, 4, 32:
+    every component against the oracle."""
     params = inputs.random_product(fam, d, seed=3 * d + a)
     val, g = mdi.mdi_lr_grad(fam, dev(params), d, a, nd, state="nodes", nodes=P, checkpoint=C)
     ref = o.mdi_nodes_grad(fam, d, a, nd, P, params[:d], params[d:])
