@@ -286,10 +286,12 @@ mdi_status mdi_lr_workspace_size(int32_t family, int32_t d, int64_t a, int64_t n
  * NODES (d <= 65536, a <= 64, n_last <= 4096): every level's P x P operator is
  * built in parallel, one CTA runs the forward and the reverse (adjoint) chains
  * keeping level states only every opts->checkpoint levels (0: ceil(sqrt(d))),
- * and each level's contribution is then formed in parallel after recomputing its
- * states from the nearest checkpoints.  With opts->step = m > 1 the same runs over
- * the step-m operators (one per m axes), and each operator's m axes take their
- * derivatives by the product rule over the a^m digit tuples.
+ * and the levels' contributions are then formed in parallel, each CTA taking a
+ * block of consecutive levels of one checkpoint group and recomputing their
+ * states once from the nearest checkpoints.  With opts->step = m > 1 the same
+ * runs over the step-m operators (one per m axes), and each operator's m axes
+ * take their derivatives by the product rule over the a^m digit tuples, which
+ * are cut into slices on separate CTAs.
  * ------------------------------------------------------------------------- */
 mdi_status mdi_lr_grad(int32_t family, int32_t d, int64_t a, int64_t n_last, const int64_t *z,
                        const double *params, const mdi_opts *opts, double *value, double *grad, void *workspace,
@@ -400,8 +402,9 @@ mdi_status mdi_get_device_status(const void *workspace, size_t ws_bytes, int32_t
  *   out        DEVICE, one double
  *   workspace  DEVICE, >= mdi_midpoint_ridge_workspace_size bytes, 256-byte aligned
  * Three launches on `stream`, FP64: the d - 1 levels in one thread-block cluster
- * (the histogram split over its CTAs' shared memory, a cluster barrier per level;
- * d + 1 plain launches instead when the histogram does not fit), every (S, k)
+ * (the histogram split over its CTAs' shared memory, halos exchanged and a
+ * cluster barrier every K <= 8 levels; d + 1 plain launches instead when the
+ * histogram does not fit), every (S, k)
  * pair of the last axis, and the sum of the partials.  MDI_EINVAL unless d, N,
  * n_last >= 1, c0 > 0 and power finite, (d-1)(N-1) + 1 <= 2^26 and
  * ((d-1)(N-1) + 1) n_last <= 2^62; MDI_EWORKSPACE for a bad workspace.  f_6's integral is 1/(d+1)!, which leaves the double range near
