@@ -455,7 +455,6 @@ __global__ void levels_step_sum_kernel(int d, int a, int m, int ns, int S, int p
 // cp.async helpers for staging operators into shared memory (hardware
 // wait_group, double-buffered), so no product waits on an L2 round trip.
 constexpr int kChainMaxThreads = 8 * kNodesPMax;  // eight lanes per row of a P x P product
-constexpr int kChainSmem = 64 * 1024;  // two buffers of operators
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -565,9 +564,12 @@ template <> __device__ __forceinline__ double2 group_sum<double2>(double2 v, int
   return v;
 }
 
-static int chain_levels_per_chunk(int P) {
-  return std::max(1, std::min(8, kChainSmem / 2 / (P * P * (int)sizeof(double2))));
+// One entry of a level operator: real families read the real part only.
+template <typename V> __device__ __forceinline__ V op_entry(const double2 *e);
+template <> __device__ __forceinline__ double op_entry<double>(const double2 *e) {
+  return reinterpret_cast<const double *>(e)[0];
 }
+template <> __device__ __forceinline__ double2 op_entry<double2>(const double2 *e) { return *e; }
 
 // K3: the chain over the ng group operators (R_g, or M_k when C = 1), forward
 // with a checkpoint at every group boundary and the value, backward for the
@@ -575,11 +577,17 @@ static int chain_levels_per_chunk(int P) {
 // summing every eighth term, then three shuffle rounds (on GB300 a warp's FP64
 // instruction holds its sub-partition's FP64 unit for about 64 cycles, so fewer,
 // fuller warps finish a product sooner than one multiply per thread); the vector
-// is double-buffered in shared memory, one barrier per product; all threads stage
-// the next chunk of operators with cp.async.  Real families use real arithmetic
-// on the real parts.  misc[0] = Q before the front factor.
+// is double-buffered in shared memory, one barrier per product.  Each lane reads
+// its entries of the operators straight from global memory into a ring of
+// registers kChainAhead products ahead of their use, so no product waits on an L2
+// round trip and nothing is staged through shared memory.  Real families use real
+// arithmetic on the real parts (and load only those).  misc[0] = Q before the
+// front factor.
+constexpr int kChainAhead = 4;                  // products in flight per lane
+constexpr int kChainMaxE = kNodesPMax / 8;      // entries per lane and product
+
 template <int FAM>
-__global__ void __launch_bounds__(kChainMaxThreads) levels_chain_kernel(int d, int ng, int P, int LC,
+__global__ void __launch_bounds__(kChainMaxThreads) levels_chain_kernel(int d, int ng, int P,
                                                                      const double *__restrict__ prm,
                                                                      const double2 *__restrict__ ops,
                                                                      const double2 *__restrict__ w,
@@ -589,54 +597,71 @@ __global__ void __launch_bounds__(kChainMaxThreads) levels_chain_kernel(int d, i
                                                                      double *__restrict__ value,
                                                                      double *__restrict__ grad, int adjoint) {
   using V = typename FamTraits<FAM>::V;
-  extern __shared__ __align__(16) unsigned char chain_smem[];
-  double2 *const buf0 = (double2 *)chain_smem;  // two chunks of LC operators
-  const size_t bstride = (size_t)LC * P * P;
+  using O = VOps<V>;
   __shared__ V s_v[2][kNodesPMax];  // the chain's vector, double-buffered
   const int row = threadIdx.x >> 3, part = threadIdx.x & 7;
   const bool rowok = row < P;
   const int p = threadIdx.x;
   const bool on = p < P;
-  // out[row] = sum_col Rk[row][col] v[col] (Rk row-major as staged), into s_v[nb]
-  auto product = [&](const double2 *Rk, int vb) -> V {
-    V acc = VOps<V>::zero();
-    if (rowok)
-      for (int col = part; col < P; col += 8) {
-        const double2 m = Rk[row * P + col];
-        if constexpr (FAM == MDI_FAM_OSC) acc = c_add(acc, c_mul(m, s_v[vb][col]));
-        else acc = fma(m.x, s_v[vb][col], acc);
-      }
-    return group_sum(acc, 8);
+  const size_t pp = (size_t)P * P;
+  // This lane's entries of product st: forward, operator st + 1, row p and column
+  // t at t*P + p; backward, operator ng - st transposed, row t and column p at
+  // t*P + p.
+  auto fetch = [&](bool fwd, int st, V(&e)[kChainMaxE]) {
+    const double2 *Op = ops + (size_t)(fwd ? st : ng - 1 - st) * pp;
+#pragma unroll
+    for (int j = 0; j < kChainMaxE; ++j) {
+      const int col = part + 8 * j;
+      if (rowok && col < P) e[j] = op_entry<V>(Op + (fwd ? col * P + row : row * P + col));
+    }
   };
-  int vb = 0;
-  if (on) s_v[0][p] = VOps<V>::one();
-  __syncthreads();
-  if (on) gck[p] = as2(s_v[0][p]);
-  const int nchunks = (ng + LC - 1) / LC;
-  // Forward: chunk c holds operators 1 + c*LC .. min(ng, (c+1)*LC), staged as [p][t].
-  // S_k[p] = sum_t R_k[p][t] S_{k-1}[t]: row = p, col = t.
-  if (nchunks > 0) stage_ops(buf0, ops, 1, std::min(LC, ng), P, true);
-  for (int c = 0; c < nchunks; ++c) {
-    const int k0 = 1 + c * LC, k1 = std::min(ng, (c + 1) * LC);
-    if (c + 1 < nchunks) {
-      const int n0 = k1 + 1;
-      stage_ops(buf0 + ((c + 1) & 1) * bstride, ops, n0, std::min(LC, ng - n0 + 1), P, true);
-      cp_async_wait_prev();
-    } else {
-      cp_async_wait_all();
-    }
-    __syncthreads();
-    const double2 *B = buf0 + (c & 1) * bstride;
-    for (int k = k0; k <= k1; ++k) {
-      const V prod = product(B + (size_t)(k - k0) * P * P, vb);
-      if (rowok && part == 0) {
-        s_v[vb ^ 1][row] = prod;
-        gck[(size_t)k * P + row] = as2(prod);
+  // The ng products in order; the new vector of product st goes to the checkpoint
+  // st + 1 (forward) or ng - 1 - st (backward).  Returns the buffer holding the
+  // last vector.
+  auto run = [&](bool fwd, double2 *ck) -> int {
+    int vb = 0;
+    V ring[kChainAhead][kChainMaxE];
+#pragma unroll
+    for (int u = 0; u < kChainAhead; ++u)
+#pragma unroll
+      for (int j = 0; j < kChainMaxE; ++j) ring[u][j] = O::zero();
+#pragma unroll
+    for (int u = 0; u < kChainAhead; ++u)
+      if (u < ng) fetch(fwd, u, ring[u]);
+    for (int k0 = 0; k0 < ng; k0 += kChainAhead) {
+#pragma unroll
+      for (int u = 0; u < kChainAhead; ++u) {
+        const int st = k0 + u;
+        if (st < ng) {  // the same in every thread
+          V acc = O::zero();
+#pragma unroll
+          for (int j = 0; j < kChainMaxE; ++j) {
+            const int col = part + 8 * j;
+            if (rowok && col < P) {
+              if constexpr (FAM == MDI_FAM_OSC) acc = c_add(acc, c_mul(ring[u][j], s_v[vb][col]));
+              else acc = fma(ring[u][j], s_v[vb][col], acc);
+            }
+          }
+          acc = group_sum(acc, 8);
+          if (st + kChainAhead < ng) fetch(fwd, st + kChainAhead, ring[u]);
+          if (rowok && part == 0) {
+            s_v[vb ^ 1][row] = acc;
+            ck[(size_t)(fwd ? st + 1 : ng - 1 - st) * P + row] = as2(acc);
+          }
+          vb ^= 1;
+          __syncthreads();
+        }
       }
-      vb ^= 1;
-      __syncthreads();
     }
+    return vb;
+  };
+  if (on) {
+    s_v[0][p] = O::one();
+    gck[p] = as2(O::one());
   }
+  __syncthreads();
+  // Forward: S_k[p] = sum_t R_k[p][t] S_{k-1}[t], checkpoints gck[1..ng].
+  const int vb = run(true, gck);
   // Q = front * sum_t w[t] G_{d-1}[t]
   double2 front = make_double2(1.0, 0.0);
   if (FAM == MDI_FAM_OSC) {
@@ -665,41 +690,14 @@ __global__ void __launch_bounds__(kChainMaxThreads) levels_chain_kernel(int d, i
   if (!adjoint) return;
   __syncthreads();
   // lambda at b_ng = d-1 is front * w (real for real families: front = 1, w real).
-  vb = 0;
   if (on) {
     const double2 l = c_mul(front, w[p]);
     s_v[0][p] = from2<V>(l);
     lck[(size_t)ng * P + p] = l;
   }
   __syncthreads();
-  // Backward: chunk c holds operators max(1, top - LC + 1) .. top, top = ng - c*LC,
-  // staged as stored ([t][p]).  Lambda_{k-1}[t] = sum_p Lambda_k[p] R_k[p][t]:
-  // row = t, col = p.
-  if (nchunks > 0) {
-    const int top = ng, bot = std::max(1, top - LC + 1);
-    stage_ops(buf0, ops, bot, top - bot + 1, P, false);
-  }
-  for (int c = 0; c < nchunks; ++c) {
-    const int top = ng - c * LC, bot = std::max(1, top - LC + 1);
-    if (c + 1 < nchunks) {
-      const int ntop = bot - 1, nbot = std::max(1, ntop - LC + 1);
-      stage_ops(buf0 + ((c + 1) & 1) * bstride, ops, nbot, ntop - nbot + 1, P, false);
-      cp_async_wait_prev();
-    } else {
-      cp_async_wait_all();
-    }
-    __syncthreads();
-    const double2 *B = buf0 + (c & 1) * bstride;
-    for (int k = top; k >= bot; --k) {
-      const V prod = product(B + (size_t)(k - bot) * P * P, vb);
-      if (rowok && part == 0) {
-        s_v[vb ^ 1][row] = prod;
-        lck[(size_t)(k - 1) * P + row] = as2(prod);
-      }
-      vb ^= 1;
-      __syncthreads();
-    }
-  }
+  // Backward: Lambda_{k-1}[t] = sum_p Lambda_k[p] R_k[p][t], checkpoints lck[ng-1..0].
+  run(false, lck);
 }
 
 // Product of a level operator (stored [t][p]: entry (p, t) at t*P + p) with a
@@ -736,11 +734,6 @@ __device__ __forceinline__ void matvec8(const double2 *__restrict__ Op, const V 
 __host__ __device__ constexpr int rec_lanes(int E) { return E == 2 ? 8 : 4; }
 constexpr int kGradMaxLevels = 8;  // levels per CTA in K4
 
-template <typename V> __device__ __forceinline__ V op_entry(const double2 *e);
-template <> __device__ __forceinline__ double op_entry<double>(const double2 *e) {
-  return reinterpret_cast<const double *>(e)[0];  // real families: the real part only
-}
-template <> __device__ __forceinline__ double2 op_entry<double2>(const double2 *e) { return *e; }
 
 // A lane's entries (row, part + j rec_lanes(E)), j < E, of a level operator stored
 // [t][p]: not TRANSPOSE, out[p] = sum_t Op[p][t] in[t] (row p, column t at t*P + p);
@@ -1150,7 +1143,7 @@ __global__ void levels_step_grad_sum_kernel(int d, int a, int m, int ns, int S, 
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-// The chain and group kernels' dynamic shared-memory limits, set once per device
+// The group kernel's dynamic shared-memory limit, set once per device
 // (an attribute belongs to the device whose context sets it; setting it twice from
 // racing threads is harmless).
 template <int FAM> static mdi_status levels_kernel_attrs() {
@@ -1160,11 +1153,8 @@ template <int FAM> static mdi_status levels_kernel_attrs() {
   cudaGetLastError();
   const bool cached = dev >= 0 && dev < 64;
   if (cached && done[dev].load(std::memory_order_acquire)) return MDI_OK;
-  cudaError_t e = cudaFuncSetAttribute(levels_chain_kernel<FAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kChainSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(levels_group_kernel<FAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(4 * sizeof(double2) * kNodesPMax * kNodesPMax));
+  const cudaError_t e = cudaFuncSetAttribute(levels_group_kernel<FAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(4 * sizeof(double2) * kNodesPMax * kNodesPMax));
   if (e != cudaSuccess) {
     set_cuda_error(e);
     return MDI_ECUDA;
@@ -1228,11 +1218,9 @@ static mdi_status run_levels(int d, int a, int n_last, const double *params, con
     ops = M;
     nchain = nsg;
   }
-  const int LC = chain_levels_per_chunk(P);
-  const size_t chain_smem = 2 * (size_t)LC * P * P * sizeof(double2);
   const int chain_threads = std::max(32, (8 * P + 31) / 32 * 32);
-  levels_chain_kernel<FAM><<<1, chain_threads, chain_smem, stream>>>(d, nchain, P, LC, params, ops, w, gck, lck, misc,
-                                                                     value, grad, grad ? 1 : 0);
+  levels_chain_kernel<FAM><<<1, chain_threads, 0, stream>>>(d, nchain, P, params, ops, w, gck, lck, misc, value, grad,
+                                                            grad ? 1 : 0);
   if ((st = check_launch()) != MDI_OK) return st;
   if (grad) {
     // Blocks of B levels per CTA: one level each while the grid stays near 256 CTAs
@@ -1356,11 +1344,9 @@ static mdi_status run_levels_step(int d, int a, int n_last, const double *params
     if ((st = check_launch()) != MDI_OK) return st;
     ops = Rg;
   }
-  const int LC = chain_levels_per_chunk(P);
-  const size_t chain_smem = 2 * (size_t)LC * P * P * sizeof(double2);
   const int chain_threads = std::max(32, (8 * P + 31) / 32 * 32);
-  levels_chain_kernel<FAM><<<1, chain_threads, chain_smem, stream>>>(d, Lo.ng, P, LC, params, ops, w, gck, lck, misc,
-                                                                     value, grad, grad ? 1 : 0);
+  levels_chain_kernel<FAM><<<1, chain_threads, 0, stream>>>(d, Lo.ng, P, params, ops, w, gck, lck, misc, value, grad,
+                                                            grad ? 1 : 0);
   if ((st = check_launch()) != MDI_OK || !grad) return st;
   levels_step_grad_kernel<FAM><<<Lo.ns * Lo.S + 1, kLvThreads, 0, stream>>>(d, a, n_last, P, m, Lo.ns, Lo.S, Lo.C,
                                                                            params, Lm, Lr, M, gck, lck, Gpart, grad);
