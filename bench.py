@@ -537,14 +537,14 @@ def extra_time_to_1e6_vs_d(torch, mdi, inputs, dims=(4, 6, 8, 10, 12, 16, 20, 24
 # is repeated.
 TRAFFIC_SOURCES = ["paper_2404_08867_gb300/csrc/mdi_nodes.cu", "paper_2404_08867_gb300/csrc/mdi_nodes.cuh",
                    "paper_2404_08867_gb300/csrc/mdi_common.cuh", "paper_2404_08867_gb300/csrc/mdi_fp64.cuh"]
-PROFILED_TRAFFIC = {"fp64": ("17fe4096f9049691", 1703424), "df64": ("17fe4096f9049691", 1754112)}
+PROFILED_TRAFFIC = {"fp64": ("06e548c0a4bc3142", 1703680), "df64": ("06e548c0a4bc3142", 1753856)}
 # The same captures' pipe utilisation (fractions of peak over the SMs' active
 # cycles, or the elapsed time where stated), under the same key: the FP64 mode is
 # bound by the FP64 pipe, the double-float mode by instruction issue.
 PROFILED_PIPE = {
-    "fp64": ("17fe4096f9049691", {"fp64_pipe_active": 0.911, "fp64_pipe_elapsed": 0.875,
+    "fp64": ("06e548c0a4bc3142", {"fp64_pipe_active": 0.912, "fp64_pipe_elapsed": 0.882,
                                   "metric": "sm__inst_executed_pipe_fp64"}),
-    "df64": ("17fe4096f9049691", {"issue_active": 0.638, "fma_pipe_active": 0.532,
+    "df64": ("06e548c0a4bc3142", {"issue_active": 0.637, "fma_pipe_active": 0.533,
                                   "metric": "smsp__issue_active, sm__pipe_fma_cycles_active"}),
 }
 
