@@ -14,16 +14,18 @@
 // GB300 mapping (instead of walking the levels one by one on one SM):
 //   K0  basis table l_t(u_qp) of this a (a*P*P entries).
 //   K1  every M_k (and w) at once, one CTA per level, across the whole GPU.
-//   K2  the levels are cut into groups of C (the checkpoint interval); one CTA
-//       per group multiplies its operators, R_g = M_top ... M_{gC+1}, so the
-//       P^3-per-level work runs on many SMs at once.
+//   K2  the levels are cut into groups of C (the checkpoint interval); the
+//       group products R_g = M_top ... M_{gC+1} are formed on many SMs at once,
+//       in two stages of about sqrt(C) operators when C >= 8 (and, for the
+//       value alone with 16 or more groups, a third stage over the groups).
 //   K3  one CTA runs the short chain over the groups forward (G at every group
 //       boundary -- the checkpoints -- and the value) and, for the adjoint,
 //       backward: lambda_{d-1} = front * w, lambda_{gC} = lambda_{top} R_g
 //       (lambda_k = dQ/dG_k).  The sequential part is ceil((d-1)/C) steps, not d.
-//   K4  (adjoint) one CTA per level k recomputes G_{k-1} from the checkpoint
-//       below and lambda_k from the checkpoint above -- the level states are not
-//       all stored -- and contracts
+//   K4  (adjoint) each CTA takes a block of consecutive levels of one group,
+//       recomputes their G_{k-1} from the checkpoint below and lambda_k from the
+//       checkpoint above once for the block -- the level states are not all
+//       stored -- and contracts
 //           dQ/dtheta_k = lambda_k (dM_k/dtheta_k) G_{k-1}
 //                       = (1/a) sum_{q,p} lambda_k[p] dphi_k(u_qp)/dtheta G~_{k-1}(u_qp),
 //       theta_k = (c_k, w_k); level d uses the points s/n_last.  For OSC the
